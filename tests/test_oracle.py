@@ -1,0 +1,338 @@
+"""Pins for the CPU oracle (no GPU).  Each test checks the oracle against
+something other than itself: the plain definition of the result (sorted order,
+computed by numpy on the total-order integer keys), published constants,
+closed forms and hand-worked examples of Alg. 1 / Alg. 2."""
+import itertools
+import math
+import struct
+
+import numpy as np
+import pytest
+
+import lsgen
+import oracle
+from conftest import read_golden
+
+
+def tk_numpy(a: np.ndarray) -> np.ndarray:
+    """Total-order integer key computed with numpy bit ops (independent of the oracle)."""
+    if a.dtype == np.float64:
+        u = a.view(np.uint64)
+        neg = (u >> np.uint64(63)) != 0
+        return np.where(neg, ~u, u | np.uint64(1 << 63))
+    if a.dtype == np.float32:
+        u = a.view(np.uint32).astype(np.uint64)
+        neg = (u >> np.uint64(31)) != 0
+        return np.where(neg, (~u) & np.uint64(0xFFFFFFFF), u | np.uint64(0x80000000))
+    return a.astype(np.uint64)
+
+
+def assert_sorted_permutation(out: np.ndarray, inp: np.ndarray):
+    """Invariants: non-decreasing by total order; same multiset of bit patterns."""
+    t_out, t_in = tk_numpy(out), tk_numpy(inp)
+    assert np.all(t_out[1:] >= t_out[:-1]), "not non-decreasing"
+    assert np.array_equal(t_out, np.sort(t_in)), "not a permutation of the input"
+
+
+def test_default_params_match_paper():
+    g = {r[0]: int(r[1]) for r in read_golden("paper_params.txt")}
+    p = oracle.params()
+    assert p.leaves == g["leaves"]
+    assert p.fanout == g["fanout"]
+    assert p.frag_cap == g["frag_cap"]
+    assert 100 // p.sample_div == g["sample_percent"]
+
+
+@pytest.mark.parametrize("fname,dt,fmt", [("total_order_f64.txt", np.float64, "<Q"),
+                                          ("total_order_f32.txt", np.float32, "<I")])
+def test_total_order_golden(fname, dt, fmt):
+    rows = read_golden(fname)
+    bits = [int(r[0], 16) for r in rows]
+    keys = np.array([struct.unpack("<d" if dt == np.float64 else "<f",
+                                   struct.pack(fmt, b))[0] for b in bits], dtype=dt)
+    tk = oracle.total_order_keys(keys)
+    assert np.all(tk[1:] > tk[:-1])
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        perm = rng.permutation(len(keys))
+        got = oracle.reference_sort(keys[perm])
+        assert got.view(np.uint64 if dt == np.float64 else np.uint32).tolist() == bits
+        got2 = oracle.learned_sort(keys[perm], oracle.params(n_small=0, fanout=4, leaves=2))
+        assert got2.view(np.uint64 if dt == np.float64 else np.uint32).tolist() == bits
+
+
+def test_splitmix64_published_vector():
+    g = {r[0]: int(r[1], 16) for r in read_golden("splitmix64.txt")}
+    # s = 1 sample over n = 2^63 keys: offset = mix64(seed ^ 0) mod 2^63.
+    assert int(oracle.sample_indices(1 << 63, 1, 0)[0]) == g["output0"] % (1 << 63)
+    # the second output of the generator is mix64 of its second state
+    st = 0x9E3779B97F4A7C15
+    assert int(oracle.sample_indices(1 << 63, 1, st)[0]) == g["output1"] % (1 << 63)
+
+
+@pytest.mark.parametrize("n,s", [(1000, 10), (1000, 1000), (12345, 678), (10**9, 10**5),
+                                 (7, 3), (1, 1)])
+def test_sample_indices_stratified(n, s):
+    idx = oracle.sample_indices(n, s, 7).astype(np.int64)
+    k = np.arange(s, dtype=object)
+    lo = np.array([kk * n // s for kk in k], dtype=np.int64)
+    stride = max(1, n // s)
+    assert np.all(idx >= lo) and np.all(idx < lo + stride)
+    assert np.all(idx < n) and np.all(np.diff(idx) > 0)
+    if s == n:
+        assert np.array_equal(idx, np.arange(n))
+
+
+def test_sample_size_rule():
+    p = oracle.params()
+    assert oracle.sample_size(1_000_000, p) == 10_000          # 1% (Sec. 5.1)
+    assert oracle.sample_size(200_000_000, p) == 2_000_000
+    assert oracle.sample_size(1000, p) == 1000                 # at least min(n, 2L)
+    assert oracle.sample_size(0, p) == 0
+    assert oracle.sample_size(10**9, oracle.params(sample_max=12345)) == 12345
+
+
+def test_fit_closed_form_line():
+    # keys 0..m-1: eCDF y_k = k/m, so least squares is exact: slope 1/m.
+    m = 4096
+    xs = np.arange(m, dtype=np.float64)
+    fm = oracle.fit_sorted(xs, 1)
+    a, c, b = fm.root
+    assert a == pytest.approx(1.0 / m, rel=1e-12)
+    assert c == pytest.approx((m - 1) / 2, rel=1e-12)
+    assert b == pytest.approx((m - 1) / (2 * m), rel=1e-12)
+    la, lc, lb, lo, hi = fm.leaf[0]
+    assert la == pytest.approx(1.0 / m, rel=1e-12)
+    assert (lo, hi) == (0.0, 1.0)
+    # L leaves over a uniform grid: leaf l holds keys [l k, (l+1) k).
+    L = 16
+    fm = oracle.fit_sorted(xs, L)
+    k = m // L
+    for l in range(L):
+        la, lc, lb, lo, hi = fm.leaf[l]
+        assert la == pytest.approx(1.0 / m, rel=1e-9)
+        assert lc == pytest.approx(l * k + (k - 1) / 2, rel=1e-12)
+        assert lo == pytest.approx(l / L, abs=1e-15)
+        assert hi == pytest.approx((l + 1) / L, abs=1e-15)
+        # F reproduces the eCDF at every key of the leaf
+        for x in (l * k, l * k + k // 2, (l + 1) * k - 1):
+            assert fm.predict(float(x)) == pytest.approx(x / m, abs=1e-12)
+
+
+def test_fit_closed_form_degenerate():
+    fm = oracle.fit_sorted(np.full(100, 3.5), 4)          # all equal: eCDF 0 everywhere
+    assert fm.root[0] == 0.0 and fm.root[2] == 0.0
+    assert fm.predict(3.5) == 0.0
+    fm = oracle.fit_sorted(np.array([0.0] * 50 + [1.0] * 50), 1)   # two values
+    a, c, b = fm.root
+    assert a == pytest.approx(0.5) and c == pytest.approx(0.5) and b == pytest.approx(0.25)
+    assert fm.predict(0.0) == pytest.approx(0.0) and fm.predict(1.0) == pytest.approx(0.5)
+    fm = oracle.fit_sorted(np.zeros(0), 8)                 # no finite sample
+    assert 0.0 <= fm.predict(1.0) <= 1.0
+
+
+@pytest.mark.parametrize("gen", ["normal", "zipf", "mix", "uniform_u64"])
+def test_model_monotone_and_bounded(gen):
+    n = 200_000
+    a = {"normal": lambda: lsgen.normal_f64(n, 11),
+         "zipf": lambda: lsgen.zipf_lognormal_f64(n, 12, k=1000),
+         "mix": lambda: lsgen.gauss_mix_f64(n, 13),
+         "uniform_u64": lambda: lsgen.uniform_u64(n, 14).astype(np.float64)}[gen]()
+    fm = oracle.train(a, oracle.params(leaves=256))
+    xs = np.sort(np.concatenate([a[:5000], [-np.inf, np.inf, -1e300, 1e300, 0.0, -0.0]]))
+    F = np.array([fm.predict(float(x)) for x in xs])
+    assert np.all(F >= 0) and np.all(F <= 1)
+    assert np.all(np.diff(F) >= 0)
+    # across every leaf boundary
+    for l in range(1, 256):
+        c = fm.leaf[l][1]
+        if fm.leaf[l][0] == 0:
+            continue
+        x0 = np.nextafter(c, -np.inf)
+        assert fm.predict(float(x0)) <= fm.predict(float(c)) <= fm.predict(float(np.nextafter(c, np.inf)))
+
+
+def test_partition_worked_example():
+    g = {r[0]: r[1:] for r in read_golden("partition_example.txt")}
+    inp = np.array([float(v) for v in g["input"]])
+    fm = oracle.FittedModel(1)
+    fm.m.root[0], fm.m.root[1], fm.m.root[2] = 0.0, 0.0, 0.0      # all keys to leaf 0
+    fm.leaf[0] = [1.0, 0.0, 0.0, 0.0, 1.0]                         # F(x) = x
+    after, sizes, owners, fsz = oracle.partition(inp, fm, 0, 4, 2)
+    assert after.tolist() == [float(v) for v in g["after_partition"]]
+    assert sizes.tolist() == [int(v) for v in g["bucket_sizes"]]
+    frags = [tuple(int(t) for t in v.split(":")) for v in g["fragments"]]
+    assert list(zip(owners.tolist(), fsz.tolist())) == frags
+    dfr = oracle.defragment(after, 4, sizes, owners, fsz)
+    assert dfr.tolist() == [float(v) for v in g["after_defragment"]]
+
+
+def test_partition_invariants():
+    n, f, c = 50_000, 64, 100
+    a = lsgen.normal_f64(n, 21)
+    fm = oracle.train(a, oracle.params(leaves=128))
+    after, sizes, owners, fsz = oracle.partition(a, fm, 0, f, c)
+    assert int(sizes.sum()) == n and int(fsz.sum()) == n
+    nfull = len(owners) - f
+    assert np.all(fsz[:nfull] == c)            # flushed inside the loop: exactly c
+    assert np.all(fsz[nfull:] < c)             # leftovers: one per bucket, < c
+    assert owners[nfull:].tolist() == list(range(f))
+    bucket = lambda x: min(f - 1, max(0, math.floor(fm.predict(float(x)) * f)))
+    pos = 0
+    for o, s in zip(owners.tolist(), fsz.tolist()):
+        assert all(bucket(x) == o for x in after[pos:pos + s])
+        pos += s
+    dfr = oracle.defragment(after, f, sizes, owners, fsz)
+    starts = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    expect = np.array([bucket(x) for x in a])
+    for i in range(f):
+        seg = dfr[starts[i]:starts[i + 1]]
+        assert np.array_equal(np.sort(seg), np.sort(a[expect == i]))
+    # level 1 with the monotone model: sub-buckets of bucket i are ordered
+    i = int(np.argmax(sizes))
+    seg = dfr[starts[i]:starts[i + 1]]
+    after1, sizes1, own1, fsz1 = oracle.partition(seg, fm, 1, f, c, parent=i)
+    d1 = oracle.defragment(after1, f, sizes1, own1, fsz1)
+    st1 = np.concatenate([[0], np.cumsum(sizes1)]).astype(np.int64)
+    nonempty = [j for j in range(f) if sizes1[j]]
+    for j0, j1 in zip(nonempty, nonempty[1:]):
+        assert d1[st1[j0]:st1[j0 + 1]].max() <= d1[st1[j1]:st1[j1 + 1]].min()
+
+
+def _inputs():
+    n = 60_000
+    rng = np.random.default_rng(5)
+    yield "normal", lsgen.normal_f64(n, 1)
+    yield "uniform", lsgen.uniform_f64(n, 2)
+    yield "zipf_lognormal", lsgen.zipf_lognormal_f64(n, 3, k=2000)
+    yield "gauss_mix", lsgen.gauss_mix_f64(n, 4)
+    yield "u64", lsgen.uniform_u64(n, 5)
+    yield "u32_timestamp", lsgen.timestamp_u32(n, 6)
+    yield "f32_exponential", lsgen.exponential_f32(n, 7)
+    yield "rootdups", lsgen.rootdups_f64(n)
+    yield "twodups", lsgen.twodups_f64(n)
+    yield "sorted", np.sort(lsgen.normal_f64(n, 8))
+    yield "reverse", np.sort(lsgen.normal_f64(n, 9))[::-1].copy()
+    yield "all_equal", np.full(n, 2.5)
+    yield "two_values", rng.choice([1.0, 7.0], n)
+    yield "signed_zeros", rng.choice([-0.0, 0.0], n)
+    heavy = np.full(n, 42.0)
+    heavy[rng.integers(0, n, 3)] = rng.normal(size=3)
+    yield "one_heavy_99.99", heavy
+    yield "u32_small_range", lsgen.uniform_u32(n, 10, bits=4)
+    yield "f32_specials", rng.choice(np.array([-np.inf, -1.0, -0.0, 0.0, 1e-45, 3.0, np.inf],
+                                              np.float32), n)
+
+
+@pytest.mark.parametrize("name,keys", list(_inputs()), ids=[x[0] for x in _inputs()])
+@pytest.mark.parametrize("cfg", [dict(), dict(fanout=16, leaves=8, frag_cap=4, n_small=0)],
+                         ids=["paper", "small_fanout"])
+def test_learned_sort_equals_definition(name, keys, cfg):
+    out = oracle.learned_sort(keys, oracle.params(**cfg))
+    assert_sorted_permutation(out, keys)
+    ref = oracle.reference_sort(keys)
+    assert np.array_equal(out.view(np.uint8), ref.view(np.uint8))
+
+
+def test_reference_sort_is_numpy_sort():
+    for a in (lsgen.normal_f64(10_000, 3), lsgen.uniform_u64(10_000, 4),
+              lsgen.exponential_f32(10_000, 5)):
+        out = oracle.reference_sort(a)
+        assert np.array_equal(tk_numpy(out), np.sort(tk_numpy(a)))
+
+
+F64_SPECIALS = [-np.inf, -1.0, -0.0, 0.0, 1.0, 1.0, 2.0, np.inf, 5e-324, 1.7976931348623157e308]
+
+
+@pytest.mark.parametrize("vals,dt", [
+    (F64_SPECIALS[:8], np.float64),
+    ([F64_SPECIALS[i] for i in (1, 2, 3, 8, 9, 4, 4, 0)], np.float64),
+    ([0, 2**32 - 1, 5, 5, 0, 7, 2**31, 1], np.uint32),
+    ([0, 2**64 - 1, 2**63, 3, 3, 3, 2**63 - 1, 12], np.uint64),
+    ([-np.inf, -0.0, 0.0, 1e-45, 1.0, np.inf, np.nan, -np.nan], np.float32),
+])
+def test_exhaustive_permutations(vals, dt):
+    """Every permutation of an 8-key multiset; the model path is forced (n_small = 0)."""
+    base = np.array(vals, dtype=dt)
+    expect = oracle.reference_sort(base)
+    assert np.array_equal(tk_numpy(expect), np.sort(tk_numpy(base)))
+    p = oracle.params(n_small=0, fanout=4, leaves=2, frag_cap=2)
+    seen = set()
+    for perm in itertools.permutations(range(len(base))):
+        key = tuple(base[list(perm)].view(np.uint8).tolist())
+        if key in seen:
+            continue
+        seen.add(key)
+        out = oracle.learned_sort(base[list(perm)], p)
+        assert np.array_equal(out.view(np.uint8), expect.view(np.uint8)), perm
+
+
+def test_tiny_sizes():
+    p = oracle.params(n_small=0)
+    for n in range(0, 20):
+        a = lsgen.normal_f64(n, 100 + n) if n else np.zeros(0)
+        out = oracle.learned_sort(a, p)
+        assert np.array_equal(out, oracle.reference_sort(a))
+
+
+def test_model_quality_bounds_touch_up_work():
+    """A wrong fit (dropped term, wrong sign) still sorts -- the insertion sort
+    fixes it -- but leaves far more work to the touch-up.  Bound that work."""
+    a = lsgen.uniform_f64(400_000, 31)
+    out, tr = oracle.learned_sort(a, trace=True)
+    assert tr["insertion_moves"] < 40 * a.size
+    assert tr["max_bucket"] < 4 * a.size / 1000
+    assert tr["sample_size"] == 4000 and tr["l1_partitions"] > 900
+
+
+# --------------------------------------------------------------------- spec functions
+def test_spec_fixed_point_closed_forms():
+    f = lambda v, E, dt=np.float64: int(oracle.spec_fixed_point(np.array([v], dt), E)[0])
+    assert f(1.0, 0) == 1
+    assert f(-1.5, 0) == -2                  # floor
+    assert f(0.75, -2) == 3
+    assert f(-0.75, -2) == -3
+    assert f(-0.0, 0) == 0 and f(0.0, 5) == 0
+    assert f(2.0 ** 70, 0) == 2 ** 62        # saturates
+    assert f(-np.inf, 0) == -(2 ** 62) and f(np.inf, 0) == 2 ** 62
+    assert f(5e-324, -1074) == 1
+    assert f(5e-324, -1073) == 0             # floor(1/2)
+    assert f(-5e-324, -1073) == -1
+    assert f(2 ** 64 - 1, 3, np.uint64) == 2 ** 61 - 1
+    assert f(7, -2, np.uint32) == 28
+    assert f(1.5, -1, np.float32) == 3
+    assert f(-1e-45, -149, np.float32) == -1
+
+
+def _eval_for(a, L=128):
+    fm = oracle.train(a, oracle.params(leaves=L))
+    smp = a[oracle.sample_indices(a.size, oracle.sample_size(a.size, oracle.params(leaves=L)))
+            .astype(np.int64)].astype(np.float64)
+    smp = np.sort(smp[np.isfinite(smp)])
+    return fm, smp, oracle.spec_eval_params(fm, smp, "f64")
+
+
+def test_spec_F_monotone_and_close_to_fp64():
+    a = lsgen.normal_f64(100_000, 41)
+    fm, smp, ev = _eval_for(a)
+    xs = np.sort(a[:4000])
+    F32 = oracle.spec_F(ev, xs)
+    assert np.all(np.diff(F32) >= 0)
+    F64 = np.array([fm.predict(float(x)) for x in xs])
+    # the FP32 feature path tracks the FP64 model except next to leaf edges
+    assert np.median(np.abs(F32 - F64)) < 1e-5
+    b = oracle.spec_buckets(ev, xs, 1000)
+    assert np.all(np.diff(b.astype(np.int64)) >= 0)
+
+
+def test_spec_heavy_and_ext_histogram():
+    keys = np.array([1.0] * 5 + [2.0] + [3.0] * 3 + [4.0] * 4, np.float64)
+    fm = oracle.fit_sorted(keys, 2)
+    ev = oracle.spec_eval_params(fm, keys, "f64")
+    h = oracle.spec_heavy(keys, 3, 8, ev, 4)
+    assert h.tolist() == oracle.total_order_keys(np.array([1.0, 3.0, 4.0])).tolist()
+    h1 = oracle.spec_heavy(keys, 3, 1, ev, 1)          # one bucket, keep the longest run
+    assert h1.tolist() == oracle.total_order_keys(np.array([1.0])).tolist()
+    hist = oracle.spec_ext_histogram(ev, keys, 1, h)
+    # one bucket owning heavies 1 < 3 < 4: slots <1, =1, (1,3), =3, (3,4), =4, >4
+    assert hist.tolist() == [0, 5, 1, 3, 0, 4, 0]
