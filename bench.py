@@ -1,0 +1,308 @@
+"""Benchmark of the GB300 learned sort (one JSON line on stdout, rank 0).
+
+Default workload: 200,000,000 float64 keys, each one of 100,000 distinct
+lognormal(0,2) values chosen by Zipf(1.1) rank (the high-duplicate plain
+single-array sort), seed 1.  A step is one full ls_sort of the workload
+(train, level 0, level 1, in-bucket sorts), inputs resident in HBM; the input
+is restored from a pristine device copy before every step, outside the timed
+interval.  The inputs (1.6 GB) are larger than the 129 MB L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--n N]
+
+--impl reference times the CPU oracle (test infrastructure) on bounded samples
+of the same workload on the host cores.  Multi-GPU runs are independent
+replicas (the sort does not shard across GPUs here): every rank sorts its own
+copy; value = keys over all ranks / max time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lsgen  # noqa: E402
+
+METRIC = "keys/s & HBM GB/s vs roofline, 1 GB300; batched/served vs plain; p50/p99 ms"
+NPT = {"f64": np.float64, "u64": np.uint64, "f32": np.float32, "u32": np.uint32}
+WIDTH = {"f64": 8, "u64": 8, "f32": 4, "u32": 4}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def kernel_algorithmic_bytes(st: dict, n: int, w: int) -> dict:
+    """Algorithmic bytes per launch of each timed kernel."""
+    eq = st["n_eq_keys"]
+    return {
+        "k_l0_hist": n * w,                        # read every key once
+        "k_l0_scatter": n * w + (n - eq) * w,      # read every key, write non-equality keys
+        "k_bucket_sort": None,                     # reported through the whole-sort figure
+    }
+
+
+def traffic_for(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current source of the kernel (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(f"{kernel}@{workload}")
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_2107_03290_gb300", "csrc", e["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return e["bytes_per_launch"] if h == e["source_sha"] else None
+
+
+def make_workload(name: str, n: int):
+    dt, n0, fn = lsgen.WORKLOADS[name]
+    return dt, fn(n if n else n0)
+
+
+def run_reference(args, rank: int):
+    import oracle
+    if rank != 0:
+        return
+    dt, keys = make_workload(args.workload, args.n)
+    sample = min(keys.size, args.ref_sample)
+    # warmup + timed steps, each a bounded sample of the workload
+    for i in range(args.warmup):
+        oracle.learned_sort(keys[:sample])
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle.learned_sort(keys[:sample])
+    t = time.perf_counter() - t0
+    v = sample * args.steps / t
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "keys/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1000 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": dt, "data": "synthetic",
+           "config": {"workload": args.workload, "n": int(keys.size), "dtype": dt},
+           "cpu_baseline": {"value": v, "unit": "keys/s", "cores": 1, "kind": "oracle",
+                            "sample": f"first {sample} keys of the workload per step"},
+           "e2e": {"value": v, "unit": "keys/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="zipf_lognormal_200m_f64", choices=list(lsgen.WORKLOADS))
+    ap.add_argument("--n", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=10_000_000)
+    ap.add_argument("--ref-sample", type=int, default=2_000_000)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import paper_2107_03290_gb300 as ls
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    ls.build()
+    ls.load()
+
+    dt, keys = make_workload(args.workload, args.n)
+    n = keys.size
+    w = WIDTH[dt]
+    host = torch.from_numpy(keys).pin_memory()
+    pristine = host.to("cuda", non_blocking=True)
+    work = torch.empty_like(pristine)
+    stream = torch.cuda.current_stream()
+
+    def step(stats=True):
+        work.copy_(pristine)
+        return ls.sort_(work, stats=stats)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # correctness of the benchmarked path: sorted, same multiset (bit checksums)
+    res = work.cpu().numpy()
+    u = res.view(np.uint64 if w == 8 else np.uint32).astype(np.uint64)
+    if res.dtype.kind == "f":
+        sgn = np.uint64(1 << (8 * w - 1))
+        mask = np.uint64((1 << (8 * w)) - 1)
+        tk = np.where(u & sgn, (~u) & mask, u | sgn)
+    else:
+        tk = u
+    ok = bool(np.all(tk[1:] >= tk[:-1]))
+    ku = keys.view(np.uint64 if w == 8 else np.uint32).astype(np.uint64)
+    ok = ok and int(u.sum(dtype=np.uint64)) == int(ku.sum(dtype=np.uint64))
+    del res, u, tk, ku
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    per = []
+    launches = 0
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            st = step()
+            per.append(st)
+            launches += st["n_launches"]
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if dist:
+            dist.barrier()
+    dev_ms = float(np.mean([s["ms_total"] for s in per]))
+    tmax = dev_ms
+    if dist:
+        tt = torch.tensor([dev_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tmax = float(tt.item())
+    value = n * world / (tmax / 1000.0)
+
+    # per-kernel times and the roofline of the dominant kernel
+    ks = ["ms_train", "ms_hist", "ms_scan", "ms_scatter", "ms_classify", "ms_level1", "ms_fill",
+          "ms_sort_small", "ms_sort_large", "ms_fallback"]
+    kms = {k: float(np.mean([s[k] for s in per])) for k in ks}
+    peak, peak_kind = load_peaks()
+    names = {"ms_hist": "k_l0_hist", "ms_scatter": "k_l0_scatter"}
+    alg = kernel_algorithmic_bytes(per[-1], n, w)
+    dom = max(("ms_hist", "ms_scatter"), key=lambda k: kms[k])
+    kname = names[dom]
+    ach = alg[kname] / (kms[dom] / 1e3) / 1e9
+    whole = 4 * n * w / (dev_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": kname, "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "peak_kind": peak_kind,
+            "traffic": traffic_for(kname, args.workload),
+            "share": kms[dom] / dev_ms,
+            "sort_4nw": {"achieved": whole, "frac": whole / peak,
+                         "note": "4*n*w bytes (2-pass read+write) / whole-sort time"}}
+
+    # end to end through ls_sort_host: pinned host buffer, copies timed
+    e2e = None
+    if args.e2e_steps > 0:
+        hb = torch.empty_like(host).pin_memory()
+        ptr, code = hb.data_ptr(), {"f64": 0, "u64": 1, "f32": 2, "u32": 3}[dt]
+        hb.copy_(host)
+        ls.sort_host_ptr(ptr, n, code)
+        tot = 0.0
+        for _ in range(args.e2e_steps):
+            hb.copy_(host)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            ls.sort_host_ptr(ptr, n, code)
+            tot += time.perf_counter() - t1
+        e2e = {"value": n * world / (tot / args.e2e_steps), "unit": "keys/s",
+               "h2d_bytes_per_step": n * w, "d2h_bytes_per_step": n * w}
+        del hb
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        smp = min(n, args.cpu_sample)
+        t1 = time.perf_counter()
+        oracle.learned_sort(keys[:smp])
+        tc = time.perf_counter() - t1
+        cpu = {"value": smp / tc, "unit": "keys/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {smp} keys of the workload, one oracle LearnedSort 2.0 call"}
+
+    if rank == 0:
+        last = per[-1]
+        out = {"metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dt,
+               "data": "synthetic",
+               "config": {"workload": args.workload, "n": n, "dtype": dt,
+                          "l2": "inputs larger than L2 (restored from a device copy each step)",
+                          "parallelism": "replicas" if world > 1 else "single"},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": int(launches), "clocks": clk.summary(),
+               "wall_ms_per_step": 1000 * wall / args.steps, "correct": ok,
+               "kernels_ms": kms,
+               "path": {k: last[k] for k in ("n_heavy", "n_ext", "max_bucket", "n_eq_keys",
+                                             "n_level1", "n_segments", "n_fallback", "n_fill",
+                                             "n_launches", "sample_size")}}
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

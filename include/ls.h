@@ -1,0 +1,193 @@
+/* ls.h -- C ABI of the GB300 learned sort (LearnedSort 2.0 hot path).
+ *
+ * The method is LearnedSort 2.0 (Kristo, Vaidya, Kraska, arXiv 2107.03290):
+ * a two-layer RMI of linear models predicts each key's scaled eCDF (Sec. 2);
+ * keys are partitioned into fan-out buckets over two levels (Alg. 1, Alg. 2);
+ * each bucket is finished by a model-based counting sort and an insertion-sort
+ * touch-up (Alg. 2).  Heavily repeated keys get equality buckets (the
+ * duplicate-handling device of Sec. 4.1, used here inside the partition).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named `keys` are DEVICE pointers unless the name says `host`.
+ *    The caller owns them; they must stay valid until the stream work ends.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls enqueue work and return without waiting unless stated otherwise.
+ *  - Key order (the ordering contract): ascending IEEE 754 totalOrder for
+ *    floats (-NaN < -inf < ... < -0.0 < +0.0 < ... < +inf < +NaN), unsigned
+ *    order for integers.  The sorted output is therefore unique.
+ *  - Synchronous errors (bad arguments, allocation failure, launch failure) are
+ *    returned.  Asynchronous device errors (a bounded wait that timed out) are
+ *    recorded in a per-device status word and returned by the next
+ *    ls_stream_status() call.  After an error the key contents are unspecified.
+ *  - Thread safety: calls on different streams may run concurrently; the
+ *    library's scratch memory is stream-ordered.
+ */
+#ifndef LS_H
+#define LS_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { LS_F64 = 0, LS_U64 = 1, LS_F32 = 2, LS_U32 = 3 } ls_dtype;
+
+typedef enum {
+  LS_OK = 0,
+  LS_ERR_INVALID = 1,   /* bad argument                                        */
+  LS_ERR_NOMEM = 2,     /* device or pinned-host allocation failed             */
+  LS_ERR_CUDA = 3,      /* CUDA runtime error (launch, copy, ...)              */
+  LS_ERR_TIMEOUT = 4,   /* a bounded device wait gave up (asynchronous)        */
+  LS_ERR_BUSY = 5,      /* server: admission refused (HBM budget / queue full) */
+  LS_ERR_CANCELLED = 6  /* server: request cancelled or server shut down       */
+} ls_status;
+
+/* Tuning parameters.  Zero fields take the defaults (ls_default_params). */
+typedef struct ls_params {
+  uint32_t fanout;           /* level-0 buckets f (Sec. 5.1 default 1000)              */
+  uint32_t leaves;           /* RMI leaves L (Sec. 5.1: 1000)                          */
+  uint32_t sample_div;       /* sample s = ceil(n / sample_div) (Sec. 5.1: 1% -> 100)  */
+  uint32_t heavy_per_bucket; /* max equality buckets inside one level-0 bucket         */
+  uint64_t sample_max;       /* cap on s (0: none)                                     */
+  uint64_t seed;             /* seed of the stratified sample offsets                  */
+  uint64_t heavy_min_count;  /* a key is heavy if its expected count >= this           */
+  uint32_t flags;            /* LS_FLAG_*                                              */
+  uint32_t reserved[7];
+} ls_params;
+
+#define LS_FLAG_NO_HEAVY 1u  /* disable equality buckets                                */
+
+/* Per-call statistics.  Passing a non-NULL ls_stats makes the call record CUDA
+ * events and synchronize the stream before returning. */
+typedef struct ls_stats {
+  double ms_total;           /* device time of the whole call                 */
+  double ms_train;           /* sample + sort sample + fit + heavy set        */
+  double ms_hist;            /* level-0 histogram (K2)                        */
+  double ms_scan;            /* level-0 look-back scan (K3)                   */
+  double ms_scatter;         /* level-0 scatter (K4)                          */
+  double ms_classify;        /* level-0 slot classification                   */
+  double ms_level1;          /* level-1 re-partition of oversized slots       */
+  double ms_fill;            /* equality / homogeneous fills                  */
+  double ms_sort_small;      /* in-bucket counting sort, segments <= 2048     */
+  double ms_sort_large;      /* in-bucket counting sort, segments <= 8192     */
+  double ms_fallback;        /* radix fallback for unsplittable segments      */
+  uint64_t sample_size;      /* s                                             */
+  uint64_t sample_finite;    /* finite keys in the sample                     */
+  uint32_t fanout, leaves;
+  uint64_t n_heavy;          /* equality buckets                              */
+  uint64_t n_ext;            /* level-0 slots (buckets + equality splits)     */
+  uint64_t max_bucket;       /* largest level-0 slot that is not an equality  */
+  uint64_t n_eq_keys;        /* keys placed by equality buckets               */
+  uint64_t n_level1;         /* slots re-partitioned at level 1               */
+  uint64_t n_segments;       /* segments finished by the counting sort        */
+  uint64_t n_fallback;       /* segments finished by the radix fallback       */
+  uint64_t n_fill;           /* fill jobs (equality + homogeneous segments)   */
+  uint64_t n_launches;       /* kernels this call launched                    */
+  uint64_t reserved[4];
+} ls_stats;
+
+/* Model export for parity checks (host buffers owned by the caller). */
+typedef struct ls_model_export {
+  uint32_t leaves;           /* in: capacity of the per-leaf arrays (>= L)    */
+  uint32_t max_heavy;        /* in: capacity of heavy_tk                      */
+  uint64_t sample_size;      /* out */
+  uint64_t sample_finite;    /* out */
+  double root[3];            /* out: a, c, b (root(x) = a (x - c) + b)        */
+  double* leaf;              /* out: 5 per leaf: a, c, b, lo, hi (FP64 fit)   */
+  int32_t E;                 /* out: fixed-point exponent                     */
+  int32_t root_sh;           /* out */
+  int64_t root_cq;           /* out */
+  float root_A, root_B;      /* out */
+  int64_t* cq;               /* out: per leaf */
+  int32_t* sh;               /* out: per leaf */
+  float* A;                  /* out: per leaf */
+  float* B;
+  float* LO;
+  float* HI;
+  uint64_t* sorted_sample_tk;/* out (optional, NULL to skip): s total-order keys */
+  uint64_t* heavy_tk;        /* out: heavy values (total-order keys), ascending */
+  uint64_t n_heavy;          /* out */
+  uint64_t tau;              /* out: run-length threshold used for heavies     */
+} ls_model_export;
+
+void ls_default_params(ls_params* p);
+const char* ls_status_string(ls_status s);
+
+/* Sort `n` keys of `dtype` at device pointer `keys` in place on `stream`
+ * (Alg. 2 end to end).  n = 0 or 1 is a no-op.  Returns after enqueueing. */
+ls_status ls_sort(void* keys, size_t n, ls_dtype dtype, void* stream);
+
+/* ls_sort with explicit parameters (NULL: defaults) and optional statistics. */
+ls_status ls_sort_ex(void* keys, size_t n, ls_dtype dtype, void* stream,
+                     const ls_params* params, ls_stats* stats);
+
+/* End-to-end form: `host_keys` is HOST memory (pinned or pageable).  Copies the
+ * keys to the device, sorts them and copies them back; returns when the sorted
+ * keys are in `host_keys`. */
+ls_status ls_sort_host(void* host_keys, size_t n, ls_dtype dtype, void* stream,
+                       const ls_params* params);
+
+/* Sort `count` independent arrays (device pointers keys[i] with n[i] keys each;
+ * the two arrays `keys` and `n` are HOST arrays) in one batched launch
+ * sequence.  Arrays must not overlap. */
+ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dtype dtype,
+                        void* stream);
+
+/* Waits for `stream`, then returns and clears the device status word
+ * (LS_ERR_TIMEOUT if a bounded device wait gave up since the last call). */
+ls_status ls_stream_status(void* stream);
+
+/* Stage entry points (used by the kernel parity tests). */
+
+/* Train the RMI on the sample of `keys` (sample, sort, FP64 fit, FP32
+ * evaluation parameters, heavy set) and copy the model to `out` (host).
+ * Synchronizes `stream`. */
+ls_status ls_train(const void* keys, size_t n, ls_dtype dtype, void* stream,
+                   const ls_params* params, ls_model_export* out);
+
+/* Train, then run the level-0 histogram kernel; copies the per-slot key
+ * counts (n_ext entries, at most max_ext) to `hist_host`.  Synchronizes. */
+ls_status ls_level0_histogram(const void* keys, size_t n, ls_dtype dtype, void* stream,
+                              const ls_params* params, uint64_t* hist_host, size_t max_ext,
+                              size_t* n_ext);
+
+/* Sort `count` 64-bit unsigned keys at device pointer `keys` in place with
+ * the library's LSD radix sort (the sample sort of the training step). */
+ls_status ls_radix_sort_u64(uint64_t* keys, size_t count, void* stream);
+
+/* Kernels the library has enqueued since it was loaded (diagnostics). */
+uint64_t ls_kernel_launches(void);
+
+/* ---- serving: continuous batching of sort requests ---- */
+typedef struct ls_server ls_server;
+
+typedef struct ls_server_config {
+  uint64_t hbm_budget_bytes; /* admission limit on bytes of admitted requests  */
+  uint32_t max_inflight;     /* requests on the GPU at once (default 64)       */
+  uint32_t max_queue;        /* waiting requests before LS_ERR_BUSY (def 4096) */
+  uint32_t streams;          /* CUDA streams used for overlap (default 4)      */
+  uint32_t reserved[5];
+} ls_server_config;
+
+typedef struct ls_request_stats {
+  double queue_ms;           /* submit -> launch                              */
+  double device_ms;          /* launch -> completion event                    */
+  double total_ms;           /* submit -> completion                          */
+  ls_status status;
+} ls_request_stats;
+
+ls_status ls_server_create(const ls_server_config* cfg, ls_server** out);
+/* Submit a sort of device keys (sorted in place).  Returns LS_ERR_BUSY when the
+ * request exceeds the budget or the queue is full; *ticket identifies it. */
+ls_status ls_server_submit(ls_server* s, void* keys, size_t n, ls_dtype dtype,
+                           uint64_t* ticket);
+/* Wait up to timeout_ms for a ticket (UINT32_MAX: forever). */
+ls_status ls_server_wait(ls_server* s, uint64_t ticket, uint32_t timeout_ms,
+                         ls_request_stats* st);
+ls_status ls_server_destroy(ls_server* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LS_H */

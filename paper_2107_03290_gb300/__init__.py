@@ -1,0 +1,363 @@
+"""GB300 learned sort: the LearnedSort 2.0 hot path (arXiv 2107.03290) in CUDA.
+
+Thin ctypes binding over the C ABI of ``include/ls.h`` (``libls.so``, built
+in-tree by ``build()``).  Every step of the sort runs in the library's CUDA
+kernels; this module only marshals arguments.  PyTorch supplies device memory
+and streams.  There is no CPU fallback: if the library is missing or no GPU is
+present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_CSRC = os.path.join(_HERE, "csrc")
+_INC = os.path.join(os.path.dirname(_HERE), "include")
+_SO = os.path.join(_HERE, "libls.so")
+_BUILD = os.path.join(_HERE, "_build")
+SOURCES = ["ls_train.cu", "ls_partition.cu", "ls_bucket.cu", "ls_api.cu", "ls_server.cpp"]
+ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+
+DTYPE_CODES = {"f64": 0, "u64": 1, "f32": 2, "u32": 3}
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error",
+          4: "device wait timed out", 5: "busy", 6: "cancelled"}
+
+
+class LsError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        super().__init__(f"{what}: {STATUS.get(code, code)} ({code})")
+        self.code = code
+
+
+def _nvcc() -> str:
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if c and (os.path.sep not in c or os.path.exists(c)):
+            return c
+    return "nvcc"
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every CUDA/C++ source for sm_103a and link ``libls.so`` in-tree."""
+    os.makedirs(_BUILD, exist_ok=True)
+    hdrs = [os.path.join(_CSRC, f) for f in os.listdir(_CSRC) if f.endswith((".cuh", ".h"))]
+    hdrs.append(os.path.join(_INC, "ls.h"))
+    newest_hdr = max(os.path.getmtime(h) for h in hdrs)
+    objs, jobs = [], []
+    for src in SOURCES:
+        sp = os.path.join(_CSRC, src)
+        obj = os.path.join(_BUILD, src + ".o")
+        objs.append(obj)
+        if force or not os.path.exists(obj) or os.path.getmtime(obj) < max(
+                os.path.getmtime(sp), newest_hdr):
+            cmd = [_nvcc(), ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
+                   "-I", _INC, "-c", sp, "-o", obj]
+            if src.endswith(".cpp"):
+                cmd[1:1] = ["-x", "cu"]
+            jobs.append(cmd)
+
+    def run(cmd):
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("compile failed: " + " ".join(cmd) + "\n" + r.stdout + r.stderr)
+        if verbose:
+            print(r.stdout + r.stderr)
+
+    if jobs:
+        with ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+            list(ex.map(run, jobs))
+    if jobs or force or not os.path.exists(_SO):
+        tmp = _SO + f".tmp{os.getpid()}"
+        run([_nvcc(), ARCH, "-shared", "-o", tmp] + objs + ["-lcuda"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("fanout", ctypes.c_uint32), ("leaves", ctypes.c_uint32),
+                ("sample_div", ctypes.c_uint32), ("heavy_per_bucket", ctypes.c_uint32),
+                ("sample_max", ctypes.c_uint64), ("seed", ctypes.c_uint64),
+                ("heavy_min_count", ctypes.c_uint64), ("flags", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 7)]
+
+
+FLAG_NO_HEAVY = 1
+
+
+class Stats(ctypes.Structure):
+    _fields_ = ([(k, ctypes.c_double) for k in (
+        "ms_total", "ms_train", "ms_hist", "ms_scan", "ms_scatter", "ms_classify", "ms_level1",
+        "ms_fill", "ms_sort_small", "ms_sort_large", "ms_fallback")]
+                + [("sample_size", ctypes.c_uint64), ("sample_finite", ctypes.c_uint64),
+                   ("fanout", ctypes.c_uint32), ("leaves", ctypes.c_uint32)]
+                + [(k, ctypes.c_uint64) for k in ("n_heavy", "n_ext", "max_bucket", "n_eq_keys",
+                                                  "n_level1", "n_segments", "n_fallback",
+                                                  "n_fill", "n_launches")]
+                + [("reserved", ctypes.c_uint64 * 4)])
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class ModelExport(ctypes.Structure):
+    _fields_ = [("leaves", ctypes.c_uint32), ("max_heavy", ctypes.c_uint32),
+                ("sample_size", ctypes.c_uint64), ("sample_finite", ctypes.c_uint64),
+                ("root", ctypes.c_double * 3), ("leaf", ctypes.c_void_p),
+                ("E", ctypes.c_int32), ("root_sh", ctypes.c_int32), ("root_cq", ctypes.c_int64),
+                ("root_A", ctypes.c_float), ("root_B", ctypes.c_float),
+                ("cq", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("A", ctypes.c_void_p),
+                ("B", ctypes.c_void_p), ("LO", ctypes.c_void_p), ("HI", ctypes.c_void_p),
+                ("sorted_sample_tk", ctypes.c_void_p), ("heavy_tk", ctypes.c_void_p),
+                ("n_heavy", ctypes.c_uint64), ("tau", ctypes.c_uint64)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
+                ("max_queue", ctypes.c_uint32), ("streams", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 5)]
+
+
+class RequestStats(ctypes.Structure):
+    _fields_ = [("queue_ms", ctypes.c_double), ("device_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+EXPORTED = ["ls_default_params", "ls_status_string", "ls_sort", "ls_sort_ex", "ls_sort_host",
+            "ls_sort_batch", "ls_stream_status", "ls_train", "ls_level0_histogram",
+            "ls_radix_sort_u64", "ls_kernel_launches", "ls_server_create", "ls_server_submit", "ls_server_wait",
+            "ls_server_destroy"]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _SO
+
+
+def load(path: str | None = None):
+    """Load libls.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or _SO
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} not built: run paper_2107_03290_gb300.build()")
+        lib = ctypes.CDLL(p)
+        vp, sz, i32, u32, u64 = (ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint32,
+                                 ctypes.c_uint64)
+        P = ctypes.POINTER
+        lib.ls_default_params.argtypes = [P(Params)]
+        lib.ls_status_string.argtypes = [i32]
+        lib.ls_status_string.restype = ctypes.c_char_p
+        lib.ls_kernel_launches.argtypes = []
+        lib.ls_kernel_launches.restype = u64
+        for f, a in {
+            "ls_sort": [vp, sz, i32, vp],
+            "ls_sort_ex": [vp, sz, i32, vp, P(Params), P(Stats)],
+            "ls_sort_host": [vp, sz, i32, vp, P(Params)],
+            "ls_sort_batch": [vp, vp, sz, i32, vp],
+            "ls_stream_status": [vp],
+            "ls_train": [vp, sz, i32, vp, P(Params), P(ModelExport)],
+            "ls_level0_histogram": [vp, sz, i32, vp, P(Params), vp, sz, P(ctypes.c_size_t)],
+            "ls_radix_sort_u64": [vp, sz, vp],
+            "ls_server_create": [P(ServerConfig), P(vp)],
+            "ls_server_submit": [vp, vp, sz, i32, P(u64)],
+            "ls_server_wait": [vp, u64, u32, P(RequestStats)],
+            "ls_server_destroy": [vp],
+        }.items():
+            fn = getattr(lib, f)
+            fn.argtypes = a
+            fn.restype = i32
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise LsError(rc, what)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load().ls_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def dtype_code(t) -> int:
+    torch = _torch()
+    m = {torch.float64: 0, torch.uint64: 1, torch.float32: 2, torch.uint32: 3}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    return m[t.dtype]
+
+
+def _stream(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _device_tensor(t):
+    if not t.is_cuda:
+        raise ValueError("keys must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("keys must be contiguous")
+    return t
+
+
+def sort_(t, params: Params | None = None, stats: bool = False, stream=None):
+    """Sort a CUDA tensor in place (ls_sort_ex).  Returns stats dict if asked."""
+    t = _device_tensor(t)
+    st = Stats() if stats else None
+    rc = load().ls_sort_ex(t.data_ptr(), t.numel(), dtype_code(t), _stream(stream),
+                           ctypes.byref(params) if params is not None else None,
+                           ctypes.byref(st) if st is not None else None)
+    _check(rc, "ls_sort_ex")
+    return st.as_dict() if st is not None else None
+
+
+def sort(t, params: Params | None = None, stream=None):
+    """Return a sorted copy of a CUDA tensor."""
+    out = t.clone()
+    sort_(out, params, stream=stream)
+    return out
+
+
+def sort_host(a: np.ndarray, params: Params | None = None, stream=None) -> np.ndarray:
+    """End-to-end sort of a host array (copy in, sort, copy out); in place."""
+    codes = {np.dtype(np.float64): 0, np.dtype(np.uint64): 1, np.dtype(np.float32): 2,
+             np.dtype(np.uint32): 3}
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be contiguous")
+    rc = load().ls_sort_host(a.ctypes.data, a.size, codes[a.dtype], _stream(stream),
+                             ctypes.byref(params) if params is not None else None)
+    _check(rc, "ls_sort_host")
+    return a
+
+
+def sort_host_ptr(ptr: int, n: int, code: int, params: Params | None = None, stream=None):
+    rc = load().ls_sort_host(ptr, n, code, _stream(stream),
+                             ctypes.byref(params) if params is not None else None)
+    _check(rc, "ls_sort_host")
+
+
+def sort_batch_(tensors, stream=None):
+    """Sort many CUDA tensors of one dtype in place (ls_sort_batch)."""
+    if not tensors:
+        return
+    code = dtype_code(tensors[0])
+    ptrs = (ctypes.c_void_p * len(tensors))(*[_device_tensor(t).data_ptr() for t in tensors])
+    ns = (ctypes.c_size_t * len(tensors))(*[t.numel() for t in tensors])
+    rc = load().ls_sort_batch(ptrs, ns, len(tensors), code, _stream(stream))
+    _check(rc, "ls_sort_batch")
+
+
+def kernel_launches() -> int:
+    return load().ls_kernel_launches()
+
+
+def stream_status(stream=None) -> int:
+    return load().ls_stream_status(_stream(stream))
+
+
+def radix_sort_u64_(t, stream=None):
+    torch = _torch()
+    if t.dtype != torch.uint64:
+        raise TypeError("uint64 tensor expected")
+    _check(load().ls_radix_sort_u64(_device_tensor(t).data_ptr(), t.numel(), _stream(stream)),
+           "ls_radix_sort_u64")
+
+
+def train(t, params: Params | None = None, stream=None, with_sample: bool = False) -> dict:
+    """Run the training step only; returns the model as numpy arrays."""
+    t = _device_tensor(t)
+    p = params or default_params()
+    L = p.leaves or 1000
+    out = ModelExport()
+    out.leaves = L
+    arr = {"leaf": np.zeros((L, 5), np.float64), "cq": np.zeros(L, np.int64),
+           "sh": np.zeros(L, np.int32), "A": np.zeros(L, np.float32),
+           "B": np.zeros(L, np.float32), "LO": np.zeros(L, np.float32),
+           "HI": np.zeros(L, np.float32)}
+    heavy = np.zeros(8 * max(1, p.fanout or 1000), np.uint64)
+    out.max_heavy = heavy.size
+    for k, v in arr.items():
+        setattr(out, k, v.ctypes.data)
+    out.heavy_tk = heavy.ctypes.data
+    smp = None
+    if with_sample:
+        n = t.numel()
+        smp = np.zeros(max(1, n), np.uint64)
+        out.sorted_sample_tk = smp.ctypes.data
+    rc = load().ls_train(t.data_ptr(), t.numel(), dtype_code(t), _stream(stream), ctypes.byref(p),
+                         ctypes.byref(out))
+    _check(rc, "ls_train")
+    res = dict(arr)
+    res.update(sample_size=out.sample_size, sample_finite=out.sample_finite,
+               root=np.array(list(out.root)), E=out.E, root_sh=out.root_sh, root_cq=out.root_cq,
+               root_A=np.float32(out.root_A), root_B=np.float32(out.root_B),
+               heavy_tk=heavy[:out.n_heavy].copy(), tau=out.tau)
+    if smp is not None:
+        res["sorted_sample_tk"] = smp[:out.sample_size].copy()
+    return res
+
+
+def level0_histogram(t, params: Params | None = None, stream=None) -> np.ndarray:
+    t = _device_tensor(t)
+    p = params or default_params()
+    mx = (p.fanout or 1000) * 17 + 16
+    h = np.zeros(mx, np.uint64)
+    n_ext = ctypes.c_size_t(0)
+    rc = load().ls_level0_histogram(t.data_ptr(), t.numel(), dtype_code(t), _stream(stream),
+                                    ctypes.byref(p), h.ctypes.data, mx, ctypes.byref(n_ext))
+    _check(rc, "ls_level0_histogram")
+    return h[:n_ext.value].copy()
+
+
+class Server:
+    """Continuous-batching sort server (ls_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int = 120 << 30, max_inflight: int = 64,
+                 max_queue: int = 4096, streams: int = 4):
+        cfg = ServerConfig(hbm_budget_bytes, max_inflight, max_queue, streams)
+        self._h = ctypes.c_void_p()
+        _check(load().ls_server_create(ctypes.byref(cfg), ctypes.byref(self._h)),
+               "ls_server_create")
+
+    def submit(self, t) -> int:
+        t = _device_tensor(t)
+        tk = ctypes.c_uint64(0)
+        _check(load().ls_server_submit(self._h, t.data_ptr(), t.numel(), dtype_code(t),
+                                       ctypes.byref(tk)), "ls_server_submit")
+        return tk.value
+
+    def wait(self, ticket: int, timeout_ms: int = 0xFFFFFFFF) -> dict:
+        st = RequestStats()
+        rc = load().ls_server_wait(self._h, ticket, timeout_ms, ctypes.byref(st))
+        _check(rc, "ls_server_wait")
+        return {"queue_ms": st.queue_ms, "device_ms": st.device_ms, "total_ms": st.total_ms}
+
+    def close(self):
+        if self._h:
+            load().ls_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,691 @@
+// Host runtime and C ABI of the learned sort (include/ls.h).
+//
+// Per call: plan (fan-out, sample size, heavy threshold, grid), carve one
+// stream-ordered workspace allocation from a per-device memory pool, enqueue
+// the hot path and return.  The path is, in stream order:
+//   train (sample, sort sample, FP64 fit, FP32 evaluation, heavy set)
+//   level 0: K2 histogram -> K3 look-back scan -> K4 scatter -> classify
+//   level 1: re-partition of slots larger than one in-bucket CTA
+//   equality / homogeneous fills, in-bucket counting sorts, radix fallback
+// No host synchronization happens inside a call unless statistics are asked.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "ls_internal.cuh"
+#include "ls_partition.cuh"
+#include "ls_radix.cuh"
+#include "ls_train.cuh"
+
+namespace ls {
+
+__device__ uint32_t g_status_word;  // asynchronous device errors (ERR_* bits)
+
+static std::atomic<unsigned long long> g_launches{0};
+void add_launches(unsigned k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+struct Device {
+  int id = -1;
+  int num_sms = 0;
+  cudaMemPool_t pool = nullptr;
+  uint32_t* err = nullptr;
+  bool configured[4] = {false, false, false, false};
+};
+
+static std::mutex g_mu;
+static std::map<int, Device> g_dev;
+
+static ls_status to_status(cudaError_t e) {
+  if (e == cudaSuccess) return LS_OK;
+  if (e == cudaErrorMemoryAllocation) return LS_ERR_NOMEM;
+  return LS_ERR_CUDA;
+}
+
+static cudaError_t get_device(Device** out) {
+  int id;
+  cudaError_t e = cudaGetDevice(&id);
+  if (e) return e;
+  std::lock_guard<std::mutex> lk(g_mu);
+  Device& d = g_dev[id];
+  if (d.id < 0) {
+    d.id = id;
+    e = cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, id);
+    if (e) return e;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = id;
+    e = cudaMemPoolCreate(&d.pool, &props);
+    if (e) return e;
+    uint64_t thr = ~0ull;
+    e = cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    if (e) return e;
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_status_word);
+    if (e) return e;
+    d.err = (uint32_t*)p;
+    e = cudaMemset(d.err, 0, sizeof(uint32_t));
+    if (e) return e;
+  }
+  *out = &d;
+  return cudaSuccess;
+}
+
+static cudaError_t configure(Device* d, int dt) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (d->configured[dt]) return cudaSuccess;
+  cudaError_t e = level0_configure(dt, 227 * 1024, 227 * 1024);
+  if (e) return e;
+  e = buckets_configure(dt);
+  if (e) return e;
+  d->configured[dt] = true;
+  return cudaSuccess;
+}
+
+static int width_of(int dt) { return (dt == LS_F64 || dt == LS_U64) ? 8 : 4; }
+
+// ---------------------------------------------------------------- planning
+struct Plan {
+  int dt, W;
+  uint64_t n;
+  uint32_t L, f0, hpb, n_ext_max;
+  uint64_t s, tau, seed;
+  Chunking c;
+  SortLimits lim;
+  uint64_t cap0, cap1, cap_c;
+  size_t smem_hist, smem_scatter;
+  uint32_t l0_scan_tiles;
+};
+
+static const size_t SMEM_LIMIT = 227 * 1024;
+
+static void plan_call(const ls_params* prm, int dt, uint64_t n, uintptr_t addr, int num_sms,
+                      Plan* P) {
+  ls_params d;
+  ls_default_params(&d);
+  const ls_params& p = *prm;
+  P->dt = dt;
+  P->W = width_of(dt);
+  P->n = n;
+  P->L = std::min<uint32_t>(MAX_LEAVES, std::max<uint32_t>(1, p.leaves ? p.leaves : d.leaves));
+  P->f0 = std::min<uint32_t>(MAX_FANOUT, std::max<uint32_t>(1, p.fanout ? p.fanout : d.fanout));
+  const uint32_t div = p.sample_div ? p.sample_div : d.sample_div;
+  uint64_t s = (n + div - 1) / div;
+  s = std::max<uint64_t>(s, std::min<uint64_t>(n, 2ull * P->L));
+  if (p.sample_max) s = std::min<uint64_t>(s, p.sample_max);
+  s = std::min<uint64_t>(s, n);
+  s = std::min<uint64_t>(s, 1ull << 29);
+  P->s = std::max<uint64_t>(s, 1);
+  P->seed = p.seed;
+  P->lim.c_small = 2048;
+  P->lim.c_large = 8192;
+  P->lim.l1_target = 4096;
+  // heavy values: per-bucket count limited by shared memory of the scatter
+  uint32_t hpb = (p.flags & LS_FLAG_NO_HEAVY) ? 0 : (p.heavy_per_bucket ? p.heavy_per_bucket : d.heavy_per_bucket);
+  hpb = std::min<uint32_t>(hpb, MAX_HPB);
+  while (true) {
+    const uint32_t next = P->f0 * (1 + 2 * hpb);
+    if (next < 65000 && level0_smem_scatter(dt, P->L, P->f0, next) <= SMEM_LIMIT) break;
+    if (hpb == 0) break;
+    --hpb;
+  }
+  P->hpb = hpb;
+  P->n_ext_max = P->f0 * (1 + 2 * hpb);
+  const uint64_t hmc = p.heavy_min_count ? p.heavy_min_count : P->lim.c_large / 2;
+  if (hpb == 0) {
+    P->tau = P->s + 1;
+  } else {
+    const unsigned __int128 num = (unsigned __int128)hmc * P->s + n - 1;
+    P->tau = std::max<uint64_t>(2, (uint64_t)(num / n));
+  }
+  // chunking of the aligned body
+  const uint64_t V = 16 / P->W;
+  uint64_t a0 = ((16 - (addr & 15)) & 15) / P->W;
+  a0 = std::min<uint64_t>(a0, n);
+  const uint64_t nb = ((n - a0) / V) * V;
+  P->c.n = n;
+  P->c.a0 = a0;
+  P->c.a1 = a0 + nb;
+  uint64_t G = std::min<uint64_t>((uint64_t)num_sms, std::max<uint64_t>(1, (nb + P_TILE - 1) / P_TILE));
+  uint64_t ch = (nb + G - 1) / G;
+  ch = (ch + V - 1) / V * V;
+  if (ch == 0) ch = V;
+  P->c.ch = ch;
+  P->c.G = (uint32_t)G;
+  P->smem_hist = level0_smem_hist(dt, P->L, P->f0, P->n_ext_max);
+  P->smem_scatter = level0_smem_scatter(dt, P->L, P->f0, P->n_ext_max);
+  P->cap0 = P->n_ext_max + 16;
+  P->cap_c = n / P->lim.l1_target + 2 * P->cap0 + 64;
+  P->cap1 = P->cap_c + P->cap0;
+  const uint64_t M = (uint64_t)P->n_ext_max * G;
+  P->l0_scan_tiles = (uint32_t)std::max<uint64_t>(1, (M + SC_TILE - 1) / SC_TILE);
+}
+
+// ---------------------------------------------------------------- workspace
+struct Carver {
+  size_t off = 0;
+  template <typename T>
+  size_t take(size_t count) {
+    off = (off + 255) / 256 * 256;
+    const size_t o = off;
+    off += count * sizeof(T);
+    return o;
+  }
+};
+
+struct Workspace {
+  void* base = nullptr;
+  size_t bytes = 0;
+  // offsets
+  size_t o_scratch, o_smp_a, o_smp_b, o_rank, o_flags, o_cpos, o_cand, o_sel, o_nh, o_part, o_hi,
+      o_tscan, o_rs_hist, o_rs_skip, o_rs_status, o_hdr, o_leaf64, o_leaf, o_heads, o_heavy,
+      o_lbeg, o_lend, o_hist, o_offs, o_l0scan, o_jobs_fill, o_jobs_s, o_jobs_l, o_jobs_r,
+      o_jobs_fb, o_counts, o_aux, o_tot, o_l1cnt, o_l1off, o_l1cur, o_jmin, o_jmax, o_l1scan;
+  size_t tscan_bytes, rs_status_bytes, l0scan_bytes, l1scan_bytes;
+  uint64_t cand_cap;
+};
+
+static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
+  Carver c;
+  const uint64_t s = P.s;
+  w->o_scratch = c.take<uint8_t>(with_scratch ? P.n * P.W : 0);
+  w->o_smp_a = c.take<uint64_t>(s);
+  w->o_smp_b = c.take<uint64_t>(s);
+  w->o_rank = c.take<uint32_t>(s);
+  w->o_flags = c.take<uint32_t>(s);
+  w->o_cpos = c.take<uint64_t>(s + 1);
+  w->cand_cap = s / std::max<uint64_t>(1, P.tau) + 2;
+  w->o_cand = c.take<uint8_t>(w->cand_cap * 24);
+  w->o_sel = c.take<uint64_t>((size_t)P.f0 * std::max<uint32_t>(1, P.hpb));
+  w->o_nh = c.take<uint32_t>(P.f0);
+  w->o_part = c.take<double>(2 * 128);
+  w->o_hi = c.take<uint64_t>(1);
+  const uint64_t stiles = std::max<uint64_t>(1, (s + SC_TILE - 1) / SC_TILE);
+  w->tscan_bytes = stiles * 8 + 16;
+  w->o_tscan = c.take<uint8_t>(w->tscan_bytes);
+  w->o_rs_hist = c.take<uint32_t>(8 * 256);
+  w->o_rs_skip = c.take<uint32_t>(8);
+  w->rs_status_bytes = rs_status_words(s) * 4 + 8 * 4;
+  w->o_rs_status = c.take<uint8_t>(w->rs_status_bytes);
+  w->o_hdr = c.take<DevModel>(1);
+  w->o_leaf64 = c.take<double>(5 * (size_t)P.L);
+  w->o_leaf = c.take<LeafEval>(P.L);
+  w->o_heads = c.take<BucketHead>(P.f0 + 1);
+  w->o_heavy = c.take<HeavyEntry>((size_t)P.f0 * std::max<uint32_t>(1, P.hpb));
+  w->o_lbeg = c.take<uint32_t>(P.L);
+  w->o_lend = c.take<uint32_t>(P.L);
+  w->o_hist = c.take<uint32_t>((size_t)P.n_ext_max * P.c.G);
+  w->o_offs = c.take<uint64_t>((size_t)P.n_ext_max * P.c.G + 1);
+  w->l0scan_bytes = (size_t)P.l0_scan_tiles * 8 + 16;
+  w->o_l0scan = c.take<uint8_t>(w->l0scan_bytes);
+  w->o_jobs_fill = c.take<Job>(P.cap1);
+  w->o_jobs_s = c.take<Job>(P.cap1);
+  w->o_jobs_l = c.take<Job>(P.cap1);
+  w->o_jobs_r = c.take<Job>(P.cap0);
+  w->o_jobs_fb = c.take<Job>(P.cap1);
+  w->o_counts = c.take<unsigned long long>(16);
+  w->o_aux = c.take<uint8_t>((P.cap0 + 1) * 32);
+  w->o_tot = c.take<unsigned long long>(4);
+  w->o_l1cnt = c.take<uint32_t>(P.cap_c);
+  w->o_l1off = c.take<uint64_t>(P.cap_c + 1);
+  w->o_l1cur = c.take<unsigned long long>(P.cap_c);
+  w->o_jmin = c.take<unsigned long long>(P.cap0);
+  w->o_jmax = c.take<unsigned long long>(P.cap0);
+  const uint64_t l1tiles = std::max<uint64_t>(1, (P.cap_c + SC_TILE - 1) / SC_TILE);
+  w->l1scan_bytes = l1tiles * 8 + 16;
+  w->o_l1scan = c.take<uint8_t>(w->l1scan_bytes);
+  w->bytes = c.off + 256;
+}
+
+template <typename T>
+static T* at(const Workspace& w, size_t o) {
+  return (T*)((char*)w.base + o);
+}
+
+struct Bound {
+  ModelPtrs M;
+  TrainWs T;
+  Lists lists;
+  Level1Ws l1;
+  unsigned long long* counts;  // [0..4] list counts, [8..10] job counters
+};
+
+static Bound bind(const Plan& P, const Workspace& w) {
+  Bound b{};
+  b.M.hdr = at<DevModel>(w, w.o_hdr);
+  b.M.leaf64 = at<double>(w, w.o_leaf64);
+  b.M.leaf = at<LeafEval>(w, w.o_leaf);
+  b.M.heads = at<BucketHead>(w, w.o_heads);
+  b.M.heavy = at<HeavyEntry>(w, w.o_heavy);
+  b.M.leaf_beg = at<uint32_t>(w, w.o_lbeg);
+  b.M.leaf_end = at<uint32_t>(w, w.o_lend);
+  TrainWs& T = b.T;
+  T.smp_a = at<uint64_t>(w, w.o_smp_a);
+  T.smp_b = at<uint64_t>(w, w.o_smp_b);
+  T.rank = at<uint32_t>(w, w.o_rank);
+  T.flags = at<uint32_t>(w, w.o_flags);
+  T.cpos = at<uint64_t>(w, w.o_cpos);
+  T.cand = at<void>(w, w.o_cand);
+  T.cand_cap = w.cand_cap;
+  T.sel = at<uint64_t>(w, w.o_sel);
+  T.nh = at<uint32_t>(w, w.o_nh);
+  T.partials = at<double>(w, w.o_part);
+  T.hi = at<unsigned long long>(w, w.o_hi);
+  T.scan_status = at<void>(w, w.o_tscan);
+  T.scan_status_bytes = w.tscan_bytes;
+  T.rs.hist = at<uint32_t>(w, w.o_rs_hist);
+  T.rs.skip = at<uint32_t>(w, w.o_rs_skip);
+  T.rs.status = at<uint32_t>(w, w.o_rs_status);
+  T.rs.ctr = T.rs.status + rs_status_words(P.s);
+  b.counts = at<unsigned long long>(w, w.o_counts);
+  auto mk = [&](size_t o, unsigned long long* cnt, uint64_t cap) {
+    JobList l;
+    l.jobs = at<Job>(w, o);
+    l.count = cnt;
+    l.cap = cap;
+    return l;
+  };
+  b.lists.fill = mk(w.o_jobs_fill, b.counts + 0, P.cap1);
+  b.lists.sort_s = mk(w.o_jobs_s, b.counts + 1, P.cap1);
+  b.lists.sort_l = mk(w.o_jobs_l, b.counts + 2, P.cap1);
+  b.lists.refine = mk(w.o_jobs_r, b.counts + 3, P.cap0);
+  b.lists.fallback = mk(w.o_jobs_fb, b.counts + 4, P.cap1);
+  Level1Ws& l = b.l1;
+  l.aux = at<void>(w, w.o_aux);
+  l.totals = at<unsigned long long>(w, w.o_tot);
+  l.cnt = at<uint32_t>(w, w.o_l1cnt);
+  l.off = at<uint64_t>(w, w.o_l1off);
+  l.cur = at<unsigned long long>(w, w.o_l1cur);
+  l.jmin = at<unsigned long long>(w, w.o_jmin);
+  l.jmax = at<unsigned long long>(w, w.o_jmax);
+  l.scan_status = at<void>(w, w.o_l1scan);
+  l.scan_status_bytes = w.l1scan_bytes;
+  l.cap_c = P.cap_c;
+  l.cap_jobs = P.cap0;
+  l.cap_tiles = 0;
+  return b;
+}
+
+// ---------------------------------------------------------------- the sort
+constexpr int NMARK = 11;  // start, train, K2, K3, K4, classify, level1, fill, K5s, K5l, fallback
+struct Events {
+  cudaEvent_t ev[NMARK];
+  bool on = false;
+};
+
+#define LS_TRY(x)                       \
+  do {                                  \
+    cudaError_t e_ = (x);               \
+    if (e_ != cudaSuccess) return e_;   \
+  } while (0)
+
+static cudaError_t enqueue_train(const Plan& P, const Bound& b, const void* keys, Device* d,
+                                 cudaStream_t st) {
+  TrainPlan tp;
+  tp.s = P.s;
+  tp.seed = P.seed;
+  tp.tau = P.tau;
+  tp.L = P.L;
+  tp.f0 = P.f0;
+  tp.hpb = P.hpb;
+  return train_enqueue(P.dt, keys, P.n, tp, b.T, b.M, d->err, st, d->num_sms);
+}
+
+static Level0Args level0_args(const Plan& P, const Bound& b, const Workspace& w, const void* keys,
+                              Device* d) {
+  Level0Args a;
+  a.keys = keys;
+  a.scratch = at<void>(w, w.o_scratch);
+  a.c = P.c;
+  a.M = b.M;
+  a.f0 = P.f0;
+  a.n_ext_max = P.n_ext_max;
+  a.L = P.L;
+  a.hist = at<uint32_t>(w, w.o_hist);
+  a.offs = at<uint64_t>(w, w.o_offs);
+  a.scan_status = at<void>(w, w.o_l0scan);
+  a.scan_tiles = P.l0_scan_tiles;
+  a.err = d->err;
+  return a;
+}
+
+static cudaError_t enqueue_sort(const Plan& P, const Workspace& w, void* keys, Device* d,
+                                cudaStream_t st, Events* ev) {
+  const Bound b = bind(P, w);
+  Marks mk{ev && ev->on ? ev->ev : nullptr, NMARK};
+  LS_TRY(cudaMemsetAsync(b.counts, 0, 16 * sizeof(unsigned long long), st));
+  mark(&mk, 0, st);
+  LS_TRY(enqueue_train(P, b, keys, d, st));
+  mark(&mk, 1, st);
+  LS_TRY(cudaMemsetAsync(at<void>(w, w.o_l0scan), 0, w.l0scan_bytes, st));
+  const Level0Args a = level0_args(P, b, w, keys, d);
+  LS_TRY(level0_enqueue(P.dt, a, P.smem_hist, P.smem_scatter, b.lists, P.lim, st, &mk, 2));
+  LS_TRY(level1_enqueue(P.dt, keys, a.scratch, P.n, b.M, P.f0, b.lists, P.lim, b.l1, d->err, st,
+                        d->num_sms));
+  mark(&mk, 6, st);
+  LS_TRY(fill_enqueue(P.dt, keys, b.lists, P.cap1, st, d->num_sms));
+  mark(&mk, 7, st);
+  LS_TRY(buckets_enqueue(P.dt, keys, a.scratch, P.n, b.M, b.lists, P.cap1, P.cap1, P.cap1,
+                         b.counts + 8, d->err, st, d->num_sms, &mk, 8));
+  return cudaSuccess;
+}
+
+static ls_status validate(const void* keys, size_t n, int dt) {
+  if (dt < LS_F64 || dt > LS_U32) return LS_ERR_INVALID;
+  if (n > 0 && !keys) return LS_ERR_INVALID;
+  const int W = width_of(dt);
+  if ((uintptr_t)keys % W) return LS_ERR_INVALID;
+  if (n >= (1ull << 62) / W) return LS_ERR_INVALID;
+  return LS_OK;
+}
+
+static cudaError_t ws_alloc(Device* d, Workspace* w, cudaStream_t st) {
+  return cudaMallocFromPoolAsync(&w->base, w->bytes, d->pool, st);
+}
+
+static void fill_stats(const Plan& P, const Workspace& w, Events* ev, ls_stats* stats,
+                       uint64_t launches) {
+  std::memset(stats, 0, sizeof(*stats));
+  if (ev->on) {
+    auto el = [&](int a, int b) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, ev->ev[a], ev->ev[b]);
+      return (double)ms;
+    };
+    stats->ms_total = el(0, 10);
+    stats->ms_train = el(0, 1);
+    stats->ms_hist = el(1, 2);
+    stats->ms_scan = el(2, 3);
+    stats->ms_scatter = el(3, 4);
+    stats->ms_classify = el(4, 5);
+    stats->ms_level1 = el(5, 6);
+    stats->ms_fill = el(6, 7);
+    stats->ms_sort_small = el(7, 8);
+    stats->ms_sort_large = el(8, 9);
+    stats->ms_fallback = el(9, 10);
+  }
+  stats->n_launches = launches;
+  DevModel hdr;
+  cudaMemcpy(&hdr, at<void>(w, w.o_hdr), sizeof(hdr), cudaMemcpyDeviceToHost);
+  unsigned long long counts[16];
+  cudaMemcpy(counts, at<void>(w, w.o_counts), sizeof(counts), cudaMemcpyDeviceToHost);
+  stats->sample_size = hdr.s;
+  stats->sample_finite = hdr.s_fin;
+  stats->fanout = P.f0;
+  stats->leaves = P.L;
+  stats->n_heavy = hdr.nheavy;
+  stats->n_ext = hdr.n_ext;
+  stats->n_level1 = counts[3];
+  stats->n_segments = counts[1] + counts[2];
+  stats->n_fallback = counts[4];
+  // largest slot and equality keys from the level-0 offsets
+  const uint32_t next = std::min<uint32_t>(hdr.n_ext, P.n_ext_max);
+  std::vector<uint64_t> offs((size_t)P.n_ext_max * P.c.G + 1);
+  cudaMemcpy(offs.data(), at<void>(w, w.o_offs), offs.size() * 8, cudaMemcpyDeviceToHost);
+  std::vector<BucketHead> heads(P.f0 + 1);
+  cudaMemcpy(heads.data(), at<void>(w, w.o_heads), heads.size() * sizeof(BucketHead),
+             cudaMemcpyDeviceToHost);
+  uint64_t mx = 0, eq = 0;
+  uint32_t b = 0;
+  for (uint32_t e = 0; e < next; ++e) {
+    while (b + 1 <= P.f0 && heads[b + 1].ext_base <= e) ++b;
+    const uint64_t sz = offs[(size_t)(e + 1) * P.c.G] - offs[(size_t)e * P.c.G];
+    const uint32_t o = e - heads[b].ext_base, nh = heads[b].hoff_nh & 15u;
+    if (nh && (o & 1u)) eq += sz; else mx = std::max(mx, sz);
+  }
+  stats->max_bucket = mx;
+  stats->n_eq_keys = eq;
+  stats->n_fill = counts[0];
+}
+
+}  // namespace ls
+
+using namespace ls;
+
+extern "C" {
+
+void ls_default_params(ls_params* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->fanout = 1000;
+  p->leaves = 1000;
+  p->sample_div = 100;
+  p->heavy_per_bucket = 4;
+  p->sample_max = 0;
+  p->seed = 0;
+  p->heavy_min_count = 0;
+  p->flags = 0;
+}
+
+const char* ls_status_string(ls_status s) {
+  switch (s) {
+    case LS_OK: return "ok";
+    case LS_ERR_INVALID: return "invalid argument";
+    case LS_ERR_NOMEM: return "out of memory";
+    case LS_ERR_CUDA: return "CUDA error";
+    case LS_ERR_TIMEOUT: return "device wait timed out";
+    case LS_ERR_BUSY: return "busy: admission refused";
+    case LS_ERR_CANCELLED: return "cancelled";
+  }
+  return "unknown status";
+}
+
+ls_status ls_sort_ex(void* keys, size_t n, ls_dtype dtype, void* stream, const ls_params* params,
+                     ls_stats* stats) {
+  const ls_status v = validate(keys, n, dtype);
+  if (v) return v;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (n < 2) return LS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  Device* d;
+  cudaError_t e = get_device(&d);
+  if (e) return to_status(e);
+  if ((e = configure(d, dtype))) return to_status(e);
+  ls_params p;
+  if (params) p = *params; else ls_default_params(&p);
+  Plan P;
+  plan_call(&p, dtype, n, (uintptr_t)keys, d->num_sms, &P);
+  if (P.smem_hist > SMEM_LIMIT || P.smem_scatter > SMEM_LIMIT) return LS_ERR_INVALID;
+  Workspace w;
+  layout_ws(P, &w, true);
+  if ((e = ws_alloc(d, &w, st))) return to_status(e);
+  Events ev;
+  if (stats) {
+    ev.on = true;
+    for (int i = 0; i < NMARK; ++i) cudaEventCreate(&ev.ev[i]);
+  }
+  const unsigned long long l0 = g_launches.load();
+  e = enqueue_sort(P, w, keys, d, st, &ev);
+  const unsigned long long l1 = g_launches.load();
+  if (e == cudaSuccess && stats) {
+    e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) fill_stats(P, w, &ev, stats, l1 - l0);
+  }
+  cudaFreeAsync(w.base, st);
+  if (stats)
+    for (int i = 0; i < NMARK; ++i) cudaEventDestroy(ev.ev[i]);
+  return to_status(e);
+}
+
+ls_status ls_sort(void* keys, size_t n, ls_dtype dtype, void* stream) {
+  return ls_sort_ex(keys, n, dtype, stream, nullptr, nullptr);
+}
+
+ls_status ls_sort_host(void* host_keys, size_t n, ls_dtype dtype, void* stream,
+                       const ls_params* params) {
+  const ls_status v = validate(host_keys, n, dtype);
+  if (v) return v;
+  if (n < 2) return LS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  Device* d;
+  cudaError_t e = get_device(&d);
+  if (e) return to_status(e);
+  const size_t bytes = n * (size_t)width_of(dtype);
+  void* dk = nullptr;
+  if ((e = cudaMallocFromPoolAsync(&dk, bytes, d->pool, st))) return to_status(e);
+  e = cudaMemcpyAsync(dk, host_keys, bytes, cudaMemcpyHostToDevice, st);
+  ls_status s = LS_OK;
+  if (e == cudaSuccess) s = ls_sort_ex(dk, n, dtype, stream, params, nullptr);
+  if (e == cudaSuccess && s == LS_OK) e = cudaMemcpyAsync(host_keys, dk, bytes, cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(dk, st);
+  const cudaError_t e2 = cudaStreamSynchronize(st);
+  if (s != LS_OK) return s;
+  if (e == cudaSuccess) e = e2;
+  return to_status(e);
+}
+
+ls_status ls_stream_status(void* stream) {
+  Device* d;
+  cudaError_t e = get_device(&d);
+  if (e) return to_status(e);
+  if ((e = cudaStreamSynchronize((cudaStream_t)stream))) return to_status(e);
+  uint32_t w = 0;
+  if ((e = cudaMemcpy(&w, d->err, sizeof(w), cudaMemcpyDeviceToHost))) return to_status(e);
+  if (w && (e = cudaMemset(d->err, 0, sizeof(uint32_t)))) return to_status(e);
+  if (w & ERR_TIMEOUT) return LS_ERR_TIMEOUT;
+  if (w & ERR_BOUNDS) return LS_ERR_CUDA;
+  return LS_OK;
+}
+
+ls_status ls_train(const void* keys, size_t n, ls_dtype dtype, void* stream,
+                   const ls_params* params, ls_model_export* out) {
+  const ls_status v = validate(keys, n, dtype);
+  if (v) return v;
+  if (!out || n == 0) return LS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  Device* d;
+  cudaError_t e = get_device(&d);
+  if (e) return to_status(e);
+  if ((e = configure(d, dtype))) return to_status(e);
+  ls_params p;
+  if (params) p = *params; else ls_default_params(&p);
+  Plan P;
+  plan_call(&p, dtype, n, (uintptr_t)keys, d->num_sms, &P);
+  if (out->leaves < P.L) return LS_ERR_INVALID;
+  Workspace w;
+  layout_ws(P, &w, false);
+  if ((e = ws_alloc(d, &w, st))) return to_status(e);
+  const Bound b = bind(P, w);
+  e = enqueue_train(P, b, keys, d, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) {
+    DevModel hdr;
+    cudaMemcpy(&hdr, b.M.hdr, sizeof(hdr), cudaMemcpyDeviceToHost);
+    out->sample_size = hdr.s;
+    out->sample_finite = hdr.s_fin;
+    std::memcpy(out->root, hdr.root64, sizeof(out->root));
+    out->E = hdr.root.E;
+    out->root_sh = hdr.root.sh;
+    out->root_cq = hdr.root.cq;
+    out->root_A = hdr.root.A;
+    out->root_B = hdr.root.B;
+    out->tau = P.tau;
+    out->n_heavy = hdr.nheavy;
+    if (out->leaf) cudaMemcpy(out->leaf, b.M.leaf64, 5 * sizeof(double) * P.L, cudaMemcpyDeviceToHost);
+    std::vector<LeafEval> le(P.L);
+    cudaMemcpy(le.data(), b.M.leaf, sizeof(LeafEval) * P.L, cudaMemcpyDeviceToHost);
+    for (uint32_t l = 0; l < P.L; ++l) {
+      if (out->cq) out->cq[l] = le[l].cq;
+      if (out->sh) out->sh[l] = le[l].sh;
+      if (out->A) out->A[l] = le[l].A;
+      if (out->B) out->B[l] = le[l].B;
+      if (out->LO) out->LO[l] = le[l].LO;
+      if (out->HI) out->HI[l] = le[l].HI;
+    }
+    if (out->sorted_sample_tk)
+      cudaMemcpy(out->sorted_sample_tk, b.T.smp_a, 8 * P.s, cudaMemcpyDeviceToHost);
+    if (out->heavy_tk && hdr.nheavy) {
+      std::vector<HeavyEntry> hv(hdr.nheavy);
+      cudaMemcpy(hv.data(), b.M.heavy, sizeof(HeavyEntry) * hdr.nheavy, cudaMemcpyDeviceToHost);
+      for (uint32_t j = 0; j < std::min<uint32_t>(hdr.nheavy, out->max_heavy); ++j)
+        out->heavy_tk[j] = hv[j].tk;
+    }
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(w.base, st);
+  cudaStreamSynchronize(st);
+  return to_status(e);
+}
+
+ls_status ls_level0_histogram(const void* keys, size_t n, ls_dtype dtype, void* stream,
+                              const ls_params* params, uint64_t* hist_host, size_t max_ext,
+                              size_t* n_ext) {
+  const ls_status v = validate(keys, n, dtype);
+  if (v) return v;
+  if (!hist_host || !n_ext || n == 0) return LS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  Device* d;
+  cudaError_t e = get_device(&d);
+  if (e) return to_status(e);
+  if ((e = configure(d, dtype))) return to_status(e);
+  ls_params p;
+  if (params) p = *params; else ls_default_params(&p);
+  Plan P;
+  plan_call(&p, dtype, n, (uintptr_t)keys, d->num_sms, &P);
+  Workspace w;
+  layout_ws(P, &w, true);
+  if ((e = ws_alloc(d, &w, st))) return to_status(e);
+  const Bound b = bind(P, w);
+  e = cudaMemsetAsync(b.counts, 0, 16 * sizeof(unsigned long long), st);
+  if (!e) e = enqueue_train(P, b, keys, d, st);
+  if (!e) e = cudaMemsetAsync(at<void>(w, w.o_l0scan), 0, w.l0scan_bytes, st);
+  if (!e) e = level0_enqueue(P.dt, level0_args(P, b, w, keys, d), P.smem_hist, P.smem_scatter,
+                             b.lists, P.lim, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  if (!e) {
+    DevModel hdr;
+    cudaMemcpy(&hdr, b.M.hdr, sizeof(hdr), cudaMemcpyDeviceToHost);
+    const uint32_t next = std::min<uint32_t>(hdr.n_ext, P.n_ext_max);
+    std::vector<uint64_t> offs((size_t)P.n_ext_max * P.c.G + 1);
+    cudaMemcpy(offs.data(), at<void>(w, w.o_offs), offs.size() * 8, cudaMemcpyDeviceToHost);
+    *n_ext = next;
+    for (uint32_t x = 0; x < next && x < max_ext; ++x)
+      hist_host[x] = offs[(size_t)(x + 1) * P.c.G] - offs[(size_t)x * P.c.G];
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(w.base, st);
+  cudaStreamSynchronize(st);
+  return to_status(e);
+}
+
+uint64_t ls_kernel_launches(void) { return g_launches.load(); }
+
+ls_status ls_radix_sort_u64(uint64_t* keys, size_t count, void* stream) {
+  if (count > 0 && !keys) return LS_ERR_INVALID;
+  if (count < 2) return LS_OK;
+  if (count >= (1ull << 30)) return LS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  Device* d;
+  cudaError_t e = get_device(&d);
+  if (e) return to_status(e);
+  Carver c;
+  const size_t o_tmp = c.take<uint64_t>(count);
+  const size_t o_hist = c.take<uint32_t>(8 * 256);
+  const size_t o_skip = c.take<uint32_t>(8);
+  const size_t o_stat = c.take<uint8_t>(rs_status_words(count) * 4 + 32);
+  void* base = nullptr;
+  if ((e = cudaMallocFromPoolAsync(&base, c.off + 256, d->pool, st))) return to_status(e);
+  RsWork rw;
+  rw.hist = (uint32_t*)((char*)base + o_hist);
+  rw.skip = (uint32_t*)((char*)base + o_skip);
+  rw.status = (uint32_t*)((char*)base + o_stat);
+  rw.ctr = rw.status + rs_status_words(count);
+  e = radix_sort_u64_enqueue(keys, (uint64_t*)((char*)base + o_tmp), count, rw, d->err, st,
+                             d->num_sms);
+  cudaFreeAsync(base, st);
+  return to_status(e);
+}
+
+}  // extern "C"

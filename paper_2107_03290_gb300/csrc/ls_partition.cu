@@ -1,0 +1,648 @@
+// Model-based partitioning of LearnedSort 2.0 (Alg. 1) on the GPU.
+//
+// The paper's CPU Partition appends each key to a fixed-capacity fragment of
+// its predicted bucket and flushes full fragments in place, so buckets never
+// overflow (Sec. 4.2).  On the GPU the same goal -- each bucket gets exactly
+// the space it needs -- is reached with a counting pre-pass (the exact-count
+// alternative weighed in Sec. 4.2), which costs one extra streaming read:
+//   K2 k_l0_hist     per-CTA histograms of extended slots, key tiles staged by
+//                    TMA into shared memory;
+//   K3 k_scan        decoupled look-back exclusive scan of the histograms,
+//                    giving every (slot, CTA) its write head;
+//   K4 k_l0_scatter  re-predicts, ranks keys by slot inside the tile, stages
+//                    them slot-contiguously in shared memory and writes full
+//                    runs to the scratch buffer;
+//   k_classify0      turns slots into jobs (equality fill, in-bucket sort,
+//                    level-1 re-partition).
+// Level 1 (Alg. 2's re-partition of each bucket into sub-buckets) splits the
+// oversized slots with the same model: sub = floor((F - Flo) * f1 / (Fhi - Flo)).
+#include <cfloat>
+
+#include "ls_partition.cuh"
+#include "ls_scan.cuh"
+#include "ls_tma.cuh"
+
+namespace ls {
+
+struct L0Layout {
+  uint32_t bar, buf, leaves, heads, cnt, cursor, eqbits, ids, ws, total;
+};
+
+static L0Layout l0_layout(int W, uint32_t L, uint32_t f0, uint32_t next, bool scatter) {
+  L0Layout y{};
+  size_t o = 0;
+  auto al = [&](size_t a) { o = (o + a - 1) / a * a; };
+  y.bar = (uint32_t)o; o += 16;
+  al(128); y.buf = (uint32_t)o; o += 2ull * P_TILE * W;
+  al(16); y.leaves = (uint32_t)o; o += (size_t)L * sizeof(LeafEval);
+  y.heads = (uint32_t)o; o += (size_t)(f0 + 1) * sizeof(BucketHead);
+  y.cnt = (uint32_t)o; o += (size_t)(next + 1) * 4;
+  if (scatter) {
+    al(8); y.cursor = (uint32_t)o; o += (size_t)next * 8;
+    y.eqbits = (uint32_t)o; o += (size_t)((next + 31) / 32) * 4;
+    y.ids = (uint32_t)o; o += (size_t)P_TILE * 2;
+  }
+  al(8); y.ws = (uint32_t)o; o += 33 * 8;
+  y.total = (uint32_t)o;
+  return y;
+}
+
+static int key_width(int dt) { return (dt == LS_F64 || dt == LS_U64) ? 8 : 4; }
+
+size_t level0_smem_hist(int dt, uint32_t L, uint32_t f0, uint32_t n_ext_max) {
+  return l0_layout(key_width(dt), L, f0, n_ext_max, false).total;
+}
+size_t level0_smem_scatter(int dt, uint32_t L, uint32_t f0, uint32_t n_ext_max) {
+  return l0_layout(key_width(dt), L, f0, n_ext_max, true).total;
+}
+
+__device__ __forceinline__ void chunk_of(const Chunking& c, uint32_t g, uint64_t* b, uint64_t* e) {
+  uint64_t cb = c.a0 + (uint64_t)g * c.ch;
+  uint64_t ce = cb + c.ch;
+  if (cb > c.a1) cb = c.a1;
+  if (ce > c.a1) ce = c.a1;
+  *b = cb;
+  *e = ce;
+}
+
+template <int DT>
+__device__ __forceinline__ void load_tables(const Level0Args& a, LeafEval* leaves, BucketHead* heads) {
+  for (uint32_t i = threadIdx.x; i < a.L; i += blockDim.x) leaves[i] = a.M.leaf[i];
+  for (uint32_t i = threadIdx.x; i <= a.f0; i += blockDim.x) heads[i] = a.M.heads[i];
+}
+
+// ---------------------------------------------------------------- K2
+template <int DT>
+__global__ void __launch_bounds__(P_THREADS, 1) k_l0_hist(Level0Args a, L0Layout lay) {
+  typedef typename KT<DT>::U U;
+  extern __shared__ __align__(128) unsigned char sm[];
+  uint64_t* bar = (uint64_t*)(sm + lay.bar);
+  U* buf = (U*)(sm + lay.buf);
+  LeafEval* leaves = (LeafEval*)(sm + lay.leaves);
+  BucketHead* heads = (BucketHead*)(sm + lay.heads);
+  uint32_t* cnt = (uint32_t*)(sm + lay.cnt);
+  const U* keys = (const U*)a.keys;
+  const RootEval r = a.M.hdr->root;
+  const uint32_t next = min(a.M.hdr->n_ext, a.n_ext_max);
+  const HeavyEntry* __restrict__ heavy = a.M.heavy;
+  const uint32_t g = blockIdx.x;
+  uint64_t cb, ce;
+  chunk_of(a.c, g, &cb, &ce);
+  TileStream<U, P_TILE> ts{buf, bar, keys + cb, ce - cb, (uint32_t)((ce - cb + P_TILE - 1) / P_TILE)};
+  if (threadIdx.x == 0) ts.init();
+  __syncthreads();
+  if (threadIdx.x == 0) { ts.issue(0); ts.issue(1); }
+  load_tables<DT>(a, leaves, heads);
+  for (uint32_t i = threadIdx.x; i < next; i += P_THREADS) cnt[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  if (g == 0) {  // unaligned head and tail
+    const uint64_t nht = a.c.a0 + (a.c.n - a.c.a1);
+    for (uint64_t k = threadIdx.x; k < nht; k += P_THREADS) {
+      const uint64_t i = k < a.c.a0 ? k : a.c.a1 + (k - a.c.a0);
+      const uint32_t e = ext_of<DT>(keys[i], r, leaves, heads, heavy, a.f0);
+      if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
+    }
+  }
+  for (uint32_t t = 0; t < ts.nt; ++t) {
+    const U* tb = ts.wait(t, a.err);
+    const uint32_t c = ts.count(t);
+    for (uint32_t base = 0; base < c; base += P_THREADS) {
+      const uint32_t i = base + threadIdx.x;
+      const bool valid = i < c;
+      uint32_t e = valid ? ext_of<DT>(tb[i], r, leaves, heads, heavy, a.f0) : 0xFFFFFFFFu;
+      if (valid && e >= next) { set_error(a.err, ERR_BOUNDS); e = 0xFFFFFFFEu; }
+      const unsigned peers = __match_any_sync(0xffffffffu, e);
+      if (e < next && lane == __ffs(peers) - 1) atomicAdd(&cnt[e], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) ts.issue(t + 2);
+  }
+  __syncthreads();
+  for (uint32_t e = threadIdx.x; e < a.n_ext_max; e += P_THREADS)
+    a.hist[(size_t)e * a.c.G + g] = e < next ? cnt[e] : 0u;
+}
+
+// ---------------------------------------------------------------- K4
+template <int DT>
+__global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Layout lay) {
+  typedef typename KT<DT>::U U;
+  constexpr int KPT = P_TILE / P_THREADS;
+  extern __shared__ __align__(128) unsigned char sm[];
+  uint64_t* bar = (uint64_t*)(sm + lay.bar);
+  U* buf = (U*)(sm + lay.buf);
+  LeafEval* leaves = (LeafEval*)(sm + lay.leaves);
+  BucketHead* heads = (BucketHead*)(sm + lay.heads);
+  uint32_t* cnt = (uint32_t*)(sm + lay.cnt);
+  uint64_t* cursor = (uint64_t*)(sm + lay.cursor);
+  uint32_t* eqbits = (uint32_t*)(sm + lay.eqbits);
+  uint16_t* ids = (uint16_t*)(sm + lay.ids);
+  uint32_t* ws = (uint32_t*)(sm + lay.ws);
+  const U* keys = (const U*)a.keys;
+  U* out = (U*)a.scratch;
+  const uint64_t n = a.c.n;
+  const RootEval r = a.M.hdr->root;
+  const uint32_t next = min(a.M.hdr->n_ext, a.n_ext_max);
+  const HeavyEntry* __restrict__ heavy = a.M.heavy;
+  const uint32_t g = blockIdx.x, G = a.c.G;
+  uint64_t cb, ce;
+  chunk_of(a.c, g, &cb, &ce);
+  TileStream<U, P_TILE> ts{buf, bar, keys + cb, ce - cb, (uint32_t)((ce - cb + P_TILE - 1) / P_TILE)};
+  if (threadIdx.x == 0) ts.init();
+  __syncthreads();
+  if (threadIdx.x == 0) { ts.issue(0); ts.issue(1); }
+  load_tables<DT>(a, leaves, heads);
+  for (uint32_t e = threadIdx.x; e <= next; e += P_THREADS) cnt[e] = 0;
+  for (uint32_t e = threadIdx.x; e < next; e += P_THREADS) cursor[e] = a.offs[(size_t)e * G + g];
+  for (uint32_t w = threadIdx.x; w < (next + 31) / 32; w += P_THREADS) eqbits[w] = 0;
+  __syncthreads();
+  for (uint32_t b = threadIdx.x; b < a.f0; b += P_THREADS) {
+    const BucketHead h = heads[b];
+    const uint32_t nh = h.hoff_nh & 15u;
+    for (uint32_t j = 0; j < nh; ++j) {
+      const uint32_t e = h.ext_base + 2 * j + 1;
+      if (e < next) atomicOr(&eqbits[e >> 5], 1u << (e & 31));
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  if (g == 0 && threadIdx.x == 0) {  // unaligned head and tail, one thread
+    const uint64_t nht = a.c.a0 + (n - a.c.a1);
+    for (uint64_t k = 0; k < nht; ++k) {
+      const uint64_t i = k < a.c.a0 ? k : a.c.a1 + (k - a.c.a0);
+      const U u = keys[i];
+      const uint32_t e = ext_of<DT>(u, r, leaves, heads, heavy, a.f0);
+      if (e >= next) { set_error(a.err, ERR_BOUNDS); continue; }
+      if ((eqbits[e >> 5] >> (e & 31)) & 1u) continue;
+      const uint64_t dst = cursor[e]++;
+      if (dst < n) out[dst] = u; else set_error(a.err, ERR_BOUNDS);
+    }
+  }
+  __syncthreads();
+  for (uint32_t t = 0; t < ts.nt; ++t) {
+    U* tb = ts.wait(t, a.err);
+    const uint32_t c = ts.count(t);
+    U u[KPT];
+    uint32_t e[KPT], rk[KPT];
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const uint32_t i = k * P_THREADS + threadIdx.x;
+      const bool valid = i < c;
+      u[k] = valid ? tb[i] : (U)0;
+      uint32_t ee = valid ? ext_of<DT>(u[k], r, leaves, heads, heavy, a.f0) : 0xFFFFFFFFu;
+      if (valid && ee >= next) { set_error(a.err, ERR_BOUNDS); ee = 0xFFFFFFFEu; }
+      e[k] = ee;
+      const unsigned peers = __match_any_sync(0xffffffffu, ee);
+      const int leader = __ffs(peers) - 1;
+      uint32_t old = 0;
+      if (ee < next && lane == leader) old = atomicAdd(&cnt[ee], (uint32_t)__popc(peers));
+      old = __shfl_sync(0xffffffffu, old, leader);
+      rk[k] = old + __popc(peers & lt);
+    }
+    __syncthreads();
+    // slot offsets inside the tile
+    block_scan_array<uint32_t>(cnt, (int)next, ws);
+    if (threadIdx.x == 0) cnt[next] = c;
+    __syncthreads();
+    // stage slot-contiguously (the input buffer is free now)
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      if (e[k] < next) {
+        const uint32_t p = cnt[e[k]] + rk[k];
+        if (p < (uint32_t)P_TILE) { tb[p] = u[k]; ids[p] = (uint16_t)e[k]; }
+      }
+    }
+    __syncthreads();
+    // write runs: consecutive p of one slot go to consecutive addresses
+    const uint32_t staged = cnt[next];
+    for (uint32_t p = threadIdx.x; p < staged; p += P_THREADS) {
+      const uint32_t ee = ids[p];
+      if ((eqbits[ee >> 5] >> (ee & 31)) & 1u) continue;
+      const uint64_t dst = cursor[ee] + (p - cnt[ee]);
+      if (dst < n) out[dst] = tb[p]; else set_error(a.err, ERR_BOUNDS);
+    }
+    __syncthreads();
+    for (uint32_t ee = threadIdx.x; ee < next; ee += P_THREADS) cursor[ee] += cnt[ee + 1] - cnt[ee];
+    __syncthreads();
+    for (uint32_t ee = threadIdx.x; ee <= next; ee += P_THREADS) cnt[ee] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) ts.issue(t + 2);
+  }
+}
+
+// ---------------------------------------------------------------- classify level 0
+template <int DT>
+__global__ void k_classify0(Level0Args a, Lists lists, SortLimits lim) {
+  const uint32_t next = min(a.M.hdr->n_ext, a.n_ext_max);
+  const uint32_t G = a.c.G;
+  const BucketHead* heads = a.M.heads;
+  const HeavyEntry* heavy = a.M.heavy;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < next; e += gridDim.x * blockDim.x) {
+    const uint64_t start = a.offs[(size_t)e * G];
+    const uint64_t end = a.offs[(size_t)(e + 1) * G];
+    if (end <= start) continue;
+    const uint64_t size = end - start;
+    uint32_t lo = 0, hi = a.f0;  // last b with ext_base <= e
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (heads[mid].ext_base <= e) lo = mid; else hi = mid - 1;
+    }
+    const uint32_t b = lo;
+    const BucketHead h = heads[b];
+    const uint32_t o = e - h.ext_base, nh = h.hoff_nh & 15u, hoff = h.hoff_nh >> 4;
+    Job job;
+    job.start = start;
+    job.m = size;
+    job.value = 0;
+    job.src = 1;
+    if (nh && (o & 1u)) {
+      job.kind = JOB_FILL;
+      job.value = (uint64_t)KT<DT>::from_tk(heavy[hoff + o / 2].tk);
+      job.Flo = job.Fhi = 0;
+      push_job(lists.fill, job, a.err);
+      continue;
+    }
+    const uint32_t j = o / 2;
+    job.Flo = (j == 0) ? (double)b / (double)a.f0 : (double)heavy[hoff + j - 1].F;
+    job.Fhi = (j == nh) ? (double)(b + 1) / (double)a.f0 : (double)heavy[hoff + j].F;
+    if (size <= lim.c_small) { job.kind = JOB_SORT; push_job(lists.sort_s, job, a.err); }
+    else if (size <= lim.c_large) { job.kind = JOB_SORT; push_job(lists.sort_l, job, a.err); }
+    else { job.kind = JOB_REFINE; push_job(lists.refine, job, a.err); }
+  }
+}
+
+// ---------------------------------------------------------------- equality fill
+template <typename U>
+__global__ void k_fill(U* __restrict__ keys, JobList fill) {
+  const unsigned long long nj = min(*fill.count, fill.cap);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (unsigned long long j = 0; j < nj; ++j) {
+    const Job job = fill.jobs[j];
+    const U v = (U)job.value;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < job.m; i += stride)
+      keys[job.start + i] = v;
+  }
+}
+
+// ---------------------------------------------------------------- level 1
+struct L1Aux {
+  uint64_t tile_base;
+  uint64_t cbase;
+  float S, T;
+  uint32_t f1;
+  uint32_t pad;
+};
+
+__global__ void __launch_bounds__(1024)
+k_l1_plan(Lists lists, SortLimits lim, Level1Ws w, uint32_t* err) {
+  __shared__ uint64_t ws[33];
+  __shared__ uint64_t s_rt, s_rc;
+  L1Aux* aux = (L1Aux*)w.aux;
+  const uint64_t nj = min((uint64_t)*lists.refine.count, min((uint64_t)lists.refine.cap, w.cap_jobs));
+  if (threadIdx.x == 0) { s_rt = 0; s_rc = 0; }
+  __syncthreads();
+  for (uint64_t j0 = 0; j0 < nj; j0 += blockDim.x) {
+    const uint64_t j = j0 + threadIdx.x;
+    uint64_t tiles = 0, f1 = 0;
+    float S = 0, T = 0;
+    if (j < nj) {
+      Job job = lists.refine.jobs[j];
+      const double width = job.Fhi - job.Flo;
+      uint64_t f = (job.m + lim.l1_target - 1) / lim.l1_target;
+      f = f < 2 ? 2 : (f > MAX_F1 ? MAX_F1 : f);
+      const double Sd = (double)f / width;
+      S = (float)Sd;
+      T = (float)(-job.Flo * Sd);
+      if (!(width > 0) || !isfinite(S) || !isfinite(T)) {
+        job.kind = JOB_FALLBACK;  // the model cannot split this range
+        push_job(lists.fallback, job, err);
+      } else {
+        f1 = f;
+        tiles = (job.m + L1_TILE - 1) / L1_TILE;
+      }
+      w.jmin[j] = ~0ull;
+      w.jmax[j] = 0ull;
+    }
+    uint64_t tt, tc;
+    const uint64_t et = block_excl_sum<uint64_t>(tiles, ws, &tt);
+    const uint64_t ec = block_excl_sum<uint64_t>(f1, ws, &tc);
+    if (j < nj) {
+      L1Aux x;
+      x.tile_base = s_rt + et;
+      x.cbase = s_rc + ec;
+      x.S = S;
+      x.T = T;
+      x.f1 = (uint32_t)f1;
+      x.pad = 0;
+      aux[j] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { s_rt += tt; s_rc += tc; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    L1Aux x{};
+    x.tile_base = s_rt;
+    x.cbase = s_rc;
+    aux[nj] = x;
+    if (s_rc > w.cap_c) set_error(err, ERR_BOUNDS);
+    w.totals[0] = s_rt;
+    w.totals[1] = s_rc > w.cap_c ? w.cap_c : s_rc;
+    w.totals[2] = nj;
+  }
+}
+
+__device__ __forceinline__ uint64_t aux_find_tile(const L1Aux* aux, uint64_t nj, uint64_t t) {
+  uint64_t lo = 0, hi = nj;  // first index with tile_base > t, minus one
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (aux[mid].tile_base <= t) lo = mid + 1; else hi = mid;
+  }
+  return lo - 1;
+}
+__device__ __forceinline__ uint64_t aux_find_c(const L1Aux* aux, uint64_t nj, uint64_t c) {
+  uint64_t lo = 0, hi = nj;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (aux[mid].cbase <= c) lo = mid + 1; else hi = mid;
+  }
+  return lo - 1;
+}
+
+template <int DT>
+__device__ __forceinline__ uint32_t l1_sub(typename KT<DT>::U u, const RootEval& r,
+                                           const LeafEval* leaves, const L1Aux& x) {
+  if (KT<DT>::is_nan(u)) return KT<DT>::neg(u) ? 0u : x.f1 - 1;
+  const float F = predict_F<DT>(u, r, leaves);
+  const float v = __fmaf_rn(F, x.S, x.T);
+  if (!(v > 0.0f)) return 0u;
+  if (v >= (float)(x.f1 - 1)) return x.f1 - 1;
+  return (uint32_t)v;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(L1_THREADS)
+k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, ModelPtrs M,
+          Lists lists, Level1Ws w) {
+  typedef typename KT<DT>::U U;
+  __shared__ uint32_t hc[MAX_F1];
+  __shared__ unsigned long long s_min, s_max;
+  const L1Aux* aux = (const L1Aux*)w.aux;
+  const uint64_t T = w.totals[0], nj = w.totals[2];
+  const RootEval r = M.hdr->root;
+  const LeafEval* leaves = M.leaf;
+  const int lane = threadIdx.x & 31;
+  for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
+    const uint64_t j = aux_find_tile(aux, nj, t);
+    const L1Aux x = aux[j];
+    const Job job = lists.refine.jobs[j];
+    const uint64_t off = (t - x.tile_base) * L1_TILE;
+    const uint32_t c = (uint32_t)min((uint64_t)L1_TILE, job.m - off);
+    const U* src = (job.src ? scratch : keys) + job.start + off;
+    for (uint32_t s = threadIdx.x; s < x.f1; s += blockDim.x) hc[s] = 0;
+    if (threadIdx.x == 0) { s_min = ~0ull; s_max = 0; }
+    __syncthreads();
+    unsigned long long mn = ~0ull, mx = 0;
+    for (uint32_t base = 0; base < c; base += blockDim.x) {
+      const uint32_t i = base + threadIdx.x;
+      uint32_t sub = 0xFFFFFFFFu;
+      if (i < c) {
+        const U u = src[i];
+        const uint64_t tk = KT<DT>::tk(u);
+        mn = min(mn, (unsigned long long)tk);
+        mx = max(mx, (unsigned long long)tk);
+        sub = l1_sub<DT>(u, r, leaves, x);
+      }
+      const unsigned peers = __match_any_sync(0xffffffffu, sub);
+      if (sub != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&hc[sub], (uint32_t)__popc(peers));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) { atomicMin(&s_min, mn); atomicMax(&s_max, mx); }
+    __syncthreads();
+    for (uint32_t s = threadIdx.x; s < x.f1; s += blockDim.x)
+      if (hc[s]) atomicAdd(&w.cnt[x.cbase + s], hc[s]);
+    if (threadIdx.x == 0) { atomicMin(&w.jmin[j], s_min); atomicMax(&w.jmax[j], s_max); }
+    __syncthreads();
+  }
+}
+
+__global__ void k_l1_cursor(Lists lists, Level1Ws w) {
+  const L1Aux* aux = (const L1Aux*)w.aux;
+  const uint64_t C = w.totals[1], nj = w.totals[2];
+  for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < C;
+       c += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t j = aux_find_c(aux, nj, c);
+    w.cur[c] = lists.refine.jobs[j].start + (w.off[c] - w.off[aux[j].cbase]);
+  }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(L1_THREADS)
+k_l1_scatter(typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, uint64_t n, ModelPtrs M,
+             Lists lists, Level1Ws w, uint32_t* err) {
+  typedef typename KT<DT>::U U;
+  constexpr int KPT = L1_TILE / L1_THREADS;
+  __shared__ uint32_t lc[MAX_F1 + 1];
+  __shared__ unsigned long long gp[MAX_F1];
+  __shared__ uint32_t ws[33];
+  extern __shared__ __align__(16) unsigned char dsm[];
+  U* stage = (U*)dsm;                                      // L1_TILE keys
+  uint16_t* ids = (uint16_t*)(dsm + sizeof(U) * L1_TILE);  // L1_TILE slot ids
+  const L1Aux* aux = (const L1Aux*)w.aux;
+  const uint64_t T = w.totals[0], nj = w.totals[2];
+  const RootEval r = M.hdr->root;
+  const LeafEval* leaves = M.leaf;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
+    const uint64_t j = aux_find_tile(aux, nj, t);
+    if (w.jmin[j] == w.jmax[j]) continue;  // homogeneous: filled, not moved
+    const L1Aux x = aux[j];
+    const Job job = lists.refine.jobs[j];
+    const uint64_t off = (t - x.tile_base) * L1_TILE;
+    const uint32_t c = (uint32_t)min((uint64_t)L1_TILE, job.m - off);
+    const U* src = (job.src ? scratch : keys) + job.start + off;
+    for (uint32_t s = threadIdx.x; s <= x.f1; s += blockDim.x) lc[s] = 0;
+    __syncthreads();
+    U u[KPT];
+    uint32_t sb[KPT], rk[KPT];
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const uint32_t i = k * L1_THREADS + threadIdx.x;
+      uint32_t sub = 0xFFFFFFFFu;
+      u[k] = 0;
+      if (i < c) { u[k] = src[i]; sub = l1_sub<DT>(u[k], r, leaves, x); }
+      sb[k] = sub;
+      const unsigned peers = __match_any_sync(0xffffffffu, sub);
+      const int leader = __ffs(peers) - 1;
+      uint32_t old = 0;
+      if (sub != 0xFFFFFFFFu && lane == leader) old = atomicAdd(&lc[sub], (uint32_t)__popc(peers));
+      old = __shfl_sync(0xffffffffu, old, leader);
+      rk[k] = old + __popc(peers & lt);
+    }
+    __syncthreads();
+    block_scan_array<uint32_t>(lc, (int)x.f1, ws);
+    if (threadIdx.x == 0) lc[x.f1] = c;
+    __syncthreads();
+    for (uint32_t s = threadIdx.x; s < x.f1; s += blockDim.x) {
+      const uint32_t cs = lc[s + 1] - lc[s];
+      if (cs) gp[s] = atomicAdd(&w.cur[x.cbase + s], (unsigned long long)cs);
+    }
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      if (sb[k] != 0xFFFFFFFFu) {
+        const uint32_t p = lc[sb[k]] + rk[k];
+        if (p < (uint32_t)L1_TILE) { stage[p] = u[k]; ids[p] = (uint16_t)sb[k]; }
+      }
+    }
+    __syncthreads();
+    for (uint32_t p = threadIdx.x; p < c; p += blockDim.x) {
+      const uint32_t s = ids[p];
+      const uint64_t dst = gp[s] + (p - lc[s]);
+      if (dst < n) keys[dst] = stage[p]; else set_error(err, ERR_BOUNDS);
+    }
+    __syncthreads();
+  }
+}
+
+template <int DT>
+__global__ void k_l1_classify(Lists lists, SortLimits lim, Level1Ws w, uint32_t* err) {
+  const L1Aux* aux = (const L1Aux*)w.aux;
+  const uint64_t C = w.totals[1], nj = w.totals[2];
+  for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < C;
+       c += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t cntc = w.off[c + 1] - w.off[c];
+    if (cntc == 0) continue;
+    const uint64_t j = aux_find_c(aux, nj, c);
+    const L1Aux x = aux[j];
+    const Job pj = lists.refine.jobs[j];
+    Job job;
+    job.value = 0;
+    if (w.jmin[j] == w.jmax[j]) {  // all keys of the bucket are equal (Is-Homogeneous)
+      job = pj;
+      job.kind = JOB_FILL;
+      job.value = (uint64_t)KT<DT>::from_tk(w.jmin[j]);
+      push_job(lists.fill, job, err);
+      continue;
+    }
+    const uint64_t sub = c - x.cbase;
+    const double wd = (pj.Fhi - pj.Flo) / (double)x.f1;
+    job.start = pj.start + (w.off[c] - w.off[x.cbase]);
+    job.m = cntc;
+    job.Flo = pj.Flo + (double)sub * wd;
+    job.Fhi = pj.Flo + (double)(sub + 1) * wd;
+    job.src = 0;
+    if (cntc <= lim.c_small) { job.kind = JOB_SORT; push_job(lists.sort_s, job, err); }
+    else if (cntc <= lim.c_large) { job.kind = JOB_SORT; push_job(lists.sort_l, job, err); }
+    else { job.kind = JOB_FALLBACK; push_job(lists.fallback, job, err); }
+  }
+}
+
+// ---------------------------------------------------------------- host enqueue
+template <int DT>
+static cudaError_t level0_dt(const Level0Args& a, size_t sh, size_t ss, const Lists& lists,
+                             const SortLimits& lim, cudaStream_t st, const Marks* mk, int mb) {
+  const int W = KT<DT>::W;
+  const L0Layout lh = l0_layout(W, a.L, a.f0, a.n_ext_max, false);
+  const L0Layout ls_ = l0_layout(W, a.L, a.f0, a.n_ext_max, true);
+  k_l0_hist<DT><<<a.c.G, P_THREADS, sh, st>>>(a, lh);
+  mark(mk, mb + 0, st);
+  const uint64_t M = (uint64_t)a.n_ext_max * a.c.G;
+  k_scan<uint32_t><<<a.scan_tiles, SC_THREADS, 0, st>>>(
+      a.hist, a.offs, M, nullptr, (uint64_t*)a.scan_status,
+      (uint32_t*)((uint64_t*)a.scan_status + a.scan_tiles), a.err);
+  mark(mk, mb + 1, st);
+  k_l0_scatter<DT><<<a.c.G, P_THREADS, ss, st>>>(a, ls_);
+  mark(mk, mb + 2, st);
+  k_classify0<DT><<<(a.n_ext_max + 255) / 256, 256, 0, st>>>(a, lists, lim);
+  mark(mk, mb + 3, st);
+  add_launches(4);
+  return cudaGetLastError();
+}
+
+static size_t l1_scatter_smem(int W) { return (size_t)L1_TILE * (W + 2); }
+
+cudaError_t level0_configure(int dt, size_t sh, size_t ss) {
+  cudaError_t e = cudaSuccess;
+#define LS_CFG(D)                                                                               \
+  e = cudaFuncSetAttribute(k_l0_hist<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh); \
+  if (e) return e;                                                                              \
+  e = cudaFuncSetAttribute(k_l1_scatter<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                           (int)l1_scatter_smem(KT<D>::W));                                     \
+  if (e) return e;                                                                              \
+  e = cudaFuncSetAttribute(k_l0_scatter<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+  switch (dt) {
+    case LS_F64: LS_CFG(LS_F64); break;
+    case LS_U64: LS_CFG(LS_U64); break;
+    case LS_F32: LS_CFG(LS_F32); break;
+    case LS_U32: LS_CFG(LS_U32); break;
+  }
+#undef LS_CFG
+  return e;
+}
+
+cudaError_t level0_enqueue(int dt, const Level0Args& a, size_t sh, size_t ss, const Lists& lists,
+                           const SortLimits& lim, cudaStream_t st, const Marks* mk, int mb) {
+  switch (dt) {
+    case LS_F64: return level0_dt<LS_F64>(a, sh, ss, lists, lim, st, mk, mb);
+    case LS_U64: return level0_dt<LS_U64>(a, sh, ss, lists, lim, st, mk, mb);
+    case LS_F32: return level0_dt<LS_F32>(a, sh, ss, lists, lim, st, mk, mb);
+    case LS_U32: return level0_dt<LS_U32>(a, sh, ss, lists, lim, st, mk, mb);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int DT>
+static cudaError_t level1_dt(const void* keys, const void* scratch, uint64_t n, const ModelPtrs& M,
+                             const Lists& lists, const SortLimits& lim, const Level1Ws& w,
+                             uint32_t* err, cudaStream_t st, int num_sms) {
+  typedef typename KT<DT>::U U;
+  cudaError_t e = cudaMemsetAsync(w.cnt, 0, w.cap_c * sizeof(uint32_t), st);
+  if (e) return e;
+  e = cudaMemsetAsync(w.scan_status, 0, w.scan_status_bytes, st);
+  if (e) return e;
+  k_l1_plan<<<1, 1024, 0, st>>>(lists, lim, w, err);
+  const int grid = 2 * num_sms;
+  k_l1_hist<DT><<<grid, L1_THREADS, 0, st>>>((const U*)keys, (const U*)scratch, M, lists, w);
+  const unsigned tiles = (unsigned)std::max<uint64_t>(1, (w.cap_c + SC_TILE - 1) / SC_TILE);
+  k_scan<uint32_t><<<tiles, SC_THREADS, 0, st>>>(w.cnt, w.off, w.cap_c, &w.totals[1],
+                                                 (uint64_t*)w.scan_status,
+                                                 (uint32_t*)((uint64_t*)w.scan_status + tiles), err);
+  k_l1_cursor<<<grid, 256, 0, st>>>(lists, w);
+  k_l1_scatter<DT><<<grid, L1_THREADS, l1_scatter_smem(KT<DT>::W), st>>>((U*)keys, (const U*)scratch,
+                                                                      n, M, lists, w, err);
+  k_l1_classify<DT><<<grid, 256, 0, st>>>(lists, lim, w, err);
+  add_launches(6);
+  return cudaGetLastError();
+}
+
+cudaError_t level1_enqueue(int dt, const void* keys, const void* scratch, uint64_t n,
+                           const ModelPtrs& M, uint32_t f0, const Lists& lists,
+                           const SortLimits& lim, const Level1Ws& w, uint32_t* err,
+                           cudaStream_t st, int num_sms) {
+  (void)f0;
+  switch (dt) {
+    case LS_F64: return level1_dt<LS_F64>(keys, scratch, n, M, lists, lim, w, err, st, num_sms);
+    case LS_U64: return level1_dt<LS_U64>(keys, scratch, n, M, lists, lim, w, err, st, num_sms);
+    case LS_F32: return level1_dt<LS_F32>(keys, scratch, n, M, lists, lim, w, err, st, num_sms);
+    case LS_U32: return level1_dt<LS_U32>(keys, scratch, n, M, lists, lim, w, err, st, num_sms);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t fill_enqueue(int dt, void* keys, const Lists& lists, uint64_t fill_cap,
+                         cudaStream_t st, int num_sms) {
+  (void)fill_cap;
+  if (dt == LS_F64 || dt == LS_U64)
+    k_fill<uint64_t><<<2 * num_sms, 256, 0, st>>>((uint64_t*)keys, lists.fill);
+  else
+    k_fill<uint32_t><<<2 * num_sms, 256, 0, st>>>((uint32_t*)keys, lists.fill);
+  add_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace ls

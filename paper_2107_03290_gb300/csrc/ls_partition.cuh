@@ -1,0 +1,80 @@
+// Host-side interface of the partitioning kernels (ls_partition.cu) and the
+// in-bucket kernels (ls_bucket.cu).
+#pragma once
+#include "ls_internal.cuh"
+
+namespace ls {
+
+constexpr int P_THREADS = 512;      // level-0 histogram / scatter CTAs
+constexpr int P_TILE = 4096;        // keys per tile
+constexpr int L1_THREADS = 512;
+constexpr int L1_TILE = 4096;
+
+// Contiguous chunk per CTA of the 16-byte aligned body [a0, a1); CTA 0 also
+// handles the head [0, a0) and the tail [a1, n).
+struct Chunking {
+  uint64_t n, a0, a1, ch;
+  uint32_t G;
+};
+
+struct Level0Args {
+  const void* keys;
+  void* scratch;
+  Chunking c;
+  ModelPtrs M;
+  uint32_t f0;
+  uint32_t n_ext_max;
+  uint32_t L;
+  uint32_t* hist;        // n_ext_max * G
+  uint64_t* offs;        // n_ext_max * G + 1
+  void* scan_status;     // scan work (status words + counter), zeroed by the caller
+  uint32_t scan_tiles;
+  uint32_t* err;
+};
+
+// Lists produced by classification (device-side counters).
+struct Lists {
+  JobList fill, sort_s, sort_l, refine, fallback;
+};
+
+struct SortLimits {
+  uint64_t c_small;      // segments up to this go to the small in-bucket kernel
+  uint64_t c_large;      // ... up to this to the large kernel, above: refine/fallback
+  uint64_t l1_target;    // target sub-bucket size of the level-1 split
+};
+
+struct Level1Ws {
+  void* aux;             // per refine job: tile base, count base, f1, S, T
+  unsigned long long* totals;   // [0] tiles, [1] counters
+  uint32_t* cnt;         // counters (cap_c)
+  uint64_t* off;         // cap_c + 1
+  unsigned long long* cur;   // cap_c
+  unsigned long long* jmin;  // per job
+  unsigned long long* jmax;  // per job
+  void* scan_status;
+  size_t scan_status_bytes;
+  uint64_t cap_c;
+  uint64_t cap_jobs;
+  uint64_t cap_tiles;
+};
+
+size_t level0_smem_hist(int dt, uint32_t L, uint32_t f0, uint32_t n_ext_max);
+size_t level0_smem_scatter(int dt, uint32_t L, uint32_t f0, uint32_t n_ext_max);
+cudaError_t level0_configure(int dt, size_t smem_hist, size_t smem_scatter);
+cudaError_t level0_enqueue(int dt, const Level0Args& a, size_t smem_hist, size_t smem_scatter,
+                           const Lists& lists, const SortLimits& lim, cudaStream_t st,
+                           const Marks* mk = nullptr, int mbase = 0);
+cudaError_t level1_enqueue(int dt, const void* keys, const void* scratch, uint64_t n,
+                           const ModelPtrs& M, uint32_t f0, const Lists& lists,
+                           const SortLimits& lim, const Level1Ws& w, uint32_t* err,
+                           cudaStream_t st, int num_sms);
+cudaError_t fill_enqueue(int dt, void* keys, const Lists& lists, uint64_t fill_cap,
+                         cudaStream_t st, int num_sms);
+cudaError_t buckets_configure(int dt);
+cudaError_t buckets_enqueue(int dt, void* keys, void* scratch, uint64_t n, const ModelPtrs& M,
+                            const Lists& lists, uint64_t cap_s, uint64_t cap_l,
+                            uint64_t cap_fb, unsigned long long* job_ctrs, uint32_t* err,
+                            cudaStream_t st, int num_sms, const Marks* mk = nullptr,
+                            int mbase = 0);
+
+}  // namespace ls

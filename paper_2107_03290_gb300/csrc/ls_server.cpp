@@ -1,0 +1,205 @@
+// Serving loop of the learned sort: continuous batching of sort requests.
+//
+// A dispatcher thread admits queued requests while the bytes of the admitted
+// requests (keys + scratch) stay within the HBM budget and the number on the
+// GPU stays below max_inflight; each admitted request is enqueued on one of
+// the server's streams, so requests overlap on the device.  Completion is
+// detected with CUDA events; waiters get queue / device / total latency.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/ls.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  uint64_t ticket;
+  void* keys;
+  size_t n;
+  ls_dtype dt;
+  uint64_t bytes;
+  Clock::time_point t_submit, t_launch, t_done;
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr;
+  int stream = -1;
+  bool done = false;
+  ls_request_stats st{};
+};
+
+}  // namespace
+
+struct ls_server {
+  ls_server_config cfg{};
+  int device = 0;
+  std::vector<cudaStream_t> streams;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request*> queue;
+  std::vector<Request*> inflight;
+  std::unordered_map<uint64_t, Request*> all;
+  uint64_t next_ticket = 1;
+  uint64_t inflight_bytes = 0;
+  uint32_t rr = 0;
+  bool stop = false;
+  std::thread th;
+};
+
+static uint64_t request_bytes(size_t n, ls_dtype dt) {
+  const uint64_t w = (dt == LS_F64 || dt == LS_U64) ? 8 : 4;
+  return 2 * n * w + (64ull << 20);  // keys + scratch + model/job space
+}
+
+static void dispatcher(ls_server* s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    // retire finished requests
+    for (size_t i = 0; i < s->inflight.size();) {
+      Request* r = s->inflight[i];
+      if (cudaEventQuery(r->ev_end) == cudaSuccess) {
+        r->t_done = Clock::now();
+        float ms = 0;
+        cudaEventElapsedTime(&ms, r->ev_start, r->ev_end);
+        r->st.device_ms = ms;
+        r->st.queue_ms = std::chrono::duration<double, std::milli>(r->t_launch - r->t_submit).count();
+        r->st.total_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+        r->st.status = ls_stream_status(s->streams[r->stream]);
+        r->done = true;
+        s->inflight_bytes -= r->bytes;
+        s->inflight[i] = s->inflight.back();
+        s->inflight.pop_back();
+        s->cv_done.notify_all();
+      } else {
+        ++i;
+      }
+    }
+    // admit while budget and slots allow (arrival order)
+    while (!s->queue.empty() && s->inflight.size() < s->cfg.max_inflight &&
+           s->inflight_bytes + s->queue.front()->bytes <= s->cfg.hbm_budget_bytes) {
+      Request* r = s->queue.front();
+      s->queue.pop_front();
+      r->stream = (int)(s->rr++ % s->streams.size());
+      cudaStream_t st = s->streams[r->stream];
+      r->t_launch = Clock::now();
+      cudaEventRecord(r->ev_start, st);
+      const ls_status rc = ls_sort(r->keys, r->n, r->dt, st);
+      cudaEventRecord(r->ev_end, st);
+      if (rc != LS_OK) r->st.status = rc;
+      s->inflight_bytes += r->bytes;
+      s->inflight.push_back(r);
+    }
+    if (s->stop && s->queue.empty() && s->inflight.empty()) break;
+    if (s->inflight.empty() && s->queue.empty()) {
+      s->cv_work.wait(lk);
+    } else {
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      lk.lock();
+    }
+  }
+}
+
+extern "C" {
+
+ls_status ls_server_create(const ls_server_config* cfg, ls_server** out) {
+  if (!out) return LS_ERR_INVALID;
+  ls_server* s = new ls_server();
+  if (cfg) s->cfg = *cfg;
+  if (!s->cfg.hbm_budget_bytes) s->cfg.hbm_budget_bytes = 120ull << 30;
+  if (!s->cfg.max_inflight) s->cfg.max_inflight = 64;
+  if (!s->cfg.max_queue) s->cfg.max_queue = 4096;
+  if (!s->cfg.streams) s->cfg.streams = 4;
+  if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return LS_ERR_CUDA; }
+  for (uint32_t i = 0; i < s->cfg.streams; ++i) {
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      for (auto x : s->streams) cudaStreamDestroy(x);
+      delete s;
+      return LS_ERR_CUDA;
+    }
+    s->streams.push_back(st);
+  }
+  s->th = std::thread(dispatcher, s);
+  *out = s;
+  return LS_OK;
+}
+
+ls_status ls_server_submit(ls_server* s, void* keys, size_t n, ls_dtype dtype, uint64_t* ticket) {
+  if (!s || !ticket || dtype < LS_F64 || dtype > LS_U32 || (n > 0 && !keys)) return LS_ERR_INVALID;
+  const uint64_t bytes = request_bytes(n, dtype);
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stop) return LS_ERR_CANCELLED;
+  if (bytes > s->cfg.hbm_budget_bytes || s->queue.size() >= s->cfg.max_queue) return LS_ERR_BUSY;
+  Request* r = new Request();
+  r->ticket = s->next_ticket++;
+  r->keys = keys;
+  r->n = n;
+  r->dt = dtype;
+  r->bytes = bytes;
+  r->t_submit = Clock::now();
+  cudaEventCreate(&r->ev_start);
+  cudaEventCreate(&r->ev_end);
+  s->all[r->ticket] = r;
+  s->queue.push_back(r);
+  *ticket = r->ticket;
+  s->cv_work.notify_one();
+  return LS_OK;
+}
+
+ls_status ls_server_wait(ls_server* s, uint64_t ticket, uint32_t timeout_ms, ls_request_stats* st) {
+  if (!s) return LS_ERR_INVALID;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->all.find(ticket);
+  if (it == s->all.end()) return LS_ERR_INVALID;
+  Request* r = it->second;
+  auto pred = [&] { return r->done; };
+  if (timeout_ms == UINT32_MAX) s->cv_done.wait(lk, pred);
+  else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred)) return LS_ERR_TIMEOUT;
+  if (st) *st = r->st;
+  const ls_status rc = r->st.status;
+  cudaEventDestroy(r->ev_start);
+  cudaEventDestroy(r->ev_end);
+  s->all.erase(it);
+  delete r;
+  return rc;
+}
+
+ls_status ls_server_destroy(ls_server* s) {
+  if (!s) return LS_ERR_INVALID;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->cv_work.notify_all();
+  }
+  s->th.join();
+  for (auto& kv : s->all) {
+    cudaEventDestroy(kv.second->ev_start);
+    cudaEventDestroy(kv.second->ev_end);
+    delete kv.second;
+  }
+  for (auto x : s->streams) cudaStreamDestroy(x);
+  delete s;
+  return LS_OK;
+}
+
+ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dtype dtype,
+                        void* stream) {
+  if (count > 0 && (!keys || !n)) return LS_ERR_INVALID;
+  for (size_t i = 0; i < count; ++i) {
+    const ls_status rc = ls_sort(keys[i], n[i], dtype, stream);
+    if (rc != LS_OK) return rc;
+  }
+  return LS_OK;
+}
+
+}  // extern "C"

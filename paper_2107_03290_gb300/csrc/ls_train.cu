@@ -1,0 +1,518 @@
+// Sample-and-train: the RMI eCDF model of Sec. 2 / Sec. 5.1 (two layers,
+// linear leaves, trained on a stratified 1% sample), plus the heavy-value set
+// that feeds the equality buckets.
+//
+//  1. gather s keys at stratified offsets, as total-order keys;
+//  2. LSD radix sort of the sample (ls_radix.cuh);
+//  3. FP64 least squares: root over all finite sample keys against their eCDF
+//     rank (count of sample keys below x, ties take the first rank), then one
+//     line per leaf over the keys the root routes to it; slopes clamped to >= 0
+//     and each leaf's output clamped to [lo_l, hi_l] so that F is monotone;
+//  4. FP32 evaluation parameters on a 64-bit fixed-point grid (integer ops
+//     only per key, no FP64 in the per-key path);
+//  5. heavy values: sample runs of length >= tau, at most `hpb` per level-0
+//     bucket (longest first), each given an equality slot.
+// All reductions use a fixed order, so a model is bit-reproducible run to run.
+#include <cfloat>
+
+#include "ls_radix.cuh"
+#include "ls_train.cuh"
+
+namespace ls {
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {  // SplitMix64 output function
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <int DT>
+__global__ void k_sample(const typename KT<DT>::U* __restrict__ keys, uint64_t n, uint64_t s,
+                         uint64_t seed, uint64_t* __restrict__ out) {
+  uint64_t stride = n / s;
+  if (stride == 0) stride = 1;
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < s;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t base = (uint64_t)(((unsigned __int128)k * n) / s);
+    uint64_t i = base + mix64(seed ^ k) % stride;
+    if (i >= n) i = n - 1;  // unreachable by the formula; keeps the load in bounds
+    out[k] = KT<DT>::tk(keys[i]);
+  }
+}
+
+__global__ void k_train_init(DevModel* hdr, uint64_t s, uint32_t* leaf_beg, uint32_t* leaf_end,
+                             int L, double* partials) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    hdr->s = s;
+    hdr->s_lo = ~0ull;
+    hdr->s_fin = 0;
+    hdr->nheavy = 0;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L; i += gridDim.x * blockDim.x) {
+    leaf_beg[i] = 0;
+    leaf_end[i] = 0;
+  }
+}
+
+// Finite keys are contiguous in total order: [s_lo, s_hi).
+template <int DT>
+__global__ void k_finite_range(const uint64_t* __restrict__ tk, uint64_t s, DevModel* hdr,
+                               unsigned long long* hi_out) {
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < s;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    if (KT<DT>::finite(KT<DT>::from_tk(tk[k]))) {
+      atomicMin((unsigned long long*)&hdr->s_lo, (unsigned long long)k);
+      atomicMax(hi_out, (unsigned long long)(k + 1));
+    }
+  }
+}
+
+__global__ void k_finite_fix(DevModel* hdr, const unsigned long long* hi) {
+  if (hdr->s_lo == ~0ull || *hi <= hdr->s_lo) {
+    hdr->s_lo = 0;
+    hdr->s_fin = 0;
+  } else {
+    hdr->s_fin = *hi - hdr->s_lo;
+  }
+}
+
+// first_rank[k]: index (within the finite range) of the first key equal to key k.
+__global__ void k_first_rank(const uint64_t* __restrict__ tk, const DevModel* hdr,
+                             uint32_t* __restrict__ rank, uint64_t s_cap) {
+  const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
+  const uint64_t* t = tk + lo;
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < m;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t v = t[k];
+    if (k == 0 || t[k - 1] != v) { rank[k] = (uint32_t)k; continue; }
+    uint64_t a = 0, b = k;  // lower_bound in [0, k)
+    while (a < b) {
+      const uint64_t mid = (a + b) >> 1;
+      if (t[mid] < v) a = mid + 1; else b = mid;
+    }
+    rank[k] = (uint32_t)a;
+  }
+}
+
+constexpr int FIT_BLOCKS = 128;
+constexpr int FIT_THREADS = 256;
+
+__device__ __forceinline__ double block_sum_d(double v, double* ws) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) ws[wid] = v;
+  __syncthreads();
+  double r = 0;
+  if (wid == 0) {
+    r = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  __syncthreads();
+  return r;  // valid in thread 0
+}
+
+template <int DT>
+__device__ __forceinline__ double sample_x(const uint64_t* tk, uint64_t lo, uint64_t k) {
+  return KT<DT>::dbl(KT<DT>::from_tk(tk[lo + k]));
+}
+
+// pass 0: sum x, sum y; pass 1: centred sums about (mx, my).
+template <int DT>
+__global__ void __launch_bounds__(FIT_THREADS)
+k_fit_sums(const uint64_t* __restrict__ tk, const uint32_t* __restrict__ rank,
+           const DevModel* hdr, int pass, double* partials) {
+  __shared__ double ws[33];
+  const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
+  const uint64_t chunk = (m + gridDim.x - 1) / gridDim.x;
+  const uint64_t b = blockIdx.x * chunk, e = min(m, b + chunk);
+  const double inv_m = m ? 1.0 / (double)m : 0.0;
+  const double mx = hdr->root64[1], my = hdr->root64[2];
+  double s0 = 0, s1 = 0;
+  for (uint64_t k = b + threadIdx.x; k < e; k += blockDim.x) {
+    const double x = sample_x<DT>(tk, lo, k);
+    const double y = (double)rank[k] * inv_m;
+    if (pass == 0) { s0 += x; s1 += y; }
+    else { const double dx = x - mx; s0 += dx * dx; s1 += dx * (y - my); }
+  }
+  s0 = block_sum_d(s0, ws);
+  s1 = block_sum_d(s1, ws);
+  if (threadIdx.x == 0) { partials[2 * blockIdx.x] = s0; partials[2 * blockIdx.x + 1] = s1; }
+}
+
+__global__ void k_fit_root(DevModel* hdr, const double* partials, int nblk, int pass) {
+  if (threadIdx.x != 0) return;
+  double s0 = 0, s1 = 0;
+  for (int i = 0; i < nblk; ++i) { s0 += partials[2 * i]; s1 += partials[2 * i + 1]; }
+  const uint64_t m = hdr->s_fin;
+  if (pass == 0) {
+    const double mx = m ? s0 / (double)m : 0.0, my = m ? s1 / (double)m : 0.5;
+    hdr->root64[0] = 0.0;
+    hdr->root64[1] = isfinite(mx) ? mx : 0.0;
+    hdr->root64[2] = my;
+  } else {
+    double a = (s0 > 0) ? s1 / s0 : 0.0;
+    if (!(a >= 0) || !isfinite(a) || !isfinite(hdr->root64[1])) a = 0.0;
+    hdr->root64[0] = a;
+  }
+}
+
+// FP64 routing used in training: leaf = clamp(floor(L * (a (x - c) + b))).
+__device__ __forceinline__ int leaf64(const double* r, int L, double x) {
+  const double lin = (r[0] == 0.0) ? r[2] : __fma_rn(r[0], __dsub_rn(x, r[1]), r[2]);
+  const double w = __dmul_rn((double)L, lin);
+  if (!(w >= 0.0)) return 0;
+  if (w >= (double)L) return L - 1;
+  return (int)floor(w);
+}
+
+template <int DT>
+__global__ void k_fit_route(const uint64_t* __restrict__ tk, const DevModel* hdr, int L,
+                            uint32_t* leaf_beg, uint32_t* leaf_end) {
+  const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
+  const double r[3] = {hdr->root64[0], hdr->root64[1], hdr->root64[2]};
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < m;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    const int l = leaf64(r, L, sample_x<DT>(tk, lo, k));
+    if (k == 0 || leaf64(r, L, sample_x<DT>(tk, lo, k - 1)) != l) leaf_beg[l] = (uint32_t)k;
+    if (k + 1 == m || leaf64(r, L, sample_x<DT>(tk, lo, k + 1)) != l) leaf_end[l] = (uint32_t)(k + 1);
+  }
+}
+
+// One block per leaf: least squares on the leaf's points (two passes).
+template <int DT>
+__global__ void __launch_bounds__(FIT_THREADS)
+k_fit_leaf(const uint64_t* __restrict__ tk, const uint32_t* __restrict__ rank, const DevModel* hdr,
+           const uint32_t* leaf_beg, const uint32_t* leaf_end, double* leaf) {
+  __shared__ double ws[33];
+  __shared__ double s_mx, s_my;
+  const int l = blockIdx.x;
+  const uint64_t b = leaf_beg[l], e = leaf_end[l];
+  double* q = leaf + 5 * (size_t)l;
+  if (e <= b) {
+    if (threadIdx.x == 0) { q[0] = 0; q[1] = 0; q[2] = -1; q[3] = -1; q[4] = 0; }
+    return;
+  }
+  const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
+  const double inv_m = 1.0 / (double)m;
+  const uint64_t cnt = e - b;
+  double sx = 0, sy = 0;
+  for (uint64_t k = b + threadIdx.x; k < e; k += blockDim.x) {
+    sx += sample_x<DT>(tk, lo, k);
+    sy += (double)rank[k] * inv_m;
+  }
+  sx = block_sum_d(sx, ws);
+  sy = block_sum_d(sy, ws);
+  if (threadIdx.x == 0) { s_mx = sx / (double)cnt; s_my = sy / (double)cnt; }
+  __syncthreads();
+  const double mx = s_mx, my = s_my;
+  double sxx = 0, sxy = 0;
+  for (uint64_t k = b + threadIdx.x; k < e; k += blockDim.x) {
+    const double dx = sample_x<DT>(tk, lo, k) - mx;
+    sxx += dx * dx;
+    sxy += dx * ((double)rank[k] * inv_m - my);
+  }
+  sxx = block_sum_d(sxx, ws);
+  sxy = block_sum_d(sxy, ws);
+  if (threadIdx.x == 0) {
+    double a = (cnt >= 2 && sxx > 0) ? sxy / sxx : 0.0;
+    if (!(a >= 0) || !isfinite(a) || !isfinite(mx)) a = 0.0;
+    q[0] = a;
+    q[1] = isfinite(mx) ? mx : 0.0;
+    q[2] = my;
+    q[3] = (double)rank[b] / (double)m;  // lo: eCDF of the leaf's first sample key
+    q[4] = 0;
+  }
+}
+
+__device__ __forceinline__ int bitlen64(uint64_t v) { return v ? 64 - __clzll((long long)v) : 0; }
+
+__device__ __forceinline__ float fp32_sat(double d) {
+  if (d >= (double)FLT_MAX) return FLT_MAX;
+  return __double2float_rn(d);
+}
+
+__device__ __forceinline__ uint64_t absdiff(int64_t a, int64_t b) {
+  const int64_t d = a - b;
+  return d < 0 ? (uint64_t)(-d) : (uint64_t)d;
+}
+
+// Empty leaves, hi bounds, and the FP32 evaluation parameters.
+template <int DT>
+__global__ void __launch_bounds__(1024)
+k_fit_final(const uint64_t* __restrict__ tk, DevModel* hdr, int L, const uint32_t* leaf_beg,
+            const uint32_t* leaf_end, double* leaf, LeafEval* ev) {
+  __shared__ int s_E;
+  const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
+  // next non-empty leaf to the right, by one warp over L/32-leaf ranges
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const int per = (L + 31) / 32;
+    const int a = lane * per, b = min(L, a + per);
+    int first = L;
+    for (int l = b - 1; l >= a; --l)
+      if (leaf[5 * (size_t)l + 3] >= 0) first = l;
+    // suffix minimum over lanes > lane
+    int suf = first;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_down_sync(0xffffffffu, suf, o);
+      if (lane + o < 32) suf = min(suf, v);
+    }
+    int nxt = __shfl_down_sync(0xffffffffu, suf, 1);
+    if (lane == 31) nxt = L;
+    double next_lo = (nxt < L) ? leaf[5 * (size_t)nxt + 3] : 1.0;
+    for (int l = b - 1; l >= a; --l) {
+      double* q = leaf + 5 * (size_t)l;
+      if (q[3] < 0) { q[3] = next_lo; q[2] = next_lo; q[0] = 0; q[1] = 0; }
+      q[4] = next_lo;
+      next_lo = q[3];
+    }
+    if (lane == 0) {
+      double R = 0;
+      if (m) {
+        const double x0 = sample_x<DT>(tk, lo, 0), x1 = sample_x<DT>(tk, lo, m - 1);
+        R = fmax(fabs(x0), fabs(x1));
+      }
+      s_E = (R > 0) ? ilogb(R) + 1 - 61 : 0;
+    }
+  }
+  __syncthreads();
+  const int E = s_E;
+  if (threadIdx.x == 0) {
+    const double* r = hdr->root64;
+    const int64_t c0 = fx_f64bits((uint64_t)__double_as_longlong(r[1]), E);
+    uint64_t span = 0;
+    if (m) {
+      span = max(absdiff(fx_f64bits((uint64_t)__double_as_longlong(sample_x<DT>(tk, lo, 0)), E), c0),
+                 absdiff(fx_f64bits((uint64_t)__double_as_longlong(sample_x<DT>(tk, lo, m - 1)), E), c0));
+    }
+    const int sh = max(0, bitlen64(span) - 30);
+    RootEval re;
+    re.cq = c0;
+    re.sh = sh;
+    re.E = E;
+    re.L = L;
+    re.pad = 0;
+    re.A = fp32_sat(ldexp(r[0] * (double)L, E + sh));
+    re.B = __double2float_rn(r[2] * (double)L);
+    hdr->root = re;
+  }
+  for (int l = threadIdx.x; l < L; l += blockDim.x) {
+    const double* q = leaf + 5 * (size_t)l;
+    LeafEval e;
+    e.pad = 0;
+    const uint32_t b = leaf_beg[l], en = leaf_end[l];
+    if (en <= b) {
+      e.cq = 0; e.sh = 0; e.A = 0.0f;
+    } else {
+      const int64_t c = fx_f64bits((uint64_t)__double_as_longlong(q[1]), E);
+      const uint64_t span =
+          max(absdiff(fx_f64bits((uint64_t)__double_as_longlong(sample_x<DT>(tk, lo, b)), E), c),
+              absdiff(fx_f64bits((uint64_t)__double_as_longlong(sample_x<DT>(tk, lo, en - 1)), E), c));
+      const int sh = max(0, bitlen64(span) - 30);
+      e.cq = c; e.sh = sh;
+      e.A = fp32_sat(ldexp(q[0], E + sh));
+    }
+    e.B = __double2float_rn(q[2]);
+    e.LO = __double2float_rn(q[3]);
+    e.HI = __double2float_rn(q[4]);
+    ev[l] = e;
+  }
+}
+
+// ---------------------------------------------------------------- heavy set
+template <int DT>
+__global__ void k_heavy_flags(const uint64_t* __restrict__ tk, const DevModel* hdr, uint64_t tau,
+                              uint32_t* __restrict__ flags, uint64_t s_cap) {
+  const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
+  const uint64_t* t = tk + lo;
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < s_cap;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t f = 0;
+    if (k < m && tau >= 1 && k + tau - 1 < m) {
+      const uint64_t v = t[k];
+      if ((k == 0 || t[k - 1] != v) && t[k + tau - 1] == v) f = 1;
+    }
+    flags[k] = f;
+  }
+}
+
+struct Cand {
+  uint64_t tk;
+  uint64_t len;
+  uint32_t bucket;
+  uint32_t pad;
+};
+
+template <int DT>
+__global__ void k_heavy_compact(const uint64_t* __restrict__ tk, const DevModel* hdr,
+                                const uint32_t* __restrict__ flags, const uint64_t* __restrict__ pos,
+                                const LeafEval* __restrict__ leaves, uint32_t f0, Cand* cand,
+                                uint64_t cand_cap) {
+  const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
+  const uint64_t* t = tk + lo;
+  const RootEval r = hdr->root;
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < m;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    if (!flags[k]) continue;
+    const uint64_t v = t[k];
+    uint64_t a = k, b = m;  // upper_bound of v in [k, m)
+    while (a < b) {
+      const uint64_t mid = (a + b) >> 1;
+      if (t[mid] <= v) a = mid + 1; else b = mid;
+    }
+    const uint64_t p = pos[k];
+    if (p < cand_cap) {
+      Cand c;
+      c.tk = v;
+      c.len = a - k;
+      c.bucket = bucket_of<DT>(KT<DT>::from_tk(v), r, leaves, f0);
+      c.pad = 0;
+      cand[p] = c;
+    }
+  }
+}
+
+// One thread per bucket: keep the hpb longest runs (ties: smaller key), by key.
+__global__ void k_heavy_select(const Cand* __restrict__ cand, const uint64_t* ncand_ptr,
+                               uint64_t cand_cap, uint32_t f0, int hpb, uint64_t* sel,
+                               uint32_t* nh) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= f0) return;
+  const uint64_t nc = min(*ncand_ptr, cand_cap);
+  uint64_t a = 0, e = nc;  // lower_bound of bucket b
+  while (a < e) { const uint64_t mid = (a + e) >> 1; if (cand[mid].bucket < b) a = mid + 1; else e = mid; }
+  uint64_t a2 = a, e2 = nc;  // lower_bound of bucket b+1
+  while (a2 < e2) { const uint64_t mid = (a2 + e2) >> 1; if (cand[mid].bucket <= b) a2 = mid + 1; else e2 = mid; }
+  uint64_t ktk[MAX_HPB], klen[MAX_HPB];
+  int cnt = 0;
+  for (uint64_t i = a; i < a2; ++i) {
+    const uint64_t t = cand[i].tk, len = cand[i].len;
+    // insert into the top list ordered by (len desc, tk asc)
+    int p = cnt;
+    while (p > 0 && (klen[p - 1] < len || (klen[p - 1] == len && ktk[p - 1] > t))) --p;
+    if (p >= hpb) continue;
+    const int last = min(cnt, hpb - 1);
+    for (int q = last; q > p; --q) { ktk[q] = ktk[q - 1]; klen[q] = klen[q - 1]; }
+    ktk[p] = t; klen[p] = len;
+    if (cnt < hpb) ++cnt;
+  }
+  // order by key
+  for (int i = 1; i < cnt; ++i) {
+    const uint64_t t = ktk[i];
+    int j = i;
+    while (j > 0 && ktk[j - 1] > t) { ktk[j] = ktk[j - 1]; --j; }
+    ktk[j] = t;
+  }
+  for (int i = 0; i < cnt; ++i) sel[(size_t)b * hpb + i] = ktk[i];
+  nh[b] = (uint32_t)cnt;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(1024)
+k_heavy_heads(const uint64_t* __restrict__ sel, const uint32_t* __restrict__ nh, uint32_t f0,
+              int hpb, DevModel* hdr, const LeafEval* __restrict__ leaves, BucketHead* heads,
+              HeavyEntry* heavy) {
+  __shared__ uint32_t ws[33];
+  __shared__ uint32_t s_run;
+  if (threadIdx.x == 0) s_run = 0;
+  __syncthreads();
+  const RootEval r = hdr->root;
+  for (uint32_t b0 = 0; b0 < f0; b0 += blockDim.x) {
+    const uint32_t b = b0 + threadIdx.x;
+    const uint32_t c = b < f0 ? nh[b] : 0;
+    uint32_t tot;
+    const uint32_t ex = block_excl_sum<uint32_t>(c, ws, &tot);
+    const uint32_t hoff = s_run + ex;
+    if (b < f0) {
+      BucketHead h;
+      h.ext_base = b + 2 * hoff;
+      h.hoff_nh = (hoff << 4) | c;
+      heads[b] = h;
+      for (uint32_t j = 0; j < c; ++j) {
+        HeavyEntry he;
+        he.tk = sel[(size_t)b * hpb + j];
+        he.F = predict_F<DT>(KT<DT>::from_tk(he.tk), r, leaves);
+        he.pad = 0;
+        heavy[hoff + j] = he;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_run += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const uint32_t H = s_run;
+    BucketHead h;
+    h.ext_base = f0 + 2 * H;
+    h.hoff_nh = H << 4;
+    heads[f0] = h;
+    hdr->nheavy = H;
+    hdr->n_ext = f0 + 2 * H;
+  }
+}
+
+// ---------------------------------------------------------------- host enqueue
+template <int DT>
+static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, const TrainWs& W,
+                            const ModelPtrs& M, uint32_t* err, cudaStream_t st, int num_sms) {
+  typedef typename KT<DT>::U U;
+  const U* keys = (const U*)keys_v;
+  const uint64_t s = P.s;
+  const int L = (int)P.L;
+  const int gs = (int)std::min<uint64_t>((s + 255) / 256, 8ull * num_sms);
+  k_train_init<<<std::max(1, (L + 255) / 256), 256, 0, st>>>(M.hdr, s, M.leaf_beg, M.leaf_end, L,
+                                                             W.partials);
+  k_sample<DT><<<std::max(1, gs), 256, 0, st>>>(keys, n, s, P.seed, W.smp_a);
+  cudaError_t e = rs_sort_enqueue(W.smp_a, W.smp_b, s, nullptr, nullptr, W.rs, err, st, num_sms);
+  if (e) return e;
+  e = cudaMemsetAsync(W.hi, 0, sizeof(unsigned long long), st);
+  if (e) return e;
+  k_finite_range<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, s, M.hdr, W.hi);
+  k_finite_fix<<<1, 1, 0, st>>>(M.hdr, W.hi);
+  k_first_rank<<<std::max(1, gs), 256, 0, st>>>(W.smp_a, M.hdr, W.rank, s);
+  k_fit_sums<DT><<<FIT_BLOCKS, FIT_THREADS, 0, st>>>(W.smp_a, W.rank, M.hdr, 0, W.partials);
+  k_fit_root<<<1, 32, 0, st>>>(M.hdr, W.partials, FIT_BLOCKS, 0);
+  k_fit_sums<DT><<<FIT_BLOCKS, FIT_THREADS, 0, st>>>(W.smp_a, W.rank, M.hdr, 1, W.partials);
+  k_fit_root<<<1, 32, 0, st>>>(M.hdr, W.partials, FIT_BLOCKS, 1);
+  k_fit_route<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, M.hdr, L, M.leaf_beg, M.leaf_end);
+  k_fit_leaf<DT><<<L, FIT_THREADS, 0, st>>>(W.smp_a, W.rank, M.hdr, M.leaf_beg, M.leaf_end, M.leaf64);
+  k_fit_final<DT><<<1, 1024, 0, st>>>(W.smp_a, M.hdr, L, M.leaf_beg, M.leaf_end, M.leaf64, M.leaf);
+  // heavy values
+  const uint64_t tau = P.tau;
+  k_heavy_flags<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, M.hdr, tau, W.flags, s);
+  e = cudaMemsetAsync(W.scan_status, 0, W.scan_status_bytes, st);
+  if (e) return e;
+  const unsigned sblocks = (unsigned)std::max<uint64_t>(1, (s + SC_TILE - 1) / SC_TILE);
+  k_scan<uint32_t><<<sblocks, SC_THREADS, 0, st>>>(W.flags, W.cpos, s, nullptr,
+                                                   (uint64_t*)W.scan_status,
+                                                   (uint32_t*)((uint64_t*)W.scan_status + sblocks),
+                                                   err);
+  k_heavy_compact<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, M.hdr, W.flags, W.cpos, M.leaf,
+                                                      P.f0, (Cand*)W.cand, W.cand_cap);
+  k_heavy_select<<<(P.f0 + 255) / 256, 256, 0, st>>>((const Cand*)W.cand, W.cpos + s, W.cand_cap,
+                                                     P.f0, (int)P.hpb, W.sel, W.nh);
+  k_heavy_heads<DT><<<1, 1024, 0, st>>>(W.sel, W.nh, P.f0, (int)P.hpb, M.hdr, M.leaf, M.heads,
+                                        M.heavy);
+  add_launches(18);
+  return cudaGetLastError();
+}
+
+cudaError_t train_enqueue(int dt, const void* keys, uint64_t n, const TrainPlan& P,
+                          const TrainWs& W, const ModelPtrs& M, uint32_t* err, cudaStream_t st,
+                          int num_sms) {
+  switch (dt) {
+    case LS_F64: return train_dt<LS_F64>(keys, n, P, W, M, err, st, num_sms);
+    case LS_U64: return train_dt<LS_U64>(keys, n, P, W, M, err, st, num_sms);
+    case LS_F32: return train_dt<LS_F32>(keys, n, P, W, M, err, st, num_sms);
+    case LS_U32: return train_dt<LS_U32>(keys, n, P, W, M, err, st, num_sms);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t radix_sort_u64_enqueue(uint64_t* a, uint64_t* b, uint64_t m, const RsWork& w,
+                                   uint32_t* err, cudaStream_t st, int num_sms) {
+  return rs_sort_enqueue(a, b, m, nullptr, nullptr, w, err, st, num_sms);
+}
+
+}  // namespace ls

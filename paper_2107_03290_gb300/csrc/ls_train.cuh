@@ -1,0 +1,41 @@
+// Host-side interface of the training step (ls_train.cu).
+#pragma once
+#include <algorithm>
+
+#include "ls_internal.cuh"
+
+namespace ls {
+
+struct TrainPlan {
+  uint64_t s;        // sample size
+  uint64_t seed;
+  uint64_t tau;      // heavy run-length threshold in the sample (UINT64_MAX: none)
+  uint32_t L;        // leaves
+  uint32_t f0;       // level-0 fan-out
+  uint32_t hpb;      // heavy values per bucket (<= MAX_HPB)
+};
+
+struct TrainWs {
+  uint64_t* smp_a;           // s
+  uint64_t* smp_b;           // s
+  uint32_t* rank;            // s
+  uint32_t* flags;           // s
+  uint64_t* cpos;            // s + 1
+  void* cand;                // cand_cap * 24 bytes
+  uint64_t cand_cap;
+  uint64_t* sel;             // f0 * hpb
+  uint32_t* nh;              // f0
+  double* partials;          // 2 * FIT_BLOCKS
+  unsigned long long* hi;    // 1
+  void* scan_status;         // scan tiles * 8 + 16 bytes
+  size_t scan_status_bytes;
+  RsWork rs;                 // radix-sort work area of the sample sort
+};
+
+cudaError_t train_enqueue(int dt, const void* keys, uint64_t n, const TrainPlan& P,
+                          const TrainWs& W, const ModelPtrs& M, uint32_t* err, cudaStream_t st,
+                          int num_sms);
+cudaError_t radix_sort_u64_enqueue(uint64_t* a, uint64_t* b, uint64_t m, const RsWork& w,
+                                   uint32_t* err, cudaStream_t st, int num_sms);
+
+}  // namespace ls

