@@ -159,6 +159,24 @@ ls_status ls_radix_sort_u64(uint64_t* keys, size_t count, void* stream);
 /* Kernels the library has enqueued since it was loaded (diagnostics). */
 uint64_t ls_kernel_launches(void);
 
+/* Largest `count` accepted by ls_radix_sort_u64_noalloc (2^20 keys). */
+#define LS_NOALLOC_RADIX_MAX (1u << 20)
+
+/* ls_radix_sort_u64 for callers that cannot allocate device memory when they
+ * sort: a framework whose caching allocator already owns the GPU's memory, a
+ * latency-bound loop that must stay out of the driver's allocator, or a library
+ * that promises never to allocate.  The paper has no counterpart; it is a
+ * service of this library.  Allocates nothing: the scratch is one static device
+ * array inside the library sized for LS_NOALLOC_RADIX_MAX keys (about 10.5 MB,
+ * held on every GPU that loads the library until the process exits).
+ * `keys`: device pointer to `count` uint64 keys, sorted in place on `stream`.
+ * count > LS_NOALLOC_RADIX_MAX: LS_ERR_INVALID, keys untouched.  The first call
+ * on a device looks up the array's device address; make that first call before
+ * any stream capture.  All calls share the array (it keeps the last call's
+ * contents; the call clears what must start at zero): calls whose work
+ * overlaps on the GPU race, so the caller must order them. */
+ls_status ls_radix_sort_u64_noalloc(uint64_t* keys, size_t count, void* stream);
+
 /* ---- serving: continuous batching of sort requests ---- */
 typedef struct ls_server ls_server;
 

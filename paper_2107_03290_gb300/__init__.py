@@ -21,7 +21,8 @@ _CSRC = os.path.join(_HERE, "csrc")
 _INC = os.path.join(os.path.dirname(_HERE), "include")
 _SO = os.path.join(_HERE, "libls.so")
 _BUILD = os.path.join(_HERE, "_build")
-SOURCES = ["ls_train.cu", "ls_partition.cu", "ls_bucket.cu", "ls_api.cu", "ls_server.cpp"]
+SOURCES = ["ls_train.cu", "ls_partition.cu", "ls_bucket.cu", "ls_api.cu", "ls_server.cpp",
+           "ls_noalloc.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 DTYPE_CODES = {"f64": 0, "u64": 1, "f32": 2, "u32": 3}
@@ -129,7 +130,8 @@ class RequestStats(ctypes.Structure):
 
 EXPORTED = ["ls_default_params", "ls_status_string", "ls_sort", "ls_sort_ex", "ls_sort_host",
             "ls_sort_batch", "ls_stream_status", "ls_train", "ls_level0_histogram",
-            "ls_radix_sort_u64", "ls_kernel_launches", "ls_server_create", "ls_server_submit", "ls_server_wait",
+            "ls_radix_sort_u64", "ls_radix_sort_u64_noalloc", "ls_kernel_launches",
+            "ls_server_create", "ls_server_submit", "ls_server_wait",
             "ls_server_destroy"]
 
 _lib = None
@@ -167,6 +169,7 @@ def load(path: str | None = None):
             "ls_train": [vp, sz, i32, vp, P(Params), P(ModelExport)],
             "ls_level0_histogram": [vp, sz, i32, vp, P(Params), vp, sz, P(ctypes.c_size_t)],
             "ls_radix_sort_u64": [vp, sz, vp],
+            "ls_radix_sort_u64_noalloc": [vp, sz, vp],
             "ls_server_create": [P(ServerConfig), P(vp)],
             "ls_server_submit": [vp, vp, sz, i32, P(u64)],
             "ls_server_wait": [vp, u64, u32, P(RequestStats)],
@@ -280,6 +283,19 @@ def radix_sort_u64_(t, stream=None):
         raise TypeError("uint64 tensor expected")
     _check(load().ls_radix_sort_u64(_device_tensor(t).data_ptr(), t.numel(), _stream(stream)),
            "ls_radix_sort_u64")
+
+
+NOALLOC_RADIX_MAX = 1 << 20
+
+
+def radix_sort_u64_noalloc_(t, stream=None):
+    """ls_radix_sort_u64 without any allocation (static device scratch, at most
+    NOALLOC_RADIX_MAX keys); for callers that cannot allocate when they sort."""
+    torch = _torch()
+    if t.dtype != torch.uint64:
+        raise TypeError("uint64 tensor expected")
+    _check(load().ls_radix_sort_u64_noalloc(_device_tensor(t).data_ptr(), t.numel(),
+                                            _stream(stream)), "ls_radix_sort_u64_noalloc")
 
 
 def train(t, params: Params | None = None, stream=None, with_sample: bool = False) -> dict:

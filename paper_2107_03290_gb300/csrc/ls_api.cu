@@ -36,6 +36,13 @@ __device__ uint32_t g_status_word;  // asynchronous device errors (ERR_* bits)
 static std::atomic<unsigned long long> g_launches{0};
 void add_launches(unsigned k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+cudaError_t status_word_ptr(uint32_t** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_status_word);
+  *out = (uint32_t*)p;
+  return e;
+}
+
 struct Device {
   int id = -1;
   int num_sms = 0;

@@ -293,6 +293,8 @@ inline void mark(const Marks* m, int i, cudaStream_t st) {
 }
 // Number of kernel launches the library has enqueued (diagnostics).
 void add_launches(unsigned k);
+// Device address of the current device's status word (no allocation).
+cudaError_t status_word_ptr(uint32_t** out);
 
 // Model storage in device memory (one per sort call / array).
 struct DevModel {
