@@ -77,11 +77,11 @@ class Model(ctypes.Structure):
 
 
 class Eval(ctypes.Structure):
-    _fields_ = [("E", ctypes.c_int32), ("leaves", ctypes.c_uint32), ("root_cq", ctypes.c_int64),
-                ("root_sh", ctypes.c_int32), ("root_A", ctypes.c_float),
-                ("root_B", ctypes.c_float), ("cq", ctypes.c_void_p), ("sh", ctypes.c_void_p),
-                ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("LO", ctypes.c_void_p),
-                ("HI", ctypes.c_void_p)]
+    _fields_ = [("E", ctypes.c_int32), ("leaves", ctypes.c_uint32), ("f0", ctypes.c_uint32),
+                ("root_P0", ctypes.c_int32), ("root_C0", ctypes.c_int64),
+                ("root_RA", ctypes.c_int32), ("root_RB", ctypes.c_int64)] + [
+                    (k, ctypes.c_void_p) for k in ("AL", "BL", "lohi", "C", "P", "A", "B", "LO",
+                                                   "HI")]
 
 
 def _L():
@@ -111,16 +111,16 @@ def _L():
                                               u64]
             lib.lso_partition_f64.restype = u64
             lib.lso_defragment_f64.argtypes = [vp, u64, u32, vp, vp, vp, u64]
-            lib.lso_spec_eval_params.argtypes = [P(Model), vp, u64, i32] + [vp] * 11
+            lib.lso_spec_eval_params.argtypes = [P(Model), vp, u64, i32, u32] + [vp] * 14
             lib.lso_spec_fixed_point.argtypes = [vp, u64, i32, i32]
             lib.lso_spec_fixed_point.restype = i64
-            lib.lso_spec_F.argtypes = [P(Eval), vp, u64, i32]
-            lib.lso_spec_F.restype = ctypes.c_float
-            lib.lso_spec_bucket.argtypes = [P(Eval), vp, u64, i32, u32]
+            lib.lso_spec_F_fine.argtypes = [P(Eval), vp, u64, i32]
+            lib.lso_spec_F_fine.restype = ctypes.c_float
+            lib.lso_spec_bucket.argtypes = [P(Eval), vp, u64, i32]
             lib.lso_spec_bucket.restype = u32
-            lib.lso_spec_heavy.argtypes = [vp, vp, u64, i32, u64, u32, P(Eval), u32, vp, u64]
+            lib.lso_spec_heavy.argtypes = [vp, vp, u64, i32, u64, u32, P(Eval), vp, u64]
             lib.lso_spec_heavy.restype = u64
-            lib.lso_spec_ext_histogram.argtypes = [P(Eval), vp, u64, i32, u32, vp, u64, vp, u64]
+            lib.lso_spec_ext_histogram.argtypes = [P(Eval), vp, u64, i32, vp, u64, vp, u64]
             lib.lso_spec_ext_histogram.restype = u64
             _lib = lib
     return _lib
@@ -238,40 +238,48 @@ def defragment(a: np.ndarray, f: int, sizes, owners, fsizes) -> np.ndarray:
 
 
 class EvalParams:
-    """FP32 evaluation parameters (the GPU's documented per-key formula)."""
+    """Evaluation parameters (the GPU's documented per-key formulas)."""
 
-    def __init__(self, leaves: int):
+    FIELDS = {"AL": np.int32, "BL": np.int64, "lohi": np.uint32, "C": np.int64, "P": np.int32,
+              "A": np.float32, "B": np.float32, "LO": np.float32, "HI": np.float32}
+    ROOT = {"E": np.int32, "root_P0": np.int32, "root_C0": np.int64, "root_RA": np.int32,
+            "root_RB": np.int64}
+
+    def __init__(self, leaves: int, f0: int):
         self.L = leaves
-        self.E = np.zeros(1, np.int32)
-        self.root_cq = np.zeros(1, np.int64)
-        self.root_sh = np.zeros(1, np.int32)
-        self.root_A = np.zeros(1, np.float32)
-        self.root_B = np.zeros(1, np.float32)
-        self.cq = np.zeros(leaves, np.int64)
-        self.sh = np.zeros(leaves, np.int32)
-        self.A = np.zeros(leaves, np.float32)
-        self.B = np.zeros(leaves, np.float32)
-        self.LO = np.zeros(leaves, np.float32)
-        self.HI = np.zeros(leaves, np.float32)
+        self.f0 = f0
+        for k, t in self.ROOT.items():
+            setattr(self, k, np.zeros(1, t))
+        for k, t in self.FIELDS.items():
+            setattr(self, k, np.zeros(leaves, t))
 
     def struct(self) -> Eval:
         e = Eval()
-        e.E = int(self.E[0]); e.leaves = self.L
-        e.root_cq = int(self.root_cq[0]); e.root_sh = int(self.root_sh[0])
-        e.root_A = float(self.root_A[0]); e.root_B = float(self.root_B[0])
-        e.cq, e.sh, e.A, e.B, e.LO, e.HI = (_ptr(self.cq), _ptr(self.sh), _ptr(self.A),
-                                            _ptr(self.B), _ptr(self.LO), _ptr(self.HI))
+        e.leaves, e.f0 = self.L, self.f0
+        for k in self.ROOT:
+            setattr(e, k, int(getattr(self, k)[0]))
+        for k in self.FIELDS:
+            setattr(e, k, _ptr(getattr(self, k)))
         self._keep = e
         return e
 
+    @classmethod
+    def from_export(cls, m: dict, leaves: int, f0: int) -> "EvalParams":
+        ev = cls(leaves, f0)
+        for k in cls.ROOT:
+            getattr(ev, k)[0] = m[k]
+        for k in cls.FIELDS:
+            getattr(ev, k)[:] = m[k]
+        return ev
 
-def spec_eval_params(model: FittedModel, sorted_finite_x: np.ndarray, dtype: str) -> EvalParams:
+
+def spec_eval_params(model: FittedModel, sorted_finite_x: np.ndarray, dtype: str,
+                     f0: int) -> EvalParams:
     xs = np.ascontiguousarray(sorted_finite_x, np.float64)
-    ev = EvalParams(model.m.leaves)
-    _L().lso_spec_eval_params(ctypes.byref(model.m), _ptr(xs), xs.size, DTYPES[dtype],
-                              _ptr(ev.E), _ptr(ev.root_cq), _ptr(ev.root_sh), _ptr(ev.root_A),
-                              _ptr(ev.root_B), _ptr(ev.cq), _ptr(ev.sh), _ptr(ev.A), _ptr(ev.B),
-                              _ptr(ev.LO), _ptr(ev.HI))
+    ev = EvalParams(model.m.leaves, f0)
+    _L().lso_spec_eval_params(ctypes.byref(model.m), _ptr(xs), xs.size, DTYPES[dtype], f0,
+                              *[_ptr(getattr(ev, k)) for k in EvalParams.ROOT],
+                              *[_ptr(getattr(ev, k)) for k in EvalParams.FIELDS])
     return ev
 
 
@@ -282,38 +290,38 @@ def spec_fixed_point(keys: np.ndarray, E: int) -> np.ndarray:
     return np.array([f(_ptr(a), i, d, E) for i in range(a.size)], dtype=np.int64)
 
 
-def spec_F(ev: EvalParams, keys: np.ndarray) -> np.ndarray:
+def spec_F_fine(ev: EvalParams, keys: np.ndarray) -> np.ndarray:
     a = np.ascontiguousarray(keys)
     d = DTYPES[dtype_name(a)]
     s = ev.struct()
-    f = _L().lso_spec_F
+    f = _L().lso_spec_F_fine
     return np.array([f(ctypes.byref(s), _ptr(a), i, d) for i in range(a.size)], np.float32)
 
 
-def spec_buckets(ev: EvalParams, keys: np.ndarray, f0: int) -> np.ndarray:
+def spec_buckets(ev: EvalParams, keys: np.ndarray) -> np.ndarray:
     a = np.ascontiguousarray(keys)
     d = DTYPES[dtype_name(a)]
     s = ev.struct()
     f = _L().lso_spec_bucket
-    return np.array([f(ctypes.byref(s), _ptr(a), i, d, f0) for i in range(a.size)], np.uint32)
+    return np.array([f(ctypes.byref(s), _ptr(a), i, d) for i in range(a.size)], np.uint32)
 
 
-def spec_heavy(sorted_keys: np.ndarray, tau: int, per_bucket: int, ev: EvalParams, f0: int):
+def spec_heavy(sorted_keys: np.ndarray, tau: int, per_bucket: int, ev: EvalParams):
     a = np.ascontiguousarray(sorted_keys)
     tk = total_order_keys(a)
     out = np.zeros(max(1, a.size), np.uint64)
     s = ev.struct()
     nh = _L().lso_spec_heavy(_ptr(tk), _ptr(a), a.size, DTYPES[dtype_name(a)], tau, per_bucket,
-                             ctypes.byref(s), f0, _ptr(out), out.size)
+                             ctypes.byref(s), _ptr(out), out.size)
     return out[:nh]
 
 
-def spec_ext_histogram(ev: EvalParams, keys: np.ndarray, f0: int, heavy_tk: np.ndarray):
+def spec_ext_histogram(ev: EvalParams, keys: np.ndarray, heavy_tk: np.ndarray):
     a = np.ascontiguousarray(keys)
     h = np.ascontiguousarray(heavy_tk, np.uint64)
-    mx = f0 + 2 * h.size + 1
+    mx = ev.f0 + 2 * h.size + 1
     hist = np.zeros(mx, np.uint64)
     s = ev.struct()
     ne = _L().lso_spec_ext_histogram(ctypes.byref(s), _ptr(a), a.size, DTYPES[dtype_name(a)],
-                                     f0, _ptr(h), h.size, _ptr(hist), mx)
+                                     _ptr(h), h.size, _ptr(hist), mx)
     return hist[:ne]

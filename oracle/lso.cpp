@@ -355,13 +355,6 @@ float fp32_sat(double d) {
   return (float)d;
 }
 
-inline float feature(int64_t q, int64_t cq, int32_t sh) {
-  int64_t d = (q - cq) >> sh;  // arithmetic shift: floor division
-  const int64_t LIM = 2147483647;
-  if (d > LIM) d = LIM;
-  if (d < -LIM) d = -LIM;
-  return (float)(int32_t)d;
-}
 
 }  // namespace
 
@@ -549,28 +542,36 @@ void lso_defragment_f64(double* a, uint64_t m, uint32_t f, const uint64_t* sizes
 }
 
 // ---------------------------------------------------------------- spec functions
+static long long floor_scaled(double v, int k, double lo, double hi) {
+  double w = std::floor(std::ldexp(v, k));
+  w = w < lo ? lo : w;
+  w = w > hi ? hi : w;
+  return (long long)w;
+}
+
 void lso_spec_eval_params(const lso_model* model, const double* xs, uint64_t m, int dtype,
-                          int32_t* E, int64_t* root_cq, int32_t* root_sh, float* root_A,
-                          float* root_B, int64_t* cq, int32_t* sh, float* A, float* B,
+                          uint32_t f0, int32_t* E, int32_t* root_P0, int64_t* root_C0,
+                          int32_t* root_RA, int64_t* root_RB, int32_t* AL, int64_t* BL,
+                          uint32_t* lohi, int64_t* C, int32_t* P, float* A, float* B,
                           float* LO, float* HI) {
   (void)dtype;
   const uint32_t L = model->leaves;
+  const double INT31 = 2147483647.0, F0 = (double)f0;
   double R = 0;
   if (m) R = std::max(std::fabs(xs[0]), std::fabs(xs[m - 1]));
   const int e = (R > 0) ? std::ilogb(R) + 1 - 61 : 0;
   *E = e;
-  const int64_t c0 = fixed_point_f64(model->root[1], e);
+  auto absd = [](int64_t d) { return d < 0 ? (uint64_t)(-d) : (uint64_t)d; };
+  const int64_t c0e = fixed_point_f64(model->root[1], e);
   uint64_t span0 = 0;
-  if (m) {
-    const int64_t d0 = fixed_point_f64(xs[0], e) - c0, d1 = fixed_point_f64(xs[m - 1], e) - c0;
-    span0 = std::max<uint64_t>(d0 < 0 ? (uint64_t)(-d0) : (uint64_t)d0,
-                               d1 < 0 ? (uint64_t)(-d1) : (uint64_t)d1);
-  }
-  const int s0 = std::max(0, bitlen(span0) - 30);
-  *root_cq = c0;
-  *root_sh = s0;
-  *root_A = fp32_sat(std::ldexp(model->root[0] * (double)L, e + s0));
-  *root_B = (float)(model->root[2] * (double)L);
+  if (m)
+    span0 = std::max(absd(fixed_point_f64(xs[0], e) - c0e), absd(fixed_point_f64(xs[m - 1], e) - c0e));
+  const int p0 = e + std::max(0, bitlen(span0) - 30);
+  const int64_t C0 = fixed_point_f64(model->root[1], p0);
+  *root_P0 = p0;
+  *root_C0 = C0;
+  *root_RA = (int32_t)floor_scaled(model->root[0] * (double)L, p0 + 40, 0.0, INT31);
+  *root_RB = floor_scaled(model->root[2] * (double)L, 40, -9.0e18, 9.0e18);
   // Leaf ranges of the sorted sample under the FP64 routing used in training.
   std::vector<uint64_t> beg(L, 0), end(L, 0);
   std::vector<char> seen(L, 0);
@@ -579,20 +580,28 @@ void lso_spec_eval_params(const lso_model* model, const double* xs, uint64_t m, 
     if (!seen[l]) { seen[l] = 1; beg[l] = k; }
     end[l] = k + 1;
   }
+  const int64_t T0 = (1ll << 30) - 1;
   for (uint32_t l = 0; l < L; ++l) {
     const double* q = model->leaf + 5 * (size_t)l;
+    const long long bl = floor_scaled(q[2] * F0, 32, -9.0e18, 9.0e18);
     if (!seen[l]) {
-      cq[l] = 0; sh[l] = 0; A[l] = 0.0f;
+      AL[l] = 0; BL[l] = bl; C[l] = 0; P[l] = e; A[l] = 0.0f;
     } else {
-      const int64_t c = fixed_point_f64(q[1], e);
-      const int64_t d0 = fixed_point_f64(xs[beg[l]], e) - c;
-      const int64_t d1 = fixed_point_f64(xs[end[l] - 1], e) - c;
-      const uint64_t span = std::max<uint64_t>(d0 < 0 ? (uint64_t)(-d0) : (uint64_t)d0,
-                                               d1 < 0 ? (uint64_t)(-d1) : (uint64_t)d1);
-      const int s = std::max(0, bitlen(span) - 30);
-      cq[l] = c; sh[l] = s;
-      A[l] = fp32_sat(std::ldexp(q[0], e + s));
+      const int64_t ce = fixed_point_f64(q[1], e);
+      const uint64_t span = std::max(absd(fixed_point_f64(xs[beg[l]], e) - ce),
+                                     absd(fixed_point_f64(xs[end[l] - 1], e) - ce));
+      const int pl = e + std::max(0, bitlen(span) - 30);
+      P[l] = pl;
+      C[l] = fixed_point_f64(q[1], pl);
+      A[l] = fp32_sat(std::ldexp(q[0], pl));
+      int64_t t = fixed_point_f64(q[1], p0) - C0;
+      t = std::min(T0, std::max(-T0, t));
+      AL[l] = (int32_t)floor_scaled(q[0] * F0, p0 + 32, 0.0, INT31);
+      BL[l] = bl - (int64_t)AL[l] * t;
     }
+    const double lob = std::min(std::floor(q[3] * F0), F0 - 1.0);
+    const double hib = std::min(std::floor(q[4] * F0), F0 - 1.0);
+    lohi[l] = (uint32_t)lob | ((uint32_t)hib << 16);
     B[l] = (float)q[2];
     LO[l] = (float)q[3];
     HI[l] = (float)q[4];
@@ -630,43 +639,57 @@ static int key_nan(const void* keys, uint64_t i, int dtype, int* negative) {
   return 0;
 }
 
-float lso_spec_F(const lso_eval* ev, const void* keys, uint64_t i, int dtype) {
+static int32_t spec_t0(const lso_eval* ev, const void* keys, uint64_t i, int dtype) {
+  const int64_t T0 = (1ll << 30) - 1;
+  int64_t t = lso_spec_fixed_point(keys, i, dtype, ev->root_P0) - ev->root_C0;
+  t = std::min(T0, std::max(-T0, t));
+  return (int32_t)t;
+}
+
+static uint32_t spec_leaf(const lso_eval* ev, int32_t t0) {
+  const int64_t v = (int64_t)ev->root_RA * (int64_t)t0 + ev->root_RB;
+  int64_t l = v >> 40;  // arithmetic shift: floor
+  if (l < 0) l = 0;
+  if (l >= (int64_t)ev->leaves) l = ev->leaves - 1;
+  return (uint32_t)l;
+}
+
+float lso_spec_F_fine(const lso_eval* ev, const void* keys, uint64_t i, int dtype) {
   int negative;
   if (key_nan(keys, i, dtype, &negative)) return negative ? -1.0f : 2.0f;
-  const int64_t q = lso_spec_fixed_point(keys, i, dtype, ev->E);
-  const float v = std::fmaf(ev->root_A, feature(q, ev->root_cq, ev->root_sh), ev->root_B);
-  const float Lf = (float)ev->leaves;
-  uint32_t l;
-  if (v >= Lf) l = ev->leaves - 1;
-  else if (v > 0.0f) l = (uint32_t)v;
-  else l = 0;
-  const float t = feature(q, ev->cq[l], ev->sh[l]);
-  float F = std::fmaf(ev->A[l], t, ev->B[l]);
+  const uint32_t l = spec_leaf(ev, spec_t0(ev, keys, i, dtype));
+  const int64_t LIM = 2147483647;
+  int64_t d = lso_spec_fixed_point(keys, i, dtype, ev->P[l]) - ev->C[l];
+  d = std::min(LIM, std::max(-LIM, d));
+  float F = std::fmaf(ev->A[l], (float)(int32_t)d, ev->B[l]);
   F = std::fmax(F, ev->LO[l]);
   F = std::fmin(F, ev->HI[l]);
   return F;
 }
 
-uint32_t lso_spec_bucket(const lso_eval* ev, const void* keys, uint64_t i, int dtype,
-                         uint32_t f0) {
-  const float F = lso_spec_F(ev, keys, i, dtype);
-  if (F < 0.0f) return 0;
-  if (F > 1.0f) return f0 - 1;
-  const float w = F * (float)f0;
-  const uint32_t b = (uint32_t)w;
-  return b < f0 ? b : f0 - 1;
+uint32_t lso_spec_bucket(const lso_eval* ev, const void* keys, uint64_t i, int dtype) {
+  int negative;
+  if (key_nan(keys, i, dtype, &negative)) return negative ? 0u : ev->f0 - 1;
+  const int32_t t0 = spec_t0(ev, keys, i, dtype);
+  const uint32_t l = spec_leaf(ev, t0);
+  const int64_t v = (int64_t)ev->AL[l] * (int64_t)t0 + ev->BL[l];
+  int64_t b = v >> 32;
+  const int64_t lo = ev->lohi[l] & 0xFFFFu, hi = ev->lohi[l] >> 16;
+  if (b < lo) b = lo;
+  if (b > hi) b = hi;
+  return (uint32_t)b;
 }
 
 uint64_t lso_spec_heavy(const uint64_t* tk, const void* keys, uint64_t m, int dtype,
-                        uint64_t tau, uint32_t per_bucket, const lso_eval* ev, uint32_t f0,
-                        uint64_t* out, uint64_t max_out) {
+                        uint64_t tau, uint32_t per_bucket, const lso_eval* ev, uint64_t* out,
+                        uint64_t max_out) {
   struct Cand { uint64_t tk, len, idx; uint32_t b; };
   std::vector<Cand> cand;
   uint64_t k = 0;
   while (k < m) {
     uint64_t e = k + 1;
     while (e < m && tk[e] == tk[k]) ++e;
-    if (e - k >= tau) cand.push_back({tk[k], e - k, k, lso_spec_bucket(ev, keys, k, dtype, f0)});
+    if (e - k >= tau) cand.push_back({tk[k], e - k, k, lso_spec_bucket(ev, keys, k, dtype)});
     k = e;
   }
   std::vector<uint64_t> res;
@@ -689,8 +712,9 @@ uint64_t lso_spec_heavy(const uint64_t* tk, const void* keys, uint64_t m, int dt
 }
 
 uint64_t lso_spec_ext_histogram(const lso_eval* ev, const void* keys, uint64_t n, int dtype,
-                                uint32_t f0, const uint64_t* heavy, uint64_t nheavy,
-                                uint64_t* hist, uint64_t max_ext) {
+                                const uint64_t* heavy, uint64_t nheavy, uint64_t* hist,
+                                uint64_t max_ext) {
+  const uint32_t f0 = ev->f0;
   // Heavy values per bucket (heavy list is ascending, buckets non-decreasing).
   std::vector<std::vector<uint64_t>> hb(f0);
   for (uint64_t j = 0; j < nheavy; ++j) {
@@ -700,17 +724,17 @@ uint64_t lso_spec_ext_histogram(const lso_eval* ev, const void* keys, uint64_t n
     if (dtype == LSO_F64) {
       const uint64_t u = (t >> 63) ? (t & ~(1ull << 63)) : ~t;
       double x; std::memcpy(&x, &u, 8);
-      b = lso_spec_bucket(ev, &x, 0, dtype, f0);
+      b = lso_spec_bucket(ev, &x, 0, dtype);
     } else if (dtype == LSO_F32) {
       const uint32_t t32 = (uint32_t)t;
       const uint32_t u = (t32 >> 31) ? (t32 & 0x7FFFFFFFu) : ~t32;
       float x; std::memcpy(&x, &u, 4);
-      b = lso_spec_bucket(ev, &x, 0, dtype, f0);
+      b = lso_spec_bucket(ev, &x, 0, dtype);
     } else if (dtype == LSO_U64) {
-      b = lso_spec_bucket(ev, &t, 0, dtype, f0);
+      b = lso_spec_bucket(ev, &t, 0, dtype);
     } else {
       const uint32_t x = (uint32_t)t;
-      b = lso_spec_bucket(ev, &x, 0, dtype, f0);
+      b = lso_spec_bucket(ev, &x, 0, dtype);
     }
     hb[b].push_back(t);
   }
@@ -720,7 +744,7 @@ uint64_t lso_spec_ext_histogram(const lso_eval* ev, const void* keys, uint64_t n
   const uint64_t next = acc;
   for (uint64_t j = 0; j < std::min(next, max_ext); ++j) hist[j] = 0;
   for (uint64_t i = 0; i < n; ++i) {
-    const uint32_t b = lso_spec_bucket(ev, keys, i, dtype, f0);
+    const uint32_t b = lso_spec_bucket(ev, keys, i, dtype);
     const uint64_t t = lso_total_order_key(keys, i, dtype);
     uint64_t e = base[b];
     for (uint64_t h : hb[b]) {

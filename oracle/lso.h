@@ -90,43 +90,54 @@ void lso_defragment_f64(double* a, uint64_t m, uint32_t f, const uint64_t* sizes
 
 /* ---- Part 3: spec functions for kernel parity (see header comment) ---- */
 
-/* The GPU evaluation parameters (FP32 on centred fixed-point features). */
+/* The GPU evaluation parameters.  fx(x, P) = floor(x * 2^-P) saturated to
+ * +-2^62.  Level 0 (integer): t0 = clamp(fx(x, P0) - C0, +-(2^30-1));
+ *   leaf = clamp((RA*t0 + RB) >> 40, 0, L-1);
+ *   bucket = clamp((AL_l*t0 + BL_l) >> 32, lo_l, hi_l).
+ * Fine (level-1 split, in-bucket slots), FP32:
+ *   F = clamp(fmaf(A_l, clamp(fx(x, P_l) - C_l, +-(2^31-1)), B_l), LO_l, HI_l). */
 typedef struct lso_eval {
-  int32_t E;           /* fixed-point exponent: q(x) = floor(x * 2^-E) saturated to +-2^62 */
+  int32_t E;           /* exponent of the sample's fixed-point grid */
   uint32_t leaves;
-  int64_t root_cq;     /* root centre on the fixed-point grid */
-  int32_t root_sh;     /* root feature shift                 */
-  float root_A, root_B;
-  const int64_t* cq;   /* per leaf */
-  const int32_t* sh;
+  uint32_t f0;         /* level-0 fan-out the tables were built for */
+  int32_t root_P0;
+  int64_t root_C0;
+  int32_t root_RA;
+  int64_t root_RB;
+  const int32_t* AL;   /* per leaf, level 0 */
+  const int64_t* BL;
+  const uint32_t* lohi;
+  const int64_t* C;    /* per leaf, fine */
+  const int32_t* P;
   const float* A;
   const float* B;
   const float* LO;
   const float* HI;
 } lso_eval;
 
-/* Derive FP32 evaluation parameters from an FP64 model; the per-leaf feature
+/* Derive the evaluation parameters from an FP64 model; the per-leaf feature
  * spans come from the first/last finite sorted sample key of each leaf. */
-void lso_spec_eval_params(const lso_model* model, const double* sorted_x, uint64_t m,
-                          int dtype, int32_t* E, int64_t* root_cq, int32_t* root_sh,
-                          float* root_A, float* root_B, int64_t* cq, int32_t* sh, float* A,
-                          float* B, float* LO, float* HI);
+void lso_spec_eval_params(const lso_model* model, const double* sorted_x, uint64_t m, int dtype,
+                          uint32_t f0, int32_t* E, int32_t* root_P0, int64_t* root_C0,
+                          int32_t* root_RA, int64_t* root_RB, int32_t* AL, int64_t* BL,
+                          uint32_t* lohi, int64_t* C, int32_t* P, float* A, float* B,
+                          float* LO, float* HI);
 int64_t lso_spec_fixed_point(const void* keys, uint64_t i, int dtype, int32_t E);
-/* FP32 eCDF estimate of key i; returns -1 / 2 for negative / positive NaN. */
-float lso_spec_F(const lso_eval* ev, const void* keys, uint64_t i, int dtype);
-uint32_t lso_spec_bucket(const lso_eval* ev, const void* keys, uint64_t i, int dtype,
-                         uint32_t f0);
+/* Fine FP32 eCDF estimate of key i; returns -1 / 2 for negative / positive NaN. */
+float lso_spec_F_fine(const lso_eval* ev, const void* keys, uint64_t i, int dtype);
+/* Level-0 bucket of key i (integer map; NaNs by sign to bucket 0 / f0-1). */
+uint32_t lso_spec_bucket(const lso_eval* ev, const void* keys, uint64_t i, int dtype);
 /* Heavy set from a sorted (ascending tk) finite sample: values whose run
  * length is >= tau, at most per_bucket per level-0 bucket (longest runs
  * first, ties by smaller key), returned in ascending key order. */
 uint64_t lso_spec_heavy(const uint64_t* sorted_tk, const void* sorted_keys, uint64_t m,
                         int dtype, uint64_t tau, uint32_t per_bucket, const lso_eval* ev,
-                        uint32_t f0, uint64_t* heavy_tk_out, uint64_t max_out);
+                        uint64_t* heavy_tk_out, uint64_t max_out);
 /* Level-0 extended-bucket histogram: regular bucket b owning heavy values
  * h_1<...<h_k gets 2k+1 slots (<h_1, =h_1, between, ..., >h_k). */
 uint64_t lso_spec_ext_histogram(const lso_eval* ev, const void* keys, uint64_t n, int dtype,
-                                uint32_t f0, const uint64_t* heavy_tk, uint64_t nheavy,
-                                uint64_t* hist_out, uint64_t max_ext);
+                                const uint64_t* heavy_tk, uint64_t nheavy, uint64_t* hist_out,
+                                uint64_t max_ext);
 
 #ifdef __cplusplus
 }

@@ -109,9 +109,10 @@ class ModelExport(ctypes.Structure):
     _fields_ = [("leaves", ctypes.c_uint32), ("max_heavy", ctypes.c_uint32),
                 ("sample_size", ctypes.c_uint64), ("sample_finite", ctypes.c_uint64),
                 ("root", ctypes.c_double * 3), ("leaf", ctypes.c_void_p),
-                ("E", ctypes.c_int32), ("root_sh", ctypes.c_int32), ("root_cq", ctypes.c_int64),
-                ("root_A", ctypes.c_float), ("root_B", ctypes.c_float),
-                ("cq", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("A", ctypes.c_void_p),
+                ("E", ctypes.c_int32), ("root_P0", ctypes.c_int32), ("root_C0", ctypes.c_int64),
+                ("root_RA", ctypes.c_int32), ("root_RB", ctypes.c_int64),
+                ("AL", ctypes.c_void_p), ("BL", ctypes.c_void_p), ("lohi", ctypes.c_void_p),
+                ("C", ctypes.c_void_p), ("P", ctypes.c_void_p), ("A", ctypes.c_void_p),
                 ("B", ctypes.c_void_p), ("LO", ctypes.c_void_p), ("HI", ctypes.c_void_p),
                 ("sorted_sample_tk", ctypes.c_void_p), ("heavy_tk", ctypes.c_void_p),
                 ("n_heavy", ctypes.c_uint64), ("tau", ctypes.c_uint64)]
@@ -305,8 +306,9 @@ def train(t, params: Params | None = None, stream=None, with_sample: bool = Fals
     L = p.leaves or 1000
     out = ModelExport()
     out.leaves = L
-    arr = {"leaf": np.zeros((L, 5), np.float64), "cq": np.zeros(L, np.int64),
-           "sh": np.zeros(L, np.int32), "A": np.zeros(L, np.float32),
+    arr = {"leaf": np.zeros((L, 5), np.float64), "AL": np.zeros(L, np.int32),
+           "BL": np.zeros(L, np.int64), "lohi": np.zeros(L, np.uint32), "C": np.zeros(L, np.int64),
+           "P": np.zeros(L, np.int32), "A": np.zeros(L, np.float32),
            "B": np.zeros(L, np.float32), "LO": np.zeros(L, np.float32),
            "HI": np.zeros(L, np.float32)}
     heavy = np.zeros(8 * max(1, p.fanout or 1000), np.uint64)
@@ -324,8 +326,8 @@ def train(t, params: Params | None = None, stream=None, with_sample: bool = Fals
     _check(rc, "ls_train")
     res = dict(arr)
     res.update(sample_size=out.sample_size, sample_finite=out.sample_finite,
-               root=np.array(list(out.root)), E=out.E, root_sh=out.root_sh, root_cq=out.root_cq,
-               root_A=np.float32(out.root_A), root_B=np.float32(out.root_B),
+               root=np.array(list(out.root)), E=out.E, root_P0=out.root_P0, root_C0=out.root_C0,
+               root_RA=out.root_RA, root_RB=out.root_RB,
                heavy_tk=heavy[:out.n_heavy].copy(), tau=out.tau)
     if smp is not None:
         res["sorted_sample_tk"] = smp[:out.sample_size].copy()

@@ -198,9 +198,10 @@ struct Workspace {
   size_t bytes = 0;
   // offsets
   size_t o_scratch, o_smp_a, o_smp_b, o_rank, o_flags, o_cpos, o_cand, o_sel, o_nh, o_part, o_hi,
-      o_tscan, o_rs_hist, o_rs_skip, o_rs_status, o_hdr, o_leaf64, o_leaf, o_heads, o_heavy,
+      o_tscan, o_rs_hist, o_rs_skip, o_rs_status, o_hdr, o_leaf64, o_leafc, o_leaff, o_heads, o_heavy,
       o_lbeg, o_lend, o_hist, o_offs, o_l0scan, o_jobs_fill, o_jobs_s, o_jobs_l, o_jobs_r,
-      o_jobs_fb, o_counts, o_aux, o_tot, o_l1cnt, o_l1off, o_l1cur, o_jmin, o_jmax, o_l1scan;
+      o_jobs_fb, o_counts, o_aux, o_tot, o_l1cnt, o_l1off, o_l1cur, o_jmin, o_jmax, o_l1scan,
+      o_ubase, o_units;
   size_t tscan_bytes, rs_status_bytes, l0scan_bytes, l1scan_bytes;
   uint64_t cand_cap;
 };
@@ -219,6 +220,8 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->o_sel = c.take<uint64_t>((size_t)P.f0 * std::max<uint32_t>(1, P.hpb));
   w->o_nh = c.take<uint32_t>(P.f0);
   w->o_part = c.take<double>(2 * 128);
+  w->o_ubase = c.take<uint32_t>(P.L + 2);
+  w->o_units = c.take<double>(4 * (P.s / 2048 + P.L + 2));
   w->o_hi = c.take<uint64_t>(1);
   const uint64_t stiles = std::max<uint64_t>(1, (s + SC_TILE - 1) / SC_TILE);
   w->tscan_bytes = stiles * 8 + 16;
@@ -229,7 +232,8 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->o_rs_status = c.take<uint8_t>(w->rs_status_bytes);
   w->o_hdr = c.take<DevModel>(1);
   w->o_leaf64 = c.take<double>(5 * (size_t)P.L);
-  w->o_leaf = c.take<LeafEval>(P.L);
+  w->o_leafc = c.take<LeafL0>(P.L);
+  w->o_leaff = c.take<LeafFine>(P.L + 1);
   w->o_heads = c.take<BucketHead>(P.f0 + 1);
   w->o_heavy = c.take<HeavyEntry>((size_t)P.f0 * std::max<uint32_t>(1, P.hpb));
   w->o_lbeg = c.take<uint32_t>(P.L);
@@ -274,10 +278,12 @@ static Bound bind(const Plan& P, const Workspace& w) {
   Bound b{};
   b.M.hdr = at<DevModel>(w, w.o_hdr);
   b.M.leaf64 = at<double>(w, w.o_leaf64);
-  b.M.leaf = at<LeafEval>(w, w.o_leaf);
+  b.M.leafc = at<LeafL0>(w, w.o_leafc);
+  b.M.leaff = at<LeafFine>(w, w.o_leaff);
   b.M.heads = at<BucketHead>(w, w.o_heads);
   b.M.heavy = at<HeavyEntry>(w, w.o_heavy);
   b.M.leaf_beg = at<uint32_t>(w, w.o_lbeg);
+  b.M.L = (int)P.L;
   b.M.leaf_end = at<uint32_t>(w, w.o_lend);
   TrainWs& T = b.T;
   T.smp_a = at<uint64_t>(w, w.o_smp_a);
@@ -290,6 +296,9 @@ static Bound bind(const Plan& P, const Workspace& w) {
   T.sel = at<uint64_t>(w, w.o_sel);
   T.nh = at<uint32_t>(w, w.o_nh);
   T.partials = at<double>(w, w.o_part);
+  T.ubase = at<uint32_t>(w, w.o_ubase);
+  T.utotal = T.ubase + P.L + 1;
+  T.units = at<double>(w, w.o_units);
   T.hi = at<unsigned long long>(w, w.o_hi);
   T.scan_status = at<void>(w, w.o_tscan);
   T.scan_status_bytes = w.tscan_bytes;
@@ -594,22 +603,27 @@ ls_status ls_train(const void* keys, size_t n, ls_dtype dtype, void* stream,
     out->sample_finite = hdr.s_fin;
     std::memcpy(out->root, hdr.root64, sizeof(out->root));
     out->E = hdr.root.E;
-    out->root_sh = hdr.root.sh;
-    out->root_cq = hdr.root.cq;
-    out->root_A = hdr.root.A;
-    out->root_B = hdr.root.B;
+    out->root_P0 = hdr.root.P0;
+    out->root_C0 = hdr.root.C0;
+    out->root_RA = hdr.root.RA;
+    out->root_RB = hdr.root.RB;
     out->tau = P.tau;
     out->n_heavy = hdr.nheavy;
     if (out->leaf) cudaMemcpy(out->leaf, b.M.leaf64, 5 * sizeof(double) * P.L, cudaMemcpyDeviceToHost);
-    std::vector<LeafEval> le(P.L);
-    cudaMemcpy(le.data(), b.M.leaf, sizeof(LeafEval) * P.L, cudaMemcpyDeviceToHost);
+    std::vector<LeafL0> lc(P.L);
+    std::vector<LeafFine> lf(P.L + 1);
+    cudaMemcpy(lc.data(), b.M.leafc, sizeof(LeafL0) * P.L, cudaMemcpyDeviceToHost);
+    cudaMemcpy(lf.data(), b.M.leaff, sizeof(LeafFine) * (P.L + 1), cudaMemcpyDeviceToHost);
     for (uint32_t l = 0; l < P.L; ++l) {
-      if (out->cq) out->cq[l] = le[l].cq;
-      if (out->sh) out->sh[l] = le[l].sh;
-      if (out->A) out->A[l] = le[l].A;
-      if (out->B) out->B[l] = le[l].B;
-      if (out->LO) out->LO[l] = le[l].LO;
-      if (out->HI) out->HI[l] = le[l].HI;
+      if (out->AL) out->AL[l] = lc[l].AL;
+      if (out->BL) out->BL[l] = lc[l].BL;
+      if (out->lohi) out->lohi[l] = lc[l].lohi;
+      if (out->C) out->C[l] = lf[l].C;
+      if (out->P) out->P[l] = lf[l].P;
+      if (out->A) out->A[l] = lf[l].A;
+      if (out->B) out->B[l] = lf[l].B;
+      if (out->LO) out->LO[l] = lf[l].LO;
+      if (out->HI) out->HI[l] = lf[l + 1].LO;
     }
     if (out->sorted_sample_tk)
       cudaMemcpy(out->sorted_sample_tk, b.T.smp_a, 8 * P.s, cudaMemcpyDeviceToHost);

@@ -1,18 +1,24 @@
 // In-bucket finish of LearnedSort 2.0 (Alg. 2): the model-based counting sort
 // of each (sub-)bucket followed by the insertion-sort touch-up.
 //
-// One CTA per segment of m keys (m <= CAP) in shared memory:
+// One CTA per segment of m keys (m <= CAP), keys held in registers, counts and
+// the placed keys in shared memory:
 //   slot(x) = clamp(floor((F(x) - Flo) * m / (Fhi - Flo)), 0, m - 1)
-// evaluated per leaf with FP32 coefficients derived in FP64 for this segment
-// (so the slot resolution is 1/m of the segment's eCDF range, not of [0,1]);
-// histogram of slots -> exclusive scan (the running totals of Alg. 2) ->
-// placement -> touch-up.  The slot map is monotone in the key, so keys of
-// different slots are already in order and the touch-up only sorts each group
-// of keys that share a slot: insertion sort (<= 8 keys, one thread), rank sort
-// (<= 128, one warp) or a bitonic network over the group (one CTA).
+// evaluated per leaf with FP32 coefficients derived in FP64 for this segment,
+// so the slot resolution is 1/m of the segment's eCDF range.  The leaves that
+// can hold the segment's keys are known from the job (la..lb); keys routed to
+// a leaf outside that range take slot 0 or m-1.  Histogram of slots ->
+// exclusive scan (the running totals of Alg. 2) -> placement -> touch-up.  The
+// slot map is monotone in the key, so keys of different slots are already in
+// order and the touch-up only sorts each group of keys sharing a slot: an
+// insertion sort (<= 16 keys, one thread), a rank sort (<= 128, one warp) or,
+// unless the group holds one value, a bitonic network (one CTA).
 //
-// Segments the model cannot split below CAP keys go to the fallback: an LSD
-// radix sort over the segment's varying total-order-key bytes, one CTA each.
+// Segments the model cannot split below CAP keys go to the fallback: per job
+// one CTA splits by the top byte in which the segment's total-order keys
+// differ (MSD), stops as soon as a piece holds one value, and finishes pieces
+// of at most CAP keys with the same counting sort on a linear map of the
+// piece's key range.
 #include <cfloat>
 
 #include "ls_partition.cuh"
@@ -22,12 +28,13 @@
 namespace ls {
 
 constexpr int MAXL = 64;        // leaves with per-segment coefficients
-constexpr int BIGCAP = 512;     // slot groups > 8 keys tracked per segment
+constexpr int BIGCAP = 512;     // slot groups > 16 keys tracked per segment
+constexpr int STACK = 2048;     // fallback work stack entries per CTA
 
 struct Coef {
   float A, B, LO, HI;
-  long long cq;
-  int sh;
+  long long C;
+  int P;
   int pad;
 };
 
@@ -41,6 +48,18 @@ struct BucketCfg {
   static constexpr size_t OFF_BIG = OFF_COEF + sizeof(Coef) * MAXL;
   static constexpr size_t OFF_WS = OFF_BIG + 8 * BIGCAP;
   static constexpr size_t SMEM = OFF_WS + 8 * 40;
+  // fallback extras
+  static constexpr size_t OFF_STACK = (SMEM + 15) / 16 * 16;
+  static constexpr size_t OFF_HIST = OFF_STACK + 16 * STACK;
+  static constexpr size_t SMEM_FB = OFF_HIST + 4 * 512;
+};
+
+struct SegShared {            // per-CTA scalars of the segment sort
+  unsigned long long tmin, tmax;
+  uint32_t nbig, all;
+  int mode;
+  float S, T, rscale;
+  int sh;
 };
 
 __device__ __forceinline__ float fp32_sat_d(double d) {
@@ -79,6 +98,201 @@ __device__ void block_bitonic(typename KT<DT>::U* a, uint32_t sz) {
   }
 }
 
+__device__ __forceinline__ int bitlen64d(uint64_t v) { return v ? 64 - __clzll((long long)v) : 0; }
+
+// Counting sort + touch-up of src[0..m) into dst[0..m) (dst may equal src).
+// model: use the model slot map (job F range, leaves la..lb); otherwise, or if
+// the model cannot split the range, a linear map of the total-order key range.
+template <int DT, int THREADS, int KPT>
+__device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* src, uint32_t m,
+                             bool model, double Flo, double Fhi, int la, int lb,
+                             const ModelPtrs& M, const RootEval& r, unsigned char* sm,
+                             SegShared& ss, uint32_t* err) {
+  typedef typename KT<DT>::U U;
+  typedef BucketCfg<DT, THREADS, KPT> C;
+  U* out = (U*)(sm + C::OFF_OUT);
+  uint32_t* cnt = (uint32_t*)(sm + C::OFF_CNT);
+  Coef* coef = (Coef*)(sm + C::OFF_COEF);
+  uint2* big = (uint2*)(sm + C::OFF_BIG);
+  unsigned long long* ws = (unsigned long long*)(sm + C::OFF_WS);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // load, total-order key range
+  U u[KPT];
+  unsigned long long mn = ~0ull, mx = 0;
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    const uint32_t i = k * THREADS + threadIdx.x;
+    u[k] = i < m ? src[i] : (U)0;
+    if (i < m) {
+      const unsigned long long t = KT<DT>::tk(u[k]);
+      mn = min(mn, t);
+      mx = max(mx, t);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if (threadIdx.x == 0) { ss.tmin = ~0ull; ss.tmax = 0; ss.nbig = 0; ss.all = 0; }
+  for (uint32_t i = threadIdx.x; i <= m; i += THREADS) cnt[i] = 0;
+  __syncthreads();
+  if (lane == 0) { atomicMin(&ss.tmin, mn); atomicMax(&ss.tmax, mx); }
+  const double width = Fhi - Flo;
+  const double scale = (double)m / width;
+  const int nl = lb - la + 1;
+  const bool use_model = model && (width > 0) && isfinite(scale) && nl >= 1;
+  if (use_model && nl <= MAXL) {
+    for (int j = threadIdx.x; j < nl; j += THREADS) {
+      const int l = la + j;
+      const double* q = M.leaf64 + 5 * (size_t)l;
+      const LeafFine lf = M.leaff[l];
+      Coef c;
+      c.A = fp32_sat_d(ldexp(q[0], lf.P) * scale);
+      c.B = fp32_sat_d((q[2] - Flo) * scale);
+      c.LO = fp32_sat_d((q[3] - Flo) * scale);
+      c.HI = fp32_sat_d((q[4] - Flo) * scale);
+      c.C = lf.C;
+      c.P = lf.P;
+      c.pad = 0;
+      coef[j] = c;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint64_t R = ss.tmax - ss.tmin;
+    const int sh = max(0, bitlen64d(R) - 24);
+    ss.sh = sh;
+    ss.rscale = (float)m / ((float)(R >> sh) + 1.0f);
+    ss.mode = use_model ? (nl <= MAXL ? 0 : 1) : 3;
+    ss.S = use_model ? fp32_sat_d(scale) : 0.0f;
+    ss.T = use_model ? fp32_sat_d(-Flo * scale) : 0.0f;
+  }
+  __syncthreads();
+  const int mode = ss.mode;
+  const float S = ss.S, T = ss.T, rscale = ss.rscale;
+  const int sh = ss.sh;
+  const unsigned long long tmin = ss.tmin;
+  const float mlim = (float)(m - 1);
+  // slots, histogram, ranks
+  uint32_t sl[KPT], rk[KPT];
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    const uint32_t i = k * THREADS + threadIdx.x;
+    uint32_t s = 0xFFFFFFFFu;
+    if (i < m) {
+      const U x = u[k];
+      float v;
+      if (mode == 3) {
+        v = __uint2float_rn((uint32_t)((KT<DT>::tk(x) - tmin) >> sh)) * rscale;
+      } else if (KT<DT>::is_nan(x)) {
+        v = KT<DT>::neg(x) ? 0.0f : mlim;
+      } else if (mode == 0) {
+        const int l = predict_leaf<DT>(x, r);
+        if (l < la) v = 0.0f;
+        else if (l > lb) v = mlim;
+        else {
+          const Coef c = coef[l - la];
+          const float d = __int2float_rn(feat32(fixed_point<DT>(x, c.P), c.C, TF_LIM));
+          v = fminf(fmaxf(__fmaf_rn(c.A, d, c.B), c.LO), c.HI);
+        }
+      } else {
+        v = __fmaf_rn(predict_F<DT>(x, r, M.leaff), S, T);
+      }
+      s = (v > 0.0f) ? (v >= mlim ? m - 1 : (uint32_t)v) : 0u;
+    }
+    sl[k] = s;
+    rk[k] = s != 0xFFFFFFFFu ? atomicAdd(&cnt[s], 1u) : 0u;  // rank inside the slot
+  }
+  __syncthreads();
+  {
+    const int per = (int)((m + THREADS - 1) / THREADS);
+    const int b = threadIdx.x * per;
+    uint32_t s = 0;
+    for (int i = 0; i < per; ++i)
+      if (b + i < (int)m) s += cnt[b + i];
+    unsigned long long tot;
+    unsigned long long run = block_excl_sum<unsigned long long>(s, ws, &tot);
+    for (int i = 0; i < per; ++i)
+      if (b + i < (int)m) { const uint32_t t = cnt[b + i]; cnt[b + i] = (uint32_t)run; run += t; }
+    if (threadIdx.x == 0) cnt[m] = m;
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    if (sl[k] != 0xFFFFFFFFu) {
+      const uint32_t p = cnt[sl[k]] + rk[k];
+      if (p < m) out[p] = u[k]; else set_error(err, ERR_BOUNDS);
+    }
+  }
+  __syncthreads();
+  // touch-up: sort every group of keys that share a slot
+  for (uint32_t s = threadIdx.x; s < m; s += THREADS) {
+    const uint32_t a = cnt[s], b = cnt[s + 1];
+    if (b <= a + 1) continue;
+    const uint32_t sz = b - a;
+    if (sz <= 16) {  // (a run of equal keys costs one compare per key)
+      for (uint32_t i = a + 1; i < b; ++i) {
+        const U x = out[i];
+        const uint64_t t = KT<DT>::tk(x);
+        uint32_t j = i;
+        while (j > a && KT<DT>::tk(out[j - 1]) > t) { out[j] = out[j - 1]; --j; }
+        out[j] = x;
+      }
+    } else {
+      const uint32_t idx = atomicAdd(&ss.nbig, 1u);
+      if (idx < BIGCAP) big[idx] = make_uint2(a, sz);
+      else ss.all = 1;
+    }
+  }
+  __syncthreads();
+  if (ss.all) {
+    block_bitonic<DT>(out, m);
+  } else {
+    const uint32_t nb = ss.nbig;
+    for (uint32_t g = wid; g < nb; g += THREADS / 32) {
+      const uint2 gr = big[g];
+      if (gr.y > 128) continue;
+      U x[4];
+      uint32_t rank[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t i = lane + 32 * q;
+        rank[q] = 0;
+        x[q] = i < gr.y ? out[gr.x + i] : (U)0;
+      }
+      for (uint32_t j = 0; j < gr.y; ++j) {
+        const uint64_t tj = KT<DT>::tk(out[gr.x + j]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t i = lane + 32 * q;
+          const uint64_t ti = KT<DT>::tk(x[q]);
+          rank[q] += (tj < ti || (tj == ti && j < i)) ? 1u : 0u;
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t i = lane + 32 * q;
+        if (i < gr.y) out[gr.x + rank[q]] = x[q];
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    for (uint32_t g = 0; g < nb; ++g) {
+      const uint2 gr = big[g];
+      if (gr.y <= 128) continue;
+      const uint64_t t0 = KT<DT>::tk(out[gr.x]);
+      int diff = 0;
+      for (uint32_t i = threadIdx.x; i < gr.y; i += THREADS)
+        diff |= KT<DT>::tk(out[gr.x + i]) != t0;
+      if (__syncthreads_or(diff)) block_bitonic<DT>(out + gr.x, gr.y);
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < m; i += THREADS) dst[i] = out[i];
+  __syncthreads();
+}
+
 template <int DT, int THREADS, int KPT>
 __global__ void __launch_bounds__(THREADS)
 k_bucket_sort(typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, ModelPtrs M,
@@ -86,293 +300,133 @@ k_bucket_sort(typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Model
   typedef typename KT<DT>::U U;
   typedef BucketCfg<DT, THREADS, KPT> C;
   extern __shared__ __align__(16) unsigned char sm[];
-  U* out = (U*)(sm + C::OFF_OUT);
-  uint32_t* cnt = (uint32_t*)(sm + C::OFF_CNT);
-  Coef* coef = (Coef*)(sm + C::OFF_COEF);
-  uint2* big = (uint2*)(sm + C::OFF_BIG);
-  unsigned long long* ws = (unsigned long long*)(sm + C::OFF_WS);
+  __shared__ SegShared ss;
   __shared__ unsigned long long s_job;
-  __shared__ int s_lmin, s_lmax;
-  __shared__ uint32_t s_nbig, s_all;
-  __shared__ float s_S, s_T;
-  __shared__ int s_mode;  // 0: per-leaf coefficients, 1: global F, 2: single slot
   const RootEval r = M.hdr->root;
-  const int E = r.E;
   const unsigned long long nj = min(*list.count, list.cap);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const unsigned lt = lanemask_lt();
   while (true) {
     if (threadIdx.x == 0) s_job = atomicAdd(ctr, 1ull);
     __syncthreads();
     const unsigned long long jid = s_job;
     if (jid >= nj) break;
     const Job job = list.jobs[jid];
-    const uint32_t m = (uint32_t)job.m;
     if (job.m > (uint64_t)C::CAP) {  // classification guarantees m <= CAP
       if (threadIdx.x == 0) set_error(err, ERR_BOUNDS);
       __syncthreads();
       continue;
     }
     const U* src = (job.src ? scratch : keys) + job.start;
-    // pass 1: load keys, leaf range
-    U u[KPT];
-    int lmin = 0x7fffffff, lmax = -1;
-#pragma unroll
-    for (int k = 0; k < KPT; ++k) {
-      const uint32_t i = k * THREADS + threadIdx.x;
-      u[k] = i < m ? src[i] : (U)0;
-      if (i < m && !KT<DT>::is_nan(u[k])) {
-        int64_t q;
-        const int l = predict_leaf<DT>(u[k], r, &q);
-        lmin = min(lmin, l);
-        lmax = max(lmax, l);
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      lmin = min(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
-      lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
-    }
-    if (threadIdx.x == 0) { s_lmin = 0x7fffffff; s_lmax = -1; s_nbig = 0; s_all = 0; }
-    for (uint32_t i = threadIdx.x; i <= m; i += THREADS) cnt[i] = 0;
-    __syncthreads();
-    if (lane == 0) { atomicMin(&s_lmin, lmin); atomicMax(&s_lmax, lmax); }
-    __syncthreads();
-    const int l0 = s_lmin, nl = s_lmax - s_lmin + 1;
-    const double width = job.Fhi - job.Flo;
-    const double scale = (double)m / width;
-    const bool ok = (width > 0) && isfinite(scale) && m > 0;
-    if (threadIdx.x == 0) {
-      s_mode = !ok ? 2 : (nl >= 1 && nl <= MAXL ? 0 : 1);
-      s_S = ok ? fp32_sat_d(scale) : 0.0f;
-      s_T = ok ? fp32_sat_d(-job.Flo * scale) : 0.0f;
-    }
-    if (ok && nl >= 1 && nl <= MAXL) {
-      for (int j = threadIdx.x; j < nl; j += THREADS) {
-        const int l = l0 + j;
-        const double* q = M.leaf64 + 5 * (size_t)l;
-        const LeafEval le = M.leaf[l];
-        Coef c;
-        c.A = fp32_sat_d(ldexp(q[0], E + le.sh) * scale);
-        c.B = fp32_sat_d((q[2] - job.Flo) * scale);
-        c.LO = fp32_sat_d((q[3] - job.Flo) * scale);
-        c.HI = fp32_sat_d((q[4] - job.Flo) * scale);
-        c.cq = le.cq;
-        c.sh = le.sh;
-        c.pad = 0;
-        coef[j] = c;
-      }
-    }
-    __syncthreads();
-    const int mode = s_mode;
-    const float S = s_S, T = s_T;
-    const float mlim = (float)(m - 1);
-    // pass 2: slots, histogram, ranks
-    uint32_t sl[KPT], rk[KPT];
-#pragma unroll
-    for (int k = 0; k < KPT; ++k) {
-      const uint32_t i = k * THREADS + threadIdx.x;
-      uint32_t s = 0xFFFFFFFFu;
-      if (i < m) {
-        const U x = u[k];
-        if (KT<DT>::is_nan(x)) {
-          s = KT<DT>::neg(x) ? 0u : m - 1;
-        } else if (mode == 2) {
-          s = 0;
-        } else {
-          float v;
-          if (mode == 0) {
-            int64_t q;
-            const int l = predict_leaf<DT>(x, r, &q);
-            const Coef c = coef[l - l0];
-            v = __fmaf_rn(c.A, feature(q, c.cq, c.sh), c.B);
-            v = fminf(fmaxf(v, c.LO), c.HI);
-          } else {
-            v = __fmaf_rn(predict_F<DT>(x, r, M.leaf), S, T);
-          }
-          s = (v > 0.0f) ? (v >= mlim ? m - 1 : (uint32_t)v) : 0u;
-        }
-      }
-      sl[k] = s;
-      const unsigned peers = __match_any_sync(0xffffffffu, s);
-      const int leader = __ffs(peers) - 1;
-      uint32_t old = 0;
-      if (s != 0xFFFFFFFFu && lane == leader) old = atomicAdd(&cnt[s], (uint32_t)__popc(peers));
-      old = __shfl_sync(0xffffffffu, old, leader);
-      rk[k] = old + __popc(peers & lt);
-    }
-    __syncthreads();
-    {
-      // exclusive scan of cnt[0..m) in place (32-bit)
-      const int per = (int)((m + THREADS - 1) / THREADS);
-      const int b = threadIdx.x * per;
-      uint32_t s = 0;
-      for (int i = 0; i < per; ++i)
-        if (b + i < (int)m) s += cnt[b + i];
-      unsigned long long tot;
-      unsigned long long run = block_excl_sum<unsigned long long>(s, ws, &tot);
-      for (int i = 0; i < per; ++i)
-        if (b + i < (int)m) { const uint32_t t = cnt[b + i]; cnt[b + i] = (uint32_t)run; run += t; }
-      if (threadIdx.x == 0) cnt[m] = m;
-      __syncthreads();
-    }
-#pragma unroll
-    for (int k = 0; k < KPT; ++k) {
-      if (sl[k] != 0xFFFFFFFFu) {
-        const uint32_t p = cnt[sl[k]] + rk[k];
-        if (p < m) out[p] = u[k]; else set_error(err, ERR_BOUNDS);
-      }
-    }
-    __syncthreads();
-    // touch-up: sort every group of keys that share a slot
-    for (uint32_t s = threadIdx.x; s < m; s += THREADS) {
-      const uint32_t a = cnt[s], b = cnt[s + 1];
-      if (b <= a + 1) continue;
-      const uint32_t sz = b - a;
-      if (sz <= 8) {
-        for (uint32_t i = a + 1; i < b; ++i) {
-          const U x = out[i];
-          const uint64_t t = KT<DT>::tk(x);
-          uint32_t j = i;
-          while (j > a && KT<DT>::tk(out[j - 1]) > t) { out[j] = out[j - 1]; --j; }
-          out[j] = x;
-        }
-      } else {
-        const uint32_t idx = atomicAdd(&s_nbig, 1u);
-        if (idx < BIGCAP) big[idx] = make_uint2(a, sz);
-        else s_all = 1;
-      }
-    }
-    __syncthreads();
-    if (s_all) {
-      block_bitonic<DT>(out, m);
-    } else {
-      const uint32_t nb = s_nbig;
-      for (uint32_t g = wid; g < nb; g += THREADS / 32) {
-        const uint2 gr = big[g];
-        if (gr.y > 128) continue;
-        U x[4];
-        uint32_t rank[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint32_t i = lane + 32 * q;
-          rank[q] = 0;
-          x[q] = i < gr.y ? out[gr.x + i] : (U)0;
-        }
-        for (uint32_t j = 0; j < gr.y; ++j) {
-          const uint64_t tj = KT<DT>::tk(out[gr.x + j]);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const uint32_t i = lane + 32 * q;
-            const uint64_t ti = KT<DT>::tk(x[q]);
-            rank[q] += (tj < ti || (tj == ti && j < i)) ? 1u : 0u;
-          }
-        }
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint32_t i = lane + 32 * q;
-          if (i < gr.y) out[gr.x + rank[q]] = x[q];
-        }
-        __syncwarp();
-      }
-      __syncthreads();
-      for (uint32_t g = 0; g < nb; ++g) {
-        const uint2 gr = big[g];
-        if (gr.y <= 128) continue;
-        const uint64_t t0 = KT<DT>::tk(out[gr.x]);
-        int diff = 0;
-        for (uint32_t i = threadIdx.x; i < gr.y; i += THREADS)
-          diff |= KT<DT>::tk(out[gr.x + i]) != t0;
-        if (__syncthreads_or(diff)) block_bitonic<DT>(out + gr.x, gr.y);
-      }
-    }
-    __syncthreads();
-    U* dst = keys + job.start;
-    for (uint32_t i = threadIdx.x; i < m; i += THREADS) dst[i] = out[i];
-    __syncthreads();
+    segment_sort<DT, THREADS, KPT>(keys + job.start, src, (uint32_t)job.m, true, job.Flo, job.Fhi,
+                                   (int)job.la, (int)job.lb, M, r, sm, ss, err);
   }
 }
 
 // ---------------------------------------------------------------- fallback
+struct StackEnt {
+  unsigned long long start;
+  uint32_t m;
+  uint32_t buf;  // 0: keys, 1: scratch
+};
+
 template <int DT>
-__global__ void __launch_bounds__(RS_THREADS)
-k_fallback(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, JobList list,
+__global__ void __launch_bounds__(512)
+k_fallback(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, ModelPtrs M, JobList list,
            unsigned long long* ctr, uint32_t* err) {
   typedef typename KT<DT>::U U;
-  constexpr int NDIG = KT<DT>::W;
-  __shared__ RsShared sh;
-  __shared__ uint32_t hist[256];
-  __shared__ uint32_t ws[33];
+  typedef BucketCfg<DT, 512, 16> C;
+  extern __shared__ __align__(16) unsigned char sm[];
+  StackEnt* stack = (StackEnt*)(sm + C::OFF_STACK);
+  uint32_t* hist = (uint32_t*)(sm + C::OFF_HIST);
+  uint32_t* cur = hist + 256;
+  __shared__ SegShared ss;
   __shared__ unsigned long long s_job, s_or, s_and;
+  __shared__ int s_top;
+  __shared__ StackEnt s_e;
+  __shared__ uint32_t ws32[33];
+  const RootEval r = M.hdr->root;
   const unsigned long long nj = min(*list.count, list.cap);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
   while (true) {
-    if (threadIdx.x == 0) { s_job = atomicAdd(ctr, 1ull); s_or = 0; s_and = ~0ull; }
+    if (threadIdx.x == 0) s_job = atomicAdd(ctr, 1ull);
     __syncthreads();
     const unsigned long long jid = s_job;
     if (jid >= nj) break;
-    const Job job = list.jobs[jid];
-    const uint64_t m = job.m;
-    U* X = (job.src ? scratch : keys) + job.start;
-    U* Y = (job.src ? keys : scratch) + job.start;
-    unsigned long long o = 0, a = ~0ull;
-    for (uint64_t i = threadIdx.x; i < m; i += RS_THREADS) {
-      const uint64_t t = KT<DT>::tk(X[i]);
-      o |= t;
-      a &= t;
+    if (threadIdx.x == 0) {
+      const Job job = list.jobs[jid];
+      stack[0].start = job.start;
+      stack[0].m = (uint32_t)job.m;
+      stack[0].buf = job.src;
+      s_top = 1;
     }
-    for (int s = 16; s > 0; s >>= 1) {
-      o |= __shfl_xor_sync(0xffffffffu, o, s);
-      a &= __shfl_xor_sync(0xffffffffu, a, s);
-    }
-    if (lane == 0) { atomicOr(&s_or, o); atomicAnd(&s_and, a); }
     __syncthreads();
-    const uint64_t diff = s_or ^ s_and;
-    for (int d = 0; d < NDIG; ++d) {
-      if (((diff >> (8 * d)) & 255u) == 0) continue;
-      const int shift = 8 * d;
+    while (true) {
+      if (threadIdx.x == 0) {
+        if (s_top > 0) { s_e = stack[s_top - 1]; --s_top; }
+        else s_e.m = 0xFFFFFFFFu;
+        s_or = 0;
+        s_and = ~0ull;
+      }
+      __syncthreads();
+      const StackEnt e = s_e;
+      if (e.m == 0xFFFFFFFFu) break;
+      U* X = (e.buf ? scratch : keys) + e.start;
+      U* Y = (e.buf ? keys : scratch) + e.start;
+      U* D = keys + e.start;
+      if (e.m <= (uint32_t)C::CAP) {
+        segment_sort<DT, 512, 16>(D, X, e.m, false, 0.0, 0.0, 0, 0, M, r, sm, ss, err);
+        continue;
+      }
+      unsigned long long o = 0, a = ~0ull;
+      for (uint32_t i = threadIdx.x; i < e.m; i += 512) {
+        const uint64_t t = KT<DT>::tk(X[i]);
+        o |= t;
+        a &= t;
+      }
+      for (int s = 16; s > 0; s >>= 1) {
+        o |= __shfl_xor_sync(0xffffffffu, o, s);
+        a &= __shfl_xor_sync(0xffffffffu, a, s);
+      }
+      if (lane == 0) { atomicOr(&s_or, o); atomicAnd(&s_and, a); }
       if (threadIdx.x < 256) hist[threadIdx.x] = 0;
       __syncthreads();
-      for (uint64_t i = threadIdx.x; i < m; i += RS_THREADS)
+      const uint64_t diff = s_or ^ s_and;
+      if (diff == 0) {  // one value: already in order
+        if (X != D)
+          for (uint32_t i = threadIdx.x; i < e.m; i += 512) D[i] = X[i];
+        __syncthreads();
+        continue;
+      }
+      const int shift = ((63 - __clzll((long long)diff)) >> 3) << 3;  // top differing byte
+      for (uint32_t i = threadIdx.x; i < e.m; i += 512)
         atomicAdd(&hist[(KT<DT>::tk(X[i]) >> shift) & 255u], 1u);
       __syncthreads();
-      uint32_t c = threadIdx.x < 256 ? hist[threadIdx.x] : 0u;
+      const uint32_t c = threadIdx.x < 256 ? hist[threadIdx.x] : 0u;
       uint32_t tot;
-      const uint32_t ex = block_excl_sum<uint32_t>(c, ws, &tot);
-      if (threadIdx.x < 256) sh.run[threadIdx.x] = ex;
+      const uint32_t ex = block_excl_sum<uint32_t>(c, ws32, &tot);
+      if (threadIdx.x < 256) cur[threadIdx.x] = ex;
       __syncthreads();
-      for (uint64_t base = 0; base < m; base += RS_TILE) {
-        uint64_t key[RS_ROUNDS];
-        bool valid[RS_ROUNDS];
-        uint32_t lrank[RS_ROUNDS];
-#pragma unroll
-        for (int r = 0; r < RS_ROUNDS; ++r) {
-          const uint64_t i = base + (uint64_t)w * (32 * RS_ROUNDS) + r * 32 + lane;
-          valid[r] = i < m;
-          key[r] = valid[r] ? (uint64_t)X[i] : 0;
-        }
-        uint32_t tcnt = 0;
-        rs_rank_tile(sh, key, valid, lrank,
-                     [shift](uint64_t k) { return (uint32_t)(KT<DT>::tk((U)k) >> shift) & 255u; },
-                     &tcnt);
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < RS_ROUNDS; ++r) {
-          if (!valid[r]) continue;
-          const uint32_t dg = (uint32_t)(KT<DT>::tk((U)key[r]) >> shift) & 255u;
-          const uint64_t pos = (uint64_t)sh.run[dg] + sh.whist[w][dg] + lrank[r];
-          if (pos < m) Y[pos] = (U)key[r]; else set_error(err, ERR_BOUNDS);
-        }
-        __syncthreads();
-        if (threadIdx.x < 256) sh.run[threadIdx.x] += tcnt;
-        __syncthreads();
+      for (uint32_t i = threadIdx.x; i < e.m; i += 512) {
+        const U x = X[i];
+        const uint32_t p = atomicAdd(&cur[(KT<DT>::tk(x) >> shift) & 255u], 1u);
+        if (p < e.m) Y[p] = x; else set_error(err, ERR_BOUNDS);
       }
-      U* t = X; X = Y; Y = t;
+      __syncthreads();
+      if (threadIdx.x < 256 && c > 0) {
+        const int slot = atomicAdd(&s_top, 1);
+        if (slot < STACK) {
+          StackEnt ne;
+          ne.start = e.start + ex;
+          ne.m = c;
+          ne.buf = e.buf ^ 1u;
+          stack[slot] = ne;
+        } else {
+          set_error(err, ERR_BOUNDS);
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0 && s_top > STACK) s_top = STACK;
+      __syncthreads();
     }
-    U* dst = keys + job.start;
-    if (X != dst)
-      for (uint64_t i = threadIdx.x; i < m; i += RS_THREADS) dst[i] = X[i];
-    __syncthreads();
   }
 }
 
@@ -386,9 +440,12 @@ static cudaError_t buckets_cfg_dt() {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)BucketCfg<DT, BS_SMALL_T, BS_SMALL_K>::SMEM);
   if (e) return e;
-  return cudaFuncSetAttribute(k_bucket_sort<DT, BS_LARGE_T, BS_LARGE_K>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)BucketCfg<DT, BS_LARGE_T, BS_LARGE_K>::SMEM);
+  e = cudaFuncSetAttribute(k_bucket_sort<DT, BS_LARGE_T, BS_LARGE_K>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)BucketCfg<DT, BS_LARGE_T, BS_LARGE_K>::SMEM);
+  if (e) return e;
+  return cudaFuncSetAttribute(k_fallback<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)BucketCfg<DT, 512, 16>::SMEM_FB);
 }
 
 cudaError_t buckets_configure(int dt) {
@@ -409,7 +466,7 @@ static cudaError_t buckets_dt(void* keys, void* scratch, const ModelPtrs& M, con
   typedef typename KT<DT>::U U;
   const unsigned gs = (unsigned)std::min<uint64_t>(std::max<uint64_t>(cap_s, 1), 8ull * num_sms);
   const unsigned gl = (unsigned)std::min<uint64_t>(std::max<uint64_t>(cap_l, 1), 2ull * num_sms);
-  const unsigned gf = (unsigned)std::min<uint64_t>(std::max<uint64_t>(cap_fb, 1), 2ull * num_sms);
+  const unsigned gf = (unsigned)std::min<uint64_t>(std::max<uint64_t>(cap_fb, 1), 1ull * num_sms);
   k_bucket_sort<DT, BS_SMALL_T, BS_SMALL_K>
       <<<gs, BS_SMALL_T, BucketCfg<DT, BS_SMALL_T, BS_SMALL_K>::SMEM, st>>>(
           (U*)keys, (const U*)scratch, M, lists.sort_s, ctrs + 0, err);
@@ -418,7 +475,8 @@ static cudaError_t buckets_dt(void* keys, void* scratch, const ModelPtrs& M, con
       <<<gl, BS_LARGE_T, BucketCfg<DT, BS_LARGE_T, BS_LARGE_K>::SMEM, st>>>(
           (U*)keys, (const U*)scratch, M, lists.sort_l, ctrs + 1, err);
   mark(mk, mb + 1, st);
-  k_fallback<DT><<<gf, RS_THREADS, 0, st>>>((U*)keys, (U*)scratch, lists.fallback, ctrs + 2, err);
+  k_fallback<DT><<<gf, 512, BucketCfg<DT, 512, 16>::SMEM_FB, st>>>((U*)keys, (U*)scratch, M,
+                                                                  lists.fallback, ctrs + 2, err);
   mark(mk, mb + 2, st);
   add_launches(3);
   return cudaGetLastError();

@@ -73,82 +73,95 @@ template <> struct KT<LS_U32> {
 };
 
 // ------------------------------------------------------------------ fixed point
-// q(x) = floor(x * 2^-E) saturated to [-2^62, 2^62]; |x| = M * 2^exp2.
-// Integer arithmetic only (monotone in x by construction).
-__device__ __forceinline__ int64_t fx_core(bool neg, uint64_t M, int exp2, int E) {
-  if (M == 0) return 0;
-  const int k = exp2 - E;
-  uint64_t v;
-  uint64_t rem = 0;
-  if (k >= 0) {
-    v = (k > 62 || M > (1ull << (62 - k))) ? (uint64_t)Q_SAT : (M << k);
-  } else {
-    const int j = -k;
-    if (j >= 64) { v = 0; rem = 1; }
-    else { v = M >> j; rem = (M & ((1ull << j) - 1)) != 0; }
-  }
-  int64_t q = neg ? -(int64_t)(v + rem) : (int64_t)v;
-  q = q > Q_SAT ? Q_SAT : q;
-  q = q < -Q_SAT ? -Q_SAT : q;
-  return q;
+// fx(x, P) = floor(x * 2^-P) saturated to [-2^62, 2^62] for a non-NaN key
+// (infinities saturate).  |x| = M * 2^exp2.  Integer operations only, exact,
+// hence monotone in x.  For the usual right shift j = P - exp2 > 0 the floor of
+// a negative value is ~((M - 1) >> j).
+__device__ __forceinline__ int64_t fx_core(bool neg, uint64_t M, int exp2, int P) {
+  // Branch-free (selects only) so that the keys a thread holds interleave.
+  const int j = P - exp2;                          // right shift
+  const int jr = j < 1 ? 1 : (j > 63 ? 63 : j);
+  const int64_t rpos = (int64_t)(M >> jr);
+  const int64_t rneg = (int64_t)~((M - 1) >> jr);  // floor(-M / 2^j), M >= 1
+  int64_t r = neg ? rneg : rpos;
+  r = (j >= 64) ? (neg ? -1 : 0) : r;
+  const int k = -j;                                // left shift (j <= 0)
+  const int kk = k < 0 ? 0 : (k > 62 ? 62 : k);
+  const bool ok = (k <= 62) && (M <= (1ull << (62 - kk)));
+  const int64_t lv = ok ? (int64_t)(M << kk) : Q_SAT;
+  r = (j <= 0) ? (neg ? -lv : lv) : r;
+  return M == 0 ? 0 : r;
 }
 
-__device__ __forceinline__ int64_t fx_f64bits(uint64_t u, int E) {
+__device__ __forceinline__ int64_t fx_f64bits(uint64_t u, int P) {
   const bool neg = (u >> 63) != 0;
   const int e = (int)((u >> 52) & 0x7FF);
-  const uint64_t m = u & ((1ull << 52) - 1);
-  if (e == 0x7FF) return neg ? -Q_SAT : Q_SAT;
-  if (e == 0) return fx_core(neg, m, -1074, E);
-  return fx_core(neg, m | (1ull << 52), e - 1075, E);
+  const uint64_t M = (u & ((1ull << 52) - 1)) | ((uint64_t)(e != 0) << 52);
+  const int64_t r = fx_core(neg, M, (e ? e : 1) - 1075, P);
+  return e == 0x7FF ? (neg ? -Q_SAT : Q_SAT) : r;
 }
 
-template <int DT> __device__ __forceinline__ int64_t fixed_point(typename KT<DT>::U u, int E);
-template <> __device__ __forceinline__ int64_t fixed_point<LS_F64>(uint64_t u, int E) {
-  return fx_f64bits(u, E);
+template <int DT> __device__ __forceinline__ int64_t fixed_point(typename KT<DT>::U u, int P);
+template <> __device__ __forceinline__ int64_t fixed_point<LS_F64>(uint64_t u, int P) {
+  return fx_f64bits(u, P);
 }
-template <> __device__ __forceinline__ int64_t fixed_point<LS_F32>(uint32_t u, int E) {
+template <> __device__ __forceinline__ int64_t fixed_point<LS_F32>(uint32_t u, int P) {
   const bool neg = (u >> 31) != 0;
   const int e = (int)((u >> 23) & 0xFF);
-  const uint64_t m = u & ((1u << 23) - 1);
-  if (e == 0xFF) return neg ? -Q_SAT : Q_SAT;
-  if (e == 0) return fx_core(neg, m, -149, E);
-  return fx_core(neg, m | (1u << 23), e - 150, E);
+  const uint64_t M = (uint64_t)((u & ((1u << 23) - 1)) | ((uint32_t)(e != 0) << 23));
+  const int64_t r = fx_core(neg, M, (e ? e : 1) - 150, P);
+  return e == 0xFF ? (neg ? -Q_SAT : Q_SAT) : r;
 }
-template <> __device__ __forceinline__ int64_t fixed_point<LS_U64>(uint64_t u, int E) {
-  return fx_core(false, u, 0, E);
+template <> __device__ __forceinline__ int64_t fixed_point<LS_U64>(uint64_t u, int P) {
+  return fx_core(false, u, 0, P);
 }
-template <> __device__ __forceinline__ int64_t fixed_point<LS_U32>(uint32_t u, int E) {
-  return fx_core(false, (uint64_t)u, 0, E);
+template <> __device__ __forceinline__ int64_t fixed_point<LS_U32>(uint32_t u, int P) {
+  return fx_core(false, (uint64_t)u, 0, P);
 }
 
-// Centred feature: floor((q - cq) / 2^sh) clamped to +-(2^31 - 1), as float.
-__device__ __forceinline__ float feature(int64_t q, int64_t cq, int sh) {
-  int64_t d = (q - cq) >> sh;
-  const int64_t LIM = 2147483647;
-  d = d > LIM ? LIM : d;
-  d = d < -LIM ? -LIM : d;
-  return __int2float_rn((int)d);
+// Centred 32-bit feature: clamp(fx - C, +-lim).
+__device__ __forceinline__ int feat32(int64_t fx, int64_t C, int64_t lim) {
+  int64_t d = fx - C;
+  d = d > lim ? lim : d;
+  d = d < -lim ? -lim : d;
+  return (int)d;
 }
+constexpr int64_t T0_LIM = (1ll << 30) - 1;   // root feature range
+constexpr int64_t TF_LIM = 2147483647ll;      // fine feature range
 
 // ------------------------------------------------------------------ model
-struct LeafEval {      // 32 bytes, FP32 evaluation of one leaf
-  long long cq;
-  float A, B, LO, HI;
-  int sh;
-  int pad;
+// Two evaluations of the same monotone model F:
+//  * level 0 (buckets), integer only: the root feature
+//      t0 = clamp(fx(x, P0) - C0, +-(2^30 - 1)),
+//    leaf l = clamp((RA * t0 + RB) >> 40, 0, L-1), and the bucket
+//      b = clamp((AL_l * t0 + BL_l) >> 32, lo_l, hi_l),
+//    the fixed-point form of floor(F(x) * f0) with hi_l = lo_{l+1};
+//  * fine (level-1 split, in-bucket slots), FP32 on the leaf's own grid:
+//      F = clamp(A_l * clamp(fx(x, P_l) - C_l) + B_l, LO_l, HI_l),  HI_l = LO_{l+1}.
+struct LeafL0 {        // 16 bytes
+  int AL;              // slope, bucket units * 2^32 per root-feature unit
+  uint32_t lohi;       // lo_l | hi_l << 16 (bucket clamps)
+  long long BL;        // intercept at t0 = 0, bucket units * 2^32
+};
+struct LeafFine {      // 32 bytes; record L is a sentinel with LO = 1
+  long long C;
+  float A;
+  int P;
+  float B, LO;
+  int pad0, pad1;
 };
 struct RootEval {
-  long long cq;
-  float A, B;
-  int sh;
+  long long C0;        // root feature centre on the grid 2^P0
+  long long RB;        // leaf intercept * 2^40
+  int RA;              // leaf slope * 2^40 per root-feature unit
+  int P0;
   int E;
   int L;
-  int pad;
 };
 
 struct HeavyEntry {    // a heavy value of one level-0 bucket
   uint64_t tk;         // total-order key
-  float F;             // FP32 eCDF estimate of the value
+  float F;             // fine FP32 eCDF estimate of the value
   uint32_t pad;
 };
 
@@ -158,64 +171,94 @@ struct BucketHead {
   uint32_t hoff_nh;    // hoff << 4 | nh
 };
 
-// FP32 eCDF estimate F(x) in [0,1] for a non-NaN key; leaf from the root.
 template <int DT>
-__device__ __forceinline__ float predict_F(typename KT<DT>::U u, const RootEval& r,
-                                           const LeafEval* __restrict__ leaves) {
-  const int64_t q = fixed_point<DT>(u, r.E);
-  const float v = __fmaf_rn(r.A, feature(q, r.cq, r.sh), r.B);
-  int l;
-  if (v >= (float)r.L) l = r.L - 1;
-  else if (v > 0.0f) l = (int)v;
-  else l = 0;
-  const LeafEval le = leaves[l];
-  float F = __fmaf_rn(le.A, feature(q, le.cq, le.sh), le.B);
-  F = fmaxf(F, le.LO);
-  F = fminf(F, le.HI);
-  return F;
+__device__ __forceinline__ int root_t0(typename KT<DT>::U u, const RootEval& r) {
+  return feat32(fixed_point<DT>(u, r.P0), r.C0, T0_LIM);
+}
+__device__ __forceinline__ int leaf_of_t0(int t0, const RootEval& r) {
+  const long long v = (long long)r.RA * (long long)t0 + r.RB;
+  int l = (int)(v >> 40);
+  l = l < 0 ? 0 : l;
+  return l >= r.L ? r.L - 1 : l;
 }
 
 template <int DT>
-__device__ __forceinline__ int predict_leaf(typename KT<DT>::U u, const RootEval& r, int64_t* q_out) {
-  const int64_t q = fixed_point<DT>(u, r.E);
-  *q_out = q;
-  const float v = __fmaf_rn(r.A, feature(q, r.cq, r.sh), r.B);
-  if (v >= (float)r.L) return r.L - 1;
-  if (v > 0.0f) return (int)v;
-  return 0;
+__device__ __forceinline__ int predict_leaf(typename KT<DT>::U u, const RootEval& r) {
+  return leaf_of_t0(root_t0<DT>(u, r), r);
+}
+
+// Level-0 bucket of a non-NaN key (integer evaluation).
+__device__ __forceinline__ uint32_t bucket_of_t0(int t0, const RootEval& r,
+                                                 const LeafL0* __restrict__ l0) {
+  const LeafL0 c = l0[leaf_of_t0(t0, r)];
+  const long long v = (long long)c.AL * (long long)t0 + c.BL;
+  int b = (int)(v >> 32);
+  const int lo = (int)(c.lohi & 0xFFFFu), hi = (int)(c.lohi >> 16);
+  b = b < lo ? lo : b;
+  return (uint32_t)(b > hi ? hi : b);
+}
+
+// Fine feature of a key in leaf l.
+template <int DT>
+__device__ __forceinline__ float fine_feature(typename KT<DT>::U u, const LeafFine& f) {
+  return __int2float_rn(feat32(fixed_point<DT>(u, f.P), f.C, TF_LIM));
+}
+
+// Fine FP32 eCDF estimate F(x) for a non-NaN key.
+template <int DT>
+__device__ __forceinline__ float predict_F(typename KT<DT>::U u, const RootEval& r,
+                                           const LeafFine* __restrict__ lf) {
+  const int l = predict_leaf<DT>(u, r);
+  const LeafFine f = lf[l];
+  float F = __fmaf_rn(f.A, fine_feature<DT>(u, f), f.B);
+  F = fmaxf(F, f.LO);
+  F = fminf(F, lf[l + 1].LO);
+  return F;
 }
 
 // Level-0 bucket of a key (NaNs go to the end buckets by sign).
 template <int DT>
 __device__ __forceinline__ uint32_t bucket_of(typename KT<DT>::U u, const RootEval& r,
-                                              const LeafEval* __restrict__ leaves, uint32_t f0) {
-  if (KT<DT>::is_nan(u)) return KT<DT>::neg(u) ? 0u : f0 - 1;
-  const float F = predict_F<DT>(u, r, leaves);
-  const uint32_t b = (uint32_t)__fmul_rn(F, (float)f0);
-  return b < f0 ? b : f0 - 1;
+                                              const LeafL0* __restrict__ l0, uint32_t f0) {
+  const uint32_t b = bucket_of_t0(root_t0<DT>(u, r), r, l0);
+  return KT<DT>::is_nan(u) ? (KT<DT>::neg(u) ? 0u : f0 - 1) : b;
 }
 
 // Extended slot: regular bucket b with heavies h_1<..<h_k has slots
-// ext_base + {0: <h_1, 1: =h_1, 2: (h_1,h_2), ..., 2k: >h_k}.
+// ext_base + {0: <h_1, 1: =h_1, 2: (h_1,h_2), ..., 2k: >h_k}.  `htk` holds the
+// heavy values' total-order keys (bucket b's at [hoff, hoff + nh)).  Returns
+// the slot; *bucket gets b.
 template <int DT>
-__device__ __forceinline__ uint32_t ext_of(typename KT<DT>::U u, const RootEval& r,
-                                           const LeafEval* __restrict__ leaves,
-                                           const BucketHead* __restrict__ heads,
-                                           const HeavyEntry* __restrict__ heavy, uint32_t f0) {
-  const uint32_t b = bucket_of<DT>(u, r, leaves, f0);
+__device__ __forceinline__ uint32_t ext_of2(typename KT<DT>::U u, const RootEval& r,
+                                            const LeafL0* __restrict__ lc,
+                                            const BucketHead* __restrict__ heads,
+                                            const uint64_t* __restrict__ htk, uint32_t f0,
+                                            uint32_t* bucket, uint32_t* nheavy = nullptr) {
+  const uint32_t b = bucket_of<DT>(u, r, lc, f0);
+  *bucket = b;
   const BucketHead h = heads[b];
   uint32_t e = h.ext_base;
   const uint32_t nh = h.hoff_nh & 15u;
+  if (nheavy) *nheavy = nh;
   if (nh) {
     const uint64_t t = KT<DT>::tk(u);
     const uint32_t ho = h.hoff_nh >> 4;
     for (uint32_t j = 0; j < nh; ++j) {
-      const uint64_t hv = heavy[ho + j].tk;
+      const uint64_t hv = htk[ho + j];
       if (hv < t) e += 2;
       else { e += (hv == t) ? 1u : 0u; break; }
     }
   }
   return e;
+}
+
+template <int DT>
+__device__ __forceinline__ uint32_t ext_of(typename KT<DT>::U u, const RootEval& r,
+                                           const LeafL0* __restrict__ lc,
+                                           const BucketHead* __restrict__ heads,
+                                           const uint64_t* __restrict__ htk, uint32_t f0) {
+  uint32_t b;
+  return ext_of2<DT>(u, r, lc, heads, htk, f0, &b);
 }
 
 // ------------------------------------------------------------------ jobs
@@ -229,7 +272,20 @@ struct Job {
   uint64_t value;      // FILL: the key bits to write
   uint32_t src;
   uint32_t kind;
+  uint32_t la, lb;     // SORT: leaves whose [lo, hi] meets [Flo, Fhi]
 };
+
+// Leaves whose output range meets [Flo, Fhi): la = last leaf with lo <= Flo,
+// lb = last leaf with lo < Fhi (FP64 lo values of the fitted model).
+__device__ __forceinline__ void leaf_range(const double* leaf64, int L, double Flo, double Fhi,
+                                           uint32_t* la, uint32_t* lb) {
+  int a = 0, b = L - 1;
+  while (a < b) { const int mid = (a + b + 1) >> 1; if (leaf64[5 * mid + 3] <= Flo) a = mid; else b = mid - 1; }
+  int c = a, d = L - 1;
+  while (c < d) { const int mid = (c + d + 1) >> 1; if (leaf64[5 * mid + 3] < Fhi) c = mid; else d = mid - 1; }
+  *la = (uint32_t)a;
+  *lb = (uint32_t)c;
+}
 
 // Job list: count + capacity-bounded array.
 struct JobList {
@@ -310,10 +366,12 @@ struct DevModel {
 struct ModelPtrs {         // device pointers of one model
   DevModel* hdr;
   double* leaf64;          // 5 * L
-  LeafEval* leaf;          // L
+  LeafL0* leafc;           // L (integer level-0 records)
+  LeafFine* leaff;         // L + 1 (sentinel record L: LO = 1)
   BucketHead* heads;       // f0 + 1
   HeavyEntry* heavy;       // max heavy
   uint32_t* leaf_beg;      // L (sample index ranges per leaf)
+  int L;                   // leaves
   uint32_t* leaf_end;      // L
 };
 

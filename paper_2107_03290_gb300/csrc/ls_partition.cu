@@ -25,22 +25,30 @@
 namespace ls {
 
 struct L0Layout {
-  uint32_t bar, buf, leaves, heads, cnt, cursor, eqbits, ids, ws, total;
+  uint32_t bar, buf, leaves, heads, htk, cnt, bcnt, boff, ecnt, cursor, sdst, ws, total;
 };
 
-static L0Layout l0_layout(int W, uint32_t L, uint32_t f0, uint32_t next, bool scatter) {
+// Shared-memory layout of the level-0 kernels.  hmax: heavy values; the
+// scatter keeps counters and cursors for the f0 + hmax non-equality slots.
+static L0Layout l0_layout(int W, uint32_t L, uint32_t f0, uint32_t next, uint32_t hmax,
+                          bool scatter) {
   L0Layout y{};
   size_t o = 0;
   auto al = [&](size_t a) { o = (o + a - 1) / a * a; };
   y.bar = (uint32_t)o; o += 16;
   al(128); y.buf = (uint32_t)o; o += 2ull * P_TILE * W;
-  al(16); y.leaves = (uint32_t)o; o += (size_t)L * sizeof(LeafEval);
+  al(16); y.leaves = (uint32_t)o; o += (size_t)L * sizeof(LeafL0);
   y.heads = (uint32_t)o; o += (size_t)(f0 + 1) * sizeof(BucketHead);
-  y.cnt = (uint32_t)o; o += (size_t)(next + 1) * 4;
-  if (scatter) {
-    al(8); y.cursor = (uint32_t)o; o += (size_t)next * 8;
-    y.eqbits = (uint32_t)o; o += (size_t)((next + 31) / 32) * 4;
-    y.ids = (uint32_t)o; o += (size_t)P_TILE * 2;
+  y.htk = (uint32_t)o; o += (size_t)hmax * 8;
+  if (!scatter) {
+    y.cnt = (uint32_t)o; o += (size_t)(next + 1) * 4;
+  } else {
+    const size_t nc = (size_t)f0 + hmax;
+    y.bcnt = (uint32_t)o; o += (size_t)f0 * 4;
+    y.boff = (uint32_t)o; o += (size_t)(f0 + 1) * 4;
+    y.ecnt = (uint32_t)o; o += nc * 4;
+    al(8); y.cursor = (uint32_t)o; o += nc * 8;
+    y.sdst = (uint32_t)o; o += (size_t)P_TILE * 4;
   }
   al(8); y.ws = (uint32_t)o; o += 33 * 8;
   y.total = (uint32_t)o;
@@ -50,10 +58,10 @@ static L0Layout l0_layout(int W, uint32_t L, uint32_t f0, uint32_t next, bool sc
 static int key_width(int dt) { return (dt == LS_F64 || dt == LS_U64) ? 8 : 4; }
 
 size_t level0_smem_hist(int dt, uint32_t L, uint32_t f0, uint32_t n_ext_max) {
-  return l0_layout(key_width(dt), L, f0, n_ext_max, false).total;
+  return l0_layout(key_width(dt), L, f0, n_ext_max, (n_ext_max - f0) / 2, false).total;
 }
 size_t level0_smem_scatter(int dt, uint32_t L, uint32_t f0, uint32_t n_ext_max) {
-  return l0_layout(key_width(dt), L, f0, n_ext_max, true).total;
+  return l0_layout(key_width(dt), L, f0, n_ext_max, (n_ext_max - f0) / 2, true).total;
 }
 
 __device__ __forceinline__ void chunk_of(const Chunking& c, uint32_t g, uint64_t* b, uint64_t* e) {
@@ -66,25 +74,28 @@ __device__ __forceinline__ void chunk_of(const Chunking& c, uint32_t g, uint64_t
 }
 
 template <int DT>
-__device__ __forceinline__ void load_tables(const Level0Args& a, LeafEval* leaves, BucketHead* heads) {
-  for (uint32_t i = threadIdx.x; i < a.L; i += blockDim.x) leaves[i] = a.M.leaf[i];
+__device__ __forceinline__ void load_tables(const Level0Args& a, LeafL0* leaves, BucketHead* heads,
+                                            uint64_t* htk, uint32_t H) {
+  for (uint32_t i = threadIdx.x; i < a.L; i += blockDim.x) leaves[i] = a.M.leafc[i];
   for (uint32_t i = threadIdx.x; i <= a.f0; i += blockDim.x) heads[i] = a.M.heads[i];
+  for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) htk[i] = a.M.heavy[i].tk;
 }
 
 // ---------------------------------------------------------------- K2
 template <int DT>
-__global__ void __launch_bounds__(P_THREADS, 1) k_l0_hist(Level0Args a, L0Layout lay) {
+__global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout lay) {
   typedef typename KT<DT>::U U;
   extern __shared__ __align__(128) unsigned char sm[];
   uint64_t* bar = (uint64_t*)(sm + lay.bar);
   U* buf = (U*)(sm + lay.buf);
-  LeafEval* leaves = (LeafEval*)(sm + lay.leaves);
+  LeafL0* leaves = (LeafL0*)(sm + lay.leaves);
   BucketHead* heads = (BucketHead*)(sm + lay.heads);
   uint32_t* cnt = (uint32_t*)(sm + lay.cnt);
   const U* keys = (const U*)a.keys;
   const RootEval r = a.M.hdr->root;
   const uint32_t next = min(a.M.hdr->n_ext, a.n_ext_max);
-  const HeavyEntry* __restrict__ heavy = a.M.heavy;
+  uint64_t* heavy = (uint64_t*)(sm + lay.htk);
+  const uint32_t H = min(a.M.hdr->nheavy, (next - a.f0) / 2);
   const uint32_t g = blockIdx.x;
   uint64_t cb, ce;
   chunk_of(a.c, g, &cb, &ce);
@@ -92,38 +103,57 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
   if (threadIdx.x == 0) ts.init();
   __syncthreads();
   if (threadIdx.x == 0) { ts.issue(0); ts.issue(1); }
-  load_tables<DT>(a, leaves, heads);
-  for (uint32_t i = threadIdx.x; i < next; i += P_THREADS) cnt[i] = 0;
+  load_tables<DT>(a, leaves, heads, heavy, H);
+  for (uint32_t i = threadIdx.x; i < next; i += H_THREADS) cnt[i] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   if (g == 0) {  // unaligned head and tail
     const uint64_t nht = a.c.a0 + (a.c.n - a.c.a1);
-    for (uint64_t k = threadIdx.x; k < nht; k += P_THREADS) {
+    for (uint64_t k = threadIdx.x; k < nht; k += H_THREADS) {
       const uint64_t i = k < a.c.a0 ? k : a.c.a1 + (k - a.c.a0);
       const uint32_t e = ext_of<DT>(keys[i], r, leaves, heads, heavy, a.f0);
       if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
     }
   }
+  constexpr int KPT = P_TILE / H_THREADS;
   for (uint32_t t = 0; t < ts.nt; ++t) {
     const U* tb = ts.wait(t, a.err);
     const uint32_t c = ts.count(t);
-    for (uint32_t base = 0; base < c; base += P_THREADS) {
-      const uint32_t i = base + threadIdx.x;
-      const bool valid = i < c;
-      uint32_t e = valid ? ext_of<DT>(tb[i], r, leaves, heads, heavy, a.f0) : 0xFFFFFFFFu;
-      if (valid && e >= next) { set_error(a.err, ERR_BOUNDS); e = 0xFFFFFFFEu; }
-      const unsigned peers = __match_any_sync(0xffffffffu, e);
-      if (e < next && lane == __ffs(peers) - 1) atomicAdd(&cnt[e], (uint32_t)__popc(peers));
+    uint32_t e[KPT];
+    if (c == (uint32_t)P_TILE) {  // full tile: no bounds tests, predictions interleave
+      U u[KPT];
+#pragma unroll
+      for (int k = 0; k < KPT; ++k) u[k] = tb[k * H_THREADS + threadIdx.x];
+#pragma unroll
+      for (int k = 0; k < KPT; ++k) e[k] = ext_of<DT>(u[k], r, leaves, heads, heavy, a.f0);
+    } else {
+#pragma unroll
+      for (int k = 0; k < KPT; ++k) {
+        const uint32_t i = k * H_THREADS + threadIdx.x;
+        e[k] = i < c ? ext_of<DT>(tb[i], r, leaves, heads, heavy, a.f0) : 0xFFFFFFFFu;
+      }
     }
+#pragma unroll
+    for (int k = 0; k < KPT; ++k)
+      if (e[k] != 0xFFFFFFFFu && e[k] >= next) { set_error(a.err, ERR_BOUNDS); e[k] = 0xFFFFFFFEu; }
+#pragma unroll
+    for (int k = 0; k < KPT; ++k)  // shared-memory counts
+      if (e[k] < next) atomicAdd(&cnt[e[k]], 1u);
     __syncthreads();
     if (threadIdx.x == 0) ts.issue(t + 2);
   }
   __syncthreads();
-  for (uint32_t e = threadIdx.x; e < a.n_ext_max; e += P_THREADS)
+  for (uint32_t e = threadIdx.x; e < a.n_ext_max; e += H_THREADS)
     a.hist[(size_t)e * a.c.G + g] = e < next ? cnt[e] : 0u;
 }
 
 // ---------------------------------------------------------------- K4
+// Per tile: each key's slot (equality keys are skipped: filled later), its rank
+// inside the slot and inside its level-0 bucket (shared atomics); an exclusive
+// scan over the f0 bucket counts gives the staging offsets; keys are staged
+// bucket-contiguously together with their final address, then written out so
+// that consecutive threads write consecutive addresses of a run.  The last key
+// of a slot advances that slot's cursor.  Per-tile work is O(tile + f0).
 template <int DT>
 __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Layout lay) {
   typedef typename KT<DT>::U U;
@@ -131,19 +161,23 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
   extern __shared__ __align__(128) unsigned char sm[];
   uint64_t* bar = (uint64_t*)(sm + lay.bar);
   U* buf = (U*)(sm + lay.buf);
-  LeafEval* leaves = (LeafEval*)(sm + lay.leaves);
+  LeafL0* leaves = (LeafL0*)(sm + lay.leaves);
   BucketHead* heads = (BucketHead*)(sm + lay.heads);
-  uint32_t* cnt = (uint32_t*)(sm + lay.cnt);
+  uint64_t* heavy = (uint64_t*)(sm + lay.htk);
+  uint32_t* bcnt = (uint32_t*)(sm + lay.bcnt);
+  uint32_t* boff = (uint32_t*)(sm + lay.boff);
+  uint32_t* ecnt = (uint32_t*)(sm + lay.ecnt);
   uint64_t* cursor = (uint64_t*)(sm + lay.cursor);
-  uint32_t* eqbits = (uint32_t*)(sm + lay.eqbits);
-  uint16_t* ids = (uint16_t*)(sm + lay.ids);
+  uint32_t* sinfo = (uint32_t*)(sm + lay.sdst);  // staged slot | rank << 16
   uint32_t* ws = (uint32_t*)(sm + lay.ws);
   const U* keys = (const U*)a.keys;
   U* out = (U*)a.scratch;
   const uint64_t n = a.c.n;
   const RootEval r = a.M.hdr->root;
   const uint32_t next = min(a.M.hdr->n_ext, a.n_ext_max);
-  const HeavyEntry* __restrict__ heavy = a.M.heavy;
+  const uint32_t f0 = a.f0;
+  const uint32_t H = min(a.M.hdr->nheavy, (next - f0) / 2);
+  const uint32_t nc = f0 + H;  // non-equality slots
   const uint32_t g = blockIdx.x, G = a.c.G;
   uint64_t cb, ce;
   chunk_of(a.c, g, &cb, &ce);
@@ -151,81 +185,97 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
   if (threadIdx.x == 0) ts.init();
   __syncthreads();
   if (threadIdx.x == 0) { ts.issue(0); ts.issue(1); }
-  load_tables<DT>(a, leaves, heads);
-  for (uint32_t e = threadIdx.x; e <= next; e += P_THREADS) cnt[e] = 0;
-  for (uint32_t e = threadIdx.x; e < next; e += P_THREADS) cursor[e] = a.offs[(size_t)e * G + g];
-  for (uint32_t w = threadIdx.x; w < (next + 31) / 32; w += P_THREADS) eqbits[w] = 0;
+  load_tables<DT>(a, leaves, heads, heavy, H);
+  for (uint32_t i = threadIdx.x; i < f0; i += P_THREADS) bcnt[i] = 0;
+  for (uint32_t i = threadIdx.x; i < nc; i += P_THREADS) ecnt[i] = 0;
   __syncthreads();
-  for (uint32_t b = threadIdx.x; b < a.f0; b += P_THREADS) {
+  for (uint32_t b = threadIdx.x; b < f0; b += P_THREADS) {  // cursors of non-equality slots
     const BucketHead h = heads[b];
-    const uint32_t nh = h.hoff_nh & 15u;
-    for (uint32_t j = 0; j < nh; ++j) {
-      const uint32_t e = h.ext_base + 2 * j + 1;
-      if (e < next) atomicOr(&eqbits[e >> 5], 1u << (e & 31));
+    const uint32_t nh = h.hoff_nh & 15u, hoff = h.hoff_nh >> 4;
+    for (uint32_t j = 0; j <= nh; ++j) {
+      const uint32_t c = b + hoff + j, e = h.ext_base + 2 * j;
+      if (c < nc && e < next) cursor[c] = a.offs[(size_t)e * G + g];
     }
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = lanemask_lt();
   if (g == 0 && threadIdx.x == 0) {  // unaligned head and tail, one thread
     const uint64_t nht = a.c.a0 + (n - a.c.a1);
     for (uint64_t k = 0; k < nht; ++k) {
       const uint64_t i = k < a.c.a0 ? k : a.c.a1 + (k - a.c.a0);
       const U u = keys[i];
-      const uint32_t e = ext_of<DT>(u, r, leaves, heads, heavy, a.f0);
+      uint32_t b;
+      const uint32_t e = ext_of2<DT>(u, r, leaves, heads, heavy, f0, &b);
       if (e >= next) { set_error(a.err, ERR_BOUNDS); continue; }
-      if ((eqbits[e >> 5] >> (e & 31)) & 1u) continue;
-      const uint64_t dst = cursor[e]++;
+      if ((e - b) & 1u) continue;  // equality slot: filled later
+      const uint32_t c = (e + b) >> 1;
+      const uint64_t dst = cursor[c]++;
       if (dst < n) out[dst] = u; else set_error(a.err, ERR_BOUNDS);
     }
   }
   __syncthreads();
   for (uint32_t t = 0; t < ts.nt; ++t) {
     U* tb = ts.wait(t, a.err);
-    const uint32_t c = ts.count(t);
+    const uint32_t cnt_t = ts.count(t);
     U u[KPT];
-    uint32_t e[KPT], rk[KPT];
+    uint32_t e[KPT], bk[KPT], nh[KPT];
+    if (cnt_t == (uint32_t)P_TILE) {  // full tile: branch-free, predictions interleave
 #pragma unroll
-    for (int k = 0; k < KPT; ++k) {
-      const uint32_t i = k * P_THREADS + threadIdx.x;
-      const bool valid = i < c;
-      u[k] = valid ? tb[i] : (U)0;
-      uint32_t ee = valid ? ext_of<DT>(u[k], r, leaves, heads, heavy, a.f0) : 0xFFFFFFFFu;
-      if (valid && ee >= next) { set_error(a.err, ERR_BOUNDS); ee = 0xFFFFFFFEu; }
-      e[k] = ee;
-      const unsigned peers = __match_any_sync(0xffffffffu, ee);
-      const int leader = __ffs(peers) - 1;
-      uint32_t old = 0;
-      if (ee < next && lane == leader) old = atomicAdd(&cnt[ee], (uint32_t)__popc(peers));
-      old = __shfl_sync(0xffffffffu, old, leader);
-      rk[k] = old + __popc(peers & lt);
-    }
-    __syncthreads();
-    // slot offsets inside the tile
-    block_scan_array<uint32_t>(cnt, (int)next, ws);
-    if (threadIdx.x == 0) cnt[next] = c;
-    __syncthreads();
-    // stage slot-contiguously (the input buffer is free now)
+      for (int k = 0; k < KPT; ++k) u[k] = tb[k * P_THREADS + threadIdx.x];
 #pragma unroll
-    for (int k = 0; k < KPT; ++k) {
-      if (e[k] < next) {
-        const uint32_t p = cnt[e[k]] + rk[k];
-        if (p < (uint32_t)P_TILE) { tb[p] = u[k]; ids[p] = (uint16_t)e[k]; }
+      for (int k = 0; k < KPT; ++k)
+        e[k] = ext_of2<DT>(u[k], r, leaves, heads, heavy, f0, &bk[k], &nh[k]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < KPT; ++k) {
+        const uint32_t i = k * P_THREADS + threadIdx.x;
+        u[k] = i < cnt_t ? tb[i] : (U)0;
+        nh[k] = 0;
+        e[k] = i < cnt_t ? ext_of2<DT>(u[k], r, leaves, heads, heavy, f0, &bk[k], &nh[k])
+                         : 0xFFFFFFFFu;
       }
     }
+    uint32_t cc[KPT], rk[KPT], sr[KPT];
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      uint32_t ee = e[k];
+      if (ee != 0xFFFFFFFFu && ee >= next) { set_error(a.err, ERR_BOUNDS); ee = 0xFFFFFFFFu; }
+      const bool live = ee != 0xFFFFFFFFu && ((ee - bk[k]) & 1u) == 0;
+      cc[k] = live ? (ee + bk[k]) >> 1 : 0xFFFFFFFFu;
+      if (live && cc[k] >= nc) { set_error(a.err, ERR_BOUNDS); cc[k] = 0xFFFFFFFFu; }
+      sr[k] = cc[k] != 0xFFFFFFFFu ? atomicAdd(&bcnt[bk[k]], 1u) : 0u;
+      // a bucket without heavy values has one slot: its rank is the bucket rank
+      rk[k] = (cc[k] != 0xFFFFFFFFu && nh[k]) ? atomicAdd(&ecnt[cc[k]], 1u) : sr[k];
+    }
     __syncthreads();
-    // write runs: consecutive p of one slot go to consecutive addresses
-    const uint32_t staged = cnt[next];
+    for (uint32_t i = threadIdx.x; i < f0; i += P_THREADS) boff[i] = bcnt[i];
+    __syncthreads();
+    const uint32_t staged = block_scan_array<uint32_t>(boff, (int)f0, ws);
+    // stage bucket-contiguously with the final address
+    uint32_t last = 0;
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      if (cc[k] == 0xFFFFFFFFu) continue;
+      const uint32_t p = boff[bk[k]] + sr[k];
+      if (p < (uint32_t)P_TILE) {
+        tb[p] = u[k];
+        sinfo[p] = cc[k] | (rk[k] << 16);
+      }
+      const uint32_t slot_n = nh[k] ? ecnt[cc[k]] : bcnt[bk[k]];
+      if (rk[k] + 1 == slot_n) last |= 1u << k;
+      if (sr[k] + 1 == bcnt[bk[k]]) last |= 1u << (16 + k);
+    }
+    __syncthreads();
     for (uint32_t p = threadIdx.x; p < staged; p += P_THREADS) {
-      const uint32_t ee = ids[p];
-      if ((eqbits[ee >> 5] >> (ee & 31)) & 1u) continue;
-      const uint64_t dst = cursor[ee] + (p - cnt[ee]);
+      const uint32_t inf = sinfo[p];
+      const uint64_t dst = cursor[inf & 0xFFFFu] + (inf >> 16);
       if (dst < n) out[dst] = tb[p]; else set_error(a.err, ERR_BOUNDS);
     }
     __syncthreads();
-    for (uint32_t ee = threadIdx.x; ee < next; ee += P_THREADS) cursor[ee] += cnt[ee + 1] - cnt[ee];
-    __syncthreads();
-    for (uint32_t ee = threadIdx.x; ee <= next; ee += P_THREADS) cnt[ee] = 0;
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {  // the last key of a slot / bucket advances / resets it
+      if ((last >> k) & 1u) { cursor[cc[k]] += rk[k] + 1; ecnt[cc[k]] = 0; }
+      if ((last >> (16 + k)) & 1u) bcnt[bk[k]] = 0;
+    }
     __syncthreads();
     if (threadIdx.x == 0) ts.issue(t + 2);
   }
@@ -266,6 +316,8 @@ __global__ void k_classify0(Level0Args a, Lists lists, SortLimits lim) {
     const uint32_t j = o / 2;
     job.Flo = (j == 0) ? (double)b / (double)a.f0 : (double)heavy[hoff + j - 1].F;
     job.Fhi = (j == nh) ? (double)(b + 1) / (double)a.f0 : (double)heavy[hoff + j].F;
+    job.la = job.lb = 0;
+    if (size <= lim.c_large) leaf_range(a.M.leaf64, (int)a.L, job.Flo, job.Fhi, &job.la, &job.lb);
     if (size <= lim.c_small) { job.kind = JOB_SORT; push_job(lists.sort_s, job, a.err); }
     else if (size <= lim.c_large) { job.kind = JOB_SORT; push_job(lists.sort_l, job, a.err); }
     else { job.kind = JOB_REFINE; push_job(lists.refine, job, a.err); }
@@ -273,15 +325,25 @@ __global__ void k_classify0(Level0Args a, Lists lists, SortLimits lim) {
 }
 
 // ---------------------------------------------------------------- equality fill
+// Large jobs are written by the whole grid, small ones by one CTA each (round
+// robin), so thousands of small equality slots still fill in parallel.
 template <typename U>
 __global__ void k_fill(U* __restrict__ keys, JobList fill) {
+  constexpr uint64_t BIG = 1u << 15;
   const unsigned long long nj = min(*fill.count, fill.cap);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  unsigned long long small_idx = 0;
   for (unsigned long long j = 0; j < nj; ++j) {
     const Job job = fill.jobs[j];
     const U v = (U)job.value;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < job.m; i += stride)
-      keys[job.start + i] = v;
+    U* dst = keys + job.start;
+    if (job.m >= BIG) {
+      for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < job.m; i += stride)
+        dst[i] = v;
+    } else {
+      if (small_idx++ % gridDim.x != blockIdx.x) continue;
+      for (uint64_t i = threadIdx.x; i < job.m; i += blockDim.x) dst[i] = v;
+    }
   }
 }
 
@@ -372,9 +434,9 @@ __device__ __forceinline__ uint64_t aux_find_c(const L1Aux* aux, uint64_t nj, ui
 
 template <int DT>
 __device__ __forceinline__ uint32_t l1_sub(typename KT<DT>::U u, const RootEval& r,
-                                           const LeafEval* leaves, const L1Aux& x) {
+                                           const LeafFine* lf, const L1Aux& x) {
   if (KT<DT>::is_nan(u)) return KT<DT>::neg(u) ? 0u : x.f1 - 1;
-  const float F = predict_F<DT>(u, r, leaves);
+  const float F = predict_F<DT>(u, r, lf);
   const float v = __fmaf_rn(F, x.S, x.T);
   if (!(v > 0.0f)) return 0u;
   if (v >= (float)(x.f1 - 1)) return x.f1 - 1;
@@ -391,7 +453,7 @@ k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Mod
   const L1Aux* aux = (const L1Aux*)w.aux;
   const uint64_t T = w.totals[0], nj = w.totals[2];
   const RootEval r = M.hdr->root;
-  const LeafEval* leaves = M.leaf;
+  const LeafFine* lf = M.leaff;
   const int lane = threadIdx.x & 31;
   for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
     const uint64_t j = aux_find_tile(aux, nj, t);
@@ -412,10 +474,9 @@ k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Mod
         const uint64_t tk = KT<DT>::tk(u);
         mn = min(mn, (unsigned long long)tk);
         mx = max(mx, (unsigned long long)tk);
-        sub = l1_sub<DT>(u, r, leaves, x);
+        sub = l1_sub<DT>(u, r, lf, x);
       }
-      const unsigned peers = __match_any_sync(0xffffffffu, sub);
-      if (sub != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&hc[sub], (uint32_t)__popc(peers));
+      if (sub != 0xFFFFFFFFu) atomicAdd(&hc[sub], 1u);
     }
     for (int o = 16; o > 0; o >>= 1) {
       mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
@@ -455,7 +516,7 @@ k_l1_scatter(typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, uint64
   const L1Aux* aux = (const L1Aux*)w.aux;
   const uint64_t T = w.totals[0], nj = w.totals[2];
   const RootEval r = M.hdr->root;
-  const LeafEval* leaves = M.leaf;
+  const LeafFine* mlf = M.leaff;
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
   for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
@@ -475,14 +536,9 @@ k_l1_scatter(typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, uint64
       const uint32_t i = k * L1_THREADS + threadIdx.x;
       uint32_t sub = 0xFFFFFFFFu;
       u[k] = 0;
-      if (i < c) { u[k] = src[i]; sub = l1_sub<DT>(u[k], r, leaves, x); }
+      if (i < c) { u[k] = src[i]; sub = l1_sub<DT>(u[k], r, mlf, x); }
       sb[k] = sub;
-      const unsigned peers = __match_any_sync(0xffffffffu, sub);
-      const int leader = __ffs(peers) - 1;
-      uint32_t old = 0;
-      if (sub != 0xFFFFFFFFu && lane == leader) old = atomicAdd(&lc[sub], (uint32_t)__popc(peers));
-      old = __shfl_sync(0xffffffffu, old, leader);
-      rk[k] = old + __popc(peers & lt);
+      rk[k] = sub != 0xFFFFFFFFu ? atomicAdd(&lc[sub], 1u) : 0u;
     }
     __syncthreads();
     block_scan_array<uint32_t>(lc, (int)x.f1, ws);
@@ -510,7 +566,8 @@ k_l1_scatter(typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, uint64
 }
 
 template <int DT>
-__global__ void k_l1_classify(Lists lists, SortLimits lim, Level1Ws w, uint32_t* err) {
+__global__ void k_l1_classify(Lists lists, SortLimits lim, Level1Ws w, ModelPtrs M, int L,
+                              uint32_t* err) {
   const L1Aux* aux = (const L1Aux*)w.aux;
   const uint64_t C = w.totals[1], nj = w.totals[2];
   for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < C;
@@ -536,6 +593,8 @@ __global__ void k_l1_classify(Lists lists, SortLimits lim, Level1Ws w, uint32_t*
     job.Flo = pj.Flo + (double)sub * wd;
     job.Fhi = pj.Flo + (double)(sub + 1) * wd;
     job.src = 0;
+    job.la = job.lb = 0;
+    if (cntc <= lim.c_large) leaf_range(M.leaf64, L, job.Flo, job.Fhi, &job.la, &job.lb);
     if (cntc <= lim.c_small) { job.kind = JOB_SORT; push_job(lists.sort_s, job, err); }
     else if (cntc <= lim.c_large) { job.kind = JOB_SORT; push_job(lists.sort_l, job, err); }
     else { job.kind = JOB_FALLBACK; push_job(lists.fallback, job, err); }
@@ -547,9 +606,10 @@ template <int DT>
 static cudaError_t level0_dt(const Level0Args& a, size_t sh, size_t ss, const Lists& lists,
                              const SortLimits& lim, cudaStream_t st, const Marks* mk, int mb) {
   const int W = KT<DT>::W;
-  const L0Layout lh = l0_layout(W, a.L, a.f0, a.n_ext_max, false);
-  const L0Layout ls_ = l0_layout(W, a.L, a.f0, a.n_ext_max, true);
-  k_l0_hist<DT><<<a.c.G, P_THREADS, sh, st>>>(a, lh);
+  const uint32_t hmax = (a.n_ext_max - a.f0) / 2;
+  const L0Layout lh = l0_layout(W, a.L, a.f0, a.n_ext_max, hmax, false);
+  const L0Layout ls_ = l0_layout(W, a.L, a.f0, a.n_ext_max, hmax, true);
+  k_l0_hist<DT><<<a.c.G, H_THREADS, sh, st>>>(a, lh);
   mark(mk, mb + 0, st);
   const uint64_t M = (uint64_t)a.n_ext_max * a.c.G;
   k_scan<uint32_t><<<a.scan_tiles, SC_THREADS, 0, st>>>(
@@ -615,7 +675,7 @@ static cudaError_t level1_dt(const void* keys, const void* scratch, uint64_t n, 
   k_l1_cursor<<<grid, 256, 0, st>>>(lists, w);
   k_l1_scatter<DT><<<grid, L1_THREADS, l1_scatter_smem(KT<DT>::W), st>>>((U*)keys, (const U*)scratch,
                                                                       n, M, lists, w, err);
-  k_l1_classify<DT><<<grid, 256, 0, st>>>(lists, lim, w, err);
+  k_l1_classify<DT><<<grid, 256, 0, st>>>(lists, lim, w, M, M.L, err);
   add_launches(6);
   return cudaGetLastError();
 }

@@ -39,8 +39,14 @@ __device__ __forceinline__ void rs_rank_tile(RsShared& sh, const uint64_t* key, 
   const unsigned lt = lanemask_lt();
 #pragma unroll
   for (int r = 0; r < RS_ROUNDS; ++r) {
-    const uint32_t d = valid[r] ? digit_of(key[r]) : 0x1000u;
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t d = valid[r] ? digit_of(key[r]) : 0x100u;
+    // lanes holding the same 9-bit value (8-bit digit + invalid flag), by ballots
+    unsigned peers = 0xffffffffu;
+#pragma unroll
+    for (int bit = 0; bit < 9; ++bit) {
+      const unsigned bal = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+      peers &= ((d >> bit) & 1u) ? bal : ~bal;
+    }
     const int leader = __ffs(peers) - 1;
     const uint32_t basec = valid[r] ? sh.whist[w][d] : 0u;
     __syncwarp();

@@ -55,16 +55,16 @@ __global__ void k_train_init(DevModel* hdr, uint64_t s, uint32_t* leaf_beg, uint
   }
 }
 
-// Finite keys are contiguous in total order: [s_lo, s_hi).
+// Finite keys are contiguous in total order: [s_lo, s_hi).  In the sorted
+// sample the two ends are where finiteness changes, so each is written once.
 template <int DT>
 __global__ void k_finite_range(const uint64_t* __restrict__ tk, uint64_t s, DevModel* hdr,
                                unsigned long long* hi_out) {
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < s;
        k += (uint64_t)gridDim.x * blockDim.x) {
-    if (KT<DT>::finite(KT<DT>::from_tk(tk[k]))) {
-      atomicMin((unsigned long long*)&hdr->s_lo, (unsigned long long)k);
-      atomicMax(hi_out, (unsigned long long)(k + 1));
-    }
+    if (!KT<DT>::finite(KT<DT>::from_tk(tk[k]))) continue;
+    if (k == 0 || !KT<DT>::finite(KT<DT>::from_tk(tk[k - 1]))) hdr->s_lo = k;
+    if (k + 1 == s || !KT<DT>::finite(KT<DT>::from_tk(tk[k + 1]))) *hi_out = k + 1;
   }
 }
 
@@ -179,50 +179,93 @@ __global__ void k_fit_route(const uint64_t* __restrict__ tk, const DevModel* hdr
   }
 }
 
-// One block per leaf: least squares on the leaf's points (two passes).
+// Per-leaf least squares in deterministic work units.  Leaf l's points
+// [beg, end) are cut into units of FIT_UNIT points; each unit sums, shifted by
+// the leaf's first point (x_r, y_r), dx, dy, dx*dx, dx*dy; the leaf then adds
+// its units in order.  Shifting by a point of the leaf keeps the one-pass
+// formulas Sxx = sum dx^2 - (sum dx)^2 / n stable.
+constexpr int FIT_UNIT = 2048;
+
+__global__ void __launch_bounds__(1024)
+k_fit_units_plan(const uint32_t* leaf_beg, const uint32_t* leaf_end, int L, uint32_t* ubase,
+                 uint32_t* utotal) {
+  __shared__ uint32_t ws[33];
+  __shared__ uint32_t s_run;
+  if (threadIdx.x == 0) s_run = 0;
+  __syncthreads();
+  for (int l0 = 0; l0 < L; l0 += blockDim.x) {
+    const int l = l0 + threadIdx.x;
+    uint32_t u = 0;
+    if (l < L && leaf_end[l] > leaf_beg[l]) u = (leaf_end[l] - leaf_beg[l] + FIT_UNIT - 1) / FIT_UNIT;
+    uint32_t tot;
+    const uint32_t ex = block_excl_sum<uint32_t>(u, ws, &tot);
+    if (l < L) ubase[l] = s_run + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) s_run += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { ubase[L] = s_run; *utotal = s_run; }
+}
+
 template <int DT>
 __global__ void __launch_bounds__(FIT_THREADS)
-k_fit_leaf(const uint64_t* __restrict__ tk, const uint32_t* __restrict__ rank, const DevModel* hdr,
-           const uint32_t* leaf_beg, const uint32_t* leaf_end, double* leaf) {
+k_fit_unit_sums(const uint64_t* __restrict__ tk, const uint32_t* __restrict__ rank,
+                const DevModel* hdr, const uint32_t* leaf_beg, const uint32_t* leaf_end,
+                const uint32_t* ubase, int L, const uint32_t* utotal, double* unit) {
   __shared__ double ws[33];
-  __shared__ double s_mx, s_my;
-  const int l = blockIdx.x;
-  const uint64_t b = leaf_beg[l], e = leaf_end[l];
-  double* q = leaf + 5 * (size_t)l;
-  if (e <= b) {
-    if (threadIdx.x == 0) { q[0] = 0; q[1] = 0; q[2] = -1; q[3] = -1; q[4] = 0; }
-    return;
+  const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
+  const double inv_m = m ? 1.0 / (double)m : 0.0;
+  const uint32_t U = *utotal;
+  for (uint32_t u = blockIdx.x; u < U; u += gridDim.x) {
+    int a = 0, b = L - 1;  // leaf: last l with ubase[l] <= u and a unit of its own
+    while (a < b) { const int mid = (a + b + 1) >> 1; if (ubase[mid] <= u) a = mid; else b = mid - 1; }
+    const int l = a;
+    const uint64_t first = leaf_beg[l];
+    const uint64_t kb = first + (uint64_t)(u - ubase[l]) * FIT_UNIT;
+    const uint64_t ke = min((uint64_t)leaf_end[l], kb + FIT_UNIT);
+    const double xr = sample_x<DT>(tk, lo, first), yr = (double)rank[first] * inv_m;
+    double s[4] = {0, 0, 0, 0};
+    for (uint64_t k = kb + threadIdx.x; k < ke; k += blockDim.x) {
+      const double dx = sample_x<DT>(tk, lo, k) - xr;
+      const double dy = (double)rank[k] * inv_m - yr;
+      s[0] += dx; s[1] += dy; s[2] += dx * dx; s[3] += dx * dy;
+    }
+    for (int i = 0; i < 4; ++i) {
+      const double t = block_sum_d(s[i], ws);
+      if (threadIdx.x == 0) unit[4 * (size_t)u + i] = t;
+    }
   }
+}
+
+template <int DT>
+__global__ void k_fit_leaf_final(const uint64_t* __restrict__ tk, const uint32_t* __restrict__ rank,
+                                 const DevModel* hdr, const uint32_t* leaf_beg,
+                                 const uint32_t* leaf_end, const uint32_t* ubase,
+                                 const double* unit, int L, double* leaf) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= L) return;
+  double* q = leaf + 5 * (size_t)l;
+  const uint64_t b = leaf_beg[l], e = leaf_end[l];
+  if (e <= b) { q[0] = 0; q[1] = 0; q[2] = -1; q[3] = -1; q[4] = 0; return; }
   const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
   const double inv_m = 1.0 / (double)m;
-  const uint64_t cnt = e - b;
-  double sx = 0, sy = 0;
-  for (uint64_t k = b + threadIdx.x; k < e; k += blockDim.x) {
-    sx += sample_x<DT>(tk, lo, k);
-    sy += (double)rank[k] * inv_m;
+  const double cnt = (double)(e - b);
+  double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  for (uint32_t u = ubase[l]; u < ubase[l + 1]; ++u) {
+    s0 += unit[4 * (size_t)u]; s1 += unit[4 * (size_t)u + 1];
+    s2 += unit[4 * (size_t)u + 2]; s3 += unit[4 * (size_t)u + 3];
   }
-  sx = block_sum_d(sx, ws);
-  sy = block_sum_d(sy, ws);
-  if (threadIdx.x == 0) { s_mx = sx / (double)cnt; s_my = sy / (double)cnt; }
-  __syncthreads();
-  const double mx = s_mx, my = s_my;
-  double sxx = 0, sxy = 0;
-  for (uint64_t k = b + threadIdx.x; k < e; k += blockDim.x) {
-    const double dx = sample_x<DT>(tk, lo, k) - mx;
-    sxx += dx * dx;
-    sxy += dx * ((double)rank[k] * inv_m - my);
-  }
-  sxx = block_sum_d(sxx, ws);
-  sxy = block_sum_d(sxy, ws);
-  if (threadIdx.x == 0) {
-    double a = (cnt >= 2 && sxx > 0) ? sxy / sxx : 0.0;
-    if (!(a >= 0) || !isfinite(a) || !isfinite(mx)) a = 0.0;
-    q[0] = a;
-    q[1] = isfinite(mx) ? mx : 0.0;
-    q[2] = my;
-    q[3] = (double)rank[b] / (double)m;  // lo: eCDF of the leaf's first sample key
-    q[4] = 0;
-  }
+  const double xr = sample_x<DT>(tk, lo, b), yr = (double)rank[b] * inv_m;
+  const double mdx = s0 / cnt, mdy = s1 / cnt;
+  const double sxx = s2 - s0 * mdx, sxy = s3 - s0 * mdy;
+  double a = (e - b >= 2 && sxx > 0) ? sxy / sxx : 0.0;
+  const double mx = xr + mdx;
+  if (!(a >= 0) || !isfinite(a) || !isfinite(mx)) a = 0.0;
+  q[0] = a;
+  q[1] = isfinite(mx) ? mx : 0.0;
+  q[2] = yr + mdy;
+  q[3] = (double)rank[b] / (double)m;  // lo: eCDF of the leaf's first sample key
+  q[4] = 0;
 }
 
 __device__ __forceinline__ int bitlen64(uint64_t v) { return v ? 64 - __clzll((long long)v) : 0; }
@@ -237,13 +280,26 @@ __device__ __forceinline__ uint64_t absdiff(int64_t a, int64_t b) {
   return d < 0 ? (uint64_t)(-d) : (uint64_t)d;
 }
 
-// Empty leaves, hi bounds, and the FP32 evaluation parameters.
+// Fixed-point conversion used by the level-0 tables: floor(v * 2^k) clamped
+// to [lo, hi] (v >= 0 or any sign for the intercepts).
+__device__ __forceinline__ long long floor_scaled(double v, int k, double lo, double hi) {
+  double w = floor(ldexp(v, k));
+  w = w < lo ? lo : w;
+  w = w > hi ? hi : w;
+  return (long long)w;
+}
+
+// Empty leaves, hi bounds, and the evaluation parameters (level-0 integer
+// tables and fine FP32 records).
 template <int DT>
 __global__ void __launch_bounds__(1024)
-k_fit_final(const uint64_t* __restrict__ tk, DevModel* hdr, int L, const uint32_t* leaf_beg,
-            const uint32_t* leaf_end, double* leaf, LeafEval* ev) {
-  __shared__ int s_E;
+k_fit_final(const uint64_t* __restrict__ tk, DevModel* hdr, int L, uint32_t f0,
+            const uint32_t* leaf_beg, const uint32_t* leaf_end, double* leaf, LeafL0* l0,
+            LeafFine* lf) {
+  __shared__ int s_E, s_P0;
+  __shared__ long long s_C0;
   const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
+  const double INT31 = 2147483647.0;
   // next non-empty leaf to the right, by one warp over L/32-leaf ranges
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
@@ -252,7 +308,6 @@ k_fit_final(const uint64_t* __restrict__ tk, DevModel* hdr, int L, const uint32_
     int first = L;
     for (int l = b - 1; l >= a; --l)
       if (leaf[5 * (size_t)l + 3] >= 0) first = l;
-    // suffix minimum over lanes > lane
     int suf = first;
     for (int o = 1; o < 32; o <<= 1) {
       const int v = __shfl_down_sync(0xffffffffu, suf, o);
@@ -273,50 +328,70 @@ k_fit_final(const uint64_t* __restrict__ tk, DevModel* hdr, int L, const uint32_
         const double x0 = sample_x<DT>(tk, lo, 0), x1 = sample_x<DT>(tk, lo, m - 1);
         R = fmax(fabs(x0), fabs(x1));
       }
-      s_E = (R > 0) ? ilogb(R) + 1 - 61 : 0;
+      const int E = (R > 0) ? ilogb(R) + 1 - 61 : 0;
+      const double* r = hdr->root64;
+      const int64_t c0 = fx_f64bits((uint64_t)__double_as_longlong(r[1]), E);
+      uint64_t span = 0;
+      if (m) {
+        span = max(absdiff(fx_f64bits((uint64_t)__double_as_longlong(sample_x<DT>(tk, lo, 0)), E), c0),
+                   absdiff(fx_f64bits((uint64_t)__double_as_longlong(sample_x<DT>(tk, lo, m - 1)), E), c0));
+      }
+      const int P0 = E + max(0, bitlen64(span) - 30);
+      s_E = E;
+      s_P0 = P0;
+      s_C0 = fx_f64bits((uint64_t)__double_as_longlong(r[1]), P0);
+      RootEval re;
+      re.C0 = s_C0;
+      re.P0 = P0;
+      re.E = E;
+      re.L = L;
+      re.RA = (int)floor_scaled(__dmul_rn(r[0], (double)L), P0 + 40, 0.0, INT31);
+      re.RB = floor_scaled(__dmul_rn(r[2], (double)L), 40, -9.0e18, 9.0e18);
+      hdr->root = re;
     }
   }
   __syncthreads();
-  const int E = s_E;
-  if (threadIdx.x == 0) {
-    const double* r = hdr->root64;
-    const int64_t c0 = fx_f64bits((uint64_t)__double_as_longlong(r[1]), E);
-    uint64_t span = 0;
-    if (m) {
-      span = max(absdiff(fx_f64bits((uint64_t)__double_as_longlong(sample_x<DT>(tk, lo, 0)), E), c0),
-                 absdiff(fx_f64bits((uint64_t)__double_as_longlong(sample_x<DT>(tk, lo, m - 1)), E), c0));
+  const int E = s_E, P0 = s_P0;
+  const long long C0 = s_C0;
+  const double f0d = (double)f0;
+  for (int l = threadIdx.x; l <= L; l += blockDim.x) {
+    if (l == L) {  // sentinel: HI of the last leaf
+      LeafFine f;
+      f.C = 0; f.A = 0.0f; f.P = E; f.B = 1.0f; f.LO = 1.0f; f.pad0 = f.pad1 = 0;
+      lf[L] = f;
+      continue;
     }
-    const int sh = max(0, bitlen64(span) - 30);
-    RootEval re;
-    re.cq = c0;
-    re.sh = sh;
-    re.E = E;
-    re.L = L;
-    re.pad = 0;
-    re.A = fp32_sat(ldexp(r[0] * (double)L, E + sh));
-    re.B = __double2float_rn(r[2] * (double)L);
-    hdr->root = re;
-  }
-  for (int l = threadIdx.x; l < L; l += blockDim.x) {
     const double* q = leaf + 5 * (size_t)l;
-    LeafEval e;
-    e.pad = 0;
+    LeafL0 c;
+    LeafFine f;
+    f.pad0 = f.pad1 = 0;
+    const long long BL = floor_scaled(__dmul_rn(q[2], f0d), 32, -9.0e18, 9.0e18);
     const uint32_t b = leaf_beg[l], en = leaf_end[l];
     if (en <= b) {
-      e.cq = 0; e.sh = 0; e.A = 0.0f;
+      c.AL = 0;
+      c.BL = BL;
+      f.C = 0; f.P = E; f.A = 0.0f;
     } else {
-      const int64_t c = fx_f64bits((uint64_t)__double_as_longlong(q[1]), E);
+      const uint64_t cb = (uint64_t)__double_as_longlong(q[1]);
+      const int64_t ce = fx_f64bits(cb, E);
       const uint64_t span =
-          max(absdiff(fx_f64bits((uint64_t)__double_as_longlong(sample_x<DT>(tk, lo, b)), E), c),
-              absdiff(fx_f64bits((uint64_t)__double_as_longlong(sample_x<DT>(tk, lo, en - 1)), E), c));
-      const int sh = max(0, bitlen64(span) - 30);
-      e.cq = c; e.sh = sh;
-      e.A = fp32_sat(ldexp(q[0], E + sh));
+          max(absdiff(fx_f64bits((uint64_t)__double_as_longlong(sample_x<DT>(tk, lo, b)), E), ce),
+              absdiff(fx_f64bits((uint64_t)__double_as_longlong(sample_x<DT>(tk, lo, en - 1)), E), ce));
+      const int P = E + max(0, bitlen64(span) - 30);
+      f.P = P;
+      f.C = fx_f64bits(cb, P);
+      f.A = fp32_sat(ldexp(q[0], P));
+      const int tc = feat32(fx_f64bits(cb, P0), C0, T0_LIM);
+      c.AL = (int)floor_scaled(__dmul_rn(q[0], f0d), P0 + 32, 0.0, INT31);
+      c.BL = BL - (long long)c.AL * (long long)tc;
     }
-    e.B = __double2float_rn(q[2]);
-    e.LO = __double2float_rn(q[3]);
-    e.HI = __double2float_rn(q[4]);
-    ev[l] = e;
+    const double lob = fmin(floor(__dmul_rn(q[3], f0d)), f0d - 1.0);
+    const double hib = fmin(floor(__dmul_rn(q[4], f0d)), f0d - 1.0);
+    c.lohi = (uint32_t)lob | ((uint32_t)hib << 16);
+    f.B = __double2float_rn(q[2]);
+    f.LO = __double2float_rn(q[3]);
+    l0[l] = c;
+    lf[l] = f;
   }
 }
 
@@ -347,7 +422,7 @@ struct Cand {
 template <int DT>
 __global__ void k_heavy_compact(const uint64_t* __restrict__ tk, const DevModel* hdr,
                                 const uint32_t* __restrict__ flags, const uint64_t* __restrict__ pos,
-                                const LeafEval* __restrict__ leaves, uint32_t f0, Cand* cand,
+                                const LeafL0* __restrict__ leaves, uint32_t f0, Cand* cand,
                                 uint64_t cand_cap) {
   const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
   const uint64_t* t = tk + lo;
@@ -411,7 +486,7 @@ __global__ void k_heavy_select(const Cand* __restrict__ cand, const uint64_t* nc
 template <int DT>
 __global__ void __launch_bounds__(1024)
 k_heavy_heads(const uint64_t* __restrict__ sel, const uint32_t* __restrict__ nh, uint32_t f0,
-              int hpb, DevModel* hdr, const LeafEval* __restrict__ leaves, BucketHead* heads,
+              int hpb, DevModel* hdr, const LeafFine* __restrict__ leaves, BucketHead* heads,
               HeavyEntry* heavy) {
   __shared__ uint32_t ws[33];
   __shared__ uint32_t s_run;
@@ -476,8 +551,16 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   k_fit_sums<DT><<<FIT_BLOCKS, FIT_THREADS, 0, st>>>(W.smp_a, W.rank, M.hdr, 1, W.partials);
   k_fit_root<<<1, 32, 0, st>>>(M.hdr, W.partials, FIT_BLOCKS, 1);
   k_fit_route<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, M.hdr, L, M.leaf_beg, M.leaf_end);
-  k_fit_leaf<DT><<<L, FIT_THREADS, 0, st>>>(W.smp_a, W.rank, M.hdr, M.leaf_beg, M.leaf_end, M.leaf64);
-  k_fit_final<DT><<<1, 1024, 0, st>>>(W.smp_a, M.hdr, L, M.leaf_beg, M.leaf_end, M.leaf64, M.leaf);
+  k_fit_units_plan<<<1, 1024, 0, st>>>(M.leaf_beg, M.leaf_end, L, W.ubase, W.utotal);
+  {
+    const unsigned ub = (unsigned)std::min<uint64_t>(s / FIT_UNIT + L + 1, 16ull * num_sms);
+    k_fit_unit_sums<DT><<<ub, FIT_THREADS, 0, st>>>(W.smp_a, W.rank, M.hdr, M.leaf_beg,
+                                                   M.leaf_end, W.ubase, L, W.utotal, W.units);
+  }
+  k_fit_leaf_final<DT><<<(L + 255) / 256, 256, 0, st>>>(W.smp_a, W.rank, M.hdr, M.leaf_beg,
+                                                       M.leaf_end, W.ubase, W.units, L, M.leaf64);
+  k_fit_final<DT><<<1, 1024, 0, st>>>(W.smp_a, M.hdr, L, P.f0, M.leaf_beg, M.leaf_end, M.leaf64,
+                                      M.leafc, M.leaff);
   // heavy values
   const uint64_t tau = P.tau;
   k_heavy_flags<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, M.hdr, tau, W.flags, s);
@@ -488,13 +571,13 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
                                                    (uint64_t*)W.scan_status,
                                                    (uint32_t*)((uint64_t*)W.scan_status + sblocks),
                                                    err);
-  k_heavy_compact<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, M.hdr, W.flags, W.cpos, M.leaf,
+  k_heavy_compact<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, M.hdr, W.flags, W.cpos, M.leafc,
                                                       P.f0, (Cand*)W.cand, W.cand_cap);
   k_heavy_select<<<(P.f0 + 255) / 256, 256, 0, st>>>((const Cand*)W.cand, W.cpos + s, W.cand_cap,
                                                      P.f0, (int)P.hpb, W.sel, W.nh);
-  k_heavy_heads<DT><<<1, 1024, 0, st>>>(W.sel, W.nh, P.f0, (int)P.hpb, M.hdr, M.leaf, M.heads,
+  k_heavy_heads<DT><<<1, 1024, 0, st>>>(W.sel, W.nh, P.f0, (int)P.hpb, M.hdr, M.leaff, M.heads,
                                         M.heavy);
-  add_launches(18);
+  add_launches(20);
   return cudaGetLastError();
 }
 

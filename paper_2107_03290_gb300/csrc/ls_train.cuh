@@ -26,6 +26,9 @@ struct TrainWs {
   uint64_t* sel;             // f0 * hpb
   uint32_t* nh;              // f0
   double* partials;          // 2 * FIT_BLOCKS
+  uint32_t* ubase;           // L + 1 (first fit unit of each leaf)
+  uint32_t* utotal;          // 1
+  double* units;             // 4 * (s / 2048 + L + 1) unit partial sums
   unsigned long long* hi;    // 1
   void* scan_status;         // scan tiles * 8 + 16 bytes
   size_t scan_status_bytes;

@@ -178,18 +178,17 @@ def test_train_matches_oracle(dist):
     gm.leaf[:] = m["leaf"]
     smp = keys[idx]
     xs = np.sort(smp.astype(np.float64)[np.isfinite(smp.astype(np.float64))])
-    ev = oracle.spec_eval_params(gm, xs, "f64")
-    assert int(ev.E[0]) == m["E"] and int(ev.root_cq[0]) == m["root_cq"]
-    assert int(ev.root_sh[0]) == m["root_sh"]
-    assert ev.root_A[0] == m["root_A"] and ev.root_B[0] == m["root_B"]
-    for k in ("cq", "sh", "A", "B", "LO", "HI"):
+    ev = oracle.spec_eval_params(gm, xs, "f64", 256)
+    for k in oracle.EvalParams.ROOT:
+        assert int(getattr(ev, k)[0]) == int(m[k]), k
+    for k in oracle.EvalParams.FIELDS:
         assert np.array_equal(getattr(ev, k), m[k]), k
     # heavy set from the sorted sample
     sorted_smp = np.sort(smp)
     fin = sorted_smp[np.isfinite(sorted_smp.astype(np.float64))] if sorted_smp.dtype.kind == "f" \
         else sorted_smp
     fin = oracle.reference_sort(fin)
-    h = oracle.spec_heavy(fin, int(m["tau"]), 4, ev, 256)
+    h = oracle.spec_heavy(fin, int(m["tau"]), 4, ev)
     assert np.array_equal(h, m["heavy_tk"])
 
 
@@ -202,15 +201,8 @@ def test_level0_histogram_matches_spec(dist):
     t = torch.from_numpy(keys).cuda()
     h = ls.level0_histogram(t, p)
     m = ls.train(t, p)
-    gm = oracle.FittedModel(128)
-    gm.m.root[0], gm.m.root[1], gm.m.root[2] = m["root"]
-    gm.leaf[:] = m["leaf"]
-    ev = oracle.EvalParams(128)
-    ev.E[0], ev.root_cq[0], ev.root_sh[0] = m["E"], m["root_cq"], m["root_sh"]
-    ev.root_A[0], ev.root_B[0] = m["root_A"], m["root_B"]
-    for k in ("cq", "sh", "A", "B", "LO", "HI"):
-        getattr(ev, k)[:] = m[k]
-    hs = oracle.spec_ext_histogram(ev, keys, 200, m["heavy_tk"])
+    ev = oracle.EvalParams.from_export(m, 128, 200)
+    hs = oracle.spec_ext_histogram(ev, keys, m["heavy_tk"])
     assert h.sum() == n
     assert np.array_equal(h, hs)
 

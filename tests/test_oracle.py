@@ -304,35 +304,43 @@ def test_spec_fixed_point_closed_forms():
     assert f(-1e-45, -149, np.float32) == -1
 
 
-def _eval_for(a, L=128):
+def _eval_for(a, L=128, f0=1000):
     fm = oracle.train(a, oracle.params(leaves=L))
     smp = a[oracle.sample_indices(a.size, oracle.sample_size(a.size, oracle.params(leaves=L)))
             .astype(np.int64)].astype(np.float64)
     smp = np.sort(smp[np.isfinite(smp)])
-    return fm, smp, oracle.spec_eval_params(fm, smp, "f64")
+    return fm, smp, oracle.spec_eval_params(fm, smp, "f64", f0)
 
 
-def test_spec_F_monotone_and_close_to_fp64():
-    a = lsgen.normal_f64(100_000, 41)
+@pytest.mark.parametrize("gen", ["normal", "gauss_mix", "zipf"])
+def test_spec_bucket_monotone_and_close_to_fp64(gen):
+    a = {"normal": lambda: lsgen.normal_f64(100_000, 41),
+         "gauss_mix": lambda: lsgen.gauss_mix_f64(100_000, 43),
+         "zipf": lambda: lsgen.zipf_lognormal_f64(100_000, 44, k=3000)}[gen]()
     fm, smp, ev = _eval_for(a)
-    xs = np.sort(a[:4000])
-    F32 = oracle.spec_F(ev, xs)
-    assert np.all(np.diff(F32) >= 0)
+    xs = np.sort(np.concatenate([a[:4000], [-np.inf, np.inf, 0.0, -0.0]]))
+    b = oracle.spec_buckets(ev, xs).astype(np.int64)
+    assert np.all(np.diff(b) >= 0) and b.min() >= 0 and b.max() <= 999
+    # the integer bucket map is floor(F * f0) up to the fixed-point rounding
     F64 = np.array([fm.predict(float(x)) for x in xs])
-    # the FP32 feature path tracks the FP64 model except next to leaf edges
-    assert np.median(np.abs(F32 - F64)) < 1e-5
-    b = oracle.spec_buckets(ev, xs, 1000)
-    assert np.all(np.diff(b.astype(np.int64)) >= 0)
+    exact = np.minimum(np.floor(F64 * 1000), 999)
+    assert np.mean(np.abs(b - exact) <= 1) > 0.995
+    Ff = oracle.spec_F_fine(ev, xs)
+    assert np.all(np.diff(Ff) >= 0)
+    fin = np.isfinite(xs)
+    assert np.median(np.abs(Ff[fin] - F64[fin])) < 1e-5
+    assert np.max(np.abs(Ff[fin] - F64[fin])) < 1e-3
 
 
 def test_spec_heavy_and_ext_histogram():
     keys = np.array([1.0] * 5 + [2.0] + [3.0] * 3 + [4.0] * 4, np.float64)
     fm = oracle.fit_sorted(keys, 2)
-    ev = oracle.spec_eval_params(fm, keys, "f64")
-    h = oracle.spec_heavy(keys, 3, 8, ev, 4)
+    ev = oracle.spec_eval_params(fm, keys, "f64", 4)
+    h = oracle.spec_heavy(keys, 3, 8, ev)
     assert h.tolist() == oracle.total_order_keys(np.array([1.0, 3.0, 4.0])).tolist()
-    h1 = oracle.spec_heavy(keys, 3, 1, ev, 1)          # one bucket, keep the longest run
+    ev1 = oracle.spec_eval_params(fm, keys, "f64", 1)
+    h1 = oracle.spec_heavy(keys, 3, 1, ev1)          # one bucket, keep the longest run
     assert h1.tolist() == oracle.total_order_keys(np.array([1.0])).tolist()
-    hist = oracle.spec_ext_histogram(ev, keys, 1, h)
+    hist = oracle.spec_ext_histogram(ev1, keys, h)
     # one bucket owning heavies 1 < 3 < 4: slots <1, =1, (1,3), =3, (3,4), =4, >4
     assert hist.tolist() == [0, 5, 1, 3, 0, 4, 0]
