@@ -84,7 +84,10 @@ typedef struct ls_stats {
   uint64_t n_fallback;       /* segments finished by the radix fallback       */
   uint64_t n_fill;           /* fill jobs (equality + homogeneous segments)   */
   uint64_t n_launches;       /* kernels this call launched                    */
-  uint64_t reserved[4];
+  uint64_t n_fallback_keys;  /* keys in segments of the radix fallback        */
+  uint64_t max_fallback;     /* largest fallback segment                      */
+  uint64_t n_large_keys;     /* keys in counting-sort segments > 2048         */
+  uint64_t n_range;          /* segments split by key range (levels 2 and 3)  */
 } ls_stats;
 
 /* Model export for parity checks (host buffers owned by the caller). */

@@ -99,10 +99,11 @@ class Stats(ctypes.Structure):
                 + [(k, ctypes.c_uint64) for k in ("n_heavy", "n_ext", "max_bucket", "n_eq_keys",
                                                   "n_level1", "n_segments", "n_fallback",
                                                   "n_fill", "n_launches")]
-                + [("reserved", ctypes.c_uint64 * 4)])
+                + [(k, ctypes.c_uint64) for k in ("n_fallback_keys", "max_fallback", "n_large_keys",
+                                                  "n_range")])
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class ModelExport(ctypes.Structure):

@@ -112,7 +112,7 @@ struct Plan {
   uint64_t s, tau, seed;
   Chunking c;
   SortLimits lim;
-  uint64_t cap0, cap1, cap_c;
+  uint64_t cap0, cap1, cap_c, cap_r, capj;
   size_t smem_hist, smem_scatter;
   uint32_t l0_scan_tiles;
 };
@@ -175,7 +175,9 @@ static void plan_call(const ls_params* prm, int dt, uint64_t n, uintptr_t addr, 
   P->smem_hist = level0_smem_hist(dt, P->L, P->f0, P->n_ext_max);
   P->smem_scatter = level0_smem_scatter(dt, P->L, P->f0, P->n_ext_max);
   P->cap0 = P->n_ext_max + 16;
-  P->cap_c = n / P->lim.l1_target + 2 * P->cap0 + 64;
+  P->cap_r = n / (P->lim.c_large + 1) + 16;     // jobs a refinement level can pass on
+  P->capj = std::max(P->cap0, P->cap_r);        // jobs of one refinement level
+  P->cap_c = n / P->lim.l1_target + 2 * P->capj + 64;
   P->cap1 = P->cap_c + P->cap0;
   const uint64_t M = (uint64_t)P->n_ext_max * G;
   P->l0_scan_tiles = (uint32_t)std::max<uint64_t>(1, (M + SC_TILE - 1) / SC_TILE);
@@ -200,7 +202,7 @@ struct Workspace {
   size_t o_scratch, o_smp_a, o_smp_b, o_rank, o_flags, o_cpos, o_cand, o_sel, o_nh, o_part, o_hi,
       o_tscan, o_rs_hist, o_rs_skip, o_rs_status, o_hdr, o_leaf64, o_leafc, o_leaff, o_heads, o_heavy,
       o_lbeg, o_lend, o_hist, o_offs, o_l0scan, o_jobs_fill, o_jobs_s, o_jobs_l, o_jobs_r,
-      o_jobs_fb, o_counts, o_aux, o_tot, o_l1cnt, o_l1off, o_l1cur, o_jmin, o_jmax, o_l1scan,
+      o_jobs_fb, o_jobs_r2, o_jobs_r3, o_counts, o_aux, o_tot, o_l1cnt, o_l1off, o_l1cur, o_jmin, o_jmax, o_l1scan,
       o_ubase, o_units;
   size_t tscan_bytes, rs_status_bytes, l0scan_bytes, l1scan_bytes;
   uint64_t cand_cap;
@@ -247,14 +249,16 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->o_jobs_l = c.take<Job>(P.cap1);
   w->o_jobs_r = c.take<Job>(P.cap0);
   w->o_jobs_fb = c.take<Job>(P.cap1);
+  w->o_jobs_r2 = c.take<Job>(P.cap_r);
+  w->o_jobs_r3 = c.take<Job>(P.cap_r);
   w->o_counts = c.take<unsigned long long>(16);
-  w->o_aux = c.take<uint8_t>((P.cap0 + 1) * 32);
+  w->o_aux = c.take<uint8_t>((P.capj + 1) * 32);
   w->o_tot = c.take<unsigned long long>(4);
   w->o_l1cnt = c.take<uint32_t>(P.cap_c);
   w->o_l1off = c.take<uint64_t>(P.cap_c + 1);
   w->o_l1cur = c.take<unsigned long long>(P.cap_c);
-  w->o_jmin = c.take<unsigned long long>(P.cap0);
-  w->o_jmax = c.take<unsigned long long>(P.cap0);
+  w->o_jmin = c.take<unsigned long long>(P.capj);
+  w->o_jmax = c.take<unsigned long long>(P.capj);
   const uint64_t l1tiles = std::max<uint64_t>(1, (P.cap_c + SC_TILE - 1) / SC_TILE);
   w->l1scan_bytes = l1tiles * 8 + 16;
   w->o_l1scan = c.take<uint8_t>(w->l1scan_bytes);
@@ -271,7 +275,7 @@ struct Bound {
   TrainWs T;
   Lists lists;
   Level1Ws l1;
-  unsigned long long* counts;  // [0..4] list counts, [8..10] job counters
+  unsigned long long* counts;  // [0..6] list counts, [8..10] job counters
 };
 
 static Bound bind(const Plan& P, const Workspace& w) {
@@ -319,6 +323,8 @@ static Bound bind(const Plan& P, const Workspace& w) {
   b.lists.sort_l = mk(w.o_jobs_l, b.counts + 2, P.cap1);
   b.lists.refine = mk(w.o_jobs_r, b.counts + 3, P.cap0);
   b.lists.fallback = mk(w.o_jobs_fb, b.counts + 4, P.cap1);
+  b.lists.refine2 = mk(w.o_jobs_r2, b.counts + 5, P.cap_r);
+  b.lists.refine3 = mk(w.o_jobs_r3, b.counts + 6, P.cap_r);
   Level1Ws& l = b.l1;
   l.aux = at<void>(w, w.o_aux);
   l.totals = at<unsigned long long>(w, w.o_tot);
@@ -330,7 +336,7 @@ static Bound bind(const Plan& P, const Workspace& w) {
   l.scan_status = at<void>(w, w.o_l1scan);
   l.scan_status_bytes = w.l1scan_bytes;
   l.cap_c = P.cap_c;
-  l.cap_jobs = P.cap0;
+  l.cap_jobs = P.capj;
   l.cap_tiles = 0;
   return b;
 }
@@ -389,7 +395,7 @@ static cudaError_t enqueue_sort(const Plan& P, const Workspace& w, void* keys, D
   LS_TRY(cudaMemsetAsync(at<void>(w, w.o_l0scan), 0, w.l0scan_bytes, st));
   const Level0Args a = level0_args(P, b, w, keys, d);
   LS_TRY(level0_enqueue(P.dt, a, P.smem_hist, P.smem_scatter, b.lists, P.lim, st, &mk, 2));
-  LS_TRY(level1_enqueue(P.dt, keys, a.scratch, P.n, b.M, P.f0, b.lists, P.lim, b.l1, d->err, st,
+  LS_TRY(level1_enqueue(P.dt, keys, a.scratch, P.n, b.M, b.lists, P.lim, b.l1, d->err, st,
                         d->num_sms));
   mark(&mk, 6, st);
   LS_TRY(fill_enqueue(P.dt, keys, b.lists, P.cap1, st, d->num_sms));
@@ -447,6 +453,7 @@ static void fill_stats(const Plan& P, const Workspace& w, Events* ev, ls_stats* 
   stats->n_level1 = counts[3];
   stats->n_segments = counts[1] + counts[2];
   stats->n_fallback = counts[4];
+  stats->n_range = counts[5] + counts[6];
   // largest slot and equality keys from the level-0 offsets
   const uint32_t next = std::min<uint32_t>(hdr.n_ext, P.n_ext_max);
   std::vector<uint64_t> offs((size_t)P.n_ext_max * P.c.G + 1);
@@ -465,6 +472,19 @@ static void fill_stats(const Plan& P, const Workspace& w, Events* ev, ls_stats* 
   stats->max_bucket = mx;
   stats->n_eq_keys = eq;
   stats->n_fill = counts[0];
+  auto job_keys = [&](size_t off, uint64_t cnt, uint64_t cap, uint64_t* mxm) {
+    std::vector<Job> jobs((size_t)std::min(cnt, cap));
+    if (!jobs.empty())
+      cudaMemcpy(jobs.data(), at<void>(w, off), jobs.size() * sizeof(Job), cudaMemcpyDeviceToHost);
+    uint64_t sum = 0;
+    for (const Job& j : jobs) {
+      sum += j.m;
+      if (mxm) *mxm = std::max<uint64_t>(*mxm, j.m);
+    }
+    return sum;
+  };
+  stats->n_fallback_keys = job_keys(w.o_jobs_fb, counts[4], P.cap1, &stats->max_fallback);
+  stats->n_large_keys = job_keys(w.o_jobs_l, counts[2], P.cap1, nullptr);
 }
 
 }  // namespace ls

@@ -316,8 +316,8 @@ k_bucket_sort(typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Model
       continue;
     }
     const U* src = (job.src ? scratch : keys) + job.start;
-    segment_sort<DT, THREADS, KPT>(keys + job.start, src, (uint32_t)job.m, true, job.Flo, job.Fhi,
-                                   (int)job.la, (int)job.lb, M, r, sm, ss, err);
+    segment_sort<DT, THREADS, KPT>(keys + job.start, src, (uint32_t)job.m, job.kind == JOB_SORT,
+                                   job.Flo, job.Fhi, (int)job.la, (int)job.lb, M, r, sm, ss, err);
   }
 }
 

@@ -264,7 +264,13 @@ __device__ __forceinline__ uint32_t ext_of(typename KT<DT>::U u, const RootEval&
 // ------------------------------------------------------------------ jobs
 // A segment of keys occupying [start, start+m) of buffer `src` (0: keys,
 // 1: scratch); its keys' F estimates lie in [Flo, Fhi).  kind: what to do.
-enum JobKind : uint32_t { JOB_SORT = 0, JOB_FILL = 1, JOB_REFINE = 2, JOB_FALLBACK = 3 };
+enum JobKind : uint32_t {
+  JOB_SORT = 0,        // counting sort on the model's slot map
+  JOB_FILL = 1,
+  JOB_REFINE = 2,
+  JOB_FALLBACK = 3,
+  JOB_SORT_RANGE = 4,  // counting sort on the segment's key range (model could not split)
+};
 struct Job {
   uint64_t start;
   uint64_t m;

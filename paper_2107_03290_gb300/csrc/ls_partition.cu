@@ -356,12 +356,38 @@ struct L1Aux {
   uint32_t pad;
 };
 
+// Split of one refine job: by the model's F (the level-1 Partition of Alg. 2)
+// or, for segments the model could not split, linearly over the segment's
+// total-order key range [jmin, jmax] (an integer map, exact at any width).
+struct RangeSplit {
+  unsigned long long tmin;
+  unsigned long long mul;
+  uint32_t sh;
+};
+
+__device__ __forceinline__ RangeSplit range_split(unsigned long long tmin, unsigned long long tmax,
+                                                  uint32_t f1) {
+  RangeSplit s;
+  const unsigned long long R = tmax - tmin;
+  const int bl = R ? 64 - __clzll((long long)R) : 0;
+  s.sh = bl > 32 ? (uint32_t)(bl - 32) : 0u;
+  const unsigned long long Q = R >> s.sh;                      // < 2^32
+  const unsigned long long fe = min((unsigned long long)f1, Q + 1);
+  s.mul = (fe << 32) / (Q + 1);                                // <= 2^32
+  s.tmin = tmin;
+  return s;
+}
+__device__ __forceinline__ uint32_t range_sub(uint64_t tk, const RangeSplit& s) {
+  const unsigned long long d = (tk - s.tmin) >> s.sh;
+  return (uint32_t)((d * s.mul) >> 32);                        // < min(f1, Q + 1)
+}
+
 __global__ void __launch_bounds__(1024)
-k_l1_plan(Lists lists, SortLimits lim, Level1Ws w, uint32_t* err) {
+k_l1_plan(LevelArgs la, SortLimits lim, Level1Ws w, uint32_t* err) {
   __shared__ uint64_t ws[33];
   __shared__ uint64_t s_rt, s_rc;
   L1Aux* aux = (L1Aux*)w.aux;
-  const uint64_t nj = min((uint64_t)*lists.refine.count, min((uint64_t)lists.refine.cap, w.cap_jobs));
+  const uint64_t nj = min((uint64_t)*la.in.count, min((uint64_t)la.in.cap, w.cap_jobs));
   if (threadIdx.x == 0) { s_rt = 0; s_rc = 0; }
   __syncthreads();
   for (uint64_t j0 = 0; j0 < nj; j0 += blockDim.x) {
@@ -369,16 +395,20 @@ k_l1_plan(Lists lists, SortLimits lim, Level1Ws w, uint32_t* err) {
     uint64_t tiles = 0, f1 = 0;
     float S = 0, T = 0;
     if (j < nj) {
-      Job job = lists.refine.jobs[j];
-      const double width = job.Fhi - job.Flo;
+      Job job = la.in.jobs[j];
       uint64_t f = (job.m + lim.l1_target - 1) / lim.l1_target;
       f = f < 2 ? 2 : (f > MAX_F1 ? MAX_F1 : f);
-      const double Sd = (double)f / width;
-      S = (float)Sd;
-      T = (float)(-job.Flo * Sd);
-      if (!(width > 0) || !isfinite(S) || !isfinite(T)) {
-        job.kind = JOB_FALLBACK;  // the model cannot split this range
-        push_job(lists.fallback, job, err);
+      bool ok = true;
+      if (la.mode == 0) {
+        const double width = job.Fhi - job.Flo;
+        const double Sd = (double)f / width;
+        S = (float)Sd;
+        T = (float)(-job.Flo * Sd);
+        ok = width > 0 && isfinite(S) && isfinite(T);
+      }
+      if (!ok) {  // the model cannot split this range: pass it to the next level
+        job.kind = la.next_kind;
+        push_job(la.next, job, err);
       } else {
         f1 = f;
         tiles = (job.m + L1_TILE - 1) / L1_TILE;
@@ -443,10 +473,45 @@ __device__ __forceinline__ uint32_t l1_sub(typename KT<DT>::U u, const RootEval&
   return (uint32_t)v;
 }
 
+// Total-order key range of every job of a range level (one atomic pair per tile).
+template <int DT>
+__global__ void __launch_bounds__(L1_THREADS)
+k_l1_minmax(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, LevelArgs la,
+            Level1Ws w) {
+  typedef typename KT<DT>::U U;
+  __shared__ unsigned long long s_min, s_max;
+  const L1Aux* aux = (const L1Aux*)w.aux;
+  const uint64_t T = w.totals[0], nj = w.totals[2];
+  const int lane = threadIdx.x & 31;
+  for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
+    const uint64_t j = aux_find_tile(aux, nj, t);
+    const Job job = la.in.jobs[j];
+    const uint64_t off = (t - aux[j].tile_base) * L1_TILE;
+    const uint32_t c = (uint32_t)min((uint64_t)L1_TILE, job.m - off);
+    const U* src = (job.src ? scratch : keys) + job.start + off;
+    if (threadIdx.x == 0) { s_min = ~0ull; s_max = 0; }
+    __syncthreads();
+    unsigned long long mn = ~0ull, mx = 0;
+    for (uint32_t i = threadIdx.x; i < c; i += blockDim.x) {
+      const unsigned long long tk = KT<DT>::tk(src[i]);
+      mn = min(mn, tk);
+      mx = max(mx, tk);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) { atomicMin(&s_min, mn); atomicMax(&s_max, mx); }
+    __syncthreads();
+    if (threadIdx.x == 0) { atomicMin(&w.jmin[j], s_min); atomicMax(&w.jmax[j], s_max); }
+    __syncthreads();
+  }
+}
+
 template <int DT>
 __global__ void __launch_bounds__(L1_THREADS)
 k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, ModelPtrs M,
-          Lists lists, Level1Ws w) {
+          LevelArgs la, Level1Ws w) {
   typedef typename KT<DT>::U U;
   __shared__ uint32_t hc[MAX_F1];
   __shared__ unsigned long long s_min, s_max;
@@ -458,10 +523,12 @@ k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Mod
   for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
     const uint64_t j = aux_find_tile(aux, nj, t);
     const L1Aux x = aux[j];
-    const Job job = lists.refine.jobs[j];
+    const Job job = la.in.jobs[j];
     const uint64_t off = (t - x.tile_base) * L1_TILE;
     const uint32_t c = (uint32_t)min((uint64_t)L1_TILE, job.m - off);
     const U* src = (job.src ? scratch : keys) + job.start + off;
+    RangeSplit rs{};
+    if (la.mode) rs = range_split(w.jmin[j], w.jmax[j], x.f1);
     for (uint32_t s = threadIdx.x; s < x.f1; s += blockDim.x) hc[s] = 0;
     if (threadIdx.x == 0) { s_min = ~0ull; s_max = 0; }
     __syncthreads();
@@ -472,39 +539,50 @@ k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Mod
       if (i < c) {
         const U u = src[i];
         const uint64_t tk = KT<DT>::tk(u);
-        mn = min(mn, (unsigned long long)tk);
-        mx = max(mx, (unsigned long long)tk);
-        sub = l1_sub<DT>(u, r, lf, x);
+        if (la.mode) {
+          sub = range_sub(tk, rs);
+        } else {
+          mn = min(mn, (unsigned long long)tk);
+          mx = max(mx, (unsigned long long)tk);
+          sub = l1_sub<DT>(u, r, lf, x);
+        }
       }
       if (sub != 0xFFFFFFFFu) atomicAdd(&hc[sub], 1u);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (!la.mode) {
+      for (int o = 16; o > 0; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      }
+      if (lane == 0) { atomicMin(&s_min, mn); atomicMax(&s_max, mx); }
     }
-    if (lane == 0) { atomicMin(&s_min, mn); atomicMax(&s_max, mx); }
     __syncthreads();
     for (uint32_t s = threadIdx.x; s < x.f1; s += blockDim.x)
       if (hc[s]) atomicAdd(&w.cnt[x.cbase + s], hc[s]);
-    if (threadIdx.x == 0) { atomicMin(&w.jmin[j], s_min); atomicMax(&w.jmax[j], s_max); }
+    if (threadIdx.x == 0 && !la.mode) {
+      atomicMin(&w.jmin[j], s_min);
+      atomicMax(&w.jmax[j], s_max);
+    }
     __syncthreads();
   }
 }
 
-__global__ void k_l1_cursor(Lists lists, Level1Ws w) {
+__global__ void k_l1_cursor(LevelArgs la, Level1Ws w) {
   const L1Aux* aux = (const L1Aux*)w.aux;
   const uint64_t C = w.totals[1], nj = w.totals[2];
   for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < C;
        c += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t j = aux_find_c(aux, nj, c);
-    w.cur[c] = lists.refine.jobs[j].start + (w.off[c] - w.off[aux[j].cbase]);
+    w.cur[c] = la.in.jobs[j].start + (w.off[c] - w.off[aux[j].cbase]);
   }
 }
 
+// Moves the keys of every refine job into its sub-buckets, from the buffer
+// the job lives in to the other one (keys <-> scratch), same positions.
 template <int DT>
 __global__ void __launch_bounds__(L1_THREADS)
-k_l1_scatter(typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, uint64_t n, ModelPtrs M,
-             Lists lists, Level1Ws w, uint32_t* err) {
+k_l1_scatter(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, uint64_t n, ModelPtrs M,
+             LevelArgs la, Level1Ws w, uint32_t* err) {
   typedef typename KT<DT>::U U;
   constexpr int KPT = L1_TILE / L1_THREADS;
   __shared__ uint32_t lc[MAX_F1 + 1];
@@ -517,16 +595,17 @@ k_l1_scatter(typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, uint64
   const uint64_t T = w.totals[0], nj = w.totals[2];
   const RootEval r = M.hdr->root;
   const LeafFine* mlf = M.leaff;
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = lanemask_lt();
   for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
     const uint64_t j = aux_find_tile(aux, nj, t);
     if (w.jmin[j] == w.jmax[j]) continue;  // homogeneous: filled, not moved
     const L1Aux x = aux[j];
-    const Job job = lists.refine.jobs[j];
+    const Job job = la.in.jobs[j];
     const uint64_t off = (t - x.tile_base) * L1_TILE;
     const uint32_t c = (uint32_t)min((uint64_t)L1_TILE, job.m - off);
     const U* src = (job.src ? scratch : keys) + job.start + off;
+    U* dstb = job.src ? keys : scratch;
+    RangeSplit rs{};
+    if (la.mode) rs = range_split(w.jmin[j], w.jmax[j], x.f1);
     for (uint32_t s = threadIdx.x; s <= x.f1; s += blockDim.x) lc[s] = 0;
     __syncthreads();
     U u[KPT];
@@ -536,7 +615,10 @@ k_l1_scatter(typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, uint64
       const uint32_t i = k * L1_THREADS + threadIdx.x;
       uint32_t sub = 0xFFFFFFFFu;
       u[k] = 0;
-      if (i < c) { u[k] = src[i]; sub = l1_sub<DT>(u[k], r, mlf, x); }
+      if (i < c) {
+        u[k] = src[i];
+        sub = la.mode ? range_sub(KT<DT>::tk(u[k]), rs) : l1_sub<DT>(u[k], r, mlf, x);
+      }
       sb[k] = sub;
       rk[k] = sub != 0xFFFFFFFFu ? atomicAdd(&lc[sub], 1u) : 0u;
     }
@@ -559,15 +641,15 @@ k_l1_scatter(typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, uint64
     for (uint32_t p = threadIdx.x; p < c; p += blockDim.x) {
       const uint32_t s = ids[p];
       const uint64_t dst = gp[s] + (p - lc[s]);
-      if (dst < n) keys[dst] = stage[p]; else set_error(err, ERR_BOUNDS);
+      if (dst < n) dstb[dst] = stage[p]; else set_error(err, ERR_BOUNDS);
     }
     __syncthreads();
   }
 }
 
 template <int DT>
-__global__ void k_l1_classify(Lists lists, SortLimits lim, Level1Ws w, ModelPtrs M, int L,
-                              uint32_t* err) {
+__global__ void k_l1_classify(Lists lists, LevelArgs la, SortLimits lim, Level1Ws w, ModelPtrs M,
+                              int L, uint32_t* err) {
   const L1Aux* aux = (const L1Aux*)w.aux;
   const uint64_t C = w.totals[1], nj = w.totals[2];
   for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < C;
@@ -576,7 +658,7 @@ __global__ void k_l1_classify(Lists lists, SortLimits lim, Level1Ws w, ModelPtrs
     if (cntc == 0) continue;
     const uint64_t j = aux_find_c(aux, nj, c);
     const L1Aux x = aux[j];
-    const Job pj = lists.refine.jobs[j];
+    const Job pj = la.in.jobs[j];
     Job job;
     job.value = 0;
     if (w.jmin[j] == w.jmax[j]) {  // all keys of the bucket are equal (Is-Homogeneous)
@@ -587,17 +669,24 @@ __global__ void k_l1_classify(Lists lists, SortLimits lim, Level1Ws w, ModelPtrs
       continue;
     }
     const uint64_t sub = c - x.cbase;
-    const double wd = (pj.Fhi - pj.Flo) / (double)x.f1;
     job.start = pj.start + (w.off[c] - w.off[x.cbase]);
     job.m = cntc;
-    job.Flo = pj.Flo + (double)sub * wd;
-    job.Fhi = pj.Flo + (double)(sub + 1) * wd;
-    job.src = 0;
+    if (la.mode == 0) {
+      const double wd = (pj.Fhi - pj.Flo) / (double)x.f1;
+      job.Flo = pj.Flo + (double)sub * wd;
+      job.Fhi = pj.Flo + (double)(sub + 1) * wd;
+    } else {
+      job.Flo = pj.Flo;
+      job.Fhi = pj.Fhi;
+    }
+    job.src = pj.src ^ 1u;
     job.la = job.lb = 0;
-    if (cntc <= lim.c_large) leaf_range(M.leaf64, L, job.Flo, job.Fhi, &job.la, &job.lb);
-    if (cntc <= lim.c_small) { job.kind = JOB_SORT; push_job(lists.sort_s, job, err); }
-    else if (cntc <= lim.c_large) { job.kind = JOB_SORT; push_job(lists.sort_l, job, err); }
-    else { job.kind = JOB_FALLBACK; push_job(lists.fallback, job, err); }
+    if (la.mode == 0 && cntc <= lim.c_large)
+      leaf_range(M.leaf64, L, job.Flo, job.Fhi, &job.la, &job.lb);
+    const uint32_t sk = la.mode ? JOB_SORT_RANGE : JOB_SORT;
+    if (cntc <= lim.c_small) { job.kind = sk; push_job(lists.sort_s, job, err); }
+    else if (cntc <= lim.c_large) { job.kind = sk; push_job(lists.sort_l, job, err); }
+    else { job.kind = la.next_kind; push_job(la.next, job, err); }
   }
 }
 
@@ -657,41 +746,52 @@ cudaError_t level0_enqueue(int dt, const Level0Args& a, size_t sh, size_t ss, co
 }
 
 template <int DT>
-static cudaError_t level1_dt(const void* keys, const void* scratch, uint64_t n, const ModelPtrs& M,
-                             const Lists& lists, const SortLimits& lim, const Level1Ws& w,
-                             uint32_t* err, cudaStream_t st, int num_sms) {
+static cudaError_t level_dt(void* keys, void* scratch, uint64_t n, const ModelPtrs& M,
+                            const Lists& lists, const LevelArgs& la, const SortLimits& lim,
+                            const Level1Ws& w, uint32_t* err, cudaStream_t st, int num_sms) {
   typedef typename KT<DT>::U U;
   cudaError_t e = cudaMemsetAsync(w.cnt, 0, w.cap_c * sizeof(uint32_t), st);
   if (e) return e;
   e = cudaMemsetAsync(w.scan_status, 0, w.scan_status_bytes, st);
   if (e) return e;
-  k_l1_plan<<<1, 1024, 0, st>>>(lists, lim, w, err);
+  k_l1_plan<<<1, 1024, 0, st>>>(la, lim, w, err);
   const int grid = 2 * num_sms;
-  k_l1_hist<DT><<<grid, L1_THREADS, 0, st>>>((const U*)keys, (const U*)scratch, M, lists, w);
+  if (la.mode) k_l1_minmax<DT><<<grid, L1_THREADS, 0, st>>>((const U*)keys, (const U*)scratch, la, w);
+  k_l1_hist<DT><<<grid, L1_THREADS, 0, st>>>((const U*)keys, (const U*)scratch, M, la, w);
   const unsigned tiles = (unsigned)std::max<uint64_t>(1, (w.cap_c + SC_TILE - 1) / SC_TILE);
   k_scan<uint32_t><<<tiles, SC_THREADS, 0, st>>>(w.cnt, w.off, w.cap_c, &w.totals[1],
                                                  (uint64_t*)w.scan_status,
                                                  (uint32_t*)((uint64_t*)w.scan_status + tiles), err);
-  k_l1_cursor<<<grid, 256, 0, st>>>(lists, w);
-  k_l1_scatter<DT><<<grid, L1_THREADS, l1_scatter_smem(KT<DT>::W), st>>>((U*)keys, (const U*)scratch,
-                                                                      n, M, lists, w, err);
-  k_l1_classify<DT><<<grid, 256, 0, st>>>(lists, lim, w, M, M.L, err);
-  add_launches(6);
+  k_l1_cursor<<<grid, 256, 0, st>>>(la, w);
+  k_l1_scatter<DT><<<grid, L1_THREADS, l1_scatter_smem(KT<DT>::W), st>>>((U*)keys, (U*)scratch,
+                                                                      n, M, la, w, err);
+  k_l1_classify<DT><<<grid, 256, 0, st>>>(lists, la, lim, w, M, M.L, err);
+  add_launches(la.mode ? 7 : 6);
   return cudaGetLastError();
 }
 
-cudaError_t level1_enqueue(int dt, const void* keys, const void* scratch, uint64_t n,
-                           const ModelPtrs& M, uint32_t f0, const Lists& lists,
-                           const SortLimits& lim, const Level1Ws& w, uint32_t* err,
-                           cudaStream_t st, int num_sms) {
-  (void)f0;
-  switch (dt) {
-    case LS_F64: return level1_dt<LS_F64>(keys, scratch, n, M, lists, lim, w, err, st, num_sms);
-    case LS_U64: return level1_dt<LS_U64>(keys, scratch, n, M, lists, lim, w, err, st, num_sms);
-    case LS_F32: return level1_dt<LS_F32>(keys, scratch, n, M, lists, lim, w, err, st, num_sms);
-    case LS_U32: return level1_dt<LS_U32>(keys, scratch, n, M, lists, lim, w, err, st, num_sms);
+cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const ModelPtrs& M,
+                           const Lists& lists, const SortLimits& lim, const Level1Ws& w,
+                           uint32_t* err, cudaStream_t st, int num_sms) {
+  // level 1 splits by the model; levels 2 and 3 split what it could not by key range
+  const JobList ins[3] = {lists.refine, lists.refine2, lists.refine3};
+  const JobList outs[3] = {lists.refine2, lists.refine3, lists.fallback};
+  for (int lv = 0; lv < 3; ++lv) {
+    LevelArgs la;
+    la.in = ins[lv];
+    la.next = outs[lv];
+    la.mode = lv == 0 ? 0 : 1;
+    la.next_kind = lv == 2 ? JOB_FALLBACK : JOB_REFINE;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (dt) {
+      case LS_F64: e = level_dt<LS_F64>(keys, scratch, n, M, lists, la, lim, w, err, st, num_sms); break;
+      case LS_U64: e = level_dt<LS_U64>(keys, scratch, n, M, lists, la, lim, w, err, st, num_sms); break;
+      case LS_F32: e = level_dt<LS_F32>(keys, scratch, n, M, lists, la, lim, w, err, st, num_sms); break;
+      case LS_U32: e = level_dt<LS_U32>(keys, scratch, n, M, lists, la, lim, w, err, st, num_sms); break;
+    }
+    if (e) return e;
   }
-  return cudaErrorInvalidValue;
+  return cudaSuccess;
 }
 
 cudaError_t fill_enqueue(int dt, void* keys, const Lists& lists, uint64_t fill_cap,

@@ -36,6 +36,16 @@ struct Level0Args {
 // Lists produced by classification (device-side counters).
 struct Lists {
   JobList fill, sort_s, sort_l, refine, fallback;
+  JobList refine2, refine3;  // segments the previous level left above c_large
+};
+
+// One refinement level: split the jobs of `in` into sub-buckets, by the model
+// (mode 0) or by the total-order key range (mode 1); sub-buckets still above
+// c_large go to `next` with kind next_kind.
+struct LevelArgs {
+  JobList in, next;
+  int mode;
+  uint32_t next_kind;
 };
 
 struct SortLimits {
@@ -65,10 +75,9 @@ cudaError_t level0_configure(int dt, size_t smem_hist, size_t smem_scatter);
 cudaError_t level0_enqueue(int dt, const Level0Args& a, size_t smem_hist, size_t smem_scatter,
                            const Lists& lists, const SortLimits& lim, cudaStream_t st,
                            const Marks* mk = nullptr, int mbase = 0);
-cudaError_t level1_enqueue(int dt, const void* keys, const void* scratch, uint64_t n,
-                           const ModelPtrs& M, uint32_t f0, const Lists& lists,
-                           const SortLimits& lim, const Level1Ws& w, uint32_t* err,
-                           cudaStream_t st, int num_sms);
+cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const ModelPtrs& M,
+                           const Lists& lists, const SortLimits& lim, const Level1Ws& w,
+                           uint32_t* err, cudaStream_t st, int num_sms);
 cudaError_t fill_enqueue(int dt, void* keys, const Lists& lists, uint64_t fill_cap,
                          cudaStream_t st, int num_sms);
 cudaError_t buckets_configure(int dt);
