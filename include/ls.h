@@ -103,9 +103,11 @@ typedef struct ls_model_export {
   int64_t root_C0;           /* out */
   int32_t root_RA;           /* out: leaf = clamp((RA t0 + RB) >> 40, 0, L-1)  */
   int64_t root_RB;           /* out */
-  int32_t* AL;               /* out per leaf: level-0 bucket slope (2^-32 units) */
-  int64_t* BL;               /* out per leaf: level-0 bucket intercept           */
-  uint32_t* lohi;            /* out per leaf: bucket clamps lo | hi << 16         */
+  uint32_t fanout;           /* in: capacity of thr (>= f0)                    */
+  uint32_t pos_max;          /* out: bucket of the largest total-order key     */
+  uint64_t* thr;             /* out: f0 level-0 thresholds: thr[b] = smallest
+                                total-order key whose bucket floor(F(x) f0)
+                                (FP64, clamped to [0, f0-1]) is >= b; thr[0] = 0 */
   int64_t* C;                /* out per leaf: fine centre on the grid 2^P        */
   int32_t* P;                /* out per leaf: fine exponent                      */
   float* A;                  /* out per leaf: fine slope                         */

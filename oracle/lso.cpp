@@ -550,13 +550,12 @@ static long long floor_scaled(double v, int k, double lo, double hi) {
 }
 
 void lso_spec_eval_params(const lso_model* model, const double* xs, uint64_t m, int dtype,
-                          uint32_t f0, int32_t* E, int32_t* root_P0, int64_t* root_C0,
-                          int32_t* root_RA, int64_t* root_RB, int32_t* AL, int64_t* BL,
-                          uint32_t* lohi, int64_t* C, int32_t* P, float* A, float* B,
+                          int32_t* E, int32_t* root_P0, int64_t* root_C0, int32_t* root_RA,
+                          int64_t* root_RB, int64_t* C, int32_t* P, float* A, float* B,
                           float* LO, float* HI) {
   (void)dtype;
   const uint32_t L = model->leaves;
-  const double INT31 = 2147483647.0, F0 = (double)f0;
+  const double INT31 = 2147483647.0;
   double R = 0;
   if (m) R = std::max(std::fabs(xs[0]), std::fabs(xs[m - 1]));
   const int e = (R > 0) ? std::ilogb(R) + 1 - 61 : 0;
@@ -580,12 +579,10 @@ void lso_spec_eval_params(const lso_model* model, const double* xs, uint64_t m, 
     if (!seen[l]) { seen[l] = 1; beg[l] = k; }
     end[l] = k + 1;
   }
-  const int64_t T0 = (1ll << 30) - 1;
   for (uint32_t l = 0; l < L; ++l) {
     const double* q = model->leaf + 5 * (size_t)l;
-    const long long bl = floor_scaled(q[2] * F0, 32, -9.0e18, 9.0e18);
     if (!seen[l]) {
-      AL[l] = 0; BL[l] = bl; C[l] = 0; P[l] = e; A[l] = 0.0f;
+      C[l] = 0; P[l] = e; A[l] = 0.0f;
     } else {
       const int64_t ce = fixed_point_f64(q[1], e);
       const uint64_t span = std::max(absd(fixed_point_f64(xs[beg[l]], e) - ce),
@@ -594,14 +591,7 @@ void lso_spec_eval_params(const lso_model* model, const double* xs, uint64_t m, 
       P[l] = pl;
       C[l] = fixed_point_f64(q[1], pl);
       A[l] = fp32_sat(std::ldexp(q[0], pl));
-      int64_t t = fixed_point_f64(q[1], p0) - C0;
-      t = std::min(T0, std::max(-T0, t));
-      AL[l] = (int32_t)floor_scaled(q[0] * F0, p0 + 32, 0.0, INT31);
-      BL[l] = bl - (int64_t)AL[l] * t;
     }
-    const double lob = std::min(std::floor(q[3] * F0), F0 - 1.0);
-    const double hib = std::min(std::floor(q[4] * F0), F0 - 1.0);
-    lohi[l] = (uint32_t)lob | ((uint32_t)hib << 16);
     B[l] = (float)q[2];
     LO[l] = (float)q[3];
     HI[l] = (float)q[4];
@@ -667,17 +657,61 @@ float lso_spec_F_fine(const lso_eval* ev, const void* keys, uint64_t i, int dtyp
   return F;
 }
 
+// Alg. 1 at level 0: pos(x) = clamp(floor(F(x) * f0), 0, f0 - 1) with the
+// FP64 model (the same expression the oracle's Partition uses).
 uint32_t lso_spec_bucket(const lso_eval* ev, const void* keys, uint64_t i, int dtype) {
-  int negative;
-  if (key_nan(keys, i, dtype, &negative)) return negative ? 0u : ev->f0 - 1;
-  const int32_t t0 = spec_t0(ev, keys, i, dtype);
-  const uint32_t l = spec_leaf(ev, t0);
-  const int64_t v = (int64_t)ev->AL[l] * (int64_t)t0 + ev->BL[l];
-  int64_t b = v >> 32;
-  const int64_t lo = ev->lohi[l] & 0xFFFFu, hi = ev->lohi[l] >> 16;
-  if (b < lo) b = lo;
-  if (b > hi) b = hi;
-  return (uint32_t)b;
+  const double ff = (double)ev->f0;
+  double F = 0.0;
+  switch (dtype) {
+    case LSO_F64: F = F_of<F64>(ev->model, ((const double*)keys)[i]); break;
+    case LSO_U64: F = F_of<U64>(ev->model, ((const uint64_t*)keys)[i]); break;
+    case LSO_F32: F = F_of<F32>(ev->model, ((const float*)keys)[i]); break;
+    case LSO_U32: F = F_of<U32>(ev->model, ((const uint32_t*)keys)[i]); break;
+  }
+  return (uint32_t)clamp_pos(F * ff, ev->f0);
+}
+
+// The key whose total-order key is t (inverse of lso_total_order_key).
+static void key_of_tk(uint64_t t, int dtype, void* out) {
+  switch (dtype) {
+    case LSO_F64: {
+      const uint64_t u = (t >> 63) ? (t & ~(1ull << 63)) : ~t;
+      std::memcpy(out, &u, 8);
+      break;
+    }
+    case LSO_F32: {
+      const uint32_t t32 = (uint32_t)t;
+      const uint32_t u = (t32 >> 31) ? (t32 & 0x7FFFFFFFu) : ~t32;
+      std::memcpy(out, &u, 4);
+      break;
+    }
+    case LSO_U64: std::memcpy(out, &t, 8); break;
+    case LSO_U32: { const uint32_t x = (uint32_t)t; std::memcpy(out, &x, 4); break; }
+  }
+}
+
+static uint32_t bucket_of_tk(const lso_eval* ev, uint64_t t, int dtype) {
+  unsigned char buf[8];
+  key_of_tk(t, dtype, buf);
+  return lso_spec_bucket(ev, buf, 0, dtype);
+}
+
+void lso_spec_thresholds(const lso_eval* ev, int dtype, uint64_t* thr, uint32_t* pos_max) {
+  const bool wide = dtype == LSO_F64 || dtype == LSO_U64;
+  const uint64_t tmax = wide ? ~0ull : 0xFFFFFFFFull;
+  const uint64_t never = wide ? ~0ull : 0x100000000ull;
+  const uint32_t top = bucket_of_tk(ev, tmax, dtype);
+  *pos_max = top;
+  thr[0] = 0;
+  for (uint32_t b = 1; b < ev->f0; ++b) {
+    if (top < b) { thr[b] = never; continue; }
+    uint64_t lo = 0, hi = tmax;  // smallest t with bucket(t) >= b
+    while (lo < hi) {
+      const uint64_t mid = lo + (hi - lo) / 2;
+      if (bucket_of_tk(ev, mid, dtype) >= b) hi = mid; else lo = mid + 1;
+    }
+    thr[b] = lo;
+  }
 }
 
 uint64_t lso_spec_heavy(const uint64_t* tk, const void* keys, uint64_t m, int dtype,
@@ -718,24 +752,9 @@ uint64_t lso_spec_ext_histogram(const lso_eval* ev, const void* keys, uint64_t n
   // Heavy values per bucket (heavy list is ascending, buckets non-decreasing).
   std::vector<std::vector<uint64_t>> hb(f0);
   for (uint64_t j = 0; j < nheavy; ++j) {
-    // Find the bucket of a heavy value by evaluating it as a key of `dtype`.
-    uint64_t t = heavy[j];
-    uint32_t b = 0;
-    if (dtype == LSO_F64) {
-      const uint64_t u = (t >> 63) ? (t & ~(1ull << 63)) : ~t;
-      double x; std::memcpy(&x, &u, 8);
-      b = lso_spec_bucket(ev, &x, 0, dtype);
-    } else if (dtype == LSO_F32) {
-      const uint32_t t32 = (uint32_t)t;
-      const uint32_t u = (t32 >> 31) ? (t32 & 0x7FFFFFFFu) : ~t32;
-      float x; std::memcpy(&x, &u, 4);
-      b = lso_spec_bucket(ev, &x, 0, dtype);
-    } else if (dtype == LSO_U64) {
-      b = lso_spec_bucket(ev, &t, 0, dtype);
-    } else {
-      const uint32_t x = (uint32_t)t;
-      b = lso_spec_bucket(ev, &x, 0, dtype);
-    }
+    // the bucket of a heavy value: evaluate it as a key of `dtype`
+    const uint64_t t = heavy[j];
+    const uint32_t b = bucket_of_tk(ev, t, dtype);
     hb[b].push_back(t);
   }
   std::vector<uint64_t> base(f0);

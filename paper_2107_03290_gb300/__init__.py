@@ -112,7 +112,7 @@ class ModelExport(ctypes.Structure):
                 ("root", ctypes.c_double * 3), ("leaf", ctypes.c_void_p),
                 ("E", ctypes.c_int32), ("root_P0", ctypes.c_int32), ("root_C0", ctypes.c_int64),
                 ("root_RA", ctypes.c_int32), ("root_RB", ctypes.c_int64),
-                ("AL", ctypes.c_void_p), ("BL", ctypes.c_void_p), ("lohi", ctypes.c_void_p),
+                ("fanout", ctypes.c_uint32), ("pos_max", ctypes.c_uint32), ("thr", ctypes.c_void_p),
                 ("C", ctypes.c_void_p), ("P", ctypes.c_void_p), ("A", ctypes.c_void_p),
                 ("B", ctypes.c_void_p), ("LO", ctypes.c_void_p), ("HI", ctypes.c_void_p),
                 ("sorted_sample_tk", ctypes.c_void_p), ("heavy_tk", ctypes.c_void_p),
@@ -307,8 +307,10 @@ def train(t, params: Params | None = None, stream=None, with_sample: bool = Fals
     L = p.leaves or 1000
     out = ModelExport()
     out.leaves = L
-    arr = {"leaf": np.zeros((L, 5), np.float64), "AL": np.zeros(L, np.int32),
-           "BL": np.zeros(L, np.int64), "lohi": np.zeros(L, np.uint32), "C": np.zeros(L, np.int64),
+    f0 = p.fanout or 1000
+    out.fanout = f0
+    arr = {"leaf": np.zeros((L, 5), np.float64), "thr": np.zeros(f0, np.uint64),
+           "C": np.zeros(L, np.int64),
            "P": np.zeros(L, np.int32), "A": np.zeros(L, np.float32),
            "B": np.zeros(L, np.float32), "LO": np.zeros(L, np.float32),
            "HI": np.zeros(L, np.float32)}
@@ -329,7 +331,7 @@ def train(t, params: Params | None = None, stream=None, with_sample: bool = Fals
     res.update(sample_size=out.sample_size, sample_finite=out.sample_finite,
                root=np.array(list(out.root)), E=out.E, root_P0=out.root_P0, root_C0=out.root_C0,
                root_RA=out.root_RA, root_RB=out.root_RB,
-               heavy_tk=heavy[:out.n_heavy].copy(), tau=out.tau)
+               heavy_tk=heavy[:out.n_heavy].copy(), tau=out.tau, pos_max=out.pos_max)
     if smp is not None:
         res["sorted_sample_tk"] = smp[:out.sample_size].copy()
     return res

@@ -177,7 +177,7 @@ static void plan_call(const ls_params* prm, int dt, uint64_t n, uintptr_t addr, 
   P->cap0 = P->n_ext_max + 16;
   P->cap_r = n / (P->lim.c_large + 1) + 16;     // jobs a refinement level can pass on
   P->capj = std::max(P->cap0, P->cap_r);        // jobs of one refinement level
-  P->cap_c = n / P->lim.l1_target + 2 * P->capj + 64;
+  P->cap_c = std::max(n / P->lim.l1_target + 2 * P->capj, n / (P->lim.l1_target >> 4) + P->capj) + 64;
   P->cap1 = P->cap_c + P->cap0;
   const uint64_t M = (uint64_t)P->n_ext_max * G;
   P->l0_scan_tiles = (uint32_t)std::max<uint64_t>(1, (M + SC_TILE - 1) / SC_TILE);
@@ -200,7 +200,7 @@ struct Workspace {
   size_t bytes = 0;
   // offsets
   size_t o_scratch, o_smp_a, o_smp_b, o_rank, o_flags, o_cpos, o_cand, o_sel, o_nh, o_part, o_hi,
-      o_tscan, o_rs_hist, o_rs_skip, o_rs_status, o_hdr, o_leaf64, o_leafc, o_leaff, o_heads, o_heavy,
+      o_tscan, o_rs_hist, o_rs_skip, o_rs_status, o_hdr, o_leaf64, o_thr, o_cell, o_cleaf, o_leaff, o_heads, o_heavy,
       o_lbeg, o_lend, o_hist, o_offs, o_l0scan, o_jobs_fill, o_jobs_s, o_jobs_l, o_jobs_r,
       o_jobs_fb, o_jobs_r2, o_jobs_r3, o_counts, o_aux, o_tot, o_l1cnt, o_l1off, o_l1cur, o_jmin, o_jmax, o_l1scan,
       o_ubase, o_units;
@@ -234,7 +234,9 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->o_rs_status = c.take<uint8_t>(w->rs_status_bytes);
   w->o_hdr = c.take<DevModel>(1);
   w->o_leaf64 = c.take<double>(5 * (size_t)P.L);
-  w->o_leafc = c.take<LeafL0>(P.L);
+  w->o_thr = c.take<uint64_t>(P.f0);
+  w->o_cell = c.take<uint32_t>(L0_CELLS);
+  w->o_cleaf = c.take<CellLeaf>(P.L);
   w->o_leaff = c.take<LeafFine>(P.L + 1);
   w->o_heads = c.take<BucketHead>(P.f0 + 1);
   w->o_heavy = c.take<HeavyEntry>((size_t)P.f0 * std::max<uint32_t>(1, P.hpb));
@@ -282,7 +284,9 @@ static Bound bind(const Plan& P, const Workspace& w) {
   Bound b{};
   b.M.hdr = at<DevModel>(w, w.o_hdr);
   b.M.leaf64 = at<double>(w, w.o_leaf64);
-  b.M.leafc = at<LeafL0>(w, w.o_leafc);
+  b.M.thr = at<uint64_t>(w, w.o_thr);
+  b.M.cell = at<uint32_t>(w, w.o_cell);
+  b.M.cleaf = at<CellLeaf>(w, w.o_cleaf);
   b.M.leaff = at<LeafFine>(w, w.o_leaff);
   b.M.heads = at<BucketHead>(w, w.o_heads);
   b.M.heavy = at<HeavyEntry>(w, w.o_heavy);
@@ -630,14 +634,12 @@ ls_status ls_train(const void* keys, size_t n, ls_dtype dtype, void* stream,
     out->tau = P.tau;
     out->n_heavy = hdr.nheavy;
     if (out->leaf) cudaMemcpy(out->leaf, b.M.leaf64, 5 * sizeof(double) * P.L, cudaMemcpyDeviceToHost);
-    std::vector<LeafL0> lc(P.L);
+    out->pos_max = hdr.pos_max;
+    if (out->thr && out->fanout >= P.f0)
+      cudaMemcpy(out->thr, b.M.thr, sizeof(uint64_t) * P.f0, cudaMemcpyDeviceToHost);
     std::vector<LeafFine> lf(P.L + 1);
-    cudaMemcpy(lc.data(), b.M.leafc, sizeof(LeafL0) * P.L, cudaMemcpyDeviceToHost);
     cudaMemcpy(lf.data(), b.M.leaff, sizeof(LeafFine) * (P.L + 1), cudaMemcpyDeviceToHost);
     for (uint32_t l = 0; l < P.L; ++l) {
-      if (out->AL) out->AL[l] = lc[l].AL;
-      if (out->BL) out->BL[l] = lc[l].BL;
-      if (out->lohi) out->lohi[l] = lc[l].lohi;
       if (out->C) out->C[l] = lf[l].C;
       if (out->P) out->P[l] = lf[l].P;
       if (out->A) out->A[l] = lf[l].A;

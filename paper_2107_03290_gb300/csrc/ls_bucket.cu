@@ -1,24 +1,24 @@
-// In-bucket finish of LearnedSort 2.0 (Alg. 2): the model-based counting sort
-// of each (sub-)bucket followed by the insertion-sort touch-up.
+// In-bucket finish of LearnedSort 2.0 (Alg. 2): the counting sort of each
+// (sub-)bucket followed by the insertion-sort touch-up.
 //
 // One CTA per segment of m keys (m <= CAP), keys held in registers, counts and
-// the placed keys in shared memory:
-//   slot(x) = clamp(floor((F(x) - Flo) * m / (Fhi - Flo)), 0, m - 1)
-// evaluated per leaf with FP32 coefficients derived in FP64 for this segment,
-// so the slot resolution is 1/m of the segment's eCDF range.  The leaves that
-// can hold the segment's keys are known from the job (la..lb); keys routed to
-// a leaf outside that range take slot 0 or m-1.  Histogram of slots ->
-// exclusive scan (the running totals of Alg. 2) -> placement -> touch-up.  The
-// slot map is monotone in the key, so keys of different slots are already in
-// order and the touch-up only sorts each group of keys sharing a slot: an
-// insertion sort (<= 16 keys, one thread), a rank sort (<= 128, one warp) or,
-// unless the group holds one value, a bitonic network (one CTA).
+// the placed keys in shared memory.  Inside a segment the model is a straight
+// line (a segment lies within the F range of one level-1 sub-bucket), so the
+// slot map is that line drawn through the segment's own key range, evaluated
+// on the total-order key without any per-key model lookup:
+//   slot(x) = min(m - 1, floor(((tk(x) - tmin) >> sh) * m / (((tmax - tmin) >> sh) + 1)))
+// (sh keeps the scaled range within 24 bits, so the conversion is exact and
+// the map is non-decreasing).  Histogram of slots -> exclusive scan (the
+// running totals of Alg. 2) -> placement -> touch-up.  Keys of different
+// slots are already in order, so the touch-up only sorts each group of keys
+// sharing a slot: an insertion sort (<= 16 keys, one thread), a rank sort
+// (<= 128, one warp) or a bitonic network (one CTA); groups holding one value
+// are left as they are.
 //
-// Segments the model cannot split below CAP keys go to the fallback: per job
-// one CTA splits by the top byte in which the segment's total-order keys
+// Segments the levels could not split below CAP keys go to the fallback: per
+// job one CTA splits by the top byte in which the segment's total-order keys
 // differ (MSD), stops as soon as a piece holds one value, and finishes pieces
-// of at most CAP keys with the same counting sort on a linear map of the
-// piece's key range.
+// of at most CAP keys with the same counting sort.
 #include <cfloat>
 
 #include "ls_partition.cuh"
@@ -27,16 +27,8 @@
 
 namespace ls {
 
-constexpr int MAXL = 64;        // leaves with per-segment coefficients
 constexpr int BIGCAP = 512;     // slot groups > 16 keys tracked per segment
 constexpr int STACK = 2048;     // fallback work stack entries per CTA
-
-struct Coef {
-  float A, B, LO, HI;
-  long long C;
-  int P;
-  int pad;
-};
 
 template <int DT, int THREADS, int KPT>
 struct BucketCfg {
@@ -44,8 +36,7 @@ struct BucketCfg {
   static constexpr int CAP = THREADS * KPT;
   static constexpr size_t OFF_OUT = 0;
   static constexpr size_t OFF_CNT = OFF_OUT + sizeof(U) * CAP;
-  static constexpr size_t OFF_COEF = (OFF_CNT + 4 * (CAP + 1) + 15) / 16 * 16;
-  static constexpr size_t OFF_BIG = OFF_COEF + sizeof(Coef) * MAXL;
+  static constexpr size_t OFF_BIG = (OFF_CNT + 4 * (CAP + 1) + 15) / 16 * 16;
   static constexpr size_t OFF_WS = OFF_BIG + 8 * BIGCAP;
   static constexpr size_t SMEM = OFF_WS + 8 * 40;
   // fallback extras
@@ -57,16 +48,9 @@ struct BucketCfg {
 struct SegShared {            // per-CTA scalars of the segment sort
   unsigned long long tmin, tmax;
   uint32_t nbig, all;
-  int mode;
-  float S, T, rscale;
+  float rscale;
   int sh;
 };
-
-__device__ __forceinline__ float fp32_sat_d(double d) {
-  if (d >= (double)FLT_MAX) return FLT_MAX;
-  if (d <= -(double)FLT_MAX) return -FLT_MAX;
-  return __double2float_rn(d);
-}
 
 template <int DT>
 __device__ __forceinline__ void cmpswap(typename KT<DT>::U* a, uint32_t i, uint32_t j) {
@@ -101,18 +85,13 @@ __device__ void block_bitonic(typename KT<DT>::U* a, uint32_t sz) {
 __device__ __forceinline__ int bitlen64d(uint64_t v) { return v ? 64 - __clzll((long long)v) : 0; }
 
 // Counting sort + touch-up of src[0..m) into dst[0..m) (dst may equal src).
-// model: use the model slot map (job F range, leaves la..lb); otherwise, or if
-// the model cannot split the range, a linear map of the total-order key range.
 template <int DT, int THREADS, int KPT>
 __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* src, uint32_t m,
-                             bool model, double Flo, double Fhi, int la, int lb,
-                             const ModelPtrs& M, const RootEval& r, unsigned char* sm,
-                             SegShared& ss, uint32_t* err) {
+                             unsigned char* sm, SegShared& ss, uint32_t* err) {
   typedef typename KT<DT>::U U;
   typedef BucketCfg<DT, THREADS, KPT> C;
   U* out = (U*)(sm + C::OFF_OUT);
   uint32_t* cnt = (uint32_t*)(sm + C::OFF_CNT);
-  Coef* coef = (Coef*)(sm + C::OFF_COEF);
   uint2* big = (uint2*)(sm + C::OFF_BIG);
   unsigned long long* ws = (unsigned long long*)(sm + C::OFF_WS);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -137,42 +116,18 @@ __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* 
   for (uint32_t i = threadIdx.x; i <= m; i += THREADS) cnt[i] = 0;
   __syncthreads();
   if (lane == 0) { atomicMin(&ss.tmin, mn); atomicMax(&ss.tmax, mx); }
-  const double width = Fhi - Flo;
-  const double scale = (double)m / width;
-  const int nl = lb - la + 1;
-  const bool use_model = model && (width > 0) && isfinite(scale) && nl >= 1;
-  if (use_model && nl <= MAXL) {
-    for (int j = threadIdx.x; j < nl; j += THREADS) {
-      const int l = la + j;
-      const double* q = M.leaf64 + 5 * (size_t)l;
-      const LeafFine lf = M.leaff[l];
-      Coef c;
-      c.A = fp32_sat_d(ldexp(q[0], lf.P) * scale);
-      c.B = fp32_sat_d((q[2] - Flo) * scale);
-      c.LO = fp32_sat_d((q[3] - Flo) * scale);
-      c.HI = fp32_sat_d((q[4] - Flo) * scale);
-      c.C = lf.C;
-      c.P = lf.P;
-      c.pad = 0;
-      coef[j] = c;
-    }
-  }
   __syncthreads();
   if (threadIdx.x == 0) {
     const uint64_t R = ss.tmax - ss.tmin;
-    const int sh = max(0, bitlen64d(R) - 24);
+    const int bl = R ? 64 - __clzll((long long)R) : 0;
+    const int sh = bl > 24 ? bl - 24 : 0;
     ss.sh = sh;
     ss.rscale = (float)m / ((float)(R >> sh) + 1.0f);
-    ss.mode = use_model ? (nl <= MAXL ? 0 : 1) : 3;
-    ss.S = use_model ? fp32_sat_d(scale) : 0.0f;
-    ss.T = use_model ? fp32_sat_d(-Flo * scale) : 0.0f;
   }
   __syncthreads();
-  const int mode = ss.mode;
-  const float S = ss.S, T = ss.T, rscale = ss.rscale;
+  const float rscale = ss.rscale;
   const int sh = ss.sh;
   const unsigned long long tmin = ss.tmin;
-  const float mlim = (float)(m - 1);
   // slots, histogram, ranks
   uint32_t sl[KPT], rk[KPT];
 #pragma unroll
@@ -180,25 +135,8 @@ __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* 
     const uint32_t i = k * THREADS + threadIdx.x;
     uint32_t s = 0xFFFFFFFFu;
     if (i < m) {
-      const U x = u[k];
-      float v;
-      if (mode == 3) {
-        v = __uint2float_rn((uint32_t)((KT<DT>::tk(x) - tmin) >> sh)) * rscale;
-      } else if (KT<DT>::is_nan(x)) {
-        v = KT<DT>::neg(x) ? 0.0f : mlim;
-      } else if (mode == 0) {
-        const int l = predict_leaf<DT>(x, r);
-        if (l < la) v = 0.0f;
-        else if (l > lb) v = mlim;
-        else {
-          const Coef c = coef[l - la];
-          const float d = __int2float_rn(feat32(fixed_point<DT>(x, c.P), c.C, TF_LIM));
-          v = fminf(fmaxf(__fmaf_rn(c.A, d, c.B), c.LO), c.HI);
-        }
-      } else {
-        v = __fmaf_rn(predict_F<DT>(x, r, M.leaff), S, T);
-      }
-      s = (v > 0.0f) ? (v >= mlim ? m - 1 : (uint32_t)v) : 0u;
+      const float v = __uint2float_rn((uint32_t)((KT<DT>::tk(u[k]) - tmin) >> sh)) * rscale;
+      s = min((uint32_t)v, m - 1);
     }
     sl[k] = s;
     rk[k] = s != 0xFFFFFFFFu ? atomicAdd(&cnt[s], 1u) : 0u;  // rank inside the slot
@@ -254,12 +192,16 @@ __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* 
       if (gr.y > 128) continue;
       U x[4];
       uint32_t rank[4];
+      const uint64_t t0 = KT<DT>::tk(out[gr.x]);
+      bool same = true;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const uint32_t i = lane + 32 * q;
         rank[q] = 0;
         x[q] = i < gr.y ? out[gr.x + i] : (U)0;
+        if (i < gr.y) same = same && KT<DT>::tk(x[q]) == t0;
       }
+      if (__all_sync(0xffffffffu, same)) continue;  // one value: in order
       for (uint32_t j = 0; j < gr.y; ++j) {
         const uint64_t tj = KT<DT>::tk(out[gr.x + j]);
 #pragma unroll
@@ -302,7 +244,6 @@ k_bucket_sort(typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Model
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ SegShared ss;
   __shared__ unsigned long long s_job;
-  const RootEval r = M.hdr->root;
   const unsigned long long nj = min(*list.count, list.cap);
   while (true) {
     if (threadIdx.x == 0) s_job = atomicAdd(ctr, 1ull);
@@ -316,8 +257,7 @@ k_bucket_sort(typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Model
       continue;
     }
     const U* src = (job.src ? scratch : keys) + job.start;
-    segment_sort<DT, THREADS, KPT>(keys + job.start, src, (uint32_t)job.m, job.kind == JOB_SORT,
-                                   job.Flo, job.Fhi, (int)job.la, (int)job.lb, M, r, sm, ss, err);
+    segment_sort<DT, THREADS, KPT>(keys + job.start, src, (uint32_t)job.m, sm, ss, err);
   }
 }
 
@@ -343,7 +283,6 @@ k_fallback(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, ModelPtrs M, J
   __shared__ int s_top;
   __shared__ StackEnt s_e;
   __shared__ uint32_t ws32[33];
-  const RootEval r = M.hdr->root;
   const unsigned long long nj = min(*list.count, list.cap);
   const int lane = threadIdx.x & 31;
   while (true) {
@@ -373,7 +312,7 @@ k_fallback(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, ModelPtrs M, J
       U* Y = (e.buf ? keys : scratch) + e.start;
       U* D = keys + e.start;
       if (e.m <= (uint32_t)C::CAP) {
-        segment_sort<DT, 512, 16>(D, X, e.m, false, 0.0, 0.0, 0, 0, M, r, sm, ss, err);
+        segment_sort<DT, 512, 16>(D, X, e.m, sm, ss, err);
         continue;
       }
       unsigned long long o = 0, a = ~0ull;

@@ -130,19 +130,21 @@ constexpr int64_t T0_LIM = (1ll << 30) - 1;   // root feature range
 constexpr int64_t TF_LIM = 2147483647ll;      // fine feature range
 
 // ------------------------------------------------------------------ model
-// Two evaluations of the same monotone model F (see DESIGN.md):
-//  * level 0 (buckets), integer only: the root feature
-//      t0 = clamp(fx(x, P0) - C0, +-(2^30 - 1)),
-//    leaf l = clamp((RA * t0 + RB) >> 40, 0, L-1), and the bucket
-//      b = clamp((AL_l * t0 + BL_l) >> 32, lo_l, hi_l),
-//    the fixed-point form of floor(F(x) * f0) with hi_l = lo_{l+1};
+// Two evaluations of the same monotone model F:
+//  * level 0 (buckets): the bucket of key x is pos(x) = clamp(floor(F(x) * f0),
+//    0, f0-1) with F in FP64 (Alg. 1).  pos is non-decreasing in the
+//    total-order key, so it is stored as its f0 thresholds
+//      thr[b] = min { tk : pos(tk) >= b }   (thr[0] = 0)
+//    and a key's bucket is the number of thresholds <= tk(x).  The search is
+//    narrowed by a cell index: the same RMI evaluated in FP32 on a monotone
+//    FP32 image of the key, cell = floor(F32(x) * L0_CELLS); the cell table
+//    holds, per cell, the bucket range of the keys in it.  Any monotone cell
+//    map gives the exact bucket; a good one only makes the ranges short;
 //  * fine (level-1 split, in-bucket slots), FP32 on the leaf's own grid:
 //      F = clamp(A_l * clamp(fx(x, P_l) - C_l) + B_l, LO_l, HI_l),  HI_l = LO_{l+1}.
-struct LeafL0 {        // 16 bytes
-  int AL;              // slope, bucket units * 2^32 per root-feature unit
-  uint32_t lohi;       // lo_l | hi_l << 16 (bucket clamps)
-  long long BL;        // intercept at t0 = 0, bucket units * 2^32
-};
+constexpr int L0_CELL_BITS = 12;
+constexpr uint32_t L0_CELLS = 1u << L0_CELL_BITS;
+constexpr uint32_t L0_TABLE = L0_CELLS;
 struct LeafFine {      // 32 bytes; record L is a sentinel with LO = 1
   long long C;
   float A;
@@ -187,17 +189,6 @@ __device__ __forceinline__ int predict_leaf(typename KT<DT>::U u, const RootEval
   return leaf_of_t0(root_t0<DT>(u, r), r);
 }
 
-// Level-0 bucket of a non-NaN key (integer evaluation).
-__device__ __forceinline__ uint32_t bucket_of_t0(int t0, const RootEval& r,
-                                                 const LeafL0* __restrict__ l0) {
-  const LeafL0 c = l0[leaf_of_t0(t0, r)];
-  const long long v = (long long)c.AL * (long long)t0 + c.BL;
-  int b = (int)(v >> 32);
-  const int lo = (int)(c.lohi & 0xFFFFu), hi = (int)(c.lohi >> 16);
-  b = b < lo ? lo : b;
-  return (uint32_t)(b > hi ? hi : b);
-}
-
 // Fine feature of a key in leaf l.
 template <int DT>
 __device__ __forceinline__ float fine_feature(typename KT<DT>::U u, const LeafFine& f) {
@@ -216,32 +207,100 @@ __device__ __forceinline__ float predict_F(typename KT<DT>::U u, const RootEval&
   return F;
 }
 
-// Level-0 bucket of a key (NaNs go to the end buckets by sign).
+// Monotone (non-decreasing) FP32 image of a non-NaN key: doubles are
+// truncated toward zero (magnitudes below FLT_MIN become 0, above FLT_MAX
+// infinity), integers converted toward zero.
+template <int DT> __device__ __forceinline__ float key_f32(typename KT<DT>::U u);
+template <> __device__ __forceinline__ float key_f32<LS_F64>(uint64_t u) {
+  const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+  const int e = (int)((hi >> 20) & 0x7FFu) - 896;  // FP32 biased exponent
+  uint32_t mag = ((uint32_t)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  mag = e <= 0 ? 0u : mag;
+  mag = e >= 255 ? 0x7F800000u : mag;
+  return __uint_as_float((hi & 0x80000000u) | mag);
+}
+template <> __device__ __forceinline__ float key_f32<LS_F32>(uint32_t u) { return __uint_as_float(u); }
+template <> __device__ __forceinline__ float key_f32<LS_U64>(uint64_t u) { return __ull2float_rz(u); }
+template <> __device__ __forceinline__ float key_f32<LS_U32>(uint32_t u) { return __uint2float_rz(u); }
+
+struct CellRoot {          // FP32 RMI of the cell index, on key_f32(x)
+  float A0, B0;            // w = A0 x + B0 = L * root(x)
+  int L;
+  int pad;
+};
+struct CellLeaf {          // F = clamp(A x + B, LO, HI), HI_l = LO_{l+1}
+  float A, B, LO, HI;
+};
+
+// FP32 estimate of F on key_f32(x) (non-decreasing in the key: a >= 0 slopes,
+// clamps with HI_l = LO_{l+1}); NaNs take 0 / 1 by sign.
 template <int DT>
-__device__ __forceinline__ uint32_t bucket_of(typename KT<DT>::U u, const RootEval& r,
-                                              const LeafL0* __restrict__ l0, uint32_t f0) {
-  const uint32_t b = bucket_of_t0(root_t0<DT>(u, r), r, l0);
-  return KT<DT>::is_nan(u) ? (KT<DT>::neg(u) ? 0u : f0 - 1) : b;
+__device__ __forceinline__ float cell_F(typename KT<DT>::U u, const CellRoot& c,
+                                        const CellLeaf* __restrict__ leaves) {
+  const float x = key_f32<DT>(u);
+  const float w = c.A0 == 0.0f ? c.B0 : __fmaf_rn(c.A0, x, c.B0);
+  const int l = w >= 0.0f ? (w < (float)c.L ? (int)w : c.L - 1) : 0;
+  const CellLeaf q = leaves[l];
+  float F = q.A == 0.0f ? q.B : __fmaf_rn(q.A, x, q.B);
+  F = fminf(fmaxf(F, q.LO), q.HI);
+  if (KT<DT>::is_nan(u)) F = KT<DT>::neg(u) ? 0.0f : 1.0f;
+  return F;
+}
+
+// Cell of a key: clamp(floor(F32(x) * L0_CELLS)).
+template <int DT>
+__device__ __forceinline__ uint32_t cell_of(typename KT<DT>::U u, const CellRoot& c,
+                                            const CellLeaf* __restrict__ leaves) {
+  const float v = cell_F<DT>(u, c, leaves) * (float)L0_CELLS;
+  return v >= 0.0f ? (v < (float)L0_CELLS ? (uint32_t)v : L0_CELLS - 1) : 0u;
+}
+
+// Level-0 lookup tables (device or shared memory copies).
+struct L0Map {
+  const uint64_t* thr;     // f0 thresholds (thr[0] = 0)
+  const uint32_t* cell;    // L0_CELLS entries: lo | hi << 16 (bucket range)
+  const CellLeaf* cleaf;   // L cell-index leaves
+  CellRoot croot;
+  uint32_t pos_max;        // bucket of the largest total-order key
+};
+
+// Largest b in [lo, hi] with thr[b] <= t (thr[lo] <= t holds).
+__device__ __forceinline__ uint32_t thr_search(const uint64_t* thr, uint32_t lo, uint32_t hi,
+                                               uint64_t t) {
+  uint32_t b = lo;
+  for (uint32_t s = hi > lo ? 1u << (31 - __clz((int)(hi - lo))) : 0u; s; s >>= 1) {
+    const uint32_t nb = b + s;
+    if (nb <= hi && thr[nb] <= t) b = nb;
+  }
+  return b;
+}
+
+// Level-0 bucket of a key (NaNs and infinities included: the thresholds cover
+// the whole total order).
+template <int DT>
+__device__ __forceinline__ uint32_t l0_bucket(typename KT<DT>::U u, const L0Map& q) {
+  const uint32_t c = q.cell[cell_of<DT>(u, q.croot, q.cleaf)];
+  const uint32_t b = thr_search(q.thr, c & 0xFFFFu, c >> 16, KT<DT>::tk(u));
+  return min(b, q.pos_max);
 }
 
 // Extended slot: regular bucket b with heavies h_1<..<h_k has slots
 // ext_base + {0: <h_1, 1: =h_1, 2: (h_1,h_2), ..., 2k: >h_k}.  `htk` holds the
 // heavy values' total-order keys (bucket b's at [hoff, hoff + nh)).  Returns
-// the slot; *bucket gets b.
+// the slot; *bucket gets b and *nheavy its heavy count.
 template <int DT>
-__device__ __forceinline__ uint32_t ext_of2(typename KT<DT>::U u, const RootEval& r,
-                                            const LeafL0* __restrict__ lc,
+__device__ __forceinline__ uint32_t ext_of2(typename KT<DT>::U u, const L0Map& q,
                                             const BucketHead* __restrict__ heads,
-                                            const uint64_t* __restrict__ htk, uint32_t f0,
-                                            uint32_t* bucket, uint32_t* nheavy = nullptr) {
-  const uint32_t b = bucket_of<DT>(u, r, lc, f0);
+                                            const uint64_t* __restrict__ htk, uint32_t* bucket,
+                                            uint32_t* nheavy = nullptr) {
+  const uint64_t t = KT<DT>::tk(u);
+  const uint32_t b = l0_bucket<DT>(u, q);
   *bucket = b;
   const BucketHead h = heads[b];
   uint32_t e = h.ext_base;
   const uint32_t nh = h.hoff_nh & 15u;
   if (nheavy) *nheavy = nh;
   if (nh) {
-    const uint64_t t = KT<DT>::tk(u);
     const uint32_t ho = h.hoff_nh >> 4;
     for (uint32_t j = 0; j < nh; ++j) {
       const uint64_t hv = htk[ho + j];
@@ -253,12 +312,11 @@ __device__ __forceinline__ uint32_t ext_of2(typename KT<DT>::U u, const RootEval
 }
 
 template <int DT>
-__device__ __forceinline__ uint32_t ext_of(typename KT<DT>::U u, const RootEval& r,
-                                           const LeafL0* __restrict__ lc,
+__device__ __forceinline__ uint32_t ext_of(typename KT<DT>::U u, const L0Map& q,
                                            const BucketHead* __restrict__ heads,
-                                           const uint64_t* __restrict__ htk, uint32_t f0) {
+                                           const uint64_t* __restrict__ htk) {
   uint32_t b;
-  return ext_of2<DT>(u, r, lc, heads, htk, f0, &b);
+  return ext_of2<DT>(u, q, heads, htk, &b);
 }
 
 // ------------------------------------------------------------------ jobs
@@ -360,19 +418,25 @@ cudaError_t status_word_ptr(uint32_t** out);
 
 // Model storage in device memory (one per sort call / array).
 struct DevModel {
-  RootEval root;           // FP32 evaluation of the root
+  RootEval root;           // integer routing of the fine evaluation
   double root64[3];        // a, c, b
   uint64_t s, s_fin, s_lo; // sample size, finite keys, index of first finite
   uint32_t nheavy;
   uint32_t n_ext;
   uint64_t tau;
-  double f_dummy;
+  CellRoot croot;          // level-0 cell index (FP32 root)
+  uint32_t cell_span;      // widest bucket range of a cell
+  uint32_t pos_max;        // bucket of the largest total-order key
 };
+
+__device__ __forceinline__ uint32_t bitlen32(uint32_t v) { return v ? 32u - __clz((int)v) : 0u; }
 
 struct ModelPtrs {         // device pointers of one model
   DevModel* hdr;
   double* leaf64;          // 5 * L
-  LeafL0* leafc;           // L (integer level-0 records)
+  uint64_t* thr;           // f0 level-0 thresholds
+  uint32_t* cell;          // L0_CELLS level-0 cell table
+  CellLeaf* cleaf;         // L cell-index leaves
   LeafFine* leaff;         // L + 1 (sentinel record L: LO = 1)
   BucketHead* heads;       // f0 + 1
   HeavyEntry* heavy;       // max heavy

@@ -25,20 +25,28 @@
 namespace ls {
 
 struct L0Layout {
-  uint32_t bar, buf, leaves, heads, htk, cnt, bcnt, boff, ecnt, cursor, sdst, ws, total;
+  uint32_t bar, buf, thr, cell, cleaf, heads, htk, cnt, bcnt, boff, ecnt, cursor, sdst, ws, total;
 };
 
 // Shared-memory layout of the level-0 kernels.  hmax: heavy values; the
 // scatter keeps counters and cursors for the f0 + hmax non-equality slots.
+// The cell-index leaves stay in global memory (read through L1) when the
+// shared copy would not fit.
+constexpr size_t L0_SMEM_LIMIT = 227 * 1024;
+constexpr uint32_t NOT_SHARED = 0xFFFFFFFFu;
+
 static L0Layout l0_layout(int W, uint32_t L, uint32_t f0, uint32_t next, uint32_t hmax,
-                          bool scatter) {
+                          bool scatter, bool cleaf_shared = true) {
   L0Layout y{};
   size_t o = 0;
   auto al = [&](size_t a) { o = (o + a - 1) / a * a; };
   y.bar = (uint32_t)o; o += 16;
   al(128); y.buf = (uint32_t)o; o += 2ull * P_TILE * W;
-  al(16); y.leaves = (uint32_t)o; o += (size_t)L * sizeof(LeafL0);
-  y.heads = (uint32_t)o; o += (size_t)(f0 + 1) * sizeof(BucketHead);
+  al(16); y.thr = (uint32_t)o; o += (size_t)f0 * 8;
+  y.cell = (uint32_t)o; o += (size_t)L0_CELLS * 4;
+  y.cleaf = NOT_SHARED;
+  if (cleaf_shared) { al(16); y.cleaf = (uint32_t)o; o += (size_t)L * sizeof(CellLeaf); }
+  al(16); y.heads = (uint32_t)o; o += (size_t)(f0 + 1) * sizeof(BucketHead);
   y.htk = (uint32_t)o; o += (size_t)hmax * 8;
   if (!scatter) {
     y.cnt = (uint32_t)o; o += (size_t)(next + 1) * 4;
@@ -52,6 +60,7 @@ static L0Layout l0_layout(int W, uint32_t L, uint32_t f0, uint32_t next, uint32_
   }
   al(8); y.ws = (uint32_t)o; o += 33 * 8;
   y.total = (uint32_t)o;
+  if (cleaf_shared && o > L0_SMEM_LIMIT) return l0_layout(W, L, f0, next, hmax, scatter, false);
   return y;
 }
 
@@ -73,12 +82,22 @@ __device__ __forceinline__ void chunk_of(const Chunking& c, uint32_t g, uint64_t
   *e = ce;
 }
 
-template <int DT>
-__device__ __forceinline__ void load_tables(const Level0Args& a, LeafL0* leaves, BucketHead* heads,
-                                            uint64_t* htk, uint32_t H) {
-  for (uint32_t i = threadIdx.x; i < a.L; i += blockDim.x) leaves[i] = a.M.leafc[i];
+// Shared-memory copies of the level-0 tables; returns the lookup over them.
+__device__ __forceinline__ L0Map load_tables(const Level0Args& a, unsigned char* sm,
+                                             const L0Layout& lay, uint32_t H) {
+  uint64_t* thr = (uint64_t*)(sm + lay.thr);
+  uint32_t* cell = (uint32_t*)(sm + lay.cell);
+  CellLeaf* cleaf = lay.cleaf == NOT_SHARED ? a.M.cleaf : (CellLeaf*)(sm + lay.cleaf);
+  BucketHead* heads = (BucketHead*)(sm + lay.heads);
+  uint64_t* htk = (uint64_t*)(sm + lay.htk);
+  for (uint32_t i = threadIdx.x; i < a.f0; i += blockDim.x) thr[i] = a.M.thr[i];
+  for (uint32_t i = threadIdx.x; i < L0_CELLS; i += blockDim.x) cell[i] = a.M.cell[i];
+  if (lay.cleaf != NOT_SHARED)
+    for (uint32_t i = threadIdx.x; i < a.L; i += blockDim.x) cleaf[i] = a.M.cleaf[i];
   for (uint32_t i = threadIdx.x; i <= a.f0; i += blockDim.x) heads[i] = a.M.heads[i];
   for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) htk[i] = a.M.heavy[i].tk;
+  const DevModel* h = a.M.hdr;
+  return L0Map{thr, cell, cleaf, h->croot, h->pos_max};
 }
 
 // ---------------------------------------------------------------- K2
@@ -88,11 +107,9 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
   extern __shared__ __align__(128) unsigned char sm[];
   uint64_t* bar = (uint64_t*)(sm + lay.bar);
   U* buf = (U*)(sm + lay.buf);
-  LeafL0* leaves = (LeafL0*)(sm + lay.leaves);
   BucketHead* heads = (BucketHead*)(sm + lay.heads);
   uint32_t* cnt = (uint32_t*)(sm + lay.cnt);
   const U* keys = (const U*)a.keys;
-  const RootEval r = a.M.hdr->root;
   const uint32_t next = min(a.M.hdr->n_ext, a.n_ext_max);
   uint64_t* heavy = (uint64_t*)(sm + lay.htk);
   const uint32_t H = min(a.M.hdr->nheavy, (next - a.f0) / 2);
@@ -103,7 +120,7 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
   if (threadIdx.x == 0) ts.init();
   __syncthreads();
   if (threadIdx.x == 0) { ts.issue(0); ts.issue(1); }
-  load_tables<DT>(a, leaves, heads, heavy, H);
+  const L0Map q = load_tables(a, sm, lay, H);
   for (uint32_t i = threadIdx.x; i < next; i += H_THREADS) cnt[i] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -111,7 +128,7 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
     const uint64_t nht = a.c.a0 + (a.c.n - a.c.a1);
     for (uint64_t k = threadIdx.x; k < nht; k += H_THREADS) {
       const uint64_t i = k < a.c.a0 ? k : a.c.a1 + (k - a.c.a0);
-      const uint32_t e = ext_of<DT>(keys[i], r, leaves, heads, heavy, a.f0);
+      const uint32_t e = ext_of<DT>(keys[i], q, heads, heavy);
       if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
     }
   }
@@ -125,12 +142,12 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
 #pragma unroll
       for (int k = 0; k < KPT; ++k) u[k] = tb[k * H_THREADS + threadIdx.x];
 #pragma unroll
-      for (int k = 0; k < KPT; ++k) e[k] = ext_of<DT>(u[k], r, leaves, heads, heavy, a.f0);
+      for (int k = 0; k < KPT; ++k) e[k] = ext_of<DT>(u[k], q, heads, heavy);
     } else {
 #pragma unroll
       for (int k = 0; k < KPT; ++k) {
         const uint32_t i = k * H_THREADS + threadIdx.x;
-        e[k] = i < c ? ext_of<DT>(tb[i], r, leaves, heads, heavy, a.f0) : 0xFFFFFFFFu;
+        e[k] = i < c ? ext_of<DT>(tb[i], q, heads, heavy) : 0xFFFFFFFFu;
       }
     }
 #pragma unroll
@@ -161,7 +178,6 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
   extern __shared__ __align__(128) unsigned char sm[];
   uint64_t* bar = (uint64_t*)(sm + lay.bar);
   U* buf = (U*)(sm + lay.buf);
-  LeafL0* leaves = (LeafL0*)(sm + lay.leaves);
   BucketHead* heads = (BucketHead*)(sm + lay.heads);
   uint64_t* heavy = (uint64_t*)(sm + lay.htk);
   uint32_t* bcnt = (uint32_t*)(sm + lay.bcnt);
@@ -173,7 +189,6 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
   const U* keys = (const U*)a.keys;
   U* out = (U*)a.scratch;
   const uint64_t n = a.c.n;
-  const RootEval r = a.M.hdr->root;
   const uint32_t next = min(a.M.hdr->n_ext, a.n_ext_max);
   const uint32_t f0 = a.f0;
   const uint32_t H = min(a.M.hdr->nheavy, (next - f0) / 2);
@@ -185,7 +200,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
   if (threadIdx.x == 0) ts.init();
   __syncthreads();
   if (threadIdx.x == 0) { ts.issue(0); ts.issue(1); }
-  load_tables<DT>(a, leaves, heads, heavy, H);
+  const L0Map q = load_tables(a, sm, lay, H);
   for (uint32_t i = threadIdx.x; i < f0; i += P_THREADS) bcnt[i] = 0;
   for (uint32_t i = threadIdx.x; i < nc; i += P_THREADS) ecnt[i] = 0;
   __syncthreads();
@@ -204,7 +219,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
       const uint64_t i = k < a.c.a0 ? k : a.c.a1 + (k - a.c.a0);
       const U u = keys[i];
       uint32_t b;
-      const uint32_t e = ext_of2<DT>(u, r, leaves, heads, heavy, f0, &b);
+      const uint32_t e = ext_of2<DT>(u, q, heads, heavy, &b);
       if (e >= next) { set_error(a.err, ERR_BOUNDS); continue; }
       if ((e - b) & 1u) continue;  // equality slot: filled later
       const uint32_t c = (e + b) >> 1;
@@ -223,15 +238,14 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
       for (int k = 0; k < KPT; ++k) u[k] = tb[k * P_THREADS + threadIdx.x];
 #pragma unroll
       for (int k = 0; k < KPT; ++k)
-        e[k] = ext_of2<DT>(u[k], r, leaves, heads, heavy, f0, &bk[k], &nh[k]);
+        e[k] = ext_of2<DT>(u[k], q, heads, heavy, &bk[k], &nh[k]);
     } else {
 #pragma unroll
       for (int k = 0; k < KPT; ++k) {
         const uint32_t i = k * P_THREADS + threadIdx.x;
         u[k] = i < cnt_t ? tb[i] : (U)0;
         nh[k] = 0;
-        e[k] = i < cnt_t ? ext_of2<DT>(u[k], r, leaves, heads, heavy, f0, &bk[k], &nh[k])
-                         : 0xFFFFFFFFu;
+        e[k] = i < cnt_t ? ext_of2<DT>(u[k], q, heads, heavy, &bk[k], &nh[k]) : 0xFFFFFFFFu;
       }
     }
     uint32_t cc[KPT], rk[KPT], sr[KPT];
@@ -317,7 +331,6 @@ __global__ void k_classify0(Level0Args a, Lists lists, SortLimits lim) {
     job.Flo = (j == 0) ? (double)b / (double)a.f0 : (double)heavy[hoff + j - 1].F;
     job.Fhi = (j == nh) ? (double)(b + 1) / (double)a.f0 : (double)heavy[hoff + j].F;
     job.la = job.lb = 0;
-    if (size <= lim.c_large) leaf_range(a.M.leaf64, (int)a.L, job.Flo, job.Fhi, &job.la, &job.lb);
     if (size <= lim.c_small) { job.kind = JOB_SORT; push_job(lists.sort_s, job, a.err); }
     else if (size <= lim.c_large) { job.kind = JOB_SORT; push_job(lists.sort_l, job, a.err); }
     else { job.kind = JOB_REFINE; push_job(lists.refine, job, a.err); }
@@ -396,7 +409,10 @@ k_l1_plan(LevelArgs la, SortLimits lim, Level1Ws w, uint32_t* err) {
     float S = 0, T = 0;
     if (j < nj) {
       Job job = la.in.jobs[j];
-      uint64_t f = (job.m + lim.l1_target - 1) / lim.l1_target;
+      // the model's split aims at l1_target keys per sub-bucket; a key-range
+      // split (its input is skewed or clustered) uses 16x finer sub-buckets
+      const uint64_t tg = la.mode ? (lim.l1_target >> 4) : lim.l1_target;
+      uint64_t f = (job.m + tg - 1) / tg;
       f = f < 2 ? 2 : (f > MAX_F1 ? MAX_F1 : f);
       bool ok = true;
       if (la.mode == 0) {
@@ -462,11 +478,12 @@ __device__ __forceinline__ uint64_t aux_find_c(const L1Aux* aux, uint64_t nj, ui
   return lo - 1;
 }
 
+// Level-1 sub-bucket (Alg. 2's re-partition with the model): the FP32
+// estimate of F scaled onto the job's f1 sub-buckets.
 template <int DT>
-__device__ __forceinline__ uint32_t l1_sub(typename KT<DT>::U u, const RootEval& r,
-                                           const LeafFine* lf, const L1Aux& x) {
-  if (KT<DT>::is_nan(u)) return KT<DT>::neg(u) ? 0u : x.f1 - 1;
-  const float F = predict_F<DT>(u, r, lf);
+__device__ __forceinline__ uint32_t l1_sub(typename KT<DT>::U u, const CellRoot& cr,
+                                           const CellLeaf* cl, const L1Aux& x) {
+  const float F = cell_F<DT>(u, cr, cl);
   const float v = __fmaf_rn(F, x.S, x.T);
   if (!(v > 0.0f)) return 0u;
   if (v >= (float)(x.f1 - 1)) return x.f1 - 1;
@@ -515,10 +532,13 @@ k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Mod
   typedef typename KT<DT>::U U;
   __shared__ uint32_t hc[MAX_F1];
   __shared__ unsigned long long s_min, s_max;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  CellLeaf* cl = (CellLeaf*)dsm;  // M.L cell-index leaves
   const L1Aux* aux = (const L1Aux*)w.aux;
   const uint64_t T = w.totals[0], nj = w.totals[2];
-  const RootEval r = M.hdr->root;
-  const LeafFine* lf = M.leaff;
+  const CellRoot cr = M.hdr->croot;
+  for (int i = threadIdx.x; i < M.L; i += blockDim.x) cl[i] = M.cleaf[i];
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
     const uint64_t j = aux_find_tile(aux, nj, t);
@@ -544,7 +564,7 @@ k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Mod
         } else {
           mn = min(mn, (unsigned long long)tk);
           mx = max(mx, (unsigned long long)tk);
-          sub = l1_sub<DT>(u, r, lf, x);
+          sub = l1_sub<DT>(u, cr, cl, x);
         }
       }
       if (sub != 0xFFFFFFFFu) atomicAdd(&hc[sub], 1u);
@@ -591,10 +611,12 @@ k_l1_scatter(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, uint64_t n, 
   extern __shared__ __align__(16) unsigned char dsm[];
   U* stage = (U*)dsm;                                      // L1_TILE keys
   uint16_t* ids = (uint16_t*)(dsm + sizeof(U) * L1_TILE);  // L1_TILE slot ids
+  CellLeaf* cl = (CellLeaf*)(dsm + (size_t)(sizeof(U) + 2) * L1_TILE);  // M.L leaves
   const L1Aux* aux = (const L1Aux*)w.aux;
   const uint64_t T = w.totals[0], nj = w.totals[2];
-  const RootEval r = M.hdr->root;
-  const LeafFine* mlf = M.leaff;
+  const CellRoot cr = M.hdr->croot;
+  for (int i = threadIdx.x; i < M.L; i += blockDim.x) cl[i] = M.cleaf[i];
+  __syncthreads();
   for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
     const uint64_t j = aux_find_tile(aux, nj, t);
     if (w.jmin[j] == w.jmax[j]) continue;  // homogeneous: filled, not moved
@@ -617,7 +639,7 @@ k_l1_scatter(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, uint64_t n, 
       u[k] = 0;
       if (i < c) {
         u[k] = src[i];
-        sub = la.mode ? range_sub(KT<DT>::tk(u[k]), rs) : l1_sub<DT>(u[k], r, mlf, x);
+        sub = la.mode ? range_sub(KT<DT>::tk(u[k]), rs) : l1_sub<DT>(u[k], cr, cl, x);
       }
       sb[k] = sub;
       rk[k] = sub != 0xFFFFFFFFu ? atomicAdd(&lc[sub], 1u) : 0u;
@@ -681,8 +703,6 @@ __global__ void k_l1_classify(Lists lists, LevelArgs la, SortLimits lim, Level1W
     }
     job.src = pj.src ^ 1u;
     job.la = job.lb = 0;
-    if (la.mode == 0 && cntc <= lim.c_large)
-      leaf_range(M.leaf64, L, job.Flo, job.Fhi, &job.la, &job.lb);
     const uint32_t sk = la.mode ? JOB_SORT_RANGE : JOB_SORT;
     if (cntc <= lim.c_small) { job.kind = sk; push_job(lists.sort_s, job, err); }
     else if (cntc <= lim.c_large) { job.kind = sk; push_job(lists.sort_l, job, err); }
@@ -713,7 +733,10 @@ static cudaError_t level0_dt(const Level0Args& a, size_t sh, size_t ss, const Li
   return cudaGetLastError();
 }
 
-static size_t l1_scatter_smem(int W) { return (size_t)L1_TILE * (W + 2); }
+static size_t l1_scatter_smem(int W, int L) {
+  return (size_t)L1_TILE * (W + 2) + (size_t)L * sizeof(CellLeaf);
+}
+static size_t l1_hist_smem(int L) { return (size_t)L * sizeof(CellLeaf); }
 
 cudaError_t level0_configure(int dt, size_t sh, size_t ss) {
   cudaError_t e = cudaSuccess;
@@ -721,7 +744,10 @@ cudaError_t level0_configure(int dt, size_t sh, size_t ss) {
   e = cudaFuncSetAttribute(k_l0_hist<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh); \
   if (e) return e;                                                                              \
   e = cudaFuncSetAttribute(k_l1_scatter<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
-                           (int)l1_scatter_smem(KT<D>::W));                                     \
+                           (int)l1_scatter_smem(KT<D>::W, MAX_LEAVES));                         \
+  if (e) return e;                                                                              \
+  e = cudaFuncSetAttribute(k_l1_hist<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                           (int)l1_hist_smem(MAX_LEAVES));                                      \
   if (e) return e;                                                                              \
   e = cudaFuncSetAttribute(k_l0_scatter<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
   switch (dt) {
@@ -757,14 +783,15 @@ static cudaError_t level_dt(void* keys, void* scratch, uint64_t n, const ModelPt
   k_l1_plan<<<1, 1024, 0, st>>>(la, lim, w, err);
   const int grid = 2 * num_sms;
   if (la.mode) k_l1_minmax<DT><<<grid, L1_THREADS, 0, st>>>((const U*)keys, (const U*)scratch, la, w);
-  k_l1_hist<DT><<<grid, L1_THREADS, 0, st>>>((const U*)keys, (const U*)scratch, M, la, w);
+  k_l1_hist<DT><<<grid, L1_THREADS, l1_hist_smem(M.L), st>>>((const U*)keys, (const U*)scratch, M,
+                                                            la, w);
   const unsigned tiles = (unsigned)std::max<uint64_t>(1, (w.cap_c + SC_TILE - 1) / SC_TILE);
   k_scan<uint32_t><<<tiles, SC_THREADS, 0, st>>>(w.cnt, w.off, w.cap_c, &w.totals[1],
                                                  (uint64_t*)w.scan_status,
                                                  (uint32_t*)((uint64_t*)w.scan_status + tiles), err);
   k_l1_cursor<<<grid, 256, 0, st>>>(la, w);
-  k_l1_scatter<DT><<<grid, L1_THREADS, l1_scatter_smem(KT<DT>::W), st>>>((U*)keys, (U*)scratch,
-                                                                      n, M, la, w, err);
+  k_l1_scatter<DT><<<grid, L1_THREADS, l1_scatter_smem(KT<DT>::W, M.L), st>>>(
+      (U*)keys, (U*)scratch, n, M, la, w, err);
   k_l1_classify<DT><<<grid, 256, 0, st>>>(lists, la, lim, w, M, M.L, err);
   add_launches(la.mode ? 7 : 6);
   return cudaGetLastError();

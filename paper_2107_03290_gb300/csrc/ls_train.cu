@@ -289,13 +289,11 @@ __device__ __forceinline__ long long floor_scaled(double v, int k, double lo, do
   return (long long)w;
 }
 
-// Empty leaves, hi bounds, and the evaluation parameters (level-0 integer
-// tables and fine FP32 records).
+// Empty leaves, hi bounds, and the fine FP32 evaluation records.
 template <int DT>
 __global__ void __launch_bounds__(1024)
-k_fit_final(const uint64_t* __restrict__ tk, DevModel* hdr, int L, uint32_t f0,
-            const uint32_t* leaf_beg, const uint32_t* leaf_end, double* leaf, LeafL0* l0,
-            LeafFine* lf) {
+k_fit_final(const uint64_t* __restrict__ tk, DevModel* hdr, int L, const uint32_t* leaf_beg,
+            const uint32_t* leaf_end, double* leaf, LeafFine* lf, CellLeaf* cleaf) {
   __shared__ int s_E, s_P0;
   __shared__ long long s_C0;
   const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
@@ -348,12 +346,16 @@ k_fit_final(const uint64_t* __restrict__ tk, DevModel* hdr, int L, uint32_t f0,
       re.RA = (int)floor_scaled(__dmul_rn(r[0], (double)L), P0 + 40, 0.0, INT31);
       re.RB = floor_scaled(__dmul_rn(r[2], (double)L), 40, -9.0e18, 9.0e18);
       hdr->root = re;
+      CellRoot cr;  // L * root(x) = L a x + L (b - a c), rounded to FP32
+      cr.A0 = fp32_sat(__dmul_rn((double)L, r[0]));
+      cr.B0 = fp32_sat(__dmul_rn((double)L, __dsub_rn(r[2], __dmul_rn(r[0], r[1]))));
+      cr.L = L;
+      cr.pad = 0;
+      hdr->croot = cr;
     }
   }
   __syncthreads();
-  const int E = s_E, P0 = s_P0;
-  const long long C0 = s_C0;
-  const double f0d = (double)f0;
+  const int E = s_E;
   for (int l = threadIdx.x; l <= L; l += blockDim.x) {
     if (l == L) {  // sentinel: HI of the last leaf
       LeafFine f;
@@ -362,14 +364,10 @@ k_fit_final(const uint64_t* __restrict__ tk, DevModel* hdr, int L, uint32_t f0,
       continue;
     }
     const double* q = leaf + 5 * (size_t)l;
-    LeafL0 c;
     LeafFine f;
     f.pad0 = f.pad1 = 0;
-    const long long BL = floor_scaled(__dmul_rn(q[2], f0d), 32, -9.0e18, 9.0e18);
     const uint32_t b = leaf_beg[l], en = leaf_end[l];
     if (en <= b) {
-      c.AL = 0;
-      c.BL = BL;
       f.C = 0; f.P = E; f.A = 0.0f;
     } else {
       const uint64_t cb = (uint64_t)__double_as_longlong(q[1]);
@@ -381,18 +379,120 @@ k_fit_final(const uint64_t* __restrict__ tk, DevModel* hdr, int L, uint32_t f0,
       f.P = P;
       f.C = fx_f64bits(cb, P);
       f.A = fp32_sat(ldexp(q[0], P));
-      const int tc = feat32(fx_f64bits(cb, P0), C0, T0_LIM);
-      c.AL = (int)floor_scaled(__dmul_rn(q[0], f0d), P0 + 32, 0.0, INT31);
-      c.BL = BL - (long long)c.AL * (long long)tc;
     }
-    const double lob = fmin(floor(__dmul_rn(q[3], f0d)), f0d - 1.0);
-    const double hib = fmin(floor(__dmul_rn(q[4], f0d)), f0d - 1.0);
-    c.lohi = (uint32_t)lob | ((uint32_t)hib << 16);
     f.B = __double2float_rn(q[2]);
     f.LO = __double2float_rn(q[3]);
-    l0[l] = c;
     lf[l] = f;
+    CellLeaf cl;
+    cl.A = fp32_sat(q[0]);
+    cl.B = fp32_sat(__dsub_rn(q[2], __dmul_rn(q[0], q[1])));
+    cl.LO = __double2float_rn(q[3]);
+    cl.HI = __double2float_rn(q[4]);
+    cleaf[l] = cl;
   }
+}
+
+// ---------------------------------------------------------------- level-0 thresholds
+// The model in FP64, operation for operation: lin = a == 0 ? b : fma(a, x - c, b);
+// leaf = clamp(floor(L * lin_root)); F = clamp(lin_leaf, lo, hi) (Sec. 2, Alg. 1).
+__device__ __forceinline__ double lin64(double a, double x, double c, double b) {
+  return a == 0.0 ? b : __fma_rn(a, __dsub_rn(x, c), b);
+}
+__device__ __forceinline__ double predict64(const double* r, const double* leaf, int L, double x) {
+  const double w = __dmul_rn((double)L, lin64(r[0], x, r[1], r[2]));
+  const int l = !(w >= 0.0) ? 0 : (w >= (double)L ? L - 1 : (int)floor(w));
+  const double* q = leaf + 5 * (size_t)l;
+  const double v = lin64(q[0], x, q[1], q[2]);
+  if (!(v >= q[3])) return q[3];
+  return v > q[4] ? q[4] : v;
+}
+// pos(t) = clamp(floor(F(x) * f0), 0, f0 - 1) for the key with total-order key t;
+// NaNs take F = 0 / 1 by sign.
+template <int DT>
+__device__ __forceinline__ uint32_t pos64(uint64_t t, const double* r, const double* leaf, int L,
+                                          uint32_t f0) {
+  const typename KT<DT>::U u = KT<DT>::from_tk(t);
+  double F;
+  if (KT<DT>::is_nan(u)) F = KT<DT>::neg(u) ? 0.0 : 1.0;
+  else F = predict64(r, leaf, L, KT<DT>::dbl(u));
+  const double w = __dmul_rn(F, (double)f0);
+  if (!(w >= 0.0)) return 0u;
+  if (w >= (double)f0) return f0 - 1;
+  return (uint32_t)floor(w);
+}
+template <int DT> struct TkRange {
+  static constexpr uint64_t MAX = KT<DT>::W == 8 ? ~0ull : 0xFFFFFFFFull;
+  static constexpr uint64_t NEVER = KT<DT>::W == 8 ? ~0ull : 0x100000000ull;
+};
+
+// thr[b] = min { t : pos(t) >= b } by bisection over the whole total order
+// (pos is non-decreasing in t); thread f0 records the bucket of the largest key.
+template <int DT>
+__global__ void __launch_bounds__(128)
+k_thresholds(DevModel* hdr, const double* __restrict__ leaf, int L, uint32_t f0, uint64_t* thr) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b > f0) return;
+  const double r[3] = {hdr->root64[0], hdr->root64[1], hdr->root64[2]};
+  const uint64_t TMAX = TkRange<DT>::MAX;
+  if (b == f0) {
+    hdr->pos_max = pos64<DT>(TMAX, r, leaf, L, f0);
+    hdr->cell_span = 0;
+    return;
+  }
+  if (b == 0) { thr[0] = 0; return; }
+  if (pos64<DT>(TMAX, r, leaf, L, f0) < b) { thr[b] = TkRange<DT>::NEVER; return; }
+  uint64_t lo = 0, hi = TMAX;
+  while (lo < hi) {
+    const uint64_t mid = lo + ((hi - lo) >> 1);
+    if (pos64<DT>(mid, r, leaf, L, f0) >= b) hi = mid; else lo = mid + 1;
+  }
+  thr[b] = lo;
+}
+
+// #{ b in [1, f0) : thr[b] <= t }
+__device__ __forceinline__ uint32_t thr_count(const uint64_t* thr, uint32_t f0, uint64_t t) {
+  uint32_t lo = 1, hi = f0;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (thr[mid] <= t) lo = mid + 1; else hi = mid;
+  }
+  return lo - 1;
+}
+
+// Smallest total-order key whose cell is >= c (NEVER if there is none).
+template <int DT>
+__device__ __forceinline__ uint64_t cell_start(uint32_t c, const CellRoot& cr,
+                                               const CellLeaf* cleaf) {
+  const uint64_t TMAX = TkRange<DT>::MAX;
+  if (cell_of<DT>(KT<DT>::from_tk(TMAX), cr, cleaf) < c) return TkRange<DT>::NEVER;
+  uint64_t lo = 0, hi = TMAX;
+  while (lo < hi) {
+    const uint64_t mid = lo + ((hi - lo) >> 1);
+    if (cell_of<DT>(KT<DT>::from_tk(mid), cr, cleaf) >= c) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+// Cell table: for cell c, the bucket range [count(first key), count(last key)]
+// of the keys whose cell is c (the cell map is non-decreasing in the key).
+template <int DT>
+__global__ void k_cell_table(DevModel* hdr, const uint64_t* __restrict__ thr, uint32_t f0,
+                             const CellLeaf* __restrict__ cleaf, uint32_t* cell) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L0_CELLS) return;
+  const uint64_t TMAX = TkRange<DT>::MAX, NEVER = TkRange<DT>::NEVER;
+  const CellRoot cr = hdr->croot;
+  const uint64_t a = c ? cell_start<DT>(c, cr, cleaf) : 0ull;
+  const uint64_t e = c + 1 < L0_CELLS ? cell_start<DT>(c + 1, cr, cleaf) : NEVER;
+  uint32_t lo, hi;
+  if (a == NEVER || a > TMAX) {          // no key maps here
+    lo = hi = thr_count(thr, f0, TMAX);
+  } else {
+    lo = thr_count(thr, f0, a);
+    hi = (e == NEVER || e > TMAX) ? thr_count(thr, f0, TMAX) : (e > a ? thr_count(thr, f0, e - 1) : lo);
+  }
+  cell[c] = lo | (hi << 16);
+  atomicMax(&hdr->cell_span, hi - lo);
 }
 
 // ---------------------------------------------------------------- heavy set
@@ -422,11 +522,11 @@ struct Cand {
 template <int DT>
 __global__ void k_heavy_compact(const uint64_t* __restrict__ tk, const DevModel* hdr,
                                 const uint32_t* __restrict__ flags, const uint64_t* __restrict__ pos,
-                                const LeafL0* __restrict__ leaves, uint32_t f0, Cand* cand,
-                                uint64_t cand_cap) {
+                                const uint64_t* __restrict__ thr, const uint32_t* __restrict__ cell,
+                                const CellLeaf* __restrict__ cleaf, Cand* cand, uint64_t cand_cap) {
   const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
   const uint64_t* t = tk + lo;
-  const RootEval r = hdr->root;
+  const L0Map q{thr, cell, cleaf, hdr->croot, hdr->pos_max};
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < m;
        k += (uint64_t)gridDim.x * blockDim.x) {
     if (!flags[k]) continue;
@@ -441,7 +541,7 @@ __global__ void k_heavy_compact(const uint64_t* __restrict__ tk, const DevModel*
       Cand c;
       c.tk = v;
       c.len = a - k;
-      c.bucket = bucket_of<DT>(KT<DT>::from_tk(v), r, leaves, f0);
+      c.bucket = l0_bucket<DT>(KT<DT>::from_tk(v), q);
       c.pad = 0;
       cand[p] = c;
     }
@@ -486,13 +586,13 @@ __global__ void k_heavy_select(const Cand* __restrict__ cand, const uint64_t* nc
 template <int DT>
 __global__ void __launch_bounds__(1024)
 k_heavy_heads(const uint64_t* __restrict__ sel, const uint32_t* __restrict__ nh, uint32_t f0,
-              int hpb, DevModel* hdr, const LeafFine* __restrict__ leaves, BucketHead* heads,
+              int hpb, DevModel* hdr, const CellLeaf* __restrict__ cleaf, BucketHead* heads,
               HeavyEntry* heavy) {
   __shared__ uint32_t ws[33];
   __shared__ uint32_t s_run;
   if (threadIdx.x == 0) s_run = 0;
   __syncthreads();
-  const RootEval r = hdr->root;
+  const CellRoot cr = hdr->croot;
   for (uint32_t b0 = 0; b0 < f0; b0 += blockDim.x) {
     const uint32_t b = b0 + threadIdx.x;
     const uint32_t c = b < f0 ? nh[b] : 0;
@@ -507,7 +607,7 @@ k_heavy_heads(const uint64_t* __restrict__ sel, const uint32_t* __restrict__ nh,
       for (uint32_t j = 0; j < c; ++j) {
         HeavyEntry he;
         he.tk = sel[(size_t)b * hpb + j];
-        he.F = predict_F<DT>(KT<DT>::from_tk(he.tk), r, leaves);
+        he.F = cell_F<DT>(KT<DT>::from_tk(he.tk), cr, cleaf);
         he.pad = 0;
         heavy[hoff + j] = he;
       }
@@ -559,8 +659,10 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   }
   k_fit_leaf_final<DT><<<(L + 255) / 256, 256, 0, st>>>(W.smp_a, W.rank, M.hdr, M.leaf_beg,
                                                        M.leaf_end, W.ubase, W.units, L, M.leaf64);
-  k_fit_final<DT><<<1, 1024, 0, st>>>(W.smp_a, M.hdr, L, P.f0, M.leaf_beg, M.leaf_end, M.leaf64,
-                                      M.leafc, M.leaff);
+  k_fit_final<DT><<<1, 1024, 0, st>>>(W.smp_a, M.hdr, L, M.leaf_beg, M.leaf_end, M.leaf64,
+                                      M.leaff, M.cleaf);
+  k_thresholds<DT><<<(P.f0 + 1 + 127) / 128, 128, 0, st>>>(M.hdr, M.leaf64, L, P.f0, M.thr);
+  k_cell_table<DT><<<(L0_CELLS + 127) / 128, 128, 0, st>>>(M.hdr, M.thr, P.f0, M.cleaf, M.cell);
   // heavy values
   const uint64_t tau = P.tau;
   k_heavy_flags<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, M.hdr, tau, W.flags, s);
@@ -571,13 +673,13 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
                                                    (uint64_t*)W.scan_status,
                                                    (uint32_t*)((uint64_t*)W.scan_status + sblocks),
                                                    err);
-  k_heavy_compact<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, M.hdr, W.flags, W.cpos, M.leafc,
-                                                      P.f0, (Cand*)W.cand, W.cand_cap);
+  k_heavy_compact<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, M.hdr, W.flags, W.cpos, M.thr,
+                                                      M.cell, M.cleaf, (Cand*)W.cand, W.cand_cap);
   k_heavy_select<<<(P.f0 + 255) / 256, 256, 0, st>>>((const Cand*)W.cand, W.cpos + s, W.cand_cap,
                                                      P.f0, (int)P.hpb, W.sel, W.nh);
-  k_heavy_heads<DT><<<1, 1024, 0, st>>>(W.sel, W.nh, P.f0, (int)P.hpb, M.hdr, M.leaff, M.heads,
+  k_heavy_heads<DT><<<1, 1024, 0, st>>>(W.sel, W.nh, P.f0, (int)P.hpb, M.hdr, M.cleaf, M.heads,
                                         M.heavy);
-  add_launches(20);
+  add_launches(22);
   return cudaGetLastError();
 }
 

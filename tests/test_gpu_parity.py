@@ -183,6 +183,10 @@ def test_train_matches_oracle(dist):
         assert int(getattr(ev, k)[0]) == int(m[k]), k
     for k in oracle.EvalParams.FIELDS:
         assert np.array_equal(getattr(ev, k), m[k]), k
+    # level-0 thresholds: bisection of the FP64 bucket map over the total order
+    thr, pmax = oracle.spec_thresholds(oracle.EvalParams(gm, 256), oracle.dtype_name(keys))
+    assert np.array_equal(m["thr"], thr)
+    assert m["pos_max"] == pmax
     # heavy set from the sorted sample
     sorted_smp = np.sort(smp)
     fin = sorted_smp[np.isfinite(sorted_smp.astype(np.float64))] if sorted_smp.dtype.kind == "f" \

@@ -313,23 +313,61 @@ def _eval_for(a, L=128, f0=1000):
 
 
 @pytest.mark.parametrize("gen", ["normal", "gauss_mix", "zipf"])
-def test_spec_bucket_monotone_and_close_to_fp64(gen):
+def test_spec_bucket_monotone_and_thresholds(gen):
     a = {"normal": lambda: lsgen.normal_f64(100_000, 41),
          "gauss_mix": lambda: lsgen.gauss_mix_f64(100_000, 43),
          "zipf": lambda: lsgen.zipf_lognormal_f64(100_000, 44, k=3000)}[gen]()
     fm, smp, ev = _eval_for(a)
-    xs = np.sort(np.concatenate([a[:4000], [-np.inf, np.inf, 0.0, -0.0]]))
+    xs = np.sort(np.concatenate([a[:4000], [-np.inf, np.inf, 0.0, -0.0, np.nan, -np.nan]]))
+    xs = oracle.reference_sort(xs)
     b = oracle.spec_buckets(ev, xs).astype(np.int64)
     assert np.all(np.diff(b) >= 0) and b.min() >= 0 and b.max() <= 999
-    # the integer bucket map is floor(F * f0) up to the fixed-point rounding
+    # NaNs go to the end buckets by sign
+    tk = oracle.total_order_keys(xs)
+    assert b[0] == 0 and b[-1] == 999
+    # the bucket is the number of thresholds at or below the key (bisection
+    # over the total order agrees with the per-key evaluation)
+    thr, pmax = oracle.spec_thresholds(ev, "f64")
+    assert thr[0] == 0 and np.all(np.diff(thr.astype(object)) >= 0)
+    cnt = np.searchsorted(thr[1:], tk, side="right")
+    assert np.array_equal(np.minimum(cnt, pmax), b)
+    # just below each finite threshold the bucket is smaller
+    for bb in range(1, 1000, 97):
+        t = int(thr[bb])
+        key = lambda u: np.array([u], np.uint64).view(np.float64)
+        x_at = key(t & 0x7FFFFFFFFFFFFFFF if t >> 63 else (~t) & (2**64 - 1))
+        x_below = key((t - 1) & 0x7FFFFFFFFFFFFFFF if (t - 1) >> 63 else (~(t - 1)) & (2**64 - 1))
+        assert oracle.spec_buckets(ev, x_at)[0] >= bb > oracle.spec_buckets(ev, x_below)[0]
+    # Alg. 1 (Partition, level 0) puts the same number of keys in every bucket
+    part, sizes, _, _ = oracle.partition(a, fm, 0, 1000, 100)
+    allb = np.bincount(oracle.spec_buckets(ev, a).astype(np.int64), minlength=1000)
+    assert np.array_equal(sizes.astype(np.int64), allb)
+    # the fine FP32 estimate is monotone and close to the FP64 model
     F64 = np.array([fm.predict(float(x)) for x in xs])
-    exact = np.minimum(np.floor(F64 * 1000), 999)
-    assert np.mean(np.abs(b - exact) <= 1) > 0.995
     Ff = oracle.spec_F_fine(ev, xs)
-    assert np.all(np.diff(Ff) >= 0)
     fin = np.isfinite(xs)
+    assert np.all(np.diff(Ff[fin]) >= 0)
     assert np.median(np.abs(Ff[fin] - F64[fin])) < 1e-5
     assert np.max(np.abs(Ff[fin] - F64[fin])) < 1e-3
+
+
+@pytest.mark.parametrize("dt", ["f32", "u32", "u64"])
+def test_spec_thresholds_other_dtypes(dt):
+    n = 50_000
+    a = {"f32": lambda: lsgen.exponential_f32(n, 7),
+         "u32": lambda: lsgen.timestamp_u32(n, 8),
+         "u64": lambda: lsgen.uniform_u64(n, 9)}[dt]()
+    L = 64
+    fm = oracle.train(a, oracle.params(leaves=L))
+    ev = oracle.EvalParams(fm, 100)
+    thr, pmax = oracle.spec_thresholds(ev, dt)
+    xs = oracle.reference_sort(a[:3000])
+    b = oracle.spec_buckets(ev, xs).astype(np.int64)
+    assert np.all(np.diff(b) >= 0)
+    cnt = np.searchsorted(thr[1:], oracle.total_order_keys(xs), side="right")
+    assert np.array_equal(np.minimum(cnt, pmax), b)
+    if dt != "u64":
+        assert int(thr.max()) <= 2**32
 
 
 def test_spec_heavy_and_ext_histogram():
