@@ -113,6 +113,7 @@ struct Plan {
   Chunking c;
   SortLimits lim;
   uint64_t cap0, cap1, cap_c, cap_r, capj;
+  uint32_t kf;
   size_t smem_hist, smem_scatter;
   uint32_t l0_scan_tiles;
 };
@@ -159,7 +160,9 @@ static void plan_call(const ls_params* prm, int dt, uint64_t n, uintptr_t addr, 
     P->tau = std::max<uint64_t>(2, (uint64_t)(num / n));
   }
   // chunking of the aligned body
-  const uint64_t V = 16 / P->W;
+  // body: 16-byte aligned keys, a multiple of 4 keys per chunk so that the
+  // 4-byte ids of a chunk are 16-byte aligned too
+  const uint64_t V = 4;
   uint64_t a0 = ((16 - (addr & 15)) & 15) / P->W;
   a0 = std::min<uint64_t>(a0, n);
   const uint64_t nb = ((n - a0) / V) * V;
@@ -174,10 +177,13 @@ static void plan_call(const ls_params* prm, int dt, uint64_t n, uintptr_t addr, 
   P->c.G = (uint32_t)G;
   P->smem_hist = level0_smem_hist(dt, P->L, P->f0, P->n_ext_max);
   P->smem_scatter = level0_smem_scatter(dt, P->L, P->f0, P->n_ext_max);
+  // level-1 sub-buckets per bucket: buckets of about l1_target keys each
+  const uint64_t per = (uint64_t)P->f0 * P->lim.l1_target;
+  P->kf = (uint32_t)std::min<uint64_t>(MAX_F1, std::max<uint64_t>(1, (n + per - 1) / per));
   P->cap0 = P->n_ext_max + 16;
   P->cap_r = n / (P->lim.c_large + 1) + 16;     // jobs a refinement level can pass on
   P->capj = std::max(P->cap0, P->cap_r);        // jobs of one refinement level
-  P->cap_c = std::max(n / P->lim.l1_target + 2 * P->capj, n / (P->lim.l1_target >> 4) + P->capj) + 64;
+  P->cap_c = std::max((uint64_t)P->kf * P->cap0, n / (P->lim.l1_target >> 4) + P->capj) + 64;
   P->cap1 = P->cap_c + P->cap0;
   const uint64_t M = (uint64_t)P->n_ext_max * G;
   P->l0_scan_tiles = (uint32_t)std::max<uint64_t>(1, (M + SC_TILE - 1) / SC_TILE);
@@ -202,7 +208,7 @@ struct Workspace {
   size_t o_scratch, o_smp_a, o_smp_b, o_rank, o_flags, o_cpos, o_cand, o_sel, o_nh, o_part, o_hi,
       o_tscan, o_rs_hist, o_rs_skip, o_rs_status, o_hdr, o_leaf64, o_thr, o_cell, o_cleaf, o_leaff, o_heads, o_heavy,
       o_lbeg, o_lend, o_hist, o_offs, o_l0scan, o_jobs_fill, o_jobs_s, o_jobs_l, o_jobs_r,
-      o_jobs_fb, o_jobs_r2, o_jobs_r3, o_counts, o_aux, o_tot, o_l1cnt, o_l1off, o_l1cur, o_jmin, o_jmax, o_l1scan,
+      o_jobs_fb, o_jobs_r2, o_jobs_r3, o_pk, o_sid, o_counts, o_aux, o_tot, o_l1cnt, o_l1off, o_l1cur, o_jmin, o_jmax, o_l1scan,
       o_ubase, o_units;
   size_t tscan_bytes, rs_status_bytes, l0scan_bytes, l1scan_bytes;
   uint64_t cand_cap;
@@ -251,6 +257,8 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->o_jobs_l = c.take<Job>(P.cap1);
   w->o_jobs_r = c.take<Job>(P.cap0);
   w->o_jobs_fb = c.take<Job>(P.cap1);
+  w->o_pk = c.take<uint32_t>(with_scratch ? P.n + 16 : 0);
+  w->o_sid = c.take<uint16_t>(with_scratch ? P.n + 16 : 0);
   w->o_jobs_r2 = c.take<Job>(P.cap_r);
   w->o_jobs_r3 = c.take<Job>(P.cap_r);
   w->o_counts = c.take<unsigned long long>(16);
@@ -338,6 +346,7 @@ static Bound bind(const Plan& P, const Workspace& w) {
   l.jmin = at<unsigned long long>(w, w.o_jmin);
   l.jmax = at<unsigned long long>(w, w.o_jmax);
   l.scan_status = at<void>(w, w.o_l1scan);
+  l.sid = at<uint16_t>(w, w.o_sid);
   l.scan_status_bytes = w.l1scan_bytes;
   l.cap_c = P.cap_c;
   l.cap_jobs = P.capj;
@@ -385,6 +394,10 @@ static Level0Args level0_args(const Plan& P, const Bound& b, const Workspace& w,
   a.scan_status = at<void>(w, w.o_l0scan);
   a.scan_tiles = P.l0_scan_tiles;
   a.err = d->err;
+  a.pk = at<uint32_t>(w, w.o_pk);
+  a.sid = at<uint16_t>(w, w.o_sid);
+  a.kf = P.kf;
+  a.f0kf = (float)((double)P.f0 * P.kf);
   return a;
 }
 
@@ -399,7 +412,7 @@ static cudaError_t enqueue_sort(const Plan& P, const Workspace& w, void* keys, D
   LS_TRY(cudaMemsetAsync(at<void>(w, w.o_l0scan), 0, w.l0scan_bytes, st));
   const Level0Args a = level0_args(P, b, w, keys, d);
   LS_TRY(level0_enqueue(P.dt, a, P.smem_hist, P.smem_scatter, b.lists, P.lim, st, &mk, 2));
-  LS_TRY(level1_enqueue(P.dt, keys, a.scratch, P.n, b.M, b.lists, P.lim, b.l1, d->err, st,
+  LS_TRY(level1_enqueue(P.dt, keys, a.scratch, P.n, b.M, b.lists, P.lim, b.l1, P.kf, d->err, st,
                         d->num_sms));
   mark(&mk, 6, st);
   LS_TRY(fill_enqueue(P.dt, keys, b.lists, P.cap1, st, d->num_sms));

@@ -5,17 +5,20 @@
 // overflow (Sec. 4.2).  On the GPU the same goal -- each bucket gets exactly
 // the space it needs -- is reached with a counting pre-pass (the exact-count
 // alternative weighed in Sec. 4.2), which costs one extra streaming read:
-//   K2 k_l0_hist     per-CTA histograms of extended slots, key tiles staged by
-//                    TMA into shared memory;
+//   K2 k_l0_hist     evaluates the model once per key: its extended slot
+//                    (bucket, or an equality slot of a heavy value) counted in
+//                    a per-CTA shared-memory histogram, and a packed id
+//                    (compact slot | level-1 sub-bucket) stored for the scatter;
 //   K3 k_scan        decoupled look-back exclusive scan of the histograms,
 //                    giving every (slot, CTA) its write head;
-//   K4 k_l0_scatter  re-predicts, ranks keys by slot inside the tile, stages
-//                    them slot-contiguously in shared memory and writes full
-//                    runs to the scratch buffer;
+//   K4 k_l0_scatter  streams key and id tiles by TMA into shared memory, ranks
+//                    keys by slot inside the tile, stages them slot-contiguously
+//                    and writes full runs (keys and level-1 ids) to scratch;
 //   k_classify0      turns slots into jobs (equality fill, in-bucket sort,
 //                    level-1 re-partition).
-// Level 1 (Alg. 2's re-partition of each bucket into sub-buckets) splits the
-// oversized slots with the same model: sub = floor((F - Flo) * f1 / (Fhi - Flo)).
+// Level 1 (Alg. 2's re-partition of each bucket into sub-buckets) uses the
+// sub-bucket ids from K2: sub = clamp(floor(F(x) * f0 * Kf) - b * Kf, 0, Kf-1),
+// the paper's level-1 position with Kf sub-buckets per bucket.
 #include <cfloat>
 
 #include "ls_partition.cuh"
@@ -25,52 +28,64 @@
 namespace ls {
 
 struct L0Layout {
-  uint32_t bar, buf, thr, cell, cleaf, heads, htk, cnt, bcnt, boff, ecnt, cursor, sdst, ws, total;
+  uint32_t bar, buf, pbuf, thr, cell, cleaf, heads, htk, cnt, ecnt, soff, cursor, sinfo, sid, ws,
+      total;
 };
 
-// Shared-memory layout of the level-0 kernels.  hmax: heavy values; the
-// scatter keeps counters and cursors for the f0 + hmax non-equality slots.
 // The cell-index leaves stay in global memory (read through L1) when the
 // shared copy would not fit.
 constexpr size_t L0_SMEM_LIMIT = 227 * 1024;
 constexpr uint32_t NOT_SHARED = 0xFFFFFFFFu;
+constexpr int H_KPT = 8;             // keys per thread and step of K2
 
-static L0Layout l0_layout(int W, uint32_t L, uint32_t f0, uint32_t next, uint32_t hmax,
-                          bool scatter, bool cleaf_shared = true) {
+// K2: the lookup tables and the extended-slot counters.
+static L0Layout l0_layout_hist(uint32_t L, uint32_t f0, uint32_t next, uint32_t hmax,
+                               bool cleaf_shared = true) {
   L0Layout y{};
   size_t o = 0;
   auto al = [&](size_t a) { o = (o + a - 1) / a * a; };
-  y.bar = (uint32_t)o; o += 16;
-  al(128); y.buf = (uint32_t)o; o += 2ull * P_TILE * W;
   al(16); y.thr = (uint32_t)o; o += (size_t)f0 * 8;
   y.cell = (uint32_t)o; o += (size_t)L0_CELLS * 4;
   y.cleaf = NOT_SHARED;
   if (cleaf_shared) { al(16); y.cleaf = (uint32_t)o; o += (size_t)L * sizeof(CellLeaf); }
   al(16); y.heads = (uint32_t)o; o += (size_t)(f0 + 1) * sizeof(BucketHead);
   y.htk = (uint32_t)o; o += (size_t)hmax * 8;
-  if (!scatter) {
-    y.cnt = (uint32_t)o; o += (size_t)(next + 1) * 4;
-  } else {
-    const size_t nc = (size_t)f0 + hmax;
-    y.bcnt = (uint32_t)o; o += (size_t)f0 * 4;
-    y.boff = (uint32_t)o; o += (size_t)(f0 + 1) * 4;
-    y.ecnt = (uint32_t)o; o += nc * 4;
-    al(8); y.cursor = (uint32_t)o; o += nc * 8;
-    y.sdst = (uint32_t)o; o += (size_t)P_TILE * 4;
-  }
+  y.cnt = (uint32_t)o; o += (size_t)(next + 1) * 4;
   al(8); y.ws = (uint32_t)o; o += 33 * 8;
   y.total = (uint32_t)o;
-  if (cleaf_shared && o > L0_SMEM_LIMIT) return l0_layout(W, L, f0, next, hmax, scatter, false);
+  if (cleaf_shared && o > L0_SMEM_LIMIT) return l0_layout_hist(L, f0, next, hmax, false);
+  return y;
+}
+
+// K4: double-buffered key and id tiles, per-slot counters, offsets and
+// cursors of the nc = f0 + hmax non-equality slots, staging records.
+static L0Layout l0_layout_scatter(int W, uint32_t f0, uint32_t hmax) {
+  L0Layout y{};
+  size_t o = 0;
+  auto al = [&](size_t a) { o = (o + a - 1) / a * a; };
+  const size_t nc = (size_t)f0 + hmax;
+  y.bar = (uint32_t)o; o += 16;
+  al(128); y.buf = (uint32_t)o; o += 2ull * P_TILE * W;
+  al(128); y.pbuf = (uint32_t)o; o += 2ull * P_TILE * 4;
+  y.ecnt = (uint32_t)o; o += nc * 4;
+  y.soff = (uint32_t)o; o += (nc + 1) * 4;
+  al(8); y.cursor = (uint32_t)o; o += nc * 8;
+  y.sinfo = (uint32_t)o; o += (size_t)P_TILE * 4;
+  y.sid = (uint32_t)o; o += (size_t)P_TILE * 2;
+  al(8); y.ws = (uint32_t)o; o += 33 * 8;
+  y.total = (uint32_t)o;
   return y;
 }
 
 static int key_width(int dt) { return (dt == LS_F64 || dt == LS_U64) ? 8 : 4; }
 
 size_t level0_smem_hist(int dt, uint32_t L, uint32_t f0, uint32_t n_ext_max) {
-  return l0_layout(key_width(dt), L, f0, n_ext_max, (n_ext_max - f0) / 2, false).total;
+  (void)dt;
+  return l0_layout_hist(L, f0, n_ext_max, (n_ext_max - f0) / 2).total;
 }
 size_t level0_smem_scatter(int dt, uint32_t L, uint32_t f0, uint32_t n_ext_max) {
-  return l0_layout(key_width(dt), L, f0, n_ext_max, (n_ext_max - f0) / 2, true).total;
+  (void)L;
+  return l0_layout_scatter(key_width(dt), f0, (n_ext_max - f0) / 2).total;
 }
 
 __device__ __forceinline__ void chunk_of(const Chunking& c, uint32_t g, uint64_t* b, uint64_t* e) {
@@ -101,63 +116,82 @@ __device__ __forceinline__ L0Map load_tables(const Level0Args& a, unsigned char*
 }
 
 // ---------------------------------------------------------------- K2
+// One model evaluation per key: extended slot e (counted), and the packed id
+// c | sub << 16 (c = compact non-equality slot, 0xFFFF for equality keys;
+// sub = level-1 sub-bucket) stored at the key's position in the body.
+template <int DT>
+__device__ __forceinline__ uint32_t classify_key(typename KT<DT>::U u, const L0Map& q,
+                                                 const BucketHead* heads, const uint64_t* htk,
+                                                 float f0kf, uint32_t kf, uint32_t* packed) {
+  const float F = cell_F<DT>(u, q.croot, q.cleaf);
+  const float v = F * (float)L0_CELLS;
+  const uint32_t cl = v >= 0.0f ? (v < (float)L0_CELLS ? (uint32_t)v : L0_CELLS - 1) : 0u;
+  const uint32_t r = q.cell[cl];
+  const uint64_t t = KT<DT>::tk(u);
+  const uint32_t b = min(thr_search(q.thr, r & 0xFFFFu, r >> 16, t), q.pos_max);
+  const BucketHead h = heads[b];
+  uint32_t e = h.ext_base;
+  const uint32_t nh = h.hoff_nh & 15u;
+  if (nh) {
+    const uint32_t ho = h.hoff_nh >> 4;
+    for (uint32_t j = 0; j < nh; ++j) {
+      const uint64_t hv = htk[ho + j];
+      if (hv < t) e += 2;
+      else { e += (hv == t) ? 1u : 0u; break; }
+    }
+  }
+  const float w = F * f0kf;
+  int sub = (w >= 0.0f ? (int)w : 0) - (int)(b * kf);
+  sub = sub < 0 ? 0 : (sub >= (int)kf ? (int)kf - 1 : sub);
+  *packed = ((e - b) & 1u) ? 0xFFFFu : (((e + b) >> 1) | ((uint32_t)sub << 16));
+  return e;
+}
+
 template <int DT>
 __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout lay) {
   typedef typename KT<DT>::U U;
   extern __shared__ __align__(128) unsigned char sm[];
-  uint64_t* bar = (uint64_t*)(sm + lay.bar);
-  U* buf = (U*)(sm + lay.buf);
   BucketHead* heads = (BucketHead*)(sm + lay.heads);
   uint32_t* cnt = (uint32_t*)(sm + lay.cnt);
-  const U* keys = (const U*)a.keys;
-  const uint32_t next = min(a.M.hdr->n_ext, a.n_ext_max);
   uint64_t* heavy = (uint64_t*)(sm + lay.htk);
+  const U* keys = (const U*)a.keys;
+  uint32_t* pk = a.pk;
+  const uint32_t next = min(a.M.hdr->n_ext, a.n_ext_max);
   const uint32_t H = min(a.M.hdr->nheavy, (next - a.f0) / 2);
   const uint32_t g = blockIdx.x;
+  const uint64_t a0 = a.c.a0, nb = a.c.a1 - a.c.a0;
   uint64_t cb, ce;
   chunk_of(a.c, g, &cb, &ce);
-  TileStream<U, P_TILE> ts{buf, bar, keys + cb, ce - cb, (uint32_t)((ce - cb + P_TILE - 1) / P_TILE)};
-  if (threadIdx.x == 0) ts.init();
-  __syncthreads();
-  if (threadIdx.x == 0) { ts.issue(0); ts.issue(1); }
   const L0Map q = load_tables(a, sm, lay, H);
   for (uint32_t i = threadIdx.x; i < next; i += H_THREADS) cnt[i] = 0;
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  if (g == 0) {  // unaligned head and tail
-    const uint64_t nht = a.c.a0 + (a.c.n - a.c.a1);
+  if (g == 0) {  // unaligned head and tail: ids after the body
+    const uint64_t nht = a0 + (a.c.n - a.c.a1);
     for (uint64_t k = threadIdx.x; k < nht; k += H_THREADS) {
-      const uint64_t i = k < a.c.a0 ? k : a.c.a1 + (k - a.c.a0);
-      const uint32_t e = ext_of<DT>(keys[i], q, heads, heavy);
+      const uint64_t i = k < a0 ? k : a.c.a1 + (k - a0);
+      uint32_t p;
+      const uint32_t e = classify_key<DT>(keys[i], q, heads, heavy, a.f0kf, a.kf, &p);
       if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
+      pk[nb + k] = p;
     }
   }
-  constexpr int KPT = P_TILE / H_THREADS;
-  for (uint32_t t = 0; t < ts.nt; ++t) {
-    const U* tb = ts.wait(t, a.err);
-    const uint32_t c = ts.count(t);
-    uint32_t e[KPT];
-    if (c == (uint32_t)P_TILE) {  // full tile: no bounds tests, predictions interleave
-      U u[KPT];
+  for (uint64_t base = cb; base < ce; base += (uint64_t)H_THREADS * H_KPT) {
+    U u[H_KPT];
 #pragma unroll
-      for (int k = 0; k < KPT; ++k) u[k] = tb[k * H_THREADS + threadIdx.x];
-#pragma unroll
-      for (int k = 0; k < KPT; ++k) e[k] = ext_of<DT>(u[k], q, heads, heavy);
-    } else {
-#pragma unroll
-      for (int k = 0; k < KPT; ++k) {
-        const uint32_t i = k * H_THREADS + threadIdx.x;
-        e[k] = i < c ? ext_of<DT>(tb[i], q, heads, heavy) : 0xFFFFFFFFu;
-      }
+    for (int k = 0; k < H_KPT; ++k) {
+      const uint64_t i = base + (uint64_t)k * H_THREADS + threadIdx.x;
+      u[k] = i < ce ? keys[i] : (U)0;
     }
 #pragma unroll
-    for (int k = 0; k < KPT; ++k)
-      if (e[k] != 0xFFFFFFFFu && e[k] >= next) { set_error(a.err, ERR_BOUNDS); e[k] = 0xFFFFFFFEu; }
-#pragma unroll
-    for (int k = 0; k < KPT; ++k)  // shared-memory counts
-      if (e[k] < next) atomicAdd(&cnt[e[k]], 1u);
-    __syncthreads();
-    if (threadIdx.x == 0) ts.issue(t + 2);
+    for (int k = 0; k < H_KPT; ++k) {
+      const uint64_t i = base + (uint64_t)k * H_THREADS + threadIdx.x;
+      if (i < ce) {
+        uint32_t p;
+        const uint32_t e = classify_key<DT>(u[k], q, heads, heavy, a.f0kf, a.kf, &p);
+        if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
+        pk[i - a0] = p;
+      }
+    }
   }
   __syncthreads();
   for (uint32_t e = threadIdx.x; e < a.n_ext_max; e += H_THREADS)
@@ -165,12 +199,12 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
 }
 
 // ---------------------------------------------------------------- K4
-// Per tile: each key's slot (equality keys are skipped: filled later), its rank
-// inside the slot and inside its level-0 bucket (shared atomics); an exclusive
-// scan over the f0 bucket counts gives the staging offsets; keys are staged
-// bucket-contiguously together with their final address, then written out so
-// that consecutive threads write consecutive addresses of a run.  The last key
-// of a slot advances that slot's cursor.  Per-tile work is O(tile + f0).
+// Key tiles and their packed ids stream in by TMA (double buffered).  Per
+// tile: each non-equality key's rank inside its slot (shared atomics), an
+// exclusive scan over the slots gives the staging offsets, keys are staged
+// slot-contiguously and written out so that consecutive threads write
+// consecutive addresses of a run; the level-1 ids follow their keys.
+// Equality keys are skipped (their slots are filled later).
 template <int DT>
 __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Layout lay) {
   typedef typename KT<DT>::U U;
@@ -178,32 +212,44 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
   extern __shared__ __align__(128) unsigned char sm[];
   uint64_t* bar = (uint64_t*)(sm + lay.bar);
   U* buf = (U*)(sm + lay.buf);
-  BucketHead* heads = (BucketHead*)(sm + lay.heads);
-  uint64_t* heavy = (uint64_t*)(sm + lay.htk);
-  uint32_t* bcnt = (uint32_t*)(sm + lay.bcnt);
-  uint32_t* boff = (uint32_t*)(sm + lay.boff);
+  uint32_t* pbuf = (uint32_t*)(sm + lay.pbuf);
   uint32_t* ecnt = (uint32_t*)(sm + lay.ecnt);
+  uint32_t* soff = (uint32_t*)(sm + lay.soff);
   uint64_t* cursor = (uint64_t*)(sm + lay.cursor);
-  uint32_t* sinfo = (uint32_t*)(sm + lay.sdst);  // staged slot | rank << 16
+  uint32_t* sinfo = (uint32_t*)(sm + lay.sinfo);   // staged slot | rank << 16
+  uint16_t* sid = (uint16_t*)(sm + lay.sid);       // staged level-1 ids
   uint32_t* ws = (uint32_t*)(sm + lay.ws);
   const U* keys = (const U*)a.keys;
   U* out = (U*)a.scratch;
+  uint16_t* oid = a.sid;
   const uint64_t n = a.c.n;
   const uint32_t next = min(a.M.hdr->n_ext, a.n_ext_max);
   const uint32_t f0 = a.f0;
   const uint32_t H = min(a.M.hdr->nheavy, (next - f0) / 2);
   const uint32_t nc = f0 + H;  // non-equality slots
   const uint32_t g = blockIdx.x, G = a.c.G;
+  const uint64_t a0 = a.c.a0, nb = a.c.a1 - a.c.a0;
   uint64_t cb, ce;
   chunk_of(a.c, g, &cb, &ce);
-  TileStream<U, P_TILE> ts{buf, bar, keys + cb, ce - cb, (uint32_t)((ce - cb + P_TILE - 1) / P_TILE)};
-  if (threadIdx.x == 0) ts.init();
+  const uint32_t nt = (uint32_t)((ce - cb + P_TILE - 1) / P_TILE);
+  auto tcount = [&](uint32_t t) {
+    const uint64_t b = (uint64_t)t * P_TILE;
+    return (uint32_t)min((uint64_t)P_TILE, ce - cb - b);
+  };
+  auto issue = [&](uint32_t t) {  // thread 0: keys and ids of tile t on one barrier
+    if (t >= nt) return;
+    const uint32_t c = tcount(t);
+    uint64_t* br = bar + (t & 1);
+    fence_proxy_async();
+    mbar_arrive_expect_tx(br, c * (uint32_t)(sizeof(U) + 4));
+    tma_load_1d(buf + (size_t)(t & 1) * P_TILE, keys + cb + (size_t)t * P_TILE, c * (uint32_t)sizeof(U), br);
+    tma_load_1d(pbuf + (size_t)(t & 1) * P_TILE, a.pk + (cb - a0) + (size_t)t * P_TILE, c * 4u, br);
+  };
+  if (threadIdx.x == 0) { mbar_init(bar, 1); mbar_init(bar + 1, 1); fence_mbar_init(); }
   __syncthreads();
-  if (threadIdx.x == 0) { ts.issue(0); ts.issue(1); }
-  const L0Map q = load_tables(a, sm, lay, H);
-  for (uint32_t i = threadIdx.x; i < f0; i += P_THREADS) bcnt[i] = 0;
+  if (threadIdx.x == 0) { issue(0); issue(1); }
   for (uint32_t i = threadIdx.x; i < nc; i += P_THREADS) ecnt[i] = 0;
-  __syncthreads();
+  const BucketHead* heads = a.M.heads;
   for (uint32_t b = threadIdx.x; b < f0; b += P_THREADS) {  // cursors of non-equality slots
     const BucketHead h = heads[b];
     const uint32_t nh = h.hoff_nh & 15u, hoff = h.hoff_nh >> 4;
@@ -214,84 +260,64 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
   }
   __syncthreads();
   if (g == 0 && threadIdx.x == 0) {  // unaligned head and tail, one thread
-    const uint64_t nht = a.c.a0 + (n - a.c.a1);
+    const uint64_t nht = a0 + (n - a.c.a1);
     for (uint64_t k = 0; k < nht; ++k) {
-      const uint64_t i = k < a.c.a0 ? k : a.c.a1 + (k - a.c.a0);
-      const U u = keys[i];
-      uint32_t b;
-      const uint32_t e = ext_of2<DT>(u, q, heads, heavy, &b);
-      if (e >= next) { set_error(a.err, ERR_BOUNDS); continue; }
-      if ((e - b) & 1u) continue;  // equality slot: filled later
-      const uint32_t c = (e + b) >> 1;
+      const uint64_t i = k < a0 ? k : a.c.a1 + (k - a0);
+      const uint32_t p = a.pk[nb + k];
+      const uint32_t c = p & 0xFFFFu;
+      if (c == 0xFFFFu) continue;  // equality slot: filled later
+      if (c >= nc) { set_error(a.err, ERR_BOUNDS); continue; }
       const uint64_t dst = cursor[c]++;
-      if (dst < n) out[dst] = u; else set_error(a.err, ERR_BOUNDS);
+      if (dst < n) { out[dst] = keys[i]; oid[dst] = (uint16_t)(p >> 16); }
+      else set_error(a.err, ERR_BOUNDS);
     }
   }
   __syncthreads();
-  for (uint32_t t = 0; t < ts.nt; ++t) {
-    U* tb = ts.wait(t, a.err);
-    const uint32_t cnt_t = ts.count(t);
+  for (uint32_t t = 0; t < nt; ++t) {
+    mbar_wait(bar + (t & 1), (t >> 1) & 1, a.err);
+    U* tb = buf + (size_t)(t & 1) * P_TILE;
+    const uint32_t* pb = pbuf + (size_t)(t & 1) * P_TILE;
+    const uint32_t cnt_t = tcount(t);
     U u[KPT];
-    uint32_t e[KPT], bk[KPT], nh[KPT];
-    if (cnt_t == (uint32_t)P_TILE) {  // full tile: branch-free, predictions interleave
-#pragma unroll
-      for (int k = 0; k < KPT; ++k) u[k] = tb[k * P_THREADS + threadIdx.x];
-#pragma unroll
-      for (int k = 0; k < KPT; ++k)
-        e[k] = ext_of2<DT>(u[k], q, heads, heavy, &bk[k], &nh[k]);
-    } else {
-#pragma unroll
-      for (int k = 0; k < KPT; ++k) {
-        const uint32_t i = k * P_THREADS + threadIdx.x;
-        u[k] = i < cnt_t ? tb[i] : (U)0;
-        nh[k] = 0;
-        e[k] = i < cnt_t ? ext_of2<DT>(u[k], q, heads, heavy, &bk[k], &nh[k]) : 0xFFFFFFFFu;
-      }
-    }
-    uint32_t cc[KPT], rk[KPT], sr[KPT];
+    uint32_t pp[KPT], rk[KPT];
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
-      uint32_t ee = e[k];
-      if (ee != 0xFFFFFFFFu && ee >= next) { set_error(a.err, ERR_BOUNDS); ee = 0xFFFFFFFFu; }
-      const bool live = ee != 0xFFFFFFFFu && ((ee - bk[k]) & 1u) == 0;
-      cc[k] = live ? (ee + bk[k]) >> 1 : 0xFFFFFFFFu;
-      if (live && cc[k] >= nc) { set_error(a.err, ERR_BOUNDS); cc[k] = 0xFFFFFFFFu; }
-      sr[k] = cc[k] != 0xFFFFFFFFu ? atomicAdd(&bcnt[bk[k]], 1u) : 0u;
-      // a bucket without heavy values has one slot: its rank is the bucket rank
-      rk[k] = (cc[k] != 0xFFFFFFFFu && nh[k]) ? atomicAdd(&ecnt[cc[k]], 1u) : sr[k];
+      const uint32_t i = k * P_THREADS + threadIdx.x;
+      u[k] = i < cnt_t ? tb[i] : (U)0;
+      uint32_t p = i < cnt_t ? pb[i] : 0xFFFFu;
+      if ((p & 0xFFFFu) != 0xFFFFu && (p & 0xFFFFu) >= nc) { set_error(a.err, ERR_BOUNDS); p = 0xFFFFu; }
+      pp[k] = p;
+      rk[k] = (p & 0xFFFFu) != 0xFFFFu ? atomicAdd(&ecnt[p & 0xFFFFu], 1u) : 0u;
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < f0; i += P_THREADS) boff[i] = bcnt[i];
+    for (uint32_t i = threadIdx.x; i < nc; i += P_THREADS) soff[i] = ecnt[i];
     __syncthreads();
-    const uint32_t staged = block_scan_array<uint32_t>(boff, (int)f0, ws);
-    // stage bucket-contiguously with the final address
-    uint32_t last = 0;
+    const uint32_t staged = block_scan_array<uint32_t>(soff, (int)nc, ws);
 #pragma unroll
-    for (int k = 0; k < KPT; ++k) {
-      if (cc[k] == 0xFFFFFFFFu) continue;
-      const uint32_t p = boff[bk[k]] + sr[k];
-      if (p < (uint32_t)P_TILE) {
-        tb[p] = u[k];
-        sinfo[p] = cc[k] | (rk[k] << 16);
+    for (int k = 0; k < KPT; ++k) {  // stage slot-contiguously
+      const uint32_t c = pp[k] & 0xFFFFu;
+      if (c == 0xFFFFu) continue;
+      const uint32_t s = soff[c] + rk[k];
+      if (s < (uint32_t)P_TILE) {
+        tb[s] = u[k];
+        sinfo[s] = c | (rk[k] << 16);
+        sid[s] = (uint16_t)(pp[k] >> 16);
       }
-      const uint32_t slot_n = nh[k] ? ecnt[cc[k]] : bcnt[bk[k]];
-      if (rk[k] + 1 == slot_n) last |= 1u << k;
-      if (sr[k] + 1 == bcnt[bk[k]]) last |= 1u << (16 + k);
     }
     __syncthreads();
-    for (uint32_t p = threadIdx.x; p < staged; p += P_THREADS) {
-      const uint32_t inf = sinfo[p];
+    for (uint32_t s = threadIdx.x; s < staged; s += P_THREADS) {
+      const uint32_t inf = sinfo[s];
       const uint64_t dst = cursor[inf & 0xFFFFu] + (inf >> 16);
-      if (dst < n) out[dst] = tb[p]; else set_error(a.err, ERR_BOUNDS);
+      if (dst < n) { out[dst] = tb[s]; oid[dst] = sid[s]; }
+      else set_error(a.err, ERR_BOUNDS);
     }
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < KPT; ++k) {  // the last key of a slot / bucket advances / resets it
-      if ((last >> k) & 1u) { cursor[cc[k]] += rk[k] + 1; ecnt[cc[k]] = 0; }
-      if ((last >> (16 + k)) & 1u) bcnt[bk[k]] = 0;
+    for (uint32_t i = threadIdx.x; i < nc; i += P_THREADS) {  // advance the touched slots
+      const uint32_t c = ecnt[i];
+      if (c) { cursor[i] += c; ecnt[i] = 0; }
     }
     __syncthreads();
-    if (threadIdx.x == 0) ts.issue(t + 2);
+    if (threadIdx.x == 0) issue(t + 2);
   }
 }
 
@@ -406,29 +432,18 @@ k_l1_plan(LevelArgs la, SortLimits lim, Level1Ws w, uint32_t* err) {
   for (uint64_t j0 = 0; j0 < nj; j0 += blockDim.x) {
     const uint64_t j = j0 + threadIdx.x;
     uint64_t tiles = 0, f1 = 0;
-    float S = 0, T = 0;
+    const float S = 0, T = 0;
     if (j < nj) {
       Job job = la.in.jobs[j];
       // the model's split aims at l1_target keys per sub-bucket; a key-range
       // split (its input is skewed or clustered) uses 16x finer sub-buckets
-      const uint64_t tg = la.mode ? (lim.l1_target >> 4) : lim.l1_target;
-      uint64_t f = (job.m + tg - 1) / tg;
+      // the model's split has the call's Kf sub-buckets per bucket (ids from
+      // K2); a key-range split aims at l1_target / 16 keys per sub-bucket
+      uint64_t f = (job.m + (lim.l1_target >> 4) - 1) / (lim.l1_target >> 4);
       f = f < 2 ? 2 : (f > MAX_F1 ? MAX_F1 : f);
-      bool ok = true;
-      if (la.mode == 0) {
-        const double width = job.Fhi - job.Flo;
-        const double Sd = (double)f / width;
-        S = (float)Sd;
-        T = (float)(-job.Flo * Sd);
-        ok = width > 0 && isfinite(S) && isfinite(T);
-      }
-      if (!ok) {  // the model cannot split this range: pass it to the next level
-        job.kind = la.next_kind;
-        push_job(la.next, job, err);
-      } else {
-        f1 = f;
-        tiles = (job.m + L1_TILE - 1) / L1_TILE;
-      }
+      if (la.mode == 0) f = la.kf;
+      f1 = f;
+      tiles = (job.m + L1_TILE - 1) / L1_TILE;
       w.jmin[j] = ~0ull;
       w.jmax[j] = 0ull;
     }
@@ -478,18 +493,6 @@ __device__ __forceinline__ uint64_t aux_find_c(const L1Aux* aux, uint64_t nj, ui
   return lo - 1;
 }
 
-// Level-1 sub-bucket (Alg. 2's re-partition with the model): the FP32
-// estimate of F scaled onto the job's f1 sub-buckets.
-template <int DT>
-__device__ __forceinline__ uint32_t l1_sub(typename KT<DT>::U u, const CellRoot& cr,
-                                           const CellLeaf* cl, const L1Aux& x) {
-  const float F = cell_F<DT>(u, cr, cl);
-  const float v = __fmaf_rn(F, x.S, x.T);
-  if (!(v > 0.0f)) return 0u;
-  if (v >= (float)(x.f1 - 1)) return x.f1 - 1;
-  return (uint32_t)v;
-}
-
 // Total-order key range of every job of a range level (one atomic pair per tile).
 template <int DT>
 __global__ void __launch_bounds__(L1_THREADS)
@@ -531,15 +534,8 @@ k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Mod
           LevelArgs la, Level1Ws w) {
   typedef typename KT<DT>::U U;
   __shared__ uint32_t hc[MAX_F1];
-  __shared__ unsigned long long s_min, s_max;
-  extern __shared__ __align__(16) unsigned char dsm[];
-  CellLeaf* cl = (CellLeaf*)dsm;  // M.L cell-index leaves
   const L1Aux* aux = (const L1Aux*)w.aux;
   const uint64_t T = w.totals[0], nj = w.totals[2];
-  const CellRoot cr = M.hdr->croot;
-  for (int i = threadIdx.x; i < M.L; i += blockDim.x) cl[i] = M.cleaf[i];
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
   for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
     const uint64_t j = aux_find_tile(aux, nj, t);
     const L1Aux x = aux[j];
@@ -547,42 +543,20 @@ k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Mod
     const uint64_t off = (t - x.tile_base) * L1_TILE;
     const uint32_t c = (uint32_t)min((uint64_t)L1_TILE, job.m - off);
     const U* src = (job.src ? scratch : keys) + job.start + off;
+    const uint16_t* ids = w.sid + job.start + off;
     RangeSplit rs{};
     if (la.mode) rs = range_split(w.jmin[j], w.jmax[j], x.f1);
     for (uint32_t s = threadIdx.x; s < x.f1; s += blockDim.x) hc[s] = 0;
-    if (threadIdx.x == 0) { s_min = ~0ull; s_max = 0; }
     __syncthreads();
-    unsigned long long mn = ~0ull, mx = 0;
     for (uint32_t base = 0; base < c; base += blockDim.x) {
       const uint32_t i = base + threadIdx.x;
       uint32_t sub = 0xFFFFFFFFu;
-      if (i < c) {
-        const U u = src[i];
-        const uint64_t tk = KT<DT>::tk(u);
-        if (la.mode) {
-          sub = range_sub(tk, rs);
-        } else {
-          mn = min(mn, (unsigned long long)tk);
-          mx = max(mx, (unsigned long long)tk);
-          sub = l1_sub<DT>(u, cr, cl, x);
-        }
-      }
+      if (i < c) sub = la.mode ? range_sub(KT<DT>::tk(src[i]), rs) : min((uint32_t)ids[i], x.f1 - 1);
       if (sub != 0xFFFFFFFFu) atomicAdd(&hc[sub], 1u);
-    }
-    if (!la.mode) {
-      for (int o = 16; o > 0; o >>= 1) {
-        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      }
-      if (lane == 0) { atomicMin(&s_min, mn); atomicMax(&s_max, mx); }
     }
     __syncthreads();
     for (uint32_t s = threadIdx.x; s < x.f1; s += blockDim.x)
       if (hc[s]) atomicAdd(&w.cnt[x.cbase + s], hc[s]);
-    if (threadIdx.x == 0 && !la.mode) {
-      atomicMin(&w.jmin[j], s_min);
-      atomicMax(&w.jmax[j], s_max);
-    }
     __syncthreads();
   }
 }
@@ -611,12 +585,8 @@ k_l1_scatter(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, uint64_t n, 
   extern __shared__ __align__(16) unsigned char dsm[];
   U* stage = (U*)dsm;                                      // L1_TILE keys
   uint16_t* ids = (uint16_t*)(dsm + sizeof(U) * L1_TILE);  // L1_TILE slot ids
-  CellLeaf* cl = (CellLeaf*)(dsm + (size_t)(sizeof(U) + 2) * L1_TILE);  // M.L leaves
   const L1Aux* aux = (const L1Aux*)w.aux;
   const uint64_t T = w.totals[0], nj = w.totals[2];
-  const CellRoot cr = M.hdr->croot;
-  for (int i = threadIdx.x; i < M.L; i += blockDim.x) cl[i] = M.cleaf[i];
-  __syncthreads();
   for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
     const uint64_t j = aux_find_tile(aux, nj, t);
     if (w.jmin[j] == w.jmax[j]) continue;  // homogeneous: filled, not moved
@@ -625,6 +595,7 @@ k_l1_scatter(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, uint64_t n, 
     const uint64_t off = (t - x.tile_base) * L1_TILE;
     const uint32_t c = (uint32_t)min((uint64_t)L1_TILE, job.m - off);
     const U* src = (job.src ? scratch : keys) + job.start + off;
+    const uint16_t* idsrc = w.sid + job.start + off;
     U* dstb = job.src ? keys : scratch;
     RangeSplit rs{};
     if (la.mode) rs = range_split(w.jmin[j], w.jmax[j], x.f1);
@@ -639,7 +610,7 @@ k_l1_scatter(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, uint64_t n, 
       u[k] = 0;
       if (i < c) {
         u[k] = src[i];
-        sub = la.mode ? range_sub(KT<DT>::tk(u[k]), rs) : l1_sub<DT>(u[k], cr, cl, x);
+        sub = la.mode ? range_sub(KT<DT>::tk(u[k]), rs) : min((uint32_t)idsrc[i], x.f1 - 1);
       }
       sb[k] = sub;
       rk[k] = sub != 0xFFFFFFFFu ? atomicAdd(&lc[sub], 1u) : 0u;
@@ -693,14 +664,9 @@ __global__ void k_l1_classify(Lists lists, LevelArgs la, SortLimits lim, Level1W
     const uint64_t sub = c - x.cbase;
     job.start = pj.start + (w.off[c] - w.off[x.cbase]);
     job.m = cntc;
-    if (la.mode == 0) {
-      const double wd = (pj.Fhi - pj.Flo) / (double)x.f1;
-      job.Flo = pj.Flo + (double)sub * wd;
-      job.Fhi = pj.Flo + (double)(sub + 1) * wd;
-    } else {
-      job.Flo = pj.Flo;
-      job.Fhi = pj.Fhi;
-    }
+    job.Flo = pj.Flo;
+    job.Fhi = pj.Fhi;
+    (void)sub;
     job.src = pj.src ^ 1u;
     job.la = job.lb = 0;
     const uint32_t sk = la.mode ? JOB_SORT_RANGE : JOB_SORT;
@@ -716,8 +682,8 @@ static cudaError_t level0_dt(const Level0Args& a, size_t sh, size_t ss, const Li
                              const SortLimits& lim, cudaStream_t st, const Marks* mk, int mb) {
   const int W = KT<DT>::W;
   const uint32_t hmax = (a.n_ext_max - a.f0) / 2;
-  const L0Layout lh = l0_layout(W, a.L, a.f0, a.n_ext_max, hmax, false);
-  const L0Layout ls_ = l0_layout(W, a.L, a.f0, a.n_ext_max, hmax, true);
+  const L0Layout lh = l0_layout_hist(a.L, a.f0, a.n_ext_max, hmax);
+  const L0Layout ls_ = l0_layout_scatter(W, a.f0, hmax);
   k_l0_hist<DT><<<a.c.G, H_THREADS, sh, st>>>(a, lh);
   mark(mk, mb + 0, st);
   const uint64_t M = (uint64_t)a.n_ext_max * a.c.G;
@@ -733,10 +699,7 @@ static cudaError_t level0_dt(const Level0Args& a, size_t sh, size_t ss, const Li
   return cudaGetLastError();
 }
 
-static size_t l1_scatter_smem(int W, int L) {
-  return (size_t)L1_TILE * (W + 2) + (size_t)L * sizeof(CellLeaf);
-}
-static size_t l1_hist_smem(int L) { return (size_t)L * sizeof(CellLeaf); }
+static size_t l1_scatter_smem(int W) { return (size_t)L1_TILE * (W + 2); }
 
 cudaError_t level0_configure(int dt, size_t sh, size_t ss) {
   cudaError_t e = cudaSuccess;
@@ -744,10 +707,7 @@ cudaError_t level0_configure(int dt, size_t sh, size_t ss) {
   e = cudaFuncSetAttribute(k_l0_hist<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh); \
   if (e) return e;                                                                              \
   e = cudaFuncSetAttribute(k_l1_scatter<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
-                           (int)l1_scatter_smem(KT<D>::W, MAX_LEAVES));                         \
-  if (e) return e;                                                                              \
-  e = cudaFuncSetAttribute(k_l1_hist<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
-                           (int)l1_hist_smem(MAX_LEAVES));                                      \
+                           (int)l1_scatter_smem(KT<D>::W));                                     \
   if (e) return e;                                                                              \
   e = cudaFuncSetAttribute(k_l0_scatter<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
   switch (dt) {
@@ -783,14 +743,13 @@ static cudaError_t level_dt(void* keys, void* scratch, uint64_t n, const ModelPt
   k_l1_plan<<<1, 1024, 0, st>>>(la, lim, w, err);
   const int grid = 2 * num_sms;
   if (la.mode) k_l1_minmax<DT><<<grid, L1_THREADS, 0, st>>>((const U*)keys, (const U*)scratch, la, w);
-  k_l1_hist<DT><<<grid, L1_THREADS, l1_hist_smem(M.L), st>>>((const U*)keys, (const U*)scratch, M,
-                                                            la, w);
+  k_l1_hist<DT><<<grid, L1_THREADS, 0, st>>>((const U*)keys, (const U*)scratch, M, la, w);
   const unsigned tiles = (unsigned)std::max<uint64_t>(1, (w.cap_c + SC_TILE - 1) / SC_TILE);
   k_scan<uint32_t><<<tiles, SC_THREADS, 0, st>>>(w.cnt, w.off, w.cap_c, &w.totals[1],
                                                  (uint64_t*)w.scan_status,
                                                  (uint32_t*)((uint64_t*)w.scan_status + tiles), err);
   k_l1_cursor<<<grid, 256, 0, st>>>(la, w);
-  k_l1_scatter<DT><<<grid, L1_THREADS, l1_scatter_smem(KT<DT>::W, M.L), st>>>(
+  k_l1_scatter<DT><<<grid, L1_THREADS, l1_scatter_smem(KT<DT>::W), st>>>(
       (U*)keys, (U*)scratch, n, M, la, w, err);
   k_l1_classify<DT><<<grid, 256, 0, st>>>(lists, la, lim, w, M, M.L, err);
   add_launches(la.mode ? 7 : 6);
@@ -799,7 +758,7 @@ static cudaError_t level_dt(void* keys, void* scratch, uint64_t n, const ModelPt
 
 cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const ModelPtrs& M,
                            const Lists& lists, const SortLimits& lim, const Level1Ws& w,
-                           uint32_t* err, cudaStream_t st, int num_sms) {
+                           uint32_t kf, uint32_t* err, cudaStream_t st, int num_sms) {
   // level 1 splits by the model; levels 2 and 3 split what it could not by key range
   const JobList ins[3] = {lists.refine, lists.refine2, lists.refine3};
   const JobList outs[3] = {lists.refine2, lists.refine3, lists.fallback};
@@ -809,6 +768,7 @@ cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const 
     la.next = outs[lv];
     la.mode = lv == 0 ? 0 : 1;
     la.next_kind = lv == 2 ? JOB_FALLBACK : JOB_REFINE;
+    la.kf = kf;
     cudaError_t e = cudaErrorInvalidValue;
     switch (dt) {
       case LS_F64: e = level_dt<LS_F64>(keys, scratch, n, M, lists, la, lim, w, err, st, num_sms); break;

@@ -31,6 +31,10 @@ struct Level0Args {
   void* scan_status;     // scan work (status words + counter), zeroed by the caller
   uint32_t scan_tiles;
   uint32_t* err;
+  uint32_t* pk;          // per key: compact slot | level-1 sub << 16 (body, then head/tail)
+  uint16_t* sid;         // level-1 sub-bucket id at each scattered position
+  uint32_t kf;           // level-1 sub-buckets per bucket
+  float f0kf;            // f0 * kf
 };
 
 // Lists produced by classification (device-side counters).
@@ -46,6 +50,7 @@ struct LevelArgs {
   JobList in, next;
   int mode;
   uint32_t next_kind;
+  uint32_t kf;           // mode 0: sub-buckets per job (ids from the level-0 pass)
 };
 
 struct SortLimits {
@@ -64,6 +69,7 @@ struct Level1Ws {
   unsigned long long* jmax;  // per job
   void* scan_status;
   size_t scan_status_bytes;
+  const uint16_t* sid;   // level-1 ids (positions of the level-0 output)
   uint64_t cap_c;
   uint64_t cap_jobs;
   uint64_t cap_tiles;
@@ -77,7 +83,7 @@ cudaError_t level0_enqueue(int dt, const Level0Args& a, size_t smem_hist, size_t
                            const Marks* mk = nullptr, int mbase = 0);
 cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const ModelPtrs& M,
                            const Lists& lists, const SortLimits& lim, const Level1Ws& w,
-                           uint32_t* err, cudaStream_t st, int num_sms);
+                           uint32_t kf, uint32_t* err, cudaStream_t st, int num_sms);
 cudaError_t fill_enqueue(int dt, void* keys, const Lists& lists, uint64_t fill_cap,
                          cudaStream_t st, int num_sms);
 cudaError_t buckets_configure(int dt);
