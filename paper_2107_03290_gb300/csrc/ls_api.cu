@@ -139,8 +139,9 @@ static void plan_call(const ls_params* prm, int dt, uint64_t n, uintptr_t addr, 
   P->s = std::max<uint64_t>(s, 1);
   P->seed = p.seed;
   P->lim.c_small = 2048;
+  P->lim.c_mid = 4096;
   P->lim.c_large = 8192;
-  P->lim.l1_target = 4096;
+  P->lim.l1_target = 3072;
   // heavy values: per-bucket count limited by shared memory of the scatter
   uint32_t hpb = (p.flags & LS_FLAG_NO_HEAVY) ? 0 : (p.heavy_per_bucket ? p.heavy_per_bucket : d.heavy_per_bucket);
   hpb = std::min<uint32_t>(hpb, MAX_HPB);
@@ -207,7 +208,7 @@ struct Workspace {
   // offsets
   size_t o_scratch, o_smp_a, o_smp_b, o_rank, o_flags, o_cpos, o_cand, o_sel, o_nh, o_part, o_hi,
       o_tscan, o_rs_hist, o_rs_skip, o_rs_status, o_hdr, o_leaf64, o_thr, o_cell, o_cleaf, o_leaff, o_heads, o_heavy,
-      o_lbeg, o_lend, o_hist, o_offs, o_l0scan, o_jobs_fill, o_jobs_s, o_jobs_l, o_jobs_r,
+      o_lbeg, o_lend, o_hist, o_offs, o_l0scan, o_jobs_fill, o_jobs_s, o_jobs_l, o_jobs_m, o_jobs_r,
       o_jobs_fb, o_jobs_r2, o_jobs_r3, o_pk, o_sid, o_counts, o_aux, o_tot, o_l1cnt, o_l1off, o_l1cur, o_jmin, o_jmax, o_l1scan,
       o_ubase, o_units;
   size_t tscan_bytes, rs_status_bytes, l0scan_bytes, l1scan_bytes;
@@ -255,6 +256,7 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->o_jobs_fill = c.take<Job>(P.cap1);
   w->o_jobs_s = c.take<Job>(P.cap1);
   w->o_jobs_l = c.take<Job>(P.cap1);
+  w->o_jobs_m = c.take<Job>(P.cap1);
   w->o_jobs_r = c.take<Job>(P.cap0);
   w->o_jobs_fb = c.take<Job>(P.cap1);
   w->o_pk = c.take<uint32_t>(with_scratch ? P.n + 16 : 0);
@@ -285,7 +287,7 @@ struct Bound {
   TrainWs T;
   Lists lists;
   Level1Ws l1;
-  unsigned long long* counts;  // [0..6] list counts, [8..10] job counters
+  unsigned long long* counts;  // [0..7] list counts, [8..11] job counters
 };
 
 static Bound bind(const Plan& P, const Workspace& w) {
@@ -333,6 +335,7 @@ static Bound bind(const Plan& P, const Workspace& w) {
   b.lists.fill = mk(w.o_jobs_fill, b.counts + 0, P.cap1);
   b.lists.sort_s = mk(w.o_jobs_s, b.counts + 1, P.cap1);
   b.lists.sort_l = mk(w.o_jobs_l, b.counts + 2, P.cap1);
+  b.lists.sort_m = mk(w.o_jobs_m, b.counts + 7, P.cap1);
   b.lists.refine = mk(w.o_jobs_r, b.counts + 3, P.cap0);
   b.lists.fallback = mk(w.o_jobs_fb, b.counts + 4, P.cap1);
   b.lists.refine2 = mk(w.o_jobs_r2, b.counts + 5, P.cap_r);
@@ -468,7 +471,7 @@ static void fill_stats(const Plan& P, const Workspace& w, Events* ev, ls_stats* 
   stats->n_heavy = hdr.nheavy;
   stats->n_ext = hdr.n_ext;
   stats->n_level1 = counts[3];
-  stats->n_segments = counts[1] + counts[2];
+  stats->n_segments = counts[1] + counts[2] + counts[7];
   stats->n_fallback = counts[4];
   stats->n_range = counts[5] + counts[6];
   // largest slot and equality keys from the level-0 offsets
@@ -501,7 +504,8 @@ static void fill_stats(const Plan& P, const Workspace& w, Events* ev, ls_stats* 
     return sum;
   };
   stats->n_fallback_keys = job_keys(w.o_jobs_fb, counts[4], P.cap1, &stats->max_fallback);
-  stats->n_large_keys = job_keys(w.o_jobs_l, counts[2], P.cap1, nullptr);
+  stats->n_large_keys = job_keys(w.o_jobs_l, counts[2], P.cap1, nullptr) +
+                        job_keys(w.o_jobs_m, counts[7], P.cap1, nullptr);
 }
 
 }  // namespace ls

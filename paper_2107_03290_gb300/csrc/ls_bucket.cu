@@ -128,18 +128,18 @@ __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* 
   const float rscale = ss.rscale;
   const int sh = ss.sh;
   const unsigned long long tmin = ss.tmin;
-  // slots, histogram, ranks
-  uint32_t sl[KPT], rk[KPT];
+  // slots, histogram, ranks (packed slot | rank << 16; m <= 2^15)
+  uint32_t sr[KPT];
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
     const uint32_t i = k * THREADS + threadIdx.x;
-    uint32_t s = 0xFFFFFFFFu;
+    uint32_t v = 0xFFFFFFFFu;
     if (i < m) {
-      const float v = __uint2float_rn((uint32_t)((KT<DT>::tk(u[k]) - tmin) >> sh)) * rscale;
-      s = min((uint32_t)v, m - 1);
+      const float f = __uint2float_rn((uint32_t)((KT<DT>::tk(u[k]) - tmin) >> sh)) * rscale;
+      const uint32_t s = min((uint32_t)f, m - 1);
+      v = s | (atomicAdd(&cnt[s], 1u) << 16);  // rank inside the slot
     }
-    sl[k] = s;
-    rk[k] = s != 0xFFFFFFFFu ? atomicAdd(&cnt[s], 1u) : 0u;  // rank inside the slot
+    sr[k] = v;
   }
   __syncthreads();
   {
@@ -157,8 +157,8 @@ __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* 
   }
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
-    if (sl[k] != 0xFFFFFFFFu) {
-      const uint32_t p = cnt[sl[k]] + rk[k];
+    if (sr[k] != 0xFFFFFFFFu) {
+      const uint32_t p = cnt[sr[k] & 0xFFFFu] + (sr[k] >> 16);
       if (p < m) out[p] = u[k]; else set_error(err, ERR_BOUNDS);
     }
   }
@@ -236,7 +236,7 @@ __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* 
 }
 
 template <int DT, int THREADS, int KPT>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, THREADS == 512 ? 2 : (KPT == 16 ? 3 : 4))
 k_bucket_sort(typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, ModelPtrs M,
               JobList list, unsigned long long* ctr, uint32_t* err) {
   typedef typename KT<DT>::U U;
@@ -371,6 +371,7 @@ k_fallback(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, ModelPtrs M, J
 
 // ---------------------------------------------------------------- host enqueue
 constexpr int BS_SMALL_T = 256, BS_SMALL_K = 8;    // CAP 2048
+constexpr int BS_MID_T = 256, BS_MID_K = 16;       // CAP 4096
 constexpr int BS_LARGE_T = 512, BS_LARGE_K = 16;   // CAP 8192
 
 template <int DT>
@@ -378,6 +379,10 @@ static cudaError_t buckets_cfg_dt() {
   cudaError_t e = cudaFuncSetAttribute(k_bucket_sort<DT, BS_SMALL_T, BS_SMALL_K>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)BucketCfg<DT, BS_SMALL_T, BS_SMALL_K>::SMEM);
+  if (e) return e;
+  e = cudaFuncSetAttribute(k_bucket_sort<DT, BS_MID_T, BS_MID_K>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)BucketCfg<DT, BS_MID_T, BS_MID_K>::SMEM);
   if (e) return e;
   e = cudaFuncSetAttribute(k_bucket_sort<DT, BS_LARGE_T, BS_LARGE_K>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -410,6 +415,12 @@ static cudaError_t buckets_dt(void* keys, void* scratch, const ModelPtrs& M, con
       <<<gs, BS_SMALL_T, BucketCfg<DT, BS_SMALL_T, BS_SMALL_K>::SMEM, st>>>(
           (U*)keys, (const U*)scratch, M, lists.sort_s, ctrs + 0, err);
   mark(mk, mb + 0, st);
+  {
+    const unsigned gm = (unsigned)std::min<uint64_t>(std::max<uint64_t>(cap_s, 1), 4ull * num_sms);
+    k_bucket_sort<DT, BS_MID_T, BS_MID_K>
+        <<<gm, BS_MID_T, BucketCfg<DT, BS_MID_T, BS_MID_K>::SMEM, st>>>(
+            (U*)keys, (const U*)scratch, M, lists.sort_m, ctrs + 3, err);
+  }
   k_bucket_sort<DT, BS_LARGE_T, BS_LARGE_K>
       <<<gl, BS_LARGE_T, BucketCfg<DT, BS_LARGE_T, BS_LARGE_K>::SMEM, st>>>(
           (U*)keys, (const U*)scratch, M, lists.sort_l, ctrs + 1, err);
@@ -417,7 +428,7 @@ static cudaError_t buckets_dt(void* keys, void* scratch, const ModelPtrs& M, con
   k_fallback<DT><<<gf, 512, BucketCfg<DT, 512, 16>::SMEM_FB, st>>>((U*)keys, (U*)scratch, M,
                                                                   lists.fallback, ctrs + 2, err);
   mark(mk, mb + 2, st);
-  add_launches(3);
+  add_launches(4);
   return cudaGetLastError();
 }
 

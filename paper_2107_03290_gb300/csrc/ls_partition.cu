@@ -358,6 +358,7 @@ __global__ void k_classify0(Level0Args a, Lists lists, SortLimits lim) {
     job.Fhi = (j == nh) ? (double)(b + 1) / (double)a.f0 : (double)heavy[hoff + j].F;
     job.la = job.lb = 0;
     if (size <= lim.c_small) { job.kind = JOB_SORT; push_job(lists.sort_s, job, a.err); }
+    else if (size <= lim.c_mid) { job.kind = JOB_SORT; push_job(lists.sort_m, job, a.err); }
     else if (size <= lim.c_large) { job.kind = JOB_SORT; push_job(lists.sort_l, job, a.err); }
     else { job.kind = JOB_REFINE; push_job(lists.refine, job, a.err); }
   }
@@ -548,11 +549,25 @@ k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Mod
     if (la.mode) rs = range_split(w.jmin[j], w.jmax[j], x.f1);
     for (uint32_t s = threadIdx.x; s < x.f1; s += blockDim.x) hc[s] = 0;
     __syncthreads();
-    for (uint32_t base = 0; base < c; base += blockDim.x) {
-      const uint32_t i = base + threadIdx.x;
-      uint32_t sub = 0xFFFFFFFFu;
-      if (i < c) sub = la.mode ? range_sub(KT<DT>::tk(src[i]), rs) : min((uint32_t)ids[i], x.f1 - 1);
-      if (sub != 0xFFFFFFFFu) atomicAdd(&hc[sub], 1u);
+    constexpr int U8 = 8;  // independent loads in flight per thread
+    for (uint32_t base = 0; base < c; base += blockDim.x * U8) {
+      uint32_t sub[U8];
+      if (la.mode) {
+#pragma unroll
+        for (int k = 0; k < U8; ++k) {
+          const uint32_t i = base + k * blockDim.x + threadIdx.x;
+          sub[k] = i < c ? range_sub(KT<DT>::tk(src[i]), rs) : 0xFFFFFFFFu;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < U8; ++k) {
+          const uint32_t i = base + k * blockDim.x + threadIdx.x;
+          sub[k] = i < c ? min((uint32_t)ids[i], x.f1 - 1) : 0xFFFFFFFFu;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < U8; ++k)
+        if (sub[k] != 0xFFFFFFFFu) atomicAdd(&hc[sub[k]], 1u);
     }
     __syncthreads();
     for (uint32_t s = threadIdx.x; s < x.f1; s += blockDim.x)
@@ -604,14 +619,15 @@ k_l1_scatter(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, uint64_t n, 
     U u[KPT];
     uint32_t sb[KPT], rk[KPT];
 #pragma unroll
-    for (int k = 0; k < KPT; ++k) {
+    for (int k = 0; k < KPT; ++k) {  // all loads first, then the ranks
       const uint32_t i = k * L1_THREADS + threadIdx.x;
-      uint32_t sub = 0xFFFFFFFFu;
-      u[k] = 0;
-      if (i < c) {
-        u[k] = src[i];
-        sub = la.mode ? range_sub(KT<DT>::tk(u[k]), rs) : min((uint32_t)idsrc[i], x.f1 - 1);
-      }
+      u[k] = i < c ? src[i] : (U)0;
+      sb[k] = i < c ? (la.mode ? 0u : (uint32_t)idsrc[i]) : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      uint32_t sub = sb[k];
+      if (sub != 0xFFFFFFFFu) sub = la.mode ? range_sub(KT<DT>::tk(u[k]), rs) : min(sub, x.f1 - 1);
       sb[k] = sub;
       rk[k] = sub != 0xFFFFFFFFu ? atomicAdd(&lc[sub], 1u) : 0u;
     }
@@ -671,6 +687,7 @@ __global__ void k_l1_classify(Lists lists, LevelArgs la, SortLimits lim, Level1W
     job.la = job.lb = 0;
     const uint32_t sk = la.mode ? JOB_SORT_RANGE : JOB_SORT;
     if (cntc <= lim.c_small) { job.kind = sk; push_job(lists.sort_s, job, err); }
+    else if (cntc <= lim.c_mid) { job.kind = sk; push_job(lists.sort_m, job, err); }
     else if (cntc <= lim.c_large) { job.kind = sk; push_job(lists.sort_l, job, err); }
     else { job.kind = la.next_kind; push_job(la.next, job, err); }
   }

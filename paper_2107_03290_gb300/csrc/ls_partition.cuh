@@ -41,6 +41,7 @@ struct Level0Args {
 struct Lists {
   JobList fill, sort_s, sort_l, refine, fallback;
   JobList refine2, refine3;  // segments the previous level left above c_large
+  JobList sort_m;            // segments in (c_small, c_mid]
 };
 
 // One refinement level: split the jobs of `in` into sub-buckets, by the model
@@ -55,6 +56,7 @@ struct LevelArgs {
 
 struct SortLimits {
   uint64_t c_small;      // segments up to this go to the small in-bucket kernel
+  uint64_t c_mid;        // ... up to this to the middle one
   uint64_t c_large;      // ... up to this to the large kernel, above: refine/fallback
   uint64_t l1_target;    // target sub-bucket size of the level-1 split
 };
