@@ -45,10 +45,13 @@ typedef enum {
 
 /* Tuning parameters.  Zero fields take the defaults (ls_default_params). */
 typedef struct ls_params {
-  uint32_t fanout;           /* level-0 buckets f (Sec. 5.1 default 1000)              */
+  uint32_t fanout;           /* level-0 buckets f; 0: chosen by the planner (256,
+                                so level-0 and level-1 scatters write 128-byte runs;
+                                Sec. 5.1 uses 1000, which stays available)          */
   uint32_t leaves;           /* RMI leaves L (Sec. 5.1: 1000)                          */
   uint32_t sample_div;       /* sample s = ceil(n / sample_div) (Sec. 5.1: 1% -> 100)  */
-  uint32_t heavy_per_bucket; /* max equality buckets inside one level-0 bucket         */
+  uint32_t heavy_per_bucket; /* max equality buckets inside one level-0 bucket (<= 15);
+                                0: chosen by the planner                              */
   uint64_t sample_max;       /* cap on s (0: none)                                     */
   uint64_t seed;             /* seed of the stratified sample offsets                  */
   uint64_t heavy_min_count;  /* a key is heavy if its expected count >= this           */
@@ -103,7 +106,7 @@ typedef struct ls_model_export {
   int64_t root_C0;           /* out */
   int32_t root_RA;           /* out: leaf = clamp((RA t0 + RB) >> 40, 0, L-1)  */
   int64_t root_RB;           /* out */
-  uint32_t fanout;           /* in: capacity of thr (>= f0)                    */
+  uint32_t fanout;           /* in: capacity of thr (>= f0); out: f0 used      */
   uint32_t pos_max;          /* out: bucket of the largest total-order key     */
   uint64_t* thr;             /* out: f0 level-0 thresholds: thr[b] = smallest
                                 total-order key whose bucket floor(F(x) f0)

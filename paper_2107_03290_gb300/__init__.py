@@ -288,6 +288,7 @@ def radix_sort_u64_(t, stream=None):
 
 
 NOALLOC_RADIX_MAX = 1 << 20
+MAX_FANOUT = 4096
 
 
 def radix_sort_u64_noalloc_(t, stream=None):
@@ -307,14 +308,13 @@ def train(t, params: Params | None = None, stream=None, with_sample: bool = Fals
     L = p.leaves or 1000
     out = ModelExport()
     out.leaves = L
-    f0 = p.fanout or 1000
-    out.fanout = f0
-    arr = {"leaf": np.zeros((L, 5), np.float64), "thr": np.zeros(f0, np.uint64),
+    out.fanout = MAX_FANOUT
+    arr = {"leaf": np.zeros((L, 5), np.float64), "thr": np.zeros(MAX_FANOUT, np.uint64),
            "C": np.zeros(L, np.int64),
            "P": np.zeros(L, np.int32), "A": np.zeros(L, np.float32),
            "B": np.zeros(L, np.float32), "LO": np.zeros(L, np.float32),
            "HI": np.zeros(L, np.float32)}
-    heavy = np.zeros(8 * max(1, p.fanout or 1000), np.uint64)
+    heavy = np.zeros(16 * MAX_FANOUT, np.uint64)
     out.max_heavy = heavy.size
     for k, v in arr.items():
         setattr(out, k, v.ctypes.data)
@@ -328,7 +328,8 @@ def train(t, params: Params | None = None, stream=None, with_sample: bool = Fals
                          ctypes.byref(out))
     _check(rc, "ls_train")
     res = dict(arr)
-    res.update(sample_size=out.sample_size, sample_finite=out.sample_finite,
+    res["thr"] = arr["thr"][:out.fanout].copy()
+    res.update(fanout=out.fanout, sample_size=out.sample_size, sample_finite=out.sample_finite,
                root=np.array(list(out.root)), E=out.E, root_P0=out.root_P0, root_C0=out.root_C0,
                root_RA=out.root_RA, root_RB=out.root_RB,
                heavy_tk=heavy[:out.n_heavy].copy(), tau=out.tau, pos_max=out.pos_max)
@@ -340,7 +341,7 @@ def train(t, params: Params | None = None, stream=None, with_sample: bool = Fals
 def level0_histogram(t, params: Params | None = None, stream=None) -> np.ndarray:
     t = _device_tensor(t)
     p = params or default_params()
-    mx = (p.fanout or 1000) * 17 + 16
+    mx = 65536
     h = np.zeros(mx, np.uint64)
     n_ext = ctypes.c_size_t(0)
     rc = load().ls_level0_histogram(t.data_ptr(), t.numel(), dtype_code(t), _stream(stream),

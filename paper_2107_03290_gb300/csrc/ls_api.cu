@@ -129,7 +129,8 @@ static void plan_call(const ls_params* prm, int dt, uint64_t n, uintptr_t addr, 
   P->W = width_of(dt);
   P->n = n;
   P->L = std::min<uint32_t>(MAX_LEAVES, std::max<uint32_t>(1, p.leaves ? p.leaves : d.leaves));
-  P->f0 = std::min<uint32_t>(MAX_FANOUT, std::max<uint32_t>(1, p.fanout ? p.fanout : d.fanout));
+  // level 0: 256 buckets, so that a 4096-key tile writes runs of ~16 keys
+  P->f0 = std::min<uint32_t>(MAX_FANOUT, std::max<uint32_t>(1, p.fanout ? p.fanout : 256));
   const uint32_t div = p.sample_div ? p.sample_div : d.sample_div;
   uint64_t s = (n + div - 1) / div;
   s = std::max<uint64_t>(s, std::min<uint64_t>(n, 2ull * P->L));
@@ -143,7 +144,8 @@ static void plan_call(const ls_params* prm, int dt, uint64_t n, uintptr_t addr, 
   P->lim.c_large = 8192;
   P->lim.l1_target = 3072;
   // heavy values: per-bucket count limited by shared memory of the scatter
-  uint32_t hpb = (p.flags & LS_FLAG_NO_HEAVY) ? 0 : (p.heavy_per_bucket ? p.heavy_per_bucket : d.heavy_per_bucket);
+  uint32_t hpb = (p.flags & LS_FLAG_NO_HEAVY) ? 0
+                 : (p.heavy_per_bucket ? p.heavy_per_bucket : (P->f0 <= 512 ? MAX_HPB : 4));
   hpb = std::min<uint32_t>(hpb, MAX_HPB);
   while (true) {
     const uint32_t next = P->f0 * (1 + 2 * hpb);
@@ -516,10 +518,10 @@ extern "C" {
 
 void ls_default_params(ls_params* p) {
   std::memset(p, 0, sizeof(*p));
-  p->fanout = 1000;
+  p->fanout = 0;               // planner's choice (Sec. 5.1's 1000 on request)
   p->leaves = 1000;
   p->sample_div = 100;
-  p->heavy_per_bucket = 4;
+  p->heavy_per_bucket = 0;     // planner's choice
   p->sample_max = 0;
   p->seed = 0;
   p->heavy_min_count = 0;
@@ -654,6 +656,7 @@ ls_status ls_train(const void* keys, size_t n, ls_dtype dtype, void* stream,
     out->pos_max = hdr.pos_max;
     if (out->thr && out->fanout >= P.f0)
       cudaMemcpy(out->thr, b.M.thr, sizeof(uint64_t) * P.f0, cudaMemcpyDeviceToHost);
+    out->fanout = P.f0;
     std::vector<LeafFine> lf(P.L + 1);
     cudaMemcpy(lf.data(), b.M.leaff, sizeof(LeafFine) * (P.L + 1), cudaMemcpyDeviceToHost);
     for (uint32_t l = 0; l < P.L; ++l) {

@@ -13,7 +13,7 @@ namespace ls {
 // ------------------------------------------------------------------ constants
 constexpr int MAX_LEAVES = 4096;
 constexpr int MAX_FANOUT = 4096;
-constexpr int MAX_HPB = 8;          // equality buckets per level-0 bucket
+constexpr int MAX_HPB = 15;         // equality buckets per level-0 bucket (4-bit count)
 constexpr int MAX_F1 = 1024;        // level-1 sub-buckets per segment
 constexpr int64_t Q_SAT = (int64_t)1 << 62;
 constexpr unsigned long long SPIN_LIMIT = 1ull << 26;  // bounded waits
@@ -284,6 +284,17 @@ __device__ __forceinline__ uint32_t l0_bucket(typename KT<DT>::U u, const L0Map&
   return min(b, q.pos_max);
 }
 
+// Offset of key t among a bucket's ascending heavy values h[0..nh): 2 * #{h < t},
+// plus 1 if t equals a heavy value (bisection).
+__device__ __forceinline__ uint32_t heavy_offset(const uint64_t* h, uint32_t nh, uint64_t t) {
+  uint32_t lo = 0, cnt = nh;
+  while (cnt) {
+    const uint32_t half = cnt >> 1;
+    if (h[lo + half] < t) { lo += half + 1; cnt -= half + 1; } else cnt = half;
+  }
+  return 2 * lo + ((lo < nh && h[lo] == t) ? 1u : 0u);
+}
+
 // Extended slot: regular bucket b with heavies h_1<..<h_k has slots
 // ext_base + {0: <h_1, 1: =h_1, 2: (h_1,h_2), ..., 2k: >h_k}.  `htk` holds the
 // heavy values' total-order keys (bucket b's at [hoff, hoff + nh)).  Returns
@@ -300,14 +311,7 @@ __device__ __forceinline__ uint32_t ext_of2(typename KT<DT>::U u, const L0Map& q
   uint32_t e = h.ext_base;
   const uint32_t nh = h.hoff_nh & 15u;
   if (nheavy) *nheavy = nh;
-  if (nh) {
-    const uint32_t ho = h.hoff_nh >> 4;
-    for (uint32_t j = 0; j < nh; ++j) {
-      const uint64_t hv = htk[ho + j];
-      if (hv < t) e += 2;
-      else { e += (hv == t) ? 1u : 0u; break; }
-    }
-  }
+  if (nh) e += heavy_offset(htk + (h.hoff_nh >> 4), nh, t);
   return e;
 }
 

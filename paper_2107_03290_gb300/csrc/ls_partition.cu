@@ -132,14 +132,7 @@ __device__ __forceinline__ uint32_t classify_key(typename KT<DT>::U u, const L0M
   const BucketHead h = heads[b];
   uint32_t e = h.ext_base;
   const uint32_t nh = h.hoff_nh & 15u;
-  if (nh) {
-    const uint32_t ho = h.hoff_nh >> 4;
-    for (uint32_t j = 0; j < nh; ++j) {
-      const uint64_t hv = htk[ho + j];
-      if (hv < t) e += 2;
-      else { e += (hv == t) ? 1u : 0u; break; }
-    }
-  }
+  if (nh) e += heavy_offset(htk + (h.hoff_nh >> 4), nh, t);
   const float w = F * f0kf;
   int sub = (w >= 0.0f ? (int)w : 0) - (int)(b * kf);
   sub = sub < 0 ? 0 : (sub >= (int)kf ? (int)kf - 1 : sub);
@@ -242,8 +235,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
     uint64_t* br = bar + (t & 1);
     fence_proxy_async();
     mbar_arrive_expect_tx(br, c * (uint32_t)(sizeof(U) + 4));
-    tma_load_1d(buf + (size_t)(t & 1) * P_TILE, keys + cb + (size_t)t * P_TILE, c * (uint32_t)sizeof(U), br);
-    tma_load_1d(pbuf + (size_t)(t & 1) * P_TILE, a.pk + (cb - a0) + (size_t)t * P_TILE, c * 4u, br);
+    tma_load_1d_stream(buf + (size_t)(t & 1) * P_TILE, keys + cb + (size_t)t * P_TILE,
+                       c * (uint32_t)sizeof(U), br);
+    tma_load_1d_stream(pbuf + (size_t)(t & 1) * P_TILE, a.pk + (cb - a0) + (size_t)t * P_TILE, c * 4u,
+                       br);
   };
   if (threadIdx.x == 0) { mbar_init(bar, 1); mbar_init(bar + 1, 1); fence_mbar_init(); }
   __syncthreads();
@@ -366,23 +361,45 @@ __global__ void k_classify0(Level0Args a, Lists lists, SortLimits lim) {
 
 // ---------------------------------------------------------------- equality fill
 // Large jobs are written by the whole grid, small ones by one CTA each (round
-// robin), so thousands of small equality slots still fill in parallel.
+// robin), so thousands of small equality slots still fill in parallel; the
+// 16-byte aligned body of a job is written with vector stores.
 template <typename U>
-__global__ void k_fill(U* __restrict__ keys, JobList fill) {
+__device__ __forceinline__ void fill_range(U* dst, uint64_t m, U v, uint64_t tid, uint64_t stride) {
+  constexpr uint32_t V = 16 / sizeof(U);
+  uint64_t head = ((16 - ((uintptr_t)dst & 15)) & 15) / sizeof(U);
+  head = head < m ? head : m;
+  const uint64_t body = (m - head) / V;
+  const uint64_t tail0 = head + body * V;
+  uint4 w;
+  if (sizeof(U) == 8) {
+    const uint64_t x = (uint64_t)v;
+    w = make_uint4((uint32_t)x, (uint32_t)(x >> 32), (uint32_t)x, (uint32_t)(x >> 32));
+  } else {
+    const uint32_t x = (uint32_t)v;
+    w = make_uint4(x, x, x, x);
+  }
+  uint4* vb = (uint4*)(dst + head);
+  for (uint64_t i = tid; i < body; i += stride) vb[i] = w;
+  const uint64_t ne = head + (m - tail0);
+  for (uint64_t i = tid; i < ne; i += stride) dst[i < head ? i : tail0 + (i - head)] = v;
+}
+
+template <typename U>
+__global__ void __launch_bounds__(256) k_fill(U* __restrict__ keys, JobList fill) {
   constexpr uint64_t BIG = 1u << 15;
   const unsigned long long nj = min(*fill.count, fill.cap);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t gtid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   unsigned long long small_idx = 0;
   for (unsigned long long j = 0; j < nj; ++j) {
-    const Job job = fill.jobs[j];
-    const U v = (U)job.value;
-    U* dst = keys + job.start;
-    if (job.m >= BIG) {
-      for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < job.m; i += stride)
-        dst[i] = v;
+    const uint64_t m = fill.jobs[j].m;
+    if (m >= BIG) {
+      const Job job = fill.jobs[j];
+      fill_range<U>(keys + job.start, job.m, (U)job.value, gtid, stride);
     } else {
       if (small_idx++ % gridDim.x != blockIdx.x) continue;
-      for (uint64_t i = threadIdx.x; i < job.m; i += blockDim.x) dst[i] = v;
+      const Job job = fill.jobs[j];
+      fill_range<U>(keys + job.start, job.m, (U)job.value, threadIdx.x, blockDim.x);
     }
   }
 }
@@ -802,9 +819,9 @@ cudaError_t fill_enqueue(int dt, void* keys, const Lists& lists, uint64_t fill_c
                          cudaStream_t st, int num_sms) {
   (void)fill_cap;
   if (dt == LS_F64 || dt == LS_U64)
-    k_fill<uint64_t><<<2 * num_sms, 256, 0, st>>>((uint64_t*)keys, lists.fill);
+    k_fill<uint64_t><<<4 * num_sms, 256, 0, st>>>((uint64_t*)keys, lists.fill);
   else
-    k_fill<uint32_t><<<2 * num_sms, 256, 0, st>>>((uint32_t*)keys, lists.fill);
+    k_fill<uint32_t><<<4 * num_sms, 256, 0, st>>>((uint32_t*)keys, lists.fill);
   add_launches(1);
   return cudaGetLastError();
 }

@@ -5,7 +5,7 @@
 
 namespace ls {
 
-constexpr int P_THREADS = 512;      // level-0 scatter CTAs
+constexpr int P_THREADS = 1024;     // level-0 scatter CTAs
 constexpr int H_THREADS = 1024;     // level-0 histogram CTAs
 constexpr int P_TILE = 4096;        // keys per tile
 constexpr int L1_THREADS = 512;

@@ -123,6 +123,7 @@ def test_sort_matches_oracle(dist, n):
 @pytest.mark.parametrize("cfg", [
     dict(fanout=1, leaves=1), dict(fanout=4, leaves=8), dict(fanout=16, leaves=64),
     dict(fanout=3000, leaves=2000), dict(flags=ls.FLAG_NO_HEAVY), dict(heavy_per_bucket=8),
+    dict(fanout=1000, heavy_per_bucket=4), dict(fanout=64, heavy_per_bucket=15),
     dict(sample_div=1000, sample_max=500)], ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
 def test_sort_params(dist, cfg):
     """Small fan-outs force level-1 re-partitions and the radix fallback."""
@@ -157,7 +158,7 @@ def test_sort_fallback_path():
 def test_train_matches_oracle(dist):
     n = 400_000
     keys = make(dist, n)
-    p = ls.default_params(leaves=256, fanout=256)
+    p = ls.default_params(leaves=256, fanout=256, heavy_per_bucket=4)
     m = ls.train(torch.from_numpy(keys).cuda(), p, with_sample=True)
     op = oracle.params(leaves=256, fanout=256)
     # sample: stratified offsets, sorted by total order -- exact
@@ -201,7 +202,7 @@ def test_train_matches_oracle(dist):
 def test_level0_histogram_matches_spec(dist):
     n = 300_000
     keys = make(dist, n)
-    p = ls.default_params(leaves=128, fanout=200)
+    p = ls.default_params(leaves=128, fanout=200, heavy_per_bucket=4)
     t = torch.from_numpy(keys).cuda()
     h = ls.level0_histogram(t, p)
     m = ls.train(t, p)
