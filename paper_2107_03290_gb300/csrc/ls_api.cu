@@ -149,7 +149,9 @@ static void plan_call(const ls_params* prm, int dt, uint64_t n, uintptr_t addr, 
   hpb = std::min<uint32_t>(hpb, MAX_HPB);
   while (true) {
     const uint32_t next = P->f0 * (1 + 2 * hpb);
-    if (next < 65000 && level0_smem_scatter(dt, P->L, P->f0, next) <= SMEM_LIMIT) break;
+    if (next < 65000 && level0_smem_scatter(dt, P->L, P->f0, next) <= SMEM_LIMIT &&
+        level0_smem_hist(dt, P->L, P->f0, next) <= SMEM_LIMIT)
+      break;
     if (hpb == 0) break;
     --hpb;
   }

@@ -262,6 +262,7 @@ struct L0Map {
   const CellLeaf* cleaf;   // L cell-index leaves
   CellRoot croot;
   uint32_t pos_max;        // bucket of the largest total-order key
+  uint32_t f0;             // buckets
 };
 
 // Largest b in [lo, hi] with thr[b] <= t (thr[lo] <= t holds).

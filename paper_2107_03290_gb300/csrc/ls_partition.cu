@@ -30,7 +30,17 @@ namespace ls {
 struct L0Layout {
   uint32_t bar, buf, pbuf, thr, cell, cleaf, heads, htk, cnt, ecnt, soff, cursor, sinfo, sid, ws,
       total;
+  uint32_t hs;           // K2: heavy values per bucket row (power of two > per-bucket maximum)
 };
+
+// Row width of the padded per-bucket heavy table of K2.
+static uint32_t heavy_stride(uint32_t f0, uint32_t next) {
+  const uint32_t hpb = f0 ? (next - f0) / (2 * f0) : 0;
+  if (!hpb) return 0;
+  uint32_t hs = 1;
+  while (hs <= hpb) hs <<= 1;
+  return hs;
+}
 
 // The cell-index leaves stay in global memory (read through L1) when the
 // shared copy would not fit.
@@ -42,6 +52,8 @@ constexpr int H_KPT = 8;             // keys per thread and step of K2
 static L0Layout l0_layout_hist(uint32_t L, uint32_t f0, uint32_t next, uint32_t hmax,
                                bool cleaf_shared = true) {
   L0Layout y{};
+  (void)hmax;
+  y.hs = heavy_stride(f0, next);
   size_t o = 0;
   auto al = [&](size_t a) { o = (o + a - 1) / a * a; };
   al(16); y.thr = (uint32_t)o; o += (size_t)f0 * 8;
@@ -49,7 +61,7 @@ static L0Layout l0_layout_hist(uint32_t L, uint32_t f0, uint32_t next, uint32_t 
   y.cleaf = NOT_SHARED;
   if (cleaf_shared) { al(16); y.cleaf = (uint32_t)o; o += (size_t)L * sizeof(CellLeaf); }
   al(16); y.heads = (uint32_t)o; o += (size_t)(f0 + 1) * sizeof(BucketHead);
-  y.htk = (uint32_t)o; o += (size_t)hmax * 8;
+  y.htk = (uint32_t)o; o += (size_t)f0 * y.hs * 8;
   y.cnt = (uint32_t)o; o += (size_t)(next + 1) * 4;
   al(8); y.ws = (uint32_t)o; o += 33 * 8;
   y.total = (uint32_t)o;
@@ -110,19 +122,40 @@ __device__ __forceinline__ L0Map load_tables(const Level0Args& a, unsigned char*
   if (lay.cleaf != NOT_SHARED)
     for (uint32_t i = threadIdx.x; i < a.L; i += blockDim.x) cleaf[i] = a.M.cleaf[i];
   for (uint32_t i = threadIdx.x; i <= a.f0; i += blockDim.x) heads[i] = a.M.heads[i];
-  for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) htk[i] = a.M.heavy[i].tk;
+  // bucket b's heavy values at htk[j * f0 + b] (column-major, so lanes probing
+  // different buckets hit different banks), padded with the largest key
+  for (uint32_t i = threadIdx.x; i < a.f0 * lay.hs; i += blockDim.x) {
+    const uint32_t j = i / a.f0, b = i % a.f0;
+    const uint32_t hn = a.M.heads[b].hoff_nh;
+    const uint32_t nh = hn & 15u, ho = hn >> 4;
+    htk[i] = (j < nh && ho + j < H) ? a.M.heavy[ho + j].tk : ~0ull;
+  }
   const DevModel* h = a.M.hdr;
-  return L0Map{thr, cell, cleaf, h->croot, h->pos_max};
+  return L0Map{thr, cell, cleaf, h->croot, h->pos_max, a.f0};
 }
 
 // ---------------------------------------------------------------- K2
 // One model evaluation per key: extended slot e (counted), and the packed id
 // c | sub << 16 (c = compact non-equality slot, 0xFFFF for equality keys;
 // sub = level-1 sub-bucket) stored at the key's position in the body.
+// 2 * #{heavy < t} + [t is heavy] over bucket b's padded row (hs entries at
+// stride f0, ascending, padded with the largest key): fixed bisection steps,
+// no divergence.
+__device__ __forceinline__ uint32_t heavy_offset_row(const uint64_t* h, uint32_t f0, uint32_t hs,
+                                                     uint32_t nh, uint64_t t) {
+  uint32_t lo = 0;
+  for (uint32_t s = hs >> 1; s; s >>= 1)
+    if (h[(size_t)(lo + s - 1) * f0] < t) lo += s;
+  if (h[(size_t)lo * f0] < t) lo += 1;  // lo: #{h < t} over the row
+  lo = min(lo, nh);
+  return 2 * lo + ((lo < nh && h[(size_t)lo * f0] == t) ? 1u : 0u);
+}
+
 template <int DT>
 __device__ __forceinline__ uint32_t classify_key(typename KT<DT>::U u, const L0Map& q,
                                                  const BucketHead* heads, const uint64_t* htk,
-                                                 float f0kf, uint32_t kf, uint32_t* packed) {
+                                                 uint32_t hs, float f0kf, uint32_t kf,
+                                                 uint32_t* packed) {
   const float F = cell_F<DT>(u, q.croot, q.cleaf);
   const float v = F * (float)L0_CELLS;
   const uint32_t cl = v >= 0.0f ? (v < (float)L0_CELLS ? (uint32_t)v : L0_CELLS - 1) : 0u;
@@ -132,7 +165,7 @@ __device__ __forceinline__ uint32_t classify_key(typename KT<DT>::U u, const L0M
   const BucketHead h = heads[b];
   uint32_t e = h.ext_base;
   const uint32_t nh = h.hoff_nh & 15u;
-  if (nh) e += heavy_offset(htk + (h.hoff_nh >> 4), nh, t);
+  if (nh) e += heavy_offset_row(htk + b, q.f0, hs, nh, t);
   const float w = F * f0kf;
   int sub = (w >= 0.0f ? (int)w : 0) - (int)(b * kf);
   sub = sub < 0 ? 0 : (sub >= (int)kf ? (int)kf - 1 : sub);
@@ -163,7 +196,7 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
     for (uint64_t k = threadIdx.x; k < nht; k += H_THREADS) {
       const uint64_t i = k < a0 ? k : a.c.a1 + (k - a0);
       uint32_t p;
-      const uint32_t e = classify_key<DT>(keys[i], q, heads, heavy, a.f0kf, a.kf, &p);
+      const uint32_t e = classify_key<DT>(keys[i], q, heads, heavy, lay.hs, a.f0kf, a.kf, &p);
       if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
       pk[nb + k] = p;
     }
@@ -180,7 +213,7 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
       const uint64_t i = base + (uint64_t)k * H_THREADS + threadIdx.x;
       if (i < ce) {
         uint32_t p;
-        const uint32_t e = classify_key<DT>(u[k], q, heads, heavy, a.f0kf, a.kf, &p);
+        const uint32_t e = classify_key<DT>(u[k], q, heads, heavy, lay.hs, a.f0kf, a.kf, &p);
         if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
         pk[i - a0] = p;
       }
@@ -387,20 +420,30 @@ __device__ __forceinline__ void fill_range(U* dst, uint64_t m, U v, uint64_t tid
 template <typename U>
 __global__ void __launch_bounds__(256) k_fill(U* __restrict__ keys, JobList fill) {
   constexpr uint64_t BIG = 1u << 15;
+  __shared__ unsigned long long s_start[256], s_m[256], s_v[256];
   const unsigned long long nj = min(*fill.count, fill.cap);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t gtid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   unsigned long long small_idx = 0;
-  for (unsigned long long j = 0; j < nj; ++j) {
-    const uint64_t m = fill.jobs[j].m;
-    if (m >= BIG) {
-      const Job job = fill.jobs[j];
-      fill_range<U>(keys + job.start, job.m, (U)job.value, gtid, stride);
-    } else {
-      if (small_idx++ % gridDim.x != blockIdx.x) continue;
-      const Job job = fill.jobs[j];
-      fill_range<U>(keys + job.start, job.m, (U)job.value, threadIdx.x, blockDim.x);
+  for (unsigned long long j0 = 0; j0 < nj; j0 += 256) {  // job records in batches
+    const unsigned long long nb = min(256ull, nj - j0);
+    if (threadIdx.x < nb) {
+      const Job job = fill.jobs[j0 + threadIdx.x];
+      s_start[threadIdx.x] = job.start;
+      s_m[threadIdx.x] = job.m;
+      s_v[threadIdx.x] = job.value;
     }
+    __syncthreads();
+    for (unsigned long long jj = 0; jj < nb; ++jj) {
+      const uint64_t m = s_m[jj];
+      if (m >= BIG) {
+        fill_range<U>(keys + s_start[jj], m, (U)s_v[jj], gtid, stride);
+      } else {
+        if (small_idx++ % gridDim.x != blockIdx.x) continue;
+        fill_range<U>(keys + s_start[jj], m, (U)s_v[jj], threadIdx.x, blockDim.x);
+      }
+    }
+    __syncthreads();
   }
 }
 

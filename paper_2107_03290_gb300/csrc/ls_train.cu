@@ -526,7 +526,7 @@ __global__ void k_heavy_compact(const uint64_t* __restrict__ tk, const DevModel*
                                 const CellLeaf* __restrict__ cleaf, Cand* cand, uint64_t cand_cap) {
   const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
   const uint64_t* t = tk + lo;
-  const L0Map q{thr, cell, cleaf, hdr->croot, hdr->pos_max};
+  const L0Map q{thr, cell, cleaf, hdr->croot, hdr->pos_max, 0};
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < m;
        k += (uint64_t)gridDim.x * blockDim.x) {
     if (!flags[k]) continue;
