@@ -211,9 +211,9 @@ struct Workspace {
   size_t bytes = 0;
   // offsets
   size_t o_scratch, o_smp_a, o_smp_b, o_rank, o_flags, o_cpos, o_cand, o_sel, o_nh, o_part, o_hi,
-      o_tscan, o_rs_hist, o_rs_skip, o_rs_status, o_hdr, o_leaf64, o_thr, o_cell, o_cleaf, o_leaff, o_heads, o_heavy,
-      o_lbeg, o_lend, o_hist, o_offs, o_l0scan, o_jobs_fill, o_jobs_s, o_jobs_l, o_jobs_m, o_jobs_r,
-      o_jobs_fb, o_jobs_r2, o_jobs_r3, o_pk, o_sid, o_counts, o_aux, o_tot, o_l1cnt, o_l1off, o_l1cur, o_jmin, o_jmax, o_l1scan,
+      o_tscan, o_rs_hist, o_rs_skip, o_rs_status, o_hdr, o_leaf64, o_thr, o_cell, o_cleaf, o_hkey, o_hval, o_leaff, o_heads, o_heavy,
+      o_lbeg, o_lend, o_hist, o_offs, o_l0scan, o_jobs_fill, o_jobs_s, o_jobs_l, o_jobs_m, o_jobs_fb2, o_jobs_r,
+      o_jobs_fb, o_jobs_r2, o_jobs_r3, o_pk, o_sid, o_ccount, o_counts, o_aux, o_tot, o_l1cnt, o_l1off, o_l1cur, o_jmin, o_jmax, o_l1scan,
       o_ubase, o_units;
   size_t tscan_bytes, rs_status_bytes, l0scan_bytes, l1scan_bytes;
   uint64_t cand_cap;
@@ -248,6 +248,8 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->o_thr = c.take<uint64_t>(P.f0);
   w->o_cell = c.take<uint32_t>(L0_CELLS);
   w->o_cleaf = c.take<CellLeaf>(P.L);
+  w->o_hkey = c.take<uint64_t>(HASH_SIZE);
+  w->o_hval = c.take<uint16_t>(HASH_SIZE);
   w->o_leaff = c.take<LeafFine>(P.L + 1);
   w->o_heads = c.take<BucketHead>(P.f0 + 1);
   w->o_heavy = c.take<HeavyEntry>((size_t)P.f0 * std::max<uint32_t>(1, P.hpb));
@@ -261,9 +263,11 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->o_jobs_s = c.take<Job>(P.cap1);
   w->o_jobs_l = c.take<Job>(P.cap1);
   w->o_jobs_m = c.take<Job>(P.cap1);
+  w->o_jobs_fb2 = c.take<Job>(P.cap1);
   w->o_jobs_r = c.take<Job>(P.cap0);
   w->o_jobs_fb = c.take<Job>(P.cap1);
   w->o_pk = c.take<uint32_t>(with_scratch ? P.n + 16 : 0);
+  w->o_ccount = c.take<uint64_t>(P.c.G + 1);
   w->o_sid = c.take<uint16_t>(with_scratch ? P.n + 16 : 0);
   w->o_jobs_r2 = c.take<Job>(P.cap_r);
   w->o_jobs_r3 = c.take<Job>(P.cap_r);
@@ -291,7 +295,7 @@ struct Bound {
   TrainWs T;
   Lists lists;
   Level1Ws l1;
-  unsigned long long* counts;  // [0..7] list counts, [8..11] job counters
+  unsigned long long* counts;  // [0..7], [12] list counts, [8..11] job counters
 };
 
 static Bound bind(const Plan& P, const Workspace& w) {
@@ -301,6 +305,8 @@ static Bound bind(const Plan& P, const Workspace& w) {
   b.M.thr = at<uint64_t>(w, w.o_thr);
   b.M.cell = at<uint32_t>(w, w.o_cell);
   b.M.cleaf = at<CellLeaf>(w, w.o_cleaf);
+  b.M.hkey = at<uint64_t>(w, w.o_hkey);
+  b.M.hval = at<uint16_t>(w, w.o_hval);
   b.M.leaff = at<LeafFine>(w, w.o_leaff);
   b.M.heads = at<BucketHead>(w, w.o_heads);
   b.M.heavy = at<HeavyEntry>(w, w.o_heavy);
@@ -340,6 +346,7 @@ static Bound bind(const Plan& P, const Workspace& w) {
   b.lists.sort_s = mk(w.o_jobs_s, b.counts + 1, P.cap1);
   b.lists.sort_l = mk(w.o_jobs_l, b.counts + 2, P.cap1);
   b.lists.sort_m = mk(w.o_jobs_m, b.counts + 7, P.cap1);
+  b.lists.fill_big = mk(w.o_jobs_fb2, b.counts + 12, P.cap1);
   b.lists.refine = mk(w.o_jobs_r, b.counts + 3, P.cap0);
   b.lists.fallback = mk(w.o_jobs_fb, b.counts + 4, P.cap1);
   b.lists.refine2 = mk(w.o_jobs_r2, b.counts + 5, P.cap_r);
@@ -404,6 +411,8 @@ static Level0Args level0_args(const Plan& P, const Bound& b, const Workspace& w,
   a.pk = at<uint32_t>(w, w.o_pk);
   a.sid = at<uint16_t>(w, w.o_sid);
   a.kf = P.kf;
+  a.ccount = at<uint64_t>(w, w.o_ccount);
+  a.may_compact = 1;
   a.f0kf = (float)((double)P.f0 * P.kf);
   return a;
 }
@@ -495,7 +504,7 @@ static void fill_stats(const Plan& P, const Workspace& w, Events* ev, ls_stats* 
   }
   stats->max_bucket = mx;
   stats->n_eq_keys = eq;
-  stats->n_fill = counts[0];
+  stats->n_fill = counts[0] + counts[12];
   auto job_keys = [&](size_t off, uint64_t cnt, uint64_t cap, uint64_t* mxm) {
     std::vector<Job> jobs((size_t)std::min(cnt, cap));
     if (!jobs.empty())
@@ -706,7 +715,9 @@ ls_status ls_level0_histogram(const void* keys, size_t n, ls_dtype dtype, void* 
   e = cudaMemsetAsync(b.counts, 0, 16 * sizeof(unsigned long long), st);
   if (!e) e = enqueue_train(P, b, keys, d, st);
   if (!e) e = cudaMemsetAsync(at<void>(w, w.o_l0scan), 0, w.l0scan_bytes, st);
-  if (!e) e = level0_enqueue(P.dt, level0_args(P, b, w, keys, d), P.smem_hist, P.smem_scatter,
+  Level0Args a0 = level0_args(P, b, w, keys, d);
+  a0.may_compact = 0;  // the histogram entry point leaves `keys` as it is
+  if (!e) e = level0_enqueue(P.dt, a0, P.smem_hist, P.smem_scatter,
                              b.lists, P.lim, st);
   if (!e) e = cudaStreamSynchronize(st);
   if (!e) {

@@ -163,9 +163,18 @@ struct RootEval {
 
 struct HeavyEntry {    // a heavy value of one level-0 bucket
   uint64_t tk;         // total-order key
-  float F;             // fine FP32 eCDF estimate of the value
-  uint32_t pad;
+  float F;             // FP32 eCDF estimate of the value
+  uint32_t ext;        // its equality slot
 };
+
+// Open-addressing table of the heavy values (total-order key -> equality
+// slot), linear probing; empty entries hold HASH_EMPTY (never a finite key).
+constexpr uint32_t HASH_BITS = 13;
+constexpr uint32_t HASH_SIZE = 1u << HASH_BITS;
+constexpr uint64_t HASH_EMPTY = ~0ull;
+__device__ __forceinline__ uint32_t heavy_hash(uint64_t t) {
+  return (uint32_t)((t * 0x9E3779B97F4A7C15ull) >> (64 - HASH_BITS));
+}
 
 // Level-0 bucket head: first extended slot and heavy list [hoff, hoff+nh).
 struct BucketHead {
@@ -432,6 +441,9 @@ struct DevModel {
   CellRoot croot;          // level-0 cell index (FP32 root)
   uint32_t cell_span;      // widest bucket range of a cell
   uint32_t pos_max;        // bucket of the largest total-order key
+  unsigned long long heavy_len;  // sample keys equal to a selected heavy value
+  uint32_t compact;        // 1: the level-0 histogram compacts non-equality keys
+  uint32_t hash_probes;    // longest probe sequence of the heavy table (0: no table)
 };
 
 __device__ __forceinline__ uint32_t bitlen32(uint32_t v) { return v ? 32u - __clz((int)v) : 0u; }
@@ -442,6 +454,8 @@ struct ModelPtrs {         // device pointers of one model
   uint64_t* thr;           // f0 level-0 thresholds
   uint32_t* cell;          // L0_CELLS level-0 cell table
   CellLeaf* cleaf;         // L cell-index leaves
+  uint64_t* hkey;          // HASH_SIZE heavy-table keys
+  uint16_t* hval;          // HASH_SIZE heavy-table equality slots
   LeafFine* leaff;         // L + 1 (sentinel record L: LO = 1)
   BucketHead* heads;       // f0 + 1
   HeavyEntry* heavy;       // max heavy

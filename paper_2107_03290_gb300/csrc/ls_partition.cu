@@ -29,7 +29,7 @@ namespace ls {
 
 struct L0Layout {
   uint32_t bar, buf, pbuf, thr, cell, cleaf, heads, htk, cnt, ecnt, soff, cursor, sinfo, sid, ws,
-      total;
+      hkey, hval, queue, total;
   uint32_t hs;           // K2: heavy values per bucket row (power of two > per-bucket maximum)
 };
 
@@ -49,8 +49,12 @@ constexpr uint32_t NOT_SHARED = 0xFFFFFFFFu;
 constexpr int H_KPT = 8;             // keys per thread and step of K2
 
 // K2: the lookup tables and the extended-slot counters.
-static L0Layout l0_layout_hist(uint32_t L, uint32_t f0, uint32_t next, uint32_t hmax,
-                               bool cleaf_shared = true) {
+static int key_width(int dt) { return (dt == LS_F64 || dt == LS_U64) ? 8 : 4; }
+
+constexpr int QCAP = 64;              // K2 per-warp queue of keys missing the heavy table
+
+static L0Layout l0_layout_hist(int W, uint32_t L, uint32_t f0, uint32_t next, uint32_t hmax,
+                               bool cleaf_shared = true, bool hashed = true) {
   L0Layout y{};
   (void)hmax;
   y.hs = heavy_stride(f0, next);
@@ -64,8 +68,15 @@ static L0Layout l0_layout_hist(uint32_t L, uint32_t f0, uint32_t next, uint32_t 
   y.htk = (uint32_t)o; o += (size_t)f0 * y.hs * 8;
   y.cnt = (uint32_t)o; o += (size_t)(next + 1) * 4;
   al(8); y.ws = (uint32_t)o; o += 33 * 8;
+  y.hkey = y.hval = y.queue = NOT_SHARED;
+  if (hashed && y.hs) {  // heavy table and per-warp miss queues
+    al(16); y.hkey = (uint32_t)o; o += (size_t)HASH_SIZE * 8;
+    y.hval = (uint32_t)o; o += (size_t)HASH_SIZE * 2;
+    al(16); y.queue = (uint32_t)o; o += (size_t)(H_THREADS / 32) * QCAP * (W + 4);
+  }
   y.total = (uint32_t)o;
-  if (cleaf_shared && o > L0_SMEM_LIMIT) return l0_layout_hist(L, f0, next, hmax, false);
+  if (hashed && y.hs && o > L0_SMEM_LIMIT) return l0_layout_hist(W, L, f0, next, hmax, cleaf_shared, false);
+  if (cleaf_shared && o > L0_SMEM_LIMIT) return l0_layout_hist(W, L, f0, next, hmax, false, false);
   return y;
 }
 
@@ -89,11 +100,8 @@ static L0Layout l0_layout_scatter(int W, uint32_t f0, uint32_t hmax) {
   return y;
 }
 
-static int key_width(int dt) { return (dt == LS_F64 || dt == LS_U64) ? 8 : 4; }
-
 size_t level0_smem_hist(int dt, uint32_t L, uint32_t f0, uint32_t n_ext_max) {
-  (void)dt;
-  return l0_layout_hist(L, f0, n_ext_max, (n_ext_max - f0) / 2).total;
+  return l0_layout_hist(key_width(dt), L, f0, n_ext_max, (n_ext_max - f0) / 2).total;
 }
 size_t level0_smem_scatter(int dt, uint32_t L, uint32_t f0, uint32_t n_ext_max) {
   (void)L;
@@ -129,6 +137,11 @@ __device__ __forceinline__ L0Map load_tables(const Level0Args& a, unsigned char*
     const uint32_t hn = a.M.heads[b].hoff_nh;
     const uint32_t nh = hn & 15u, ho = hn >> 4;
     htk[i] = (j < nh && ho + j < H) ? a.M.heavy[ho + j].tk : ~0ull;
+  }
+  if (lay.hkey != NOT_SHARED) {
+    uint64_t* hk = (uint64_t*)(sm + lay.hkey);
+    uint16_t* hv = (uint16_t*)(sm + lay.hval);
+    for (uint32_t i = threadIdx.x; i < HASH_SIZE; i += blockDim.x) { hk[i] = a.M.hkey[i]; hv[i] = a.M.hval[i]; }
   }
   const DevModel* h = a.M.hdr;
   return L0Map{thr, cell, cleaf, h->croot, h->pos_max, a.f0};
@@ -173,7 +186,10 @@ __device__ __forceinline__ uint32_t classify_key(typename KT<DT>::U u, const L0M
   return e;
 }
 
-template <int DT>
+// Two instantiations, launched back to back: HASHED handles calls whose
+// heavy table is present (decided on the device by training), the other the
+// rest; each returns at once when the call is not its kind.
+template <int DT, bool HASHED>
 __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout lay) {
   typedef typename KT<DT>::U U;
   extern __shared__ __align__(128) unsigned char sm[];
@@ -181,11 +197,14 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
   uint32_t* cnt = (uint32_t*)(sm + lay.cnt);
   uint64_t* heavy = (uint64_t*)(sm + lay.htk);
   const U* keys = (const U*)a.keys;
+  U* keys_w = (U*)a.keys;  // compaction target (the caller's array is sorted in place)
   uint32_t* pk = a.pk;
   const uint32_t next = min(a.M.hdr->n_ext, a.n_ext_max);
   const uint32_t H = min(a.M.hdr->nheavy, (next - a.f0) / 2);
   const uint32_t g = blockIdx.x;
   const uint64_t a0 = a.c.a0, nb = a.c.a1 - a.c.a0;
+  const bool hashed = lay.hkey != NOT_SHARED && a.M.hdr->hash_probes > 0;
+  if (hashed != HASHED) return;
   uint64_t cb, ce;
   chunk_of(a.c, g, &cb, &ce);
   const L0Map q = load_tables(a, sm, lay, H);
@@ -201,6 +220,46 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
       pk[nb + k] = p;
     }
   }
+  // Compaction (equality keys dominate): the chunk's non-equality keys and
+  // their ids are packed to the front of the chunk, in place, so that K4
+  // reads only those.  Every thread loads its keys of a step before the
+  // step's barrier and writes after it, and a step's writes stay below the
+  // step's end, so no key is overwritten before it is read.
+  const bool compact = a.may_compact && a.M.hdr->compact != 0;
+  unsigned long long* s_cpos = (unsigned long long*)(sm + lay.ws);
+  if (threadIdx.x == 0) *s_cpos = 0;
+  const int lane = threadIdx.x & 31;
+  // Heavy table path: a key equal to a heavy value is counted from one table
+  // probe; the others queue per warp (QCAP entries) and take the full lookup
+  // 32 at a time, so the lanes stay converged.
+  const uint64_t* hk = (const uint64_t*)(sm + (hashed ? lay.hkey : 0));
+  const uint16_t* hv = (const uint16_t*)(sm + (hashed ? lay.hval : 0));
+  const int wid = threadIdx.x >> 5;
+  U* qk = (U*)(sm + (hashed ? lay.queue : 0)) + (size_t)wid * QCAP;
+  uint32_t* qi = (uint32_t*)(sm + (hashed ? lay.queue : 0) + (size_t)(H_THREADS / 32) * QCAP * sizeof(U)) +
+                 (size_t)wid * QCAP;
+  const unsigned lt = lanemask_lt();
+  // full lookup of `valid` lanes' keys, then count and place the id
+  auto finish = [&](bool valid, U x, uint64_t i) {
+    uint32_t pv = 0xFFFFu;
+    if (valid) {
+      const uint32_t e = classify_key<DT>(x, q, heads, heavy, lay.hs, a.f0kf, a.kf, &pv);
+      if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
+      if (!compact) pk[i - a0] = pv;
+    }
+    if (compact) {
+      const bool keep = valid && (pv & 0xFFFFu) != 0xFFFFu;
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      unsigned long long wb = 0;
+      if (lane == 0 && m) wb = atomicAdd(s_cpos, (unsigned long long)__popc(m));
+      wb = __shfl_sync(0xffffffffu, wb, 0);
+      if (keep) {
+        const uint64_t r = wb + __popc(m & lt);
+        keys_w[cb + r] = x;
+        pk[cb - a0 + r] = pv;
+      }
+    }
+  };
   for (uint64_t base = cb; base < ce; base += (uint64_t)H_THREADS * H_KPT) {
     U u[H_KPT];
 #pragma unroll
@@ -208,16 +267,88 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
       const uint64_t i = base + (uint64_t)k * H_THREADS + threadIdx.x;
       u[k] = i < ce ? keys[i] : (U)0;
     }
+    if (compact) __syncthreads();
+    if (!HASHED) {  // every key takes the full lookup; the chains interleave
+      uint32_t pp[H_KPT];
+#pragma unroll
+      for (int k = 0; k < H_KPT; ++k) {
+        const uint64_t i = base + (uint64_t)k * H_THREADS + threadIdx.x;
+        pp[k] = 0xFFFFu;
+        if (i < ce) {
+          const uint32_t e = classify_key<DT>(u[k], q, heads, heavy, lay.hs, a.f0kf, a.kf, &pp[k]);
+          if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
+          if (!compact) pk[i - a0] = pp[k];
+        }
+      }
+      if (compact) {
+#pragma unroll
+        for (int k = 0; k < H_KPT; ++k) {
+          const bool keep = (pp[k] & 0xFFFFu) != 0xFFFFu;
+          const unsigned m = __ballot_sync(0xffffffffu, keep);
+          unsigned long long wb = 0;
+          if (lane == 0 && m) wb = atomicAdd(s_cpos, (unsigned long long)__popc(m));
+          wb = __shfl_sync(0xffffffffu, wb, 0);
+          if (keep) {
+            const uint64_t r = wb + __popc(m & lt);
+            keys_w[cb + r] = u[k];
+            pk[cb - a0 + r] = pp[k];
+          }
+        }
+      }
+      continue;
+    }
+    uint32_t nq = 0;
 #pragma unroll
     for (int k = 0; k < H_KPT; ++k) {
       const uint64_t i = base + (uint64_t)k * H_THREADS + threadIdx.x;
+      bool miss = false;
       if (i < ce) {
-        uint32_t p;
-        const uint32_t e = classify_key<DT>(u[k], q, heads, heavy, lay.hs, a.f0kf, a.kf, &p);
-        if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
-        pk[i - a0] = p;
+        // one probe: a hit is a heavy value; anything else (including a heavy
+        // value displaced by a collision) takes the full lookup
+        const uint64_t t = KT<DT>::tk(u[k]);
+        const uint32_t p = heavy_hash(t);
+        const uint32_t e = hk[p] == t ? (uint32_t)hv[p] : 0xFFFFFFFFu;
+        if (e != 0xFFFFFFFFu) {  // equality key: counted, never moved
+          if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
+          if (!compact) pk[i - a0] = 0xFFFFu;
+        } else {
+          miss = true;
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, miss);
+      if (miss) {
+        const uint32_t pos = nq + __popc(m & lt);
+        qk[pos] = u[k];
+        qi[pos] = (uint32_t)(i - cb);
+      }
+      nq += __popc(m);
+      if (nq >= 32) {
+        __syncwarp();
+        const U x = qk[lane];
+        const uint32_t xi = qi[lane];
+        U y = (U)0;
+        uint32_t yi = 0;
+        if (lane < nq - 32) { y = qk[32 + lane]; yi = qi[32 + lane]; }
+        __syncwarp();
+        if (lane < nq - 32) { qk[lane] = y; qi[lane] = yi; }
+        nq -= 32;
+        finish(true, x, cb + xi);
+        __syncwarp();
       }
     }
+    if (nq) {
+      __syncwarp();
+      const bool v = lane < nq;
+      finish(v, v ? qk[lane] : (U)0, cb + (v ? qi[lane] : 0u));
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (compact) {  // pad to a multiple of 4 entries (equality marks)
+    const uint64_t cpos = *s_cpos;
+    const uint64_t r4 = (cpos + 3) & ~3ull;
+    if (threadIdx.x < r4 - cpos) pk[cb - a0 + cpos + threadIdx.x] = 0xFFFFu;
+    if (threadIdx.x == 0) a.ccount[g] = r4;
   }
   __syncthreads();
   for (uint32_t e = threadIdx.x; e < a.n_ext_max; e += H_THREADS)
@@ -257,6 +388,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
   const uint64_t a0 = a.c.a0, nb = a.c.a1 - a.c.a0;
   uint64_t cb, ce;
   chunk_of(a.c, g, &cb, &ce);
+  if (a.may_compact && a.M.hdr->compact) ce = cb + min(ce - cb, a.ccount[g]);  // packed keys
   const uint32_t nt = (uint32_t)((ce - cb + P_TILE - 1) / P_TILE);
   auto tcount = [&](uint32_t t) {
     const uint64_t b = (uint64_t)t * P_TILE;
@@ -378,7 +510,7 @@ __global__ void k_classify0(Level0Args a, Lists lists, SortLimits lim) {
       job.kind = JOB_FILL;
       job.value = (uint64_t)KT<DT>::from_tk(heavy[hoff + o / 2].tk);
       job.Flo = job.Fhi = 0;
-      push_job(lists.fill, job, a.err);
+      push_job(job.m >= FILL_BIG ? lists.fill_big : lists.fill, job, a.err);
       continue;
     }
     const uint32_t j = o / 2;
@@ -417,33 +549,21 @@ __device__ __forceinline__ void fill_range(U* dst, uint64_t m, U v, uint64_t tid
   for (uint64_t i = tid; i < ne; i += stride) dst[i < head ? i : tail0 + (i - head)] = v;
 }
 
+// Big fills: every CTA takes a share of every job; small fills: one CTA per
+// job, round robin.
 template <typename U>
-__global__ void __launch_bounds__(256) k_fill(U* __restrict__ keys, JobList fill) {
-  constexpr uint64_t BIG = 1u << 15;
-  __shared__ unsigned long long s_start[256], s_m[256], s_v[256];
-  const unsigned long long nj = min(*fill.count, fill.cap);
+__global__ void __launch_bounds__(256) k_fill(U* __restrict__ keys, JobList small, JobList big) {
+  const unsigned long long nb = min(*big.count, big.cap);
+  const unsigned long long ns = min(*small.count, small.cap);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t gtid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  unsigned long long small_idx = 0;
-  for (unsigned long long j0 = 0; j0 < nj; j0 += 256) {  // job records in batches
-    const unsigned long long nb = min(256ull, nj - j0);
-    if (threadIdx.x < nb) {
-      const Job job = fill.jobs[j0 + threadIdx.x];
-      s_start[threadIdx.x] = job.start;
-      s_m[threadIdx.x] = job.m;
-      s_v[threadIdx.x] = job.value;
-    }
-    __syncthreads();
-    for (unsigned long long jj = 0; jj < nb; ++jj) {
-      const uint64_t m = s_m[jj];
-      if (m >= BIG) {
-        fill_range<U>(keys + s_start[jj], m, (U)s_v[jj], gtid, stride);
-      } else {
-        if (small_idx++ % gridDim.x != blockIdx.x) continue;
-        fill_range<U>(keys + s_start[jj], m, (U)s_v[jj], threadIdx.x, blockDim.x);
-      }
-    }
-    __syncthreads();
+  for (unsigned long long j = 0; j < nb; ++j) {
+    const Job job = big.jobs[j];
+    fill_range<U>(keys + job.start, job.m, (U)job.value, gtid, stride);
+  }
+  for (unsigned long long j = blockIdx.x; j < ns; j += gridDim.x) {
+    const Job job = small.jobs[j];
+    fill_range<U>(keys + job.start, job.m, (U)job.value, threadIdx.x, blockDim.x);
   }
 }
 
@@ -734,7 +854,7 @@ __global__ void k_l1_classify(Lists lists, LevelArgs la, SortLimits lim, Level1W
       job = pj;
       job.kind = JOB_FILL;
       job.value = (uint64_t)KT<DT>::from_tk(w.jmin[j]);
-      push_job(lists.fill, job, err);
+      push_job(job.m >= FILL_BIG ? lists.fill_big : lists.fill, job, err);
       continue;
     }
     const uint64_t sub = c - x.cbase;
@@ -759,9 +879,10 @@ static cudaError_t level0_dt(const Level0Args& a, size_t sh, size_t ss, const Li
                              const SortLimits& lim, cudaStream_t st, const Marks* mk, int mb) {
   const int W = KT<DT>::W;
   const uint32_t hmax = (a.n_ext_max - a.f0) / 2;
-  const L0Layout lh = l0_layout_hist(a.L, a.f0, a.n_ext_max, hmax);
+  const L0Layout lh = l0_layout_hist(W, a.L, a.f0, a.n_ext_max, hmax);
   const L0Layout ls_ = l0_layout_scatter(W, a.f0, hmax);
-  k_l0_hist<DT><<<a.c.G, H_THREADS, sh, st>>>(a, lh);
+  k_l0_hist<DT, false><<<a.c.G, H_THREADS, sh, st>>>(a, lh);
+  if (lh.hkey != NOT_SHARED) k_l0_hist<DT, true><<<a.c.G, H_THREADS, sh, st>>>(a, lh);
   mark(mk, mb + 0, st);
   const uint64_t M = (uint64_t)a.n_ext_max * a.c.G;
   k_scan<uint32_t><<<a.scan_tiles, SC_THREADS, 0, st>>>(
@@ -772,7 +893,7 @@ static cudaError_t level0_dt(const Level0Args& a, size_t sh, size_t ss, const Li
   mark(mk, mb + 2, st);
   k_classify0<DT><<<(a.n_ext_max + 255) / 256, 256, 0, st>>>(a, lists, lim);
   mark(mk, mb + 3, st);
-  add_launches(4);
+  add_launches(lh.hkey != NOT_SHARED ? 5 : 4);
   return cudaGetLastError();
 }
 
@@ -781,7 +902,9 @@ static size_t l1_scatter_smem(int W) { return (size_t)L1_TILE * (W + 2); }
 cudaError_t level0_configure(int dt, size_t sh, size_t ss) {
   cudaError_t e = cudaSuccess;
 #define LS_CFG(D)                                                                               \
-  e = cudaFuncSetAttribute(k_l0_hist<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh); \
+  e = cudaFuncSetAttribute(k_l0_hist<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh); \
+  if (e) return e;                                                                              \
+  e = cudaFuncSetAttribute(k_l0_hist<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh); \
   if (e) return e;                                                                              \
   e = cudaFuncSetAttribute(k_l1_scatter<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
                            (int)l1_scatter_smem(KT<D>::W));                                     \
@@ -862,9 +985,9 @@ cudaError_t fill_enqueue(int dt, void* keys, const Lists& lists, uint64_t fill_c
                          cudaStream_t st, int num_sms) {
   (void)fill_cap;
   if (dt == LS_F64 || dt == LS_U64)
-    k_fill<uint64_t><<<4 * num_sms, 256, 0, st>>>((uint64_t*)keys, lists.fill);
+    k_fill<uint64_t><<<4 * num_sms, 256, 0, st>>>((uint64_t*)keys, lists.fill, lists.fill_big);
   else
-    k_fill<uint32_t><<<4 * num_sms, 256, 0, st>>>((uint32_t*)keys, lists.fill);
+    k_fill<uint32_t><<<4 * num_sms, 256, 0, st>>>((uint32_t*)keys, lists.fill, lists.fill_big);
   add_launches(1);
   return cudaGetLastError();
 }

@@ -10,6 +10,7 @@ constexpr int H_THREADS = 1024;     // level-0 histogram CTAs
 constexpr int P_TILE = 4096;        // keys per tile
 constexpr int L1_THREADS = 512;
 constexpr int L1_TILE = 4096;
+constexpr uint64_t FILL_BIG = 1u << 15;   // fills this large are spread over the grid
 
 // Contiguous chunk per CTA of the 16-byte aligned body [a0, a1); CTA 0 also
 // handles the head [0, a0) and the tail [a1, n).
@@ -35,6 +36,8 @@ struct Level0Args {
   uint16_t* sid;         // level-1 sub-bucket id at each scattered position
   uint32_t kf;           // level-1 sub-buckets per bucket
   float f0kf;            // f0 * kf
+  uint64_t* ccount;      // per CTA: packed non-equality keys (compaction mode)
+  uint32_t may_compact;  // 0: leave `keys` untouched (read-only callers)
 };
 
 // Lists produced by classification (device-side counters).
@@ -42,6 +45,7 @@ struct Lists {
   JobList fill, sort_s, sort_l, refine, fallback;
   JobList refine2, refine3;  // segments the previous level left above c_large
   JobList sort_m;            // segments in (c_small, c_mid]
+  JobList fill_big;          // fills of at least FILL_BIG keys (written by the whole grid)
 };
 
 // One refinement level: split the jobs of `in` into sub-buckets, by the model

@@ -48,6 +48,9 @@ __global__ void k_train_init(DevModel* hdr, uint64_t s, uint32_t* leaf_beg, uint
     hdr->s_lo = ~0ull;
     hdr->s_fin = 0;
     hdr->nheavy = 0;
+    hdr->heavy_len = 0;
+    hdr->compact = 0;
+    hdr->hash_probes = 0;
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L; i += gridDim.x * blockDim.x) {
     leaf_beg[i] = 0;
@@ -551,7 +554,7 @@ __global__ void k_heavy_compact(const uint64_t* __restrict__ tk, const DevModel*
 // One thread per bucket: keep the hpb longest runs (ties: smaller key), by key.
 __global__ void k_heavy_select(const Cand* __restrict__ cand, const uint64_t* ncand_ptr,
                                uint64_t cand_cap, uint32_t f0, int hpb, uint64_t* sel,
-                               uint32_t* nh) {
+                               uint32_t* nh, DevModel* hdr) {
   const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= f0) return;
   const uint64_t nc = min(*ncand_ptr, cand_cap);
@@ -572,6 +575,9 @@ __global__ void k_heavy_select(const Cand* __restrict__ cand, const uint64_t* nc
     ktk[p] = t; klen[p] = len;
     if (cnt < hpb) ++cnt;
   }
+  unsigned long long len = 0;
+  for (int i = 0; i < cnt; ++i) len += klen[i];
+  if (len) atomicAdd(&hdr->heavy_len, len);
   // order by key
   for (int i = 1; i < cnt; ++i) {
     const uint64_t t = ktk[i];
@@ -608,7 +614,7 @@ k_heavy_heads(const uint64_t* __restrict__ sel, const uint32_t* __restrict__ nh,
         HeavyEntry he;
         he.tk = sel[(size_t)b * hpb + j];
         he.F = cell_F<DT>(KT<DT>::from_tk(he.tk), cr, cleaf);
-        he.pad = 0;
+        he.ext = h.ext_base + 2 * j + 1;
         heavy[hoff + j] = he;
       }
     }
@@ -624,6 +630,30 @@ k_heavy_heads(const uint64_t* __restrict__ sel, const uint32_t* __restrict__ nh,
     heads[f0] = h;
     hdr->nheavy = H;
     hdr->n_ext = f0 + 2 * H;
+    // equality keys dominate (> 1/4 of the sample): compact the others in K2
+    hdr->compact = (4 * hdr->heavy_len > hdr->s_fin) ? 1u : 0u;
+  }
+}
+
+// Heavy table: one thread per heavy value; the slot of a key is claimed with a
+// compare-and-swap.  Records the longest probe sequence (0 when the table
+// would be too full to help, so the histogram skips it).
+__global__ void k_heavy_hash(DevModel* hdr, const HeavyEntry* __restrict__ heavy, uint64_t* hkey,
+                             uint16_t* hval) {
+  const uint32_t H = hdr->nheavy;
+  if (2 * H > HASH_SIZE) return;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < H; i += gridDim.x * blockDim.x) {
+    const uint64_t t = heavy[i].tk;
+    uint32_t p = heavy_hash(t);
+    for (uint32_t r = 1; r <= HASH_SIZE; ++r) {
+      const unsigned long long old = atomicCAS((unsigned long long*)&hkey[p], HASH_EMPTY, t);
+      if (old == HASH_EMPTY) {
+        hval[p] = (uint16_t)heavy[i].ext;
+        atomicMax(&hdr->hash_probes, r);
+        break;
+      }
+      p = (p + 1) & (HASH_SIZE - 1);
+    }
   }
 }
 
@@ -676,10 +706,13 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   k_heavy_compact<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, M.hdr, W.flags, W.cpos, M.thr,
                                                       M.cell, M.cleaf, (Cand*)W.cand, W.cand_cap);
   k_heavy_select<<<(P.f0 + 255) / 256, 256, 0, st>>>((const Cand*)W.cand, W.cpos + s, W.cand_cap,
-                                                     P.f0, (int)P.hpb, W.sel, W.nh);
+                                                     P.f0, (int)P.hpb, W.sel, W.nh, M.hdr);
   k_heavy_heads<DT><<<1, 1024, 0, st>>>(W.sel, W.nh, P.f0, (int)P.hpb, M.hdr, M.cleaf, M.heads,
                                         M.heavy);
-  add_launches(22);
+  e = cudaMemsetAsync(M.hkey, 0xFF, HASH_SIZE * sizeof(uint64_t), st);
+  if (e) return e;
+  k_heavy_hash<<<(HASH_SIZE / 2 + 255) / 256, 256, 0, st>>>(M.hdr, M.heavy, M.hkey, M.hval);
+  add_launches(23);
   return cudaGetLastError();
 }
 
