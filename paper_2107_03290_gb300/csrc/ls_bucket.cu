@@ -10,10 +10,10 @@
 // (sh keeps the scaled range within 24 bits, so the conversion is exact and
 // the map is non-decreasing).  Histogram of slots -> exclusive scan (the
 // running totals of Alg. 2) -> placement -> touch-up.  Keys of different
-// slots are already in order, so the touch-up only sorts each group of keys
-// sharing a slot: an insertion sort (<= 16 keys, one thread), a rank sort
-// (<= 128, one warp) or a bitonic network (one CTA); groups holding one value
-// are left as they are.
+// slots are already in order, so the touch-up only orders each group of keys
+// sharing a slot: every key of a group of at most 32 counts the members below
+// it and writes itself to its final place; larger groups are copied when they
+// hold one value and sorted by a bitonic network otherwise.
 //
 // Segments the levels could not split below CAP keys go to the fallback: per
 // job one CTA splits by the top byte in which the segment's total-order keys
@@ -27,7 +27,7 @@
 
 namespace ls {
 
-constexpr int BIGCAP = 512;     // slot groups > 16 keys tracked per segment
+constexpr int BIGCAP = 512;     // slot groups > 32 keys tracked per segment
 constexpr int STACK = 2048;     // fallback work stack entries per CTA
 
 template <int DT, int THREADS, int KPT>
@@ -94,7 +94,7 @@ __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* 
   uint32_t* cnt = (uint32_t*)(sm + C::OFF_CNT);
   uint2* big = (uint2*)(sm + C::OFF_BIG);
   unsigned long long* ws = (unsigned long long*)(sm + C::OFF_WS);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   // load, total-order key range
   U u[KPT];
   unsigned long long mn = ~0ull, mx = 0;
@@ -163,76 +163,55 @@ __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* 
     }
   }
   __syncthreads();
-  // touch-up: sort every group of keys that share a slot
-  for (uint32_t s = threadIdx.x; s < m; s += THREADS) {
+  // Final positions straight from the registers.  Keys of different slots are
+  // in order (the slot map is monotone); inside a slot group [a, b) a key's
+  // place is a + #{members smaller, or equal and placed earlier}: the
+  // insertion-sort touch-up of Alg. 2 restricted to the group, computed per
+  // key so that the lanes do not wait on each other.  Groups above GROUP_MAX
+  // are finished cooperatively below.
+  constexpr uint32_t GROUP_MAX = 32;
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    if (sr[k] == 0xFFFFFFFFu) continue;
+    const uint32_t s = sr[k] & 0xFFFFu;
     const uint32_t a = cnt[s], b = cnt[s + 1];
-    if (b <= a + 1) continue;
-    const uint32_t sz = b - a;
-    if (sz <= 16) {  // (a run of equal keys costs one compare per key)
-      for (uint32_t i = a + 1; i < b; ++i) {
-        const U x = out[i];
-        const uint64_t t = KT<DT>::tk(x);
-        uint32_t j = i;
-        while (j > a && KT<DT>::tk(out[j - 1]) > t) { out[j] = out[j - 1]; --j; }
-        out[j] = x;
+    if (b - a == 1) { dst[a] = u[k]; continue; }
+    if (b - a > GROUP_MAX) {
+      if ((sr[k] >> 16) == 0) {  // the group's first key records it
+        const uint32_t idx = atomicAdd(&ss.nbig, 1u);
+        if (idx < BIGCAP) big[idx] = make_uint2(a, b - a);
+        else ss.all = 1;
       }
-    } else {
-      const uint32_t idx = atomicAdd(&ss.nbig, 1u);
-      if (idx < BIGCAP) big[idx] = make_uint2(a, sz);
-      else ss.all = 1;
+      continue;
     }
+    const uint64_t t = KT<DT>::tk(u[k]);
+    const uint32_t me = a + (sr[k] >> 16);
+    uint32_t r = 0;
+    for (uint32_t j = a; j < b; ++j) {
+      const uint64_t tj = KT<DT>::tk(out[j]);
+      r += (tj < t || (tj == t && j < me)) ? 1u : 0u;
+    }
+    dst[a + r] = u[k];
   }
   __syncthreads();
-  if (ss.all) {
+  const uint32_t nb = ss.nbig;
+  if (nb == 0) return;
+  if (ss.all) {  // too many large groups: sort the whole segment in shared memory
     block_bitonic<DT>(out, m);
-  } else {
-    const uint32_t nb = ss.nbig;
-    for (uint32_t g = wid; g < nb; g += THREADS / 32) {
-      const uint2 gr = big[g];
-      if (gr.y > 128) continue;
-      U x[4];
-      uint32_t rank[4];
-      const uint64_t t0 = KT<DT>::tk(out[gr.x]);
-      bool same = true;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint32_t i = lane + 32 * q;
-        rank[q] = 0;
-        x[q] = i < gr.y ? out[gr.x + i] : (U)0;
-        if (i < gr.y) same = same && KT<DT>::tk(x[q]) == t0;
-      }
-      if (__all_sync(0xffffffffu, same)) continue;  // one value: in order
-      for (uint32_t j = 0; j < gr.y; ++j) {
-        const uint64_t tj = KT<DT>::tk(out[gr.x + j]);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint32_t i = lane + 32 * q;
-          const uint64_t ti = KT<DT>::tk(x[q]);
-          rank[q] += (tj < ti || (tj == ti && j < i)) ? 1u : 0u;
-        }
-      }
-      __syncwarp();
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint32_t i = lane + 32 * q;
-        if (i < gr.y) out[gr.x + rank[q]] = x[q];
-      }
-      __syncwarp();
-    }
+    for (uint32_t i = threadIdx.x; i < m; i += THREADS) dst[i] = out[i];
     __syncthreads();
-    for (uint32_t g = 0; g < nb; ++g) {
-      const uint2 gr = big[g];
-      if (gr.y <= 128) continue;
-      const uint64_t t0 = KT<DT>::tk(out[gr.x]);
-      int diff = 0;
-      for (uint32_t i = threadIdx.x; i < gr.y; i += THREADS)
-        diff |= KT<DT>::tk(out[gr.x + i]) != t0;
-      if (__syncthreads_or(diff)) block_bitonic<DT>(out + gr.x, gr.y);
-    }
+    return;
   }
-  __syncthreads();
-  for (uint32_t i = threadIdx.x; i < m; i += THREADS) dst[i] = out[i];
-  __syncthreads();
+  for (uint32_t g = 0; g < nb; ++g) {  // a large group: one value is already in order
+    const uint2 gr = big[g];
+    const uint64_t t0 = KT<DT>::tk(out[gr.x]);
+    int diff = 0;
+    for (uint32_t i = threadIdx.x; i < gr.y; i += THREADS)
+      diff |= KT<DT>::tk(out[gr.x + i]) != t0;
+    if (__syncthreads_or(diff)) block_bitonic<DT>(out + gr.x, gr.y);
+    for (uint32_t i = threadIdx.x; i < gr.y; i += THREADS) dst[gr.x + i] = out[gr.x + i];
+    __syncthreads();
+  }
 }
 
 template <int DT, int THREADS, int KPT>
@@ -258,6 +237,7 @@ k_bucket_sort(typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Model
     }
     const U* src = (job.src ? scratch : keys) + job.start;
     segment_sort<DT, THREADS, KPT>(keys + job.start, src, (uint32_t)job.m, sm, ss, err);
+    __syncthreads();
   }
 }
 
