@@ -101,22 +101,11 @@ typedef struct ls_model_export {
   uint64_t sample_finite;    /* out */
   double root[3];            /* out: a, c, b (root(x) = a (x - c) + b)        */
   double* leaf;              /* out: 5 per leaf: a, c, b, lo, hi (FP64 fit)   */
-  int32_t E;                 /* out: exponent of the sample's fixed-point grid */
-  int32_t root_P0;           /* out: root feature t0 = clamp(fx(x, P0) - C0)   */
-  int64_t root_C0;           /* out */
-  int32_t root_RA;           /* out: leaf = clamp((RA t0 + RB) >> 40, 0, L-1)  */
-  int64_t root_RB;           /* out */
   uint32_t fanout;           /* in: capacity of thr (>= f0); out: f0 used      */
   uint32_t pos_max;          /* out: bucket of the largest total-order key     */
   uint64_t* thr;             /* out: f0 level-0 thresholds: thr[b] = smallest
                                 total-order key whose bucket floor(F(x) f0)
                                 (FP64, clamped to [0, f0-1]) is >= b; thr[0] = 0 */
-  int64_t* C;                /* out per leaf: fine centre on the grid 2^P        */
-  int32_t* P;                /* out per leaf: fine exponent                      */
-  float* A;                  /* out per leaf: fine slope                         */
-  float* B;                  /* out per leaf: intercept                          */
-  float* LO;                 /* out per leaf: lower clamp (HI_l = LO_{l+1})      */
-  float* HI;                 /* out per leaf: upper clamp                        */
   uint64_t* sorted_sample_tk;/* out (optional, NULL to skip): s total-order keys */
   uint64_t* heavy_tk;        /* out: heavy values (total-order keys), ascending */
   uint64_t n_heavy;          /* out */

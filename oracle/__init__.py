@@ -77,11 +77,7 @@ class Model(ctypes.Structure):
 
 
 class Eval(ctypes.Structure):
-    _fields_ = [("model", ctypes.POINTER(Model)), ("E", ctypes.c_int32),
-                ("leaves", ctypes.c_uint32), ("f0", ctypes.c_uint32),
-                ("root_P0", ctypes.c_int32), ("root_C0", ctypes.c_int64),
-                ("root_RA", ctypes.c_int32), ("root_RB", ctypes.c_int64)] + [
-                    (k, ctypes.c_void_p) for k in ("C", "P", "A", "B", "LO", "HI")]
+    _fields_ = [("model", ctypes.POINTER(Model)), ("f0", ctypes.c_uint32)]
 
 
 def _L():
@@ -111,12 +107,7 @@ def _L():
                                               u64]
             lib.lso_partition_f64.restype = u64
             lib.lso_defragment_f64.argtypes = [vp, u64, u32, vp, vp, vp, u64]
-            lib.lso_spec_eval_params.argtypes = [P(Model), vp, u64, i32] + [vp] * 11
             lib.lso_spec_thresholds.argtypes = [P(Eval), i32, vp, vp]
-            lib.lso_spec_fixed_point.argtypes = [vp, u64, i32, i32]
-            lib.lso_spec_fixed_point.restype = i64
-            lib.lso_spec_F_fine.argtypes = [P(Eval), vp, u64, i32]
-            lib.lso_spec_F_fine.restype = ctypes.c_float
             lib.lso_spec_bucket.argtypes = [P(Eval), vp, u64, i32]
             lib.lso_spec_bucket.restype = u32
             lib.lso_spec_heavy.argtypes = [vp, vp, u64, i32, u64, u32, P(Eval), vp, u64]
@@ -239,55 +230,27 @@ def defragment(a: np.ndarray, f: int, sizes, owners, fsizes) -> np.ndarray:
 
 
 class EvalParams:
-    """Evaluation parameters: the FP64 model (level 0) and the fine FP32
-    records (the GPU's documented per-key formulas)."""
-
-    FIELDS = {"C": np.int64, "P": np.int32, "A": np.float32, "B": np.float32, "LO": np.float32,
-              "HI": np.float32}
-    ROOT = {"E": np.int32, "root_P0": np.int32, "root_C0": np.int64, "root_RA": np.int32,
-            "root_RB": np.int64}
+    """The level-0 map's parameters: the FP64 model and the fan-out f0."""
 
     def __init__(self, model: "FittedModel", f0: int):
         self.model = model
         self.L = model.m.leaves
         self.f0 = f0
-        for k, t in self.ROOT.items():
-            setattr(self, k, np.zeros(1, t))
-        for k, t in self.FIELDS.items():
-            setattr(self, k, np.zeros(self.L, t))
 
     def struct(self) -> Eval:
         e = Eval()
         e.model = ctypes.pointer(self.model.m)
-        e.leaves, e.f0 = self.L, self.f0
-        for k in self.ROOT:
-            setattr(e, k, int(getattr(self, k)[0]))
-        for k in self.FIELDS:
-            setattr(e, k, _ptr(getattr(self, k)))
+        e.f0 = self.f0
         self._keep = e
         return e
 
     @classmethod
     def from_export(cls, m: dict, leaves: int, f0: int) -> "EvalParams":
+        """From the GPU's exported FP64 model."""
         fm = FittedModel(leaves)
         fm.m.root[0], fm.m.root[1], fm.m.root[2] = [float(v) for v in m["root"]]
         fm.leaf[:] = m["leaf"][:leaves]
-        ev = cls(fm, f0)
-        for k in cls.ROOT:
-            getattr(ev, k)[0] = m[k]
-        for k in cls.FIELDS:
-            getattr(ev, k)[:] = m[k]
-        return ev
-
-
-def spec_eval_params(model: FittedModel, sorted_finite_x: np.ndarray, dtype: str,
-                     f0: int) -> EvalParams:
-    xs = np.ascontiguousarray(sorted_finite_x, np.float64)
-    ev = EvalParams(model, f0)
-    _L().lso_spec_eval_params(ctypes.byref(model.m), _ptr(xs), xs.size, DTYPES[dtype],
-                              *[_ptr(getattr(ev, k)) for k in EvalParams.ROOT],
-                              *[_ptr(getattr(ev, k)) for k in EvalParams.FIELDS])
-    return ev
+        return cls(fm, f0)
 
 
 def spec_thresholds(ev: EvalParams, dtype: str):
@@ -296,21 +259,6 @@ def spec_thresholds(ev: EvalParams, dtype: str):
     pm = np.zeros(1, np.uint32)
     _L().lso_spec_thresholds(ctypes.byref(ev.struct()), DTYPES[dtype], _ptr(thr), _ptr(pm))
     return thr, int(pm[0])
-
-
-def spec_fixed_point(keys: np.ndarray, E: int) -> np.ndarray:
-    a = np.ascontiguousarray(keys)
-    d = DTYPES[dtype_name(a)]
-    f = _L().lso_spec_fixed_point
-    return np.array([f(_ptr(a), i, d, E) for i in range(a.size)], dtype=np.int64)
-
-
-def spec_F_fine(ev: EvalParams, keys: np.ndarray) -> np.ndarray:
-    a = np.ascontiguousarray(keys)
-    d = DTYPES[dtype_name(a)]
-    s = ev.struct()
-    f = _L().lso_spec_F_fine
-    return np.array([f(ctypes.byref(s), _ptr(a), i, d) for i in range(a.size)], np.float32)
 
 
 def spec_buckets(ev: EvalParams, keys: np.ndarray) -> np.ndarray:

@@ -305,57 +305,6 @@ void reference_sort(typename K::T* a, uint64_t n) {
   std::sort(a, a + n, [](typename K::T u, typename K::T v) { return K::tk(u) < K::tk(v); });
 }
 
-// ---------------------------------------------------------------- spec: fixed point
-const int64_t Q_SAT = (int64_t)1 << 62;
-
-// floor(sign * M * 2^exp2 * 2^-E), saturated to [-2^62, 2^62].
-int64_t fixed_point(bool neg, uint64_t M, int exp2, int E) {
-  if (M == 0) return 0;
-  const long k = (long)exp2 - (long)E;
-  uint64_t v;
-  bool rem = false;
-  if (k >= 0) {
-    if (k > 62 || M > (1ull << (62 - k))) v = (uint64_t)Q_SAT;
-    else v = M << k;
-  } else {
-    const long j = -k;
-    if (j >= 64) { v = 0; rem = true; }
-    else { v = M >> j; rem = (M & ((1ull << j) - 1)) != 0; }
-  }
-  int64_t q = neg ? -(int64_t)(v + (rem ? 1 : 0)) : (int64_t)v;
-  if (q > Q_SAT) q = Q_SAT;
-  if (q < -Q_SAT) q = -Q_SAT;
-  return q;
-}
-
-int64_t fixed_point_f64(double x, int E) {
-  uint64_t u; std::memcpy(&u, &x, 8);
-  const bool neg = (u >> 63) != 0;
-  const int e = (int)((u >> 52) & 0x7FF);
-  const uint64_t m = u & ((1ull << 52) - 1);
-  if (e == 0x7FF) return neg ? -Q_SAT : Q_SAT;  // infinities (NaN never asked)
-  if (e == 0) return fixed_point(neg, m, -1074, E);
-  return fixed_point(neg, m | (1ull << 52), e - 1075, E);
-}
-
-int64_t fixed_point_f32(float x, int E) {
-  uint32_t u; std::memcpy(&u, &x, 4);
-  const bool neg = (u >> 31) != 0;
-  const int e = (int)((u >> 23) & 0xFF);
-  const uint64_t m = u & ((1u << 23) - 1);
-  if (e == 0xFF) return neg ? -Q_SAT : Q_SAT;
-  if (e == 0) return fixed_point(neg, m, -149, E);
-  return fixed_point(neg, m | (1u << 23), e - 150, E);
-}
-
-int bitlen(uint64_t v) { return v ? 64 - __builtin_clzll(v) : 0; }
-
-float fp32_sat(double d) {
-  if (d >= (double)FLT_MAX) return FLT_MAX;
-  return (float)d;
-}
-
-
 }  // namespace
 
 // ============================================================================ C API
@@ -542,120 +491,6 @@ void lso_defragment_f64(double* a, uint64_t m, uint32_t f, const uint64_t* sizes
 }
 
 // ---------------------------------------------------------------- spec functions
-static long long floor_scaled(double v, int k, double lo, double hi) {
-  double w = std::floor(std::ldexp(v, k));
-  w = w < lo ? lo : w;
-  w = w > hi ? hi : w;
-  return (long long)w;
-}
-
-void lso_spec_eval_params(const lso_model* model, const double* xs, uint64_t m, int dtype,
-                          int32_t* E, int32_t* root_P0, int64_t* root_C0, int32_t* root_RA,
-                          int64_t* root_RB, int64_t* C, int32_t* P, float* A, float* B,
-                          float* LO, float* HI) {
-  (void)dtype;
-  const uint32_t L = model->leaves;
-  const double INT31 = 2147483647.0;
-  double R = 0;
-  if (m) R = std::max(std::fabs(xs[0]), std::fabs(xs[m - 1]));
-  const int e = (R > 0) ? std::ilogb(R) + 1 - 61 : 0;
-  *E = e;
-  auto absd = [](int64_t d) { return d < 0 ? (uint64_t)(-d) : (uint64_t)d; };
-  const int64_t c0e = fixed_point_f64(model->root[1], e);
-  uint64_t span0 = 0;
-  if (m)
-    span0 = std::max(absd(fixed_point_f64(xs[0], e) - c0e), absd(fixed_point_f64(xs[m - 1], e) - c0e));
-  const int p0 = e + std::max(0, bitlen(span0) - 30);
-  const int64_t C0 = fixed_point_f64(model->root[1], p0);
-  *root_P0 = p0;
-  *root_C0 = C0;
-  *root_RA = (int32_t)floor_scaled(model->root[0] * (double)L, p0 + 40, 0.0, INT31);
-  *root_RB = floor_scaled(model->root[2] * (double)L, 40, -9.0e18, 9.0e18);
-  // Leaf ranges of the sorted sample under the FP64 routing used in training.
-  std::vector<uint64_t> beg(L, 0), end(L, 0);
-  std::vector<char> seen(L, 0);
-  for (uint64_t k = 0; k < m; ++k) {
-    const uint32_t l = leaf_of(model, xs[k]);
-    if (!seen[l]) { seen[l] = 1; beg[l] = k; }
-    end[l] = k + 1;
-  }
-  for (uint32_t l = 0; l < L; ++l) {
-    const double* q = model->leaf + 5 * (size_t)l;
-    if (!seen[l]) {
-      C[l] = 0; P[l] = e; A[l] = 0.0f;
-    } else {
-      const int64_t ce = fixed_point_f64(q[1], e);
-      const uint64_t span = std::max(absd(fixed_point_f64(xs[beg[l]], e) - ce),
-                                     absd(fixed_point_f64(xs[end[l] - 1], e) - ce));
-      const int pl = e + std::max(0, bitlen(span) - 30);
-      P[l] = pl;
-      C[l] = fixed_point_f64(q[1], pl);
-      A[l] = fp32_sat(std::ldexp(q[0], pl));
-    }
-    B[l] = (float)q[2];
-    LO[l] = (float)q[3];
-    HI[l] = (float)q[4];
-  }
-}
-
-int64_t lso_spec_fixed_point(const void* keys, uint64_t i, int dtype, int32_t E) {
-  switch (dtype) {
-    case LSO_F64: return fixed_point_f64(((const double*)keys)[i], E);
-    case LSO_F32: return fixed_point_f32(((const float*)keys)[i], E);
-    case LSO_U64: {
-      const uint64_t x = ((const uint64_t*)keys)[i];
-      return fixed_point(false, x, 0, E);
-    }
-    case LSO_U32: {
-      const uint64_t x = ((const uint32_t*)keys)[i];
-      return fixed_point(false, x, 0, E);
-    }
-  }
-  return 0;
-}
-
-static int key_nan(const void* keys, uint64_t i, int dtype, int* negative) {
-  if (dtype == LSO_F64) {
-    const double x = ((const double*)keys)[i];
-    *negative = std::signbit(x);
-    return std::isnan(x);
-  }
-  if (dtype == LSO_F32) {
-    const float x = ((const float*)keys)[i];
-    *negative = std::signbit(x);
-    return std::isnan(x);
-  }
-  *negative = 0;
-  return 0;
-}
-
-static int32_t spec_t0(const lso_eval* ev, const void* keys, uint64_t i, int dtype) {
-  const int64_t T0 = (1ll << 30) - 1;
-  int64_t t = lso_spec_fixed_point(keys, i, dtype, ev->root_P0) - ev->root_C0;
-  t = std::min(T0, std::max(-T0, t));
-  return (int32_t)t;
-}
-
-static uint32_t spec_leaf(const lso_eval* ev, int32_t t0) {
-  const int64_t v = (int64_t)ev->root_RA * (int64_t)t0 + ev->root_RB;
-  int64_t l = v >> 40;  // arithmetic shift: floor
-  if (l < 0) l = 0;
-  if (l >= (int64_t)ev->leaves) l = ev->leaves - 1;
-  return (uint32_t)l;
-}
-
-float lso_spec_F_fine(const lso_eval* ev, const void* keys, uint64_t i, int dtype) {
-  int negative;
-  if (key_nan(keys, i, dtype, &negative)) return negative ? -1.0f : 2.0f;
-  const uint32_t l = spec_leaf(ev, spec_t0(ev, keys, i, dtype));
-  const int64_t LIM = 2147483647;
-  int64_t d = lso_spec_fixed_point(keys, i, dtype, ev->P[l]) - ev->C[l];
-  d = std::min(LIM, std::max(-LIM, d));
-  float F = std::fmaf(ev->A[l], (float)(int32_t)d, ev->B[l]);
-  F = std::fmax(F, ev->LO[l]);
-  F = std::fmin(F, ev->HI[l]);
-  return F;
-}
 
 // Alg. 1 at level 0: pos(x) = clamp(floor(F(x) * f0), 0, f0 - 1) with the
 // FP64 model (the same expression the oracle's Partition uses).

@@ -13,8 +13,8 @@
  * keys in ascending IEEE total order (unsigned order for integers).
  * Part 3 (lso_spec_*) restates, independently of the CUDA sources, the
  * per-key arithmetic that the GPU kernels document (sample indices, heavy
- * set, the FP64 level-0 bucket map and its thresholds, the fine FP32
- * estimate) so that single kernels can be checked.
+ * set, the FP64 level-0 bucket map and its thresholds, the extended-slot
+ * histogram) so that single kernels can be checked.
  */
 #ifndef LSO_H
 #define LSO_H
@@ -91,39 +91,14 @@ void lso_defragment_f64(double* a, uint64_t m, uint32_t f, const uint64_t* sizes
 
 /* ---- Part 3: spec functions for kernel parity (see header comment) ---- */
 
-/* The GPU evaluation parameters.
- * Level 0: bucket(x) = clamp(floor(F(x) * f0), 0, f0 - 1) with the FP64 model
- *   (Alg. 1); its thresholds thr[b] = min { total-order key t : bucket >= b }.
- * Fine (level-1 split, in-bucket slots), FP32, with fx(x, P) = floor(x * 2^-P)
- *   saturated to +-2^62: t0 = clamp(fx(x, P0) - C0, +-(2^30-1)),
- *   leaf = clamp((RA*t0 + RB) >> 40, 0, L-1),
- *   F = clamp(fmaf(A_l, clamp(fx(x, P_l) - C_l, +-(2^31-1)), B_l), LO_l, HI_l). */
+/* The GPU's level-0 map: bucket(x) = clamp(floor(F(x) * f0), 0, f0 - 1) with
+ * the FP64 model (Alg. 1); its thresholds thr[b] = min { total-order key t :
+ * bucket >= b }. */
 typedef struct lso_eval {
-  const lso_model* model;  /* FP64 model (level 0) */
-  int32_t E;           /* exponent of the sample's fixed-point grid */
-  uint32_t leaves;
-  uint32_t f0;         /* level-0 fan-out */
-  int32_t root_P0;
-  int64_t root_C0;
-  int32_t root_RA;
-  int64_t root_RB;
-  const int64_t* C;    /* per leaf, fine */
-  const int32_t* P;
-  const float* A;
-  const float* B;
-  const float* LO;
-  const float* HI;
+  const lso_model* model;  /* FP64 model */
+  uint32_t f0;             /* level-0 fan-out */
 } lso_eval;
 
-/* Derive the fine evaluation parameters from an FP64 model; the per-leaf
- * feature spans come from the first/last finite sorted sample key of each leaf. */
-void lso_spec_eval_params(const lso_model* model, const double* sorted_x, uint64_t m, int dtype,
-                          int32_t* E, int32_t* root_P0, int64_t* root_C0, int32_t* root_RA,
-                          int64_t* root_RB, int64_t* C, int32_t* P, float* A, float* B,
-                          float* LO, float* HI);
-int64_t lso_spec_fixed_point(const void* keys, uint64_t i, int dtype, int32_t E);
-/* Fine FP32 eCDF estimate of key i; returns -1 / 2 for negative / positive NaN. */
-float lso_spec_F_fine(const lso_eval* ev, const void* keys, uint64_t i, int dtype);
 /* Level-0 bucket of key i: clamp(floor(F(x) * f0), 0, f0-1), FP64 model;
  * NaNs take F = 0 / 1 by sign. */
 uint32_t lso_spec_bucket(const lso_eval* ev, const void* keys, uint64_t i, int dtype);

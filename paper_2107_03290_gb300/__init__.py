@@ -110,11 +110,7 @@ class ModelExport(ctypes.Structure):
     _fields_ = [("leaves", ctypes.c_uint32), ("max_heavy", ctypes.c_uint32),
                 ("sample_size", ctypes.c_uint64), ("sample_finite", ctypes.c_uint64),
                 ("root", ctypes.c_double * 3), ("leaf", ctypes.c_void_p),
-                ("E", ctypes.c_int32), ("root_P0", ctypes.c_int32), ("root_C0", ctypes.c_int64),
-                ("root_RA", ctypes.c_int32), ("root_RB", ctypes.c_int64),
                 ("fanout", ctypes.c_uint32), ("pos_max", ctypes.c_uint32), ("thr", ctypes.c_void_p),
-                ("C", ctypes.c_void_p), ("P", ctypes.c_void_p), ("A", ctypes.c_void_p),
-                ("B", ctypes.c_void_p), ("LO", ctypes.c_void_p), ("HI", ctypes.c_void_p),
                 ("sorted_sample_tk", ctypes.c_void_p), ("heavy_tk", ctypes.c_void_p),
                 ("n_heavy", ctypes.c_uint64), ("tau", ctypes.c_uint64)]
 
@@ -309,11 +305,7 @@ def train(t, params: Params | None = None, stream=None, with_sample: bool = Fals
     out = ModelExport()
     out.leaves = L
     out.fanout = MAX_FANOUT
-    arr = {"leaf": np.zeros((L, 5), np.float64), "thr": np.zeros(MAX_FANOUT, np.uint64),
-           "C": np.zeros(L, np.int64),
-           "P": np.zeros(L, np.int32), "A": np.zeros(L, np.float32),
-           "B": np.zeros(L, np.float32), "LO": np.zeros(L, np.float32),
-           "HI": np.zeros(L, np.float32)}
+    arr = {"leaf": np.zeros((L, 5), np.float64), "thr": np.zeros(MAX_FANOUT, np.uint64)}
     heavy = np.zeros(16 * MAX_FANOUT, np.uint64)
     out.max_heavy = heavy.size
     for k, v in arr.items():
@@ -330,8 +322,7 @@ def train(t, params: Params | None = None, stream=None, with_sample: bool = Fals
     res = dict(arr)
     res["thr"] = arr["thr"][:out.fanout].copy()
     res.update(fanout=out.fanout, sample_size=out.sample_size, sample_finite=out.sample_finite,
-               root=np.array(list(out.root)), E=out.E, root_P0=out.root_P0, root_C0=out.root_C0,
-               root_RA=out.root_RA, root_RB=out.root_RB,
+               root=np.array(list(out.root)),
                heavy_tk=heavy[:out.n_heavy].copy(), tau=out.tau, pos_max=out.pos_max)
     if smp is not None:
         res["sorted_sample_tk"] = smp[:out.sample_size].copy()

@@ -211,7 +211,7 @@ struct Workspace {
   size_t bytes = 0;
   // offsets
   size_t o_scratch, o_smp_a, o_smp_b, o_rank, o_flags, o_cpos, o_cand, o_sel, o_nh, o_part, o_hi,
-      o_tscan, o_rs_hist, o_rs_skip, o_rs_status, o_hdr, o_leaf64, o_thr, o_cell, o_cleaf, o_hkey, o_hval, o_leaff, o_heads, o_heavy,
+      o_tscan, o_rs_hist, o_rs_skip, o_rs_status, o_hdr, o_leaf64, o_thr, o_cell, o_cleaf, o_hkey, o_hval, o_heads, o_heavy,
       o_lbeg, o_lend, o_hist, o_offs, o_l0scan, o_jobs_fill, o_jobs_s, o_jobs_l, o_jobs_m, o_jobs_fb2, o_jobs_r,
       o_jobs_fb, o_jobs_r2, o_jobs_r3, o_pk, o_sid, o_ccount, o_counts, o_aux, o_tot, o_l1cnt, o_l1off, o_l1cur, o_jmin, o_jmax, o_l1scan,
       o_ubase, o_units;
@@ -250,7 +250,6 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->o_cleaf = c.take<CellLeaf>(P.L);
   w->o_hkey = c.take<uint64_t>(HASH_SIZE);
   w->o_hval = c.take<uint16_t>(HASH_SIZE);
-  w->o_leaff = c.take<LeafFine>(P.L + 1);
   w->o_heads = c.take<BucketHead>(P.f0 + 1);
   w->o_heavy = c.take<HeavyEntry>((size_t)P.f0 * std::max<uint32_t>(1, P.hpb));
   w->o_lbeg = c.take<uint32_t>(P.L);
@@ -307,7 +306,6 @@ static Bound bind(const Plan& P, const Workspace& w) {
   b.M.cleaf = at<CellLeaf>(w, w.o_cleaf);
   b.M.hkey = at<uint64_t>(w, w.o_hkey);
   b.M.hval = at<uint16_t>(w, w.o_hval);
-  b.M.leaff = at<LeafFine>(w, w.o_leaff);
   b.M.heads = at<BucketHead>(w, w.o_heads);
   b.M.heavy = at<HeavyEntry>(w, w.o_heavy);
   b.M.leaf_beg = at<uint32_t>(w, w.o_lbeg);
@@ -656,11 +654,6 @@ ls_status ls_train(const void* keys, size_t n, ls_dtype dtype, void* stream,
     out->sample_size = hdr.s;
     out->sample_finite = hdr.s_fin;
     std::memcpy(out->root, hdr.root64, sizeof(out->root));
-    out->E = hdr.root.E;
-    out->root_P0 = hdr.root.P0;
-    out->root_C0 = hdr.root.C0;
-    out->root_RA = hdr.root.RA;
-    out->root_RB = hdr.root.RB;
     out->tau = P.tau;
     out->n_heavy = hdr.nheavy;
     if (out->leaf) cudaMemcpy(out->leaf, b.M.leaf64, 5 * sizeof(double) * P.L, cudaMemcpyDeviceToHost);
@@ -668,16 +661,6 @@ ls_status ls_train(const void* keys, size_t n, ls_dtype dtype, void* stream,
     if (out->thr && out->fanout >= P.f0)
       cudaMemcpy(out->thr, b.M.thr, sizeof(uint64_t) * P.f0, cudaMemcpyDeviceToHost);
     out->fanout = P.f0;
-    std::vector<LeafFine> lf(P.L + 1);
-    cudaMemcpy(lf.data(), b.M.leaff, sizeof(LeafFine) * (P.L + 1), cudaMemcpyDeviceToHost);
-    for (uint32_t l = 0; l < P.L; ++l) {
-      if (out->C) out->C[l] = lf[l].C;
-      if (out->P) out->P[l] = lf[l].P;
-      if (out->A) out->A[l] = lf[l].A;
-      if (out->B) out->B[l] = lf[l].B;
-      if (out->LO) out->LO[l] = lf[l].LO;
-      if (out->HI) out->HI[l] = lf[l + 1].LO;
-    }
     if (out->sorted_sample_tk)
       cudaMemcpy(out->sorted_sample_tk, b.T.smp_a, 8 * P.s, cudaMemcpyDeviceToHost);
     if (out->heavy_tk && hdr.nheavy) {

@@ -15,7 +15,6 @@ constexpr int MAX_LEAVES = 4096;
 constexpr int MAX_FANOUT = 4096;
 constexpr int MAX_HPB = 15;         // equality buckets per level-0 bucket (4-bit count)
 constexpr int MAX_F1 = 1024;        // level-1 sub-buckets per segment
-constexpr int64_t Q_SAT = (int64_t)1 << 62;
 constexpr unsigned long long SPIN_LIMIT = 1ull << 26;  // bounded waits
 
 // Device status word bits (ls_stream_status).
@@ -72,63 +71,6 @@ template <> struct KT<LS_U32> {
   __device__ static inline double dbl(U u) { return (double)u; }
 };
 
-// ------------------------------------------------------------------ fixed point
-// fx(x, P) = floor(x * 2^-P) saturated to [-2^62, 2^62] for a non-NaN key
-// (infinities saturate).  |x| = M * 2^exp2.  Integer operations only, exact,
-// hence monotone in x.  For the usual right shift j = P - exp2 > 0 the floor of
-// a negative value is ~((M - 1) >> j).
-__device__ __forceinline__ int64_t fx_core(bool neg, uint64_t M, int exp2, int P) {
-  // Branch-free (selects only) so that the keys a thread holds interleave.
-  const int j = P - exp2;                          // right shift
-  const int jr = j < 1 ? 1 : (j > 63 ? 63 : j);
-  const int64_t rpos = (int64_t)(M >> jr);
-  const int64_t rneg = (int64_t)~((M - 1) >> jr);  // floor(-M / 2^j), M >= 1
-  int64_t r = neg ? rneg : rpos;
-  r = (j >= 64) ? (neg ? -1 : 0) : r;
-  const int k = -j;                                // left shift (j <= 0)
-  const int kk = k < 0 ? 0 : (k > 62 ? 62 : k);
-  const bool ok = (k <= 62) && (M <= (1ull << (62 - kk)));
-  const int64_t lv = ok ? (int64_t)(M << kk) : Q_SAT;
-  r = (j <= 0) ? (neg ? -lv : lv) : r;
-  return M == 0 ? 0 : r;
-}
-
-__device__ __forceinline__ int64_t fx_f64bits(uint64_t u, int P) {
-  const bool neg = (u >> 63) != 0;
-  const int e = (int)((u >> 52) & 0x7FF);
-  const uint64_t M = (u & ((1ull << 52) - 1)) | ((uint64_t)(e != 0) << 52);
-  const int64_t r = fx_core(neg, M, (e ? e : 1) - 1075, P);
-  return e == 0x7FF ? (neg ? -Q_SAT : Q_SAT) : r;
-}
-
-template <int DT> __device__ __forceinline__ int64_t fixed_point(typename KT<DT>::U u, int P);
-template <> __device__ __forceinline__ int64_t fixed_point<LS_F64>(uint64_t u, int P) {
-  return fx_f64bits(u, P);
-}
-template <> __device__ __forceinline__ int64_t fixed_point<LS_F32>(uint32_t u, int P) {
-  const bool neg = (u >> 31) != 0;
-  const int e = (int)((u >> 23) & 0xFF);
-  const uint64_t M = (uint64_t)((u & ((1u << 23) - 1)) | ((uint32_t)(e != 0) << 23));
-  const int64_t r = fx_core(neg, M, (e ? e : 1) - 150, P);
-  return e == 0xFF ? (neg ? -Q_SAT : Q_SAT) : r;
-}
-template <> __device__ __forceinline__ int64_t fixed_point<LS_U64>(uint64_t u, int P) {
-  return fx_core(false, u, 0, P);
-}
-template <> __device__ __forceinline__ int64_t fixed_point<LS_U32>(uint32_t u, int P) {
-  return fx_core(false, (uint64_t)u, 0, P);
-}
-
-// Centred 32-bit feature: clamp(fx - C, +-lim).
-__device__ __forceinline__ int feat32(int64_t fx, int64_t C, int64_t lim) {
-  int64_t d = fx - C;
-  d = d > lim ? lim : d;
-  d = d < -lim ? -lim : d;
-  return (int)d;
-}
-constexpr int64_t T0_LIM = (1ll << 30) - 1;   // root feature range
-constexpr int64_t TF_LIM = 2147483647ll;      // fine feature range
-
 // ------------------------------------------------------------------ model
 // Two evaluations of the same monotone model F:
 //  * level 0 (buckets): the bucket of key x is pos(x) = clamp(floor(F(x) * f0),
@@ -140,27 +82,11 @@ constexpr int64_t TF_LIM = 2147483647ll;      // fine feature range
 //    FP32 image of the key, cell = floor(F32(x) * L0_CELLS); the cell table
 //    holds, per cell, the bucket range of the keys in it.  Any monotone cell
 //    map gives the exact bucket; a good one only makes the ranges short;
-//  * fine (level-1 split, in-bucket slots), FP32 on the leaf's own grid:
-//      F = clamp(A_l * clamp(fx(x, P_l) - C_l) + B_l, LO_l, HI_l),  HI_l = LO_{l+1}.
+// The same FP32 estimate (cell_F) also gives the level-1 sub-bucket of a key and
+// the F value of each heavy value.
 constexpr int L0_CELL_BITS = 12;
 constexpr uint32_t L0_CELLS = 1u << L0_CELL_BITS;
 constexpr uint32_t L0_TABLE = L0_CELLS;
-struct LeafFine {      // 32 bytes; record L is a sentinel with LO = 1
-  long long C;
-  float A;
-  int P;
-  float B, LO;
-  int pad0, pad1;
-};
-struct RootEval {
-  long long C0;        // root feature centre on the grid 2^P0
-  long long RB;        // leaf intercept * 2^40
-  int RA;              // leaf slope * 2^40 per root-feature unit
-  int P0;
-  int E;
-  int L;
-};
-
 struct HeavyEntry {    // a heavy value of one level-0 bucket
   uint64_t tk;         // total-order key
   float F;             // FP32 eCDF estimate of the value
@@ -181,40 +107,6 @@ struct BucketHead {
   uint32_t ext_base;
   uint32_t hoff_nh;    // hoff << 4 | nh
 };
-
-template <int DT>
-__device__ __forceinline__ int root_t0(typename KT<DT>::U u, const RootEval& r) {
-  return feat32(fixed_point<DT>(u, r.P0), r.C0, T0_LIM);
-}
-__device__ __forceinline__ int leaf_of_t0(int t0, const RootEval& r) {
-  const long long v = (long long)r.RA * (long long)t0 + r.RB;
-  int l = (int)(v >> 40);
-  l = l < 0 ? 0 : l;
-  return l >= r.L ? r.L - 1 : l;
-}
-
-template <int DT>
-__device__ __forceinline__ int predict_leaf(typename KT<DT>::U u, const RootEval& r) {
-  return leaf_of_t0(root_t0<DT>(u, r), r);
-}
-
-// Fine feature of a key in leaf l.
-template <int DT>
-__device__ __forceinline__ float fine_feature(typename KT<DT>::U u, const LeafFine& f) {
-  return __int2float_rn(feat32(fixed_point<DT>(u, f.P), f.C, TF_LIM));
-}
-
-// Fine FP32 eCDF estimate F(x) for a non-NaN key.
-template <int DT>
-__device__ __forceinline__ float predict_F(typename KT<DT>::U u, const RootEval& r,
-                                           const LeafFine* __restrict__ lf) {
-  const int l = predict_leaf<DT>(u, r);
-  const LeafFine f = lf[l];
-  float F = __fmaf_rn(f.A, fine_feature<DT>(u, f), f.B);
-  F = fmaxf(F, f.LO);
-  F = fminf(F, lf[l + 1].LO);
-  return F;
-}
 
 // Monotone (non-decreasing) FP32 image of a non-NaN key: doubles are
 // truncated toward zero (magnitudes below FLT_MIN become 0, above FLT_MAX
@@ -432,7 +324,6 @@ cudaError_t status_word_ptr(uint32_t** out);
 
 // Model storage in device memory (one per sort call / array).
 struct DevModel {
-  RootEval root;           // integer routing of the fine evaluation
   double root64[3];        // a, c, b
   uint64_t s, s_fin, s_lo; // sample size, finite keys, index of first finite
   uint32_t nheavy;
@@ -456,7 +347,6 @@ struct ModelPtrs {         // device pointers of one model
   CellLeaf* cleaf;         // L cell-index leaves
   uint64_t* hkey;          // HASH_SIZE heavy-table keys
   uint16_t* hval;          // HASH_SIZE heavy-table equality slots
-  LeafFine* leaff;         // L + 1 (sentinel record L: LO = 1)
   BucketHead* heads;       // f0 + 1
   HeavyEntry* heavy;       // max heavy
   uint32_t* leaf_beg;      // L (sample index ranges per leaf)

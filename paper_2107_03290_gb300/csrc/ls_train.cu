@@ -271,36 +271,21 @@ __global__ void k_fit_leaf_final(const uint64_t* __restrict__ tk, const uint32_t
   q[4] = 0;
 }
 
-__device__ __forceinline__ int bitlen64(uint64_t v) { return v ? 64 - __clzll((long long)v) : 0; }
 
-__device__ __forceinline__ float fp32_sat(double d) {
+__device__ __forceinline__ float fp32_sat(double d) {  // round to FP32, finite
   if (d >= (double)FLT_MAX) return FLT_MAX;
+  if (d <= -(double)FLT_MAX) return -FLT_MAX;
   return __double2float_rn(d);
 }
 
-__device__ __forceinline__ uint64_t absdiff(int64_t a, int64_t b) {
-  const int64_t d = a - b;
-  return d < 0 ? (uint64_t)(-d) : (uint64_t)d;
-}
 
-// Fixed-point conversion used by the level-0 tables: floor(v * 2^k) clamped
-// to [lo, hi] (v >= 0 or any sign for the intercepts).
-__device__ __forceinline__ long long floor_scaled(double v, int k, double lo, double hi) {
-  double w = floor(ldexp(v, k));
-  w = w < lo ? lo : w;
-  w = w > hi ? hi : w;
-  return (long long)w;
-}
 
-// Empty leaves, hi bounds, and the fine FP32 evaluation records.
+// Empty leaves, hi bounds (hi_l = lo_{l+1}), and the FP32 records of the cell
+// index (the RMI rewritten on x: L root(x) = L a x + L (b - a c); leaf
+// F = clamp(a x + (b - a c), lo, hi)).
 template <int DT>
 __global__ void __launch_bounds__(1024)
-k_fit_final(const uint64_t* __restrict__ tk, DevModel* hdr, int L, const uint32_t* leaf_beg,
-            const uint32_t* leaf_end, double* leaf, LeafFine* lf, CellLeaf* cleaf) {
-  __shared__ int s_E, s_P0;
-  __shared__ long long s_C0;
-  const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
-  const double INT31 = 2147483647.0;
+k_fit_final(DevModel* hdr, int L, double* leaf, CellLeaf* cleaf) {
   // next non-empty leaf to the right, by one warp over L/32-leaf ranges
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
@@ -324,32 +309,8 @@ k_fit_final(const uint64_t* __restrict__ tk, DevModel* hdr, int L, const uint32_
       next_lo = q[3];
     }
     if (lane == 0) {
-      double R = 0;
-      if (m) {
-        const double x0 = sample_x<DT>(tk, lo, 0), x1 = sample_x<DT>(tk, lo, m - 1);
-        R = fmax(fabs(x0), fabs(x1));
-      }
-      const int E = (R > 0) ? ilogb(R) + 1 - 61 : 0;
       const double* r = hdr->root64;
-      const int64_t c0 = fx_f64bits((uint64_t)__double_as_longlong(r[1]), E);
-      uint64_t span = 0;
-      if (m) {
-        span = max(absdiff(fx_f64bits((uint64_t)__double_as_longlong(sample_x<DT>(tk, lo, 0)), E), c0),
-                   absdiff(fx_f64bits((uint64_t)__double_as_longlong(sample_x<DT>(tk, lo, m - 1)), E), c0));
-      }
-      const int P0 = E + max(0, bitlen64(span) - 30);
-      s_E = E;
-      s_P0 = P0;
-      s_C0 = fx_f64bits((uint64_t)__double_as_longlong(r[1]), P0);
-      RootEval re;
-      re.C0 = s_C0;
-      re.P0 = P0;
-      re.E = E;
-      re.L = L;
-      re.RA = (int)floor_scaled(__dmul_rn(r[0], (double)L), P0 + 40, 0.0, INT31);
-      re.RB = floor_scaled(__dmul_rn(r[2], (double)L), 40, -9.0e18, 9.0e18);
-      hdr->root = re;
-      CellRoot cr;  // L * root(x) = L a x + L (b - a c), rounded to FP32
+      CellRoot cr;
       cr.A0 = fp32_sat(__dmul_rn((double)L, r[0]));
       cr.B0 = fp32_sat(__dmul_rn((double)L, __dsub_rn(r[2], __dmul_rn(r[0], r[1]))));
       cr.L = L;
@@ -358,34 +319,8 @@ k_fit_final(const uint64_t* __restrict__ tk, DevModel* hdr, int L, const uint32_
     }
   }
   __syncthreads();
-  const int E = s_E;
-  for (int l = threadIdx.x; l <= L; l += blockDim.x) {
-    if (l == L) {  // sentinel: HI of the last leaf
-      LeafFine f;
-      f.C = 0; f.A = 0.0f; f.P = E; f.B = 1.0f; f.LO = 1.0f; f.pad0 = f.pad1 = 0;
-      lf[L] = f;
-      continue;
-    }
+  for (int l = threadIdx.x; l < L; l += blockDim.x) {
     const double* q = leaf + 5 * (size_t)l;
-    LeafFine f;
-    f.pad0 = f.pad1 = 0;
-    const uint32_t b = leaf_beg[l], en = leaf_end[l];
-    if (en <= b) {
-      f.C = 0; f.P = E; f.A = 0.0f;
-    } else {
-      const uint64_t cb = (uint64_t)__double_as_longlong(q[1]);
-      const int64_t ce = fx_f64bits(cb, E);
-      const uint64_t span =
-          max(absdiff(fx_f64bits((uint64_t)__double_as_longlong(sample_x<DT>(tk, lo, b)), E), ce),
-              absdiff(fx_f64bits((uint64_t)__double_as_longlong(sample_x<DT>(tk, lo, en - 1)), E), ce));
-      const int P = E + max(0, bitlen64(span) - 30);
-      f.P = P;
-      f.C = fx_f64bits(cb, P);
-      f.A = fp32_sat(ldexp(q[0], P));
-    }
-    f.B = __double2float_rn(q[2]);
-    f.LO = __double2float_rn(q[3]);
-    lf[l] = f;
     CellLeaf cl;
     cl.A = fp32_sat(q[0]);
     cl.B = fp32_sat(__dsub_rn(q[2], __dmul_rn(q[0], q[1])));
@@ -689,8 +624,7 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   }
   k_fit_leaf_final<DT><<<(L + 255) / 256, 256, 0, st>>>(W.smp_a, W.rank, M.hdr, M.leaf_beg,
                                                        M.leaf_end, W.ubase, W.units, L, M.leaf64);
-  k_fit_final<DT><<<1, 1024, 0, st>>>(W.smp_a, M.hdr, L, M.leaf_beg, M.leaf_end, M.leaf64,
-                                      M.leaff, M.cleaf);
+  k_fit_final<DT><<<1, 1024, 0, st>>>(M.hdr, L, M.leaf64, M.cleaf);
   k_thresholds<DT><<<(P.f0 + 1 + 127) / 128, 128, 0, st>>>(M.hdr, M.leaf64, L, P.f0, M.thr);
   k_cell_table<DT><<<(L0_CELLS + 127) / 128, 128, 0, st>>>(M.hdr, M.thr, P.f0, M.cleaf, M.cell);
   // heavy values
