@@ -141,8 +141,8 @@ ls_status ls_stream_status(void* stream);
 
 /* Stage entry points (used by the kernel parity tests). */
 
-/* Train the RMI on the sample of `keys` (sample, sort, FP64 fit, FP32
- * evaluation parameters, heavy set) and copy the model to `out` (host).
+/* Train the RMI on the sample of `keys` (sample, sort, FP64 fit, level-0
+ * thresholds, heavy set) and copy the model to `out` (host).
  * Synchronizes `stream`. */
 ls_status ls_train(const void* keys, size_t n, ls_dtype dtype, void* stream,
                    const ls_params* params, ls_model_export* out);
