@@ -591,6 +591,136 @@ ls_status ls_sort(void* keys, size_t n, ls_dtype dtype, void* stream) {
   return ls_sort_ex(keys, n, dtype, stream, nullptr, nullptr);
 }
 
+// Batched sort of many independent arrays in one launch sequence.  Every job
+// record names its own array (and its region of one shared scratch buffer), so
+// thousands of arrays share the same kernels: arrays of at most 8192 keys are
+// in-bucket jobs from the start; larger ones enter the key-range levels (each
+// array split by a line through its own key range, twice), and all finish in
+// the shared in-bucket sort, fill and fallback launches.
+ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dtype dtype,
+                        void* stream) {
+  if (count > 0 && (!keys || !n)) return LS_ERR_INVALID;
+  if (dtype < LS_F64 || dtype > LS_U32) return LS_ERR_INVALID;
+  const int W = width_of(dtype);
+  uint64_t N = 0;
+  for (size_t i = 0; i < count; ++i) {
+    const ls_status v = validate(keys[i], n[i], dtype);
+    if (v) return v;
+    if (n[i] >= 2) N += n[i];
+  }
+  if (N == 0) return LS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  Device* d;
+  cudaError_t e = get_device(&d);
+  if (e) return to_status(e);
+  if ((e = configure(d, dtype))) return to_status(e);
+  SortLimits lim;
+  lim.c_small = 2048;
+  lim.c_mid = 4096;
+  lim.c_large = 8192;
+  lim.l1_target = 3072;
+  const uint64_t capj = count + N / (lim.c_large + 1) + 16;
+  const uint64_t cap_c = N / (lim.l1_target >> 4) + capj + 64;
+  const uint64_t cap1 = cap_c + count + 64;
+  // workspace
+  Carver c;
+  const size_t o_scr = c.take<uint8_t>(N * W);
+  size_t o_list[10];
+  const uint64_t caps[10] = {cap1, cap1, cap1, cap1, cap1, capj, capj, cap1, cap1, 1};
+  for (int i = 0; i < 10; ++i) o_list[i] = c.take<Job>(caps[i]);
+  const size_t o_counts = c.take<unsigned long long>(16);
+  const size_t o_aux = c.take<uint8_t>((capj + 1) * 32);
+  const size_t o_tot = c.take<unsigned long long>(4);
+  const size_t o_cnt = c.take<uint32_t>(cap_c);
+  const size_t o_off = c.take<uint64_t>(cap_c + 1);
+  const size_t o_cur = c.take<unsigned long long>(cap_c);
+  const size_t o_jmin = c.take<unsigned long long>(capj);
+  const size_t o_jmax = c.take<unsigned long long>(capj);
+  const uint64_t tiles = std::max<uint64_t>(1, (cap_c + SC_TILE - 1) / SC_TILE);
+  const size_t scan_bytes = (tiles + 1) * sizeof(uint64_t) + 16;
+  const size_t o_scan = c.take<uint8_t>(scan_bytes);
+  Workspace w;
+  w.bytes = c.off + 256;
+  if ((e = ws_alloc(d, &w, st))) return to_status(e);
+  unsigned long long* counts = at<unsigned long long>(w, o_counts);
+  auto mk = [&](int i, int ci) {
+    JobList l;
+    l.jobs = at<Job>(w, o_list[i]);
+    l.count = counts + ci;
+    l.cap = caps[i];
+    return l;
+  };
+  Lists lists;
+  lists.fill = mk(0, 0);
+  lists.sort_s = mk(1, 1);
+  lists.sort_l = mk(2, 2);
+  lists.fallback = mk(3, 4);
+  lists.sort_m = mk(4, 7);
+  lists.refine2 = mk(5, 5);
+  lists.refine3 = mk(6, 6);
+  lists.fill_big = mk(7, 12);
+  lists.refine = mk(8, 3);
+  // initial jobs, one per array
+  std::vector<Job> js, jm, jl, jr;
+  uint64_t off = 0;
+  char* scr = at<char>(w, o_scr);
+  for (size_t i = 0; i < count; ++i) {
+    if (n[i] < 2) continue;
+    Job j{};
+    j.start = 0;
+    j.m = n[i];
+    j.Flo = 0.0;
+    j.Fhi = 1.0;
+    j.src = 0;
+    j.kb = (uint64_t)(uintptr_t)keys[i];
+    j.sb = (uint64_t)(uintptr_t)(scr + off * W);
+    off += n[i];
+    if (n[i] <= lim.c_small) { j.kind = JOB_SORT_RANGE; js.push_back(j); }
+    else if (n[i] <= lim.c_mid) { j.kind = JOB_SORT_RANGE; jm.push_back(j); }
+    else if (n[i] <= lim.c_large) { j.kind = JOB_SORT_RANGE; jl.push_back(j); }
+    else { j.kind = JOB_REFINE; jr.push_back(j); }
+  }
+  unsigned long long hc[16] = {0};
+  hc[1] = js.size(); hc[7] = jm.size(); hc[2] = jl.size(); hc[5] = jr.size();
+  auto put = [&](const std::vector<Job>& v, int i) {
+    return v.empty() ? cudaSuccess
+                     : cudaMemcpyAsync(at<void>(w, o_list[i]), v.data(), v.size() * sizeof(Job),
+                                       cudaMemcpyHostToDevice, st);
+  };
+  if (!e) e = put(js, 1);
+  if (!e) e = put(jm, 4);
+  if (!e) e = put(jl, 2);
+  if (!e) e = put(jr, 5);
+  if (!e) e = cudaMemcpyAsync(counts, hc, sizeof(hc), cudaMemcpyHostToDevice, st);
+  if (!e) {
+    Level1Ws l{};
+    l.aux = at<void>(w, o_aux);
+    l.totals = at<unsigned long long>(w, o_tot);
+    l.cnt = at<uint32_t>(w, o_cnt);
+    l.off = at<uint64_t>(w, o_off);
+    l.cur = at<unsigned long long>(w, o_cur);
+    l.jmin = at<unsigned long long>(w, o_jmin);
+    l.jmax = at<unsigned long long>(w, o_jmax);
+    l.scan_status = at<void>(w, o_scan);
+    l.scan_status_bytes = scan_bytes;
+    l.sid = nullptr;
+    l.cap_c = cap_c;
+    l.cap_jobs = capj;
+    LevelArgs lv[2];
+    lv[0].in = lists.refine2; lv[0].next = lists.refine3; lv[0].mode = 1;
+    lv[0].next_kind = JOB_REFINE; lv[0].kf = 0;
+    lv[1].in = lists.refine3; lv[1].next = lists.fallback; lv[1].mode = 1;
+    lv[1].next_kind = JOB_FALLBACK; lv[1].kf = 0;
+    ModelPtrs M{};
+    e = levels_enqueue(dtype, nullptr, nullptr, N, M, lists, lim, l, lv, 2, d->err, st, d->num_sms);
+    if (!e) e = fill_enqueue(dtype, nullptr, lists, cap1, st, d->num_sms);
+    if (!e) e = buckets_enqueue(dtype, nullptr, nullptr, N, M, lists, cap1, cap1, cap1, counts + 8,
+                                d->err, st, d->num_sms, nullptr, 0);
+  }
+  cudaFreeAsync(w.base, st);
+  return to_status(e);
+}
+
 ls_status ls_sort_host(void* host_keys, size_t n, ls_dtype dtype, void* stream,
                        const ls_params* params) {
   const ls_status v = validate(host_keys, n, dtype);

@@ -235,8 +235,9 @@ k_bucket_sort(typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Model
       __syncthreads();
       continue;
     }
-    const U* src = (job.src ? scratch : keys) + job.start;
-    segment_sort<DT, THREADS, KPT>(keys + job.start, src, (uint32_t)job.m, sm, ss, err);
+    const U* src = (job.src ? job_scratch(job, scratch) : job_keys(job, (U*)keys)) + job.start;
+    segment_sort<DT, THREADS, KPT>(job_keys(job, keys) + job.start, src, (uint32_t)job.m, sm, ss,
+                                   err);
     __syncthreads();
   }
 }
@@ -270,8 +271,11 @@ k_fallback(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, ModelPtrs M, J
     __syncthreads();
     const unsigned long long jid = s_job;
     if (jid >= nj) break;
+    const Job fjob = list.jobs[jid];
+    U* const K = job_keys(fjob, keys);
+    U* const S = job_scratch(fjob, scratch);
     if (threadIdx.x == 0) {
-      const Job job = list.jobs[jid];
+      const Job job = fjob;
       stack[0].start = job.start;
       stack[0].m = (uint32_t)job.m;
       stack[0].buf = job.src;
@@ -288,9 +292,9 @@ k_fallback(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, ModelPtrs M, J
       __syncthreads();
       const StackEnt e = s_e;
       if (e.m == 0xFFFFFFFFu) break;
-      U* X = (e.buf ? scratch : keys) + e.start;
-      U* Y = (e.buf ? keys : scratch) + e.start;
-      U* D = keys + e.start;
+      U* X = (e.buf ? S : K) + e.start;
+      U* Y = (e.buf ? K : S) + e.start;
+      U* D = K + e.start;
       if (e.m <= (uint32_t)C::CAP) {
         segment_sort<DT, 512, 16>(D, X, e.m, sm, ss, err);
         continue;

@@ -242,8 +242,17 @@ struct Job {
   uint64_t value;      // FILL: the key bits to write
   uint32_t src;
   uint32_t kind;
-  uint32_t la, lb;     // SORT: leaves whose [lo, hi] meets [Flo, Fhi]
+  uint32_t la, lb;     // unused by the current kernels (zero)
+  uint64_t kb, sb;     // batched arrays: this job's key / scratch array (0: the call's)
 };
+
+// Buffers of a job: its own array (batched sorts) or the call's.
+template <typename U>
+__device__ __forceinline__ U* job_keys(const Job& j, U* keys) { return j.kb ? (U*)j.kb : keys; }
+template <typename U>
+__device__ __forceinline__ U* job_scratch(const Job& j, U* scratch) {
+  return j.sb ? (U*)j.sb : scratch;
+}
 
 // Leaves whose output range meets [Flo, Fhi): la = last leaf with lo <= Flo,
 // lb = last leaf with lo < Fhi (FP64 lo values of the fitted model).

@@ -506,6 +506,7 @@ __global__ void k_classify0(Level0Args a, Lists lists, SortLimits lim) {
     job.m = size;
     job.value = 0;
     job.src = 1;
+    job.kb = job.sb = 0;
     if (nh && (o & 1u)) {
       job.kind = JOB_FILL;
       job.value = (uint64_t)KT<DT>::from_tk(heavy[hoff + o / 2].tk);
@@ -559,11 +560,11 @@ __global__ void __launch_bounds__(256) k_fill(U* __restrict__ keys, JobList smal
   const uint64_t gtid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   for (unsigned long long j = 0; j < nb; ++j) {
     const Job job = big.jobs[j];
-    fill_range<U>(keys + job.start, job.m, (U)job.value, gtid, stride);
+    fill_range<U>(job_keys(job, keys) + job.start, job.m, (U)job.value, gtid, stride);
   }
   for (unsigned long long j = blockIdx.x; j < ns; j += gridDim.x) {
     const Job job = small.jobs[j];
-    fill_range<U>(keys + job.start, job.m, (U)job.value, threadIdx.x, blockDim.x);
+    fill_range<U>(job_keys(job, keys) + job.start, job.m, (U)job.value, threadIdx.x, blockDim.x);
   }
 }
 
@@ -689,7 +690,7 @@ k_l1_minmax(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, L
     const Job job = la.in.jobs[j];
     const uint64_t off = (t - aux[j].tile_base) * L1_TILE;
     const uint32_t c = (uint32_t)min((uint64_t)L1_TILE, job.m - off);
-    const U* src = (job.src ? scratch : keys) + job.start + off;
+    const U* src = (job.src ? job_scratch(job, scratch) : job_keys(job, keys)) + job.start + off;
     if (threadIdx.x == 0) { s_min = ~0ull; s_max = 0; }
     __syncthreads();
     unsigned long long mn = ~0ull, mx = 0;
@@ -723,7 +724,7 @@ k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Mod
     const Job job = la.in.jobs[j];
     const uint64_t off = (t - x.tile_base) * L1_TILE;
     const uint32_t c = (uint32_t)min((uint64_t)L1_TILE, job.m - off);
-    const U* src = (job.src ? scratch : keys) + job.start + off;
+    const U* src = (job.src ? job_scratch(job, scratch) : job_keys(job, keys)) + job.start + off;
     const uint16_t* ids = w.sid + job.start + off;
     RangeSplit rs{};
     if (la.mode) rs = range_split(w.jmin[j], w.jmax[j], x.f1);
@@ -789,9 +790,9 @@ k_l1_scatter(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, uint64_t n, 
     const Job job = la.in.jobs[j];
     const uint64_t off = (t - x.tile_base) * L1_TILE;
     const uint32_t c = (uint32_t)min((uint64_t)L1_TILE, job.m - off);
-    const U* src = (job.src ? scratch : keys) + job.start + off;
+    const U* src = (job.src ? job_scratch(job, scratch) : job_keys(job, keys)) + job.start + off;
     const uint16_t* idsrc = w.sid + job.start + off;
-    U* dstb = job.src ? keys : scratch;
+    U* dstb = job.src ? job_keys(job, keys) : job_scratch(job, scratch);
     RangeSplit rs{};
     if (la.mode) rs = range_split(w.jmin[j], w.jmax[j], x.f1);
     for (uint32_t s = threadIdx.x; s <= x.f1; s += blockDim.x) lc[s] = 0;
@@ -830,7 +831,7 @@ k_l1_scatter(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, uint64_t n, 
     for (uint32_t p = threadIdx.x; p < c; p += blockDim.x) {
       const uint32_t s = ids[p];
       const uint64_t dst = gp[s] + (p - lc[s]);
-      if (dst < n) dstb[dst] = stage[p]; else set_error(err, ERR_BOUNDS);
+      if (dst - job.start < job.m) dstb[dst] = stage[p]; else set_error(err, ERR_BOUNDS);
     }
     __syncthreads();
   }
@@ -865,6 +866,8 @@ __global__ void k_l1_classify(Lists lists, LevelArgs la, SortLimits lim, Level1W
     (void)sub;
     job.src = pj.src ^ 1u;
     job.la = job.lb = 0;
+    job.kb = pj.kb;
+    job.sb = pj.sb;
     const uint32_t sk = la.mode ? JOB_SORT_RANGE : JOB_SORT;
     if (cntc <= lim.c_small) { job.kind = sk; push_job(lists.sort_s, job, err); }
     else if (cntc <= lim.c_mid) { job.kind = sk; push_job(lists.sort_m, job, err); }
@@ -956,19 +959,12 @@ static cudaError_t level_dt(void* keys, void* scratch, uint64_t n, const ModelPt
   return cudaGetLastError();
 }
 
-cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const ModelPtrs& M,
+cudaError_t levels_enqueue(int dt, void* keys, void* scratch, uint64_t n, const ModelPtrs& M,
                            const Lists& lists, const SortLimits& lim, const Level1Ws& w,
-                           uint32_t kf, uint32_t* err, cudaStream_t st, int num_sms) {
-  // level 1 splits by the model; levels 2 and 3 split what it could not by key range
-  const JobList ins[3] = {lists.refine, lists.refine2, lists.refine3};
-  const JobList outs[3] = {lists.refine2, lists.refine3, lists.fallback};
-  for (int lv = 0; lv < 3; ++lv) {
-    LevelArgs la;
-    la.in = ins[lv];
-    la.next = outs[lv];
-    la.mode = lv == 0 ? 0 : 1;
-    la.next_kind = lv == 2 ? JOB_FALLBACK : JOB_REFINE;
-    la.kf = kf;
+                           const LevelArgs* lvs, int nlv, uint32_t* err, cudaStream_t st,
+                           int num_sms) {
+  for (int lv = 0; lv < nlv; ++lv) {
+    const LevelArgs& la = lvs[lv];
     cudaError_t e = cudaErrorInvalidValue;
     switch (dt) {
       case LS_F64: e = level_dt<LS_F64>(keys, scratch, n, M, lists, la, lim, w, err, st, num_sms); break;
@@ -979,6 +975,23 @@ cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const 
     if (e) return e;
   }
   return cudaSuccess;
+}
+
+cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const ModelPtrs& M,
+                           const Lists& lists, const SortLimits& lim, const Level1Ws& w,
+                           uint32_t kf, uint32_t* err, cudaStream_t st, int num_sms) {
+  // level 1 splits by the model; levels 2 and 3 split what it could not by key range
+  const JobList ins[3] = {lists.refine, lists.refine2, lists.refine3};
+  const JobList outs[3] = {lists.refine2, lists.refine3, lists.fallback};
+  LevelArgs lvs[3];
+  for (int lv = 0; lv < 3; ++lv) {
+    lvs[lv].in = ins[lv];
+    lvs[lv].next = outs[lv];
+    lvs[lv].mode = lv == 0 ? 0 : 1;
+    lvs[lv].next_kind = lv == 2 ? JOB_FALLBACK : JOB_REFINE;
+    lvs[lv].kf = kf;
+  }
+  return levels_enqueue(dt, keys, scratch, n, M, lists, lim, w, lvs, 3, err, st, num_sms);
 }
 
 cudaError_t fill_enqueue(int dt, void* keys, const Lists& lists, uint64_t fill_cap,

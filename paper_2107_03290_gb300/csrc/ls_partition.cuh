@@ -90,6 +90,10 @@ cudaError_t level0_enqueue(int dt, const Level0Args& a, size_t smem_hist, size_t
 cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const ModelPtrs& M,
                            const Lists& lists, const SortLimits& lim, const Level1Ws& w,
                            uint32_t kf, uint32_t* err, cudaStream_t st, int num_sms);
+cudaError_t levels_enqueue(int dt, void* keys, void* scratch, uint64_t n, const ModelPtrs& M,
+                           const Lists& lists, const SortLimits& lim, const Level1Ws& w,
+                           const LevelArgs* lvs, int nlv, uint32_t* err, cudaStream_t st,
+                           int num_sms);
 cudaError_t fill_enqueue(int dt, void* keys, const Lists& lists, uint64_t fill_cap,
                          cudaStream_t st, int num_sms);
 cudaError_t buckets_configure(int dt);

@@ -192,14 +192,4 @@ ls_status ls_server_destroy(ls_server* s) {
   return LS_OK;
 }
 
-ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dtype dtype,
-                        void* stream) {
-  if (count > 0 && (!keys || !n)) return LS_ERR_INVALID;
-  for (size_t i = 0; i < count; ++i) {
-    const ls_status rc = ls_sort(keys[i], n[i], dtype, stream);
-    if (rc != LS_OK) return rc;
-  }
-  return LS_OK;
-}
-
 }  // extern "C"

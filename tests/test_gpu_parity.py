@@ -250,6 +250,35 @@ def test_sort_batch():
         assert_same(t.cpu().numpy(), a)
 
 
+BATCH_MIX = [("normal", 0), ("normal", 1), ("uniform_u64", 2), ("two_values", 3),
+             ("normal", 2047), ("zipf_lognormal", 2048), ("normal", 2049), ("uniform_u64", 4096),
+             ("exponential_f32", 4097), ("f64_specials", 8192), ("f32_specials", 8193),
+             ("heavy_99.99", 50_000), ("zipf_lognormal", 300_001), ("timestamp_u32", 200_000),
+             ("uniform_u64", 1_000_003), ("gauss_mix", 777_777)]
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.uint64, np.float32, np.uint32])
+def test_sort_batch_mixed_sizes(dt):
+    """Arrays of every size class (in-bucket jobs, key-range levels) in one call."""
+    arrays = []
+    for d, n in BATCH_MIX:
+        a = make(d, n)
+        if a.dtype != dt:  # re-type the distribution's values for this dtype
+            a = a.astype(np.float64)
+            if np.dtype(dt).kind == "u":
+                a = np.nan_to_num(a, nan=0.0, posinf=1e18, neginf=0.0)
+                a = np.abs(a) * (1 << 20)
+                a = np.minimum(a, float(np.iinfo(dt).max) / 2)
+            a = a.astype(dt)
+        arrays.append(a)
+    ts = [torch.from_numpy(a.copy()).cuda() for a in arrays]
+    ls.sort_batch_(ts)
+    torch.cuda.synchronize()
+    assert ls.stream_status() == 0
+    for a, t in zip(arrays, ts):
+        assert_same(t.cpu().numpy(), a)
+
+
 def test_server_alone_equals_mix():
     """Each request's result is the same alone and in a concurrent mix."""
     arrays = [make(d, n) for d, n in [("normal", 300_000), ("zipf_lognormal", 1_000_000),
