@@ -151,6 +151,56 @@ def run_reference(args, rank: int):
     print(json.dumps(out), flush=True)
 
 
+def run_batched(ls, torch, count: int, steps: int, warmup: int, with_loop: bool = True):
+    """Batched workload: `count` float64 arrays (lognormal sizes, median 64K,
+    clipped to [1K, 4M]; N(0,1) / U[0,1) / Zipf(1.1) over 10^4 values), sorted
+    by one ls_sort_batch call per step; baseline: ls_sort on each array in turn
+    on the same stream.  Inputs restored from a device copy outside the timing."""
+    arrays = lsgen.batch_arrays(count, seed=6)
+    sizes = [a.size for a in arrays]
+    total = int(sum(sizes))
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    host = torch.from_numpy(np.concatenate(arrays))
+    pristine = host.to("cuda")
+    work = torch.empty_like(pristine)
+    views = [work[offs[i]:offs[i + 1]] for i in range(count)]
+    st = torch.cuda.current_stream()
+
+    def timed(fn, k):
+        ms = []
+        for _ in range(k):
+            work.copy_(pristine)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    batch = lambda: ls.sort_batch_(views)
+    loop = lambda: [ls.sort_(v) for v in views]
+    timed(batch, warmup)
+    mb = timed(batch, steps)
+    ok = True
+    res = work.cpu().numpy()
+    for i in (0, count // 2, count - 1):
+        seg = res[offs[i]:offs[i + 1]]
+        ok = ok and bool(np.all(seg[1:] >= seg[:-1]))
+    out = {"workload": f"batch_{count}_f64", "arrays": count, "keys": total,
+           "batched_ms": float(np.median(mb)), "batched_keys_per_s": total / (np.median(mb) / 1e3),
+           "steps": steps, "warmup": warmup, "sorted_sampled": ok}
+    if with_loop:
+        timed(loop, 1)
+        ml = timed(loop, max(1, steps // 2))
+        out.update(loop_ms=float(np.median(ml)), loop_keys_per_s=total / (np.median(ml) / 1e3),
+                   batched_vs_loop=float(np.median(ml) / np.median(mb)))
+    del pristine, work, views
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -163,6 +213,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=10_000_000)
     ap.add_argument("--ref-sample", type=int, default=2_000_000)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch", type=int, default=4096, help="arrays of the batched line (0: skip)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
@@ -282,6 +333,10 @@ def main():
         cpu = {"value": smp / tc, "unit": "keys/s", "cores": 1, "kind": "oracle",
                "sample": f"first {smp} keys of the workload, one oracle LearnedSort 2.0 call"}
 
+    batched = None
+    if args.batch > 0 and rank == 0:
+        batched = run_batched(ls, torch, args.batch, steps=5, warmup=2)
+
     if rank == 0:
         last = per[-1]
         out = {"metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": world,
@@ -294,7 +349,7 @@ def main():
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": int(launches), "clocks": clk.summary(),
                "wall_ms_per_step": 1000 * wall / args.steps, "correct": ok,
-               "kernels_ms": kms,
+               "kernels_ms": kms, "batched": batched,
                "path": {k: last[k] for k in ("n_heavy", "n_ext", "max_bucket", "n_eq_keys",
                                              "n_level1", "n_segments", "n_fallback", "n_fill",
                                              "n_launches", "sample_size")}}

@@ -139,6 +139,7 @@ static void plan_call(const ls_params* prm, int dt, uint64_t n, uintptr_t addr, 
   s = std::min<uint64_t>(s, 1ull << 29);
   P->s = std::max<uint64_t>(s, 1);
   P->seed = p.seed;
+  P->lim.c_tiny = 512;
   P->lim.c_small = 2048;
   P->lim.c_mid = 4096;
   P->lim.c_large = 8192;
@@ -188,7 +189,7 @@ static void plan_call(const ls_params* prm, int dt, uint64_t n, uintptr_t addr, 
   P->cap0 = P->n_ext_max + 16;
   P->cap_r = n / (P->lim.c_large + 1) + 16;     // jobs a refinement level can pass on
   P->capj = std::max(P->cap0, P->cap_r);        // jobs of one refinement level
-  P->cap_c = std::max((uint64_t)P->kf * P->cap0, n / (P->lim.l1_target >> 4) + P->capj) + 64;
+  P->cap_c = std::max((uint64_t)P->kf * P->cap0, n / 32 + n / (P->lim.l1_target / 3) + P->capj) + 64;
   P->cap1 = P->cap_c + P->cap0;
   const uint64_t M = (uint64_t)P->n_ext_max * G;
   P->l0_scan_tiles = (uint32_t)std::max<uint64_t>(1, (M + SC_TILE - 1) / SC_TILE);
@@ -212,7 +213,7 @@ struct Workspace {
   // offsets
   size_t o_scratch, o_smp_a, o_smp_b, o_rank, o_flags, o_cpos, o_cand, o_sel, o_nh, o_part, o_hi,
       o_tscan, o_rs_hist, o_rs_skip, o_rs_status, o_hdr, o_leaf64, o_thr, o_cell, o_cleaf, o_hkey, o_hval, o_heads, o_heavy,
-      o_lbeg, o_lend, o_hist, o_offs, o_l0scan, o_jobs_fill, o_jobs_s, o_jobs_l, o_jobs_m, o_jobs_fb2, o_jobs_r,
+      o_lbeg, o_lend, o_hist, o_offs, o_l0scan, o_jobs_fill, o_jobs_s, o_jobs_l, o_jobs_m, o_jobs_fb2, o_jobs_t, o_jobs_r,
       o_jobs_fb, o_jobs_r2, o_jobs_r3, o_pk, o_sid, o_ccount, o_counts, o_aux, o_tot, o_l1cnt, o_l1off, o_l1cur, o_jmin, o_jmax, o_l1scan,
       o_ubase, o_units;
   size_t tscan_bytes, rs_status_bytes, l0scan_bytes, l1scan_bytes;
@@ -263,6 +264,7 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->o_jobs_l = c.take<Job>(P.cap1);
   w->o_jobs_m = c.take<Job>(P.cap1);
   w->o_jobs_fb2 = c.take<Job>(P.cap1);
+  w->o_jobs_t = c.take<Job>(P.cap1);
   w->o_jobs_r = c.take<Job>(P.cap0);
   w->o_jobs_fb = c.take<Job>(P.cap1);
   w->o_pk = c.take<uint32_t>(with_scratch ? P.n + 16 : 0);
@@ -294,7 +296,7 @@ struct Bound {
   TrainWs T;
   Lists lists;
   Level1Ws l1;
-  unsigned long long* counts;  // [0..7], [12] list counts, [8..11] job counters
+  unsigned long long* counts;  // [0..7], [12], [13] list counts, [8..11], [14] job counters
 };
 
 static Bound bind(const Plan& P, const Workspace& w) {
@@ -345,6 +347,7 @@ static Bound bind(const Plan& P, const Workspace& w) {
   b.lists.sort_l = mk(w.o_jobs_l, b.counts + 2, P.cap1);
   b.lists.sort_m = mk(w.o_jobs_m, b.counts + 7, P.cap1);
   b.lists.fill_big = mk(w.o_jobs_fb2, b.counts + 12, P.cap1);
+  b.lists.sort_t = mk(w.o_jobs_t, b.counts + 13, P.cap1);
   b.lists.refine = mk(w.o_jobs_r, b.counts + 3, P.cap0);
   b.lists.fallback = mk(w.o_jobs_fb, b.counts + 4, P.cap1);
   b.lists.refine2 = mk(w.o_jobs_r2, b.counts + 5, P.cap_r);
@@ -482,7 +485,7 @@ static void fill_stats(const Plan& P, const Workspace& w, Events* ev, ls_stats* 
   stats->n_heavy = hdr.nheavy;
   stats->n_ext = hdr.n_ext;
   stats->n_level1 = counts[3];
-  stats->n_segments = counts[1] + counts[2] + counts[7];
+  stats->n_segments = counts[1] + counts[2] + counts[7] + counts[13];
   stats->n_fallback = counts[4];
   stats->n_range = counts[5] + counts[6];
   // largest slot and equality keys from the level-0 offsets
@@ -615,18 +618,19 @@ ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dty
   if (e) return to_status(e);
   if ((e = configure(d, dtype))) return to_status(e);
   SortLimits lim;
+  lim.c_tiny = 512;
   lim.c_small = 2048;
   lim.c_mid = 4096;
   lim.c_large = 8192;
   lim.l1_target = 3072;
   const uint64_t capj = count + N / (lim.c_large + 1) + 16;
-  const uint64_t cap_c = N / (lim.l1_target >> 4) + capj + 64;
+  const uint64_t cap_c = N / 32 + N / (lim.l1_target / 3) + capj + 64;
   const uint64_t cap1 = cap_c + count + 64;
   // workspace
   Carver c;
   const size_t o_scr = c.take<uint8_t>(N * W);
   size_t o_list[10];
-  const uint64_t caps[10] = {cap1, cap1, cap1, cap1, cap1, capj, capj, cap1, cap1, 1};
+  const uint64_t caps[10] = {cap1, cap1, cap1, cap1, cap1, capj, capj, cap1, capj, cap1};
   for (int i = 0; i < 10; ++i) o_list[i] = c.take<Job>(caps[i]);
   const size_t o_counts = c.take<unsigned long long>(16);
   const size_t o_aux = c.take<uint8_t>((capj + 1) * 32);
@@ -660,8 +664,9 @@ ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dty
   lists.refine3 = mk(6, 6);
   lists.fill_big = mk(7, 12);
   lists.refine = mk(8, 3);
+  lists.sort_t = mk(9, 13);
   // initial jobs, one per array
-  std::vector<Job> js, jm, jl, jr;
+  std::vector<Job> jt, js, jm, jl, jr;
   uint64_t off = 0;
   char* scr = at<char>(w, o_scr);
   for (size_t i = 0; i < count; ++i) {
@@ -675,18 +680,20 @@ ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dty
     j.kb = (uint64_t)(uintptr_t)keys[i];
     j.sb = (uint64_t)(uintptr_t)(scr + off * W);
     off += n[i];
-    if (n[i] <= lim.c_small) { j.kind = JOB_SORT_RANGE; js.push_back(j); }
+    if (n[i] <= lim.c_tiny) { j.kind = JOB_SORT_RANGE; jt.push_back(j); }
+    else if (n[i] <= lim.c_small) { j.kind = JOB_SORT_RANGE; js.push_back(j); }
     else if (n[i] <= lim.c_mid) { j.kind = JOB_SORT_RANGE; jm.push_back(j); }
     else if (n[i] <= lim.c_large) { j.kind = JOB_SORT_RANGE; jl.push_back(j); }
     else { j.kind = JOB_REFINE; jr.push_back(j); }
   }
   unsigned long long hc[16] = {0};
-  hc[1] = js.size(); hc[7] = jm.size(); hc[2] = jl.size(); hc[5] = jr.size();
+  hc[1] = js.size(); hc[7] = jm.size(); hc[2] = jl.size(); hc[5] = jr.size(); hc[13] = jt.size();
   auto put = [&](const std::vector<Job>& v, int i) {
     return v.empty() ? cudaSuccess
                      : cudaMemcpyAsync(at<void>(w, o_list[i]), v.data(), v.size() * sizeof(Job),
                                        cudaMemcpyHostToDevice, st);
   };
+  if (!e) e = put(jt, 9);
   if (!e) e = put(js, 1);
   if (!e) e = put(jm, 4);
   if (!e) e = put(jl, 2);
@@ -706,13 +713,18 @@ ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dty
     l.sid = nullptr;
     l.cap_c = cap_c;
     l.cap_jobs = capj;
-    LevelArgs lv[2];
-    lv[0].in = lists.refine2; lv[0].next = lists.refine3; lv[0].mode = 1;
-    lv[0].next_kind = JOB_REFINE; lv[0].kf = 0;
-    lv[1].in = lists.refine3; lv[1].next = lists.fallback; lv[1].mode = 1;
-    lv[1].next_kind = JOB_FALLBACK; lv[1].kf = 0;
+    // value range, value range again, total-order key range, then the fallback
+    LevelArgs lv[3];
+    lv[0].in = lists.refine2; lv[0].next = lists.refine3; lv[0].mode = 2;
+    lv[0].next_kind = JOB_REFINE; lv[0].kf = 0; lv[0].target = lim.l1_target;
+    lv[1].in = lists.refine3; lv[1].next = lists.refine; lv[1].mode = 2;
+    lv[1].next_kind = JOB_REFINE; lv[1].kf = 0; lv[1].target = lim.l1_target / 3;
+    lv[2].in = lists.refine; lv[2].next = lists.fallback; lv[2].mode = 1;
+    lv[2].next_kind = JOB_FALLBACK; lv[2].kf = 0; lv[2].target = 16;
+    lv[0].fmax = lv[1].fmax = MAX_F1;
+    lv[2].fmax = 256;
     ModelPtrs M{};
-    e = levels_enqueue(dtype, nullptr, nullptr, N, M, lists, lim, l, lv, 2, d->err, st, d->num_sms);
+    e = levels_enqueue(dtype, nullptr, nullptr, N, M, lists, lim, l, lv, 3, d->err, st, d->num_sms);
     if (!e) e = fill_enqueue(dtype, nullptr, lists, cap1, st, d->num_sms);
     if (!e) e = buckets_enqueue(dtype, nullptr, nullptr, N, M, lists, cap1, cap1, cap1, counts + 8,
                                 d->err, st, d->num_sms, nullptr, 0);

@@ -215,7 +215,7 @@ __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* 
 }
 
 template <int DT, int THREADS, int KPT>
-__global__ void __launch_bounds__(THREADS, THREADS == 512 ? 2 : (KPT == 16 ? 3 : 4))
+__global__ void __launch_bounds__(THREADS, THREADS == 512 ? 2 : (KPT == 16 ? 3 : (THREADS == 128 ? 8 : 4)))
 k_bucket_sort(typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, ModelPtrs M,
               JobList list, unsigned long long* ctr, uint32_t* err) {
   typedef typename KT<DT>::U U;
@@ -354,13 +354,18 @@ k_fallback(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, ModelPtrs M, J
 }
 
 // ---------------------------------------------------------------- host enqueue
+constexpr int BS_TINY_T = 128, BS_TINY_K = 4;      // CAP 512
 constexpr int BS_SMALL_T = 256, BS_SMALL_K = 8;    // CAP 2048
 constexpr int BS_MID_T = 256, BS_MID_K = 16;       // CAP 4096
 constexpr int BS_LARGE_T = 512, BS_LARGE_K = 16;   // CAP 8192
 
 template <int DT>
 static cudaError_t buckets_cfg_dt() {
-  cudaError_t e = cudaFuncSetAttribute(k_bucket_sort<DT, BS_SMALL_T, BS_SMALL_K>,
+  cudaError_t e = cudaFuncSetAttribute(k_bucket_sort<DT, BS_TINY_T, BS_TINY_K>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)BucketCfg<DT, BS_TINY_T, BS_TINY_K>::SMEM);
+  if (e) return e;
+  e = cudaFuncSetAttribute(k_bucket_sort<DT, BS_SMALL_T, BS_SMALL_K>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)BucketCfg<DT, BS_SMALL_T, BS_SMALL_K>::SMEM);
   if (e) return e;
@@ -395,6 +400,12 @@ static cudaError_t buckets_dt(void* keys, void* scratch, const ModelPtrs& M, con
   const unsigned gs = (unsigned)std::min<uint64_t>(std::max<uint64_t>(cap_s, 1), 8ull * num_sms);
   const unsigned gl = (unsigned)std::min<uint64_t>(std::max<uint64_t>(cap_l, 1), 2ull * num_sms);
   const unsigned gf = (unsigned)std::min<uint64_t>(std::max<uint64_t>(cap_fb, 1), 1ull * num_sms);
+  {
+    const unsigned gt = (unsigned)std::min<uint64_t>(std::max<uint64_t>(cap_s, 1), 16ull * num_sms);
+    k_bucket_sort<DT, BS_TINY_T, BS_TINY_K>
+        <<<gt, BS_TINY_T, BucketCfg<DT, BS_TINY_T, BS_TINY_K>::SMEM, st>>>(
+            (U*)keys, (const U*)scratch, M, lists.sort_t, ctrs + 6, err);
+  }
   k_bucket_sort<DT, BS_SMALL_T, BS_SMALL_K>
       <<<gs, BS_SMALL_T, BucketCfg<DT, BS_SMALL_T, BS_SMALL_K>::SMEM, st>>>(
           (U*)keys, (const U*)scratch, M, lists.sort_s, ctrs + 0, err);
@@ -412,7 +423,7 @@ static cudaError_t buckets_dt(void* keys, void* scratch, const ModelPtrs& M, con
   k_fallback<DT><<<gf, 512, BucketCfg<DT, 512, 16>::SMEM_FB, st>>>((U*)keys, (U*)scratch, M,
                                                                   lists.fallback, ctrs + 2, err);
   mark(mk, mb + 2, st);
-  add_launches(4);
+  add_launches(5);
   return cudaGetLastError();
 }
 

@@ -518,7 +518,8 @@ __global__ void k_classify0(Level0Args a, Lists lists, SortLimits lim) {
     job.Flo = (j == 0) ? (double)b / (double)a.f0 : (double)heavy[hoff + j - 1].F;
     job.Fhi = (j == nh) ? (double)(b + 1) / (double)a.f0 : (double)heavy[hoff + j].F;
     job.la = job.lb = 0;
-    if (size <= lim.c_small) { job.kind = JOB_SORT; push_job(lists.sort_s, job, a.err); }
+    if (size <= lim.c_tiny) { job.kind = JOB_SORT; push_job(lists.sort_t, job, a.err); }
+    else if (size <= lim.c_small) { job.kind = JOB_SORT; push_job(lists.sort_s, job, a.err); }
     else if (size <= lim.c_mid) { job.kind = JOB_SORT; push_job(lists.sort_m, job, a.err); }
     else if (size <= lim.c_large) { job.kind = JOB_SORT; push_job(lists.sort_l, job, a.err); }
     else { job.kind = JOB_REFINE; push_job(lists.refine, job, a.err); }
@@ -578,16 +579,22 @@ struct L1Aux {
 };
 
 // Split of one refine job: by the model's F (the level-1 Partition of Alg. 2)
-// or, for segments the model could not split, linearly over the segment's
-// total-order key range [jmin, jmax] (an integer map, exact at any width).
+// or, for segments the model could not split, linearly over the segment's key
+// range: on the FP32 image of the key for floating-point keys (value space,
+// where a float range is close to linear in density), else, or when the image
+// cannot resolve the range, on the total-order key (an integer map, exact at
+// any width).  Both maps are non-decreasing in the key.
 struct RangeSplit {
   unsigned long long tmin;
   unsigned long long mul;
   uint32_t sh;
+  uint32_t fe;
+  float xmin, xscale;    // value-space map when xscale > 0
 };
 
+template <int DT>
 __device__ __forceinline__ RangeSplit range_split(unsigned long long tmin, unsigned long long tmax,
-                                                  uint32_t f1) {
+                                                  uint32_t f1, bool value_space) {
   RangeSplit s;
   const unsigned long long R = tmax - tmin;
   const int bl = R ? 64 - __clzll((long long)R) : 0;
@@ -596,10 +603,28 @@ __device__ __forceinline__ RangeSplit range_split(unsigned long long tmin, unsig
   const unsigned long long fe = min((unsigned long long)f1, Q + 1);
   s.mul = (fe << 32) / (Q + 1);                                // <= 2^32
   s.tmin = tmin;
+  s.fe = (uint32_t)fe;
+  s.xmin = 0.0f;
+  s.xscale = 0.0f;
+  if (value_space && (DT == LS_F64 || DT == LS_F32)) {
+    const float x0 = key_f32<DT>(KT<DT>::from_tk(tmin));
+    const float x1 = key_f32<DT>(KT<DT>::from_tk(tmax));
+    const float sc = (float)f1 / (x1 - x0);
+    if (x1 > x0 && isfinite(x0) && isfinite(x1) && isfinite(sc) && sc > 0.0f) {
+      s.xmin = x0;
+      s.xscale = sc;
+      s.fe = f1;
+    }
+  }
   return s;
 }
-__device__ __forceinline__ uint32_t range_sub(uint64_t tk, const RangeSplit& s) {
-  const unsigned long long d = (tk - s.tmin) >> s.sh;
+template <int DT>
+__device__ __forceinline__ uint32_t range_sub(typename KT<DT>::U u, const RangeSplit& s) {
+  if (s.xscale > 0.0f) {
+    const float v = (key_f32<DT>(u) - s.xmin) * s.xscale;
+    return v > 0.0f ? min((uint32_t)v, s.fe - 1) : 0u;         // NaN keys cannot occur here
+  }
+  const unsigned long long d = (KT<DT>::tk(u) - s.tmin) >> s.sh;
   return (uint32_t)((d * s.mul) >> 32);                        // < min(f1, Q + 1)
 }
 
@@ -620,9 +645,11 @@ k_l1_plan(LevelArgs la, SortLimits lim, Level1Ws w, uint32_t* err) {
       // the model's split aims at l1_target keys per sub-bucket; a key-range
       // split (its input is skewed or clustered) uses 16x finer sub-buckets
       // the model's split has the call's Kf sub-buckets per bucket (ids from
-      // K2); a key-range split aims at l1_target / 16 keys per sub-bucket
-      uint64_t f = (job.m + (lim.l1_target >> 4) - 1) / (lim.l1_target >> 4);
-      f = f < 2 ? 2 : (f > MAX_F1 ? MAX_F1 : f);
+      // K2); a key-range split aims at la.target keys per sub-bucket
+      const uint64_t tg = la.target ? la.target : 1;
+      const uint64_t fmx = la.fmax ? min((uint64_t)la.fmax, (uint64_t)MAX_F1) : (uint64_t)MAX_F1;
+      uint64_t f = (job.m + tg - 1) / tg;
+      f = f < 2 ? 2 : (f > fmx ? fmx : f);
       if (la.mode == 0) f = la.kf;
       f1 = f;
       tiles = (job.m + L1_TILE - 1) / L1_TILE;
@@ -727,7 +754,7 @@ k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Mod
     const U* src = (job.src ? job_scratch(job, scratch) : job_keys(job, keys)) + job.start + off;
     const uint16_t* ids = w.sid + job.start + off;
     RangeSplit rs{};
-    if (la.mode) rs = range_split(w.jmin[j], w.jmax[j], x.f1);
+    if (la.mode) rs = range_split<DT>(w.jmin[j], w.jmax[j], x.f1, la.mode == 2);
     for (uint32_t s = threadIdx.x; s < x.f1; s += blockDim.x) hc[s] = 0;
     __syncthreads();
     constexpr int U8 = 8;  // independent loads in flight per thread
@@ -737,7 +764,7 @@ k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Mod
 #pragma unroll
         for (int k = 0; k < U8; ++k) {
           const uint32_t i = base + k * blockDim.x + threadIdx.x;
-          sub[k] = i < c ? range_sub(KT<DT>::tk(src[i]), rs) : 0xFFFFFFFFu;
+          sub[k] = i < c ? range_sub<DT>(src[i], rs) : 0xFFFFFFFFu;
         }
       } else {
 #pragma unroll
@@ -794,7 +821,7 @@ k_l1_scatter(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, uint64_t n, 
     const uint16_t* idsrc = w.sid + job.start + off;
     U* dstb = job.src ? job_keys(job, keys) : job_scratch(job, scratch);
     RangeSplit rs{};
-    if (la.mode) rs = range_split(w.jmin[j], w.jmax[j], x.f1);
+    if (la.mode) rs = range_split<DT>(w.jmin[j], w.jmax[j], x.f1, la.mode == 2);
     for (uint32_t s = threadIdx.x; s <= x.f1; s += blockDim.x) lc[s] = 0;
     __syncthreads();
     U u[KPT];
@@ -808,7 +835,7 @@ k_l1_scatter(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, uint64_t n, 
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
       uint32_t sub = sb[k];
-      if (sub != 0xFFFFFFFFu) sub = la.mode ? range_sub(KT<DT>::tk(u[k]), rs) : min(sub, x.f1 - 1);
+      if (sub != 0xFFFFFFFFu) sub = la.mode ? range_sub<DT>(u[k], rs) : min(sub, x.f1 - 1);
       sb[k] = sub;
       rk[k] = sub != 0xFFFFFFFFu ? atomicAdd(&lc[sub], 1u) : 0u;
     }
@@ -869,7 +896,8 @@ __global__ void k_l1_classify(Lists lists, LevelArgs la, SortLimits lim, Level1W
     job.kb = pj.kb;
     job.sb = pj.sb;
     const uint32_t sk = la.mode ? JOB_SORT_RANGE : JOB_SORT;
-    if (cntc <= lim.c_small) { job.kind = sk; push_job(lists.sort_s, job, err); }
+    if (cntc <= lim.c_tiny) { job.kind = sk; push_job(lists.sort_t, job, err); }
+    else if (cntc <= lim.c_small) { job.kind = sk; push_job(lists.sort_s, job, err); }
     else if (cntc <= lim.c_mid) { job.kind = sk; push_job(lists.sort_m, job, err); }
     else if (cntc <= lim.c_large) { job.kind = sk; push_job(lists.sort_l, job, err); }
     else { job.kind = la.next_kind; push_job(la.next, job, err); }
@@ -983,13 +1011,17 @@ cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const 
   // level 1 splits by the model; levels 2 and 3 split what it could not by key range
   const JobList ins[3] = {lists.refine, lists.refine2, lists.refine3};
   const JobList outs[3] = {lists.refine2, lists.refine3, lists.fallback};
+  // re-splits of what the model left large: the value range first, then the
+  // total-order key range (which separates clustered distinct values)
   LevelArgs lvs[3];
   for (int lv = 0; lv < 3; ++lv) {
     lvs[lv].in = ins[lv];
     lvs[lv].next = outs[lv];
-    lvs[lv].mode = lv == 0 ? 0 : 1;
+    lvs[lv].mode = lv == 0 ? 0 : (lv == 1 ? 2 : 1);
     lvs[lv].next_kind = lv == 2 ? JOB_FALLBACK : JOB_REFINE;
     lvs[lv].kf = kf;
+    lvs[lv].target = lv == 2 ? 16 : lim.l1_target / 3;
+    lvs[lv].fmax = lv == 2 ? 256 : MAX_F1;
   }
   return levels_enqueue(dt, keys, scratch, n, M, lists, lim, w, lvs, 3, err, st, num_sms);
 }

@@ -46,20 +46,24 @@ struct Lists {
   JobList refine2, refine3;  // segments the previous level left above c_large
   JobList sort_m;            // segments in (c_small, c_mid]
   JobList fill_big;          // fills of at least FILL_BIG keys (written by the whole grid)
+  JobList sort_t;            // segments of at most c_tiny keys
 };
 
 // One refinement level: split the jobs of `in` into sub-buckets, by the model
-// (mode 0) or by the total-order key range (mode 1); sub-buckets still above
+// (mode 0) or by the job's key range (modes 1 and 2); sub-buckets still above
 // c_large go to `next` with kind next_kind.
 struct LevelArgs {
   JobList in, next;
-  int mode;
+  int mode;              // 0: model ids; 1: total-order key range; 2: value range (floats)
   uint32_t next_kind;
   uint32_t kf;           // mode 0: sub-buckets per job (ids from the level-0 pass)
+  uint32_t target;       // modes 1-2: keys per sub-bucket aimed at
+  uint32_t fmax;         // modes 1-2: most sub-buckets per job (<= MAX_F1)
 };
 
 struct SortLimits {
-  uint64_t c_small;      // segments up to this go to the small in-bucket kernel
+  uint64_t c_tiny;       // segments up to this go to the tiny in-bucket kernel
+  uint64_t c_small;      // ... up to this to the small one
   uint64_t c_mid;        // ... up to this to the middle one
   uint64_t c_large;      // ... up to this to the large kernel, above: refine/fallback
   uint64_t l1_target;    // target sub-bucket size of the level-1 split
