@@ -201,6 +201,13 @@ ls_status ls_server_create(const ls_server_config* cfg, ls_server** out);
  * request exceeds the budget or the queue is full; *ticket identifies it. */
 ls_status ls_server_submit(ls_server* s, void* keys, size_t n, ls_dtype dtype,
                            uint64_t* ticket);
+/* As ls_server_submit, with the keys first copied from the device array `src`
+ * (n keys, not overlapping `keys`) into `keys` on the server's stream; the
+ * copy counts in queue and total latency but not in device_ms.  Requests of
+ * at most 2^22 keys that are admitted together are sorted by one batched
+ * launch sequence per key type; larger ones by the full learned sort. */
+ls_status ls_server_submit_from(ls_server* s, const void* src, void* keys, size_t n,
+                                ls_dtype dtype, uint64_t* ticket);
 /* Wait up to timeout_ms for a ticket (UINT32_MAX: forever). */
 ls_status ls_server_wait(ls_server* s, uint64_t ticket, uint32_t timeout_ms,
                          ls_request_stats* st);

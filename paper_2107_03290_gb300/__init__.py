@@ -129,7 +129,7 @@ class RequestStats(ctypes.Structure):
 EXPORTED = ["ls_default_params", "ls_status_string", "ls_sort", "ls_sort_ex", "ls_sort_host",
             "ls_sort_batch", "ls_stream_status", "ls_train", "ls_level0_histogram",
             "ls_radix_sort_u64", "ls_radix_sort_u64_noalloc", "ls_kernel_launches",
-            "ls_server_create", "ls_server_submit", "ls_server_wait",
+            "ls_server_create", "ls_server_submit", "ls_server_submit_from", "ls_server_wait",
             "ls_server_destroy"]
 
 _lib = None
@@ -170,6 +170,7 @@ def load(path: str | None = None):
             "ls_radix_sort_u64_noalloc": [vp, sz, vp],
             "ls_server_create": [P(ServerConfig), P(vp)],
             "ls_server_submit": [vp, vp, sz, i32, P(u64)],
+            "ls_server_submit_from": [vp, vp, vp, sz, i32, P(u64)],
             "ls_server_wait": [vp, u64, u32, P(RequestStats)],
             "ls_server_destroy": [vp],
         }.items():
@@ -351,11 +352,21 @@ class Server:
         _check(load().ls_server_create(ctypes.byref(cfg), ctypes.byref(self._h)),
                "ls_server_create")
 
-    def submit(self, t) -> int:
+    def submit(self, t, src=None) -> int:
+        """Queue an in-place sort of CUDA tensor `t`; with `src` (a CUDA tensor of
+        the same dtype and size) the server first copies `src` into `t`."""
         t = _device_tensor(t)
         tk = ctypes.c_uint64(0)
-        _check(load().ls_server_submit(self._h, t.data_ptr(), t.numel(), dtype_code(t),
-                                       ctypes.byref(tk)), "ls_server_submit")
+        if src is None:
+            _check(load().ls_server_submit(self._h, t.data_ptr(), t.numel(), dtype_code(t),
+                                           ctypes.byref(tk)), "ls_server_submit")
+        else:
+            src = _device_tensor(src)
+            if src.numel() != t.numel() or src.dtype != t.dtype:
+                raise ValueError("src must match t in dtype and size")
+            _check(load().ls_server_submit_from(self._h, src.data_ptr(), t.data_ptr(), t.numel(),
+                                                dtype_code(t), ctypes.byref(tk)),
+                   "ls_server_submit_from")
         return tk.value
 
     def wait(self, ticket: int, timeout_ms: int = 0xFFFFFFFF) -> dict:

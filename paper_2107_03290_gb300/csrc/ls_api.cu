@@ -43,16 +43,56 @@ cudaError_t status_word_ptr(uint32_t** out) {
   return e;
 }
 
+// Pinned host staging for small uploads (the batched entry's job lists): a
+// chunk is reused once the event recorded after its copy has completed, so
+// uploads never go through pageable memory (which would wait for the stream).
+struct Staging {
+  void* host = nullptr;
+  size_t bytes = 0;
+  cudaEvent_t done = nullptr;
+  bool busy = false;     // handed out, event not yet recorded
+};
+
 struct Device {
   int id = -1;
   int num_sms = 0;
   cudaMemPool_t pool = nullptr;
   uint32_t* err = nullptr;
   bool configured[4] = {false, false, false, false};
+  std::vector<Staging> staging;
 };
 
 static std::mutex g_mu;
 static std::map<int, Device> g_dev;
+
+// A pinned chunk of at least `bytes` whose previous copy has completed.
+static cudaError_t staging_acquire(Device* d, size_t bytes, Staging** out) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (Staging& s : d->staging) {
+    if (!s.busy && s.bytes >= bytes && cudaEventQuery(s.done) == cudaSuccess) {
+      s.busy = true;
+      *out = &s;
+      return cudaSuccess;
+    }
+  }
+  Staging s;
+  s.bytes = std::max<size_t>(bytes, 1 << 20);
+  cudaError_t e = cudaHostAlloc(&s.host, s.bytes, cudaHostAllocDefault);
+  if (e) return e;
+  e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+  if (e) { cudaFreeHost(s.host); return e; }
+  d->staging.reserve(64);
+  if (d->staging.size() >= 64) { cudaFreeHost(s.host); cudaEventDestroy(s.done); return cudaErrorMemoryAllocation; }
+  s.busy = true;
+  d->staging.push_back(s);
+  *out = &d->staging.back();
+  return cudaSuccess;
+}
+
+static void staging_release(Staging* s) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  s->busy = false;
+}
 
 static ls_status to_status(cudaError_t e) {
   if (e == cudaSuccess) return LS_OK;
@@ -688,17 +728,31 @@ ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dty
   }
   unsigned long long hc[16] = {0};
   hc[1] = js.size(); hc[7] = jm.size(); hc[2] = jl.size(); hc[5] = jr.size(); hc[13] = jt.size();
-  auto put = [&](const std::vector<Job>& v, int i) {
-    return v.empty() ? cudaSuccess
-                     : cudaMemcpyAsync(at<void>(w, o_list[i]), v.data(), v.size() * sizeof(Job),
-                                       cudaMemcpyHostToDevice, st);
-  };
-  if (!e) e = put(jt, 9);
-  if (!e) e = put(js, 1);
-  if (!e) e = put(jm, 4);
-  if (!e) e = put(jl, 2);
-  if (!e) e = put(jr, 5);
-  if (!e) e = cudaMemcpyAsync(counts, hc, sizeof(hc), cudaMemcpyHostToDevice, st);
+  // one pinned upload: the counters, then the five initial lists
+  const size_t up_bytes = sizeof(hc) + (jt.size() + js.size() + jm.size() + jl.size() + jr.size()) * sizeof(Job);
+  Staging* sg = nullptr;
+  if (!e) e = staging_acquire(d, up_bytes, &sg);
+  if (!e) {
+    char* hp = (char*)sg->host;
+    std::memcpy(hp, hc, sizeof(hc));
+    size_t o = sizeof(hc);
+    auto put = [&](const std::vector<Job>& v, int i) {
+      if (v.empty()) return cudaSuccess;
+      std::memcpy(hp + o, v.data(), v.size() * sizeof(Job));
+      cudaError_t r = cudaMemcpyAsync(at<void>(w, o_list[i]), hp + o, v.size() * sizeof(Job),
+                                      cudaMemcpyHostToDevice, st);
+      o += v.size() * sizeof(Job);
+      return r;
+    };
+    e = cudaMemcpyAsync(counts, hp, sizeof(hc), cudaMemcpyHostToDevice, st);
+    if (!e) e = put(jt, 9);
+    if (!e) e = put(js, 1);
+    if (!e) e = put(jm, 4);
+    if (!e) e = put(jl, 2);
+    if (!e) e = put(jr, 5);
+    if (!e) e = cudaEventRecord(sg->done, st);
+  }
+  if (sg) staging_release(sg);
   if (!e) {
     Level1Ws l{};
     l.aux = at<void>(w, o_aux);

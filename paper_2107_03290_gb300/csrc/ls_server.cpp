@@ -1,10 +1,13 @@
 // Serving loop of the learned sort: continuous batching of sort requests.
 //
-// A dispatcher thread admits queued requests while the bytes of the admitted
-// requests (keys + scratch) stay within the HBM budget and the number on the
-// GPU stays below max_inflight; each admitted request is enqueued on one of
-// the server's streams, so requests overlap on the device.  Completion is
-// detected with CUDA events; waiters get queue / device / total latency.
+// A dispatcher thread admits queued requests, in arrival order, while the
+// bytes of the admitted requests (keys + scratch) stay within the HBM budget
+// and the number on the GPU stays below max_inflight.  Whatever has arrived is
+// launched together: the small requests of one key type go through one
+// batched launch sequence (ls_sort_batch), larger ones through the full
+// learned sort, on the server's streams in turn, so requests overlap on the
+// device.  Completion is detected with CUDA events; waiters get queue /
+// device / total latency.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -23,9 +26,12 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+constexpr size_t SERVER_BATCH_MAX = size_t(1) << 22;  // requests this small are batched
+
 struct Request {
   uint64_t ticket;
   void* keys;
+  const void* src;       // optional device source copied into keys first
   size_t n;
   ls_dtype dt;
   uint64_t bytes;
@@ -84,19 +90,50 @@ static void dispatcher(ls_server* s) {
       }
     }
     // admit while budget and slots allow (arrival order)
-    while (!s->queue.empty() && s->inflight.size() < s->cfg.max_inflight &&
+    std::vector<Request*> adm;
+    while (!s->queue.empty() && s->inflight.size() + adm.size() < s->cfg.max_inflight &&
            s->inflight_bytes + s->queue.front()->bytes <= s->cfg.hbm_budget_bytes) {
       Request* r = s->queue.front();
       s->queue.pop_front();
-      r->stream = (int)(s->rr++ % s->streams.size());
-      cudaStream_t st = s->streams[r->stream];
-      r->t_launch = Clock::now();
-      cudaEventRecord(r->ev_start, st);
-      const ls_status rc = ls_sort(r->keys, r->n, r->dt, st);
-      cudaEventRecord(r->ev_end, st);
-      if (rc != LS_OK) r->st.status = rc;
       s->inflight_bytes += r->bytes;
-      s->inflight.push_back(r);
+      adm.push_back(r);
+    }
+    if (!adm.empty()) {
+      const auto now = Clock::now();
+      auto prologue = [&](Request* r, cudaStream_t st, int si) {
+        r->stream = si;
+        r->t_launch = now;
+        if (r->src && r->n)
+          cudaMemcpyAsync(r->keys, r->src, r->n * ((r->dt == LS_F64 || r->dt == LS_U64) ? 8 : 4),
+                          cudaMemcpyDeviceToDevice, st);
+        cudaEventRecord(r->ev_start, st);
+      };
+      for (int dt = LS_F64; dt <= LS_U32; ++dt) {  // one batched launch per key type
+        std::vector<Request*> grp;
+        for (Request* r : adm)
+          if (r->dt == dt && r->n <= SERVER_BATCH_MAX) grp.push_back(r);
+        if (grp.empty()) continue;
+        const int si = (int)(s->rr++ % s->streams.size());
+        cudaStream_t st = s->streams[si];
+        std::vector<void*> ptrs;
+        std::vector<size_t> ns;
+        for (Request* r : grp) { prologue(r, st, si); ptrs.push_back(r->keys); ns.push_back(r->n); }
+        const ls_status rc = ls_sort_batch(ptrs.data(), ns.data(), grp.size(), (ls_dtype)dt, st);
+        for (Request* r : grp) {
+          cudaEventRecord(r->ev_end, st);
+          if (rc != LS_OK) r->st.status = rc;
+        }
+      }
+      for (Request* r : adm) {  // larger requests: the full learned sort each
+        if (r->n <= SERVER_BATCH_MAX) continue;
+        const int si = (int)(s->rr++ % s->streams.size());
+        cudaStream_t st = s->streams[si];
+        prologue(r, st, si);
+        const ls_status rc = ls_sort(r->keys, r->n, r->dt, st);
+        cudaEventRecord(r->ev_end, st);
+        if (rc != LS_OK) r->st.status = rc;
+      }
+      for (Request* r : adm) s->inflight.push_back(r);
     }
     if (s->stop && s->queue.empty() && s->inflight.empty()) break;
     if (s->inflight.empty() && s->queue.empty()) {
@@ -135,6 +172,11 @@ ls_status ls_server_create(const ls_server_config* cfg, ls_server** out) {
 }
 
 ls_status ls_server_submit(ls_server* s, void* keys, size_t n, ls_dtype dtype, uint64_t* ticket) {
+  return ls_server_submit_from(s, nullptr, keys, n, dtype, ticket);
+}
+
+ls_status ls_server_submit_from(ls_server* s, const void* src, void* keys, size_t n,
+                                ls_dtype dtype, uint64_t* ticket) {
   if (!s || !ticket || dtype < LS_F64 || dtype > LS_U32 || (n > 0 && !keys)) return LS_ERR_INVALID;
   const uint64_t bytes = request_bytes(n, dtype);
   std::lock_guard<std::mutex> lk(s->mu);
@@ -143,6 +185,7 @@ ls_status ls_server_submit(ls_server* s, void* keys, size_t n, ls_dtype dtype, u
   Request* r = new Request();
   r->ticket = s->next_ticket++;
   r->keys = keys;
+  r->src = src;
   r->n = n;
   r->dt = dtype;
   r->bytes = bytes;
