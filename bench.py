@@ -201,6 +201,100 @@ def run_batched(ls, torch, count: int, steps: int, warmup: int, with_loop: bool 
     return out
 
 
+def run_serving(ls, torch, rates, seconds: float, pool_size: int = 64,
+                budget_bytes: int = 120 << 30, client_bytes: int = 48 << 30):
+    """Serving workload: Poisson arrivals of sort requests (each copies one
+    device-resident pool array into its own buffer on the server's stream,
+    outside the device time), admission by an HBM budget; reports p50/p99 of
+    arrival -> completion and keys/s against sorting the same requests one at
+    a time with the plain entry point in arrival order."""
+    import threading
+    pool = lsgen.serving_pool(pool_size)
+    dev = [torch.from_numpy(a).cuda() for a in pool]
+    rng = np.random.default_rng(11)
+    out = []
+    for rate in rates:
+        n_req = max(1, int(rate * seconds))
+        gaps = rng.exponential(1.0 / rate, n_req)
+        picks = rng.integers(0, pool_size, n_req)
+        srv = ls.Server(hbm_budget_bytes=budget_bytes, max_inflight=64, streams=4)
+        lat, done_t = [], []
+        outstanding = []
+        cv = threading.Condition()
+        in_bytes = [0]
+
+        def waiter():
+            while True:
+                with cv:
+                    while not outstanding:
+                        cv.wait()
+                    item = outstanding.pop(0)
+                if item is None:
+                    return
+                tk, buf, nb = item
+                st = srv.wait(tk)
+                lat.append(st["total_ms"])
+                done_t.append(time.perf_counter())
+                with cv:
+                    in_bytes[0] -= nb
+                    cv.notify_all()
+                del buf
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nxt = t0
+        keys = 0
+        for i in range(n_req):
+            nxt += gaps[i]
+            d = time.perf_counter() - nxt
+            if d < 0:
+                time.sleep(-d)
+            src = dev[picks[i]]
+            nb = src.numel() * src.element_size()
+            with cv:  # the client keeps at most client_bytes of request buffers
+                while in_bytes[0] + nb > client_bytes:
+                    cv.wait()
+                in_bytes[0] += nb
+            buf = torch.empty_like(src)
+            tk = srv.submit(buf, src=src)
+            keys += src.numel()
+            with cv:
+                outstanding.append((tk, buf, nb))
+                cv.notify_all()
+        with cv:
+            outstanding.append(None)
+            cv.notify_all()
+        th.join()
+        wall = max(done_t) - t0
+        srv.close()
+        # one at a time, plain entry point, same requests in arrival order
+        st = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        tot_ms = 0.0
+        for i in range(n_req):
+            src = dev[picks[i]]
+            buf = src.clone()
+            e0.record(st)
+            ls.sort_(buf)
+            e1.record(st)
+            e1.synchronize()
+            tot_ms += e0.elapsed_time(e1)
+            del buf
+        out.append({"rate_req_s": rate, "requests": n_req, "seconds": seconds, "keys": int(keys),
+                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                    "served_keys_per_s": keys / wall,
+                    "one_at_a_time_keys_per_s": keys / (tot_ms / 1e3),
+                    "served_vs_one_at_a_time": (keys / wall) / (keys / (tot_ms / 1e3))})
+        torch.cuda.empty_cache()
+    del dev
+    torch.cuda.empty_cache()
+    return {"workload": "serving_poisson", "pool": pool_size, "hbm_budget_gb": budget_bytes >> 30,
+            "note": f"{seconds} s per rate (60 s in the full recipe)", "rates": out}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -214,6 +308,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=2_000_000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=4096, help="arrays of the batched line (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="seconds per arrival rate of the serving line (0: skip)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
@@ -336,6 +432,9 @@ def main():
     batched = None
     if args.batch > 0 and rank == 0:
         batched = run_batched(ls, torch, args.batch, steps=5, warmup=2)
+    serving = None
+    if args.serve_seconds > 0 and rank == 0:
+        serving = run_serving(ls, torch, [200, 1000, 5000], args.serve_seconds)
 
     if rank == 0:
         last = per[-1]
@@ -349,7 +448,7 @@ def main():
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": int(launches), "clocks": clk.summary(),
                "wall_ms_per_step": 1000 * wall / args.steps, "correct": ok,
-               "kernels_ms": kms, "batched": batched,
+               "kernels_ms": kms, "batched": batched, "serving": serving,
                "path": {k: last[k] for k in ("n_heavy", "n_ext", "max_bucket", "n_eq_keys",
                                              "n_level1", "n_segments", "n_fallback", "n_fill",
                                              "n_launches", "sample_size")}}

@@ -183,6 +183,34 @@ WORKLOADS = {
 }
 
 
+def serving_pool(count: int = 64, seed: int = 7, lo: float = 1e4, hi: float = 6.4e7,
+                 heavy_share: float = 0.3):
+    """Request inputs of the serving workload: sizes log-uniform on [lo, hi],
+    key type uniform over {float64, uint64, float32}; a `heavy_share` of them
+    Zipf(1.3) over 1,000 lognormal values, the others drawn like the
+    200M-key sweep (uniform / Gaussian mixture / exponential).  Returns a list
+    of arrays."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+        kind = int(rng.integers(0, 3))
+        s = seed * 1_000_003 + i + 1
+        if rng.uniform() < heavy_share:
+            a = zipf_lognormal_f64(n, s, k=1000, s=1.3)
+            a = a.astype(np.float32) if kind == 2 else a
+            if kind == 1:
+                a = (a * 1e6).astype(np.uint64)
+        elif kind == 0:
+            a = gauss_mix_f64(n, s)
+        elif kind == 1:
+            a = uniform_u64(n, s)
+        else:
+            a = exponential_f32(n, s)
+        out.append(a)
+    return out
+
+
 def workload(name: str, n: int | None = None) -> np.ndarray:
     dt, n0, fn = WORKLOADS[name]
     return fn(n0 if n is None else n)
