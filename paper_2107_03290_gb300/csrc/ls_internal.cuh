@@ -93,13 +93,17 @@ struct HeavyEntry {    // a heavy value of one level-0 bucket
   uint32_t ext;        // its equality slot
 };
 
-// Open-addressing table of the heavy values (total-order key -> equality
-// slot), linear probing; empty entries hold HASH_EMPTY (never a finite key).
-constexpr uint32_t HASH_BITS = 13;
-constexpr uint32_t HASH_SIZE = 1u << HASH_BITS;
+// Two-way set-associative table of the heavy values (total-order key ->
+// equality slot): a key's two candidate entries are one 16-byte set; empty
+// entries hold HASH_EMPTY.  A value whose set is full, and the value
+// HASH_EMPTY itself (a valid uint64 key), are not in the table: their keys
+// take the full lookup.
+constexpr uint32_t HASH_SET_BITS = 12;
+constexpr uint32_t HASH_SETS = 1u << HASH_SET_BITS;
+constexpr uint32_t HASH_SIZE = 2 * HASH_SETS;      // entries
 constexpr uint64_t HASH_EMPTY = ~0ull;
-__device__ __forceinline__ uint32_t heavy_hash(uint64_t t) {
-  return (uint32_t)((t * 0x9E3779B97F4A7C15ull) >> (64 - HASH_BITS));
+__device__ __forceinline__ uint32_t heavy_hash(uint64_t t) {  // set index
+  return (uint32_t)((t * 0x9E3779B97F4A7C15ull) >> (64 - HASH_SET_BITS));
 }
 
 // Level-0 bucket head: first extended slot and heavy list [hoff, hoff+nh).

@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
   // step's barrier and writes after it, and a step's writes stay below the
   // step's end, so no key is overwritten before it is read.
   const bool compact = a.may_compact && a.M.hdr->compact != 0;
-  unsigned long long* s_cpos = (unsigned long long*)(sm + lay.ws);
+  uint32_t* s_cpos = (uint32_t*)(sm + lay.ws);  // chunk lengths < 2^32
   if (threadIdx.x == 0) *s_cpos = 0;
   const int lane = threadIdx.x & 31;
   // Heavy table path: a key equal to a heavy value is counted from one table
@@ -250,8 +250,8 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
     if (compact) {
       const bool keep = valid && (pv & 0xFFFFu) != 0xFFFFu;
       const unsigned m = __ballot_sync(0xffffffffu, keep);
-      unsigned long long wb = 0;
-      if (lane == 0 && m) wb = atomicAdd(s_cpos, (unsigned long long)__popc(m));
+      uint32_t wb = 0;
+      if (lane == 0 && m) wb = atomicAdd(s_cpos, (uint32_t)__popc(m));
       wb = __shfl_sync(0xffffffffu, wb, 0);
       if (keep) {
         const uint64_t r = wb + __popc(m & lt);
@@ -285,8 +285,8 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
         for (int k = 0; k < H_KPT; ++k) {
           const bool keep = (pp[k] & 0xFFFFu) != 0xFFFFu;
           const unsigned m = __ballot_sync(0xffffffffu, keep);
-          unsigned long long wb = 0;
-          if (lane == 0 && m) wb = atomicAdd(s_cpos, (unsigned long long)__popc(m));
+          uint32_t wb = 0;
+          if (lane == 0 && m) wb = atomicAdd(s_cpos, (uint32_t)__popc(m));
           wb = __shfl_sync(0xffffffffu, wb, 0);
           if (keep) {
             const uint64_t r = wb + __popc(m & lt);
@@ -306,8 +306,11 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
         // one probe: a hit is a heavy value; anything else (including a heavy
         // value displaced by a collision) takes the full lookup
         const uint64_t t = KT<DT>::tk(u[k]);
-        const uint32_t p = heavy_hash(t);
-        const uint32_t e = hk[p] == t ? (uint32_t)hv[p] : 0xFFFFFFFFu;
+        const uint32_t set = heavy_hash(t);
+        const ulonglong2 kk = ((const ulonglong2*)hk)[set];
+        const uint32_t vv = ((const uint32_t*)hv)[set];
+        uint32_t e = kk.x == t ? (vv & 0xFFFFu) : (kk.y == t ? (vv >> 16) : 0xFFFFFFFFu);
+        if (t == HASH_EMPTY) e = 0xFFFFFFFFu;  // the empty mark is never a table key
         if (e != 0xFFFFFFFFu) {  // equality key: counted, never moved
           if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
           if (!compact) pk[i - a0] = 0xFFFFu;
@@ -345,7 +348,7 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
   }
   __syncthreads();
   if (compact) {  // pad to a multiple of 4 entries (equality marks)
-    const uint64_t cpos = *s_cpos;
+    const uint64_t cpos = *s_cpos;  // (read after the loop's last barrier)
     const uint64_t r4 = (cpos + 3) & ~3ull;
     if (threadIdx.x < r4 - cpos) pk[cb - a0 + cpos + threadIdx.x] = 0xFFFFu;
     if (threadIdx.x == 0) a.ccount[g] = r4;

@@ -570,26 +570,25 @@ k_heavy_heads(const uint64_t* __restrict__ sel, const uint32_t* __restrict__ nh,
   }
 }
 
-// Heavy table: one thread per heavy value; the slot of a key is claimed with a
-// compare-and-swap.  Records the longest probe sequence (0 when the table
-// would be too full to help, so the histogram skips it).
+// Heavy table: one thread per heavy value claims one of the two entries of its
+// set with a compare-and-swap (hash_probes = 1 marks the table as built).
 __global__ void k_heavy_hash(DevModel* hdr, const HeavyEntry* __restrict__ heavy, uint64_t* hkey,
                              uint16_t* hval) {
   const uint32_t H = hdr->nheavy;
-  if (2 * H > HASH_SIZE) return;
+  if (2 * H > HASH_SIZE) return;  // too full to help
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < H; i += gridDim.x * blockDim.x) {
     const uint64_t t = heavy[i].tk;
-    uint32_t p = heavy_hash(t);
-    for (uint32_t r = 1; r <= HASH_SIZE; ++r) {
-      const unsigned long long old = atomicCAS((unsigned long long*)&hkey[p], HASH_EMPTY, t);
+    if (t == HASH_EMPTY) continue;  // (uint64 key 2^64-1): left to the full lookup
+    const uint32_t p = 2 * heavy_hash(t);
+    for (uint32_t w = 0; w < 2; ++w) {
+      const unsigned long long old = atomicCAS((unsigned long long*)&hkey[p + w], HASH_EMPTY, t);
       if (old == HASH_EMPTY) {
-        hval[p] = (uint16_t)heavy[i].ext;
-        atomicMax(&hdr->hash_probes, r);
+        hval[p + w] = (uint16_t)heavy[i].ext;
         break;
       }
-      p = (p + 1) & (HASH_SIZE - 1);
     }
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && H > 0) hdr->hash_probes = 1;
 }
 
 // ---------------------------------------------------------------- host enqueue
@@ -645,7 +644,7 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
                                         M.heavy);
   e = cudaMemsetAsync(M.hkey, 0xFF, HASH_SIZE * sizeof(uint64_t), st);
   if (e) return e;
-  k_heavy_hash<<<(HASH_SIZE / 2 + 255) / 256, 256, 0, st>>>(M.hdr, M.heavy, M.hkey, M.hval);
+  k_heavy_hash<<<(HASH_SIZE / 4 + 255) / 256, 256, 0, st>>>(M.hdr, M.heavy, M.hkey, M.hval);
   add_launches(23);
   return cudaGetLastError();
 }
