@@ -273,7 +273,7 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->o_cand = c.take<uint8_t>(w->cand_cap * 24);
   w->o_sel = c.take<uint64_t>((size_t)P.f0 * std::max<uint32_t>(1, P.hpb));
   w->o_nh = c.take<uint32_t>(P.f0);
-  w->o_part = c.take<double>(2 * 128);
+  w->o_part = c.take<double>(4 * 128);
   w->o_ubase = c.take<uint32_t>(P.L + 2);
   w->o_units = c.take<double>(4 * (P.s / 2048 + P.L + 2));
   w->o_hi = c.take<uint64_t>(1);

@@ -81,20 +81,66 @@ __global__ void k_finite_fix(DevModel* hdr, const unsigned long long* hi) {
 }
 
 // first_rank[k]: index (within the finite range) of the first key equal to key k.
-__global__ void k_first_rank(const uint64_t* __restrict__ tk, const DevModel* hdr,
-                             uint32_t* __restrict__ rank, uint64_t s_cap) {
+// Per block of FR_CHUNK keys: one bisection for the block's first key, then the
+// latest run start at or before each key by a block max-scan.
+constexpr int FR_THREADS = 1024;
+constexpr int FR_PER = 2;
+constexpr int FR_CHUNK = FR_THREADS * FR_PER;
+
+__global__ void __launch_bounds__(FR_THREADS)
+k_first_rank(const uint64_t* __restrict__ tk, const DevModel* hdr, uint32_t* __restrict__ rank,
+             uint64_t s_cap) {
+  __shared__ uint32_t ws[33];
+  __shared__ uint32_t s_r0;
   const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
   const uint64_t* t = tk + lo;
-  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < m;
-       k += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t v = t[k];
-    if (k == 0 || t[k - 1] != v) { rank[k] = (uint32_t)k; continue; }
-    uint64_t a = 0, b = k;  // lower_bound in [0, k)
-    while (a < b) {
-      const uint64_t mid = (a + b) >> 1;
-      if (t[mid] < v) a = mid + 1; else b = mid;
+  for (uint64_t k0 = (uint64_t)blockIdx.x * FR_CHUNK; k0 < m; k0 += (uint64_t)gridDim.x * FR_CHUNK) {
+    if (threadIdx.x == 0) {
+      const uint64_t v = t[k0];
+      uint64_t a = 0, b = k0;  // lower_bound of the block's first key
+      while (a < b) {
+        const uint64_t mid = (a + b) >> 1;
+        if (t[mid] < v) a = mid + 1; else b = mid;
+      }
+      s_r0 = (uint32_t)a;
     }
-    rank[k] = (uint32_t)a;
+    uint32_t st[FR_PER], mx = 0;
+#pragma unroll
+    for (int j = 0; j < FR_PER; ++j) {
+      const uint64_t k = k0 + (uint64_t)threadIdx.x * FR_PER + j;
+      st[j] = 0;
+      if (k < m && (k == 0 || t[k - 1] != t[k])) st[j] = (uint32_t)k;
+      mx = max(mx, st[j]);
+    }
+    // inclusive max-scan of the thread maxima (warp shuffles, then warps)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t inc = mx;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc = max(inc, y);
+    }
+    if (lane == 31) ws[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t w = lane < FR_THREADS / 32 ? ws[lane] : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w = max(w, y);
+      }
+      ws[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = max(s_r0, wid ? ws[wid - 1] : 0u);
+    run = max(run, __shfl_up_sync(0xffffffffu, inc, 1) * (lane ? 1u : 0u));
+#pragma unroll
+    for (int j = 0; j < FR_PER; ++j) {
+      const uint64_t k = k0 + (uint64_t)threadIdx.x * FR_PER + j;
+      run = max(run, st[j]);
+      if (k < m) rank[k] = run;
+    }
+    __syncthreads();
   }
 }
 
@@ -120,44 +166,51 @@ __device__ __forceinline__ double sample_x(const uint64_t* tk, uint64_t lo, uint
   return KT<DT>::dbl(KT<DT>::from_tk(tk[lo + k]));
 }
 
-// pass 0: sum x, sum y; pass 1: centred sums about (mx, my).
+// Root least squares in one pass, shifted by the first point (x_r, y_r):
+// sums of dx, dy, dx*dx, dx*dy per block (the leaves use the same formulas).
 template <int DT>
 __global__ void __launch_bounds__(FIT_THREADS)
 k_fit_sums(const uint64_t* __restrict__ tk, const uint32_t* __restrict__ rank,
-           const DevModel* hdr, int pass, double* partials) {
+           const DevModel* hdr, double* partials) {
   __shared__ double ws[33];
   const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
   const uint64_t chunk = (m + gridDim.x - 1) / gridDim.x;
   const uint64_t b = blockIdx.x * chunk, e = min(m, b + chunk);
   const double inv_m = m ? 1.0 / (double)m : 0.0;
-  const double mx = hdr->root64[1], my = hdr->root64[2];
-  double s0 = 0, s1 = 0;
+  const double xr = m ? sample_x<DT>(tk, lo, 0) : 0.0, yr = m ? (double)rank[0] * inv_m : 0.0;
+  double s[4] = {0, 0, 0, 0};
   for (uint64_t k = b + threadIdx.x; k < e; k += blockDim.x) {
-    const double x = sample_x<DT>(tk, lo, k);
-    const double y = (double)rank[k] * inv_m;
-    if (pass == 0) { s0 += x; s1 += y; }
-    else { const double dx = x - mx; s0 += dx * dx; s1 += dx * (y - my); }
+    const double dx = sample_x<DT>(tk, lo, k) - xr;
+    const double dy = (double)rank[k] * inv_m - yr;
+    s[0] += dx; s[1] += dy; s[2] += dx * dx; s[3] += dx * dy;
   }
-  s0 = block_sum_d(s0, ws);
-  s1 = block_sum_d(s1, ws);
-  if (threadIdx.x == 0) { partials[2 * blockIdx.x] = s0; partials[2 * blockIdx.x + 1] = s1; }
+  for (int i = 0; i < 4; ++i) {
+    const double t = block_sum_d(s[i], ws);
+    if (threadIdx.x == 0) partials[4 * blockIdx.x + i] = t;
+  }
 }
 
-__global__ void k_fit_root(DevModel* hdr, const double* partials, int nblk, int pass) {
+template <int DT>
+__global__ void k_fit_root(DevModel* hdr, const uint64_t* __restrict__ tk,
+                           const uint32_t* __restrict__ rank, const double* partials, int nblk) {
   if (threadIdx.x != 0) return;
-  double s0 = 0, s1 = 0;
-  for (int i = 0; i < nblk; ++i) { s0 += partials[2 * i]; s1 += partials[2 * i + 1]; }
-  const uint64_t m = hdr->s_fin;
-  if (pass == 0) {
-    const double mx = m ? s0 / (double)m : 0.0, my = m ? s1 / (double)m : 0.5;
-    hdr->root64[0] = 0.0;
-    hdr->root64[1] = isfinite(mx) ? mx : 0.0;
-    hdr->root64[2] = my;
-  } else {
-    double a = (s0 > 0) ? s1 / s0 : 0.0;
-    if (!(a >= 0) || !isfinite(a) || !isfinite(hdr->root64[1])) a = 0.0;
-    hdr->root64[0] = a;
+  double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  for (int i = 0; i < nblk; ++i) {
+    s0 += partials[4 * i]; s1 += partials[4 * i + 1];
+    s2 += partials[4 * i + 2]; s3 += partials[4 * i + 3];
   }
+  const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
+  if (!m) { hdr->root64[0] = 0.0; hdr->root64[1] = 0.0; hdr->root64[2] = 0.5; return; }
+  const double xr = sample_x<DT>(tk, lo, 0), yr = (double)rank[0] / (double)m;
+  const double cnt = (double)m;
+  const double mdx = s0 / cnt, mdy = s1 / cnt;
+  const double sxx = s2 - s0 * mdx, sxy = s3 - s0 * mdy;
+  const double mx = xr + mdx;
+  double a = (sxx > 0) ? sxy / sxx : 0.0;
+  if (!(a >= 0) || !isfinite(a) || !isfinite(mx)) a = 0.0;
+  hdr->root64[0] = a;
+  hdr->root64[1] = isfinite(mx) ? mx : 0.0;
+  hdr->root64[2] = yr + mdy;
 }
 
 // FP64 routing used in training: leaf = clamp(floor(L * (a (x - c) + b))).
@@ -169,16 +222,32 @@ __device__ __forceinline__ int leaf64(const double* r, int L, double x) {
   return (int)floor(w);
 }
 
+// Leaf ranges of the sorted sample: each key's leaf once; the neighbours'
+// leaves come from shared memory (block ends evaluate one extra key).
+constexpr int RT_THREADS = 512;
+
 template <int DT>
-__global__ void k_fit_route(const uint64_t* __restrict__ tk, const DevModel* hdr, int L,
-                            uint32_t* leaf_beg, uint32_t* leaf_end) {
+__global__ void __launch_bounds__(RT_THREADS)
+k_fit_route(const uint64_t* __restrict__ tk, const DevModel* hdr, int L, uint32_t* leaf_beg,
+            uint32_t* leaf_end) {
+  __shared__ int lf[RT_THREADS + 2];
   const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
   const double r[3] = {hdr->root64[0], hdr->root64[1], hdr->root64[2]};
-  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < m;
-       k += (uint64_t)gridDim.x * blockDim.x) {
-    const int l = leaf64(r, L, sample_x<DT>(tk, lo, k));
-    if (k == 0 || leaf64(r, L, sample_x<DT>(tk, lo, k - 1)) != l) leaf_beg[l] = (uint32_t)k;
-    if (k + 1 == m || leaf64(r, L, sample_x<DT>(tk, lo, k + 1)) != l) leaf_end[l] = (uint32_t)(k + 1);
+  for (uint64_t k0 = (uint64_t)blockIdx.x * RT_THREADS; k0 < m; k0 += (uint64_t)gridDim.x * RT_THREADS) {
+    const uint64_t k = k0 + threadIdx.x;
+    lf[threadIdx.x + 1] = k < m ? leaf64(r, L, sample_x<DT>(tk, lo, k)) : -1;
+    if (threadIdx.x == 0) lf[0] = k0 ? leaf64(r, L, sample_x<DT>(tk, lo, k0 - 1)) : -1;
+    if (threadIdx.x == 1) {
+      const uint64_t kn = k0 + RT_THREADS;
+      lf[RT_THREADS + 1] = kn < m ? leaf64(r, L, sample_x<DT>(tk, lo, kn)) : -1;
+    }
+    __syncthreads();
+    if (k < m) {
+      const int l = lf[threadIdx.x + 1];
+      if (lf[threadIdx.x] != l) leaf_beg[l] = (uint32_t)k;
+      if (lf[threadIdx.x + 2] != l) leaf_end[l] = (uint32_t)(k + 1);
+    }
+    __syncthreads();
   }
 }
 
@@ -245,19 +314,26 @@ __global__ void k_fit_leaf_final(const uint64_t* __restrict__ tk, const uint32_t
                                  const DevModel* hdr, const uint32_t* leaf_beg,
                                  const uint32_t* leaf_end, const uint32_t* ubase,
                                  const double* unit, int L, double* leaf) {
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int l = (int)((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5);  // one warp per leaf
   if (l >= L) return;
   double* q = leaf + 5 * (size_t)l;
   const uint64_t b = leaf_beg[l], e = leaf_end[l];
-  if (e <= b) { q[0] = 0; q[1] = 0; q[2] = -1; q[3] = -1; q[4] = 0; return; }
-  const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
-  const double inv_m = 1.0 / (double)m;
-  const double cnt = (double)(e - b);
+  if (e <= b) {
+    if (lane == 0) { q[0] = 0; q[1] = 0; q[2] = -1; q[3] = -1; q[4] = 0; }
+    return;
+  }
+  // units of the leaf summed in a fixed order: lane-strided, then a fixed tree
   double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-  for (uint32_t u = ubase[l]; u < ubase[l + 1]; ++u) {
+  for (uint32_t u = ubase[l] + lane; u < ubase[l + 1]; u += 32) {
     s0 += unit[4 * (size_t)u]; s1 += unit[4 * (size_t)u + 1];
     s2 += unit[4 * (size_t)u + 2]; s3 += unit[4 * (size_t)u + 3];
   }
+  s0 = warp_sum(s0); s1 = warp_sum(s1); s2 = warp_sum(s2); s3 = warp_sum(s3);
+  if (lane) return;
+  const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
+  const double inv_m = 1.0 / (double)m;
+  const double cnt = (double)(e - b);
   const double xr = sample_x<DT>(tk, lo, b), yr = (double)rank[b] * inv_m;
   const double mdx = s0 / cnt, mdy = s1 / cnt;
   const double sxx = s2 - s0 * mdx, sxy = s3 - s0 * mdy;
@@ -270,7 +346,6 @@ __global__ void k_fit_leaf_final(const uint64_t* __restrict__ tk, const uint32_t
   q[3] = (double)rank[b] / (double)m;  // lo: eCDF of the leaf's first sample key
   q[4] = 0;
 }
-
 
 __device__ __forceinline__ float fp32_sat(double d) {  // round to FP32, finite
   if (d >= (double)FLT_MAX) return FLT_MAX;
@@ -609,19 +684,19 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   if (e) return e;
   k_finite_range<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, s, M.hdr, W.hi);
   k_finite_fix<<<1, 1, 0, st>>>(M.hdr, W.hi);
-  k_first_rank<<<std::max(1, gs), 256, 0, st>>>(W.smp_a, M.hdr, W.rank, s);
-  k_fit_sums<DT><<<FIT_BLOCKS, FIT_THREADS, 0, st>>>(W.smp_a, W.rank, M.hdr, 0, W.partials);
-  k_fit_root<<<1, 32, 0, st>>>(M.hdr, W.partials, FIT_BLOCKS, 0);
-  k_fit_sums<DT><<<FIT_BLOCKS, FIT_THREADS, 0, st>>>(W.smp_a, W.rank, M.hdr, 1, W.partials);
-  k_fit_root<<<1, 32, 0, st>>>(M.hdr, W.partials, FIT_BLOCKS, 1);
-  k_fit_route<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, M.hdr, L, M.leaf_beg, M.leaf_end);
+  const int fr = (int)std::min<uint64_t>((s + FR_CHUNK - 1) / FR_CHUNK, 4ull * num_sms);
+  k_first_rank<<<std::max(1, fr), FR_THREADS, 0, st>>>(W.smp_a, M.hdr, W.rank, s);
+  k_fit_sums<DT><<<FIT_BLOCKS, FIT_THREADS, 0, st>>>(W.smp_a, W.rank, M.hdr, W.partials);
+  k_fit_root<DT><<<1, 32, 0, st>>>(M.hdr, W.smp_a, W.rank, W.partials, FIT_BLOCKS);
+  const int rb = (int)std::min<uint64_t>((s + RT_THREADS - 1) / RT_THREADS, 8ull * num_sms);
+  k_fit_route<DT><<<std::max(1, rb), RT_THREADS, 0, st>>>(W.smp_a, M.hdr, L, M.leaf_beg, M.leaf_end);
   k_fit_units_plan<<<1, 1024, 0, st>>>(M.leaf_beg, M.leaf_end, L, W.ubase, W.utotal);
   {
     const unsigned ub = (unsigned)std::min<uint64_t>(s / FIT_UNIT + L + 1, 16ull * num_sms);
     k_fit_unit_sums<DT><<<ub, FIT_THREADS, 0, st>>>(W.smp_a, W.rank, M.hdr, M.leaf_beg,
                                                    M.leaf_end, W.ubase, L, W.utotal, W.units);
   }
-  k_fit_leaf_final<DT><<<(L + 255) / 256, 256, 0, st>>>(W.smp_a, W.rank, M.hdr, M.leaf_beg,
+  k_fit_leaf_final<DT><<<(32 * L + 255) / 256, 256, 0, st>>>(W.smp_a, W.rank, M.hdr, M.leaf_beg,
                                                        M.leaf_end, W.ubase, W.units, L, M.leaf64);
   k_fit_final<DT><<<1, 1024, 0, st>>>(M.hdr, L, M.leaf64, M.cleaf);
   k_thresholds<DT><<<(P.f0 + 1 + 127) / 128, 128, 0, st>>>(M.hdr, M.leaf64, L, P.f0, M.thr);
@@ -645,7 +720,7 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   e = cudaMemsetAsync(M.hkey, 0xFF, HASH_SIZE * sizeof(uint64_t), st);
   if (e) return e;
   k_heavy_hash<<<(HASH_SIZE / 4 + 255) / 256, 256, 0, st>>>(M.hdr, M.heavy, M.hkey, M.hval);
-  add_launches(23);
+  add_launches(21);
   return cudaGetLastError();
 }
 
