@@ -225,11 +225,12 @@ static void plan_call(const ls_params* prm, int dt, uint64_t n, uintptr_t addr, 
   P->smem_scatter = level0_smem_scatter(dt, P->L, P->f0, P->n_ext_max);
   // level-1 sub-buckets per bucket: buckets of about l1_target keys each
   const uint64_t per = (uint64_t)P->f0 * P->lim.l1_target;
-  P->kf = (uint32_t)std::min<uint64_t>(MAX_F1, std::max<uint64_t>(1, (n + per - 1) / per));
+  // (ids sub + interval stay below MAX_F1 with up to MAX_HPB heavy values)
+  P->kf = (uint32_t)std::min<uint64_t>(MAX_F1 - MAX_HPB, std::max<uint64_t>(1, (n + per - 1) / per));
   P->cap0 = P->n_ext_max + 16;
   P->cap_r = n / (P->lim.c_large + 1) + 16;     // jobs a refinement level can pass on
   P->capj = std::max(P->cap0, P->cap_r);        // jobs of one refinement level
-  P->cap_c = std::max((uint64_t)P->kf * P->cap0, n / 32 + n / (P->lim.l1_target / 3) + P->capj) + 64;
+  P->cap_c = std::max((uint64_t)(P->kf + MAX_HPB) * P->cap0, n / 32 + n / (P->lim.l1_target / 3) + P->capj) + 64;
   P->cap1 = P->cap_c + P->cap0;
   const uint64_t M = (uint64_t)P->n_ext_max * G;
   P->l0_scan_tiles = (uint32_t)std::max<uint64_t>(1, (M + SC_TILE - 1) / SC_TILE);
@@ -469,8 +470,8 @@ static cudaError_t enqueue_sort(const Plan& P, const Workspace& w, void* keys, D
   LS_TRY(cudaMemsetAsync(at<void>(w, w.o_l0scan), 0, w.l0scan_bytes, st));
   const Level0Args a = level0_args(P, b, w, keys, d);
   LS_TRY(level0_enqueue(P.dt, a, P.smem_hist, P.smem_scatter, b.lists, P.lim, st, &mk, 2));
-  LS_TRY(level1_enqueue(P.dt, keys, a.scratch, P.n, b.M, b.lists, P.lim, b.l1, P.kf, d->err, st,
-                        d->num_sms));
+  LS_TRY(level1_enqueue(P.dt, keys, a.scratch, P.n, b.M, b.lists, P.lim, b.l1, P.kf, a.f0kf,
+                        a.offs, P.c.G, d->err, st, d->num_sms));
   mark(&mk, 6, st);
   LS_TRY(fill_enqueue(P.dt, keys, b.lists, P.cap1, st, d->num_sms));
   mark(&mk, 7, st);
@@ -714,8 +715,7 @@ ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dty
     Job j{};
     j.start = 0;
     j.m = n[i];
-    j.Flo = 0.0;
-    j.Fhi = 1.0;
+    j.span = n[i];
     j.src = 0;
     j.kb = (uint64_t)(uintptr_t)keys[i];
     j.sb = (uint64_t)(uintptr_t)(scr + off * W);
@@ -768,7 +768,7 @@ ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dty
     l.cap_c = cap_c;
     l.cap_jobs = capj;
     // value range, value range again, total-order key range, then the fallback
-    LevelArgs lv[3];
+    LevelArgs lv[3] = {};
     lv[0].in = lists.refine2; lv[0].next = lists.refine3; lv[0].mode = 2;
     lv[0].next_kind = JOB_REFINE; lv[0].kf = 0; lv[0].target = lim.l1_target;
     lv[1].in = lists.refine3; lv[1].next = lists.refine; lv[1].mode = 2;

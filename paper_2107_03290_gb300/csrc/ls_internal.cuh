@@ -15,6 +15,12 @@ constexpr int MAX_LEAVES = 4096;
 constexpr int MAX_FANOUT = 4096;
 constexpr int MAX_HPB = 15;         // equality buckets per level-0 bucket (4-bit count)
 constexpr int MAX_F1 = 1024;        // level-1 sub-buckets per segment
+// Level-0 id of a key (histogram pass -> scatter pass): b | sid << PK_B_BITS
+// for a non-equality key (b: its level-0 bucket; sid: its level-1 id), PK_EQ
+// for a key equal to a heavy value.
+constexpr int PK_B_BITS = 12;       // f0 <= MAX_FANOUT
+constexpr uint32_t PK_B_MASK = (1u << PK_B_BITS) - 1;
+constexpr uint32_t PK_EQ = 0xFFFFFFFFu;
 constexpr unsigned long long SPIN_LIMIT = 1ull << 26;  // bounded waits
 
 // Device status word bits (ls_stream_status).
@@ -231,7 +237,7 @@ __device__ __forceinline__ uint32_t ext_of(typename KT<DT>::U u, const L0Map& q,
 
 // ------------------------------------------------------------------ jobs
 // A segment of keys occupying [start, start+m) of buffer `src` (0: keys,
-// 1: scratch); its keys' F estimates lie in [Flo, Fhi).  kind: what to do.
+// 1: scratch).  kind: what to do.
 enum JobKind : uint32_t {
   JOB_SORT = 0,        // counting sort on the model's slot map
   JOB_FILL = 1,
@@ -242,11 +248,14 @@ enum JobKind : uint32_t {
 struct Job {
   uint64_t start;
   uint64_t m;
-  double Flo, Fhi;
+  uint64_t span;       // refine jobs: keys move within [start, start+span) of the other
+                       // buffer (m, except for a level-0 bucket with heavy values, whose
+                       // non-equality keys spread over the bucket's whole range)
+  uint64_t pad;
   uint64_t value;      // FILL: the key bits to write
   uint32_t src;
   uint32_t kind;
-  uint32_t la, lb;     // unused by the current kernels (zero)
+  uint32_t la, lb;     // model refine jobs: level-0 bucket and its number of heavy values
   uint64_t kb, sb;     // batched arrays: this job's key / scratch array (0: the call's)
 };
 
@@ -256,18 +265,6 @@ __device__ __forceinline__ U* job_keys(const Job& j, U* keys) { return j.kb ? (U
 template <typename U>
 __device__ __forceinline__ U* job_scratch(const Job& j, U* scratch) {
   return j.sb ? (U*)j.sb : scratch;
-}
-
-// Leaves whose output range meets [Flo, Fhi): la = last leaf with lo <= Flo,
-// lb = last leaf with lo < Fhi (FP64 lo values of the fitted model).
-__device__ __forceinline__ void leaf_range(const double* leaf64, int L, double Flo, double Fhi,
-                                           uint32_t* la, uint32_t* lb) {
-  int a = 0, b = L - 1;
-  while (a < b) { const int mid = (a + b + 1) >> 1; if (leaf64[5 * mid + 3] <= Flo) a = mid; else b = mid - 1; }
-  int c = a, d = L - 1;
-  while (c < d) { const int mid = (c + d + 1) >> 1; if (leaf64[5 * mid + 3] < Fhi) c = mid; else d = mid - 1; }
-  *la = (uint32_t)a;
-  *lb = (uint32_t)c;
 }
 
 // Job list: count + capacity-bounded array.

@@ -80,13 +80,14 @@ static L0Layout l0_layout_hist(int W, uint32_t L, uint32_t f0, uint32_t next, ui
   return y;
 }
 
-// K4: double-buffered key and id tiles, per-slot counters, offsets and
-// cursors of the nc = f0 + hmax non-equality slots, staging records.
+// K4: double-buffered key and id tiles, per-bucket counters, offsets and
+// cursors, staging records.
 static L0Layout l0_layout_scatter(int W, uint32_t f0, uint32_t hmax) {
   L0Layout y{};
   size_t o = 0;
   auto al = [&](size_t a) { o = (o + a - 1) / a * a; };
-  const size_t nc = (size_t)f0 + hmax;
+  (void)hmax;
+  const size_t nc = f0;
   y.bar = (uint32_t)o; o += 16;
   al(128); y.buf = (uint32_t)o; o += 2ull * P_TILE * W;
   al(128); y.pbuf = (uint32_t)o; o += 2ull * P_TILE * 4;
@@ -149,8 +150,11 @@ __device__ __forceinline__ L0Map load_tables(const Level0Args& a, unsigned char*
 
 // ---------------------------------------------------------------- K2
 // One model evaluation per key: extended slot e (counted), and the packed id
-// c | sub << 16 (c = compact non-equality slot, 0xFFFF for equality keys;
-// sub = level-1 sub-bucket) stored at the key's position in the body.
+// b | sid << PK_B_BITS (PK_EQ for equality keys) stored at the key's position
+// in the body.  sid = sub + j, sub the key's level-1 sub-bucket and j its
+// interval between the bucket's heavy values: sub is non-decreasing in the key
+// and the heavy values split the key order, so sid is an order-preserving id
+// of the pair (j, sub) in [0, kf + nh).
 // 2 * #{heavy < t} + [t is heavy] over bucket b's padded row (hs entries at
 // stride f0, ascending, padded with the largest key): fixed bisection steps,
 // no divergence.
@@ -182,7 +186,8 @@ __device__ __forceinline__ uint32_t classify_key(typename KT<DT>::U u, const L0M
   const float w = F * f0kf;
   int sub = (w >= 0.0f ? (int)w : 0) - (int)(b * kf);
   sub = sub < 0 ? 0 : (sub >= (int)kf ? (int)kf - 1 : sub);
-  *packed = ((e - b) & 1u) ? 0xFFFFu : (((e + b) >> 1) | ((uint32_t)sub << 16));
+  const uint32_t o = e - h.ext_base;
+  *packed = (o & 1u) ? PK_EQ : (b | ((uint32_t)sub + (o >> 1)) << PK_B_BITS);
   return e;
 }
 
@@ -241,14 +246,14 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
   const unsigned lt = lanemask_lt();
   // full lookup of `valid` lanes' keys, then count and place the id
   auto finish = [&](bool valid, U x, uint64_t i) {
-    uint32_t pv = 0xFFFFu;
+    uint32_t pv = PK_EQ;
     if (valid) {
       const uint32_t e = classify_key<DT>(x, q, heads, heavy, lay.hs, a.f0kf, a.kf, &pv);
       if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
       if (!compact) pk[i - a0] = pv;
     }
     if (compact) {
-      const bool keep = valid && (pv & 0xFFFFu) != 0xFFFFu;
+      const bool keep = valid && pv != PK_EQ;
       const unsigned m = __ballot_sync(0xffffffffu, keep);
       uint32_t wb = 0;
       if (lane == 0 && m) wb = atomicAdd(s_cpos, (uint32_t)__popc(m));
@@ -273,7 +278,7 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
 #pragma unroll
       for (int k = 0; k < H_KPT; ++k) {
         const uint64_t i = base + (uint64_t)k * H_THREADS + threadIdx.x;
-        pp[k] = 0xFFFFu;
+        pp[k] = PK_EQ;
         if (i < ce) {
           const uint32_t e = classify_key<DT>(u[k], q, heads, heavy, lay.hs, a.f0kf, a.kf, &pp[k]);
           if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
@@ -283,7 +288,7 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
       if (compact) {
 #pragma unroll
         for (int k = 0; k < H_KPT; ++k) {
-          const bool keep = (pp[k] & 0xFFFFu) != 0xFFFFu;
+          const bool keep = pp[k] != PK_EQ;
           const unsigned m = __ballot_sync(0xffffffffu, keep);
           uint32_t wb = 0;
           if (lane == 0 && m) wb = atomicAdd(s_cpos, (uint32_t)__popc(m));
@@ -313,7 +318,7 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
         if (t == HASH_EMPTY) e = 0xFFFFFFFFu;  // the empty mark is never a table key
         if (e != 0xFFFFFFFFu) {  // equality key: counted, never moved
           if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
-          if (!compact) pk[i - a0] = 0xFFFFu;
+          if (!compact) pk[i - a0] = PK_EQ;
         } else {
           miss = true;
         }
@@ -350,7 +355,7 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
   if (compact) {  // pad to a multiple of 4 entries (equality marks)
     const uint64_t cpos = *s_cpos;  // (read after the loop's last barrier)
     const uint64_t r4 = (cpos + 3) & ~3ull;
-    if (threadIdx.x < r4 - cpos) pk[cb - a0 + cpos + threadIdx.x] = 0xFFFFu;
+    if (threadIdx.x < r4 - cpos) pk[cb - a0 + cpos + threadIdx.x] = PK_EQ;
     if (threadIdx.x == 0) a.ccount[g] = r4;
   }
   __syncthreads();
@@ -359,10 +364,13 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
 }
 
 // ---------------------------------------------------------------- K4
-// Key tiles and their packed ids stream in by TMA (double buffered).  Per
-// tile: each non-equality key's rank inside its slot (shared atomics), an
-// exclusive scan over the slots gives the staging offsets, keys are staged
-// slot-contiguously and written out so that consecutive threads write
+// Key tiles and their packed ids stream in by TMA (double buffered).  Every
+// non-equality key moves to its level-0 bucket: a bucket's non-equality keys
+// gather at the start of the bucket's range in scratch, in chunk order (a
+// bucket with heavy values is split between its intervals by level 1).  Per
+// tile: each key's rank inside its bucket (shared atomics), an exclusive scan
+// over the buckets gives the staging offsets, keys are staged
+// bucket-contiguously and written out so that consecutive threads write
 // consecutive addresses of a run; the level-1 ids follow their keys.
 // Equality keys are skipped (their slots are filled later).
 template <int DT>
@@ -376,7 +384,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
   uint32_t* ecnt = (uint32_t*)(sm + lay.ecnt);
   uint32_t* soff = (uint32_t*)(sm + lay.soff);
   uint64_t* cursor = (uint64_t*)(sm + lay.cursor);
-  uint32_t* sinfo = (uint32_t*)(sm + lay.sinfo);   // staged slot | rank << 16
+  uint32_t* sinfo = (uint32_t*)(sm + lay.sinfo);   // staged bucket | rank << 16
   uint16_t* sid = (uint16_t*)(sm + lay.sid);       // staged level-1 ids
   uint32_t* ws = (uint32_t*)(sm + lay.ws);
   const U* keys = (const U*)a.keys;
@@ -384,9 +392,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
   uint16_t* oid = a.sid;
   const uint64_t n = a.c.n;
   const uint32_t next = min(a.M.hdr->n_ext, a.n_ext_max);
-  const uint32_t f0 = a.f0;
-  const uint32_t H = min(a.M.hdr->nheavy, (next - f0) / 2);
-  const uint32_t nc = f0 + H;  // non-equality slots
+  const uint32_t nc = a.f0;  // buckets
   const uint32_t g = blockIdx.x, G = a.c.G;
   const uint64_t a0 = a.c.a0, nb = a.c.a1 - a.c.a0;
   uint64_t cb, ce;
@@ -413,13 +419,17 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
   if (threadIdx.x == 0) { issue(0); issue(1); }
   for (uint32_t i = threadIdx.x; i < nc; i += P_THREADS) ecnt[i] = 0;
   const BucketHead* heads = a.M.heads;
-  for (uint32_t b = threadIdx.x; b < f0; b += P_THREADS) {  // cursors of non-equality slots
+  // this chunk's place in bucket b: the bucket's start plus the non-equality
+  // keys of b in earlier chunks (offs[e * G + g] - offs[e * G] over b's intervals)
+  for (uint32_t b = threadIdx.x; b < nc; b += P_THREADS) {
     const BucketHead h = heads[b];
-    const uint32_t nh = h.hoff_nh & 15u, hoff = h.hoff_nh >> 4;
+    const uint32_t nh = h.hoff_nh & 15u;
+    uint64_t cur = h.ext_base < next ? a.offs[(size_t)h.ext_base * G] : n;
     for (uint32_t j = 0; j <= nh; ++j) {
-      const uint32_t c = b + hoff + j, e = h.ext_base + 2 * j;
-      if (c < nc && e < next) cursor[c] = a.offs[(size_t)e * G + g];
+      const uint32_t e = h.ext_base + 2 * j;
+      if (e < next) cur += a.offs[(size_t)e * G + g] - a.offs[(size_t)e * G];
     }
+    cursor[b] = cur;
   }
   __syncthreads();
   if (g == 0 && threadIdx.x == 0) {  // unaligned head and tail, one thread
@@ -427,11 +437,11 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
     for (uint64_t k = 0; k < nht; ++k) {
       const uint64_t i = k < a0 ? k : a.c.a1 + (k - a0);
       const uint32_t p = a.pk[nb + k];
-      const uint32_t c = p & 0xFFFFu;
-      if (c == 0xFFFFu) continue;  // equality slot: filled later
-      if (c >= nc) { set_error(a.err, ERR_BOUNDS); continue; }
-      const uint64_t dst = cursor[c]++;
-      if (dst < n) { out[dst] = keys[i]; oid[dst] = (uint16_t)(p >> 16); }
+      if (p == PK_EQ) continue;  // equality slot: filled later
+      const uint32_t b = p & PK_B_MASK;
+      if (b >= nc) { set_error(a.err, ERR_BOUNDS); continue; }
+      const uint64_t dst = cursor[b]++;
+      if (dst < n) { out[dst] = keys[i]; oid[dst] = (uint16_t)(p >> PK_B_BITS); }
       else set_error(a.err, ERR_BOUNDS);
     }
   }
@@ -447,24 +457,24 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
     for (int k = 0; k < KPT; ++k) {
       const uint32_t i = k * P_THREADS + threadIdx.x;
       u[k] = i < cnt_t ? tb[i] : (U)0;
-      uint32_t p = i < cnt_t ? pb[i] : 0xFFFFu;
-      if ((p & 0xFFFFu) != 0xFFFFu && (p & 0xFFFFu) >= nc) { set_error(a.err, ERR_BOUNDS); p = 0xFFFFu; }
+      uint32_t p = i < cnt_t ? pb[i] : PK_EQ;
+      if (p != PK_EQ && (p & PK_B_MASK) >= nc) { set_error(a.err, ERR_BOUNDS); p = PK_EQ; }
       pp[k] = p;
-      rk[k] = (p & 0xFFFFu) != 0xFFFFu ? atomicAdd(&ecnt[p & 0xFFFFu], 1u) : 0u;
+      rk[k] = p != PK_EQ ? atomicAdd(&ecnt[p & PK_B_MASK], 1u) : 0u;
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < nc; i += P_THREADS) soff[i] = ecnt[i];
     __syncthreads();
     const uint32_t staged = block_scan_array<uint32_t>(soff, (int)nc, ws);
 #pragma unroll
-    for (int k = 0; k < KPT; ++k) {  // stage slot-contiguously
-      const uint32_t c = pp[k] & 0xFFFFu;
-      if (c == 0xFFFFu) continue;
-      const uint32_t s = soff[c] + rk[k];
+    for (int k = 0; k < KPT; ++k) {  // stage bucket-contiguously
+      if (pp[k] == PK_EQ) continue;
+      const uint32_t b = pp[k] & PK_B_MASK;
+      const uint32_t s = soff[b] + rk[k];
       if (s < (uint32_t)P_TILE) {
         tb[s] = u[k];
-        sinfo[s] = c | (rk[k] << 16);
-        sid[s] = (uint16_t)(pp[k] >> 16);
+        sinfo[s] = b | (rk[k] << 16);
+        sid[s] = (uint16_t)(pp[k] >> PK_B_BITS);
       }
     }
     __syncthreads();
@@ -475,7 +485,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
       else set_error(a.err, ERR_BOUNDS);
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < nc; i += P_THREADS) {  // advance the touched slots
+    for (uint32_t i = threadIdx.x; i < nc; i += P_THREADS) {  // advance the touched buckets
       const uint32_t c = ecnt[i];
       if (c) { cursor[i] += c; ecnt[i] = 0; }
     }
@@ -485,6 +495,11 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
 }
 
 // ---------------------------------------------------------------- classify level 0
+// Per extended slot: an equality slot becomes a fill job; the non-equality
+// keys of a bucket without heavy values are sorted (or refined) where they
+// are; those of a bucket with heavy values (gathered at the bucket's start in
+// scratch) always take one level-1 job, which spreads them over the bucket's
+// intervals.
 template <int DT>
 __global__ void k_classify0(Level0Args a, Lists lists, SortLimits lim) {
   const uint32_t next = min(a.M.hdr->n_ext, a.n_ext_max);
@@ -494,8 +509,6 @@ __global__ void k_classify0(Level0Args a, Lists lists, SortLimits lim) {
   for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < next; e += gridDim.x * blockDim.x) {
     const uint64_t start = a.offs[(size_t)e * G];
     const uint64_t end = a.offs[(size_t)(e + 1) * G];
-    if (end <= start) continue;
-    const uint64_t size = end - start;
     uint32_t lo = 0, hi = a.f0;  // last b with ext_base <= e
     while (lo < hi) {
       const uint32_t mid = (lo + hi + 1) >> 1;
@@ -505,22 +518,42 @@ __global__ void k_classify0(Level0Args a, Lists lists, SortLimits lim) {
     const BucketHead h = heads[b];
     const uint32_t o = e - h.ext_base, nh = h.hoff_nh & 15u, hoff = h.hoff_nh >> 4;
     Job job;
-    job.start = start;
-    job.m = size;
     job.value = 0;
     job.src = 1;
+    job.pad = 0;
     job.kb = job.sb = 0;
+    job.la = b;
+    job.lb = 0;
     if (nh && (o & 1u)) {
+      if (end <= start) continue;
+      job.start = start;
+      job.m = job.span = end - start;
       job.kind = JOB_FILL;
       job.value = (uint64_t)KT<DT>::from_tk(heavy[hoff + o / 2].tk);
-      job.Flo = job.Fhi = 0;
       push_job(job.m >= FILL_BIG ? lists.fill_big : lists.fill, job, a.err);
       continue;
     }
-    const uint32_t j = o / 2;
-    job.Flo = (j == 0) ? (double)b / (double)a.f0 : (double)heavy[hoff + j - 1].F;
-    job.Fhi = (j == nh) ? (double)(b + 1) / (double)a.f0 : (double)heavy[hoff + j].F;
-    job.la = job.lb = 0;
+    if (nh) {  // the bucket's non-equality keys, one job from its first slot
+      if (o != 0) continue;
+      uint64_t m = 0;
+      for (uint32_t j = 0; j <= nh; ++j) {
+        const uint32_t ej = e + 2 * j;
+        if (ej < next) m += a.offs[(size_t)(ej + 1) * G] - a.offs[(size_t)ej * G];
+      }
+      if (m == 0) continue;
+      const uint32_t eend = min(e + 2 * nh + 1, next);
+      job.start = start;
+      job.m = m;
+      job.span = a.offs[(size_t)eend * G] - start;
+      job.lb = nh;
+      job.kind = JOB_REFINE;
+      push_job(lists.refine, job, a.err);
+      continue;
+    }
+    if (end <= start) continue;
+    const uint64_t size = end - start;
+    job.start = start;
+    job.m = job.span = size;
     if (size <= lim.c_tiny) { job.kind = JOB_SORT; push_job(lists.sort_t, job, a.err); }
     else if (size <= lim.c_small) { job.kind = JOB_SORT; push_job(lists.sort_s, job, a.err); }
     else if (size <= lim.c_mid) { job.kind = JOB_SORT; push_job(lists.sort_m, job, a.err); }
@@ -653,7 +686,7 @@ k_l1_plan(LevelArgs la, SortLimits lim, Level1Ws w, uint32_t* err) {
       const uint64_t fmx = la.fmax ? min((uint64_t)la.fmax, (uint64_t)MAX_F1) : (uint64_t)MAX_F1;
       uint64_t f = (job.m + tg - 1) / tg;
       f = f < 2 ? 2 : (f > fmx ? fmx : f);
-      if (la.mode == 0) f = la.kf;
+      if (la.mode == 0) f = la.kf + job.lb;  // ids sub + interval
       f1 = f;
       tiles = (job.m + L1_TILE - 1) / L1_TILE;
       w.jmin[j] = ~0ull;
@@ -787,13 +820,36 @@ k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Mod
   }
 }
 
-__global__ void k_l1_cursor(LevelArgs la, Level1Ws w) {
+// First output position of every sub-bucket.  A level-0 bucket with heavy
+// values has ids sub + j over its intervals j; interval j's ids start at
+// sub(h_{j-1}) + j (h the bucket's heavy values, sub(h) from their stored F
+// exactly as the level-0 pass computes a key's), and its keys start where the
+// level-0 offsets put the interval.
+__global__ void k_l1_cursor(LevelArgs la, Level1Ws w, ModelPtrs M) {
   const L1Aux* aux = (const L1Aux*)w.aux;
   const uint64_t C = w.totals[1], nj = w.totals[2];
   for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < C;
        c += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t j = aux_find_c(aux, nj, c);
-    w.cur[c] = la.in.jobs[j].start + (w.off[c] - w.off[aux[j].cbase]);
+    const Job job = la.in.jobs[j];
+    const uint64_t cbase = aux[j].cbase;
+    uint64_t first = cbase, dst0 = job.start;
+    if (la.mode == 0 && job.lb) {
+      const uint32_t b = job.la, cc = (uint32_t)(c - cbase);
+      const BucketHead h = M.heads[b];
+      const uint32_t hoff = h.hoff_nh >> 4;
+      uint32_t iv = 0, f = 0;
+      for (uint32_t i = 0; i < job.lb; ++i) {
+        const float wv = M.heavy[hoff + i].F * la.f0kf;
+        int sub = (wv >= 0.0f ? (int)wv : 0) - (int)(b * la.kf);
+        sub = sub < 0 ? 0 : (sub >= (int)la.kf ? (int)la.kf - 1 : sub);
+        const uint32_t hs = (uint32_t)sub + i + 1;  // first id of interval i + 1
+        if (hs <= cc) { iv = i + 1; f = hs; }
+      }
+      first = cbase + f;
+      dst0 = la.l0offs[(size_t)(h.ext_base + 2 * iv) * la.l0G];
+    }
+    w.cur[c] = dst0 + (w.off[c] - w.off[first]);
   }
 }
 
@@ -861,7 +917,7 @@ k_l1_scatter(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, uint64_t n, 
     for (uint32_t p = threadIdx.x; p < c; p += blockDim.x) {
       const uint32_t s = ids[p];
       const uint64_t dst = gp[s] + (p - lc[s]);
-      if (dst - job.start < job.m) dstb[dst] = stage[p]; else set_error(err, ERR_BOUNDS);
+      if (dst - job.start < job.span) dstb[dst] = stage[p]; else set_error(err, ERR_BOUNDS);
     }
     __syncthreads();
   }
@@ -888,12 +944,9 @@ __global__ void k_l1_classify(Lists lists, LevelArgs la, SortLimits lim, Level1W
       push_job(job.m >= FILL_BIG ? lists.fill_big : lists.fill, job, err);
       continue;
     }
-    const uint64_t sub = c - x.cbase;
-    job.start = pj.start + (w.off[c] - w.off[x.cbase]);
-    job.m = cntc;
-    job.Flo = pj.Flo;
-    job.Fhi = pj.Fhi;
-    (void)sub;
+    job.start = w.cur[c] - cntc;  // the cursor ends past the sub-bucket's keys
+    job.m = job.span = cntc;
+    job.pad = 0;
     job.src = pj.src ^ 1u;
     job.la = job.lb = 0;
     job.kb = pj.kb;
@@ -982,7 +1035,7 @@ static cudaError_t level_dt(void* keys, void* scratch, uint64_t n, const ModelPt
   k_scan<uint32_t><<<tiles, SC_THREADS, 0, st>>>(w.cnt, w.off, w.cap_c, &w.totals[1],
                                                  (uint64_t*)w.scan_status,
                                                  (uint32_t*)((uint64_t*)w.scan_status + tiles), err);
-  k_l1_cursor<<<grid, 256, 0, st>>>(la, w);
+  k_l1_cursor<<<grid, 256, 0, st>>>(la, w, M);
   k_l1_scatter<DT><<<grid, L1_THREADS, l1_scatter_smem(KT<DT>::W), st>>>(
       (U*)keys, (U*)scratch, n, M, la, w, err);
   k_l1_classify<DT><<<grid, 256, 0, st>>>(lists, la, lim, w, M, M.L, err);
@@ -1010,7 +1063,8 @@ cudaError_t levels_enqueue(int dt, void* keys, void* scratch, uint64_t n, const 
 
 cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const ModelPtrs& M,
                            const Lists& lists, const SortLimits& lim, const Level1Ws& w,
-                           uint32_t kf, uint32_t* err, cudaStream_t st, int num_sms) {
+                           uint32_t kf, float f0kf, const uint64_t* l0offs, uint32_t l0G,
+                           uint32_t* err, cudaStream_t st, int num_sms) {
   // level 1 splits by the model; levels 2 and 3 split what it could not by key range
   const JobList ins[3] = {lists.refine, lists.refine2, lists.refine3};
   const JobList outs[3] = {lists.refine2, lists.refine3, lists.fallback};
@@ -1025,6 +1079,9 @@ cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const 
     lvs[lv].kf = kf;
     lvs[lv].target = lv == 2 ? 16 : lim.l1_target / 3;
     lvs[lv].fmax = lv == 2 ? 256 : MAX_F1;
+    lvs[lv].l0offs = l0offs;
+    lvs[lv].l0G = l0G;
+    lvs[lv].f0kf = f0kf;
   }
   return levels_enqueue(dt, keys, scratch, n, M, lists, lim, w, lvs, 3, err, st, num_sms);
 }

@@ -59,6 +59,11 @@ struct LevelArgs {
   uint32_t kf;           // mode 0: sub-buckets per job (ids from the level-0 pass)
   uint32_t target;       // modes 1-2: keys per sub-bucket aimed at
   uint32_t fmax;         // modes 1-2: most sub-buckets per job (<= MAX_F1)
+  // mode 0, jobs of level-0 buckets with heavy values: where each interval
+  // starts (the level-0 slot offsets, G per slot) and the sub-bucket map
+  const uint64_t* l0offs;
+  uint32_t l0G;
+  float f0kf;
 };
 
 struct SortLimits {
@@ -93,7 +98,8 @@ cudaError_t level0_enqueue(int dt, const Level0Args& a, size_t smem_hist, size_t
                            const Marks* mk = nullptr, int mbase = 0);
 cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const ModelPtrs& M,
                            const Lists& lists, const SortLimits& lim, const Level1Ws& w,
-                           uint32_t kf, uint32_t* err, cudaStream_t st, int num_sms);
+                           uint32_t kf, float f0kf, const uint64_t* l0offs, uint32_t l0G,
+                           uint32_t* err, cudaStream_t st, int num_sms);
 cudaError_t levels_enqueue(int dt, void* keys, void* scratch, uint64_t n, const ModelPtrs& M,
                            const Lists& lists, const SortLimits& lim, const Level1Ws& w,
                            const LevelArgs* lvs, int nlv, uint32_t* err, cudaStream_t st,
