@@ -104,9 +104,17 @@ def kernel_algorithmic_bytes(st: dict, n: int, w: int) -> dict:
     }
 
 
+def _region_sha(path: str, begin: str, end: str) -> str:
+    text = open(path, "rb").read()
+    a = text.index(begin.encode())
+    b = text.index(end.encode(), a)
+    return hashlib.sha256(text[a:b]).hexdigest()[:16]
+
+
 def traffic_for(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current source of the kernel (else None)."""
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source (the region of its file between two markers) is still the one the
+    counters were taken on (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -116,7 +124,10 @@ def traffic_for(kernel: str, workload: str):
     if not e:
         return None
     src = os.path.join(ROOT, "paper_2107_03290_gb300", "csrc", e["source"])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    try:
+        h = _region_sha(src, e["begin"], e["end"])
+    except (OSError, ValueError, KeyError):
+        return None
     return e["bytes_per_launch"] if h == e["source_sha"] else None
 
 
