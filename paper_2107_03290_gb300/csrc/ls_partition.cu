@@ -28,8 +28,8 @@
 namespace ls {
 
 struct L0Layout {
-  uint32_t bar, buf, pbuf, thr, cell, cleaf, heads, htk, cnt, ecnt, soff, cursor, sinfo, sid, ws,
-      hkey, hval, queue, total;
+  uint32_t bar, buf, pbuf, thr, cell, cleaf, heads, htk, cnt, ecnt, soff, cursor, gbase, sinfo, sid,
+      ws, hkey, hval, queue, total;
   uint32_t hs;           // K2: heavy values per bucket row (power of two > per-bucket maximum)
 };
 
@@ -94,7 +94,8 @@ static L0Layout l0_layout_scatter(int W, uint32_t f0, uint32_t hmax) {
   y.ecnt = (uint32_t)o; o += nc * 4;
   y.soff = (uint32_t)o; o += (nc + 1) * 4;
   al(8); y.cursor = (uint32_t)o; o += nc * 8;
-  y.sinfo = (uint32_t)o; o += (size_t)P_TILE * 4;
+  y.gbase = (uint32_t)o; o += nc * 8;
+  y.sinfo = (uint32_t)o; o += (size_t)P_TILE * 2;
   y.sid = (uint32_t)o; o += (size_t)P_TILE * 2;
   al(8); y.ws = (uint32_t)o; o += 33 * 8;
   y.total = (uint32_t)o;
@@ -384,7 +385,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
   uint32_t* ecnt = (uint32_t*)(sm + lay.ecnt);
   uint32_t* soff = (uint32_t*)(sm + lay.soff);
   uint64_t* cursor = (uint64_t*)(sm + lay.cursor);
-  uint32_t* sinfo = (uint32_t*)(sm + lay.sinfo);   // staged bucket | rank << 16
+  uint64_t* gbase = (uint64_t*)(sm + lay.gbase);  // output of staged position s of bucket b: gbase[b] + s
+  uint16_t* sinfo = (uint16_t*)(sm + lay.sinfo);   // staged keys' buckets
   uint16_t* sid = (uint16_t*)(sm + lay.sid);       // staged level-1 ids
   uint32_t* ws = (uint32_t*)(sm + lay.ws);
   const U* keys = (const U*)a.keys;
@@ -463,9 +465,28 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
       rk[k] = p != PK_EQ ? atomicAdd(&ecnt[p & PK_B_MASK], 1u) : 0u;
     }
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < nc; i += P_THREADS) soff[i] = ecnt[i];
+    // the tile's bucket offsets; each bucket's output base moves past the tile
+    uint32_t staged;
+    {
+      const uint32_t per = (nc + P_THREADS - 1) / P_THREADS;
+      const uint32_t b0 = threadIdx.x * per;
+      uint32_t sum = 0;
+      for (uint32_t i = 0; i < per; ++i)
+        if (b0 + i < nc) sum += ecnt[b0 + i];
+      uint32_t run = block_excl_sum<uint32_t>(sum, ws, &staged);
+      for (uint32_t i = 0; i < per; ++i) {
+        const uint32_t b = b0 + i;
+        if (b < nc) {
+          const uint32_t c = ecnt[b];
+          soff[b] = run;
+          gbase[b] = cursor[b] - run;  // (mod 2^64)
+          cursor[b] += c;
+          ecnt[b] = 0;
+          run += c;
+        }
+      }
+    }
     __syncthreads();
-    const uint32_t staged = block_scan_array<uint32_t>(soff, (int)nc, ws);
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {  // stage bucket-contiguously
       if (pp[k] == PK_EQ) continue;
@@ -473,21 +494,15 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
       const uint32_t s = soff[b] + rk[k];
       if (s < (uint32_t)P_TILE) {
         tb[s] = u[k];
-        sinfo[s] = b | (rk[k] << 16);
+        sinfo[s] = (uint16_t)b;
         sid[s] = (uint16_t)(pp[k] >> PK_B_BITS);
       }
     }
     __syncthreads();
     for (uint32_t s = threadIdx.x; s < staged; s += P_THREADS) {
-      const uint32_t inf = sinfo[s];
-      const uint64_t dst = cursor[inf & 0xFFFFu] + (inf >> 16);
+      const uint64_t dst = gbase[sinfo[s]] + s;
       if (dst < n) { out[dst] = tb[s]; oid[dst] = sid[s]; }
       else set_error(a.err, ERR_BOUNDS);
-    }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < nc; i += P_THREADS) {  // advance the touched buckets
-      const uint32_t c = ecnt[i];
-      if (c) { cursor[i] += c; ecnt[i] = 0; }
     }
     __syncthreads();
     if (threadIdx.x == 0) issue(t + 2);
@@ -587,12 +602,42 @@ __device__ __forceinline__ void fill_range(U* dst, uint64_t m, U v, uint64_t tid
   for (uint64_t i = tid; i < ne; i += stride) dst[i < head ? i : tail0 + (i - head)] = v;
 }
 
-// Big fills: every CTA takes a share of every job; small fills: one CTA per
-// job, round robin.
+// Fill jobs are cut into units of FILL_UNIT keys and CTAs take units round
+// robin (a unit's job found by bisection over the units' prefix, which every
+// CTA scans for itself), so the stores spread evenly over the grid whatever
+// the mix of job sizes.  More jobs than FILL_MAXJ: big jobs shared by the
+// whole grid, small ones one CTA each.
+constexpr uint32_t FILL_UNIT = 4096;
+constexpr int FILL_MAXJ = 4096;
+
 template <typename U>
 __global__ void __launch_bounds__(256) k_fill(U* __restrict__ keys, JobList small, JobList big) {
+  __shared__ uint32_t pre[FILL_MAXJ + 1];
+  __shared__ uint32_t ws[33];
   const unsigned long long nb = min(*big.count, big.cap);
   const unsigned long long ns = min(*small.count, small.cap);
+  const unsigned long long nj = nb + ns;
+  auto job_at = [&](unsigned long long j) -> const Job& { return j < nb ? big.jobs[j] : small.jobs[j - nb]; };
+  if (nj <= (unsigned long long)FILL_MAXJ) {
+    for (uint32_t j = threadIdx.x; j < nj; j += blockDim.x)
+      pre[j] = (uint32_t)((job_at(j).m + FILL_UNIT - 1) / FILL_UNIT);
+    __syncthreads();
+    const uint32_t T = block_scan_array<uint32_t>(pre, (int)nj, ws);  // exclusive, in place
+    if (threadIdx.x == 0) pre[nj] = T;
+    __syncthreads();
+    for (uint32_t u = blockIdx.x; u < T; u += gridDim.x) {
+      uint32_t lo = 0, hi = (uint32_t)nj - 1;  // last j with pre[j] <= u
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= u) lo = mid; else hi = mid - 1;
+      }
+      const Job& job = job_at(lo);
+      const uint64_t off = (uint64_t)(u - pre[lo]) * FILL_UNIT;
+      const uint64_t m = min((uint64_t)FILL_UNIT, job.m - off);
+      fill_range<U>(job_keys(job, keys) + job.start + off, m, (U)job.value, threadIdx.x, blockDim.x);
+    }
+    return;
+  }
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t gtid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   for (unsigned long long j = 0; j < nb; ++j) {
@@ -738,6 +783,25 @@ __device__ __forceinline__ uint64_t aux_find_c(const L1Aux* aux, uint64_t nj, ui
   return lo - 1;
 }
 
+// The tiles of a level are dealt to the CTAs in contiguous ranges: a CTA finds
+// its first tile's job by bisection, then steps from job to job.
+struct TileWalk {
+  uint64_t t, t1, j, nbase;
+};
+__device__ __forceinline__ bool tile_walk_begin(const L1Aux* aux, uint64_t T, uint64_t nj,
+                                                TileWalk& w) {
+  const uint64_t per = (T + gridDim.x - 1) / gridDim.x;
+  w.t = blockIdx.x * per;
+  w.t1 = min(T, w.t + per);
+  if (w.t >= w.t1) return false;
+  w.j = aux_find_tile(aux, nj, w.t);
+  w.nbase = aux[w.j + 1].tile_base;  // aux[nj] is the end sentinel
+  return true;
+}
+__device__ __forceinline__ void tile_walk_job(const L1Aux* aux, TileWalk& w) {
+  while (w.t >= w.nbase) { ++w.j; w.nbase = aux[w.j + 1].tile_base; }
+}
+
 // Total-order key range of every job of a range level (one atomic pair per tile).
 template <int DT>
 __global__ void __launch_bounds__(L1_THREADS)
@@ -748,8 +812,11 @@ k_l1_minmax(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, L
   const L1Aux* aux = (const L1Aux*)w.aux;
   const uint64_t T = w.totals[0], nj = w.totals[2];
   const int lane = threadIdx.x & 31;
-  for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
-    const uint64_t j = aux_find_tile(aux, nj, t);
+  TileWalk tw;
+  if (!tile_walk_begin(aux, T, nj, tw)) return;
+  for (; tw.t < tw.t1; ++tw.t) {
+    tile_walk_job(aux, tw);
+    const uint64_t t = tw.t, j = tw.j;
     const Job job = la.in.jobs[j];
     const uint64_t off = (t - aux[j].tile_base) * L1_TILE;
     const uint32_t c = (uint32_t)min((uint64_t)L1_TILE, job.m - off);
@@ -781,8 +848,11 @@ k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Mod
   __shared__ uint32_t hc[MAX_F1];
   const L1Aux* aux = (const L1Aux*)w.aux;
   const uint64_t T = w.totals[0], nj = w.totals[2];
-  for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
-    const uint64_t j = aux_find_tile(aux, nj, t);
+  TileWalk tw;
+  if (!tile_walk_begin(aux, T, nj, tw)) return;
+  for (; tw.t < tw.t1; ++tw.t) {
+    tile_walk_job(aux, tw);
+    const uint64_t t = tw.t, j = tw.j;
     const L1Aux x = aux[j];
     const Job job = la.in.jobs[j];
     const uint64_t off = (t - x.tile_base) * L1_TILE;
@@ -869,8 +939,11 @@ k_l1_scatter(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, uint64_t n, 
   uint16_t* ids = (uint16_t*)(dsm + sizeof(U) * L1_TILE);  // L1_TILE slot ids
   const L1Aux* aux = (const L1Aux*)w.aux;
   const uint64_t T = w.totals[0], nj = w.totals[2];
-  for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
-    const uint64_t j = aux_find_tile(aux, nj, t);
+  TileWalk tw;
+  if (!tile_walk_begin(aux, T, nj, tw)) return;
+  for (; tw.t < tw.t1; ++tw.t) {
+    tile_walk_job(aux, tw);
+    const uint64_t t = tw.t, j = tw.j;
     if (w.jmin[j] == w.jmax[j]) continue;  // homogeneous: filled, not moved
     const L1Aux x = aux[j];
     const Job job = la.in.jobs[j];
@@ -933,7 +1006,6 @@ __global__ void k_l1_classify(Lists lists, LevelArgs la, SortLimits lim, Level1W
     const uint64_t cntc = w.off[c + 1] - w.off[c];
     if (cntc == 0) continue;
     const uint64_t j = aux_find_c(aux, nj, c);
-    const L1Aux x = aux[j];
     const Job pj = la.in.jobs[j];
     Job job;
     job.value = 0;

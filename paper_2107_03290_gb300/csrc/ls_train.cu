@@ -8,8 +8,10 @@
 //     rank (count of sample keys below x, ties take the first rank), then one
 //     line per leaf over the keys the root routes to it; slopes clamped to >= 0
 //     and each leaf's output clamped to [lo_l, hi_l] so that F is monotone;
-//  4. FP32 evaluation parameters on a 64-bit fixed-point grid (integer ops
-//     only per key, no FP64 in the per-key path);
+//  4. the per-key lookup of the FP64 level-0 map: its f0 thresholds in the
+//     total order (bisection over the FP64 model), an FP32 cell-index RMI
+//     fitted to the same sample, and the bucket range of each of its cells
+//     (no FP64 in the per-key path);
 //  5. heavy values: sample runs of length >= tau, at most `hpb` per level-0
 //     bucket (longest first), each given an equality slot.
 // All reductions use a fixed order, so a model is bit-reproducible run to run.
@@ -561,42 +563,85 @@ __global__ void k_heavy_compact(const uint64_t* __restrict__ tk, const DevModel*
   }
 }
 
-// One thread per bucket: keep the hpb longest runs (ties: smaller key), by key.
-__global__ void k_heavy_select(const Cand* __restrict__ cand, const uint64_t* ncand_ptr,
-                               uint64_t cand_cap, uint32_t f0, int hpb, uint64_t* sel,
-                               uint32_t* nh, DevModel* hdr) {
-  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+// One CTA per bucket: keep the hpb longest runs (ties: smaller key), listed
+// by key.  A candidate's place is the number of the bucket's candidates that
+// beat it (candidates are distinct values, so places are distinct); a bucket
+// with more candidates than the shared copy holds takes one thread's insertion
+// pass instead.
+constexpr int SEL_THREADS = 256;
+constexpr int SEL_CAP = 1024;
+
+__global__ void __launch_bounds__(SEL_THREADS)
+k_heavy_select(const Cand* __restrict__ cand, const uint64_t* ncand_ptr, uint64_t cand_cap,
+               uint32_t f0, int hpb, uint64_t* sel, uint32_t* nh, DevModel* hdr) {
+  __shared__ uint64_t s_tk[SEL_CAP], s_len[SEL_CAP];
+  __shared__ uint64_t s_top[MAX_HPB], s_toplen[MAX_HPB];  // the selected, by place
+  __shared__ uint64_t s_ab[2];
+  const uint32_t b = blockIdx.x;
   if (b >= f0) return;
-  const uint64_t nc = min(*ncand_ptr, cand_cap);
-  uint64_t a = 0, e = nc;  // lower_bound of bucket b
-  while (a < e) { const uint64_t mid = (a + e) >> 1; if (cand[mid].bucket < b) a = mid + 1; else e = mid; }
-  uint64_t a2 = a, e2 = nc;  // lower_bound of bucket b+1
-  while (a2 < e2) { const uint64_t mid = (a2 + e2) >> 1; if (cand[mid].bucket <= b) a2 = mid + 1; else e2 = mid; }
+  if (threadIdx.x < 2) {  // lower bounds of buckets b and b + 1 (candidates are in key order)
+    const uint64_t nc = min(*ncand_ptr, cand_cap);
+    const uint32_t bb = b + threadIdx.x;
+    uint64_t lo = 0, hi = nc;
+    while (lo < hi) { const uint64_t mid = (lo + hi) >> 1; if (cand[mid].bucket < bb) lo = mid + 1; else hi = mid; }
+    s_ab[threadIdx.x] = lo;
+  }
+  __syncthreads();
+  const uint64_t a = s_ab[0], k = s_ab[1] - a;
+  const uint32_t cnt = (uint32_t)min(k, (uint64_t)hpb);
+  if (k <= (uint64_t)SEL_CAP) {
+    for (uint32_t i = threadIdx.x; i < k; i += SEL_THREADS) {
+      s_tk[i] = cand[a + i].tk;
+      s_len[i] = cand[a + i].len;
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < k; i += SEL_THREADS) {
+      const uint64_t t = s_tk[i], len = s_len[i];
+      uint32_t place = 0;
+      for (uint32_t j = 0; j < k; ++j)
+        place += (s_len[j] > len || (s_len[j] == len && s_tk[j] < t)) ? 1u : 0u;
+      if (place < cnt) { s_top[place] = t; s_toplen[place] = len; }
+    }
+    __syncthreads();
+    if (threadIdx.x < cnt) {  // key order among the selected
+      const uint64_t t = s_top[threadIdx.x];
+      uint32_t kr = 0;
+      for (uint32_t q = 0; q < cnt; ++q) kr += s_top[q] < t ? 1u : 0u;
+      sel[(size_t)b * hpb + kr] = t;
+    }
+    if (threadIdx.x == 0) {
+      unsigned long long len = 0;
+      for (uint32_t q = 0; q < cnt; ++q) len += s_toplen[q];
+      if (len) atomicAdd(&hdr->heavy_len, len);
+      nh[b] = cnt;
+    }
+    return;
+  }
+  if (threadIdx.x != 0) return;
   uint64_t ktk[MAX_HPB], klen[MAX_HPB];
-  int cnt = 0;
-  for (uint64_t i = a; i < a2; ++i) {
+  int c = 0;
+  for (uint64_t i = a; i < a + k; ++i) {
     const uint64_t t = cand[i].tk, len = cand[i].len;
     // insert into the top list ordered by (len desc, tk asc)
-    int p = cnt;
+    int p = c;
     while (p > 0 && (klen[p - 1] < len || (klen[p - 1] == len && ktk[p - 1] > t))) --p;
     if (p >= hpb) continue;
-    const int last = min(cnt, hpb - 1);
+    const int last = min(c, hpb - 1);
     for (int q = last; q > p; --q) { ktk[q] = ktk[q - 1]; klen[q] = klen[q - 1]; }
     ktk[p] = t; klen[p] = len;
-    if (cnt < hpb) ++cnt;
+    if (c < hpb) ++c;
   }
   unsigned long long len = 0;
-  for (int i = 0; i < cnt; ++i) len += klen[i];
+  for (int i = 0; i < c; ++i) len += klen[i];
   if (len) atomicAdd(&hdr->heavy_len, len);
-  // order by key
-  for (int i = 1; i < cnt; ++i) {
+  for (int i = 1; i < c; ++i) {  // order by key
     const uint64_t t = ktk[i];
     int j = i;
     while (j > 0 && ktk[j - 1] > t) { ktk[j] = ktk[j - 1]; --j; }
     ktk[j] = t;
   }
-  for (int i = 0; i < cnt; ++i) sel[(size_t)b * hpb + i] = ktk[i];
-  nh[b] = (uint32_t)cnt;
+  for (int i = 0; i < c; ++i) sel[(size_t)b * hpb + i] = ktk[i];
+  nh[b] = (uint32_t)c;
 }
 
 template <int DT>
@@ -713,7 +758,7 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
                                                    err);
   k_heavy_compact<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, M.hdr, W.flags, W.cpos, M.thr,
                                                       M.cell, M.cleaf, (Cand*)W.cand, W.cand_cap);
-  k_heavy_select<<<(P.f0 + 255) / 256, 256, 0, st>>>((const Cand*)W.cand, W.cpos + s, W.cand_cap,
+  k_heavy_select<<<P.f0, SEL_THREADS, 0, st>>>((const Cand*)W.cand, W.cpos + s, W.cand_cap,
                                                      P.f0, (int)P.hpb, W.sel, W.nh, M.hdr);
   k_heavy_heads<DT><<<1, 1024, 0, st>>>(W.sel, W.nh, P.f0, (int)P.hpb, M.hdr, M.cleaf, M.heads,
                                         M.heavy);
