@@ -154,8 +154,19 @@ ls_status ls_level0_histogram(const void* keys, size_t n, ls_dtype dtype, void* 
                               size_t* n_ext);
 
 /* Sort `count` 64-bit unsigned keys at device pointer `keys` in place with
- * the library's LSD radix sort (the sample sort of the training step). */
+ * the library's LSD radix sort (8-bit digits, one pass per digit with a
+ * decoupled look-back across tiles).  count >= 2^30: LS_ERR_INVALID. */
 ls_status ls_radix_sort_u64(uint64_t* keys, size_t count, void* stream);
+
+/* Sort `count` 64-bit unsigned keys at device pointer `keys` in place with the
+ * sample sort that orders the training sample (Sec. 5.1: the model is fitted
+ * to the sorted 1% sample): 2048 splitters from a sorted 8192-key evenly
+ * spaced oversample, each key routed to a gap between splitters or to a
+ * splitter's own value, each gap sorted in shared memory (a gap over 4096 keys
+ * is sorted in chunks and merged in global memory).  Scratch (count + 2048
+ * keys and 48 KB of counters) comes from the library's stream-ordered pool.
+ * count >= 2^32: LS_ERR_INVALID, keys untouched. */
+ls_status ls_sample_sort_u64(uint64_t* keys, size_t count, void* stream);
 
 /* Kernels the library has enqueued since it was loaded (diagnostics). */
 uint64_t ls_kernel_launches(void);

@@ -128,7 +128,8 @@ class RequestStats(ctypes.Structure):
 
 EXPORTED = ["ls_default_params", "ls_status_string", "ls_sort", "ls_sort_ex", "ls_sort_host",
             "ls_sort_batch", "ls_stream_status", "ls_train", "ls_level0_histogram",
-            "ls_radix_sort_u64", "ls_radix_sort_u64_noalloc", "ls_kernel_launches",
+            "ls_radix_sort_u64", "ls_radix_sort_u64_noalloc", "ls_sample_sort_u64",
+            "ls_kernel_launches",
             "ls_server_create", "ls_server_submit", "ls_server_submit_from", "ls_server_wait",
             "ls_server_destroy"]
 
@@ -168,6 +169,7 @@ def load(path: str | None = None):
             "ls_level0_histogram": [vp, sz, i32, vp, P(Params), vp, sz, P(ctypes.c_size_t)],
             "ls_radix_sort_u64": [vp, sz, vp],
             "ls_radix_sort_u64_noalloc": [vp, sz, vp],
+            "ls_sample_sort_u64": [vp, sz, vp],
             "ls_server_create": [P(ServerConfig), P(vp)],
             "ls_server_submit": [vp, vp, sz, i32, P(u64)],
             "ls_server_submit_from": [vp, vp, vp, sz, i32, P(u64)],
@@ -282,6 +284,16 @@ def radix_sort_u64_(t, stream=None):
         raise TypeError("uint64 tensor expected")
     _check(load().ls_radix_sort_u64(_device_tensor(t).data_ptr(), t.numel(), _stream(stream)),
            "ls_radix_sort_u64")
+
+
+def sample_sort_u64_(t, stream=None):
+    """Sort a uint64 CUDA tensor in place with the training sample's sample sort
+    (ls_sample_sort_u64)."""
+    torch = _torch()
+    if t.dtype != torch.uint64:
+        raise TypeError("uint64 tensor expected")
+    _check(load().ls_sample_sort_u64(_device_tensor(t).data_ptr(), t.numel(), _stream(stream)),
+           "ls_sample_sort_u64")
 
 
 NOALLOC_RADIX_MAX = 1 << 20

@@ -253,7 +253,7 @@ struct Workspace {
   size_t bytes = 0;
   // offsets
   size_t o_scratch, o_smp_a, o_smp_b, o_rank, o_flags, o_cpos, o_cand, o_sel, o_nh, o_part, o_hi,
-      o_tscan, o_rs_hist, o_rs_skip, o_rs_status, o_hdr, o_leaf64, o_thr, o_cell, o_cleaf, o_hkey, o_hval, o_heads, o_heavy,
+      o_tscan, o_ss_spl, o_ss_words, o_rs_hist, o_rs_skip, o_rs_status, o_hdr, o_leaf64, o_thr, o_cell, o_cleaf, o_hkey, o_hval, o_heads, o_heavy,
       o_lbeg, o_lend, o_hist, o_offs, o_l0scan, o_jobs_fill, o_jobs_s, o_jobs_l, o_jobs_m, o_jobs_fb2, o_jobs_t, o_jobs_r,
       o_jobs_fb, o_jobs_r2, o_jobs_r3, o_pk, o_sid, o_ccount, o_counts, o_aux, o_tot, o_l1cnt, o_l1off, o_l1cur, o_jmin, o_jmax, o_l1scan,
       o_ubase, o_units;
@@ -274,16 +274,19 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->o_cand = c.take<uint8_t>(w->cand_cap * 24);
   w->o_sel = c.take<uint64_t>((size_t)P.f0 * std::max<uint32_t>(1, P.hpb));
   w->o_nh = c.take<uint32_t>(P.f0);
-  w->o_part = c.take<double>(4 * 128);
+  w->o_part = c.take<double>(4 * FIT_BLOCKS);
   w->o_ubase = c.take<uint32_t>(P.L + 2);
   w->o_units = c.take<double>(4 * (P.s / 2048 + P.L + 2));
   w->o_hi = c.take<uint64_t>(1);
   const uint64_t stiles = std::max<uint64_t>(1, (s + SC_TILE - 1) / SC_TILE);
   w->tscan_bytes = stiles * 8 + 16;
   w->o_tscan = c.take<uint8_t>(w->tscan_bytes);
-  w->o_rs_hist = c.take<uint32_t>(8 * 256);
-  w->o_rs_skip = c.take<uint32_t>(8);
-  w->rs_status_bytes = rs_status_words(s) * 4 + 8 * 4;
+  w->o_ss_spl = c.take<uint64_t>(SS_P);
+  w->o_ss_words = c.take<uint32_t>(ss_work_words());
+  const bool narrow = P.W == 4;  // 4-byte keys sort their sample by radix
+  w->o_rs_hist = c.take<uint32_t>(narrow ? 8 * 256 : 0);
+  w->o_rs_skip = c.take<uint32_t>(narrow ? 8 : 0);
+  w->rs_status_bytes = narrow ? rs_status_words(s) * 4 + 8 * 4 : 0;
   w->o_rs_status = c.take<uint8_t>(w->rs_status_bytes);
   w->o_hdr = c.take<DevModel>(1);
   w->o_leaf64 = c.take<double>(5 * (size_t)P.L);
@@ -371,6 +374,10 @@ static Bound bind(const Plan& P, const Workspace& w) {
   T.hi = at<unsigned long long>(w, w.o_hi);
   T.scan_status = at<void>(w, w.o_tscan);
   T.scan_status_bytes = w.tscan_bytes;
+  T.ss.spl = at<uint64_t>(w, w.o_ss_spl);
+  T.ss.cnt = at<uint32_t>(w, w.o_ss_words);
+  T.ss.beg = T.ss.cnt + (SS_NB + 1);
+  T.ss.cur = T.ss.beg + (SS_NB + 1);
   T.rs.hist = at<uint32_t>(w, w.o_rs_hist);
   T.rs.skip = at<uint32_t>(w, w.o_rs_skip);
   T.rs.status = at<uint32_t>(w, w.o_rs_status);
@@ -473,10 +480,11 @@ static cudaError_t enqueue_sort(const Plan& P, const Workspace& w, void* keys, D
   LS_TRY(level1_enqueue(P.dt, keys, a.scratch, P.n, b.M, b.lists, P.lim, b.l1, P.kf, a.f0kf,
                         a.offs, P.c.G, d->err, st, d->num_sms));
   mark(&mk, 6, st);
-  LS_TRY(fill_enqueue(P.dt, keys, b.lists, P.cap1, st, d->num_sms));
+  LS_TRY(fill_enqueue(P.dt, keys, b.lists, nullptr, nullptr, st, d->num_sms));
   mark(&mk, 7, st);
   LS_TRY(buckets_enqueue(P.dt, keys, a.scratch, P.n, b.M, b.lists, P.cap1, P.cap1, P.cap1,
                          b.counts + 8, d->err, st, d->num_sms, &mk, 8));
+  mark(&mk, 10, st);
   return cudaSuccess;
 }
 
@@ -779,7 +787,7 @@ ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dty
     lv[2].fmax = 256;
     ModelPtrs M{};
     e = levels_enqueue(dtype, nullptr, nullptr, N, M, lists, lim, l, lv, 3, d->err, st, d->num_sms);
-    if (!e) e = fill_enqueue(dtype, nullptr, lists, cap1, st, d->num_sms);
+    if (!e) e = fill_enqueue(dtype, nullptr, lists, nullptr, nullptr, st, d->num_sms);
     if (!e) e = buckets_enqueue(dtype, nullptr, nullptr, N, M, lists, cap1, cap1, cap1, counts + 8,
                                 d->err, st, d->num_sms, nullptr, 0);
   }
@@ -939,6 +947,31 @@ ls_status ls_radix_sort_u64(uint64_t* keys, size_t count, void* stream) {
   rw.ctr = rw.status + rs_status_words(count);
   e = radix_sort_u64_enqueue(keys, (uint64_t*)((char*)base + o_tmp), count, rw, d->err, st,
                              d->num_sms);
+  cudaFreeAsync(base, st);
+  return to_status(e);
+}
+
+ls_status ls_sample_sort_u64(uint64_t* keys, size_t count, void* stream) {
+  if (count > 0 && !keys) return LS_ERR_INVALID;
+  if (count < 2) return LS_OK;
+  if (count >= (1ull << 32)) return LS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  Device* d;
+  cudaError_t e = get_device(&d);
+  if (e) return to_status(e);
+  Carver c;
+  const size_t o_tmp = c.take<uint64_t>(count);
+  const size_t o_spl = c.take<uint64_t>(SS_P);
+  const size_t o_words = c.take<uint32_t>(ss_work_words());
+  void* base = nullptr;
+  if ((e = cudaMallocFromPoolAsync(&base, c.off + 256, d->pool, st))) return to_status(e);
+  SsWork sw;
+  sw.spl = (uint64_t*)((char*)base + o_spl);
+  sw.cnt = (uint32_t*)((char*)base + o_words);
+  sw.beg = sw.cnt + (SS_NB + 1);
+  sw.cur = sw.beg + (SS_NB + 1);
+  e = sample_sort_u64_enqueue(keys, (uint64_t*)((char*)base + o_tmp), count, sw, d->err, st,
+                              d->num_sms);
   cudaFreeAsync(base, st);
   return to_status(e);
 }

@@ -215,7 +215,7 @@ __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* 
 }
 
 template <int DT, int THREADS, int KPT>
-__global__ void __launch_bounds__(THREADS, THREADS == 512 ? 2 : (KPT == 16 ? 3 : (THREADS == 128 ? 8 : 4)))
+__global__ void __launch_bounds__(THREADS, THREADS == 512 ? (KPT == 8 ? 3 : 2) : (KPT == 16 ? 3 : (THREADS == 128 ? 8 : 4)))
 k_bucket_sort(typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, ModelPtrs M,
               JobList list, unsigned long long* ctr, uint32_t* err) {
   typedef typename KT<DT>::U U;
@@ -356,7 +356,7 @@ k_fallback(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, ModelPtrs M, J
 // ---------------------------------------------------------------- host enqueue
 constexpr int BS_TINY_T = 128, BS_TINY_K = 4;      // CAP 512
 constexpr int BS_SMALL_T = 256, BS_SMALL_K = 8;    // CAP 2048
-constexpr int BS_MID_T = 256, BS_MID_K = 16;       // CAP 4096
+constexpr int BS_MID_T = 512, BS_MID_K = 8;        // CAP 4096
 constexpr int BS_LARGE_T = 512, BS_LARGE_K = 16;   // CAP 8192
 
 template <int DT>
@@ -422,7 +422,6 @@ static cudaError_t buckets_dt(void* keys, void* scratch, const ModelPtrs& M, con
   mark(mk, mb + 1, st);
   k_fallback<DT><<<gf, 512, BucketCfg<DT, 512, 16>::SMEM_FB, st>>>((U*)keys, (U*)scratch, M,
                                                                   lists.fallback, ctrs + 2, err);
-  mark(mk, mb + 2, st);
   add_launches(5);
   return cudaGetLastError();
 }

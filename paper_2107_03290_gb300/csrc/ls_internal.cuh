@@ -311,6 +311,18 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 // Work area of the LSD radix sort (ls_radix.cuh).  `ctr` must directly follow
 // `status` in memory (one memset clears both).
+// Work area of the training sample's sample sort (ls_samplesort.cuh).
+constexpr int SS_OVER = 4;                 // oversample keys per splitter
+constexpr int SS_P = 2048;                 // splitters
+constexpr int SS_NB = 2 * SS_P + 1;        // buckets: gaps 2j, splitter values 2j+1
+struct SsWork {
+  uint64_t* spl;   // SS_P
+  uint32_t* cnt;   // SS_NB + 1
+  uint32_t* beg;   // SS_NB + 1
+  uint32_t* cur;   // SS_NB + 1
+};
+inline size_t ss_work_words() { return (size_t)3 * (SS_NB + 1); }
+
 struct RsWork {
   uint32_t* hist;     // 8 * 256 digit counts / offsets
   uint32_t* skip;     // 8

@@ -611,13 +611,23 @@ constexpr uint32_t FILL_UNIT = 4096;
 constexpr int FILL_MAXJ = 4096;
 
 template <typename U>
-__global__ void __launch_bounds__(256) k_fill(U* __restrict__ keys, JobList small, JobList big) {
+__global__ void __launch_bounds__(256) k_fill(U* __restrict__ keys, JobList small, JobList big,
+                                              const unsigned long long* __restrict__ from,
+                                              const unsigned long long* __restrict__ upto) {
   __shared__ uint32_t pre[FILL_MAXJ + 1];
   __shared__ uint32_t ws[33];
-  const unsigned long long nb = min(*big.count, big.cap);
-  const unsigned long long ns = min(*small.count, small.cap);
+  // jobs [s0, s1) of `small` and [b0, b1) of `big`: from / upto hold {small, big}
+  // positions (null: the list's start / its current count)
+  const unsigned long long s1 = upto ? upto[0] : min(*small.count, small.cap);
+  const unsigned long long b1 = upto ? upto[1] : min(*big.count, big.cap);
+  const unsigned long long s0 = from ? min(from[0], s1) : 0ull;
+  const unsigned long long b0 = from ? min(from[1], b1) : 0ull;
+  const unsigned long long nb = b1 - b0, ns = s1 - s0;
   const unsigned long long nj = nb + ns;
-  auto job_at = [&](unsigned long long j) -> const Job& { return j < nb ? big.jobs[j] : small.jobs[j - nb]; };
+  auto job_at = [&](unsigned long long j) -> const Job& {
+    return j < nb ? big.jobs[b0 + j] : small.jobs[s0 + (j - nb)];
+  };
+  if (nj == 0) return;
   if (nj <= (unsigned long long)FILL_MAXJ) {
     for (uint32_t j = threadIdx.x; j < nj; j += blockDim.x)
       pre[j] = (uint32_t)((job_at(j).m + FILL_UNIT - 1) / FILL_UNIT);
@@ -641,11 +651,11 @@ __global__ void __launch_bounds__(256) k_fill(U* __restrict__ keys, JobList smal
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t gtid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   for (unsigned long long j = 0; j < nb; ++j) {
-    const Job job = big.jobs[j];
+    const Job job = big.jobs[b0 + j];
     fill_range<U>(job_keys(job, keys) + job.start, job.m, (U)job.value, gtid, stride);
   }
   for (unsigned long long j = blockIdx.x; j < ns; j += gridDim.x) {
-    const Job job = small.jobs[j];
+    const Job job = small.jobs[s0 + j];
     fill_range<U>(job_keys(job, keys) + job.start, job.m, (U)job.value, threadIdx.x, blockDim.x);
   }
 }
@@ -1158,13 +1168,12 @@ cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const 
   return levels_enqueue(dt, keys, scratch, n, M, lists, lim, w, lvs, 3, err, st, num_sms);
 }
 
-cudaError_t fill_enqueue(int dt, void* keys, const Lists& lists, uint64_t fill_cap,
-                         cudaStream_t st, int num_sms) {
-  (void)fill_cap;
+cudaError_t fill_enqueue(int dt, void* keys, const Lists& lists, const unsigned long long* from,
+                         const unsigned long long* upto, cudaStream_t st, int num_sms) {
   if (dt == LS_F64 || dt == LS_U64)
-    k_fill<uint64_t><<<4 * num_sms, 256, 0, st>>>((uint64_t*)keys, lists.fill, lists.fill_big);
+    k_fill<uint64_t><<<4 * num_sms, 256, 0, st>>>((uint64_t*)keys, lists.fill, lists.fill_big, from, upto);
   else
-    k_fill<uint32_t><<<4 * num_sms, 256, 0, st>>>((uint32_t*)keys, lists.fill, lists.fill_big);
+    k_fill<uint32_t><<<4 * num_sms, 256, 0, st>>>((uint32_t*)keys, lists.fill, lists.fill_big, from, upto);
   add_launches(1);
   return cudaGetLastError();
 }

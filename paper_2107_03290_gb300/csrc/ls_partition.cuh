@@ -104,8 +104,10 @@ cudaError_t levels_enqueue(int dt, void* keys, void* scratch, uint64_t n, const 
                            const Lists& lists, const SortLimits& lim, const Level1Ws& w,
                            const LevelArgs* lvs, int nlv, uint32_t* err, cudaStream_t st,
                            int num_sms);
-cudaError_t fill_enqueue(int dt, void* keys, const Lists& lists, uint64_t fill_cap,
-                         cudaStream_t st, int num_sms);
+// Fill jobs [from, upto) of the two fill lists ({small, big} positions in
+// device memory; null: the start / the lists' counts when the kernel runs).
+cudaError_t fill_enqueue(int dt, void* keys, const Lists& lists, const unsigned long long* from,
+                         const unsigned long long* upto, cudaStream_t st, int num_sms);
 cudaError_t buckets_configure(int dt);
 cudaError_t buckets_enqueue(int dt, void* keys, void* scratch, uint64_t n, const ModelPtrs& M,
                             const Lists& lists, uint64_t cap_s, uint64_t cap_l,

@@ -1,0 +1,291 @@
+// Sort of the training sample (Sec. 5.1 trains the model on a 1% sample,
+// which must be in key order to give each sample key its eCDF rank), as a
+// sample sort of 64-bit total-order keys:
+//
+//  1. an evenly spaced oversample of SS_CAND keys, sorted by one CTA, gives
+//     SS_P splitters (every SS_OVER-th);
+//  2. each key goes to a gap between splitters (bucket 2j: keys strictly
+//     between splitter j-1 and splitter j) or to a splitter's own value
+//     (bucket 2j+1: keys equal to splitter j, already in order);
+//  3. per-bucket sizes, their exclusive scan, and a scatter whose per-tile
+//     bucket ranges are reserved with one atomic per (tile, bucket);
+//  4. each gap sorted in shared memory by a bitonic network; a gap larger
+//     than SS_CAP keys (rare: the oversample bounds the gaps with high
+//     probability) is sorted in SS_CAP chunks and merged in global memory.
+//
+// There is no look-back chain and only five launches.  Keys equal to a
+// splitter never need a sort, so heavy repeats cost one pass.
+#pragma once
+#include "ls_scan.cuh"
+
+namespace ls {
+
+constexpr int SS_CAND = SS_P * SS_OVER;    // oversample, sorted by one CTA
+constexpr int SS_THREADS = 512;
+constexpr int SS_KPT = 8;
+constexpr int SS_TILE = SS_THREADS * SS_KPT;
+constexpr int SS_CAP = 4096;               // gap sorted in one CTA's shared memory
+
+// Ascending bitonic sort of a[0..n) in shared memory, n a power of two, by the
+// whole block.
+__device__ __forceinline__ void ss_bitonic(uint64_t* a, uint32_t n) {
+  for (uint32_t k = 2; k <= n; k <<= 1)
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < n / 2; i += blockDim.x) {
+        const uint32_t p = 2 * i - (i & (j - 1)), q = p + j;  // pair i of the stage
+        const bool up = (p & k) == 0;
+        const uint64_t x = a[p], y = a[q];
+        if ((x > y) == up) { a[p] = y; a[q] = x; }
+      }
+      __syncthreads();
+    }
+}
+
+// Bucket of key t: 2 * #{splitters < t} + [t equals the next splitter].
+__device__ __forceinline__ uint32_t ss_bucket(const uint64_t* spl, uint64_t t) {
+  uint32_t lo = 0;
+#pragma unroll
+  for (uint32_t s = SS_P / 2; s; s >>= 1)
+    if (spl[lo + s - 1] < t) lo += s;
+  if (spl[lo] < t) lo += 1;  // lo = #{spl < t} in [0, SS_P]
+  return 2 * lo + ((lo < (uint32_t)SS_P && spl[lo] == t) ? 1u : 0u);
+}
+
+// Bitonic stages j < 8 of level k over the 8 consecutive elements v[0..8) at
+// position base (pairs never leave an aligned group of 8).
+__device__ __forceinline__ void ss_bitonic_regs(uint64_t* v, uint32_t base, uint32_t k, uint32_t jmax) {
+#pragma unroll
+  for (uint32_t j = 4; j > 0; j >>= 1) {
+    if (j > jmax) continue;
+#pragma unroll
+    for (uint32_t p = 0; p < 8; ++p) {
+      if (p & j) continue;
+      const bool up = ((base + p) & k) == 0;
+      const uint64_t x = v[p], y = v[p + j];
+      if ((x > y) == up) { v[p] = y; v[p + j] = x; }
+    }
+  }
+}
+
+// The oversample sorted by one CTA of 1024 threads, 8 consecutive keys per
+// thread: the stages inside a group of 8 run in registers, the others through
+// shared memory.
+static __global__ void __launch_bounds__(1024)
+k_ss_splitters(const uint64_t* __restrict__ keys, uint64_t m, uint64_t* __restrict__ spl,
+               uint32_t* __restrict__ cnt) {
+  extern __shared__ uint64_t ss_c[];
+  static_assert(SS_CAND == 8 * 1024, "8 keys per thread");
+  const uint32_t base = 8 * threadIdx.x;
+  uint64_t v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = keys[(uint64_t)(base + q) * m / SS_CAND];
+  for (uint32_t i = threadIdx.x; i <= SS_NB; i += blockDim.x) cnt[i] = 0;
+  for (uint32_t k = 2; k <= 8; k <<= 1) ss_bitonic_regs(v, base, k, k >> 1);
+  for (uint32_t k = 16; k <= (uint32_t)SS_CAND; k <<= 1) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ss_c[base + q] = v[q];
+    __syncthreads();
+    for (uint32_t j = k >> 1; j >= 8; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < SS_CAND / 2; i += blockDim.x) {
+        const uint32_t p = 2 * i - (i & (j - 1)), q = p + j;
+        const bool up = (p & k) == 0;
+        const uint64_t x = ss_c[p], y = ss_c[q];
+        if ((x > y) == up) { ss_c[p] = y; ss_c[q] = x; }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = ss_c[base + q];
+    __syncthreads();
+    ss_bitonic_regs(v, base, k, 4);
+  }
+  // every SS_OVER-th key of the sorted oversample (SS_OVER divides 8)
+#pragma unroll
+  for (int q = SS_OVER - 1; q < 8; q += SS_OVER) spl[(base + q) / SS_OVER] = v[q];
+}
+
+static __global__ void __launch_bounds__(SS_THREADS)
+k_ss_count(const uint64_t* __restrict__ keys, uint64_t m, const uint64_t* __restrict__ spl,
+           uint32_t* __restrict__ cnt) {
+  __shared__ uint64_t s_spl[SS_P];
+  __shared__ uint32_t h[SS_NB];
+  for (uint32_t i = threadIdx.x; i < SS_P; i += blockDim.x) s_spl[i] = spl[i];
+  for (uint32_t i = threadIdx.x; i < SS_NB; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    atomicAdd(&h[ss_bucket(s_spl, keys[i])], 1u);
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < SS_NB; i += blockDim.x)
+    if (h[i]) atomicAdd(&cnt[i], h[i]);
+}
+
+// beg = exclusive scan of cnt (beg[SS_NB] = m), cur = beg.
+static __global__ void __launch_bounds__(1024)
+k_ss_scan(const uint32_t* __restrict__ cnt, uint32_t* __restrict__ beg, uint32_t* __restrict__ cur) {
+  __shared__ uint32_t a[SS_NB + 1];
+  __shared__ uint32_t ws[33];
+  for (uint32_t i = threadIdx.x; i < SS_NB; i += blockDim.x) a[i] = cnt[i];
+  __syncthreads();
+  const uint32_t tot = block_scan_array<uint32_t>(a, SS_NB, ws);
+  for (uint32_t i = threadIdx.x; i < SS_NB; i += blockDim.x) { beg[i] = a[i]; cur[i] = a[i]; }
+  if (threadIdx.x == 0) beg[SS_NB] = tot;
+}
+
+static __global__ void __launch_bounds__(SS_THREADS)
+k_ss_scatter(const uint64_t* __restrict__ keys, uint64_t m, const uint64_t* __restrict__ spl,
+             uint32_t* __restrict__ cur, uint64_t* __restrict__ out, uint32_t* err) {
+  __shared__ uint64_t s_spl[SS_P];
+  __shared__ uint32_t lc[SS_NB];  // per tile: counts, then output bases
+  for (uint32_t i = threadIdx.x; i < SS_P; i += blockDim.x) s_spl[i] = spl[i];
+  for (uint32_t i = threadIdx.x; i < SS_NB; i += blockDim.x) lc[i] = 0;
+  __syncthreads();
+  const uint64_t tiles = (m + SS_TILE - 1) / SS_TILE;
+  for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    uint64_t x[SS_KPT];
+    uint32_t bk[SS_KPT], rk[SS_KPT];
+#pragma unroll
+    for (int k = 0; k < SS_KPT; ++k) {
+      const uint64_t i = t * SS_TILE + (uint64_t)k * SS_THREADS + threadIdx.x;
+      bk[k] = 0xFFFFFFFFu;
+      rk[k] = 0;
+      if (i < m) {
+        x[k] = keys[i];
+        bk[k] = ss_bucket(s_spl, x[k]);
+        rk[k] = atomicAdd(&lc[bk[k]], 1u);
+      }
+    }
+    __syncthreads();
+    {  // reserve the tile's range of every bucket: independent atomics, issued together
+      constexpr int PER = (SS_NB + SS_THREADS - 1) / SS_THREADS;
+      uint32_t base[PER];
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const uint32_t b = q * SS_THREADS + threadIdx.x;
+        const uint32_t c = b < (uint32_t)SS_NB ? lc[b] : 0u;
+        base[q] = c ? atomicAdd(&cur[b], c) : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const uint32_t b = q * SS_THREADS + threadIdx.x;
+        if (b < (uint32_t)SS_NB) lc[b] = base[q];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < SS_KPT; ++k) {
+      if (bk[k] == 0xFFFFFFFFu) continue;
+      const uint64_t p = (uint64_t)lc[bk[k]] + rk[k];
+      if (p < m) out[p] = x[k]; else set_error(err, ERR_BOUNDS);
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < SS_NB; b += blockDim.x) lc[b] = 0;
+    __syncthreads();
+  }
+}
+
+// Number of elements of A among the first k outputs of the stable merge of
+// A[0..na) and B[0..nb) (A first on ties).
+__device__ __forceinline__ uint32_t ss_merge_path(const uint64_t* A, uint32_t na, const uint64_t* B,
+                                                  uint32_t nb, uint32_t k) {
+  uint32_t lo = k > nb ? k - nb : 0, hi = k < na ? k : na;
+  while (lo < hi) {
+    const uint32_t i = (lo + hi) >> 1;
+    if (A[i] <= B[k - i - 1]) lo = i + 1; else hi = i;
+  }
+  return lo;
+}
+
+// Loads up to SS_CAP keys, pads with the largest key to a power of two,
+// sorts, writes the first `len` back.
+__device__ __forceinline__ void ss_sort_chunk(const uint64_t* src, uint64_t* dst, uint32_t len,
+                                              uint64_t* a) {
+  uint32_t n2 = 2;
+  while (n2 < len) n2 <<= 1;
+  for (uint32_t i = threadIdx.x; i < n2; i += blockDim.x) a[i] = i < len ? src[i] : ~0ull;
+  __syncthreads();
+  ss_bitonic(a, n2);
+  for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) dst[i] = a[i];
+  __syncthreads();
+}
+
+// One CTA per gap: sorted from `in` into `out`.  The CTAs past the buckets
+// copy the splitter-value buckets, a tile of positions at a time, so that a
+// heavily repeated value does not fall to a single CTA.  A gap over SS_CAP
+// keys: sorted chunks, then merge passes that alternate between the bucket's
+// ranges of `out` and `in`.
+static __global__ void __launch_bounds__(SS_THREADS)
+k_ss_bucket_sort(uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                 const uint32_t* __restrict__ beg) {
+  __shared__ uint64_t a[SS_CAP];
+  const uint32_t b = blockIdx.x;
+  if (b >= (uint32_t)SS_NB) {
+    uint32_t* sb = (uint32_t*)a;  // bucket starts (SS_NB + 1 words fit in a[])
+    for (uint32_t i = threadIdx.x; i <= (uint32_t)SS_NB; i += blockDim.x) sb[i] = beg[i];
+    __syncthreads();
+    const uint32_t m = sb[SS_NB];
+    for (uint64_t p = (uint64_t)(b - SS_NB) * blockDim.x + threadIdx.x; p < m;
+         p += (uint64_t)(gridDim.x - SS_NB) * blockDim.x) {
+      uint32_t lo = 0, hi = SS_NB - 1;  // last bucket starting at or before p
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (sb[mid] <= p) lo = mid; else hi = mid - 1;
+      }
+      if (lo & 1u) out[p] = in[p];
+    }
+    return;
+  }
+  if (b & 1u) return;
+  const uint32_t a0 = beg[b], len = beg[b + 1] - a0;
+  if (len == 0) return;
+  if (len == 1) { if (threadIdx.x == 0) out[a0] = in[a0]; return; }
+  if (len <= (uint32_t)SS_CAP) {
+    ss_sort_chunk(in + a0, out + a0, len, a);
+    return;
+  }
+  for (uint32_t c0 = 0; c0 < len; c0 += SS_CAP)
+    ss_sort_chunk(in + a0 + c0, out + a0 + c0, min((uint32_t)SS_CAP, len - c0), a);
+  uint64_t* src = out + a0;
+  uint64_t* dst = in + a0;
+  for (uint32_t w = SS_CAP; w < len; w <<= 1) {
+    for (uint32_t p0 = 0; p0 < len; p0 += 2 * w) {
+      const uint32_t na = min(w, len - p0);
+      const uint32_t nb = len - p0 > w ? min(w, len - p0 - w) : 0u;
+      const uint64_t* A = src + p0;
+      const uint64_t* B = A + na;
+      const uint32_t tot = na + nb;
+      const uint32_t per = (tot + blockDim.x - 1) / blockDim.x;
+      const uint32_t k0 = min(tot, threadIdx.x * per), k1 = min(tot, k0 + per);
+      uint32_t i = ss_merge_path(A, na, B, nb, k0), j = k0 - i;
+      for (uint32_t k = k0; k < k1; ++k) {
+        const bool ta = i < na && (j >= nb || A[i] <= B[j]);
+        dst[p0 + k] = ta ? A[i++] : B[j++];
+      }
+    }
+    __syncthreads();
+    uint64_t* t = src; src = dst; dst = t;
+  }
+  if (src != out + a0)
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) out[a0 + i] = src[i];
+}
+
+// Sorts a[0..m) (m < 2^32) using b[0..m) as scratch; the result is in a.
+inline cudaError_t ss_sort_enqueue(uint64_t* a, uint64_t* b, uint64_t m, const SsWork& w,
+                                   uint32_t* err, cudaStream_t st, int num_sms) {
+  if (m < 2) return cudaSuccess;
+  const size_t smem = (size_t)SS_CAND * sizeof(uint64_t);
+  cudaError_t e = cudaFuncSetAttribute(k_ss_splitters, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e) return e;
+  const unsigned g = (unsigned)std::max<uint64_t>(
+      1, std::min<uint64_t>((m + SS_TILE - 1) / SS_TILE, 2ull * num_sms));
+  k_ss_splitters<<<1, 1024, smem, st>>>(a, m, w.spl, w.cnt);
+  k_ss_count<<<g, SS_THREADS, 0, st>>>(a, m, w.spl, w.cnt);
+  k_ss_scan<<<1, 1024, 0, st>>>(w.cnt, w.beg, w.cur);
+  k_ss_scatter<<<g, SS_THREADS, 0, st>>>(a, m, w.spl, w.cur, b, err);
+  k_ss_bucket_sort<<<SS_NB + 2 * num_sms, SS_THREADS, 0, st>>>(b, a, w.beg);
+  add_launches(5);
+  return cudaGetLastError();
+}
+
+}  // namespace ls

@@ -18,6 +18,7 @@
 #include <cfloat>
 
 #include "ls_radix.cuh"
+#include "ls_samplesort.cuh"
 #include "ls_train.cuh"
 
 namespace ls {
@@ -29,15 +30,33 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {  // SplitMix64 output fu
   return z ^ (z >> 31);
 }
 
+// x / d and x mod d by the reciprocal m = floor((2^64 - 1) / d) (Barrett
+// reduction): floor(x * m / 2^64) is at most 2 below the quotient, and the
+// corrections fix it exactly.
+struct Div64 {
+  uint64_t d, m;
+};
+static Div64 make_div64(uint64_t d) { return Div64{d, ~0ull / d}; }
+__device__ __forceinline__ uint64_t div64(uint64_t x, const Div64& v, uint64_t* rem) {
+  uint64_t q = __umul64hi(x, v.m);
+  uint64_t r = x - q * v.d;
+  if (r >= v.d) { r -= v.d; ++q; }
+  if (r >= v.d) { r -= v.d; ++q; }
+  *rem = r;
+  return q;
+}
+
+// Stratified sample: i_k = floor(k n / s) + mix64(seed ^ k) mod max(1, floor(n / s)).
 template <int DT>
 __global__ void k_sample(const typename KT<DT>::U* __restrict__ keys, uint64_t n, uint64_t s,
-                         uint64_t seed, uint64_t* __restrict__ out) {
-  uint64_t stride = n / s;
-  if (stride == 0) stride = 1;
+                         uint64_t seed, Div64 ds, Div64 dst, uint64_t* __restrict__ out) {
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < s;
        k += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t base = (uint64_t)(((unsigned __int128)k * n) / s);
-    uint64_t i = base + mix64(seed ^ k) % stride;
+    uint64_t base, r;
+    if (n < (1ull << 32)) base = div64(k * n, ds, &r);  // k < s <= n: k n < 2^64
+    else base = (uint64_t)(((unsigned __int128)k * n) / s);
+    div64(mix64(seed ^ k), dst, &r);
+    uint64_t i = base + r;
     if (i >= n) i = n - 1;  // unreachable by the formula; keeps the load in bounds
     out[k] = KT<DT>::tk(keys[i]);
   }
@@ -146,7 +165,6 @@ k_first_rank(const uint64_t* __restrict__ tk, const DevModel* hdr, uint32_t* __r
   }
 }
 
-constexpr int FIT_BLOCKS = 128;
 constexpr int FIT_THREADS = 256;
 
 __device__ __forceinline__ double block_sum_d(double v, double* ws) {
@@ -195,12 +213,14 @@ k_fit_sums(const uint64_t* __restrict__ tk, const uint32_t* __restrict__ rank,
 template <int DT>
 __global__ void k_fit_root(DevModel* hdr, const uint64_t* __restrict__ tk,
                            const uint32_t* __restrict__ rank, const double* partials, int nblk) {
-  if (threadIdx.x != 0) return;
+  // block partials summed lane-strided, then by a fixed warp tree (deterministic)
   double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-  for (int i = 0; i < nblk; ++i) {
+  for (int i = threadIdx.x; i < nblk; i += 32) {
     s0 += partials[4 * i]; s1 += partials[4 * i + 1];
     s2 += partials[4 * i + 2]; s3 += partials[4 * i + 3];
   }
+  s0 = warp_sum(s0); s1 = warp_sum(s1); s2 = warp_sum(s2); s3 = warp_sum(s3);
+  if (threadIdx.x != 0) return;
   const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
   if (!m) { hdr->root64[0] = 0.0; hdr->root64[1] = 0.0; hdr->root64[2] = 0.5; return; }
   const double xr = sample_x<DT>(tk, lo, 0), yr = (double)rank[0] / (double)m;
@@ -440,28 +460,50 @@ template <int DT> struct TkRange {
   static constexpr uint64_t NEVER = KT<DT>::W == 8 ? ~0ull : 0x100000000ull;
 };
 
-// thr[b] = min { t : pos(t) >= b } by bisection over the whole total order
-// (pos is non-decreasing in t); thread f0 records the bucket of the largest key.
+// Smallest t in [lo, hi] with pred(t), for a predicate non-decreasing in t
+// with pred(hi) true, by one warp: each round the 32 lanes test 31 evenly
+// spaced points and the interval shrinks to the gap holding the first true
+// one (64-bit ranges take 13 rounds instead of 64 bisection steps).
+template <typename Pred>
+__device__ __forceinline__ uint64_t warp_first_true(uint64_t lo, uint64_t hi, Pred pred) {
+  const int lane = threadIdx.x & 31;
+  while (hi - lo >= 32) {
+    const uint64_t step = (hi - lo) >> 5;
+    const uint64_t p = lane < 31 ? lo + (uint64_t)(lane + 1) * step : hi;
+    const unsigned bal = __ballot_sync(0xffffffffu, lane == 31 || pred(p));
+    const int f = __ffs(bal) - 1;
+    const uint64_t pf = __shfl_sync(0xffffffffu, p, f);
+    const uint64_t pb = __shfl_sync(0xffffffffu, p, f > 0 ? f - 1 : 0);
+    lo = f > 0 ? pb + 1 : lo;
+    hi = pf;
+  }
+  const uint64_t p = lo + (uint64_t)lane;
+  const unsigned bal = __ballot_sync(0xffffffffu, p >= hi || pred(p));
+  return lo + (uint64_t)(__ffs(bal) - 1);
+}
+
+// thr[b] = min { t : pos(t) >= b } over the whole total order (pos is
+// non-decreasing in t), one warp per bucket; warp f0 records the bucket of the
+// largest key.
 template <int DT>
 __global__ void __launch_bounds__(128)
 k_thresholds(DevModel* hdr, const double* __restrict__ leaf, int L, uint32_t f0, uint64_t* thr) {
-  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (b > f0) return;
   const double r[3] = {hdr->root64[0], hdr->root64[1], hdr->root64[2]};
   const uint64_t TMAX = TkRange<DT>::MAX;
   if (b == f0) {
-    hdr->pos_max = pos64<DT>(TMAX, r, leaf, L, f0);
-    hdr->cell_span = 0;
+    if (lane == 0) {
+      hdr->pos_max = pos64<DT>(TMAX, r, leaf, L, f0);
+      hdr->cell_span = 0;
+    }
     return;
   }
-  if (b == 0) { thr[0] = 0; return; }
-  if (pos64<DT>(TMAX, r, leaf, L, f0) < b) { thr[b] = TkRange<DT>::NEVER; return; }
-  uint64_t lo = 0, hi = TMAX;
-  while (lo < hi) {
-    const uint64_t mid = lo + ((hi - lo) >> 1);
-    if (pos64<DT>(mid, r, leaf, L, f0) >= b) hi = mid; else lo = mid + 1;
-  }
-  thr[b] = lo;
+  if (b == 0) { if (lane == 0) thr[0] = 0; return; }
+  if (pos64<DT>(TMAX, r, leaf, L, f0) < b) { if (lane == 0) thr[b] = TkRange<DT>::NEVER; return; }
+  const uint64_t t = warp_first_true(0ull, TMAX, [&](uint64_t x) { return pos64<DT>(x, r, leaf, L, f0) >= b; });
+  if (lane == 0) thr[b] = t;
 }
 
 // #{ b in [1, f0) : thr[b] <= t }
@@ -474,31 +516,30 @@ __device__ __forceinline__ uint32_t thr_count(const uint64_t* thr, uint32_t f0, 
   return lo - 1;
 }
 
-// Smallest total-order key whose cell is >= c (NEVER if there is none).
+// Smallest total-order key whose cell is >= c (NEVER if there is none), by
+// one warp.
 template <int DT>
 __device__ __forceinline__ uint64_t cell_start(uint32_t c, const CellRoot& cr,
                                                const CellLeaf* cleaf) {
   const uint64_t TMAX = TkRange<DT>::MAX;
   if (cell_of<DT>(KT<DT>::from_tk(TMAX), cr, cleaf) < c) return TkRange<DT>::NEVER;
-  uint64_t lo = 0, hi = TMAX;
-  while (lo < hi) {
-    const uint64_t mid = lo + ((hi - lo) >> 1);
-    if (cell_of<DT>(KT<DT>::from_tk(mid), cr, cleaf) >= c) hi = mid; else lo = mid + 1;
-  }
-  return lo;
+  return warp_first_true(0ull, TMAX,
+                         [&](uint64_t x) { return cell_of<DT>(KT<DT>::from_tk(x), cr, cleaf) >= c; });
 }
 
 // Cell table: for cell c, the bucket range [count(first key), count(last key)]
-// of the keys whose cell is c (the cell map is non-decreasing in the key).
+// of the keys whose cell is c (the cell map is non-decreasing in the key); one
+// warp per cell.
 template <int DT>
 __global__ void k_cell_table(DevModel* hdr, const uint64_t* __restrict__ thr, uint32_t f0,
                              const CellLeaf* __restrict__ cleaf, uint32_t* cell) {
-  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (c >= L0_CELLS) return;
   const uint64_t TMAX = TkRange<DT>::MAX, NEVER = TkRange<DT>::NEVER;
   const CellRoot cr = hdr->croot;
   const uint64_t a = c ? cell_start<DT>(c, cr, cleaf) : 0ull;
   const uint64_t e = c + 1 < L0_CELLS ? cell_start<DT>(c + 1, cr, cleaf) : NEVER;
+  if ((threadIdx.x & 31) != 0) return;
   uint32_t lo, hi;
   if (a == NEVER || a > TMAX) {          // no key maps here
     lo = hi = thr_count(thr, f0, TMAX);
@@ -722,8 +763,12 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   const int gs = (int)std::min<uint64_t>((s + 255) / 256, 8ull * num_sms);
   k_train_init<<<std::max(1, (L + 255) / 256), 256, 0, st>>>(M.hdr, s, M.leaf_beg, M.leaf_end, L,
                                                              W.partials);
-  k_sample<DT><<<std::max(1, gs), 256, 0, st>>>(keys, n, s, P.seed, W.smp_a);
-  cudaError_t e = rs_sort_enqueue(W.smp_a, W.smp_b, s, nullptr, nullptr, W.rs, err, st, num_sms);
+  const uint64_t stride = std::max<uint64_t>(1, n / s);
+  k_sample<DT><<<std::max(1, gs), 256, 0, st>>>(keys, n, s, P.seed, make_div64(s), make_div64(stride),
+                                                W.smp_a);
+  // 4-byte keys: the radix sort skips the four constant high digits; 8-byte keys: sample sort
+  cudaError_t e = KT<DT>::W == 4 ? rs_sort_enqueue(W.smp_a, W.smp_b, s, nullptr, nullptr, W.rs, err, st, num_sms)
+                                 : ss_sort_enqueue(W.smp_a, W.smp_b, s, W.ss, err, st, num_sms);
   if (e) return e;
   e = cudaMemsetAsync(W.hi, 0, sizeof(unsigned long long), st);
   if (e) return e;
@@ -744,8 +789,8 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   k_fit_leaf_final<DT><<<(32 * L + 255) / 256, 256, 0, st>>>(W.smp_a, W.rank, M.hdr, M.leaf_beg,
                                                        M.leaf_end, W.ubase, W.units, L, M.leaf64);
   k_fit_final<DT><<<1, 1024, 0, st>>>(M.hdr, L, M.leaf64, M.cleaf);
-  k_thresholds<DT><<<(P.f0 + 1 + 127) / 128, 128, 0, st>>>(M.hdr, M.leaf64, L, P.f0, M.thr);
-  k_cell_table<DT><<<(L0_CELLS + 127) / 128, 128, 0, st>>>(M.hdr, M.thr, P.f0, M.cleaf, M.cell);
+  k_thresholds<DT><<<(32 * (P.f0 + 1) + 127) / 128, 128, 0, st>>>(M.hdr, M.leaf64, L, P.f0, M.thr);
+  k_cell_table<DT><<<(32 * L0_CELLS + 127) / 128, 128, 0, st>>>(M.hdr, M.thr, P.f0, M.cleaf, M.cell);
   // heavy values
   const uint64_t tau = P.tau;
   k_heavy_flags<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, M.hdr, tau, W.flags, s);
@@ -779,6 +824,11 @@ cudaError_t train_enqueue(int dt, const void* keys, uint64_t n, const TrainPlan&
     case LS_U32: return train_dt<LS_U32>(keys, n, P, W, M, err, st, num_sms);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t sample_sort_u64_enqueue(uint64_t* a, uint64_t* b, uint64_t m, const SsWork& w,
+                                    uint32_t* err, cudaStream_t st, int num_sms) {
+  return ss_sort_enqueue(a, b, m, w, err, st, num_sms);
 }
 
 cudaError_t radix_sort_u64_enqueue(uint64_t* a, uint64_t* b, uint64_t m, const RsWork& w,

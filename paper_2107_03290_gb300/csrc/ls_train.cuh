@@ -15,6 +15,8 @@ struct TrainPlan {
   uint32_t hpb;      // heavy values per bucket (<= MAX_HPB)
 };
 
+constexpr int FIT_BLOCKS = 304;     // blocks of the root least-squares sums
+
 struct TrainWs {
   uint64_t* smp_a;           // s
   uint64_t* smp_b;           // s
@@ -25,19 +27,22 @@ struct TrainWs {
   uint64_t cand_cap;
   uint64_t* sel;             // f0 * hpb
   uint32_t* nh;              // f0
-  double* partials;          // 2 * FIT_BLOCKS
+  double* partials;          // 4 * FIT_BLOCKS
   uint32_t* ubase;           // L + 1 (first fit unit of each leaf)
   uint32_t* utotal;          // 1
   double* units;             // 4 * (s / 2048 + L + 1) unit partial sums
   unsigned long long* hi;    // 1
   void* scan_status;         // scan tiles * 8 + 16 bytes
   size_t scan_status_bytes;
-  RsWork rs;                 // radix-sort work area of the sample sort
+  SsWork ss;                 // work area of the sample sort (8-byte keys)
+  RsWork rs;                 // work area of the radix sort (4-byte keys)
 };
 
 cudaError_t train_enqueue(int dt, const void* keys, uint64_t n, const TrainPlan& P,
                           const TrainWs& W, const ModelPtrs& M, uint32_t* err, cudaStream_t st,
                           int num_sms);
+cudaError_t sample_sort_u64_enqueue(uint64_t* a, uint64_t* b, uint64_t m, const SsWork& w,
+                                    uint32_t* err, cudaStream_t st, int num_sms);
 cudaError_t radix_sort_u64_enqueue(uint64_t* a, uint64_t* b, uint64_t m, const RsWork& w,
                                    uint32_t* err, cudaStream_t st, int num_sms);
 

@@ -217,6 +217,33 @@ def test_radix_sort_u64(n):
         assert np.array_equal(t.cpu().numpy(), np.sort(a))
 
 
+@pytest.mark.parametrize("n", [2, 3, 100, 8191, 8192, 8193, 100_000, 2_000_000])
+def test_sample_sort_u64(n):
+    """The training sample's sample sort: random keys, few distinct values
+    (splitters repeat, their keys skip the sort), presorted and reversed runs."""
+    rng = np.random.default_rng(n + 1)
+    r = rng.integers(0, 2**63, n, dtype=np.uint64) * np.uint64(2) + np.uint64(1)
+    for a in (r, rng.integers(0, 300, n, dtype=np.uint64) << np.uint64(40), np.sort(r),
+              np.sort(r)[::-1].copy(), np.full(n, 2**64 - 1, dtype=np.uint64)):
+        t = torch.from_numpy(a.copy()).cuda()
+        ls.sample_sort_u64_(t)
+        assert np.array_equal(t.cpu().numpy(), np.sort(a))
+
+
+@pytest.mark.parametrize("n", [20_000, 300_001])
+def test_sample_sort_u64_oversized_gap(n):
+    """Oversample positions (i * n / 8192) hold widely spread keys and every
+    other position a small distinct key, so one gap holds almost every key:
+    the chunk-sort-and-merge path."""
+    rng = np.random.default_rng(n)
+    a = rng.permutation(np.arange(1, n + 1, dtype=np.uint64))
+    pos = (np.arange(8192, dtype=np.uint64) * np.uint64(n)) // np.uint64(8192)
+    a[pos.astype(np.int64)] = (np.arange(8192, dtype=np.uint64) + np.uint64(1)) << np.uint64(50)
+    t = torch.from_numpy(a.copy()).cuda()
+    ls.sample_sort_u64_(t)
+    assert np.array_equal(t.cpu().numpy(), np.sort(a))
+
+
 def test_empty_and_one():
     for dt in (torch.float64, torch.float32):
         for n in (0, 1):
