@@ -814,7 +814,7 @@ __device__ __forceinline__ void tile_walk_job(const L1Aux* aux, TileWalk& w) {
 
 // Total-order key range of every job of a range level (one atomic pair per tile).
 template <int DT>
-__global__ void __launch_bounds__(L1_THREADS)
+__global__ void __launch_bounds__(L1_THREADS, 4)
 k_l1_minmax(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, LevelArgs la,
             Level1Ws w) {
   typedef typename KT<DT>::U U;
@@ -851,7 +851,7 @@ k_l1_minmax(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, L
 }
 
 template <int DT>
-__global__ void __launch_bounds__(L1_THREADS)
+__global__ void __launch_bounds__(L1_THREADS, 4)
 k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, ModelPtrs M,
           LevelArgs la, Level1Ws w) {
   typedef typename KT<DT>::U U;
@@ -1110,7 +1110,7 @@ static cudaError_t level_dt(void* keys, void* scratch, uint64_t n, const ModelPt
   e = cudaMemsetAsync(w.scan_status, 0, w.scan_status_bytes, st);
   if (e) return e;
   k_l1_plan<<<1, 1024, 0, st>>>(la, lim, w, err);
-  const int grid = 2 * num_sms;
+  const int grid = 4 * num_sms;  // the histogram and range passes hold 4 CTAs per SM
   if (la.mode) k_l1_minmax<DT><<<grid, L1_THREADS, 0, st>>>((const U*)keys, (const U*)scratch, la, w);
   k_l1_hist<DT><<<grid, L1_THREADS, 0, st>>>((const U*)keys, (const U*)scratch, M, la, w);
   const unsigned tiles = (unsigned)std::max<uint64_t>(1, (w.cap_c + SC_TILE - 1) / SC_TILE);
