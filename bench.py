@@ -131,6 +131,20 @@ def traffic_for(kernel: str, workload: str):
     return e["bytes_per_launch"] if h == e["source_sha"] else None
 
 
+def replica_throughput(dev_ms: float, n: int, dist=None, device: str = "cuda"):
+    """Whole-job keys/s of independent replicas (one per rank, each sorting its
+    own n keys; nothing is exchanged): all ranks' keys over the slowest rank's
+    time.  Returns (keys/s, slowest ms)."""
+    import torch
+    tmax, world = dev_ms, 1
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        t = torch.tensor([dev_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmax = float(t.item())
+    return n * world / (tmax / 1000.0), tmax
+
+
 def make_workload(name: str, n: int):
     dt, n0, fn = lsgen.WORKLOADS[name]
     return dt, fn(n if n else n0)
@@ -387,12 +401,7 @@ def main():
         if dist:
             dist.barrier()
     dev_ms = float(np.mean([s["ms_total"] for s in per]))
-    tmax = dev_ms
-    if dist:
-        tt = torch.tensor([dev_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tmax = float(tt.item())
-    value = n * world / (tmax / 1000.0)
+    value, tmax = replica_throughput(dev_ms, n, dist, "cuda")
 
     # per-kernel times and the roofline of the dominant kernel
     ks = ["ms_train", "ms_hist", "ms_scan", "ms_scatter", "ms_classify", "ms_level1", "ms_fill",
