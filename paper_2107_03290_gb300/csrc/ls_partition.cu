@@ -82,24 +82,30 @@ static L0Layout l0_layout_hist(int W, uint32_t L, uint32_t f0, uint32_t next, ui
 
 // K4: double-buffered key and id tiles, per-bucket counters, offsets and
 // cursors, staging records.
-static L0Layout l0_layout_scatter(int W, uint32_t f0, uint32_t hmax) {
+static L0Layout l0_layout_scatter(int W, uint32_t f0, uint32_t hmax, int tile) {
   L0Layout y{};
   size_t o = 0;
   auto al = [&](size_t a) { o = (o + a - 1) / a * a; };
   (void)hmax;
   const size_t nc = f0;
   y.bar = (uint32_t)o; o += 16;
-  al(128); y.buf = (uint32_t)o; o += 2ull * P_TILE * W;
-  al(128); y.pbuf = (uint32_t)o; o += 2ull * P_TILE * 4;
+  al(128); y.buf = (uint32_t)o; o += 2ull * tile * W;
+  al(128); y.pbuf = (uint32_t)o; o += 2ull * tile * 4;
   y.ecnt = (uint32_t)o; o += nc * 4;
   y.soff = (uint32_t)o; o += (nc + 1) * 4;
   al(8); y.cursor = (uint32_t)o; o += nc * 8;
   y.gbase = (uint32_t)o; o += nc * 8;
-  y.sinfo = (uint32_t)o; o += (size_t)P_TILE * 2;
-  y.sid = (uint32_t)o; o += (size_t)P_TILE * 2;
+  y.sinfo = (uint32_t)o; o += (size_t)tile * 2;
+  y.sid = (uint32_t)o; o += (size_t)tile * 2;
   al(8); y.ws = (uint32_t)o; o += 33 * 8;
   y.total = (uint32_t)o;
   return y;
+}
+
+// K4's tile: P_TILE keys, or P_TILE_SMALL when the per-bucket arrays of a large
+// fan-out leave too little shared memory.
+static int scatter_tile(int W, uint32_t f0, uint32_t hmax) {
+  return l0_layout_scatter(W, f0, hmax, P_TILE).total <= L0_SMEM_LIMIT ? P_TILE : P_TILE_SMALL;
 }
 
 size_t level0_smem_hist(int dt, uint32_t L, uint32_t f0, uint32_t n_ext_max) {
@@ -107,7 +113,8 @@ size_t level0_smem_hist(int dt, uint32_t L, uint32_t f0, uint32_t n_ext_max) {
 }
 size_t level0_smem_scatter(int dt, uint32_t L, uint32_t f0, uint32_t n_ext_max) {
   (void)L;
-  return l0_layout_scatter(key_width(dt), f0, (n_ext_max - f0) / 2).total;
+  const uint32_t hmax = (n_ext_max - f0) / 2;
+  return l0_layout_scatter(key_width(dt), f0, hmax, scatter_tile(key_width(dt), f0, hmax)).total;
 }
 
 __device__ __forceinline__ void chunk_of(const Chunking& c, uint32_t g, uint64_t* b, uint64_t* e) {
@@ -266,6 +273,7 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
       }
     }
   };
+  uint32_t nq = 0;  // the warp's queued misses, carried from step to step
   for (uint64_t base = cb; base < ce; base += (uint64_t)H_THREADS * H_KPT) {
     U u[H_KPT];
 #pragma unroll
@@ -303,7 +311,6 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
       }
       continue;
     }
-    uint32_t nq = 0;
 #pragma unroll
     for (int k = 0; k < H_KPT; ++k) {
       const uint64_t i = base + (uint64_t)k * H_THREADS + threadIdx.x;
@@ -345,12 +352,12 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
         __syncwarp();
       }
     }
-    if (nq) {
-      __syncwarp();
-      const bool v = lane < nq;
-      finish(v, v ? qk[lane] : (U)0, cb + (v ? qi[lane] : 0u));
-      __syncwarp();
-    }
+  }
+  if (nq) {  // the last queued misses
+    __syncwarp();
+    const bool v = lane < nq;
+    finish(v, v ? qk[lane] : (U)0, cb + (v ? qi[lane] : 0u));
+    __syncwarp();
   }
   __syncthreads();
   if (compact) {  // pad to a multiple of 4 entries (equality marks)
@@ -374,10 +381,10 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
 // bucket-contiguously and written out so that consecutive threads write
 // consecutive addresses of a run; the level-1 ids follow their keys.
 // Equality keys are skipped (their slots are filled later).
-template <int DT>
+template <int DT, int TILE>
 __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Layout lay) {
   typedef typename KT<DT>::U U;
-  constexpr int KPT = P_TILE / P_THREADS;
+  constexpr int KPT = TILE / P_THREADS;
   extern __shared__ __align__(128) unsigned char sm[];
   uint64_t* bar = (uint64_t*)(sm + lay.bar);
   U* buf = (U*)(sm + lay.buf);
@@ -400,10 +407,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
   uint64_t cb, ce;
   chunk_of(a.c, g, &cb, &ce);
   if (a.may_compact && a.M.hdr->compact) ce = cb + min(ce - cb, a.ccount[g]);  // packed keys
-  const uint32_t nt = (uint32_t)((ce - cb + P_TILE - 1) / P_TILE);
+  const uint32_t nt = (uint32_t)((ce - cb + TILE - 1) / TILE);
   auto tcount = [&](uint32_t t) {
-    const uint64_t b = (uint64_t)t * P_TILE;
-    return (uint32_t)min((uint64_t)P_TILE, ce - cb - b);
+    const uint64_t b = (uint64_t)t * TILE;
+    return (uint32_t)min((uint64_t)TILE, ce - cb - b);
   };
   auto issue = [&](uint32_t t) {  // thread 0: keys and ids of tile t on one barrier
     if (t >= nt) return;
@@ -411,9 +418,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
     uint64_t* br = bar + (t & 1);
     fence_proxy_async();
     mbar_arrive_expect_tx(br, c * (uint32_t)(sizeof(U) + 4));
-    tma_load_1d_stream(buf + (size_t)(t & 1) * P_TILE, keys + cb + (size_t)t * P_TILE,
+    tma_load_1d_stream(buf + (size_t)(t & 1) * TILE, keys + cb + (size_t)t * TILE,
                        c * (uint32_t)sizeof(U), br);
-    tma_load_1d_stream(pbuf + (size_t)(t & 1) * P_TILE, a.pk + (cb - a0) + (size_t)t * P_TILE, c * 4u,
+    tma_load_1d_stream(pbuf + (size_t)(t & 1) * TILE, a.pk + (cb - a0) + (size_t)t * TILE, c * 4u,
                        br);
   };
   if (threadIdx.x == 0) { mbar_init(bar, 1); mbar_init(bar + 1, 1); fence_mbar_init(); }
@@ -450,8 +457,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
   __syncthreads();
   for (uint32_t t = 0; t < nt; ++t) {
     mbar_wait(bar + (t & 1), (t >> 1) & 1, a.err);
-    U* tb = buf + (size_t)(t & 1) * P_TILE;
-    const uint32_t* pb = pbuf + (size_t)(t & 1) * P_TILE;
+    U* tb = buf + (size_t)(t & 1) * TILE;
+    const uint32_t* pb = pbuf + (size_t)(t & 1) * TILE;
     const uint32_t cnt_t = tcount(t);
     U u[KPT];
     uint32_t pp[KPT], rk[KPT];
@@ -492,7 +499,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
       if (pp[k] == PK_EQ) continue;
       const uint32_t b = pp[k] & PK_B_MASK;
       const uint32_t s = soff[b] + rk[k];
-      if (s < (uint32_t)P_TILE) {
+      if (s < (uint32_t)TILE) {
         tb[s] = u[k];
         sinfo[s] = (uint16_t)b;
         sid[s] = (uint16_t)(pp[k] >> PK_B_BITS);
@@ -1049,7 +1056,8 @@ static cudaError_t level0_dt(const Level0Args& a, size_t sh, size_t ss, const Li
   const int W = KT<DT>::W;
   const uint32_t hmax = (a.n_ext_max - a.f0) / 2;
   const L0Layout lh = l0_layout_hist(W, a.L, a.f0, a.n_ext_max, hmax);
-  const L0Layout ls_ = l0_layout_scatter(W, a.f0, hmax);
+  const int tile = scatter_tile(W, a.f0, hmax);
+  const L0Layout ls_ = l0_layout_scatter(W, a.f0, hmax, tile);
   k_l0_hist<DT, false><<<a.c.G, H_THREADS, sh, st>>>(a, lh);
   if (lh.hkey != NOT_SHARED) k_l0_hist<DT, true><<<a.c.G, H_THREADS, sh, st>>>(a, lh);
   mark(mk, mb + 0, st);
@@ -1058,7 +1066,8 @@ static cudaError_t level0_dt(const Level0Args& a, size_t sh, size_t ss, const Li
       a.hist, a.offs, M, nullptr, (uint64_t*)a.scan_status,
       (uint32_t*)((uint64_t*)a.scan_status + a.scan_tiles), a.err);
   mark(mk, mb + 1, st);
-  k_l0_scatter<DT><<<a.c.G, P_THREADS, ss, st>>>(a, ls_);
+  if (tile == P_TILE) k_l0_scatter<DT, P_TILE><<<a.c.G, P_THREADS, ss, st>>>(a, ls_);
+  else k_l0_scatter<DT, P_TILE_SMALL><<<a.c.G, P_THREADS, ss, st>>>(a, ls_);
   mark(mk, mb + 2, st);
   k_classify0<DT><<<(a.n_ext_max + 255) / 256, 256, 0, st>>>(a, lists, lim);
   mark(mk, mb + 3, st);
@@ -1078,7 +1087,9 @@ cudaError_t level0_configure(int dt, size_t sh, size_t ss) {
   e = cudaFuncSetAttribute(k_l1_scatter<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
                            (int)l1_scatter_smem(KT<D>::W));                                     \
   if (e) return e;                                                                              \
-  e = cudaFuncSetAttribute(k_l0_scatter<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+  e = cudaFuncSetAttribute(k_l0_scatter<D, P_TILE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss); \
+  if (e) return e;                                                                              \
+  e = cudaFuncSetAttribute(k_l0_scatter<D, P_TILE_SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
   switch (dt) {
     case LS_F64: LS_CFG(LS_F64); break;
     case LS_U64: LS_CFG(LS_U64); break;

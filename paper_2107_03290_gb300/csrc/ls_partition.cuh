@@ -7,7 +7,8 @@ namespace ls {
 
 constexpr int P_THREADS = 1024;     // level-0 scatter CTAs
 constexpr int H_THREADS = 1024;     // level-0 histogram CTAs
-constexpr int P_TILE = 4096;        // keys per tile
+constexpr int P_TILE = 7168;        // keys per tile
+constexpr int P_TILE_SMALL = 4096;  // keys per tile when many buckets leave less shared memory
 constexpr int L1_THREADS = 512;
 constexpr int L1_TILE = 4096;
 constexpr uint64_t FILL_BIG = 1u << 15;   // fills this large are spread over the grid
