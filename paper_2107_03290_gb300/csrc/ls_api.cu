@@ -252,7 +252,7 @@ struct Workspace {
   void* base = nullptr;
   size_t bytes = 0;
   // offsets
-  size_t o_scratch, o_smp_a, o_smp_b, o_rank, o_flags, o_cpos, o_cand, o_sel, o_nh, o_part, o_hi,
+  size_t o_scratch, o_smp_a, o_smp_b, o_rank, o_flags, o_cpos, o_cand, o_sel, o_sellen, o_hlen, o_nh, o_part, o_hi,
       o_tscan, o_ss_spl, o_ss_words, o_rs_hist, o_rs_skip, o_rs_status, o_hdr, o_leaf64, o_thr, o_cell, o_cleaf, o_hkey, o_hval, o_heads, o_heavy,
       o_lbeg, o_lend, o_hist, o_offs, o_l0scan, o_jobs_fill, o_jobs_s, o_jobs_l, o_jobs_m, o_jobs_fb2, o_jobs_t, o_jobs_r,
       o_jobs_fb, o_jobs_r2, o_jobs_r3, o_pk, o_sid, o_ccount, o_counts, o_aux, o_tot, o_l1cnt, o_l1off, o_l1cur, o_jmin, o_jmax, o_l1scan,
@@ -273,6 +273,8 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->cand_cap = s / std::max<uint64_t>(1, P.tau) + 2;
   w->o_cand = c.take<uint8_t>(w->cand_cap * 24);
   w->o_sel = c.take<uint64_t>((size_t)P.f0 * std::max<uint32_t>(1, P.hpb));
+  w->o_sellen = c.take<uint32_t>((size_t)P.f0 * std::max<uint32_t>(1, P.hpb));
+  w->o_hlen = c.take<uint32_t>((size_t)P.f0 * std::max<uint32_t>(1, P.hpb));
   w->o_nh = c.take<uint32_t>(P.f0);
   w->o_part = c.take<double>(4 * FIT_BLOCKS);
   w->o_ubase = c.take<uint32_t>(P.L + 2);
@@ -366,6 +368,8 @@ static Bound bind(const Plan& P, const Workspace& w) {
   T.cand = at<void>(w, w.o_cand);
   T.cand_cap = w.cand_cap;
   T.sel = at<uint64_t>(w, w.o_sel);
+  T.sellen = at<uint32_t>(w, w.o_sellen);
+  T.hlen = at<uint32_t>(w, w.o_hlen);
   T.nh = at<uint32_t>(w, w.o_nh);
   T.partials = at<double>(w, w.o_part);
   T.ubase = at<uint32_t>(w, w.o_ubase);

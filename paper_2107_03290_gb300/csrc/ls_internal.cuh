@@ -100,10 +100,11 @@ struct HeavyEntry {    // a heavy value of one level-0 bucket
 };
 
 // Two-way set-associative table of the heavy values (total-order key ->
-// equality slot): a key's two candidate entries are one 16-byte set; empty
-// entries hold HASH_EMPTY.  A value whose set is full, and the value
-// HASH_EMPTY itself (a valid uint64 key), are not in the table: their keys
-// take the full lookup.
+// equality slot): a key's two candidate entries are one 16-byte set.  Built
+// with HASH_EMPTY marking free entries, which are then filled with a key that
+// hashes to another set, so a probe never matches a free entry.  A value whose
+// set is full, and the value HASH_EMPTY itself (a valid uint64 key), are not in
+// the table: their keys take the full lookup.
 constexpr uint32_t HASH_SET_BITS = 12;
 constexpr uint32_t HASH_SETS = 1u << HASH_SET_BITS;
 constexpr uint32_t HASH_SIZE = 2 * HASH_SETS;      // entries

@@ -614,7 +614,7 @@ constexpr int SEL_CAP = 1024;
 
 __global__ void __launch_bounds__(SEL_THREADS)
 k_heavy_select(const Cand* __restrict__ cand, const uint64_t* ncand_ptr, uint64_t cand_cap,
-               uint32_t f0, int hpb, uint64_t* sel, uint32_t* nh, DevModel* hdr) {
+               uint32_t f0, int hpb, uint64_t* sel, uint32_t* sellen, uint32_t* nh, DevModel* hdr) {
   __shared__ uint64_t s_tk[SEL_CAP], s_len[SEL_CAP];
   __shared__ uint64_t s_top[MAX_HPB], s_toplen[MAX_HPB];  // the selected, by place
   __shared__ uint64_t s_ab[2];
@@ -649,6 +649,7 @@ k_heavy_select(const Cand* __restrict__ cand, const uint64_t* ncand_ptr, uint64_
       uint32_t kr = 0;
       for (uint32_t q = 0; q < cnt; ++q) kr += s_top[q] < t ? 1u : 0u;
       sel[(size_t)b * hpb + kr] = t;
+      sellen[(size_t)b * hpb + kr] = (uint32_t)min(s_toplen[threadIdx.x], (uint64_t)0xFFFFFFFFu);
     }
     if (threadIdx.x == 0) {
       unsigned long long len = 0;
@@ -675,21 +676,26 @@ k_heavy_select(const Cand* __restrict__ cand, const uint64_t* ncand_ptr, uint64_
   unsigned long long len = 0;
   for (int i = 0; i < c; ++i) len += klen[i];
   if (len) atomicAdd(&hdr->heavy_len, len);
-  for (int i = 1; i < c; ++i) {  // order by key
-    const uint64_t t = ktk[i];
+  for (int i = 1; i < c; ++i) {  // order by key, lengths alongside
+    const uint64_t t = ktk[i], l = klen[i];
     int j = i;
-    while (j > 0 && ktk[j - 1] > t) { ktk[j] = ktk[j - 1]; --j; }
+    while (j > 0 && ktk[j - 1] > t) { ktk[j] = ktk[j - 1]; klen[j] = klen[j - 1]; --j; }
     ktk[j] = t;
+    klen[j] = l;
   }
-  for (int i = 0; i < c; ++i) sel[(size_t)b * hpb + i] = ktk[i];
+  for (int i = 0; i < c; ++i) {
+    sel[(size_t)b * hpb + i] = ktk[i];
+    sellen[(size_t)b * hpb + i] = (uint32_t)min(klen[i], (uint64_t)0xFFFFFFFFu);
+  }
   nh[b] = (uint32_t)c;
 }
 
 template <int DT>
 __global__ void __launch_bounds__(1024)
-k_heavy_heads(const uint64_t* __restrict__ sel, const uint32_t* __restrict__ nh, uint32_t f0,
-              int hpb, DevModel* hdr, const CellLeaf* __restrict__ cleaf, BucketHead* heads,
-              HeavyEntry* heavy) {
+k_heavy_heads(const uint64_t* __restrict__ sel, const uint32_t* __restrict__ sellen,
+              const uint32_t* __restrict__ nh, uint32_t f0, int hpb, DevModel* hdr,
+              const CellLeaf* __restrict__ cleaf, BucketHead* heads, HeavyEntry* heavy,
+              uint32_t* hlen) {
   __shared__ uint32_t ws[33];
   __shared__ uint32_t s_run;
   if (threadIdx.x == 0) s_run = 0;
@@ -712,6 +718,7 @@ k_heavy_heads(const uint64_t* __restrict__ sel, const uint32_t* __restrict__ nh,
         he.F = cell_F<DT>(KT<DT>::from_tk(he.tk), cr, cleaf);
         he.ext = h.ext_base + 2 * j + 1;
         heavy[hoff + j] = he;
+        hlen[hoff + j] = sellen[(size_t)b * hpb + j];
       }
     }
     __syncthreads();
@@ -731,25 +738,61 @@ k_heavy_heads(const uint64_t* __restrict__ sel, const uint32_t* __restrict__ nh,
   }
 }
 
-// Heavy table: one thread per heavy value claims one of the two entries of its
-// set with a compare-and-swap (hash_probes = 1 marks the table as built).
-__global__ void k_heavy_hash(DevModel* hdr, const HeavyEntry* __restrict__ heavy, uint64_t* hkey,
-                             uint16_t* hval) {
+// Heavy table, one CTA: a heavy value takes way r of its set when r values of
+// the same set are more frequent in the sample (longer run, ties: smaller key),
+// so a full set keeps its most frequent values, whatever the thread order.
+// Entries left free then get a key of another set (0, or 1 in set 0), so a
+// probe needs no emptiness test (hash_probes = 1 marks the table as built).
+__global__ void __launch_bounds__(1024)
+k_heavy_hash(DevModel* hdr, const HeavyEntry* __restrict__ heavy, const uint32_t* __restrict__ hlen,
+             uint64_t* hkey, uint16_t* hval) {
+  __shared__ uint32_t scnt[HASH_SETS];      // values per set, then fill cursors
+  __shared__ uint32_t soff[HASH_SETS + 1];  // first list position of each set
+  __shared__ uint16_t lst[HASH_SIZE / 2];   // heavy indices grouped by set
+  __shared__ uint32_t ws[33];
   const uint32_t H = hdr->nheavy;
   if (2 * H > HASH_SIZE) return;  // too full to help
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < H; i += gridDim.x * blockDim.x) {
+  for (uint32_t s = threadIdx.x; s < HASH_SETS; s += blockDim.x) scnt[s] = 0;
+  __syncthreads();
+  // (uint64 key 2^64-1 is left to the full lookup)
+  for (uint32_t i = threadIdx.x; i < H; i += blockDim.x)
+    if (heavy[i].tk != HASH_EMPTY) atomicAdd(&scnt[heavy_hash(heavy[i].tk)], 1u);
+  __syncthreads();
+  for (uint32_t s = threadIdx.x; s < HASH_SETS; s += blockDim.x) soff[s] = scnt[s];
+  __syncthreads();
+  block_scan_array<uint32_t>(soff, HASH_SETS, ws);
+  for (uint32_t s = threadIdx.x; s < HASH_SETS; s += blockDim.x) scnt[s] = 0;
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) {
     const uint64_t t = heavy[i].tk;
-    if (t == HASH_EMPTY) continue;  // (uint64 key 2^64-1): left to the full lookup
-    const uint32_t p = 2 * heavy_hash(t);
-    for (uint32_t w = 0; w < 2; ++w) {
-      const unsigned long long old = atomicCAS((unsigned long long*)&hkey[p + w], HASH_EMPTY, t);
-      if (old == HASH_EMPTY) {
-        hval[p + w] = (uint16_t)heavy[i].ext;
-        break;
-      }
+    if (t == HASH_EMPTY) continue;
+    const uint32_t set = heavy_hash(t);
+    lst[soff[set] + atomicAdd(&scnt[set], 1u)] = (uint16_t)i;
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) {
+    const uint64_t t = heavy[i].tk;
+    if (t == HASH_EMPTY) continue;
+    const uint32_t set = heavy_hash(t), len = hlen[i];
+    uint32_t r = 0;
+    for (uint32_t q = 0; q < scnt[set]; ++q) {
+      const uint32_t j = lst[soff[set] + q];
+      const uint64_t tj = heavy[j].tk;
+      const uint32_t lj = hlen[j];
+      r += (j != i && (lj > len || (lj == len && tj < t))) ? 1u : 0u;
+    }
+    if (r < 2) {
+      hkey[2 * set + r] = t;
+      hval[2 * set + r] = (uint16_t)heavy[i].ext;
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && H > 0) hdr->hash_probes = 1;
+  __syncthreads();
+  for (uint32_t p = threadIdx.x; p < HASH_SIZE; p += blockDim.x)
+    if (hkey[p] == HASH_EMPTY) {
+      hkey[p] = (p >> 1) == 0 ? 1ull : 0ull;  // heavy_hash(0) = 0, heavy_hash(1) != 0
+      hval[p] = 0xFFFFu;
+    }
+  if (threadIdx.x == 0 && H > 0) hdr->hash_probes = 1;
 }
 
 // ---------------------------------------------------------------- host enqueue
@@ -804,12 +847,12 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   k_heavy_compact<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, M.hdr, W.flags, W.cpos, M.thr,
                                                       M.cell, M.cleaf, (Cand*)W.cand, W.cand_cap);
   k_heavy_select<<<P.f0, SEL_THREADS, 0, st>>>((const Cand*)W.cand, W.cpos + s, W.cand_cap,
-                                                     P.f0, (int)P.hpb, W.sel, W.nh, M.hdr);
-  k_heavy_heads<DT><<<1, 1024, 0, st>>>(W.sel, W.nh, P.f0, (int)P.hpb, M.hdr, M.cleaf, M.heads,
-                                        M.heavy);
+                                                     P.f0, (int)P.hpb, W.sel, W.sellen, W.nh, M.hdr);
+  k_heavy_heads<DT><<<1, 1024, 0, st>>>(W.sel, W.sellen, W.nh, P.f0, (int)P.hpb, M.hdr, M.cleaf,
+                                        M.heads, M.heavy, W.hlen);
   e = cudaMemsetAsync(M.hkey, 0xFF, HASH_SIZE * sizeof(uint64_t), st);
   if (e) return e;
-  k_heavy_hash<<<(HASH_SIZE / 4 + 255) / 256, 256, 0, st>>>(M.hdr, M.heavy, M.hkey, M.hval);
+  k_heavy_hash<<<1, 1024, 0, st>>>(M.hdr, M.heavy, W.hlen, M.hkey, M.hval);
   add_launches(21);
   return cudaGetLastError();
 }

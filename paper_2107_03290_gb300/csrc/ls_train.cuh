@@ -25,7 +25,9 @@ struct TrainWs {
   uint64_t* cpos;            // s + 1
   void* cand;                // cand_cap * 24 bytes
   uint64_t cand_cap;
-  uint64_t* sel;             // f0 * hpb
+  uint64_t* sel;             // f0 * hpb selected heavy values, per bucket by key
+  uint32_t* sellen;          // f0 * hpb their sample run lengths
+  uint32_t* hlen;            // f0 * hpb run length of each heavy-list entry
   uint32_t* nh;              // f0
   double* partials;          // 4 * FIT_BLOCKS
   uint32_t* ubase;           // L + 1 (first fit unit of each leaf)
