@@ -781,6 +781,9 @@ k_l1_plan(LevelArgs la, SortLimits lim, Level1Ws w, uint32_t* err) {
     w.totals[1] = s_rc > w.cap_c ? w.cap_c : s_rc;
     w.totals[2] = nj;
   }
+  // the level's sub-bucket counters (only the ones its jobs use) start at zero
+  const uint64_t C = min((uint64_t)s_rc, w.cap_c);
+  for (uint64_t i = threadIdx.x; i < C; i += blockDim.x) w.cnt[i] = 0;
 }
 
 __device__ __forceinline__ uint64_t aux_find_tile(const L1Aux* aux, uint64_t nj, uint64_t t) {
@@ -1116,9 +1119,7 @@ static cudaError_t level_dt(void* keys, void* scratch, uint64_t n, const ModelPt
                             const Lists& lists, const LevelArgs& la, const SortLimits& lim,
                             const Level1Ws& w, uint32_t* err, cudaStream_t st, int num_sms) {
   typedef typename KT<DT>::U U;
-  cudaError_t e = cudaMemsetAsync(w.cnt, 0, w.cap_c * sizeof(uint32_t), st);
-  if (e) return e;
-  e = cudaMemsetAsync(w.scan_status, 0, w.scan_status_bytes, st);
+  cudaError_t e = cudaMemsetAsync(w.scan_status, 0, w.scan_status_bytes, st);
   if (e) return e;
   k_l1_plan<<<1, 1024, 0, st>>>(la, lim, w, err);
   const int grid = 4 * num_sms;  // the histogram and range passes hold 4 CTAs per SM
