@@ -46,7 +46,7 @@ static uint32_t heavy_stride(uint32_t f0, uint32_t next) {
 // shared copy would not fit.
 constexpr size_t L0_SMEM_LIMIT = 227 * 1024;
 constexpr uint32_t NOT_SHARED = 0xFFFFFFFFu;
-constexpr int H_KPT = 8;             // keys per thread and step of K2
+constexpr int H_KPT = 4;             // keys per thread and step of K2
 
 // K2: the lookup tables and the extended-slot counters.
 static int key_width(int dt) { return (dt == LS_F64 || dt == LS_U64) ? 8 : 4; }
@@ -210,7 +210,10 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
   uint32_t* cnt = (uint32_t*)(sm + lay.cnt);
   uint64_t* heavy = (uint64_t*)(sm + lay.htk);
   const U* keys = (const U*)a.keys;
-  U* keys_w = (U*)a.keys;  // compaction target (the caller's array is sorted in place)
+  // compaction target: scratch, indexed like the ids (body-relative, so that every
+  // chunk starts 16-byte aligned whatever the caller's pointer; head and tail
+  // after the body)
+  U* keys_w = (U*)a.scratch;
   uint32_t* pk = a.pk;
   const uint32_t next = min(a.M.hdr->n_ext, a.n_ext_max);
   const uint32_t H = min(a.M.hdr->nheavy, (next - a.f0) / 2);
@@ -222,25 +225,25 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
   chunk_of(a.c, g, &cb, &ce);
   const L0Map q = load_tables(a, sm, lay, H);
   for (uint32_t i = threadIdx.x; i < next; i += H_THREADS) cnt[i] = 0;
+  // Compaction (equality keys dominate): the chunk's non-equality keys and
+  // their ids are packed to the front of the chunk's range of scratch, so that
+  // K4 reads only those (and writes its buckets back into the caller's array).
+  const bool compact = a.may_compact && a.M.hdr->compact != 0;
+  uint32_t* s_cpos = (uint32_t*)(sm + lay.ws);  // chunk lengths < 2^32
+  if (threadIdx.x == 0) *s_cpos = 0;
   __syncthreads();
   if (g == 0) {  // unaligned head and tail: ids after the body
     const uint64_t nht = a0 + (a.c.n - a.c.a1);
     for (uint64_t k = threadIdx.x; k < nht; k += H_THREADS) {
       const uint64_t i = k < a0 ? k : a.c.a1 + (k - a0);
       uint32_t p;
-      const uint32_t e = classify_key<DT>(keys[i], q, heads, heavy, lay.hs, a.f0kf, a.kf, &p);
+      const U x = keys[i];
+      const uint32_t e = classify_key<DT>(x, q, heads, heavy, lay.hs, a.f0kf, a.kf, &p);
       if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
       pk[nb + k] = p;
+      if (compact) keys_w[nb + k] = x;  // K4 reads every key from scratch
     }
   }
-  // Compaction (equality keys dominate): the chunk's non-equality keys and
-  // their ids are packed to the front of the chunk, in place, so that K4
-  // reads only those.  Every thread loads its keys of a step before the
-  // step's barrier and writes after it, and a step's writes stay below the
-  // step's end, so no key is overwritten before it is read.
-  const bool compact = a.may_compact && a.M.hdr->compact != 0;
-  uint32_t* s_cpos = (uint32_t*)(sm + lay.ws);  // chunk lengths < 2^32
-  if (threadIdx.x == 0) *s_cpos = 0;
   const int lane = threadIdx.x & 31;
   // Heavy table path: a key equal to a heavy value is counted from one table
   // probe; the others queue per warp (QCAP entries) and take the full lookup
@@ -268,7 +271,7 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
       wb = __shfl_sync(0xffffffffu, wb, 0);
       if (keep) {
         const uint64_t r = wb + __popc(m & lt);
-        keys_w[cb + r] = x;
+        keys_w[cb - a0 + r] = x;
         pk[cb - a0 + r] = pv;
       }
     }
@@ -281,7 +284,6 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
       const uint64_t i = base + (uint64_t)k * H_THREADS + threadIdx.x;
       u[k] = i < ce ? keys[i] : (U)0;
     }
-    if (compact) __syncthreads();
     if (!HASHED) {  // every key takes the full lookup; the chains interleave
       uint32_t pp[H_KPT];
 #pragma unroll
@@ -304,7 +306,7 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
           wb = __shfl_sync(0xffffffffu, wb, 0);
           if (keep) {
             const uint64_t r = wb + __popc(m & lt);
-            keys_w[cb + r] = u[k];
+            keys_w[cb - a0 + r] = u[k];
             pk[cb - a0 + r] = pp[k];
           }
         }
@@ -396,8 +398,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
   uint16_t* sinfo = (uint16_t*)(sm + lay.sinfo);   // staged keys' buckets
   uint16_t* sid = (uint16_t*)(sm + lay.sid);       // staged level-1 ids
   uint32_t* ws = (uint32_t*)(sm + lay.ws);
+  // input: the caller's array, or scratch where K2 compacted the chunks
+  const bool compact = a.may_compact && a.M.hdr->compact;
   const U* keys = (const U*)a.keys;
-  U* out = (U*)a.scratch;
+  U* out = (U*)(compact ? a.keys : a.scratch);
   uint16_t* oid = a.sid;
   const uint64_t n = a.c.n;
   const uint32_t next = min(a.M.hdr->n_ext, a.n_ext_max);
@@ -406,7 +410,9 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
   const uint64_t a0 = a.c.a0, nb = a.c.a1 - a.c.a0;
   uint64_t cb, ce;
   chunk_of(a.c, g, &cb, &ce);
-  if (a.may_compact && a.M.hdr->compact) ce = cb + min(ce - cb, a.ccount[g]);  // packed keys
+  if (compact) ce = cb + min(ce - cb, a.ccount[g]);  // packed keys
+  // the body's first key: in the caller's array, or body-relative in scratch
+  const U* body = compact ? (const U*)a.scratch : keys + a0;
   const uint32_t nt = (uint32_t)((ce - cb + TILE - 1) / TILE);
   auto tcount = [&](uint32_t t) {
     const uint64_t b = (uint64_t)t * TILE;
@@ -418,7 +424,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
     uint64_t* br = bar + (t & 1);
     fence_proxy_async();
     mbar_arrive_expect_tx(br, c * (uint32_t)(sizeof(U) + 4));
-    tma_load_1d_stream(buf + (size_t)(t & 1) * TILE, keys + cb + (size_t)t * TILE,
+    tma_load_1d_stream(buf + (size_t)(t & 1) * TILE, body + (cb - a0) + (size_t)t * TILE,
                        c * (uint32_t)sizeof(U), br);
     tma_load_1d_stream(pbuf + (size_t)(t & 1) * TILE, a.pk + (cb - a0) + (size_t)t * TILE, c * 4u,
                        br);
@@ -450,7 +456,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
       const uint32_t b = p & PK_B_MASK;
       if (b >= nc) { set_error(a.err, ERR_BOUNDS); continue; }
       const uint64_t dst = cursor[b]++;
-      if (dst < n) { out[dst] = keys[i]; oid[dst] = (uint16_t)(p >> PK_B_BITS); }
+      const U x = compact ? ((const U*)a.scratch)[nb + k] : keys[i];
+      if (dst < n) { out[dst] = x; oid[dst] = (uint16_t)(p >> PK_B_BITS); }
       else set_error(a.err, ERR_BOUNDS);
     }
   }
@@ -541,7 +548,7 @@ __global__ void k_classify0(Level0Args a, Lists lists, SortLimits lim) {
     const uint32_t o = e - h.ext_base, nh = h.hoff_nh & 15u, hoff = h.hoff_nh >> 4;
     Job job;
     job.value = 0;
-    job.src = 1;
+    job.src = (a.may_compact && a.M.hdr->compact) ? 0u : 1u;  // where K4 put the keys
     job.pad = 0;
     job.kb = job.sb = 0;
     job.la = b;

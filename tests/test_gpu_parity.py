@@ -131,10 +131,12 @@ def test_sort_params(dist, cfg):
     assert_same(gpu_sort(keys, ls.default_params(**cfg)), keys)
 
 
-@pytest.mark.parametrize("dist", ["normal", "exponential_f32", "timestamp_u32", "uniform_u64"])
+@pytest.mark.parametrize("dist", ["normal", "exponential_f32", "timestamp_u32", "uniform_u64",
+                                  "zipf_lognormal"])
 @pytest.mark.parametrize("mis", [1, 2, 3])
 def test_sort_misaligned(dist, mis):
-    """Unaligned starts exercise the TMA head/tail path (bulk copies need 16 B)."""
+    """Unaligned starts exercise the TMA head/tail path (bulk copies need 16 B);
+    zipf_lognormal also takes the compaction of the non-equality keys."""
     for n in (5, 4099, 200_003):
         keys = make(dist, n)
         assert_same(gpu_sort(keys, misalign=mis), keys)
