@@ -46,7 +46,7 @@ static uint32_t heavy_stride(uint32_t f0, uint32_t next) {
 // shared copy would not fit.
 constexpr size_t L0_SMEM_LIMIT = 227 * 1024;
 constexpr uint32_t NOT_SHARED = 0xFFFFFFFFu;
-constexpr int H_KPT = 4;             // keys per thread and step of K2
+constexpr int H_KPT = 6;             // keys per thread and step of K2
 
 // K2: the lookup tables and the extended-slot counters.
 static int key_width(int dt) { return (dt == LS_F64 || dt == LS_U64) ? 8 : 4; }
