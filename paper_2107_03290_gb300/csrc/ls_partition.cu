@@ -8,17 +8,21 @@
 //   K2 k_l0_hist     evaluates the model once per key: its extended slot
 //                    (bucket, or an equality slot of a heavy value) counted in
 //                    a per-CTA shared-memory histogram, and a packed id
-//                    (compact slot | level-1 sub-bucket) stored for the scatter;
+//                    (bucket | level-1 id) stored for the scatter; when
+//                    equality keys dominate, the other keys and their ids are
+//                    packed into scratch;
 //   K3 k_scan        decoupled look-back exclusive scan of the histograms,
 //                    giving every (slot, CTA) its write head;
 //   K4 k_l0_scatter  streams key and id tiles by TMA into shared memory, ranks
-//                    keys by slot inside the tile, stages them slot-contiguously
-//                    and writes full runs (keys and level-1 ids) to scratch;
+//                    keys by bucket inside the tile, stages them
+//                    bucket-contiguously and writes full runs (keys and
+//                    level-1 ids) to the other buffer;
 //   k_classify0      turns slots into jobs (equality fill, in-bucket sort,
 //                    level-1 re-partition).
 // Level 1 (Alg. 2's re-partition of each bucket into sub-buckets) uses the
 // sub-bucket ids from K2: sub = clamp(floor(F(x) * f0 * Kf) - b * Kf, 0, Kf-1),
-// the paper's level-1 position with Kf sub-buckets per bucket.
+// the paper's level-1 position with Kf sub-buckets per bucket, offset by the
+// key's interval between the bucket's heavy values.
 #include <cfloat>
 
 #include "ls_partition.cuh"

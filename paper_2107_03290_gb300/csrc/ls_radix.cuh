@@ -1,7 +1,8 @@
-// LSD radix sort of 64-bit total-order keys (8-bit digits).  Sorts the RMI
-// training sample (Sec. 5.1: the model is trained on a 1% sample, which must be
-// in key order to give each sample key its eCDF rank) and, one CTA per
-// segment, the rare oversized segments that the model cannot split.
+// LSD radix sort of 64-bit total-order keys (8-bit digits; a digit that every
+// key shares is skipped).  Sorts the training sample of 4-byte keys (Sec. 5.1:
+// the model is trained on a 1% sample, which must be in key order to give each
+// sample key its eCDF rank; their total-order keys leave four high digits
+// constant) and serves ls_radix_sort_u64.
 //
 // Tile ranking is stable: warp w owns a contiguous run of the tile and walks it
 // in order, keeping a private digit histogram; warps are then combined in warp

@@ -3,7 +3,8 @@
 // that feeds the equality buckets.
 //
 //  1. gather s keys at stratified offsets, as total-order keys;
-//  2. LSD radix sort of the sample (ls_radix.cuh);
+//  2. sort of the sample: sample sort for 8-byte keys (ls_samplesort.cuh), LSD
+//     radix sort for 4-byte keys (ls_radix.cuh);
 //  3. FP64 least squares: root over all finite sample keys against their eCDF
 //     rank (count of sample keys below x, ties take the first rank), then one
 //     line per leaf over the keys the root routes to it; slopes clamped to >= 0
