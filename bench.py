@@ -227,7 +227,7 @@ def run_batched(ls, torch, count: int, steps: int, warmup: int, with_loop: bool 
 
 
 def run_serving(ls, torch, rates, seconds: float, pool_size: int = 64,
-                budget_bytes: int = 120 << 30, client_bytes: int = 48 << 30):
+                budget_bytes: int = 120 << 30, client_bytes: int = 48 << 30, streams: int = 8):
     """Serving workload: Poisson arrivals of sort requests (each copies one
     device-resident pool array into its own buffer on the server's stream,
     outside the device time), admission by an HBM budget; reports p50/p99 of
@@ -242,7 +242,7 @@ def run_serving(ls, torch, rates, seconds: float, pool_size: int = 64,
         n_req = max(1, int(rate * seconds))
         gaps = rng.exponential(1.0 / rate, n_req)
         picks = rng.integers(0, pool_size, n_req)
-        srv = ls.Server(hbm_budget_bytes=budget_bytes, max_inflight=64, streams=4)
+        srv = ls.Server(hbm_budget_bytes=budget_bytes, max_inflight=64, streams=streams)
         lat, done_t = [], []
         outstanding = []
         cv = threading.Condition()

@@ -196,7 +196,7 @@ typedef struct ls_server_config {
   uint64_t hbm_budget_bytes; /* admission limit on bytes of admitted requests  */
   uint32_t max_inflight;     /* requests on the GPU at once (default 64)       */
   uint32_t max_queue;        /* waiting requests before LS_ERR_BUSY (def 4096) */
-  uint32_t streams;          /* CUDA streams used for overlap (default 4)      */
+  uint32_t streams;          /* CUDA streams used for overlap (default 8)      */
   uint32_t reserved[5];
 } ls_server_config;
 

@@ -358,7 +358,7 @@ class Server:
     """Continuous-batching sort server (ls_server_*)."""
 
     def __init__(self, hbm_budget_bytes: int = 120 << 30, max_inflight: int = 64,
-                 max_queue: int = 4096, streams: int = 4):
+                 max_queue: int = 4096, streams: int = 8):
         cfg = ServerConfig(hbm_budget_bytes, max_inflight, max_queue, streams)
         self._h = ctypes.c_void_p()
         _check(load().ls_server_create(ctypes.byref(cfg), ctypes.byref(self._h)),

@@ -22,11 +22,16 @@
 
 #include "../../include/ls.h"
 
+namespace ls {
+cudaError_t status_word_ptr(uint32_t** out);  // the device's asynchronous error word
+constexpr uint32_t ERR_TIMEOUT_BIT = 1u, ERR_BOUNDS_BIT = 2u;
+}
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
 
-constexpr size_t SERVER_BATCH_MAX = size_t(1) << 22;  // requests this small are batched
+constexpr size_t SERVER_BATCH_MAX = size_t(1) << 24;  // requests this small are batched
 
 struct Request {
   uint64_t ticket;
@@ -38,6 +43,7 @@ struct Request {
   Clock::time_point t_submit, t_launch, t_done;
   cudaEvent_t ev_start = nullptr, ev_end = nullptr;
   int stream = -1;
+  int slot = -1;          // pinned word that receives the device status after the sort
   bool done = false;
   ls_request_stats st{};
 };
@@ -56,6 +62,9 @@ struct ls_server {
   uint64_t next_ticket = 1;
   uint64_t inflight_bytes = 0;
   uint32_t rr = 0;
+  uint32_t* dev_err = nullptr;       // device error word
+  uint32_t* hstat = nullptr;         // pinned, max_inflight words
+  std::vector<int> free_slots;
   bool stop = false;
   std::thread th;
 };
@@ -79,7 +88,13 @@ static void dispatcher(ls_server* s) {
         r->st.device_ms = ms;
         r->st.queue_ms = std::chrono::duration<double, std::milli>(r->t_launch - r->t_submit).count();
         r->st.total_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
-        r->st.status = ls_stream_status(s->streams[r->stream]);
+        // device status copied behind the sort (no stream synchronization)
+        if (r->st.status == LS_OK && r->slot >= 0) {
+          const uint32_t w = s->hstat[r->slot];
+          r->st.status = (w & ls::ERR_TIMEOUT_BIT) ? LS_ERR_TIMEOUT
+                         : ((w & ls::ERR_BOUNDS_BIT) ? LS_ERR_CUDA : LS_OK);
+        }
+        if (r->slot >= 0) s->free_slots.push_back(r->slot);
         r->done = true;
         s->inflight_bytes -= r->bytes;
         s->inflight[i] = s->inflight.back();
@@ -96,9 +111,14 @@ static void dispatcher(ls_server* s) {
       Request* r = s->queue.front();
       s->queue.pop_front();
       s->inflight_bytes += r->bytes;
+      r->slot = s->free_slots.back();  // max_inflight slots for max_inflight requests
+      s->free_slots.pop_back();
       adm.push_back(r);
     }
     if (!adm.empty()) {
+      // the admitted requests belong to this thread now: launch them without
+      // holding the lock, so that submit() and wait() are not held up
+      lk.unlock();
       const auto now = Clock::now();
       auto prologue = [&](Request* r, cudaStream_t st, int si) {
         r->stream = si;
@@ -120,6 +140,7 @@ static void dispatcher(ls_server* s) {
         for (Request* r : grp) { prologue(r, st, si); ptrs.push_back(r->keys); ns.push_back(r->n); }
         const ls_status rc = ls_sort_batch(ptrs.data(), ns.data(), grp.size(), (ls_dtype)dt, st);
         for (Request* r : grp) {
+          cudaMemcpyAsync(&s->hstat[r->slot], s->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
           cudaEventRecord(r->ev_end, st);
           if (rc != LS_OK) r->st.status = rc;
         }
@@ -130,9 +151,11 @@ static void dispatcher(ls_server* s) {
         cudaStream_t st = s->streams[si];
         prologue(r, st, si);
         const ls_status rc = ls_sort(r->keys, r->n, r->dt, st);
+        cudaMemcpyAsync(&s->hstat[r->slot], s->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
         cudaEventRecord(r->ev_end, st);
         if (rc != LS_OK) r->st.status = rc;
       }
+      lk.lock();
       for (Request* r : adm) s->inflight.push_back(r);
     }
     if (s->stop && s->queue.empty() && s->inflight.empty()) break;
@@ -155,12 +178,20 @@ ls_status ls_server_create(const ls_server_config* cfg, ls_server** out) {
   if (!s->cfg.hbm_budget_bytes) s->cfg.hbm_budget_bytes = 120ull << 30;
   if (!s->cfg.max_inflight) s->cfg.max_inflight = 64;
   if (!s->cfg.max_queue) s->cfg.max_queue = 4096;
-  if (!s->cfg.streams) s->cfg.streams = 4;
+  if (!s->cfg.streams) s->cfg.streams = 8;
   if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return LS_ERR_CUDA; }
+  if (ls::status_word_ptr(&s->dev_err) != cudaSuccess ||
+      cudaHostAlloc((void**)&s->hstat, s->cfg.max_inflight * sizeof(uint32_t), cudaHostAllocDefault) != cudaSuccess) {
+    delete s;
+    return LS_ERR_CUDA;
+  }
+  std::memset(s->hstat, 0, s->cfg.max_inflight * sizeof(uint32_t));
+  for (int i = (int)s->cfg.max_inflight - 1; i >= 0; --i) s->free_slots.push_back(i);
   for (uint32_t i = 0; i < s->cfg.streams; ++i) {
     cudaStream_t st;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
       for (auto x : s->streams) cudaStreamDestroy(x);
+      cudaFreeHost(s->hstat);
       delete s;
       return LS_ERR_CUDA;
     }
@@ -231,6 +262,7 @@ ls_status ls_server_destroy(ls_server* s) {
     delete kv.second;
   }
   for (auto x : s->streams) cudaStreamDestroy(x);
+  if (s->hstat) cudaFreeHost(s->hstat);
   delete s;
   return LS_OK;
 }

@@ -336,7 +336,8 @@ def test_server_batched_mix_from_sources():
     (large ones through the full sort); inputs copied on the server's stream."""
     specs = [("normal", 1_000), ("zipf_lognormal", 300_000), ("uniform_u64", 50_000),
              ("exponential_f32", 20_000), ("normal", 4_500_000), ("two_values", 9_000),
-             ("uniform_u64", 2_000_000), ("timestamp_u32", 100_000), ("gauss_mix", 123_457)]
+             ("uniform_u64", 2_000_000), ("timestamp_u32", 100_000), ("gauss_mix", 123_457),
+             ("normal", 17_000_000)]  # above the batching limit (2^24 keys): the full sort
     arrays = [make(d, n) for d, n in specs]
     srcs = [torch.from_numpy(a).cuda() for a in arrays]
     dsts = [torch.empty_like(x) for x in srcs]
