@@ -894,25 +894,36 @@ k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Mod
     if (la.mode) rs = range_split<DT>(w.jmin[j], w.jmax[j], x.f1, la.mode == 2);
     for (uint32_t s = threadIdx.x; s < x.f1; s += blockDim.x) hc[s] = 0;
     __syncthreads();
-    constexpr int U8 = 8;  // independent loads in flight per thread
-    for (uint32_t base = 0; base < c; base += blockDim.x * U8) {
-      uint32_t sub[U8];
-      if (la.mode) {
+    if (la.mode) {
+      constexpr int U8 = 8;  // independent loads in flight per thread
+      for (uint32_t base = 0; base < c; base += blockDim.x * U8) {
+        uint32_t sub[U8];
 #pragma unroll
         for (int k = 0; k < U8; ++k) {
           const uint32_t i = base + k * blockDim.x + threadIdx.x;
           sub[k] = i < c ? range_sub<DT>(src[i], rs) : 0xFFFFFFFFu;
         }
-      } else {
 #pragma unroll
-        for (int k = 0; k < U8; ++k) {
-          const uint32_t i = base + k * blockDim.x + threadIdx.x;
-          sub[k] = i < c ? min((uint32_t)ids[i], x.f1 - 1) : 0xFFFFFFFFu;
+        for (int k = 0; k < U8; ++k)
+          if (sub[k] != 0xFFFFFFFFu) atomicAdd(&hc[sub[k]], 1u);
+      }
+    } else {  // the ids: 8 per 16-byte load over the tile's aligned body
+      const uint32_t f1m = x.f1 - 1;
+      const uint32_t h = min(c, (uint32_t)(((16 - ((uintptr_t)ids & 15)) & 15) >> 1));
+      const uint32_t nv = (c - h) >> 3;
+      const uint4* v = (const uint4*)(ids + h);
+      for (uint32_t q = threadIdx.x; q < nv; q += blockDim.x) {
+        const uint4 x4 = v[q];
+        const uint32_t wv[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          atomicAdd(&hc[min(wv[r] & 0xFFFFu, f1m)], 1u);
+          atomicAdd(&hc[min(wv[r] >> 16, f1m)], 1u);
         }
       }
-#pragma unroll
-      for (int k = 0; k < U8; ++k)
-        if (sub[k] != 0xFFFFFFFFu) atomicAdd(&hc[sub[k]], 1u);
+      const uint32_t t0 = h + (nv << 3), ne = h + (c - t0);  // head, then tail
+      for (uint32_t i = threadIdx.x; i < ne; i += blockDim.x)
+        atomicAdd(&hc[min((uint32_t)ids[i < h ? i : t0 + (i - h)], f1m)], 1u);
     }
     __syncthreads();
     for (uint32_t s = threadIdx.x; s < x.f1; s += blockDim.x)
