@@ -261,6 +261,9 @@ struct Workspace {
   uint64_t cand_cap;
 };
 
+// Jobs of more than `m` keys cover disjoint key ranges: at most n / (m + 1) of them.
+static uint64_t cap_above(uint64_t n, uint64_t m) { return n / (m + 1) + 16; }
+
 static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   Carver c;
   const uint64_t s = P.s;
@@ -306,13 +309,13 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->l0scan_bytes = (size_t)P.l0_scan_tiles * 8 + 16;
   w->o_l0scan = c.take<uint8_t>(w->l0scan_bytes);
   w->o_jobs_fill = c.take<Job>(P.cap1);
-  w->o_jobs_s = c.take<Job>(P.cap1);
-  w->o_jobs_l = c.take<Job>(P.cap1);
-  w->o_jobs_m = c.take<Job>(P.cap1);
-  w->o_jobs_fb2 = c.take<Job>(P.cap1);
+  w->o_jobs_s = c.take<Job>(cap_above(P.n, P.lim.c_tiny));
+  w->o_jobs_l = c.take<Job>(cap_above(P.n, P.lim.c_mid));
+  w->o_jobs_m = c.take<Job>(cap_above(P.n, P.lim.c_small));
+  w->o_jobs_fb2 = c.take<Job>(cap_above(P.n, FILL_BIG - 1));
   w->o_jobs_t = c.take<Job>(P.cap1);
   w->o_jobs_r = c.take<Job>(P.cap0);
-  w->o_jobs_fb = c.take<Job>(P.cap1);
+  w->o_jobs_fb = c.take<Job>(cap_above(P.n, P.lim.c_large));
   w->o_pk = c.take<uint32_t>(with_scratch ? P.n + 16 : 0);
   w->o_ccount = c.take<uint64_t>(P.c.G + 1);
   w->o_sid = c.take<uint16_t>(with_scratch ? P.n + 16 : 0);
@@ -395,13 +398,13 @@ static Bound bind(const Plan& P, const Workspace& w) {
     return l;
   };
   b.lists.fill = mk(w.o_jobs_fill, b.counts + 0, P.cap1);
-  b.lists.sort_s = mk(w.o_jobs_s, b.counts + 1, P.cap1);
-  b.lists.sort_l = mk(w.o_jobs_l, b.counts + 2, P.cap1);
-  b.lists.sort_m = mk(w.o_jobs_m, b.counts + 7, P.cap1);
-  b.lists.fill_big = mk(w.o_jobs_fb2, b.counts + 12, P.cap1);
+  b.lists.sort_s = mk(w.o_jobs_s, b.counts + 1, cap_above(P.n, P.lim.c_tiny));
+  b.lists.sort_l = mk(w.o_jobs_l, b.counts + 2, cap_above(P.n, P.lim.c_mid));
+  b.lists.sort_m = mk(w.o_jobs_m, b.counts + 7, cap_above(P.n, P.lim.c_small));
+  b.lists.fill_big = mk(w.o_jobs_fb2, b.counts + 12, cap_above(P.n, FILL_BIG - 1));
   b.lists.sort_t = mk(w.o_jobs_t, b.counts + 13, P.cap1);
   b.lists.refine = mk(w.o_jobs_r, b.counts + 3, P.cap0);
-  b.lists.fallback = mk(w.o_jobs_fb, b.counts + 4, P.cap1);
+  b.lists.fallback = mk(w.o_jobs_fb, b.counts + 4, cap_above(P.n, P.lim.c_large));
   b.lists.refine2 = mk(w.o_jobs_r2, b.counts + 5, P.cap_r);
   b.lists.refine3 = mk(w.o_jobs_r3, b.counts + 6, P.cap_r);
   Level1Ws& l = b.l1;
@@ -570,9 +573,10 @@ static void fill_stats(const Plan& P, const Workspace& w, Events* ev, ls_stats* 
     }
     return sum;
   };
-  stats->n_fallback_keys = job_keys(w.o_jobs_fb, counts[4], P.cap1, &stats->max_fallback);
-  stats->n_large_keys = job_keys(w.o_jobs_l, counts[2], P.cap1, nullptr) +
-                        job_keys(w.o_jobs_m, counts[7], P.cap1, nullptr);
+  stats->n_fallback_keys = job_keys(w.o_jobs_fb, counts[4], cap_above(P.n, P.lim.c_large),
+                                    &stats->max_fallback);
+  stats->n_large_keys = job_keys(w.o_jobs_l, counts[2], cap_above(P.n, P.lim.c_mid), nullptr) +
+                        job_keys(w.o_jobs_m, counts[7], cap_above(P.n, P.lim.c_small), nullptr);
 }
 
 }  // namespace ls
