@@ -70,3 +70,47 @@ def test_sort_u32_past_2_32_keys():
         after = _signature(u)
         assert before[0] == after[0], dist
         assert np.array_equal(before[1], after[1]), dist
+
+
+def test_sort_f64_past_2_32_keys_zipf():
+    """2^32 + 12,345 f64 keys drawn with Zipf(1.1) weights from 100,000
+    lognormal values: the heavy-value table, compaction into scratch and the
+    sample sort of the 43M-key training sample at full scale."""
+    n = (1 << 32) + 12_345
+    free, _ = torch.cuda.mem_get_info()
+    if free < 160 << 30:  # keys 34 GB, workspace about 80 GB
+        pytest.skip("needs about 160 GB of free device memory")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    k = 100_000
+    vals = torch.exp(2.0 * torch.randn(k, dtype=torch.float64, device="cuda", generator=g))
+    w = torch.arange(1, k + 1, dtype=torch.float64, device="cuda") ** -1.1
+    cdf = torch.cumsum(w / w.sum(), 0)
+    t = torch.empty(n, dtype=torch.float64, device="cuda")
+    for a in range(0, n, CH):
+        m = min(CH, n - a)
+        r = torch.rand(m, dtype=torch.float64, device="cuda", generator=g)
+        t[a:a + m] = vals[torch.searchsorted(cdf, r).clamp_(max=k - 1)]
+    bits = t.view(torch.int64)
+
+    def signature():
+        s, h = 0, torch.zeros(4096, dtype=torch.int64, device="cuda")
+        for a in range(0, n, CH):
+            v = bits[a:a + CH]
+            s = (s + int(v.sum().item())) & ((1 << 64) - 1)  # exact modulo 2^64
+            h += torch.bincount((v >> 52) & 4095, minlength=4096)
+        return s, h.cpu().numpy()
+
+    before = signature()
+    ls.sort_(t)
+    torch.cuda.synchronize()
+    assert ls.stream_status() == 0
+    prev = None
+    for a in range(0, n, CH):  # non-decreasing (positive finite values)
+        v = t[a:a + CH]
+        assert bool(torch.all(v[1:] >= v[:-1]).item())
+        assert prev is None or float(v[0].item()) >= prev
+        prev = float(v[-1].item())
+    after = signature()
+    assert before[0] == after[0]
+    assert np.array_equal(before[1], after[1])
