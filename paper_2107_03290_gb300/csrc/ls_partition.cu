@@ -625,7 +625,7 @@ __device__ __forceinline__ void fill_range(U* dst, uint64_t m, U v, uint64_t tid
 // CTA scans for itself), so the stores spread evenly over the grid whatever
 // the mix of job sizes.  More jobs than FILL_MAXJ: big jobs shared by the
 // whole grid, small ones one CTA each.
-constexpr uint32_t FILL_UNIT = 4096;
+constexpr uint32_t FILL_UNIT = 16384;
 constexpr int FILL_MAXJ = 4096;
 
 template <typename U>
@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(256) k_fill(U* __restrict__ keys, JobList smal
 struct L1Aux {
   uint64_t tile_base;
   uint64_t cbase;
-  float S, T;
+  uint64_t pad0;
   uint32_t f1;
   uint32_t pad;
 };
@@ -748,13 +748,11 @@ k_l1_plan(LevelArgs la, SortLimits lim, Level1Ws w, uint32_t* err) {
   for (uint64_t j0 = 0; j0 < nj; j0 += blockDim.x) {
     const uint64_t j = j0 + threadIdx.x;
     uint64_t tiles = 0, f1 = 0;
-    const float S = 0, T = 0;
     if (j < nj) {
       Job job = la.in.jobs[j];
-      // the model's split aims at l1_target keys per sub-bucket; a key-range
-      // split (its input is skewed or clustered) uses 16x finer sub-buckets
       // the model's split has the call's Kf sub-buckets per bucket (ids from
-      // K2); a key-range split aims at la.target keys per sub-bucket
+      // K2, plus one per heavy value's interval); a range split aims at
+      // la.target keys per sub-bucket, at most la.fmax of them
       const uint64_t tg = la.target ? la.target : 1;
       const uint64_t fmx = la.fmax ? min((uint64_t)la.fmax, (uint64_t)MAX_F1) : (uint64_t)MAX_F1;
       uint64_t f = (job.m + tg - 1) / tg;
@@ -772,8 +770,7 @@ k_l1_plan(LevelArgs la, SortLimits lim, Level1Ws w, uint32_t* err) {
       L1Aux x;
       x.tile_base = s_rt + et;
       x.cbase = s_rc + ec;
-      x.S = S;
-      x.T = T;
+      x.pad0 = 0;
       x.f1 = (uint32_t)f1;
       x.pad = 0;
       aux[j] = x;
