@@ -99,17 +99,17 @@ struct HeavyEntry {    // a heavy value of one level-0 bucket
   uint32_t ext;        // its equality slot
 };
 
-// Two-way set-associative table of the heavy values (total-order key ->
-// equality slot): a key's two candidate entries are one 16-byte set.  Built
-// with HASH_EMPTY marking free entries, which are then filled with a key that
-// hashes to another set, so a probe never matches a free entry.  A value whose
-// set is full, and the value HASH_EMPTY itself (a valid uint64 key), are not in
-// the table: their keys take the full lookup.
-constexpr uint32_t HASH_SET_BITS = 12;
+// Direct-mapped table of the heavy values (total-order key -> equality slot):
+// one 8-byte probe per key.  A slot keeps the most frequent of the values
+// hashing to it; a free slot holds a key that hashes to another slot, so a
+// probe never matches it.  The values that lost their slot, and the value
+// HASH_EMPTY itself (a valid uint64 key), are not in the table: their keys take
+// the full lookup.
+constexpr uint32_t HASH_SET_BITS = 13;
 constexpr uint32_t HASH_SETS = 1u << HASH_SET_BITS;
-constexpr uint32_t HASH_SIZE = 2 * HASH_SETS;      // entries
+constexpr uint32_t HASH_SIZE = HASH_SETS;          // entries (one per slot)
 constexpr uint64_t HASH_EMPTY = ~0ull;
-__device__ __forceinline__ uint32_t heavy_hash(uint64_t t) {  // set index
+__device__ __forceinline__ uint32_t heavy_hash(uint64_t t) {  // slot index
   return (uint32_t)((t * 0x9E3779B97F4A7C15ull) >> (64 - HASH_SET_BITS));
 }
 
@@ -357,7 +357,7 @@ struct DevModel {
   uint32_t pos_max;        // bucket of the largest total-order key
   unsigned long long heavy_len;  // sample keys equal to a selected heavy value
   uint32_t compact;        // 1: the level-0 histogram compacts non-equality keys
-  uint32_t hash_probes;    // longest probe sequence of the heavy table (0: no table)
+  uint32_t hash_probes;    // 1: the heavy table is built (0: no table)
 };
 
 __device__ __forceinline__ uint32_t bitlen32(uint32_t v) { return v ? 32u - __clz((int)v) : 0u; }

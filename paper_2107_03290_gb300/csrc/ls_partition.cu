@@ -322,14 +322,12 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
       const uint64_t i = base + (uint64_t)k * H_THREADS + threadIdx.x;
       bool miss = false;
       if (i < ce) {
-        // one probe: a hit is a heavy value; anything else (including a heavy
-        // value displaced by a collision) takes the full lookup
-        // (free entries hold keys of other sets, so only a table key matches)
+        // one 8-byte probe: a hit is a heavy value; anything else (including a
+        // heavy value that lost its slot) takes the full lookup (free slots
+        // hold keys of other slots, so only a table key matches)
         const uint64_t t = KT<DT>::tk(u[k]);
-        const uint32_t set = heavy_hash(t);
-        const ulonglong2 kk = ((const ulonglong2*)hk)[set];
-        const uint32_t vv = ((const uint32_t*)hv)[set];
-        const uint32_t e = kk.x == t ? (vv & 0xFFFFu) : (kk.y == t ? (vv >> 16) : 0xFFFFFFFFu);
+        const uint32_t slot = heavy_hash(t);
+        const uint32_t e = hk[slot] == t ? (uint32_t)hv[slot] : 0xFFFFFFFFu;
         if (e != 0xFFFFFFFFu) {  // equality key: counted, never moved
           if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
           if (!compact) pk[i - a0] = PK_EQ;

@@ -739,60 +739,35 @@ k_heavy_heads(const uint64_t* __restrict__ sel, const uint32_t* __restrict__ sel
   }
 }
 
-// Heavy table, one CTA: a heavy value takes way r of its set when r values of
-// the same set are more frequent in the sample (longer run, ties: smaller key),
-// so a full set keeps its most frequent values, whatever the thread order.
-// Entries left free then get a key of another set (0, or 1 in set 0), so a
-// probe needs no emptiness test (hash_probes = 1 marks the table as built).
+// Heavy table, one CTA: each slot keeps the value hashing to it with the
+// longest run in the sorted sample (ties: the smaller key), whatever the thread
+// order: the caller zeroes the table, the candidates race with a 64-bit max of
+// (run << 32 | ~index), and the winners then replace their packed records.
+// Slots left free get a key of another slot (0, or 1 in slot 0), so a probe
+// needs no emptiness test (hash_probes = 1 marks the table as built).
 __global__ void __launch_bounds__(1024)
 k_heavy_hash(DevModel* hdr, const HeavyEntry* __restrict__ heavy, const uint32_t* __restrict__ hlen,
-             uint64_t* hkey, uint16_t* hval) {
-  __shared__ uint32_t scnt[HASH_SETS];      // values per set, then fill cursors
-  __shared__ uint32_t soff[HASH_SETS + 1];  // first list position of each set
-  __shared__ uint16_t lst[HASH_SIZE / 2];   // heavy indices grouped by set
-  __shared__ uint32_t ws[33];
+             unsigned long long* hkey, uint16_t* hval) {
   const uint32_t H = hdr->nheavy;
   if (2 * H > HASH_SIZE) return;  // too full to help
-  for (uint32_t s = threadIdx.x; s < HASH_SETS; s += blockDim.x) scnt[s] = 0;
-  __syncthreads();
-  // (uint64 key 2^64-1 is left to the full lookup)
-  for (uint32_t i = threadIdx.x; i < H; i += blockDim.x)
-    if (heavy[i].tk != HASH_EMPTY) atomicAdd(&scnt[heavy_hash(heavy[i].tk)], 1u);
-  __syncthreads();
-  for (uint32_t s = threadIdx.x; s < HASH_SETS; s += blockDim.x) soff[s] = scnt[s];
-  __syncthreads();
-  block_scan_array<uint32_t>(soff, HASH_SETS, ws);
-  for (uint32_t s = threadIdx.x; s < HASH_SETS; s += blockDim.x) scnt[s] = 0;
-  __syncthreads();
+  // (uint64 key 2^64-1 is left to the full lookup; a zero run never wins)
   for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) {
     const uint64_t t = heavy[i].tk;
-    if (t == HASH_EMPTY) continue;
-    const uint32_t set = heavy_hash(t);
-    lst[soff[set] + atomicAdd(&scnt[set], 1u)] = (uint16_t)i;
+    if (t != HASH_EMPTY)
+      atomicMax(&hkey[heavy_hash(t)], (unsigned long long)hlen[i] << 32 | (uint32_t)~i);
   }
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) {
-    const uint64_t t = heavy[i].tk;
-    if (t == HASH_EMPTY) continue;
-    const uint32_t set = heavy_hash(t), len = hlen[i];
-    uint32_t r = 0;
-    for (uint32_t q = 0; q < scnt[set]; ++q) {
-      const uint32_t j = lst[soff[set] + q];
-      const uint64_t tj = heavy[j].tk;
-      const uint32_t lj = hlen[j];
-      r += (j != i && (lj > len || (lj == len && tj < t))) ? 1u : 0u;
-    }
-    if (r < 2) {
-      hkey[2 * set + r] = t;
-      hval[2 * set + r] = (uint16_t)heavy[i].ext;
-    }
-  }
-  __syncthreads();
-  for (uint32_t p = threadIdx.x; p < HASH_SIZE; p += blockDim.x)
-    if (hkey[p] == HASH_EMPTY) {
-      hkey[p] = (p >> 1) == 0 ? 1ull : 0ull;  // heavy_hash(0) = 0, heavy_hash(1) != 0
+  for (uint32_t p = threadIdx.x; p < HASH_SIZE; p += blockDim.x) {
+    const unsigned long long w = hkey[p];
+    const uint32_t i = ~(uint32_t)w;
+    if ((w >> 32) != 0 && i < H) {
+      hkey[p] = heavy[i].tk;
+      hval[p] = (uint16_t)heavy[i].ext;
+    } else {
+      hkey[p] = p == 0 ? 1ull : 0ull;  // heavy_hash(0) = 0, heavy_hash(1) != 0
       hval[p] = 0xFFFFu;
     }
+  }
   if (threadIdx.x == 0 && H > 0) hdr->hash_probes = 1;
 }
 
@@ -851,9 +826,9 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
                                                      P.f0, (int)P.hpb, W.sel, W.sellen, W.nh, M.hdr);
   k_heavy_heads<DT><<<1, 1024, 0, st>>>(W.sel, W.sellen, W.nh, P.f0, (int)P.hpb, M.hdr, M.cleaf,
                                         M.heads, M.heavy, W.hlen);
-  e = cudaMemsetAsync(M.hkey, 0xFF, HASH_SIZE * sizeof(uint64_t), st);
+  e = cudaMemsetAsync(M.hkey, 0, HASH_SIZE * sizeof(uint64_t), st);
   if (e) return e;
-  k_heavy_hash<<<1, 1024, 0, st>>>(M.hdr, M.heavy, W.hlen, M.hkey, M.hval);
+  k_heavy_hash<<<1, 1024, 0, st>>>(M.hdr, M.heavy, W.hlen, (unsigned long long*)M.hkey, M.hval);
   add_launches(21);
   return cudaGetLastError();
 }

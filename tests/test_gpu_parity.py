@@ -209,6 +209,38 @@ def test_level0_histogram_matches_spec(dist):
     assert np.array_equal(h, hs)
 
 
+def _colliding_heavy(n: int, seed: int) -> np.ndarray:
+    """Heavy values that share slots of the level-0 heavy table (multiply-shift
+    of the total-order key, 13 bits): six values in each of four slots, with
+    decreasing frequencies, so that most of them lose their slot and must be
+    recognised by the full lookup; 30% normal background."""
+    rng = np.random.default_rng(seed)
+    cand = np.unique(rng.lognormal(0.0, 2.0, 200_000))
+    tk = oracle.total_order_keys(cand).astype(object)
+    slot = np.array([((int(t) * 0x9E3779B97F4A7C15) & (2**64 - 1)) >> 51 for t in tk])
+    vals = []
+    for sl in np.flatnonzero(np.bincount(slot, minlength=8192) >= 6)[:4]:
+        vals.extend(cand[slot == sl][:6])
+    vals = np.array(vals)
+    w = 1.0 / np.arange(1, vals.size + 1)
+    cnt = np.floor(0.7 * n * w / w.sum()).astype(np.int64)
+    keys = np.concatenate([np.repeat(vals, cnt), rng.normal(0.0, 3.0, n - cnt.sum())])
+    return keys[rng.permutation(n)]
+
+
+@pytest.mark.parametrize("n", [300_000, 3_000_001])
+def test_heavy_slot_collisions(n):
+    keys = _colliding_heavy(n, n)
+    assert_same(gpu_sort(keys), keys)
+    if n == 300_000:  # level-0 counts against the spec
+        p = ls.default_params(leaves=128, fanout=200, heavy_per_bucket=4)
+        t = torch.from_numpy(keys).cuda()
+        h = ls.level0_histogram(t, p)
+        m = ls.train(t, p)
+        ev = oracle.EvalParams.from_export(m, 128, 200)
+        assert np.array_equal(h, oracle.spec_ext_histogram(ev, keys, m["heavy_tk"]))
+
+
 @pytest.mark.parametrize("n", [1, 2, 100, 4095, 4096, 4097, 100_000, 1_000_000])
 def test_radix_sort_u64(n):
     rng = np.random.default_rng(n)
