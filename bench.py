@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 import lsgen  # noqa: E402
 
 METRIC = "keys/s & HBM GB/s vs roofline, 1 GB300; batched/served vs plain; p50/p99 ms"
+L2_BYTES = 129 * 1000 * 1000  # GB300 L2
 NPT = {"f64": np.float64, "u64": np.uint64, "f32": np.float32, "u32": np.uint32}
 WIDTH = {"f64": 8, "u64": 8, "f32": 4, "u32": 4}
 
@@ -463,11 +464,15 @@ def main():
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dt,
                "data": "synthetic",
                "config": {"workload": args.workload, "n": n, "dtype": dt,
-                          "l2": "inputs larger than L2 (restored from a device copy each step)",
+                          "l2": ("inputs larger than L2 (restored from a device copy each step)"
+                                 if n * w > L2_BYTES else
+                                 "inputs fit in L2 (latency case; restored from a device copy each step)"),
                           "parallelism": "replicas" if world > 1 else "single"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": int(launches), "clocks": clk.summary(),
                "wall_ms_per_step": 1000 * wall / args.steps, "correct": ok,
+               "ms_p50": float(np.median([x["ms_total"] for x in per])),
+               "ms_min": float(np.min([x["ms_total"] for x in per])),
                "kernels_ms": kms, "batched": batched, "serving": serving,
                "path": {k: last[k] for k in ("n_heavy", "n_ext", "max_bucket", "n_eq_keys",
                                              "n_level1", "n_segments", "n_fallback", "n_fill",
