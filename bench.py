@@ -169,7 +169,9 @@ def run_reference(args, rank: int):
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1000 * t / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": dt, "data": "synthetic",
-           "config": {"workload": args.workload, "n": int(keys.size), "dtype": dt},
+           "config": {"workload": args.workload, "n": int(keys.size), "dtype": dt,
+                      "l2": "host memory (the oracle runs on one host core)",
+                      "parallelism": "single"},
            "cpu_baseline": {"value": v, "unit": "keys/s", "cores": 1, "kind": "oracle",
                             "sample": f"first {sample} keys of the workload per step"},
            "e2e": {"value": v, "unit": "keys/s", "h2d_bytes_per_step": 0,
