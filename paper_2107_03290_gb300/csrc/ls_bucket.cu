@@ -50,6 +50,8 @@ struct SegShared {            // per-CTA scalars of the segment sort
   uint32_t nbig, all;
   float rscale;
   int sh;
+  float fmin, fscale;         // value-linear map (floats spanning several binades)
+  int vmap;
 };
 
 template <int DT>
@@ -123,11 +125,29 @@ __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* 
     const int sh = bl > 24 ? bl - 24 : 0;
     ss.sh = sh;
     ss.rscale = (float)m / ((float)(R >> sh) + 1.0f);
+    // Floats whose range crosses binades (typically around zero) are spread
+    // unevenly by a line in total-order key space (every binade gets the same
+    // share of slots); a line through their FP32 images keeps the groups
+    // short.  Both maps are non-decreasing in the key.
+    ss.vmap = 0;
+    if (DT == LS_F64 || DT == LS_F32) {
+      const float a = key_f32<DT>(KT<DT>::from_tk(ss.tmin));
+      const float b = key_f32<DT>(KT<DT>::from_tk(ss.tmax));
+      const float span = b - a;
+      if (((__float_as_uint(a) ^ __float_as_uint(b)) >> 23) != 0 && isfinite(a) && isfinite(b) &&
+          span > 0.0f && isfinite(span)) {
+        ss.vmap = 1;
+        ss.fmin = a;
+        ss.fscale = (float)m / span;
+      }
+    }
   }
   __syncthreads();
   const float rscale = ss.rscale;
   const int sh = ss.sh;
   const unsigned long long tmin = ss.tmin;
+  const bool vmap = (DT == LS_F64 || DT == LS_F32) && ss.vmap != 0;
+  const float fmin = ss.fmin, fscale = ss.fscale;
   // slots, histogram, ranks (packed slot | rank << 16; m <= 2^15)
   uint32_t sr[KPT];
 #pragma unroll
@@ -135,7 +155,8 @@ __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* 
     const uint32_t i = k * THREADS + threadIdx.x;
     uint32_t v = 0xFFFFFFFFu;
     if (i < m) {
-      const float f = __uint2float_rn((uint32_t)((KT<DT>::tk(u[k]) - tmin) >> sh)) * rscale;
+      const float f = vmap ? (key_f32<DT>(u[k]) - fmin) * fscale
+                           : __uint2float_rn((uint32_t)((KT<DT>::tk(u[k]) - tmin) >> sh)) * rscale;
       const uint32_t s = min((uint32_t)f, m - 1);
       v = s | (atomicAdd(&cnt[s], 1u) << 16);  // rank inside the slot
     }

@@ -26,21 +26,6 @@ constexpr int SS_KPT = 8;
 constexpr int SS_TILE = SS_THREADS * SS_KPT;
 constexpr int SS_CAP = 4096;               // gap sorted in one CTA's shared memory
 
-// Ascending bitonic sort of a[0..n) in shared memory, n a power of two, by the
-// whole block.
-__device__ __forceinline__ void ss_bitonic(uint64_t* a, uint32_t n) {
-  for (uint32_t k = 2; k <= n; k <<= 1)
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = threadIdx.x; i < n / 2; i += blockDim.x) {
-        const uint32_t p = 2 * i - (i & (j - 1)), q = p + j;  // pair i of the stage
-        const bool up = (p & k) == 0;
-        const uint64_t x = a[p], y = a[q];
-        if ((x > y) == up) { a[p] = y; a[q] = x; }
-      }
-      __syncthreads();
-    }
-}
-
 // Bucket of key t: 2 * #{splitters < t} + [t equals the next splitter].
 __device__ __forceinline__ uint32_t ss_bucket(const uint64_t* spl, uint64_t t) {
   uint32_t lo = 0;
@@ -67,9 +52,55 @@ __device__ __forceinline__ void ss_bitonic_regs(uint64_t* v, uint32_t base, uint
   }
 }
 
+// Ascending bitonic sort of n keys (n a power of two, 256 <= n <= 8 * blockDim.x)
+// held 8 consecutive keys per thread by the first n / 8 threads of the block
+// (thread t: positions 8t .. 8t+7).  Stages whose pairs stay inside a thread
+// run in registers, those inside a warp (8 <= j < 256) exchange through
+// shuffles, and only the stages across warps (j >= 256) go through shared
+// memory `sh` (n words).  Every thread of the block calls it (barriers).
+__device__ __forceinline__ void ss_sort_regs(uint64_t (&v)[8], uint64_t* sh, uint32_t n) {
+  const uint32_t t = threadIdx.x;
+  const bool act = t < (n >> 3);  // whole warps: n / 8 is a multiple of 32
+  const uint32_t base = 8 * t;
+  if (act)
+    for (uint32_t k = 2; k <= 8; k <<= 1) ss_bitonic_regs(v, base, k, k >> 1);
+  for (uint32_t k = 16; k <= n; k <<= 1) {
+    if (k > 256) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (act) sh[base + q] = v[q];
+      __syncthreads();
+      for (uint32_t j = k >> 1; j >= 256; j >>= 1) {
+        for (uint32_t i = t; i < n / 2; i += blockDim.x) {
+          const uint32_t p = 2 * i - (i & (j - 1)), q = p + j;
+          const bool up = (p & k) == 0;
+          const uint64_t x = sh[p], y = sh[q];
+          if ((x > y) == up) { sh[p] = y; sh[q] = x; }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (act) v[q] = sh[base + q];
+    }
+    if (act) {
+      const bool up = (base & k) == 0;  // the same for the thread's 8 keys (k >= 16)
+      for (uint32_t j = min(k >> 1, 128u); j >= 8; j >>= 1) {
+        const uint32_t d = j >> 3;  // partner lane
+        const bool keep_min = ((t & d) == 0) == up;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const uint64_t o = __shfl_xor_sync(0xffffffffu, v[q], d);
+          v[q] = keep_min ? min(v[q], o) : max(v[q], o);
+        }
+      }
+      ss_bitonic_regs(v, base, k, 4);
+    }
+  }
+}
+
 // The oversample sorted by one CTA of 1024 threads, 8 consecutive keys per
-// thread: the stages inside a group of 8 run in registers, the others through
-// shared memory.
+// thread (ss_sort_regs).
 static __global__ void __launch_bounds__(1024)
 k_ss_splitters(const uint64_t* __restrict__ keys, uint64_t m, uint64_t* __restrict__ spl,
                uint32_t* __restrict__ cnt) {
@@ -80,25 +111,7 @@ k_ss_splitters(const uint64_t* __restrict__ keys, uint64_t m, uint64_t* __restri
 #pragma unroll
   for (int q = 0; q < 8; ++q) v[q] = keys[(uint64_t)(base + q) * m / SS_CAND];
   for (uint32_t i = threadIdx.x; i <= SS_NB; i += blockDim.x) cnt[i] = 0;
-  for (uint32_t k = 2; k <= 8; k <<= 1) ss_bitonic_regs(v, base, k, k >> 1);
-  for (uint32_t k = 16; k <= (uint32_t)SS_CAND; k <<= 1) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) ss_c[base + q] = v[q];
-    __syncthreads();
-    for (uint32_t j = k >> 1; j >= 8; j >>= 1) {
-      for (uint32_t i = threadIdx.x; i < SS_CAND / 2; i += blockDim.x) {
-        const uint32_t p = 2 * i - (i & (j - 1)), q = p + j;
-        const bool up = (p & k) == 0;
-        const uint64_t x = ss_c[p], y = ss_c[q];
-        if ((x > y) == up) { ss_c[p] = y; ss_c[q] = x; }
-      }
-      __syncthreads();
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = ss_c[base + q];
-    __syncthreads();
-    ss_bitonic_regs(v, base, k, 4);
-  }
+  ss_sort_regs(v, ss_c, SS_CAND);
   // every SS_OVER-th key of the sorted oversample (SS_OVER divides 8)
 #pragma unroll
   for (int q = SS_OVER - 1; q < 8; q += SS_OVER) spl[(base + q) / SS_OVER] = v[q];
@@ -196,17 +209,35 @@ __device__ __forceinline__ uint32_t ss_merge_path(const uint64_t* A, uint32_t na
   return lo;
 }
 
-// Loads up to SS_CAP keys, pads with the largest key to a power of two,
-// sorts, writes the first `len` back.
+// Loads up to SS_CAP keys into registers (8 per thread), pads with the
+// largest key to a power of two of at least 256 (up to 8 keys: one thread),
+// sorts, writes the first `len` back.  Needs blockDim.x >= SS_CAP / 8.
 __device__ __forceinline__ void ss_sort_chunk(const uint64_t* src, uint64_t* dst, uint32_t len,
                                               uint64_t* a) {
-  uint32_t n2 = 2;
+  if (len <= 8) {  // one thread: the 8-key network in registers
+    if (threadIdx.x == 0) {
+      uint64_t v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = q < (int)len ? src[q] : ~0ull;
+      for (uint32_t k = 2; k <= 8; k <<= 1) ss_bitonic_regs(v, 0, k, k >> 1);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q < (int)len) dst[q] = v[q];
+    }
+    __syncthreads();
+    return;
+  }
+  uint32_t n2 = 256;
   while (n2 < len) n2 <<= 1;
-  for (uint32_t i = threadIdx.x; i < n2; i += blockDim.x) a[i] = i < len ? src[i] : ~0ull;
-  __syncthreads();
-  ss_bitonic(a, n2);
-  for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) dst[i] = a[i];
-  __syncthreads();
+  const uint32_t base = 8 * threadIdx.x;
+  uint64_t v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = base + q < len ? src[base + q] : ~0ull;
+  ss_sort_regs(v, a, n2);
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if (base + q < len) dst[base + q] = v[q];
+  __syncthreads();  // the merge passes read what the other threads wrote
 }
 
 // One CTA per gap: sorted from `in` into `out`.  The CTAs past the buckets

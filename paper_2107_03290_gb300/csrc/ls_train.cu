@@ -283,7 +283,10 @@ constexpr int FIT_UNIT = 2048;
 
 __global__ void __launch_bounds__(1024)
 k_fit_units_plan(const uint32_t* leaf_beg, const uint32_t* leaf_end, int L, uint32_t* ubase,
-                 uint32_t* utotal) {
+                 uint32_t* utotal, uint32_t ucap, uint32_t* err) {
+  // (ubase clamped to the unit buffer's ucap entries: leaf ranges that overlap,
+  // which only an unsorted sample could give, flag an error instead of
+  // writing past the buffer)
   __shared__ uint32_t ws[33];
   __shared__ uint32_t s_run;
   if (threadIdx.x == 0) s_run = 0;
@@ -294,12 +297,16 @@ k_fit_units_plan(const uint32_t* leaf_beg, const uint32_t* leaf_end, int L, uint
     if (l < L && leaf_end[l] > leaf_beg[l]) u = (leaf_end[l] - leaf_beg[l] + FIT_UNIT - 1) / FIT_UNIT;
     uint32_t tot;
     const uint32_t ex = block_excl_sum<uint32_t>(u, ws, &tot);
-    if (l < L) ubase[l] = s_run + ex;
+    if (l < L) ubase[l] = min(s_run + ex, ucap);
     __syncthreads();
     if (threadIdx.x == 0) s_run += tot;
     __syncthreads();
   }
-  if (threadIdx.x == 0) { ubase[L] = s_run; *utotal = s_run; }
+  if (threadIdx.x == 0) {
+    if (s_run > ucap) set_error(err, ERR_BOUNDS);
+    ubase[L] = min(s_run, ucap);
+    *utotal = min(s_run, ucap);
+  }
 }
 
 template <int DT>
@@ -799,7 +806,8 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   k_fit_root<DT><<<1, 32, 0, st>>>(M.hdr, W.smp_a, W.rank, W.partials, FIT_BLOCKS);
   const int rb = (int)std::min<uint64_t>((s + RT_THREADS - 1) / RT_THREADS, 8ull * num_sms);
   k_fit_route<DT><<<std::max(1, rb), RT_THREADS, 0, st>>>(W.smp_a, M.hdr, L, M.leaf_beg, M.leaf_end);
-  k_fit_units_plan<<<1, 1024, 0, st>>>(M.leaf_beg, M.leaf_end, L, W.ubase, W.utotal);
+  k_fit_units_plan<<<1, 1024, 0, st>>>(M.leaf_beg, M.leaf_end, L, W.ubase, W.utotal,
+                                       (uint32_t)(s / FIT_UNIT + L + 2), err);
   {
     const unsigned ub = (unsigned)std::min<uint64_t>(s / FIT_UNIT + L + 1, 16ull * num_sms);
     k_fit_unit_sums<DT><<<ub, FIT_THREADS, 0, st>>>(W.smp_a, W.rank, M.hdr, M.leaf_beg,
