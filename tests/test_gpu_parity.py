@@ -228,6 +228,23 @@ def _colliding_heavy(n: int, seed: int) -> np.ndarray:
     return keys[rng.permutation(n)]
 
 
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+@pytest.mark.parametrize("lim", [1e30, 1e300])
+@pytest.mark.parametrize("n", [3_000, 300_001])
+def test_keys_across_binades(dt, lim, n):
+    """Log-uniform magnitudes of both signs (every binade from 1/lim to lim,
+    zeros and denormals mixed in), so that segments span many binades: the
+    in-bucket slot map through the keys' FP32 images, and (beyond the FP32
+    range) the fallback to the total-order map."""
+    rng = np.random.default_rng(n + int(np.log10(lim)))
+    hi = min(np.log(lim), np.log(np.finfo(dt).max) - 1)
+    mag = np.exp(rng.uniform(-hi, hi, n))
+    keys = (np.where(rng.random(n) < 0.5, -mag, mag)).astype(dt)
+    k = max(1, n // 100)
+    keys[rng.integers(0, n, k)] = np.array([0.0, -0.0, np.finfo(dt).tiny / 4], dt)[rng.integers(0, 3, k)]
+    assert_same(gpu_sort(keys), keys)
+
+
 @pytest.mark.parametrize("n", [300_000, 3_000_001])
 def test_heavy_slot_collisions(n):
     keys = _colliding_heavy(n, n)
