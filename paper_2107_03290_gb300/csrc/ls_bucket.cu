@@ -8,7 +8,9 @@
 // on the total-order key without any per-key model lookup:
 //   slot(x) = min(m - 1, floor(((tk(x) - tmin) >> sh) * m / (((tmax - tmin) >> sh) + 1)))
 // (sh keeps the scaled range within 24 bits, so the conversion is exact and
-// the map is non-decreasing).  Histogram of slots -> exclusive scan (the
+// the map is non-decreasing); float segments whose range crosses binades use
+// the line through the keys' FP32 images instead, which is non-decreasing
+// too.  Histogram of slots -> exclusive scan (the
 // running totals of Alg. 2) -> placement -> touch-up.  Keys of different
 // slots are already in order, so the touch-up only orders each group of keys
 // sharing a slot: every key of a group of at most 32 counts the members below
