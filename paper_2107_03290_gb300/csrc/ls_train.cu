@@ -391,14 +391,25 @@ __device__ __forceinline__ float fp32_sat(double d) {  // round to FP32, finite
 template <int DT>
 __global__ void __launch_bounds__(1024)
 k_fit_final(DevModel* hdr, int L, double* leaf, CellLeaf* cleaf) {
-  // next non-empty leaf to the right, by one warp over L/32-leaf ranges
+  // the leaves' lo bounds staged in shared memory, so that the right-to-left
+  // pass runs on shared loads rather than a chain of global round trips
+  __shared__ double slo[MAX_LEAVES];
+  __shared__ unsigned char emp[MAX_LEAVES];
+  L = min(L, MAX_LEAVES);
+  for (int l = threadIdx.x; l < L; l += blockDim.x) {
+    slo[l] = leaf[5 * (size_t)l + 3];
+    emp[l] = 0;
+  }
+  __syncthreads();
+  // an empty leaf (lo < 0) takes the lo of the next non-empty leaf to its
+  // right (1 past the last); one warp over L/32-leaf ranges
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     const int per = (L + 31) / 32;
     const int a = lane * per, b = min(L, a + per);
     int first = L;
     for (int l = b - 1; l >= a; --l)
-      if (leaf[5 * (size_t)l + 3] >= 0) first = l;
+      if (slo[l] >= 0) first = l;
     int suf = first;
     for (int o = 1; o < 32; o <<= 1) {
       const int v = __shfl_down_sync(0xffffffffu, suf, o);
@@ -406,12 +417,10 @@ k_fit_final(DevModel* hdr, int L, double* leaf, CellLeaf* cleaf) {
     }
     int nxt = __shfl_down_sync(0xffffffffu, suf, 1);
     if (lane == 31) nxt = L;
-    double next_lo = (nxt < L) ? leaf[5 * (size_t)nxt + 3] : 1.0;
+    double next_lo = (nxt < L) ? slo[nxt] : 1.0;
     for (int l = b - 1; l >= a; --l) {
-      double* q = leaf + 5 * (size_t)l;
-      if (q[3] < 0) { q[3] = next_lo; q[2] = next_lo; q[0] = 0; q[1] = 0; }
-      q[4] = next_lo;
-      next_lo = q[3];
+      if (slo[l] < 0) { slo[l] = next_lo; emp[l] = 1; }
+      next_lo = slo[l];
     }
     if (lane == 0) {
       const double* r = hdr->root64;
@@ -424,13 +433,24 @@ k_fit_final(DevModel* hdr, int L, double* leaf, CellLeaf* cleaf) {
     }
   }
   __syncthreads();
+  // hi_l = lo_{l+1} (1 for the last leaf); an empty leaf is the constant lo
   for (int l = threadIdx.x; l < L; l += blockDim.x) {
-    const double* q = leaf + 5 * (size_t)l;
+    double* q = leaf + 5 * (size_t)l;
+    const double lo = slo[l], hi = l + 1 < L ? slo[l + 1] : 1.0;
+    double A, c, B;
+    if (emp[l]) {
+      A = 0; c = 0; B = lo;
+      q[0] = A; q[1] = c; q[2] = B;
+    } else {
+      A = q[0]; c = q[1]; B = q[2];
+    }
+    q[3] = lo;
+    q[4] = hi;
     CellLeaf cl;
-    cl.A = fp32_sat(q[0]);
-    cl.B = fp32_sat(__dsub_rn(q[2], __dmul_rn(q[0], q[1])));
-    cl.LO = __double2float_rn(q[3]);
-    cl.HI = __double2float_rn(q[4]);
+    cl.A = fp32_sat(A);
+    cl.B = fp32_sat(__dsub_rn(B, __dmul_rn(A, c)));
+    cl.LO = __double2float_rn(lo);
+    cl.HI = __double2float_rn(hi);
     cleaf[l] = cl;
   }
 }
