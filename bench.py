@@ -96,7 +96,8 @@ class Clocks:
 
 
 def kernel_algorithmic_bytes(st: dict, n: int, w: int) -> dict:
-    """Algorithmic bytes per launch of each timed kernel."""
+    """Algorithmic bytes per launch of each timed kernel: K2 reads every key
+    once (n*w); K4 reads every key and writes the non-equality ones."""
     eq = st["n_eq_keys"]
     return {
         "k_l0_hist": n * w,                        # read every key once
