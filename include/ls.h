@@ -16,11 +16,17 @@
  *    floats (-NaN < -inf < ... < -0.0 < +0.0 < ... < +inf < +NaN), unsigned
  *    order for integers.  The sorted output is therefore unique.
  *  - Synchronous errors (bad arguments, allocation failure, launch failure) are
- *    returned.  Asynchronous device errors (a bounded wait that timed out) are
- *    recorded in a per-device status word and returned by the next
- *    ls_stream_status() call.  After an error the key contents are unspecified.
+ *    returned.  Asynchronous device errors (a bounded wait that timed out, a
+ *    bounds check that failed) are recorded per call: each call has its own
+ *    device status block, cleared when the call starts, and ORs it at its end
+ *    into the status word of its stream, which ls_stream_status() returns and
+ *    clears.  A call that fails stops its remaining work (its later kernels do
+ *    nothing); the key contents are then unspecified.  An error on one stream
+ *    is never reported on another (server requests have their own words).
  *  - Thread safety: calls on different streams may run concurrently; the
- *    library's scratch memory is stream-ordered.
+ *    library's scratch memory is stream-ordered.  The one exception is
+ *    ls_radix_sort_u64_noalloc, whose calls share one static scratch array:
+ *    callers must order those calls.
  */
 #ifndef LS_H
 #define LS_H
@@ -47,9 +53,9 @@ typedef enum {
 typedef struct ls_params {
   uint32_t fanout;           /* level-0 buckets f; 0: chosen by the planner (256,
                                 so level-0 and level-1 scatters write 128-byte runs;
-                                Sec. 5.1 uses 1000, which stays available)          */
-  uint32_t leaves;           /* RMI leaves L (Sec. 5.1: 1000)                          */
-  uint32_t sample_div;       /* sample s = ceil(n / sample_div) (Sec. 5.1: 1% -> 100)  */
+                                Sec. 6.1 uses 1000, which stays available)          */
+  uint32_t leaves;           /* RMI leaves L (Sec. 6.1: 1000)                          */
+  uint32_t sample_div;       /* sample s = ceil(n / sample_div) (Sec. 6.1: 1% -> 100)  */
   uint32_t heavy_per_bucket; /* max equality buckets inside one level-0 bucket (<= 15);
                                 0: chosen by the planner                              */
   uint64_t sample_max;       /* cap on s (0: none)                                     */
@@ -135,9 +141,23 @@ ls_status ls_sort_host(void* host_keys, size_t n, ls_dtype dtype, void* stream,
 ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dtype dtype,
                         void* stream);
 
-/* Waits for `stream`, then returns and clears the device status word
- * (LS_ERR_TIMEOUT if a bounded device wait gave up since the last call). */
+/* Waits for `stream`, then returns and clears the status word of `stream`:
+ * LS_ERR_TIMEOUT if a bounded device wait of a call on this stream gave up
+ * since the last ls_stream_status(stream), LS_ERR_CUDA if a device bounds
+ * check failed, else LS_OK.  Errors of calls on other streams are not seen.
+ * (Streams are tracked in a table of 1024 entries per device; beyond that,
+ * streams share status words.) */
 ls_status ls_stream_status(void* stream);
+
+/* Test hook, not for production use: later calls on `stream` give up each
+ * bounded device wait after `spin_limit` polls (0: the default, 2^26), and
+ * with `stall` = 1 the first tile of the level-0 look-back scan never
+ * publishes its running total, so the waits of the tiles after it run out
+ * (the "flag that nothing sets").  Such a call ends in bounded time; its later
+ * kernels do nothing, the keys are left unspecified, every access stays in
+ * bounds, and ls_stream_status(stream) returns LS_ERR_TIMEOUT.  stall = 0 and
+ * spin_limit = 0 restore normal calls.  Returns LS_OK. */
+ls_status ls_debug_set_wait(void* stream, uint32_t stall, uint64_t spin_limit);
 
 /* Stage entry points (used by the kernel parity tests). */
 
@@ -159,7 +179,7 @@ ls_status ls_level0_histogram(const void* keys, size_t n, ls_dtype dtype, void* 
 ls_status ls_radix_sort_u64(uint64_t* keys, size_t count, void* stream);
 
 /* Sort `count` 64-bit unsigned keys at device pointer `keys` in place with the
- * sample sort that orders the training sample (Sec. 5.1: the model is fitted
+ * sample sort that orders the training sample (Sec. 6.1: the model is fitted
  * to the sorted 1% sample): 2048 splitters from a sorted 8192-key evenly
  * spaced oversample, each key routed to a gap between splitters or to a
  * splitter's own value, each gap sorted in shared memory (a gap over 4096 keys
@@ -197,14 +217,23 @@ typedef struct ls_server_config {
   uint32_t max_inflight;     /* requests on the GPU at once (default 64)       */
   uint32_t max_queue;        /* waiting requests before LS_ERR_BUSY (def 4096) */
   uint32_t streams;          /* CUDA streams used for overlap (default 8)      */
-  uint32_t reserved[5];
+  uint32_t debug_stall;      /* test hook (0 in normal use): ls_debug_set_wait's
+                                `stall` for every request                        */
+  uint32_t debug_spin_limit; /* test hook (0 in normal use): ls_debug_set_wait's
+                                `spin_limit` for every request                   */
+  uint32_t reserved[3];
 } ls_server_config;
+
+/* Requests of at most this many keys that are admitted together are sorted
+ * by one batched launch sequence per key type; larger ones by ls_sort. */
+#define LS_SERVER_BATCH_MAX (1u << 24)
 
 typedef struct ls_request_stats {
   double queue_ms;           /* submit -> launch                              */
   double device_ms;          /* launch -> completion event                    */
   double total_ms;           /* submit -> completion                          */
-  ls_status status;
+  ls_status status;          /* LS_OK, or the request's device error: requests
+                                sorted by one batched launch share its status  */
 } ls_request_stats;
 
 ls_status ls_server_create(const ls_server_config* cfg, ls_server** out);
@@ -215,11 +244,14 @@ ls_status ls_server_submit(ls_server* s, void* keys, size_t n, ls_dtype dtype,
 /* As ls_server_submit, with the keys first copied from the device array `src`
  * (n keys, not overlapping `keys`) into `keys` on the server's stream; the
  * copy counts in queue and total latency but not in device_ms.  Requests of
- * at most 2^22 keys that are admitted together are sorted by one batched
- * launch sequence per key type; larger ones by the full learned sort. */
+ * at most LS_SERVER_BATCH_MAX (2^24) keys that are admitted together are
+ * sorted by one batched launch sequence per key type; larger ones by the full
+ * learned sort. */
 ls_status ls_server_submit_from(ls_server* s, const void* src, void* keys, size_t n,
                                 ls_dtype dtype, uint64_t* ticket);
-/* Wait up to timeout_ms for a ticket (UINT32_MAX: forever). */
+/* Wait up to timeout_ms for a ticket (UINT32_MAX: forever).  Returns the
+ * request's status (LS_ERR_TIMEOUT also when the wait itself timed out, in
+ * which case the ticket stays valid). */
 ls_status ls_server_wait(ls_server* s, uint64_t ticket, uint32_t timeout_ms,
                          ls_request_stats* st);
 ls_status ls_server_destroy(ls_server* s);

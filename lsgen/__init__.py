@@ -7,13 +7,13 @@ drawing code lives in ``gen.cpp`` and is compiled on first use (or by
 Workloads (synthetic stand-ins with the shapes of the paper's data sets and
 of the benchmark configurations):
 
-* ``normal_f64``            N(0,1) doubles (the paper's Standard Normal set, Sec. 5.1)
+* ``normal_f64``            N(0,1) doubles (the paper's Standard Normal set, Sec. 6.1)
 * ``zipf_lognormal_f64``    k distinct lognormal values chosen by Zipf rank
 * ``uniform_u64``           uniform on [0, 2^64)
-* ``gauss_mix_f64``         equal mixture of 5 Gaussians (Mix_Gauss, Sec. 5.1)
+* ``gauss_mix_f64``         equal mixture of 5 Gaussians (Mix_Gauss, Sec. 6.1)
 * ``timestamp_u32``         sorted runs with exact repeats and local swaps
 * ``exponential_f32``       Exponential(1) rounded to float
-* ``rootdups_f64`` / ``twodups_f64``  the RootDups/TwoDups sets of Sec. 5.1
+* ``rootdups_f64`` / ``twodups_f64``  the RootDups/TwoDups sets of Sec. 6.1
 """
 from __future__ import annotations
 

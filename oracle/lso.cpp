@@ -12,7 +12,7 @@
 //    is read as "Frag[i].clear()".
 //  * S_F records (owner, size) per fragment so that Defragment can place it.
 //    Defragment is out of place: prefix sums of S_B give each bucket's start.
-//  * The model (Sec. 2, Sec. 5.1: two layers, 1000 linear leaves, 1% sample)
+//  * The model (Sec. 2, Sec. 6.1: two layers, 1000 linear leaves, 1% sample)
 //    returns the count of sample keys strictly below x divided by the sample
 //    size (ties take the first rank); root and leaves are least-squares lines;
 //    slopes are clamped to >= 0 and leaf outputs to [lo_l, hi_l] (the eCDF of

@@ -27,10 +27,10 @@ extern "C" {
 enum { LSO_F64 = 0, LSO_U64 = 1, LSO_F32 = 2, LSO_U32 = 3 };
 
 typedef struct lso_params {
-  uint32_t fanout;      /* f, buckets per level (Sec. 5.1: 1000)                 */
-  uint32_t leaves;      /* L, RMI leaf models (Sec. 5.1: 1000)                   */
-  uint32_t sample_div;  /* sample size = ceil(n / sample_div) (Sec. 5.1: 1% => 100) */
-  uint32_t frag_cap;    /* c, fragment capacity (Sec. 5.1: 100)                  */
+  uint32_t fanout;      /* f, buckets per level (Sec. 6.1: 1000)                 */
+  uint32_t leaves;      /* L, RMI leaf models (Sec. 6.1: 1000)                   */
+  uint32_t sample_div;  /* sample size = ceil(n / sample_div) (Sec. 6.1: 1% => 100) */
+  uint32_t frag_cap;    /* c, fragment capacity (Sec. 6.1: 100)                  */
   uint64_t sample_max;  /* 0 = no cap on the sample size                         */
   uint64_t seed;        /* seed of the stratified sample offsets                 */
   uint64_t n_small;     /* n below this: insertion sort only (not in the paper)  */

@@ -118,7 +118,8 @@ class ModelExport(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
                 ("max_queue", ctypes.c_uint32), ("streams", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 5)]
+                ("debug_stall", ctypes.c_uint32), ("debug_spin_limit", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 3)]
 
 
 class RequestStats(ctypes.Structure):
@@ -127,7 +128,8 @@ class RequestStats(ctypes.Structure):
 
 
 EXPORTED = ["ls_default_params", "ls_status_string", "ls_sort", "ls_sort_ex", "ls_sort_host",
-            "ls_sort_batch", "ls_stream_status", "ls_train", "ls_level0_histogram",
+            "ls_sort_batch", "ls_stream_status", "ls_debug_set_wait", "ls_train",
+            "ls_level0_histogram",
             "ls_radix_sort_u64", "ls_radix_sort_u64_noalloc", "ls_sample_sort_u64",
             "ls_kernel_launches",
             "ls_server_create", "ls_server_submit", "ls_server_submit_from", "ls_server_wait",
@@ -165,6 +167,7 @@ def load(path: str | None = None):
             "ls_sort_host": [vp, sz, i32, vp, P(Params)],
             "ls_sort_batch": [vp, vp, sz, i32, vp],
             "ls_stream_status": [vp],
+            "ls_debug_set_wait": [vp, u32, u64],
             "ls_train": [vp, sz, i32, vp, P(Params), P(ModelExport)],
             "ls_level0_histogram": [vp, sz, i32, vp, P(Params), vp, sz, P(ctypes.c_size_t)],
             "ls_radix_sort_u64": [vp, sz, vp],
@@ -275,7 +278,15 @@ def kernel_launches() -> int:
 
 
 def stream_status(stream=None) -> int:
+    """Status of the calls on `stream` since the last check (0: ok); clears it."""
     return load().ls_stream_status(_stream(stream))
+
+
+def debug_set_wait(stall: int = 0, spin_limit: int = 0, stream=None):
+    """Test hook (ls_debug_set_wait): bounded waits of later calls on `stream`
+    give up after `spin_limit` polls; stall=1 makes the level-0 scan's waits
+    run out.  (0, 0) restores normal calls."""
+    _check(load().ls_debug_set_wait(_stream(stream), stall, spin_limit), "ls_debug_set_wait")
 
 
 def radix_sort_u64_(t, stream=None):
@@ -358,8 +369,10 @@ class Server:
     """Continuous-batching sort server (ls_server_*)."""
 
     def __init__(self, hbm_budget_bytes: int = 120 << 30, max_inflight: int = 64,
-                 max_queue: int = 4096, streams: int = 8):
-        cfg = ServerConfig(hbm_budget_bytes, max_inflight, max_queue, streams)
+                 max_queue: int = 4096, streams: int = 8, debug_stall: int = 0,
+                 debug_spin_limit: int = 0):
+        cfg = ServerConfig(hbm_budget_bytes, max_inflight, max_queue, streams, debug_stall,
+                           debug_spin_limit)
         self._h = ctypes.c_void_p()
         _check(load().ls_server_create(ctypes.byref(cfg), ctypes.byref(self._h)),
                "ls_server_create")
@@ -381,11 +394,15 @@ class Server:
                    "ls_server_submit_from")
         return tk.value
 
-    def wait(self, ticket: int, timeout_ms: int = 0xFFFFFFFF) -> dict:
+    def wait(self, ticket: int, timeout_ms: int = 0xFFFFFFFF, check: bool = True) -> dict:
+        """Wait for a request; raises LsError on a failed request unless
+        check=False (then the dict's "status" holds the code)."""
         st = RequestStats()
         rc = load().ls_server_wait(self._h, ticket, timeout_ms, ctypes.byref(st))
-        _check(rc, "ls_server_wait")
-        return {"queue_ms": st.queue_ms, "device_ms": st.device_ms, "total_ms": st.total_ms}
+        if check:
+            _check(rc, "ls_server_wait")
+        return {"queue_ms": st.queue_ms, "device_ms": st.device_ms, "total_ms": st.total_ms,
+                "status": rc}
 
     def close(self):
         if self._h:

@@ -31,16 +31,68 @@
 
 namespace ls {
 
-__device__ uint32_t g_status_word;  // asynchronous device errors (ERR_* bits)
+// Persistent status blocks, one per stream that has called into the library
+// (slot 0: the legacy default stream).  A stream's calls OR their errors into
+// its block; ls_stream_status reads and clears it.  The slot of a stream is
+// found in a fixed open-addressing table (no allocation); when the table is
+// full, later streams share slots by hash.
+constexpr int STATUS_SLOTS = 1024;
+constexpr int MAX_DEVICES = 64;
+__device__ CallStatus g_stream_status[STATUS_SLOTS];
+
+struct SlotTable {
+  std::atomic<uintptr_t> key[STATUS_SLOTS];   // stream handle + 1 (0: free)
+  std::atomic<uint32_t> stall[STATUS_SLOTS];  // test hooks of ls_debug_set_wait
+  std::atomic<unsigned long long> limit[STATUS_SLOTS];
+};
+static SlotTable g_slots[MAX_DEVICES];
+
+static int slot_of(int dev, cudaStream_t st, bool insert) {
+  if (dev < 0 || dev >= MAX_DEVICES) return 0;
+  SlotTable& t = g_slots[dev];
+  const uintptr_t k = (uintptr_t)st + 1;
+  if (st == nullptr) {
+    uintptr_t z = 0;
+    t.key[0].compare_exchange_strong(z, k);
+    return 0;
+  }
+  const uint64_t h = ((uint64_t)k * 0x9E3779B97F4A7C15ull) >> 40;
+  for (int p = 0; p < STATUS_SLOTS - 1; ++p) {
+    const int i = 1 + (int)((h + p) % (STATUS_SLOTS - 1));
+    uintptr_t cur = t.key[i].load(std::memory_order_acquire);
+    if (cur == k) return i;
+    if (cur == 0) {
+      if (!insert) return -1;
+      if (t.key[i].compare_exchange_strong(cur, k) || cur == k) return i;
+    }
+  }
+  return insert ? 1 + (int)(h % (STATUS_SLOTS - 1)) : -1;  // full: shared by hash
+}
+
+// Device address of the current device's persistent blocks (looked up once
+// per device with that device current; no allocation of any kind).
+static std::atomic<CallStatus*> g_slot_base[MAX_DEVICES];
+static cudaError_t slot_base(int id, CallStatus** out) {
+  if (id < 0 || id >= MAX_DEVICES) return cudaErrorInvalidDevice;
+  CallStatus* b = g_slot_base[id].load(std::memory_order_acquire);
+  if (!b) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_stream_status);
+    if (e) return e;
+    b = (CallStatus*)p;
+    g_slot_base[id].store(b, std::memory_order_release);
+  }
+  *out = b;
+  return cudaSuccess;
+}
 
 static std::atomic<unsigned long long> g_launches{0};
 void add_launches(unsigned k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
-cudaError_t status_word_ptr(uint32_t** out) {
-  void* p = nullptr;
-  const cudaError_t e = cudaGetSymbolAddress(&p, g_status_word);
-  *out = (uint32_t*)p;
-  return e;
+// ORs a call's error word into its persistent block (stream or request).
+__global__ void k_status_fold(const CallStatus* __restrict__ local, CallStatus* to) {
+  const uint32_t w = local->word;
+  if (w) atomicOr(&to->word, w);
 }
 
 // Pinned host staging for small uploads (the batched entry's job lists): a
@@ -57,7 +109,7 @@ struct Device {
   int id = -1;
   int num_sms = 0;
   cudaMemPool_t pool = nullptr;
-  uint32_t* err = nullptr;
+  CallStatus* slots = nullptr;   // device address of g_stream_status
   bool configured[4] = {false, false, false, false};
   std::vector<Staging> staging;
 };
@@ -120,15 +172,51 @@ static cudaError_t get_device(Device** out) {
     uint64_t thr = ~0ull;
     e = cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &thr);
     if (e) return e;
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_status_word);
-    if (e) return e;
-    d.err = (uint32_t*)p;
-    e = cudaMemset(d.err, 0, sizeof(uint32_t));
+    e = slot_base(id, &d.slots);
     if (e) return e;
   }
   *out = &d;
   return cudaSuccess;
+}
+
+cudaError_t stream_status_ptr(cudaStream_t st, uint32_t** out) {
+  int id;
+  cudaError_t e = cudaGetDevice(&id);
+  if (e) return e;
+  CallStatus* b;
+  if ((e = slot_base(id, &b))) return e;
+  *out = &b[slot_of(id, st, true)].word;
+  return cudaSuccess;
+}
+
+static CallOpts stream_opts(Device* d, cudaStream_t st) {
+  const int i = slot_of(d->id, st, true);
+  CallOpts o;
+  o.fold_to = &d->slots[i];
+  o.stall = 0;
+  o.spin_limit = 0;
+  if (d->id >= 0 && d->id < MAX_DEVICES) {
+    o.stall = g_slots[d->id].stall[i].load(std::memory_order_relaxed);
+    o.spin_limit = g_slots[d->id].limit[i].load(std::memory_order_relaxed);
+  }
+  return o;
+}
+
+// Zeroes the call's status block (with the list counters in front of it, one
+// memset) and applies the test settings of its waits.
+static cudaError_t begin_call(unsigned long long* counts, size_t n_counts, const CallOpts& o,
+                              cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(counts, 0, (n_counts + 2) * sizeof(unsigned long long), st);
+  if (e || (!o.stall && !o.spin_limit)) return e;
+  CallStatus cs{0u, o.stall, o.spin_limit};
+  return cudaMemcpyAsync(counts + n_counts, &cs, sizeof(cs), cudaMemcpyHostToDevice, st);
+}
+
+static cudaError_t end_call(const unsigned long long* counts, size_t n_counts, const CallOpts& o,
+                            cudaStream_t st) {
+  k_status_fold<<<1, 1, 0, st>>>((const CallStatus*)(counts + n_counts), o.fold_to);
+  add_launches(1);
+  return cudaGetLastError();
 }
 
 static cudaError_t configure(Device* d, int dt) {
@@ -321,7 +409,7 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->o_sid = c.take<uint16_t>(with_scratch ? P.n + 16 : 0);
   w->o_jobs_r2 = c.take<Job>(P.cap_r);
   w->o_jobs_r3 = c.take<Job>(P.cap_r);
-  w->o_counts = c.take<unsigned long long>(16);
+  w->o_counts = c.take<unsigned long long>(18);  // 16 counters + the call's CallStatus
   w->o_aux = c.take<uint8_t>((P.capj + 1) * 32);
   w->o_tot = c.take<unsigned long long>(4);
   w->o_l1cnt = c.take<uint32_t>(P.cap_c);
@@ -438,7 +526,7 @@ struct Events {
   } while (0)
 
 static cudaError_t enqueue_train(const Plan& P, const Bound& b, const void* keys, Device* d,
-                                 cudaStream_t st) {
+                                 uint32_t* err, cudaStream_t st) {
   TrainPlan tp;
   tp.s = P.s;
   tp.seed = P.seed;
@@ -446,11 +534,11 @@ static cudaError_t enqueue_train(const Plan& P, const Bound& b, const void* keys
   tp.L = P.L;
   tp.f0 = P.f0;
   tp.hpb = P.hpb;
-  return train_enqueue(P.dt, keys, P.n, tp, b.T, b.M, d->err, st, d->num_sms);
+  return train_enqueue(P.dt, keys, P.n, tp, b.T, b.M, err, st, d->num_sms);
 }
 
 static Level0Args level0_args(const Plan& P, const Bound& b, const Workspace& w, const void* keys,
-                              Device* d) {
+                              uint32_t* err) {
   Level0Args a;
   a.keys = keys;
   a.scratch = at<void>(w, w.o_scratch);
@@ -463,7 +551,7 @@ static Level0Args level0_args(const Plan& P, const Bound& b, const Workspace& w,
   a.offs = at<uint64_t>(w, w.o_offs);
   a.scan_status = at<void>(w, w.o_l0scan);
   a.scan_tiles = P.l0_scan_tiles;
-  a.err = d->err;
+  a.err = err;
   a.pk = at<uint32_t>(w, w.o_pk);
   a.sid = at<uint16_t>(w, w.o_sid);
   a.kf = P.kf;
@@ -474,23 +562,25 @@ static Level0Args level0_args(const Plan& P, const Bound& b, const Workspace& w,
 }
 
 static cudaError_t enqueue_sort(const Plan& P, const Workspace& w, void* keys, Device* d,
-                                cudaStream_t st, Events* ev) {
+                                cudaStream_t st, Events* ev, const CallOpts& o) {
   const Bound b = bind(P, w);
   Marks mk{ev && ev->on ? ev->ev : nullptr, NMARK};
-  LS_TRY(cudaMemsetAsync(b.counts, 0, 16 * sizeof(unsigned long long), st));
+  uint32_t* err = (uint32_t*)(b.counts + 16);  // the call's own CallStatus
+  LS_TRY(begin_call(b.counts, 16, o, st));
   mark(&mk, 0, st);
-  LS_TRY(enqueue_train(P, b, keys, d, st));
+  LS_TRY(enqueue_train(P, b, keys, d, err, st));
   mark(&mk, 1, st);
   LS_TRY(cudaMemsetAsync(at<void>(w, w.o_l0scan), 0, w.l0scan_bytes, st));
-  const Level0Args a = level0_args(P, b, w, keys, d);
+  const Level0Args a = level0_args(P, b, w, keys, err);
   LS_TRY(level0_enqueue(P.dt, a, P.smem_hist, P.smem_scatter, b.lists, P.lim, st, &mk, 2));
   LS_TRY(level1_enqueue(P.dt, keys, a.scratch, P.n, b.M, b.lists, P.lim, b.l1, P.kf, a.f0kf,
-                        a.offs, P.c.G, d->err, st, d->num_sms));
+                        a.offs, P.c.G, err, st, d->num_sms));
   mark(&mk, 6, st);
   LS_TRY(fill_enqueue(P.dt, keys, b.lists, nullptr, nullptr, st, d->num_sms));
   mark(&mk, 7, st);
   LS_TRY(buckets_enqueue(P.dt, keys, a.scratch, P.n, b.M, b.lists, P.cap1, P.cap1, P.cap1,
-                         b.counts + 8, d->err, st, d->num_sms, &mk, 8));
+                         b.counts + 8, err, st, d->num_sms, &mk, 8));
+  LS_TRY(end_call(b.counts, 16, o, st));
   mark(&mk, 10, st);
   return cudaSuccess;
 }
@@ -587,7 +677,7 @@ extern "C" {
 
 void ls_default_params(ls_params* p) {
   std::memset(p, 0, sizeof(*p));
-  p->fanout = 0;               // planner's choice (Sec. 5.1's 1000 on request)
+  p->fanout = 0;               // planner's choice (Sec. 6.1's 1000 on request)
   p->leaves = 1000;
   p->sample_div = 100;
   p->heavy_per_bucket = 0;     // planner's choice
@@ -610,8 +700,10 @@ const char* ls_status_string(ls_status s) {
   return "unknown status";
 }
 
-ls_status ls_sort_ex(void* keys, size_t n, ls_dtype dtype, void* stream, const ls_params* params,
-                     ls_stats* stats) {
+}  // extern "C"
+
+ls_status ls::sort_call(void* keys, size_t n, ls_dtype dtype, CUstream_st* stream,
+                        const ls_params* params, ls_stats* stats, const CallOpts* opts) {
   const ls_status v = validate(keys, n, dtype);
   if (v) return v;
   if (stats) std::memset(stats, 0, sizeof(*stats));
@@ -621,6 +713,7 @@ ls_status ls_sort_ex(void* keys, size_t n, ls_dtype dtype, void* stream, const l
   cudaError_t e = get_device(&d);
   if (e) return to_status(e);
   if ((e = configure(d, dtype))) return to_status(e);
+  const CallOpts o = opts ? *opts : stream_opts(d, st);
   ls_params p;
   if (params) p = *params; else ls_default_params(&p);
   Plan P;
@@ -635,7 +728,7 @@ ls_status ls_sort_ex(void* keys, size_t n, ls_dtype dtype, void* stream, const l
     for (int i = 0; i < NMARK; ++i) cudaEventCreate(&ev.ev[i]);
   }
   const unsigned long long l0 = g_launches.load();
-  e = enqueue_sort(P, w, keys, d, st, &ev);
+  e = enqueue_sort(P, w, keys, d, st, &ev, o);
   const unsigned long long l1 = g_launches.load();
   if (e == cudaSuccess && stats) {
     e = cudaStreamSynchronize(st);
@@ -647,8 +740,15 @@ ls_status ls_sort_ex(void* keys, size_t n, ls_dtype dtype, void* stream, const l
   return to_status(e);
 }
 
+extern "C" {
+
+ls_status ls_sort_ex(void* keys, size_t n, ls_dtype dtype, void* stream, const ls_params* params,
+                     ls_stats* stats) {
+  return sort_call(keys, n, dtype, (cudaStream_t)stream, params, stats, nullptr);
+}
+
 ls_status ls_sort(void* keys, size_t n, ls_dtype dtype, void* stream) {
-  return ls_sort_ex(keys, n, dtype, stream, nullptr, nullptr);
+  return sort_call(keys, n, dtype, (cudaStream_t)stream, nullptr, nullptr, nullptr);
 }
 
 // Batched sort of many independent arrays in one launch sequence.  Every job
@@ -659,6 +759,13 @@ ls_status ls_sort(void* keys, size_t n, ls_dtype dtype, void* stream) {
 // the shared in-bucket sort, fill and fallback launches.
 ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dtype dtype,
                         void* stream) {
+  return batch_call(keys, n, count, dtype, (cudaStream_t)stream, nullptr);
+}
+
+}  // extern "C"
+
+ls_status ls::batch_call(void* const* keys, const size_t* n, size_t count, ls_dtype dtype,
+                         CUstream_st* stream, const CallOpts* opts) {
   if (count > 0 && (!keys || !n)) return LS_ERR_INVALID;
   if (dtype < LS_F64 || dtype > LS_U32) return LS_ERR_INVALID;
   const int W = width_of(dtype);
@@ -674,6 +781,7 @@ ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dty
   cudaError_t e = get_device(&d);
   if (e) return to_status(e);
   if ((e = configure(d, dtype))) return to_status(e);
+  const CallOpts o = opts ? *opts : stream_opts(d, st);
   SortLimits lim;
   lim.c_tiny = 512;
   lim.c_small = 2048;
@@ -689,7 +797,7 @@ ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dty
   size_t o_list[10];
   const uint64_t caps[10] = {cap1, cap1, cap1, cap1, cap1, capj, capj, cap1, capj, cap1};
   for (int i = 0; i < 10; ++i) o_list[i] = c.take<Job>(caps[i]);
-  const size_t o_counts = c.take<unsigned long long>(16);
+  const size_t o_counts = c.take<unsigned long long>(18);  // 16 counters + the call's CallStatus
   const size_t o_aux = c.take<uint8_t>((capj + 1) * 32);
   const size_t o_tot = c.take<unsigned long long>(4);
   const size_t o_cnt = c.take<uint32_t>(cap_c);
@@ -742,7 +850,11 @@ ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dty
     else if (n[i] <= lim.c_large) { j.kind = JOB_SORT_RANGE; jl.push_back(j); }
     else { j.kind = JOB_REFINE; jr.push_back(j); }
   }
-  unsigned long long hc[16] = {0};
+  unsigned long long hc[18] = {0};  // list counters, then the call's CallStatus
+  {
+    CallStatus cs{0u, o.stall, o.spin_limit};
+    std::memcpy(&hc[16], &cs, sizeof(cs));
+  }
   hc[1] = js.size(); hc[7] = jm.size(); hc[2] = jl.size(); hc[5] = jr.size(); hc[13] = jt.size();
   // one pinned upload: the counters, then the five initial lists
   const size_t up_bytes = sizeof(hc) + (jt.size() + js.size() + jm.size() + jl.size() + jr.size()) * sizeof(Job);
@@ -794,14 +906,18 @@ ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dty
     lv[0].fmax = lv[1].fmax = MAX_F1;
     lv[2].fmax = 256;
     ModelPtrs M{};
-    e = levels_enqueue(dtype, nullptr, nullptr, N, M, lists, lim, l, lv, 3, d->err, st, d->num_sms);
+    uint32_t* err = (uint32_t*)(counts + 16);
+    e = levels_enqueue(dtype, nullptr, nullptr, N, M, lists, lim, l, lv, 3, err, st, d->num_sms);
     if (!e) e = fill_enqueue(dtype, nullptr, lists, nullptr, nullptr, st, d->num_sms);
     if (!e) e = buckets_enqueue(dtype, nullptr, nullptr, N, M, lists, cap1, cap1, cap1, counts + 8,
-                                d->err, st, d->num_sms, nullptr, 0);
+                                err, st, d->num_sms, nullptr, 0);
+    if (!e) e = end_call(counts, 16, o, st);
   }
   cudaFreeAsync(w.base, st);
   return to_status(e);
 }
+
+extern "C" {
 
 ls_status ls_sort_host(void* host_keys, size_t n, ls_dtype dtype, void* stream,
                        const ls_params* params) {
@@ -830,10 +946,18 @@ ls_status ls_stream_status(void* stream) {
   Device* d;
   cudaError_t e = get_device(&d);
   if (e) return to_status(e);
-  if ((e = cudaStreamSynchronize((cudaStream_t)stream))) return to_status(e);
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((e = cudaStreamSynchronize(st))) return to_status(e);
+  const int i = slot_of(d->id, st, false);
+  if (i < 0) return LS_OK;  // no call on this stream yet
+  uint32_t* word = &d->slots[i].word;
   uint32_t w = 0;
-  if ((e = cudaMemcpy(&w, d->err, sizeof(w), cudaMemcpyDeviceToHost))) return to_status(e);
-  if (w && (e = cudaMemset(d->err, 0, sizeof(uint32_t)))) return to_status(e);
+  if ((e = cudaMemcpyAsync(&w, word, sizeof(w), cudaMemcpyDeviceToHost, st))) return to_status(e);
+  if ((e = cudaStreamSynchronize(st))) return to_status(e);
+  if (w) {
+    if ((e = cudaMemsetAsync(word, 0, sizeof(uint32_t), st))) return to_status(e);
+    if ((e = cudaStreamSynchronize(st))) return to_status(e);
+  }
   if (w & ERR_TIMEOUT) return LS_ERR_TIMEOUT;
   if (w & ERR_BOUNDS) return LS_ERR_CUDA;
   return LS_OK;
@@ -858,7 +982,8 @@ ls_status ls_train(const void* keys, size_t n, ls_dtype dtype, void* stream,
   layout_ws(P, &w, false);
   if ((e = ws_alloc(d, &w, st))) return to_status(e);
   const Bound b = bind(P, w);
-  e = enqueue_train(P, b, keys, d, st);
+  uint32_t* err = &d->slots[slot_of(d->id, st, true)].word;
+  e = enqueue_train(P, b, keys, d, err, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) {
     DevModel hdr;
@@ -907,10 +1032,11 @@ ls_status ls_level0_histogram(const void* keys, size_t n, ls_dtype dtype, void* 
   layout_ws(P, &w, true);
   if ((e = ws_alloc(d, &w, st))) return to_status(e);
   const Bound b = bind(P, w);
+  uint32_t* err = &d->slots[slot_of(d->id, st, true)].word;
   e = cudaMemsetAsync(b.counts, 0, 16 * sizeof(unsigned long long), st);
-  if (!e) e = enqueue_train(P, b, keys, d, st);
+  if (!e) e = enqueue_train(P, b, keys, d, err, st);
   if (!e) e = cudaMemsetAsync(at<void>(w, w.o_l0scan), 0, w.l0scan_bytes, st);
-  Level0Args a0 = level0_args(P, b, w, keys, d);
+  Level0Args a0 = level0_args(P, b, w, keys, err);
   a0.may_compact = 0;  // the histogram entry point leaves `keys` as it is
   if (!e) e = level0_enqueue(P.dt, a0, P.smem_hist, P.smem_scatter,
                              b.lists, P.lim, st);
@@ -933,6 +1059,17 @@ ls_status ls_level0_histogram(const void* keys, size_t n, ls_dtype dtype, void* 
 
 uint64_t ls_kernel_launches(void) { return g_launches.load(); }
 
+ls_status ls_debug_set_wait(void* stream, uint32_t stall, uint64_t spin_limit) {
+  Device* d;
+  const cudaError_t e = get_device(&d);
+  if (e) return to_status(e);
+  if (d->id < 0 || d->id >= MAX_DEVICES) return LS_ERR_INVALID;
+  const int i = slot_of(d->id, (cudaStream_t)stream, true);
+  g_slots[d->id].stall[i].store(stall & STALL_L0_SCAN, std::memory_order_relaxed);
+  g_slots[d->id].limit[i].store(spin_limit, std::memory_order_relaxed);
+  return LS_OK;
+}
+
 ls_status ls_radix_sort_u64(uint64_t* keys, size_t count, void* stream) {
   if (count > 0 && !keys) return LS_ERR_INVALID;
   if (count < 2) return LS_OK;
@@ -953,7 +1090,8 @@ ls_status ls_radix_sort_u64(uint64_t* keys, size_t count, void* stream) {
   rw.skip = (uint32_t*)((char*)base + o_skip);
   rw.status = (uint32_t*)((char*)base + o_stat);
   rw.ctr = rw.status + rs_status_words(count);
-  e = radix_sort_u64_enqueue(keys, (uint64_t*)((char*)base + o_tmp), count, rw, d->err, st,
+  e = radix_sort_u64_enqueue(keys, (uint64_t*)((char*)base + o_tmp), count, rw,
+                             &d->slots[slot_of(d->id, st, true)].word, st,
                              d->num_sms);
   cudaFreeAsync(base, st);
   return to_status(e);
@@ -978,7 +1116,8 @@ ls_status ls_sample_sort_u64(uint64_t* keys, size_t count, void* stream) {
   sw.cnt = (uint32_t*)((char*)base + o_words);
   sw.beg = sw.cnt + (SS_NB + 1);
   sw.cur = sw.beg + (SS_NB + 1);
-  e = sample_sort_u64_enqueue(keys, (uint64_t*)((char*)base + o_tmp), count, sw, d->err, st,
+  e = sample_sort_u64_enqueue(keys, (uint64_t*)((char*)base + o_tmp), count, sw,
+                              &d->slots[slot_of(d->id, st, true)].word, st,
                               d->num_sms);
   cudaFreeAsync(base, st);
   return to_status(e);

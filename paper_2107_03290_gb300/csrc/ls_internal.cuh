@@ -7,6 +7,7 @@
 #include <cuda/atomic>
 
 #include "../../include/ls.h"
+#include "ls_call.h"
 
 namespace ls {
 
@@ -26,6 +27,23 @@ constexpr unsigned long long SPIN_LIMIT = 1ull << 26;  // bounded waits
 // Device status word bits (ls_stream_status).
 constexpr uint32_t ERR_TIMEOUT = 1u;
 constexpr uint32_t ERR_BOUNDS = 2u;
+
+// Test injection: the first tile of the level-0 look-back scan never
+// publishes its status, so the waits of the tiles after it run out.
+constexpr uint32_t STALL_L0_SCAN = 1u;
+
+__device__ __forceinline__ unsigned long long spin_limit_of(const uint32_t* err) {
+  const unsigned long long s = err ? ((const CallStatus*)err)->spin_limit : 0ull;
+  return s ? s : SPIN_LIMIT;
+}
+__device__ __forceinline__ uint32_t stall_of(const uint32_t* err) {
+  return err ? ((const CallStatus*)err)->stall : 0u;
+}
+// True once the call has recorded an error (kernels that would consume the
+// failed step's output return at once).
+__device__ __forceinline__ bool call_failed(const uint32_t* err) {
+  return err && *(volatile const uint32_t*)err != 0u;
+}
 
 // ------------------------------------------------------------------ key traits
 // Keys are handled as raw bit patterns U; tk() is the total-order key, the
@@ -342,8 +360,10 @@ inline void mark(const Marks* m, int i, cudaStream_t st) {
 }
 // Number of kernel launches the library has enqueued (diagnostics).
 void add_launches(unsigned k);
-// Device address of the current device's status word (no allocation).
-cudaError_t status_word_ptr(uint32_t** out);
+// Persistent status block of `stream` on the current device (a slot of a
+// static device array; no allocation).  Its word collects the errors of the
+// calls on that stream until ls_stream_status reads and clears it.
+cudaError_t stream_status_ptr(cudaStream_t stream, uint32_t** out);
 
 // Model storage in device memory (one per sort call / array).
 struct DevModel {

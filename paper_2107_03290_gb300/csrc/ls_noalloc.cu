@@ -9,8 +9,9 @@
 // device array, sized for at most LS_NOALLOC_RADIX_MAX keys.  Every GPU that
 // loads the library holds that array until the process exits.
 //
-// Set-up: the first call on a device looks up the array's device address with
-// cudaGetSymbolAddress while that device is current, and caches it.  That first
+// Set-up: the first call on a device looks up the array's device address (and
+// that of the library's per-stream status blocks) with cudaGetSymbolAddress
+// while that device is current, and caches it.  That first
 // call should come before any stream capture.  The host-side name of the array
 // is only a host stand-in and must never be passed to a kernel.
 //
@@ -37,7 +38,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
 struct NoallocDev {
   unsigned char* scratch = nullptr;  // device address of g_noalloc_scratch
-  uint32_t* err = nullptr;
   int num_sms = 0;
 };
 
@@ -45,7 +45,7 @@ static std::mutex g_na_mu;
 static std::map<int, NoallocDev> g_na_dev;
 
 // Per-device set-up: device address of the static array (never the host-side
-// symbol), the status word and the SM count.  No allocation.
+// symbol) and the SM count.  No allocation.
 static cudaError_t noalloc_device(NoallocDev* out) {
   int id;
   cudaError_t e = cudaGetDevice(&id);
@@ -58,8 +58,6 @@ static cudaError_t noalloc_device(NoallocDev* out) {
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e) return e;
     d.scratch = (unsigned char*)p;
-    e = status_word_ptr(&d.err);
-    if (e) return e;
     e = cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, id);
     if (e) return e;
     it = g_na_dev.emplace(id, d).first;
@@ -78,6 +76,8 @@ extern "C" ls_status ls_radix_sort_u64_noalloc(uint64_t* keys, size_t count, voi
   NoallocDev d;
   cudaError_t e = noalloc_device(&d);
   if (e) return LS_ERR_CUDA;
+  uint32_t* err = nullptr;  // the stream's status block (a static device array)
+  if ((e = stream_status_ptr((cudaStream_t)stream, &err))) return LS_ERR_CUDA;
   RsWork w;
   w.hist = (uint32_t*)(d.scratch + NA_HIST);
   w.skip = (uint32_t*)(d.scratch + NA_SKIP);
@@ -85,7 +85,7 @@ extern "C" ls_status ls_radix_sort_u64_noalloc(uint64_t* keys, size_t count, voi
   w.ctr = w.status + rs_status_words(count);
   // rs_sort_enqueue clears the histograms, look-back words and tile counters
   // (stream-ordered memsets) before its kernels read them.
-  e = rs_sort_enqueue(keys, (uint64_t*)(d.scratch + NA_TMP), count, nullptr, nullptr, w, d.err,
+  e = rs_sort_enqueue(keys, (uint64_t*)(d.scratch + NA_TMP), count, nullptr, nullptr, w, err,
                       (cudaStream_t)stream, d.num_sms);
   return e == cudaSuccess ? LS_OK : LS_ERR_CUDA;
 }

@@ -400,6 +400,8 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
   uint16_t* sinfo = (uint16_t*)(sm + lay.sinfo);   // staged keys' buckets
   uint16_t* sid = (uint16_t*)(sm + lay.sid);       // staged level-1 ids
   uint32_t* ws = (uint32_t*)(sm + lay.ws);
+  // a failed scan (a wait that gave up) leaves the write heads unusable
+  if (call_failed(a.err)) return;
   // input: the caller's array, or scratch where K2 compacted the chunks
   const bool compact = a.may_compact && a.M.hdr->compact;
   const U* keys = (const U*)a.keys;
@@ -533,6 +535,10 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
 // intervals.
 template <int DT>
 __global__ void k_classify0(Level0Args a, Lists lists, SortLimits lim) {
+  // after a failed level-0 step no job is made, so every later kernel of the
+  // call finds empty lists (the keys are then unspecified, but every access
+  // stays in bounds)
+  if (call_failed(a.err)) return;
   const uint32_t next = min(a.M.hdr->n_ext, a.n_ext_max);
   const uint32_t G = a.c.G;
   const BucketHead* heads = a.M.heads;
@@ -1084,7 +1090,7 @@ static cudaError_t level0_dt(const Level0Args& a, size_t sh, size_t ss, const Li
   const uint64_t M = (uint64_t)a.n_ext_max * a.c.G;
   k_scan<uint32_t><<<a.scan_tiles, SC_THREADS, 0, st>>>(
       a.hist, a.offs, M, nullptr, (uint64_t*)a.scan_status,
-      (uint32_t*)((uint64_t*)a.scan_status + a.scan_tiles), a.err);
+      (uint32_t*)((uint64_t*)a.scan_status + a.scan_tiles), a.err, STALL_L0_SCAN);
   mark(mk, mb + 1, st);
   if (tile == P_TILE) k_l0_scatter<DT, P_TILE><<<a.c.G, P_THREADS, ss, st>>>(a, ls_);
   else k_l0_scatter<DT, P_TILE_SMALL><<<a.c.G, P_THREADS, ss, st>>>(a, ls_);

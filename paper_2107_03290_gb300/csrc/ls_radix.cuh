@@ -1,5 +1,5 @@
 // LSD radix sort of 64-bit total-order keys (8-bit digits; a digit that every
-// key shares is skipped).  Sorts the training sample of 4-byte keys (Sec. 5.1:
+// key shares is skipped).  Sorts the training sample of 4-byte keys (Sec. 6.1:
 // the model is trained on a 1% sample, which must be in key order to give each
 // sample key its eCDF rank; their total-order keys leave four high digits
 // constant) and serves ls_radix_sort_u64.
@@ -156,11 +156,12 @@ k_rs_pass(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint64_t 
       st_release_u32(&status[tile * 256 + dg], RS_FLAG_AGG | tcnt);
       long long j = (long long)tile - 1;
       unsigned long long spins = 0;
+      const unsigned long long lim = spin_limit_of(err);
       while (j >= 0) {
         const uint32_t v = ld_acquire_u32(&status[j * 256 + dg]);
         const uint32_t f = v & ~RS_VAL;
         if (f == 0) {
-          if (++spins > SPIN_LIMIT) { set_error(err, ERR_TIMEOUT); break; }
+          if (++spins > lim) { set_error(err, ERR_TIMEOUT); break; }
           continue;
         }
         excl += v & RS_VAL;

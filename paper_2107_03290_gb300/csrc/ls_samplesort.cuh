@@ -1,4 +1,4 @@
-// Sort of the training sample (Sec. 5.1 trains the model on a 1% sample,
+// Sort of the training sample (Sec. 6.1 trains the model on a 1% sample,
 // which must be in key order to give each sample key its eCDF rank), as a
 // sample sort of 64-bit total-order keys:
 //

@@ -75,10 +75,13 @@ constexpr uint64_t SC_VAL = (1ull << 62) - 1;
 // out[i] = sum(in[0..i)), out[M] = sum(in[0..M)).  `status` holds one word per
 // tile and `tile_ctr` one counter; both must be zero at launch.  `M` is read
 // from *M_dev when M_dev != nullptr (device-known lengths); grid covers M_cap.
+// `stall_mask`: the STALL_* bit that, when set in the call's status block,
+// keeps tile 0 from publishing (test injection of a wait that runs out).
 template <typename In>
 __global__ void __launch_bounds__(SC_THREADS)
 k_scan(const In* __restrict__ in, uint64_t* __restrict__ out, uint64_t M_cap,
-       const unsigned long long* M_dev, uint64_t* status, uint32_t* tile_ctr, uint32_t* err) {
+       const unsigned long long* M_dev, uint64_t* status, uint32_t* tile_ctr, uint32_t* err,
+       uint32_t stall_mask = 0u) {
   __shared__ uint64_t ws[33];
   __shared__ uint32_t s_tile;
   __shared__ uint64_t s_excl;
@@ -106,11 +109,13 @@ k_scan(const In* __restrict__ in, uint64_t* __restrict__ out, uint64_t M_cap,
     const int lane = threadIdx.x;
     uint64_t excl = 0;
     if (tile == 0) {
-      if (lane == 0) st_release_u64(&status[0], SC_FLAG_INC | (tot & SC_VAL));
+      const bool stalled = (stall_of(err) & stall_mask) != 0u;
+      if (lane == 0 && !stalled) st_release_u64(&status[0], SC_FLAG_INC | (tot & SC_VAL));
     } else {
       if (lane == 0) st_release_u64(&status[tile], SC_FLAG_AGG | (tot & SC_VAL));
       long long win = (long long)tile - 1;
       unsigned long long spins = 0;
+      const unsigned long long lim = spin_limit_of(err);
       while (true) {
         const long long idx = win - lane;
         const uint64_t w = (idx >= 0) ? ld_acquire_u64(&status[idx]) : SC_FLAG_INC;
@@ -120,7 +125,7 @@ k_scan(const In* __restrict__ in, uint64_t* __restrict__ out, uint64_t M_cap,
         const int first_inc = inc ? __ffs(inc) - 1 : 32;
         const unsigned need = (first_inc >= 31) ? 0xffffffffu : ((2u << first_inc) - 1u);
         if (inv & need) {
-          if (++spins > SPIN_LIMIT) {
+          if (++spins > lim) {
             if (lane == 0) set_error(err, ERR_TIMEOUT);
             break;
           }

@@ -21,9 +21,9 @@
 #include <vector>
 
 #include "../../include/ls.h"
+#include "ls_call.h"
 
 namespace ls {
-cudaError_t status_word_ptr(uint32_t** out);  // the device's asynchronous error word
 constexpr uint32_t ERR_TIMEOUT_BIT = 1u, ERR_BOUNDS_BIT = 2u;
 }
 
@@ -31,7 +31,7 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-constexpr size_t SERVER_BATCH_MAX = size_t(1) << 24;  // requests this small are batched
+constexpr size_t SERVER_BATCH_MAX = LS_SERVER_BATCH_MAX;  // requests this small are batched
 
 struct Request {
   uint64_t ticket;
@@ -43,7 +43,7 @@ struct Request {
   Clock::time_point t_submit, t_launch, t_done;
   cudaEvent_t ev_start = nullptr, ev_end = nullptr;
   int stream = -1;
-  int slot = -1;          // pinned word that receives the device status after the sort
+  int slot = -1;          // the request's status block (device) and pinned word (host)
   bool done = false;
   ls_request_stats st{};
 };
@@ -62,7 +62,7 @@ struct ls_server {
   uint64_t next_ticket = 1;
   uint64_t inflight_bytes = 0;
   uint32_t rr = 0;
-  uint32_t* dev_err = nullptr;       // device error word
+  ls::CallStatus* dstat = nullptr;   // device, max_inflight blocks (one per request slot)
   uint32_t* hstat = nullptr;         // pinned, max_inflight words
   std::vector<int> free_slots;
   bool stop = false;
@@ -128,6 +128,17 @@ static void dispatcher(ls_server* s) {
                           cudaMemcpyDeviceToDevice, st);
         cudaEventRecord(r->ev_start, st);
       };
+      // each launch reports into the status block of its (first) request,
+      // cleared on the stream first; its word is copied to every request it
+      // served, behind the sort
+      auto opts = [&](int slot, cudaStream_t st) {
+        cudaMemsetAsync(&s->dstat[slot], 0, sizeof(ls::CallStatus), st);
+        ls::CallOpts o;
+        o.fold_to = &s->dstat[slot];
+        o.stall = s->cfg.debug_stall;
+        o.spin_limit = s->cfg.debug_spin_limit;
+        return o;
+      };
       for (int dt = LS_F64; dt <= LS_U32; ++dt) {  // one batched launch per key type
         std::vector<Request*> grp;
         for (Request* r : adm)
@@ -138,9 +149,13 @@ static void dispatcher(ls_server* s) {
         std::vector<void*> ptrs;
         std::vector<size_t> ns;
         for (Request* r : grp) { prologue(r, st, si); ptrs.push_back(r->keys); ns.push_back(r->n); }
-        const ls_status rc = ls_sort_batch(ptrs.data(), ns.data(), grp.size(), (ls_dtype)dt, st);
+        const int lead = grp[0]->slot;
+        const ls::CallOpts o = opts(lead, st);
+        const ls_status rc = ls::batch_call(ptrs.data(), ns.data(), grp.size(), (ls_dtype)dt, st, &o);
+        for (Request* r : grp)  // every copy before any completion event, so that
+          cudaMemcpyAsync(&s->hstat[r->slot], &s->dstat[lead].word, sizeof(uint32_t),
+                          cudaMemcpyDeviceToHost, st);  // the lead's block outlives them
         for (Request* r : grp) {
-          cudaMemcpyAsync(&s->hstat[r->slot], s->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
           cudaEventRecord(r->ev_end, st);
           if (rc != LS_OK) r->st.status = rc;
         }
@@ -150,8 +165,10 @@ static void dispatcher(ls_server* s) {
         const int si = (int)(s->rr++ % s->streams.size());
         cudaStream_t st = s->streams[si];
         prologue(r, st, si);
-        const ls_status rc = ls_sort(r->keys, r->n, r->dt, st);
-        cudaMemcpyAsync(&s->hstat[r->slot], s->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+        const ls::CallOpts o = opts(r->slot, st);
+        const ls_status rc = ls::sort_call(r->keys, r->n, r->dt, st, nullptr, nullptr, &o);
+        cudaMemcpyAsync(&s->hstat[r->slot], &s->dstat[r->slot].word, sizeof(uint32_t),
+                        cudaMemcpyDeviceToHost, st);
         cudaEventRecord(r->ev_end, st);
         if (rc != LS_OK) r->st.status = rc;
       }
@@ -180,10 +197,14 @@ ls_status ls_server_create(const ls_server_config* cfg, ls_server** out) {
   if (!s->cfg.max_queue) s->cfg.max_queue = 4096;
   if (!s->cfg.streams) s->cfg.streams = 8;
   if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return LS_ERR_CUDA; }
-  if (ls::status_word_ptr(&s->dev_err) != cudaSuccess ||
-      cudaHostAlloc((void**)&s->hstat, s->cfg.max_inflight * sizeof(uint32_t), cudaHostAllocDefault) != cudaSuccess) {
+  if (cudaMalloc((void**)&s->dstat, s->cfg.max_inflight * sizeof(ls::CallStatus)) != cudaSuccess) {
     delete s;
-    return LS_ERR_CUDA;
+    return LS_ERR_NOMEM;
+  }
+  if (cudaHostAlloc((void**)&s->hstat, s->cfg.max_inflight * sizeof(uint32_t), cudaHostAllocDefault) != cudaSuccess) {
+    cudaFree(s->dstat);
+    delete s;
+    return LS_ERR_NOMEM;
   }
   std::memset(s->hstat, 0, s->cfg.max_inflight * sizeof(uint32_t));
   for (int i = (int)s->cfg.max_inflight - 1; i >= 0; --i) s->free_slots.push_back(i);
@@ -192,6 +213,7 @@ ls_status ls_server_create(const ls_server_config* cfg, ls_server** out) {
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
       for (auto x : s->streams) cudaStreamDestroy(x);
       cudaFreeHost(s->hstat);
+      cudaFree(s->dstat);
       delete s;
       return LS_ERR_CUDA;
     }
@@ -263,6 +285,7 @@ ls_status ls_server_destroy(ls_server* s) {
   }
   for (auto x : s->streams) cudaStreamDestroy(x);
   if (s->hstat) cudaFreeHost(s->hstat);
+  if (s->dstat) cudaFree(s->dstat);
   delete s;
   return LS_OK;
 }

@@ -66,8 +66,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // Bounded wait for the phase with `parity` to complete.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* err) {
   unsigned long long spins = 0;
+  const unsigned long long lim = spin_limit_of(err);
   while (!mbar_try_wait(bar, parity)) {
-    if (++spins > SPIN_LIMIT) { set_error(err, ERR_TIMEOUT); return false; }
+    if (++spins > lim) { set_error(err, ERR_TIMEOUT); return false; }
   }
   return true;
 }

@@ -1,4 +1,4 @@
-// Sample-and-train: the RMI eCDF model of Sec. 2 / Sec. 5.1 (two layers,
+// Sample-and-train: the RMI eCDF model of Sec. 2 / Sec. 6.1 (two layers,
 // linear leaves, trained on a stratified 1% sample), plus the heavy-value set
 // that feeds the equality buckets.
 //

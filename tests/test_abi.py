@@ -47,7 +47,7 @@ def test_python_binding_covers_exports(lib):
 
 def test_defaults_and_status_strings(lib):
     p = ls.default_params()
-    # Sec. 5.1's leaves and 1% sample; fan-out and heavy count are the planner's (0)
+    # Sec. 6.1's leaves and 1% sample; fan-out and heavy count are the planner's (0)
     assert (p.fanout, p.leaves, p.sample_div, p.heavy_per_bucket) == (0, 1000, 100, 0)
     assert lib.ls_status_string(0) == b"ok"
     assert lib.ls_status_string(4) == b"device wait timed out"

@@ -85,7 +85,7 @@ def test_sample_indices_stratified(n, s):
 
 def test_sample_size_rule():
     p = oracle.params()
-    assert oracle.sample_size(1_000_000, p) == 10_000          # 1% (Sec. 5.1)
+    assert oracle.sample_size(1_000_000, p) == 10_000          # 1% (Sec. 6.1)
     assert oracle.sample_size(200_000_000, p) == 2_000_000
     assert oracle.sample_size(1000, p) == 1000                 # at least min(n, 2L)
     assert oracle.sample_size(0, p) == 0
