@@ -91,6 +91,8 @@ def _L():
             lib.lso_default_params.argtypes = [P(Params)]
             lib.lso_sort.argtypes = [vp, u64, i32, P(Params), P(Trace)]
             lib.lso_sort.restype = i32
+            lib.lso_sort_stages.argtypes = [vp, u64, i32, P(Params), P(Model), i32, P(Trace)]
+            lib.lso_sort_stages.restype = i32
             lib.lso_reference_sort.argtypes = [vp, u64, i32]
             lib.lso_reference_sort.restype = i32
             lib.lso_total_order_key.argtypes = [vp, u64, i32]
@@ -140,6 +142,20 @@ def learned_sort(keys: np.ndarray, p: Params | None = None, trace: bool = False)
     if rc != 0:
         raise RuntimeError("lso_sort failed")
     return (a, tr.as_dict()) if trace else a
+
+
+def sort_stages(keys: np.ndarray, p: Params | None = None, model: "FittedModel | None" = None,
+                touch_up: bool = True):
+    """Alg. 2 on a copy of `keys` with an optional given model and, with
+    touch_up=False, without the closing insertion sort.  Returns (array, trace)."""
+    a = np.ascontiguousarray(keys).copy()
+    tr = Trace()
+    rc = _L().lso_sort_stages(_ptr(a), a.size, DTYPES[dtype_name(a)], ctypes.byref(p or params()),
+                              ctypes.byref(model.m) if model is not None else None,
+                              int(touch_up), ctypes.byref(tr))
+    if rc != 0:
+        raise RuntimeError("lso_sort_stages failed")
+    return a, tr.as_dict()
 
 
 def reference_sort(keys: np.ndarray) -> np.ndarray:

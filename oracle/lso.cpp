@@ -221,11 +221,17 @@ void train(const typename K::T* keys, uint64_t n, const lso_params* p, lso_model
 }
 
 // ---------------------------------------------------------------- Alg. 2
+// `given`: a model to use instead of training one (nullptr: train on the
+// sample); `touch_up` = false stops before the closing insertion sort, so that
+// the arrangement left by the level-1 partitions and the counting sorts can be
+// checked on its own.
 template <class K>
-void learned_sort(typename K::T* A, uint64_t N, const lso_params* p, lso_trace* tr) {
+void learned_sort(typename K::T* A, uint64_t N, const lso_params* p, lso_trace* tr,
+                  const lso_model* given = nullptr, bool touch_up = true) {
   typedef typename K::T T;
   if (N < 2) return;
   if (N < p->n_small) {
+    if (!touch_up) return;
     const uint64_t mv = insertion_sort<K>(A, N);
     if (tr) tr->insertion_moves = mv;
     return;
@@ -235,9 +241,12 @@ void learned_sort(typename K::T* A, uint64_t N, const lso_params* p, lso_trace* 
   lso_model model;
   model.leaves = p->leaves;
   model.leaf = leafbuf.data();
-  train<K>(A, N, p, &model, nullptr);
-  if (tr) { tr->sample_size = model.s; tr->sample_finite = model.s_fin; }
-  const lso_model* M = &model;
+  const lso_model* M = given;
+  if (!M) {
+    train<K>(A, N, p, &model, nullptr);
+    if (tr) { tr->sample_size = model.s; tr->sample_finite = model.s_fin; }
+    M = &model;
+  }
   const double ff = (double)f;
 
   // Model-based partitioning, level 0.
@@ -296,6 +305,7 @@ void learned_sort(typename K::T* A, uint64_t N, const lso_params* p, lso_trace* 
     }
   }
   // Touch-up for minor prediction errors.
+  if (!touch_up) return;
   const uint64_t mv = insertion_sort<K>(A, N);
   if (tr) tr->insertion_moves = mv;
 }
@@ -445,6 +455,19 @@ int lso_sort(void* keys, uint64_t n, int dtype, const lso_params* p, lso_trace* 
     case LSO_U64: learned_sort<U64>((uint64_t*)keys, n, p, tr); return 0;
     case LSO_F32: learned_sort<F32>((float*)keys, n, p, tr); return 0;
     case LSO_U32: learned_sort<U32>((uint32_t*)keys, n, p, tr); return 0;
+  }
+  return -1;
+}
+
+int lso_sort_stages(void* keys, uint64_t n, int dtype, const lso_params* p,
+                    const lso_model* model, int touch_up, lso_trace* tr) {
+  if (tr) std::memset(tr, 0, sizeof(*tr));
+  const bool t = touch_up != 0;
+  switch (dtype) {
+    case LSO_F64: learned_sort<F64>((double*)keys, n, p, tr, model, t); return 0;
+    case LSO_U64: learned_sort<U64>((uint64_t*)keys, n, p, tr, model, t); return 0;
+    case LSO_F32: learned_sort<F32>((float*)keys, n, p, tr, model, t); return 0;
+    case LSO_U32: learned_sort<U32>((uint32_t*)keys, n, p, tr, model, t); return 0;
   }
   return -1;
 }

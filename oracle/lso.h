@@ -64,6 +64,13 @@ void lso_default_params(lso_params* p);
  * Returns 0, or -1 on a bad dtype. */
 int lso_sort(void* keys, uint64_t n, int dtype, const lso_params* p, lso_trace* tr);
 
+/* lso_sort with an optional given model (model == NULL: train on the sample;
+ * else model->leaves must equal p->leaves) and, with touch_up == 0, without
+ * the closing insertion sort: the keys are left as the level-1 partitions and
+ * the counting sorts of Alg. 2 arranged them. */
+int lso_sort_stages(void* keys, uint64_t n, int dtype, const lso_params* p,
+                    const lso_model* model, int touch_up, lso_trace* tr);
+
 /* The plain definition: std::sort by the total-order key. */
 int lso_reference_sort(void* keys, uint64_t n, int dtype);
 

@@ -285,6 +285,73 @@ def test_model_quality_bounds_touch_up_work():
     assert tr["sample_size"] == 4000 and tr["l1_partitions"] > 900
 
 
+def _one_leaf_model(a: float) -> "oracle.FittedModel":
+    """Root sends every key to leaf 0; the leaf is F(x) = clamp(a x, 0, 1)."""
+    fm = oracle.FittedModel(1)
+    fm.m.root[0], fm.m.root[1], fm.m.root[2] = 0.0, 0.0, 0.0
+    fm.leaf[0] = [a, 0.0, 0.0, 0.0, 1.0]
+    return fm
+
+
+def test_counting_sort_worked_example():
+    """Alg. 2's level-1 Partition, per-sub-bucket adj, paper-scale slots, running
+    totals and pre-decrement placement, worked by hand on 10 keys."""
+    g = {r[0]: r[1:] for r in read_golden("alg2_example.txt")}
+    inp = np.array([float(v) for v in g["input"]])
+    p = oracle.params(fanout=2, leaves=1, frag_cap=2, n_small=0)
+    fm = _one_leaf_model(0.125)
+    before, _ = oracle.sort_stages(inp, p, fm, touch_up=False)
+    assert before.tolist() == [float(v) for v in g["before_touch_up"]]
+    after, tr = oracle.sort_stages(inp, p, fm, touch_up=True)
+    assert after.tolist() == [float(v) for v in g["sorted"]]
+    assert tr["insertion_moves"] == int(g["insertion_moves"][0])
+    assert tr["l1_partitions"] == 2 and tr["counting_sorts"] == 4
+
+
+@pytest.mark.parametrize("f", [2, 4, 16])
+def test_counting_sort_exact_under_exact_model(f):
+    """Distinct keys k / N on a grid with the exact eCDF F(x) = x: level 0
+    puts key k in bucket floor(f k / N), level 1 in sub-bucket floor(f^2 k / N)
+    - i f, and the counting sort's slot (F - adj) N = k - (i f + j) N / f^2 is
+    then the key's exact rank inside its sub-bucket, so the keys come out
+    sorted before the touch-up and the insertion sort moves nothing."""
+    N = 4096
+    k = np.random.default_rng(f).permutation(N)
+    keys = k.astype(np.float64) / N
+    p = oracle.params(fanout=f, leaves=1, frag_cap=7, n_small=0)
+    before, tr = oracle.sort_stages(keys, p, _one_leaf_model(1.0), touch_up=False)
+    assert np.array_equal(before, np.arange(N) / N)
+    assert tr["counting_sorts"] == f * f
+    _, tr = oracle.sort_stages(keys, p, _one_leaf_model(1.0), touch_up=True)
+    assert tr["insertion_moves"] == 0
+
+
+def test_counting_sort_orders_all_but_shared_slots():
+    """Before the touch-up, with a trained model and a small fan-out (large
+    sub-buckets, so that the counting sort does the ordering): the keys run in
+    (bucket, sub-bucket, slot) order, and a key is above its successor only
+    when both share all three (the insertion sort's only work)."""
+    a = lsgen.uniform_f64(40_000, 33)
+    f, N = 4, a.size
+    p = oracle.params(fanout=f, leaves=64, n_small=0)
+    fm = oracle.train(a, p)
+    before, tr = oracle.sort_stages(a, p, fm, touch_up=False)
+    assert np.array_equal(np.sort(before), np.sort(a))
+    assert tr["counting_sorts"] == f * f
+    F = np.array([fm.predict(float(x)) for x in before])
+    i = np.clip(np.floor(F * f), 0, f - 1)
+    j = np.clip(np.floor(F * f * f) - i * f, 0, f - 1)
+    sub = (i * f + j).astype(np.int64)
+    n1 = np.bincount(sub, minlength=f * f)[sub]
+    slot = np.clip(np.floor((F - sub / (f * f)) * N), 0, n1 - 1).astype(np.int64)
+    key = sub * N + slot                              # (bucket, sub-bucket, slot)
+    assert np.all(np.diff(key) >= 0)
+    desc = np.flatnonzero(before[1:] < before[:-1])
+    assert desc.size > 0 and np.all(key[desc] == key[desc + 1])
+    out, tr = oracle.sort_stages(a, p, fm, touch_up=True)
+    assert np.array_equal(out, np.sort(a))
+
+
 # --------------------------------------------------------------------- spec functions
 def _eval_for(a, L=128, f0=1000):
     fm = oracle.train(a, oracle.params(leaves=L))
