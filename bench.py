@@ -344,6 +344,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="zipf_lognormal_200m_f64", choices=list(lsgen.WORKLOADS))
     ap.add_argument("--n", type=int, default=0)
+    ap.add_argument("--fanout", type=int, default=None,
+                    help="level-0 fan-out (default: 1000 for normal_1m_f64, else the planner's)")
+    ap.add_argument("--leaves", type=int, default=1000)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=10_000_000)
     ap.add_argument("--ref-sample", type=int, default=2_000_000)
@@ -379,9 +382,15 @@ def main():
     work = torch.empty_like(pristine)
     stream = torch.cuda.current_stream()
 
+    # the 1M-key latency case runs with the stated configuration (fan-out 1000,
+    # 1000 leaves, 1% sample; Sec. 6.1); the 200M-key workloads with the
+    # planner's fan-out unless --fanout is given
+    fanout = args.fanout if args.fanout is not None else (1000 if args.workload == "normal_1m_f64" else 0)
+    prm = ls.default_params(fanout=fanout, leaves=args.leaves)
+
     def step(stats=True):
         work.copy_(pristine)
-        return ls.sort_(work, stats=stats)
+        return ls.sort_(work, prm, stats=stats)
 
     for _ in range(args.warmup):
         step()
@@ -396,20 +405,33 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    per = []
-    launches = 0
+    # timed steps: CUDA events on the launching stream around each ls_sort call
+    # (no per-phase events inside the call); the input is restored before each
+    # step, outside the events
+    step_ms = []
+    l_before = ls.kernel_launches()
     with Clocks(local) as clk:
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            st = step()
-            per.append(st)
-            launches += st["n_launches"]
+            work.copy_(pristine)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ls.sort_(work, prm)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         if dist:
             dist.barrier()
-    dev_ms = float(np.mean([s["ms_total"] for s in per]))
+    launches = ls.kernel_launches() - l_before
+    dev_ms = float(np.mean(step_ms))
     value, tmax = replica_throughput(dev_ms, n, dist, "cuda")
+    # per-phase times from separate, untimed calls with statistics (events
+    # between the phases)
+    per = [step() for _ in range(max(3, min(10, args.steps)))]
+    torch.cuda.synchronize()
 
     # per-kernel times and the roofline of the dominant kernel
     ks = ["ms_train", "ms_hist", "ms_scan", "ms_scatter", "ms_classify", "ms_level1", "ms_fill",
@@ -474,12 +496,15 @@ def main():
                           "l2": ("inputs larger than L2 (restored from a device copy each step)"
                                  if n * w > L2_BYTES else
                                  "inputs fit in L2 (latency case; restored from a device copy each step)"),
-                          "parallelism": "replicas" if world > 1 else "single"},
+                          "parallelism": "replicas" if world > 1 else "single",
+                          "fanout": per[-1]["fanout"], "leaves": per[-1]["leaves"],
+                          "sample": per[-1]["sample_size"]},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": int(launches), "clocks": clk.summary(),
                "wall_ms_per_step": 1000 * wall / args.steps, "correct": ok,
-               "ms_p50": float(np.median([x["ms_total"] for x in per])),
-               "ms_min": float(np.min([x["ms_total"] for x in per])),
+               "ms_p50": float(np.median(step_ms)),
+               "ms_min": float(np.min(step_ms)),
+               "ms_with_phase_events": float(np.mean([x["ms_total"] for x in per])),
                "kernels_ms": kms, "batched": batched, "serving": serving,
                "path": {k: last[k] for k in ("n_heavy", "n_ext", "max_bucket", "n_eq_keys",
                                              "n_level1", "n_segments", "n_fallback", "n_fill",

@@ -91,6 +91,7 @@ void add_launches(unsigned k) { g_launches.fetch_add(k, std::memory_order_relaxe
 
 // ORs a call's error word into its persistent block (stream or request).
 __global__ void k_status_fold(const CallStatus* __restrict__ local, CallStatus* to) {
+  pdl_begin();
   const uint32_t w = local->word;
   if (w) atomicOr(&to->word, w);
 }
@@ -214,7 +215,7 @@ static cudaError_t begin_call(unsigned long long* counts, size_t n_counts, const
 
 static cudaError_t end_call(const unsigned long long* counts, size_t n_counts, const CallOpts& o,
                             cudaStream_t st) {
-  k_status_fold<<<1, 1, 0, st>>>((const CallStatus*)(counts + n_counts), o.fold_to);
+  launch_k(k_status_fold, 1, 1, 0, st, (const CallStatus*)(counts + n_counts), o.fold_to);
   add_launches(1);
   return cudaGetLastError();
 }

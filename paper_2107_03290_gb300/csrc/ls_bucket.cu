@@ -117,7 +117,12 @@ __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* 
     mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   }
   if (threadIdx.x == 0) { ss.tmin = ~0ull; ss.tmax = 0; ss.nbig = 0; ss.all = 0; }
-  for (uint32_t i = threadIdx.x; i <= m; i += THREADS) cnt[i] = 0;
+  // every thread owns KPT consecutive counters (16-byte stores; the slots
+  // beyond m stay zero, so the scan leaves m in them)
+  static_assert(KPT % 4 == 0, "KPT counters per thread in 16-byte groups");
+  uint4* cnt4 = (uint4*)cnt + threadIdx.x * (KPT / 4);
+#pragma unroll
+  for (int v = 0; v < KPT / 4; ++v) cnt4[v] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   if (lane == 0) { atomicMin(&ss.tmin, mn); atomicMax(&ss.tmax, mx); }
   __syncthreads();
@@ -165,17 +170,22 @@ __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* 
     sr[k] = v;
   }
   __syncthreads();
-  {
-    const int per = (int)((m + THREADS - 1) / THREADS);
-    const int b = threadIdx.x * per;
+  {  // exclusive scan of the CAP counters (the running totals of Alg. 2)
+    uint32_t c[KPT];
+#pragma unroll
+    for (int v = 0; v < KPT / 4; ++v) {
+      const uint4 q = cnt4[v];
+      c[4 * v] = q.x; c[4 * v + 1] = q.y; c[4 * v + 2] = q.z; c[4 * v + 3] = q.w;
+    }
     uint32_t s = 0;
-    for (int i = 0; i < per; ++i)
-      if (b + i < (int)m) s += cnt[b + i];
+#pragma unroll
+    for (int i = 0; i < KPT; ++i) { const uint32_t t = c[i]; c[i] = s; s += t; }
     unsigned long long tot;
-    unsigned long long run = block_excl_sum<unsigned long long>(s, ws, &tot);
-    for (int i = 0; i < per; ++i)
-      if (b + i < (int)m) { const uint32_t t = cnt[b + i]; cnt[b + i] = (uint32_t)run; run += t; }
-    if (threadIdx.x == 0) cnt[m] = m;
+    const uint32_t run = (uint32_t)block_excl_sum<unsigned long long>(s, ws, &tot);
+#pragma unroll
+    for (int v = 0; v < KPT / 4; ++v)
+      cnt4[v] = make_uint4(run + c[4 * v], run + c[4 * v + 1], run + c[4 * v + 2], run + c[4 * v + 3]);
+    if (threadIdx.x == 0) cnt[C::CAP] = m;
     __syncthreads();
   }
 #pragma unroll
@@ -241,6 +251,7 @@ template <int DT, int THREADS, int KPT>
 __global__ void __launch_bounds__(THREADS, THREADS == 512 ? (KPT == 8 ? 3 : 2) : (KPT == 16 ? 3 : (THREADS == 128 ? 8 : 4)))
 k_bucket_sort(typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, ModelPtrs M,
               JobList list, unsigned long long* ctr, uint32_t* err) {
+  pdl_begin();
   typedef typename KT<DT>::U U;
   typedef BucketCfg<DT, THREADS, KPT> C;
   extern __shared__ __align__(16) unsigned char sm[];
@@ -276,6 +287,7 @@ template <int DT>
 __global__ void __launch_bounds__(512)
 k_fallback(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, ModelPtrs M, JobList list,
            unsigned long long* ctr, uint32_t* err) {
+  pdl_begin();
   typedef typename KT<DT>::U U;
   typedef BucketCfg<DT, 512, 16> C;
   extern __shared__ __align__(16) unsigned char sm[];
@@ -425,25 +437,17 @@ static cudaError_t buckets_dt(void* keys, void* scratch, const ModelPtrs& M, con
   const unsigned gf = (unsigned)std::min<uint64_t>(std::max<uint64_t>(cap_fb, 1), 1ull * num_sms);
   {
     const unsigned gt = (unsigned)std::min<uint64_t>(std::max<uint64_t>(cap_s, 1), 16ull * num_sms);
-    k_bucket_sort<DT, BS_TINY_T, BS_TINY_K>
-        <<<gt, BS_TINY_T, BucketCfg<DT, BS_TINY_T, BS_TINY_K>::SMEM, st>>>(
-            (U*)keys, (const U*)scratch, M, lists.sort_t, ctrs + 6, err);
+    launch_k(k_bucket_sort<DT, BS_TINY_T, BS_TINY_K>, gt, BS_TINY_T, BucketCfg<DT, BS_TINY_T, BS_TINY_K>::SMEM, st, (U*)keys, (const U*)scratch, M, lists.sort_t, ctrs + 6, err);
   }
-  k_bucket_sort<DT, BS_SMALL_T, BS_SMALL_K>
-      <<<gs, BS_SMALL_T, BucketCfg<DT, BS_SMALL_T, BS_SMALL_K>::SMEM, st>>>(
-          (U*)keys, (const U*)scratch, M, lists.sort_s, ctrs + 0, err);
+  launch_k(k_bucket_sort<DT, BS_SMALL_T, BS_SMALL_K>, gs, BS_SMALL_T, BucketCfg<DT, BS_SMALL_T, BS_SMALL_K>::SMEM, st, (U*)keys, (const U*)scratch, M, lists.sort_s, ctrs + 0, err);
   mark(mk, mb + 0, st);
   {
     const unsigned gm = (unsigned)std::min<uint64_t>(std::max<uint64_t>(cap_s, 1), 4ull * num_sms);
-    k_bucket_sort<DT, BS_MID_T, BS_MID_K>
-        <<<gm, BS_MID_T, BucketCfg<DT, BS_MID_T, BS_MID_K>::SMEM, st>>>(
-            (U*)keys, (const U*)scratch, M, lists.sort_m, ctrs + 3, err);
+    launch_k(k_bucket_sort<DT, BS_MID_T, BS_MID_K>, gm, BS_MID_T, BucketCfg<DT, BS_MID_T, BS_MID_K>::SMEM, st, (U*)keys, (const U*)scratch, M, lists.sort_m, ctrs + 3, err);
   }
-  k_bucket_sort<DT, BS_LARGE_T, BS_LARGE_K>
-      <<<gl, BS_LARGE_T, BucketCfg<DT, BS_LARGE_T, BS_LARGE_K>::SMEM, st>>>(
-          (U*)keys, (const U*)scratch, M, lists.sort_l, ctrs + 1, err);
+  launch_k(k_bucket_sort<DT, BS_LARGE_T, BS_LARGE_K>, gl, BS_LARGE_T, BucketCfg<DT, BS_LARGE_T, BS_LARGE_K>::SMEM, st, (U*)keys, (const U*)scratch, M, lists.sort_l, ctrs + 1, err);
   mark(mk, mb + 1, st);
-  k_fallback<DT><<<gf, 512, BucketCfg<DT, 512, 16>::SMEM_FB, st>>>((U*)keys, (U*)scratch, M,
+  launch_k(k_fallback<DT>, gf, 512, BucketCfg<DT, 512, 16>::SMEM_FB, st, (U*)keys, (U*)scratch, M,
                                                                   lists.fallback, ctrs + 2, err);
   add_launches(5);
   return cudaGetLastError();

@@ -45,6 +45,36 @@ __device__ __forceinline__ bool call_failed(const uint32_t* err) {
   return err && *(volatile const uint32_t*)err != 0u;
 }
 
+// ------------------------------------------------------------------ launches
+// Every kernel of the library is launched with programmatic stream
+// serialization (programmatic dependent launch): the next kernel on the
+// stream is scheduled as soon as the CTAs of the previous one have exited,
+// without waiting for the grid's completion to be signalled, which hides most
+// of the launch gap between the many short kernels of one call.  Each kernel
+// therefore begins with pdl_begin(): it waits until the previous grid on the
+// stream has completed and its memory is visible, before touching any memory.
+// (No kernel triggers its dependents early: measured, letting the next
+// kernel's CTAs occupy the SMs during the previous kernel's last wave made the
+// training kernels slower.)  Launched without the attribute, the wait does
+// nothing.
+__device__ __forceinline__ void pdl_begin() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... P, typename... A>
+inline cudaError_t launch_k(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t st, A&&... args) {
+  cudaLaunchConfig_t c{};
+  c.gridDim = grid;
+  c.blockDim = block;
+  c.dynamicSmemBytes = smem;
+  c.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  c.attrs = at;
+  c.numAttrs = 1;
+  return cudaLaunchKernelEx(&c, kernel, static_cast<P>(args)...);
+}
+
 // ------------------------------------------------------------------ key traits
 // Keys are handled as raw bit patterns U; tk() is the total-order key, the
 // ordering contract of ls.h (Sec. 4.2: the output is monotonically ordered).

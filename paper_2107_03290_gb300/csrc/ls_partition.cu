@@ -33,7 +33,7 @@ namespace ls {
 
 struct L0Layout {
   uint32_t bar, buf, pbuf, thr, cell, cleaf, heads, htk, cnt, ecnt, soff, cursor, gbase, sinfo, sid,
-      ws, hkey, hval, queue, total;
+      ws, hkey, hval, queue, tiles, total;
   uint32_t hs;           // K2: heavy values per bucket row (power of two > per-bucket maximum)
 };
 
@@ -56,6 +56,7 @@ constexpr int H_KPT = 6;             // keys per thread and step of K2
 static int key_width(int dt) { return (dt == LS_F64 || dt == LS_U64) ? 8 : 4; }
 
 constexpr int QCAP = 64;              // K2 per-warp queue of keys missing the heavy table
+constexpr int H_TILE = H_THREADS * H_KPT;  // K2 keys per TMA tile (calls without heavy values)
 
 static L0Layout l0_layout_hist(int W, uint32_t L, uint32_t f0, uint32_t next, uint32_t hmax,
                                bool cleaf_shared = true, bool hashed = true) {
@@ -72,12 +73,21 @@ static L0Layout l0_layout_hist(int W, uint32_t L, uint32_t f0, uint32_t next, ui
   y.htk = (uint32_t)o; o += (size_t)f0 * y.hs * 8;
   y.cnt = (uint32_t)o; o += (size_t)(next + 1) * 4;
   al(8); y.ws = (uint32_t)o; o += 33 * 8;
+  y.bar = (uint32_t)o; o += 16;  // two mbarriers of the TMA tiles
+  // The rest holds either the heavy table with the miss queues (the HASHED
+  // instantiation) or the double-buffered TMA key tiles (the other one, in
+  // calls without heavy values): the two kernels never use both.
+  al(128);
+  const size_t rest = o;
   y.hkey = y.hval = y.queue = NOT_SHARED;
   if (hashed && y.hs) {  // heavy table and per-warp miss queues
     al(16); y.hkey = (uint32_t)o; o += (size_t)HASH_SIZE * 8;
     y.hval = (uint32_t)o; o += (size_t)HASH_SIZE * 2;
     al(16); y.queue = (uint32_t)o; o += (size_t)(H_THREADS / 32) * QCAP * (W + 4);
   }
+  const size_t tiles_end = rest + 2ull * H_TILE * W;
+  y.tiles = tiles_end <= L0_SMEM_LIMIT ? (uint32_t)rest : NOT_SHARED;
+  if (y.tiles != NOT_SHARED && tiles_end > o) o = tiles_end;
   y.total = (uint32_t)o;
   if (hashed && y.hs && o > L0_SMEM_LIMIT) return l0_layout_hist(W, L, f0, next, hmax, cleaf_shared, false);
   if (cleaf_shared && o > L0_SMEM_LIMIT) return l0_layout_hist(W, L, f0, next, hmax, false, false);
@@ -203,11 +213,32 @@ __device__ __forceinline__ uint32_t classify_key(typename KT<DT>::U u, const L0M
   return e;
 }
 
+// Bucket and packed id of a key in a call without heavy values (every bucket
+// is one slot: e = b).
+template <int DT>
+__device__ __forceinline__ uint32_t classify_plain(typename KT<DT>::U u, const L0Map& q,
+                                                   float f0kf, uint32_t kf, uint32_t* packed) {
+  const float F = cell_F<DT>(u, q.croot, q.cleaf);
+  const float v = F * (float)L0_CELLS;
+  const uint32_t cl = v >= 0.0f ? (v < (float)L0_CELLS ? (uint32_t)v : L0_CELLS - 1) : 0u;
+  const uint32_t r = q.cell[cl];
+  const uint32_t b = min(thr_search(q.thr, r & 0xFFFFu, r >> 16, KT<DT>::tk(u)), q.pos_max);
+  const float w = F * f0kf;
+  int sub = (w >= 0.0f ? (int)w : 0) - (int)(b * kf);
+  sub = sub < 0 ? 0 : (sub >= (int)kf ? (int)kf - 1 : sub);
+  *packed = b | (uint32_t)sub << PK_B_BITS;
+  return b;
+}
+
 // Two instantiations, launched back to back: HASHED handles calls whose
 // heavy table is present (decided on the device by training), the other the
-// rest; each returns at once when the call is not its kind.
+// rest; each returns at once when the call is not its kind.  In a call
+// without heavy values the other one streams the chunk's keys through shared
+// memory in double-buffered TMA tiles (the copy of the next tile overlaps the
+// model evaluation of the current one).
 template <int DT, bool HASHED>
 __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout lay) {
+  pdl_begin();
   typedef typename KT<DT>::U U;
   extern __shared__ __align__(128) unsigned char sm[];
   BucketHead* heads = (BucketHead*)(sm + lay.heads);
@@ -247,6 +278,47 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
       pk[nb + k] = p;
       if (compact) keys_w[nb + k] = x;  // K4 reads every key from scratch
     }
+  }
+  if (!HASHED && H == 0 && lay.tiles != NOT_SHARED) {
+    // body chunk [cb, ce): 16-byte aligned, a multiple of 4 keys (as is every
+    // tile), so each tile is one bulk copy
+    TileStream<U, H_TILE> ts;
+    ts.buf = (U*)(sm + lay.tiles);
+    ts.bar = (uint64_t*)(sm + lay.bar);
+    ts.src = keys + cb;
+    ts.len = ce - cb;
+    ts.nt = (uint32_t)((ts.len + H_TILE - 1) / H_TILE);
+    if (threadIdx.x == 0) ts.init();
+    __syncthreads();
+    if (threadIdx.x == 0) { ts.issue(0); ts.issue(1); }
+    for (uint32_t t = 0; t < ts.nt; ++t) {
+      const U* tb = ts.wait(t, a.err);
+      const uint32_t c = ts.count(t);
+      uint32_t* pko = pk + (cb - a0) + (uint64_t)t * H_TILE;
+      // every key of the step is classified before any counter is touched, so
+      // that the table lookups of the six keys overlap (a shared-memory
+      // atomic between them would order the loads)
+      uint32_t ee[H_KPT], pp[H_KPT];
+#pragma unroll
+      for (int k = 0; k < H_KPT; ++k) {
+        const uint32_t i = k * H_THREADS + threadIdx.x;
+        ee[k] = classify_plain<DT>(tb[i < c ? i : 0], q, a.f0kf, a.kf, &pp[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < H_KPT; ++k) {
+        const uint32_t i = k * H_THREADS + threadIdx.x;
+        if (i < c) {
+          if (ee[k] < next) atomicAdd(&cnt[ee[k]], 1u); else set_error(a.err, ERR_BOUNDS);
+          pko[i] = pp[k];
+        }
+      }
+      __syncthreads();  // every thread is done with buffer t & 1 before it is refilled
+      if (threadIdx.x == 0) ts.issue(t + 2);
+    }
+    __syncthreads();
+    for (uint32_t e = threadIdx.x; e < a.n_ext_max; e += H_THREADS)
+      a.hist[(size_t)e * a.c.G + g] = e < next ? cnt[e] : 0u;
+    return;
   }
   const int lane = threadIdx.x & 31;
   // Heavy table path: a key equal to a heavy value is counted from one table
@@ -387,6 +459,7 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
 // Equality keys are skipped (their slots are filled later).
 template <int DT, int TILE>
 __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Layout lay) {
+  pdl_begin();
   typedef typename KT<DT>::U U;
   constexpr int KPT = TILE / P_THREADS;
   extern __shared__ __align__(128) unsigned char sm[];
@@ -535,6 +608,7 @@ __global__ void __launch_bounds__(P_THREADS, 1) k_l0_scatter(Level0Args a, L0Lay
 // intervals.
 template <int DT>
 __global__ void k_classify0(Level0Args a, Lists lists, SortLimits lim) {
+  pdl_begin();
   // after a failed level-0 step no job is made, so every later kernel of the
   // call finds empty lists (the keys are then unspecified, but every access
   // stays in bounds)
@@ -636,6 +710,7 @@ template <typename U>
 __global__ void __launch_bounds__(256) k_fill(U* __restrict__ keys, JobList small, JobList big,
                                               const unsigned long long* __restrict__ from,
                                               const unsigned long long* __restrict__ upto) {
+  pdl_begin();
   __shared__ uint32_t pre[FILL_MAXJ + 1];
   __shared__ uint32_t ws[33];
   // jobs [s0, s1) of `small` and [b0, b1) of `big`: from / upto hold {small, big}
@@ -743,6 +818,7 @@ __device__ __forceinline__ uint32_t range_sub(typename KT<DT>::U u, const RangeS
 
 __global__ void __launch_bounds__(1024)
 k_l1_plan(LevelArgs la, SortLimits lim, Level1Ws w, uint32_t* err) {
+  pdl_begin();
   __shared__ uint64_t ws[33];
   __shared__ uint64_t s_rt, s_rc;
   L1Aux* aux = (L1Aux*)w.aux;
@@ -839,6 +915,7 @@ template <int DT>
 __global__ void __launch_bounds__(L1_THREADS, 4)
 k_l1_minmax(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, LevelArgs la,
             Level1Ws w) {
+  pdl_begin();
   typedef typename KT<DT>::U U;
   __shared__ unsigned long long s_min, s_max;
   const L1Aux* aux = (const L1Aux*)w.aux;
@@ -876,6 +953,7 @@ template <int DT>
 __global__ void __launch_bounds__(L1_THREADS, 4)
 k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, ModelPtrs M,
           LevelArgs la, Level1Ws w) {
+  pdl_begin();
   typedef typename KT<DT>::U U;
   __shared__ uint32_t hc[MAX_F1];
   const L1Aux* aux = (const L1Aux*)w.aux;
@@ -939,6 +1017,7 @@ k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Mod
 // exactly as the level-0 pass computes a key's), and its keys start where the
 // level-0 offsets put the interval.
 __global__ void k_l1_cursor(LevelArgs la, Level1Ws w, ModelPtrs M) {
+  pdl_begin();
   const L1Aux* aux = (const L1Aux*)w.aux;
   const uint64_t C = w.totals[1], nj = w.totals[2];
   for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < C;
@@ -972,6 +1051,7 @@ template <int DT>
 __global__ void __launch_bounds__(L1_THREADS)
 k_l1_scatter(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, uint64_t n, ModelPtrs M,
              LevelArgs la, Level1Ws w, uint32_t* err) {
+  pdl_begin();
   typedef typename KT<DT>::U U;
   constexpr int KPT = L1_TILE / L1_THREADS;
   __shared__ uint32_t lc[MAX_F1 + 1];
@@ -1042,6 +1122,7 @@ k_l1_scatter(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, uint64_t n, 
 template <int DT>
 __global__ void k_l1_classify(Lists lists, LevelArgs la, SortLimits lim, Level1Ws w, ModelPtrs M,
                               int L, uint32_t* err) {
+  pdl_begin();
   const L1Aux* aux = (const L1Aux*)w.aux;
   const uint64_t C = w.totals[1], nj = w.totals[2];
   for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < C;
@@ -1084,18 +1165,17 @@ static cudaError_t level0_dt(const Level0Args& a, size_t sh, size_t ss, const Li
   const L0Layout lh = l0_layout_hist(W, a.L, a.f0, a.n_ext_max, hmax);
   const int tile = scatter_tile(W, a.f0, hmax);
   const L0Layout ls_ = l0_layout_scatter(W, a.f0, hmax, tile);
-  k_l0_hist<DT, false><<<a.c.G, H_THREADS, sh, st>>>(a, lh);
-  if (lh.hkey != NOT_SHARED) k_l0_hist<DT, true><<<a.c.G, H_THREADS, sh, st>>>(a, lh);
+  launch_k(k_l0_hist<DT, false>, a.c.G, H_THREADS, sh, st, a, lh);
+  if (lh.hkey != NOT_SHARED) launch_k(k_l0_hist<DT, true>, a.c.G, H_THREADS, sh, st, a, lh);
   mark(mk, mb + 0, st);
   const uint64_t M = (uint64_t)a.n_ext_max * a.c.G;
-  k_scan<uint32_t><<<a.scan_tiles, SC_THREADS, 0, st>>>(
-      a.hist, a.offs, M, nullptr, (uint64_t*)a.scan_status,
+  launch_k(k_scan<uint32_t>, a.scan_tiles, SC_THREADS, 0, st, a.hist, a.offs, M, nullptr, (uint64_t*)a.scan_status,
       (uint32_t*)((uint64_t*)a.scan_status + a.scan_tiles), a.err, STALL_L0_SCAN);
   mark(mk, mb + 1, st);
-  if (tile == P_TILE) k_l0_scatter<DT, P_TILE><<<a.c.G, P_THREADS, ss, st>>>(a, ls_);
-  else k_l0_scatter<DT, P_TILE_SMALL><<<a.c.G, P_THREADS, ss, st>>>(a, ls_);
+  if (tile == P_TILE) launch_k(k_l0_scatter<DT, P_TILE>, a.c.G, P_THREADS, ss, st, a, ls_);
+  else launch_k(k_l0_scatter<DT, P_TILE_SMALL>, a.c.G, P_THREADS, ss, st, a, ls_);
   mark(mk, mb + 2, st);
-  k_classify0<DT><<<(a.n_ext_max + 255) / 256, 256, 0, st>>>(a, lists, lim);
+  launch_k(k_classify0<DT>, (a.n_ext_max + 255) / 256, 256, 0, st, a, lists, lim);
   mark(mk, mb + 3, st);
   add_launches(lh.hkey != NOT_SHARED ? 5 : 4);
   return cudaGetLastError();
@@ -1144,18 +1224,16 @@ static cudaError_t level_dt(void* keys, void* scratch, uint64_t n, const ModelPt
   typedef typename KT<DT>::U U;
   cudaError_t e = cudaMemsetAsync(w.scan_status, 0, w.scan_status_bytes, st);
   if (e) return e;
-  k_l1_plan<<<1, 1024, 0, st>>>(la, lim, w, err);
+  launch_k(k_l1_plan, 1, 1024, 0, st, la, lim, w, err);
   const int grid = 4 * num_sms;  // the histogram and range passes hold 4 CTAs per SM
-  if (la.mode) k_l1_minmax<DT><<<grid, L1_THREADS, 0, st>>>((const U*)keys, (const U*)scratch, la, w);
-  k_l1_hist<DT><<<grid, L1_THREADS, 0, st>>>((const U*)keys, (const U*)scratch, M, la, w);
+  if (la.mode) launch_k(k_l1_minmax<DT>, grid, L1_THREADS, 0, st, (const U*)keys, (const U*)scratch, la, w);
+  launch_k(k_l1_hist<DT>, grid, L1_THREADS, 0, st, (const U*)keys, (const U*)scratch, M, la, w);
   const unsigned tiles = (unsigned)std::max<uint64_t>(1, (w.cap_c + SC_TILE - 1) / SC_TILE);
-  k_scan<uint32_t><<<tiles, SC_THREADS, 0, st>>>(w.cnt, w.off, w.cap_c, &w.totals[1],
-                                                 (uint64_t*)w.scan_status,
-                                                 (uint32_t*)((uint64_t*)w.scan_status + tiles), err);
-  k_l1_cursor<<<grid, 256, 0, st>>>(la, w, M);
-  k_l1_scatter<DT><<<grid, L1_THREADS, l1_scatter_smem(KT<DT>::W), st>>>(
-      (U*)keys, (U*)scratch, n, M, la, w, err);
-  k_l1_classify<DT><<<grid, 256, 0, st>>>(lists, la, lim, w, M, M.L, err);
+  launch_k(k_scan<uint32_t>, tiles, SC_THREADS, 0, st, w.cnt, w.off, w.cap_c, &w.totals[1],
+           (uint64_t*)w.scan_status, (uint32_t*)((uint64_t*)w.scan_status + tiles), err, 0u);
+  launch_k(k_l1_cursor, grid, 256, 0, st, la, w, M);
+  launch_k(k_l1_scatter<DT>, grid, L1_THREADS, l1_scatter_smem(KT<DT>::W), st, (U*)keys, (U*)scratch, n, M, la, w, err);
+  launch_k(k_l1_classify<DT>, grid, 256, 0, st, lists, la, lim, w, M, M.L, err);
   add_launches(la.mode ? 7 : 6);
   return cudaGetLastError();
 }
@@ -1206,9 +1284,9 @@ cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const 
 cudaError_t fill_enqueue(int dt, void* keys, const Lists& lists, const unsigned long long* from,
                          const unsigned long long* upto, cudaStream_t st, int num_sms) {
   if (dt == LS_F64 || dt == LS_U64)
-    k_fill<uint64_t><<<4 * num_sms, 256, 0, st>>>((uint64_t*)keys, lists.fill, lists.fill_big, from, upto);
+    launch_k(k_fill<uint64_t>, 4 * num_sms, 256, 0, st, (uint64_t*)keys, lists.fill, lists.fill_big, from, upto);
   else
-    k_fill<uint32_t><<<4 * num_sms, 256, 0, st>>>((uint32_t*)keys, lists.fill, lists.fill_big, from, upto);
+    launch_k(k_fill<uint32_t>, 4 * num_sms, 256, 0, st, (uint32_t*)keys, lists.fill, lists.fill_big, from, upto);
   add_launches(1);
   return cudaGetLastError();
 }

@@ -72,6 +72,7 @@ __device__ __forceinline__ void rs_rank_tile(RsShared& sh, const uint64_t* key, 
 static __global__ void k_rs_hist(const uint64_t* __restrict__ keys, uint64_t m_cap,
                           const uint64_t* m_dev, const uint64_t* off_dev,
                           uint32_t* __restrict__ hist) {
+  pdl_begin();
   __shared__ uint32_t h[8][256];
   const uint64_t m = m_dev ? *m_dev : m_cap;
   const uint64_t off = off_dev ? *off_dev : 0;
@@ -94,6 +95,7 @@ static __global__ void k_rs_hist(const uint64_t* __restrict__ keys, uint64_t m_c
 // holds every key (the pass would be the identity).
 static __global__ void k_rs_digit_scan(uint32_t* hist, uint32_t* skip, uint64_t m_cap,
                                 const uint64_t* m_dev) {
+  pdl_begin();
   __shared__ uint32_t ws[33];
   const uint64_t m = m_dev ? *m_dev : m_cap;
   for (int d = 0; d < 8; ++d) {
@@ -115,6 +117,7 @@ k_rs_pass(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint64_t 
           const uint64_t* m_dev, const uint64_t* off_dev, int d,
           const uint32_t* __restrict__ digit_off, const uint32_t* skip, uint32_t* status,
           uint32_t* tile_ctr, uint32_t* err) {
+  pdl_begin();
   __shared__ RsShared sh;
   const uint64_t m = m_dev ? *m_dev : m_cap;
   const uint64_t off = off_dev ? *off_dev : 0;
@@ -202,12 +205,12 @@ inline cudaError_t rs_sort_enqueue(uint64_t* a, uint64_t* b, uint64_t m_cap, con
   int hb = (int)((m_cap + 4095) / 4096);
   if (hb > 4 * num_sms) hb = 4 * num_sms;
   if (hb < 1) hb = 1;
-  k_rs_hist<<<hb, 512, 0, st>>>(a, m_cap, m_dev, off_dev, w.hist);
-  k_rs_digit_scan<<<1, 256, 0, st>>>(w.hist, w.skip, m_cap, m_dev);
+  launch_k(k_rs_hist, hb, 512, 0, st, a, m_cap, m_dev, off_dev, w.hist);
+  launch_k(k_rs_digit_scan, 1, 256, 0, st, w.hist, w.skip, m_cap, m_dev);
   for (int d = 0; d < 8; ++d) {
     const uint64_t* src = (d & 1) ? b : a;
     uint64_t* dst = (d & 1) ? a : b;
-    k_rs_pass<<<(unsigned)tiles, RS_THREADS, 0, st>>>(src, dst, m_cap, m_dev, off_dev, d, w.hist,
+    launch_k(k_rs_pass, (unsigned)tiles, RS_THREADS, 0, st, src, dst, m_cap, m_dev, off_dev, d, w.hist,
                                                      w.skip, w.status + (size_t)d * tiles * 256,
                                                      w.ctr + d, err);
   }

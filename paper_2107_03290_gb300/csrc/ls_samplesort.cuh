@@ -104,6 +104,7 @@ __device__ __forceinline__ void ss_sort_regs(uint64_t (&v)[8], uint64_t* sh, uin
 static __global__ void __launch_bounds__(1024)
 k_ss_splitters(const uint64_t* __restrict__ keys, uint64_t m, uint64_t* __restrict__ spl,
                uint32_t* __restrict__ cnt) {
+  pdl_begin();
   extern __shared__ uint64_t ss_c[];
   static_assert(SS_CAND == 8 * 1024, "8 keys per thread");
   const uint32_t base = 8 * threadIdx.x;
@@ -120,6 +121,7 @@ k_ss_splitters(const uint64_t* __restrict__ keys, uint64_t m, uint64_t* __restri
 static __global__ void __launch_bounds__(SS_THREADS)
 k_ss_count(const uint64_t* __restrict__ keys, uint64_t m, const uint64_t* __restrict__ spl,
            uint32_t* __restrict__ cnt) {
+  pdl_begin();
   __shared__ uint64_t s_spl[SS_P];
   __shared__ uint32_t h[SS_NB];
   for (uint32_t i = threadIdx.x; i < SS_P; i += blockDim.x) s_spl[i] = spl[i];
@@ -136,6 +138,7 @@ k_ss_count(const uint64_t* __restrict__ keys, uint64_t m, const uint64_t* __rest
 // beg = exclusive scan of cnt (beg[SS_NB] = m), cur = beg.
 static __global__ void __launch_bounds__(1024)
 k_ss_scan(const uint32_t* __restrict__ cnt, uint32_t* __restrict__ beg, uint32_t* __restrict__ cur) {
+  pdl_begin();
   __shared__ uint32_t a[SS_NB + 1];
   __shared__ uint32_t ws[33];
   for (uint32_t i = threadIdx.x; i < SS_NB; i += blockDim.x) a[i] = cnt[i];
@@ -148,6 +151,7 @@ k_ss_scan(const uint32_t* __restrict__ cnt, uint32_t* __restrict__ beg, uint32_t
 static __global__ void __launch_bounds__(SS_THREADS)
 k_ss_scatter(const uint64_t* __restrict__ keys, uint64_t m, const uint64_t* __restrict__ spl,
              uint32_t* __restrict__ cur, uint64_t* __restrict__ out, uint32_t* err) {
+  pdl_begin();
   __shared__ uint64_t s_spl[SS_P];
   __shared__ uint32_t lc[SS_NB];  // per tile: counts, then output bases
   for (uint32_t i = threadIdx.x; i < SS_P; i += blockDim.x) s_spl[i] = spl[i];
@@ -248,6 +252,7 @@ __device__ __forceinline__ void ss_sort_chunk(const uint64_t* src, uint64_t* dst
 static __global__ void __launch_bounds__(SS_THREADS)
 k_ss_bucket_sort(uint64_t* __restrict__ in, uint64_t* __restrict__ out,
                  const uint32_t* __restrict__ beg) {
+  pdl_begin();
   __shared__ uint64_t a[SS_CAP];
   const uint32_t b = blockIdx.x;
   if (b >= (uint32_t)SS_NB) {
@@ -310,11 +315,11 @@ inline cudaError_t ss_sort_enqueue(uint64_t* a, uint64_t* b, uint64_t m, const S
   if (e) return e;
   const unsigned g = (unsigned)std::max<uint64_t>(
       1, std::min<uint64_t>((m + SS_TILE - 1) / SS_TILE, 2ull * num_sms));
-  k_ss_splitters<<<1, 1024, smem, st>>>(a, m, w.spl, w.cnt);
-  k_ss_count<<<g, SS_THREADS, 0, st>>>(a, m, w.spl, w.cnt);
-  k_ss_scan<<<1, 1024, 0, st>>>(w.cnt, w.beg, w.cur);
-  k_ss_scatter<<<g, SS_THREADS, 0, st>>>(a, m, w.spl, w.cur, b, err);
-  k_ss_bucket_sort<<<SS_NB + 2 * num_sms, SS_THREADS, 0, st>>>(b, a, w.beg);
+  launch_k(k_ss_splitters, 1, 1024, smem, st, a, m, w.spl, w.cnt);
+  launch_k(k_ss_count, g, SS_THREADS, 0, st, a, m, w.spl, w.cnt);
+  launch_k(k_ss_scan, 1, 1024, 0, st, w.cnt, w.beg, w.cur);
+  launch_k(k_ss_scatter, g, SS_THREADS, 0, st, a, m, w.spl, w.cur, b, err);
+  launch_k(k_ss_bucket_sort, SS_NB + 2 * num_sms, SS_THREADS, 0, st, b, a, w.beg);
   add_launches(5);
   return cudaGetLastError();
 }

@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(SC_THREADS)
 k_scan(const In* __restrict__ in, uint64_t* __restrict__ out, uint64_t M_cap,
        const unsigned long long* M_dev, uint64_t* status, uint32_t* tile_ctr, uint32_t* err,
        uint32_t stall_mask = 0u) {
+  pdl_begin();
   __shared__ uint64_t ws[33];
   __shared__ uint32_t s_tile;
   __shared__ uint64_t s_excl;

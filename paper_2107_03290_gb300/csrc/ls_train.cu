@@ -51,6 +51,7 @@ __device__ __forceinline__ uint64_t div64(uint64_t x, const Div64& v, uint64_t* 
 template <int DT>
 __global__ void k_sample(const typename KT<DT>::U* __restrict__ keys, uint64_t n, uint64_t s,
                          uint64_t seed, Div64 ds, Div64 dst, uint64_t* __restrict__ out) {
+  pdl_begin();
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < s;
        k += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t base, r;
@@ -65,6 +66,7 @@ __global__ void k_sample(const typename KT<DT>::U* __restrict__ keys, uint64_t n
 
 __global__ void k_train_init(DevModel* hdr, uint64_t s, uint32_t* leaf_beg, uint32_t* leaf_end,
                              int L, double* partials) {
+  pdl_begin();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     hdr->s = s;
     hdr->s_lo = ~0ull;
@@ -85,6 +87,7 @@ __global__ void k_train_init(DevModel* hdr, uint64_t s, uint32_t* leaf_beg, uint
 template <int DT>
 __global__ void k_finite_range(const uint64_t* __restrict__ tk, uint64_t s, DevModel* hdr,
                                unsigned long long* hi_out) {
+  pdl_begin();
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < s;
        k += (uint64_t)gridDim.x * blockDim.x) {
     if (!KT<DT>::finite(KT<DT>::from_tk(tk[k]))) continue;
@@ -94,6 +97,7 @@ __global__ void k_finite_range(const uint64_t* __restrict__ tk, uint64_t s, DevM
 }
 
 __global__ void k_finite_fix(DevModel* hdr, const unsigned long long* hi) {
+  pdl_begin();
   if (hdr->s_lo == ~0ull || *hi <= hdr->s_lo) {
     hdr->s_lo = 0;
     hdr->s_fin = 0;
@@ -112,6 +116,7 @@ constexpr int FR_CHUNK = FR_THREADS * FR_PER;
 __global__ void __launch_bounds__(FR_THREADS)
 k_first_rank(const uint64_t* __restrict__ tk, const DevModel* hdr, uint32_t* __restrict__ rank,
              uint64_t s_cap) {
+  pdl_begin();
   __shared__ uint32_t ws[33];
   __shared__ uint32_t s_r0;
   const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
@@ -193,6 +198,7 @@ template <int DT>
 __global__ void __launch_bounds__(FIT_THREADS)
 k_fit_sums(const uint64_t* __restrict__ tk, const uint32_t* __restrict__ rank,
            const DevModel* hdr, double* partials) {
+  pdl_begin();
   __shared__ double ws[33];
   const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
   const uint64_t chunk = (m + gridDim.x - 1) / gridDim.x;
@@ -214,6 +220,7 @@ k_fit_sums(const uint64_t* __restrict__ tk, const uint32_t* __restrict__ rank,
 template <int DT>
 __global__ void k_fit_root(DevModel* hdr, const uint64_t* __restrict__ tk,
                            const uint32_t* __restrict__ rank, const double* partials, int nblk) {
+  pdl_begin();
   // block partials summed lane-strided, then by a fixed warp tree (deterministic)
   double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
   for (int i = threadIdx.x; i < nblk; i += 32) {
@@ -253,6 +260,7 @@ template <int DT>
 __global__ void __launch_bounds__(RT_THREADS)
 k_fit_route(const uint64_t* __restrict__ tk, const DevModel* hdr, int L, uint32_t* leaf_beg,
             uint32_t* leaf_end) {
+  pdl_begin();
   __shared__ int lf[RT_THREADS + 2];
   const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
   const double r[3] = {hdr->root64[0], hdr->root64[1], hdr->root64[2]};
@@ -284,6 +292,7 @@ constexpr int FIT_UNIT = 2048;
 __global__ void __launch_bounds__(1024)
 k_fit_units_plan(const uint32_t* leaf_beg, const uint32_t* leaf_end, int L, uint32_t* ubase,
                  uint32_t* utotal, uint32_t ucap, uint32_t* err) {
+  pdl_begin();
   // (ubase clamped to the unit buffer's ucap entries: leaf ranges that overlap,
   // which only an unsorted sample could give, flag an error instead of
   // writing past the buffer)
@@ -314,6 +323,7 @@ __global__ void __launch_bounds__(FIT_THREADS)
 k_fit_unit_sums(const uint64_t* __restrict__ tk, const uint32_t* __restrict__ rank,
                 const DevModel* hdr, const uint32_t* leaf_beg, const uint32_t* leaf_end,
                 const uint32_t* ubase, int L, const uint32_t* utotal, double* unit) {
+  pdl_begin();
   __shared__ double ws[33];
   const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
   const double inv_m = m ? 1.0 / (double)m : 0.0;
@@ -344,6 +354,7 @@ __global__ void k_fit_leaf_final(const uint64_t* __restrict__ tk, const uint32_t
                                  const DevModel* hdr, const uint32_t* leaf_beg,
                                  const uint32_t* leaf_end, const uint32_t* ubase,
                                  const double* unit, int L, double* leaf) {
+  pdl_begin();
   const int lane = threadIdx.x & 31;
   const int l = (int)((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5);  // one warp per leaf
   if (l >= L) return;
@@ -391,6 +402,7 @@ __device__ __forceinline__ float fp32_sat(double d) {  // round to FP32, finite
 template <int DT>
 __global__ void __launch_bounds__(1024)
 k_fit_final(DevModel* hdr, int L, double* leaf, CellLeaf* cleaf) {
+  pdl_begin();
   // the leaves' lo bounds staged in shared memory, so that the right-to-left
   // pass runs on shared loads rather than a chain of global round trips
   __shared__ double slo[MAX_LEAVES];
@@ -516,6 +528,7 @@ __device__ __forceinline__ uint64_t warp_first_true(uint64_t lo, uint64_t hi, Pr
 template <int DT>
 __global__ void __launch_bounds__(128)
 k_thresholds(DevModel* hdr, const double* __restrict__ leaf, int L, uint32_t f0, uint64_t* thr) {
+  pdl_begin();
   const uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (b > f0) return;
@@ -561,6 +574,7 @@ __device__ __forceinline__ uint64_t cell_start(uint32_t c, const CellRoot& cr,
 template <int DT>
 __global__ void k_cell_table(DevModel* hdr, const uint64_t* __restrict__ thr, uint32_t f0,
                              const CellLeaf* __restrict__ cleaf, uint32_t* cell) {
+  pdl_begin();
   const uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (c >= L0_CELLS) return;
   const uint64_t TMAX = TkRange<DT>::MAX, NEVER = TkRange<DT>::NEVER;
@@ -583,6 +597,7 @@ __global__ void k_cell_table(DevModel* hdr, const uint64_t* __restrict__ thr, ui
 template <int DT>
 __global__ void k_heavy_flags(const uint64_t* __restrict__ tk, const DevModel* hdr, uint64_t tau,
                               uint32_t* __restrict__ flags, uint64_t s_cap) {
+  pdl_begin();
   const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
   const uint64_t* t = tk + lo;
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < s_cap;
@@ -608,6 +623,7 @@ __global__ void k_heavy_compact(const uint64_t* __restrict__ tk, const DevModel*
                                 const uint32_t* __restrict__ flags, const uint64_t* __restrict__ pos,
                                 const uint64_t* __restrict__ thr, const uint32_t* __restrict__ cell,
                                 const CellLeaf* __restrict__ cleaf, Cand* cand, uint64_t cand_cap) {
+  pdl_begin();
   const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
   const uint64_t* t = tk + lo;
   const L0Map q{thr, cell, cleaf, hdr->croot, hdr->pos_max, 0};
@@ -643,6 +659,7 @@ constexpr int SEL_CAP = 1024;
 __global__ void __launch_bounds__(SEL_THREADS)
 k_heavy_select(const Cand* __restrict__ cand, const uint64_t* ncand_ptr, uint64_t cand_cap,
                uint32_t f0, int hpb, uint64_t* sel, uint32_t* sellen, uint32_t* nh, DevModel* hdr) {
+  pdl_begin();
   __shared__ uint64_t s_tk[SEL_CAP], s_len[SEL_CAP];
   __shared__ uint64_t s_top[MAX_HPB], s_toplen[MAX_HPB];  // the selected, by place
   __shared__ uint64_t s_ab[2];
@@ -724,6 +741,7 @@ k_heavy_heads(const uint64_t* __restrict__ sel, const uint32_t* __restrict__ sel
               const uint32_t* __restrict__ nh, uint32_t f0, int hpb, DevModel* hdr,
               const CellLeaf* __restrict__ cleaf, BucketHead* heads, HeavyEntry* heavy,
               uint32_t* hlen) {
+  pdl_begin();
   __shared__ uint32_t ws[33];
   __shared__ uint32_t s_run;
   if (threadIdx.x == 0) s_run = 0;
@@ -775,6 +793,7 @@ k_heavy_heads(const uint64_t* __restrict__ sel, const uint32_t* __restrict__ sel
 __global__ void __launch_bounds__(1024)
 k_heavy_hash(DevModel* hdr, const HeavyEntry* __restrict__ heavy, const uint32_t* __restrict__ hlen,
              unsigned long long* hkey, uint16_t* hval) {
+  pdl_begin();
   const uint32_t H = hdr->nheavy;
   if (2 * H > HASH_SIZE) return;  // too full to help
   // (uint64 key 2^64-1 is left to the full lookup; a zero run never wins)
@@ -807,10 +826,10 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   const uint64_t s = P.s;
   const int L = (int)P.L;
   const int gs = (int)std::min<uint64_t>((s + 255) / 256, 8ull * num_sms);
-  k_train_init<<<std::max(1, (L + 255) / 256), 256, 0, st>>>(M.hdr, s, M.leaf_beg, M.leaf_end, L,
+  launch_k(k_train_init, std::max(1, (L + 255) / 256), 256, 0, st, M.hdr, s, M.leaf_beg, M.leaf_end, L,
                                                              W.partials);
   const uint64_t stride = std::max<uint64_t>(1, n / s);
-  k_sample<DT><<<std::max(1, gs), 256, 0, st>>>(keys, n, s, P.seed, make_div64(s), make_div64(stride),
+  launch_k(k_sample<DT>, std::max(1, gs), 256, 0, st, keys, n, s, P.seed, make_div64(s), make_div64(stride),
                                                 W.smp_a);
   // 4-byte keys: the radix sort skips the four constant high digits; 8-byte keys: sample sort
   cudaError_t e = KT<DT>::W == 4 ? rs_sort_enqueue(W.smp_a, W.smp_b, s, nullptr, nullptr, W.rs, err, st, num_sms)
@@ -818,45 +837,43 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   if (e) return e;
   e = cudaMemsetAsync(W.hi, 0, sizeof(unsigned long long), st);
   if (e) return e;
-  k_finite_range<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, s, M.hdr, W.hi);
-  k_finite_fix<<<1, 1, 0, st>>>(M.hdr, W.hi);
+  launch_k(k_finite_range<DT>, std::max(1, gs), 256, 0, st, W.smp_a, s, M.hdr, W.hi);
+  launch_k(k_finite_fix, 1, 1, 0, st, M.hdr, W.hi);
   const int fr = (int)std::min<uint64_t>((s + FR_CHUNK - 1) / FR_CHUNK, 4ull * num_sms);
-  k_first_rank<<<std::max(1, fr), FR_THREADS, 0, st>>>(W.smp_a, M.hdr, W.rank, s);
-  k_fit_sums<DT><<<FIT_BLOCKS, FIT_THREADS, 0, st>>>(W.smp_a, W.rank, M.hdr, W.partials);
-  k_fit_root<DT><<<1, 32, 0, st>>>(M.hdr, W.smp_a, W.rank, W.partials, FIT_BLOCKS);
+  launch_k(k_first_rank, std::max(1, fr), FR_THREADS, 0, st, W.smp_a, M.hdr, W.rank, s);
+  launch_k(k_fit_sums<DT>, FIT_BLOCKS, FIT_THREADS, 0, st, W.smp_a, W.rank, M.hdr, W.partials);
+  launch_k(k_fit_root<DT>, 1, 32, 0, st, M.hdr, W.smp_a, W.rank, W.partials, FIT_BLOCKS);
   const int rb = (int)std::min<uint64_t>((s + RT_THREADS - 1) / RT_THREADS, 8ull * num_sms);
-  k_fit_route<DT><<<std::max(1, rb), RT_THREADS, 0, st>>>(W.smp_a, M.hdr, L, M.leaf_beg, M.leaf_end);
-  k_fit_units_plan<<<1, 1024, 0, st>>>(M.leaf_beg, M.leaf_end, L, W.ubase, W.utotal,
+  launch_k(k_fit_route<DT>, std::max(1, rb), RT_THREADS, 0, st, W.smp_a, M.hdr, L, M.leaf_beg, M.leaf_end);
+  launch_k(k_fit_units_plan, 1, 1024, 0, st, M.leaf_beg, M.leaf_end, L, W.ubase, W.utotal,
                                        (uint32_t)(s / FIT_UNIT + L + 2), err);
   {
     const unsigned ub = (unsigned)std::min<uint64_t>(s / FIT_UNIT + L + 1, 16ull * num_sms);
-    k_fit_unit_sums<DT><<<ub, FIT_THREADS, 0, st>>>(W.smp_a, W.rank, M.hdr, M.leaf_beg,
+    launch_k(k_fit_unit_sums<DT>, ub, FIT_THREADS, 0, st, W.smp_a, W.rank, M.hdr, M.leaf_beg,
                                                    M.leaf_end, W.ubase, L, W.utotal, W.units);
   }
-  k_fit_leaf_final<DT><<<(32 * L + 255) / 256, 256, 0, st>>>(W.smp_a, W.rank, M.hdr, M.leaf_beg,
+  launch_k(k_fit_leaf_final<DT>, (32 * L + 255) / 256, 256, 0, st, W.smp_a, W.rank, M.hdr, M.leaf_beg,
                                                        M.leaf_end, W.ubase, W.units, L, M.leaf64);
-  k_fit_final<DT><<<1, 1024, 0, st>>>(M.hdr, L, M.leaf64, M.cleaf);
-  k_thresholds<DT><<<(32 * (P.f0 + 1) + 127) / 128, 128, 0, st>>>(M.hdr, M.leaf64, L, P.f0, M.thr);
-  k_cell_table<DT><<<(32 * L0_CELLS + 127) / 128, 128, 0, st>>>(M.hdr, M.thr, P.f0, M.cleaf, M.cell);
+  launch_k(k_fit_final<DT>, 1, 1024, 0, st, M.hdr, L, M.leaf64, M.cleaf);
+  launch_k(k_thresholds<DT>, (32 * (P.f0 + 1) + 127) / 128, 128, 0, st, M.hdr, M.leaf64, L, P.f0, M.thr);
+  launch_k(k_cell_table<DT>, (32 * L0_CELLS + 127) / 128, 128, 0, st, M.hdr, M.thr, P.f0, M.cleaf, M.cell);
   // heavy values
   const uint64_t tau = P.tau;
-  k_heavy_flags<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, M.hdr, tau, W.flags, s);
+  launch_k(k_heavy_flags<DT>, std::max(1, gs), 256, 0, st, W.smp_a, M.hdr, tau, W.flags, s);
   e = cudaMemsetAsync(W.scan_status, 0, W.scan_status_bytes, st);
   if (e) return e;
   const unsigned sblocks = (unsigned)std::max<uint64_t>(1, (s + SC_TILE - 1) / SC_TILE);
-  k_scan<uint32_t><<<sblocks, SC_THREADS, 0, st>>>(W.flags, W.cpos, s, nullptr,
-                                                   (uint64_t*)W.scan_status,
-                                                   (uint32_t*)((uint64_t*)W.scan_status + sblocks),
-                                                   err);
-  k_heavy_compact<DT><<<std::max(1, gs), 256, 0, st>>>(W.smp_a, M.hdr, W.flags, W.cpos, M.thr,
+  launch_k(k_scan<uint32_t>, sblocks, SC_THREADS, 0, st, W.flags, W.cpos, s, nullptr,
+           (uint64_t*)W.scan_status, (uint32_t*)((uint64_t*)W.scan_status + sblocks), err, 0u);
+  launch_k(k_heavy_compact<DT>, std::max(1, gs), 256, 0, st, W.smp_a, M.hdr, W.flags, W.cpos, M.thr,
                                                       M.cell, M.cleaf, (Cand*)W.cand, W.cand_cap);
-  k_heavy_select<<<P.f0, SEL_THREADS, 0, st>>>((const Cand*)W.cand, W.cpos + s, W.cand_cap,
+  launch_k(k_heavy_select, P.f0, SEL_THREADS, 0, st, (const Cand*)W.cand, W.cpos + s, W.cand_cap,
                                                      P.f0, (int)P.hpb, W.sel, W.sellen, W.nh, M.hdr);
-  k_heavy_heads<DT><<<1, 1024, 0, st>>>(W.sel, W.sellen, W.nh, P.f0, (int)P.hpb, M.hdr, M.cleaf,
+  launch_k(k_heavy_heads<DT>, 1, 1024, 0, st, W.sel, W.sellen, W.nh, P.f0, (int)P.hpb, M.hdr, M.cleaf,
                                         M.heads, M.heavy, W.hlen);
   e = cudaMemsetAsync(M.hkey, 0, HASH_SIZE * sizeof(uint64_t), st);
   if (e) return e;
-  k_heavy_hash<<<1, 1024, 0, st>>>(M.hdr, M.heavy, W.hlen, (unsigned long long*)M.hkey, M.hval);
+  launch_k(k_heavy_hash, 1, 1024, 0, st, M.hdr, M.heavy, W.hlen, (unsigned long long*)M.hkey, M.hval);
   add_launches(21);
   return cudaGetLastError();
 }
