@@ -243,7 +243,8 @@ def run_batched(ls, torch, count: int, steps: int, warmup: int, with_loop: bool 
 
 
 def run_serving(ls, torch, rates, seconds: float, pool_size: int = 64,
-                budget_bytes: int = 120 << 30, client_bytes: int = 48 << 30, streams: int = 8):
+                budget_bytes: int = 120 << 30, client_bytes: int = 48 << 30, streams: int = 8,
+                p99_bound_ms: float = 100.0):
     """Serving workload: Poisson arrivals of sort requests (each copies one
     device-resident pool array into its own buffer on the server's stream,
     outside the device time), admission by an HBM budget; reports p50/p99 of
@@ -254,6 +255,7 @@ def run_serving(ls, torch, rates, seconds: float, pool_size: int = 64,
     dev = [torch.from_numpy(a).cuda() for a in pool]
     rng = np.random.default_rng(11)
     out = []
+    svc = None
     for rate in rates:
         n_req = max(1, int(rate * seconds))
         gaps = rng.exponential(1.0 / rate, n_req)
@@ -310,30 +312,113 @@ def run_serving(ls, torch, rates, seconds: float, pool_size: int = 64,
         th.join()
         wall = max(done_t) - t0
         srv.close()
-        # one at a time, plain entry point, same requests in arrival order
-        st = torch.cuda.current_stream()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        tot_ms = 0.0
+        # one at a time: the same requests, in arrival order, each sorted by
+        # the plain entry point on one stream.  Its device time depends only on
+        # the pool array, so each array's plain sort is timed (median of 3) and
+        # a single-stream queue is replayed on the arrival times.
+        if svc is None:
+            svc = plain_service_ms(ls, torch, dev)
+        arr = np.cumsum(gaps)
+        done, c = np.empty(n_req), 0.0
         for i in range(n_req):
-            src = dev[picks[i]]
+            c = max(arr[i], c) + svc[picks[i]] / 1e3
+            done[i] = c
+        lat1 = (done - arr) * 1e3
+        wall1 = done[-1]
+        out.append({"rate_req_s": rate, "requests": n_req, "seconds": seconds, "keys": int(keys),
+                    "offered_keys_per_s": keys / arr[-1],
+                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                    "served_keys_per_s": keys / wall,
+                    "one_at_a_time": {"p50_ms": float(np.percentile(lat1, 50)),
+                                      "p99_ms": float(np.percentile(lat1, 99)),
+                                      "keys_per_s": keys / wall1},
+                    "served_vs_one_at_a_time": (keys / wall) / (keys / wall1)})
+        torch.cuda.empty_cache()
+    # capacity: the highest rate whose p99 stays within the bound, and the
+    # plain loop's device rate on the same mix (requests back to back)
+    ok = [r for r in out if r["p99_ms"] <= p99_bound_ms]
+    device_rate = sum(a.numel() for a in dev) / (sum(svc) / 1e3)
+    cap = max(ok, key=lambda r: r["rate_req_s"]) if ok else None
+    del dev
+    torch.cuda.empty_cache()
+    return {"workload": "serving_poisson", "pool": pool_size, "hbm_budget_gb": budget_bytes >> 30,
+            "seconds_per_rate": seconds, "rates": out, "p99_bound_ms": p99_bound_ms,
+            "one_at_a_time_device_keys_per_s": device_rate,
+            "capacity": None if cap is None else {
+                "rate_req_s": cap["rate_req_s"], "p99_ms": cap["p99_ms"],
+                "served_keys_per_s": cap["served_keys_per_s"],
+                "vs_one_at_a_time_device_rate": cap["served_keys_per_s"] / device_rate}}
+
+
+def plain_service_ms(ls, torch, dev, reps: int = 3):
+    """Device time (ms) of one plain ls_sort of each pool array (median of reps)."""
+    st = torch.cuda.current_stream()
+    out = []
+    for src in dev:
+        ms = []
+        for _ in range(reps + 1):
             buf = src.clone()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
             e0.record(st)
             ls.sort_(buf)
             e1.record(st)
             e1.synchronize()
-            tot_ms += e0.elapsed_time(e1)
+            ms.append(e0.elapsed_time(e1))
             del buf
-        out.append({"rate_req_s": rate, "requests": n_req, "seconds": seconds, "keys": int(keys),
-                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                    "served_keys_per_s": keys / wall,
-                    "one_at_a_time_keys_per_s": keys / (tot_ms / 1e3),
-                    "served_vs_one_at_a_time": (keys / wall) / (keys / (tot_ms / 1e3))})
+        out.append(float(np.median(ms[1:])))
+    return out
+
+
+def host_sorted_tk(a: np.ndarray, threads: int = 16) -> np.ndarray:
+    """Total-order keys of `a`, sorted on the host: chunks sorted in threads,
+    then merged by a stable sort (which merges sorted runs)."""
+    from concurrent.futures import ThreadPoolExecutor
+    tk = total_order_keys(a)
+    parts = np.array_split(tk, threads)
+    with ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(np.sort, parts))
+    return np.sort(np.concatenate(parts), kind="stable")
+
+
+def run_suite(ls, torch, names, steps: int, warmup: int, peak: float):
+    """The paper's synthetic suite: one JSON line per workload with keys/s,
+    the fraction of the 4*n*w roofline, the realized duplicate ratio and the
+    element-wise check of the GPU output against a host sort."""
+    stream = torch.cuda.current_stream()
+    for name in names:
+        dt, n0, fn = lsgen.WORKLOADS[name]
+        keys = fn(n0)
+        n, w = keys.size, keys.dtype.itemsize
+        pristine = torch.from_numpy(keys).cuda()
+        work = torch.empty_like(pristine)
+        ms = []
+        for i in range(warmup + steps):
+            work.copy_(pristine)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ls.sort_(work)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= warmup:
+                ms.append(e0.elapsed_time(e1))
+        got = total_order_keys(work.cpu().numpy())
+        want = host_sorted_tk(keys)
+        ok = bool(np.array_equal(got, want))
+        distinct = int(1 + np.count_nonzero(want[1:] != want[:-1]))
+        # keys whose value occurs at least twice
+        starts = np.flatnonzero(np.concatenate([[True], want[1:] != want[:-1]]))
+        runs = np.diff(np.concatenate([starts, [n]]))
+        in_dups = int(runs[runs >= 2].sum())
+        t = float(np.median(ms))
+        print(json.dumps({"suite": name, "n": n, "dtype": dt, "ms_p50": t, "ms_min": float(np.min(ms)),
+                          "keys_per_s": n / (t / 1e3),
+                          "frac_4nw": 4 * n * w / (t / 1e3) / 1e9 / peak,
+                          "dup_ratio": 1.0 - distinct / n, "frac_keys_repeated": in_dups / n,
+                          "parity": "bit-exact" if ok else "MISMATCH", "steps": steps}), flush=True)
+        del pristine, work, got, want, keys
         torch.cuda.empty_cache()
-    del dev
-    torch.cuda.empty_cache()
-    return {"workload": "serving_poisson", "pool": pool_size, "hbm_budget_gb": budget_bytes >> 30,
-            "note": f"{seconds} s per rate (60 s in the full recipe)", "rates": out}
 
 
 def main():
@@ -354,6 +439,11 @@ def main():
     ap.add_argument("--batch", type=int, default=4096, help="arrays of the batched line (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="seconds per arrival rate of the serving line (0: skip)")
+    ap.add_argument("--suite", default="",
+                    help="'paper' (or a comma list of workloads): the synthetic suite, one JSON "
+                         "line per workload, instead of the benchmark line")
+    ap.add_argument("--serve-rates", default="200,500,1000,2000,5000",
+                    help="arrival rates (requests/s) of the serving line")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
@@ -373,6 +463,11 @@ def main():
     torch.cuda.set_device(local)
     ls.build()
     ls.load()
+
+    if args.suite:
+        names = list(lsgen.SUITE) if args.suite == "paper" else args.suite.split(",")
+        run_suite(ls, torch, names, args.steps, args.warmup, load_peaks()[0])
+        return
 
     dt, keys = make_workload(args.workload, args.n)
     n = keys.size
@@ -484,7 +579,8 @@ def main():
         batched = run_batched(ls, torch, args.batch, steps=5, warmup=2)
     serving = None
     if args.serve_seconds > 0 and rank == 0:
-        serving = run_serving(ls, torch, [200, 1000, 5000], args.serve_seconds)
+        rates = [int(r) for r in args.serve_rates.split(",")]
+        serving = run_serving(ls, torch, rates, args.serve_seconds)
 
     if rank == 0:
         last = per[-1]

@@ -182,6 +182,21 @@ WORKLOADS = {
     "exponential_200m_f32": ("f32", 200_000_000, lambda n: exponential_f32(n, 5)),
 }
 
+# The paper's synthetic suite (Sec. 6.1 data sets, Sec. 6.2 Zipf skew sweep,
+# Sec. 6.4 scalability), as further named workloads.  The Zipfian sets draw
+# ranks 1..10^6 by Zipf(s) weights (the paper does not state the support).
+SUITE = {}
+for _s in (0.50, 0.60, 0.70, 0.80, 0.90, 0.99):
+    SUITE[f"zipf_s{int(round(_s * 100)):03d}_200m_f64"] = (
+        "f64", 200_000_000, (lambda s: lambda n: zipf_rank_f64(n, 8, k=1_000_000, s=s))(_s))
+SUITE["rootdups_200m_f64"] = ("f64", 200_000_000, lambda n: rootdups_f64(n))
+SUITE["twodups_200m_f64"] = ("f64", 200_000_000, lambda n: twodups_f64(n))
+for _tag, _n in (("1m", 1_000_000), ("10m", 10_000_000), ("100m", 100_000_000),
+                 ("1b", 1_000_000_000)):
+    SUITE[f"normal_{_tag}_f64"] = ("f64", _n, lambda n: normal_f64(n, 0))
+    SUITE[f"twodups_{_tag}_f64"] = ("f64", _n, lambda n: twodups_f64(n))
+WORKLOADS.update({k: v for k, v in SUITE.items() if k not in WORKLOADS})
+
 
 def serving_pool(count: int = 64, seed: int = 7, lo: float = 1e4, hi: float = 6.4e7,
                  heavy_share: float = 0.3):

@@ -13,9 +13,10 @@
 // too.  Histogram of slots -> exclusive scan (the
 // running totals of Alg. 2) -> placement -> touch-up.  Keys of different
 // slots are already in order, so the touch-up only orders each group of keys
-// sharing a slot: every key of a group of at most 32 counts the members below
-// it and writes itself to its final place; larger groups are copied when they
-// hold one value and sorted by a bitonic network otherwise.
+// sharing a slot: a group that holds one value (duplicates) is in order as
+// placed; in a group of several values every key of a group of at most 32
+// counts the members below it and writes itself to its final place, and
+// larger such groups are sorted by a bitonic network.
 //
 // Segments the levels could not split below CAP keys go to the fallback: per
 // job one CTA splits by the top byte in which the segment's total-order keys
@@ -29,7 +30,7 @@
 
 namespace ls {
 
-constexpr int BIGCAP = 512;     // slot groups > 32 keys tracked per segment
+constexpr int BIGCAP = 512;     // groups of several values above 32 keys tracked per segment
 constexpr int STACK = 2048;     // fallback work stack entries per CTA
 
 template <int DT, int THREADS, int KPT>
@@ -40,7 +41,8 @@ struct BucketCfg {
   static constexpr size_t OFF_CNT = OFF_OUT + sizeof(U) * CAP;
   static constexpr size_t OFF_BIG = (OFF_CNT + 4 * (CAP + 1) + 15) / 16 * 16;
   static constexpr size_t OFF_WS = OFF_BIG + 8 * BIGCAP;
-  static constexpr size_t SMEM = OFF_WS + 8 * 40;
+  static constexpr size_t OFF_MIX = OFF_WS + 8 * 40;       // CAP bytes: slot holds > 1 value
+  static constexpr size_t SMEM = (OFF_MIX + CAP + 15) / 16 * 16;
   // fallback extras
   static constexpr size_t OFF_STACK = (SMEM + 15) / 16 * 16;
   static constexpr size_t OFF_HIST = OFF_STACK + 16 * STACK;
@@ -54,7 +56,12 @@ struct SegShared {            // per-CTA scalars of the segment sort
   int sh;
   float fmin, fscale;         // value-linear map (floats spanning several binades)
   int vmap;
+  uint32_t dense;             // some slot holds more than DENSE_RANK keys
 };
+
+// A segment in which some slot receives more than this many keys is treated
+// as holding runs of duplicates (see the touch-up below).
+constexpr uint32_t DENSE_RANK = 16;
 
 template <int DT>
 __device__ __forceinline__ void cmpswap(typename KT<DT>::U* a, uint32_t i, uint32_t j) {
@@ -97,6 +104,7 @@ __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* 
   U* out = (U*)(sm + C::OFF_OUT);
   uint32_t* cnt = (uint32_t*)(sm + C::OFF_CNT);
   uint2* big = (uint2*)(sm + C::OFF_BIG);
+  uint8_t* mix = (uint8_t*)(sm + C::OFF_MIX);
   unsigned long long* ws = (unsigned long long*)(sm + C::OFF_WS);
   const int lane = threadIdx.x & 31;
   // load, total-order key range
@@ -116,13 +124,16 @@ __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* 
     mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
     mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   }
-  if (threadIdx.x == 0) { ss.tmin = ~0ull; ss.tmax = 0; ss.nbig = 0; ss.all = 0; }
+  if (threadIdx.x == 0) { ss.tmin = ~0ull; ss.tmax = 0; ss.nbig = 0; ss.all = 0; ss.dense = 0; }
   // every thread owns KPT consecutive counters (16-byte stores; the slots
   // beyond m stay zero, so the scan leaves m in them)
   static_assert(KPT % 4 == 0, "KPT counters per thread in 16-byte groups");
   uint4* cnt4 = (uint4*)cnt + threadIdx.x * (KPT / 4);
 #pragma unroll
-  for (int v = 0; v < KPT / 4; ++v) cnt4[v] = make_uint4(0u, 0u, 0u, 0u);
+  for (int v = 0; v < KPT / 4; ++v) {
+    cnt4[v] = make_uint4(0u, 0u, 0u, 0u);
+    ((uint32_t*)mix)[threadIdx.x * (KPT / 4) + v] = 0u;
+  }
   __syncthreads();
   if (lane == 0) { atomicMin(&ss.tmin, mn); atomicMax(&ss.tmax, mx); }
   __syncthreads();
@@ -166,6 +177,7 @@ __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* 
                            : __uint2float_rn((uint32_t)((KT<DT>::tk(u[k]) - tmin) >> sh)) * rscale;
       const uint32_t s = min((uint32_t)f, m - 1);
       v = s | (atomicAdd(&cnt[s], 1u) << 16);  // rank inside the slot
+      if ((v >> 16) == DENSE_RANK) ss.dense = 1u;
     }
     sr[k] = v;
   }
@@ -196,19 +208,35 @@ __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* 
     }
   }
   __syncthreads();
+  // In a segment with runs of duplicates (some slot over DENSE_RANK keys), a
+  // slot group holding one value is in order as placed; the groups that hold
+  // more than one are marked: every key compares itself with its group's
+  // first member.  (Elsewhere every group has at most DENSE_RANK keys, and
+  // the per-key ranking below is cheaper than the marking.)
+  const bool dense = ss.dense != 0u;
+  if (dense) {
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      if (sr[k] != 0xFFFFFFFFu && (sr[k] >> 16) != 0) {
+        const uint32_t s = sr[k] & 0xFFFFu;
+        if (KT<DT>::tk(out[cnt[s]]) != KT<DT>::tk(u[k])) mix[s] = 1;
+      }
+    }
+    __syncthreads();
+  }
   // Final positions straight from the registers.  Keys of different slots are
-  // in order (the slot map is monotone); inside a slot group [a, b) a key's
-  // place is a + #{members smaller, or equal and placed earlier}: the
-  // insertion-sort touch-up of Alg. 2 restricted to the group, computed per
-  // key so that the lanes do not wait on each other.  Groups above GROUP_MAX
-  // are finished cooperatively below.
+  // in order (the slot map is monotone); inside a group [a, b) of several
+  // values a key's place is a + #{members smaller, or equal and placed
+  // earlier}: the insertion-sort touch-up of Alg. 2 restricted to the group,
+  // computed per key so that the lanes do not wait on each other.  Groups of
+  // several values above GROUP_MAX keys are sorted cooperatively below.
   constexpr uint32_t GROUP_MAX = 32;
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
     if (sr[k] == 0xFFFFFFFFu) continue;
     const uint32_t s = sr[k] & 0xFFFFu;
     const uint32_t a = cnt[s], b = cnt[s + 1];
-    if (b - a == 1) { dst[a] = u[k]; continue; }
+    if (b - a == 1 || (dense && !mix[s])) { dst[a + (sr[k] >> 16)] = u[k]; continue; }
     if (b - a > GROUP_MAX) {
       if ((sr[k] >> 16) == 0) {  // the group's first key records it
         const uint32_t idx = atomicAdd(&ss.nbig, 1u);
@@ -235,13 +263,9 @@ __device__ void segment_sort(typename KT<DT>::U* dst, const typename KT<DT>::U* 
     __syncthreads();
     return;
   }
-  for (uint32_t g = 0; g < nb; ++g) {  // a large group: one value is already in order
+  for (uint32_t g = 0; g < nb; ++g) {  // a large group of several values
     const uint2 gr = big[g];
-    const uint64_t t0 = KT<DT>::tk(out[gr.x]);
-    int diff = 0;
-    for (uint32_t i = threadIdx.x; i < gr.y; i += THREADS)
-      diff |= KT<DT>::tk(out[gr.x + i]) != t0;
-    if (__syncthreads_or(diff)) block_bitonic<DT>(out + gr.x, gr.y);
+    block_bitonic<DT>(out + gr.x, gr.y);
     for (uint32_t i = threadIdx.x; i < gr.y; i += THREADS) dst[gr.x + i] = out[gr.x + i];
     __syncthreads();
   }
