@@ -141,6 +141,26 @@ ls_status ls_sort_host(void* host_keys, size_t n, ls_dtype dtype, void* stream,
 ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dtype dtype,
                         void* stream);
 
+/* Stable argsort: perm[r] receives the position (in `keys`) of the key of
+ * rank r in the ascending order of the ordering contract; equal keys keep
+ * their input order, so perm is unique.  `keys` (n keys of `dtype`) is left
+ * unchanged; `perm` is a DEVICE array of n uint32.  n >= 2^32: LS_ERR_INVALID.
+ * The keys and their positions are packed into 64-bit composite keys (total-
+ * order key, position) sorted by the learned sort itself (ls_sort on uint64):
+ * one pass for 4-byte keys; two passes, low then high 32 bits of the
+ * total-order key, for 8-byte keys (the payload permutation that Alg. 2 does
+ * not carry, built from the same hot path).  Scratch: 8 n (4-byte keys) or
+ * 16 n bytes from the library's pool, plus the inner sorts' workspace.
+ * Asynchronous errors reach the stream's status word (ls_stream_status). */
+ls_status ls_argsort(const void* keys, uint32_t* perm, size_t n, ls_dtype dtype, void* stream);
+
+/* Key-value sort: sorts `keys` in place (as ls_sort) and permutes `values`
+ * (n elements of value_bytes = 4 or 8 bytes, a DEVICE array) alongside; equal
+ * keys keep their values in input order (stable).  Built on ls_argsort plus
+ * two gathers.  n >= 2^32 or another value_bytes: LS_ERR_INVALID. */
+ls_status ls_sort_pairs(void* keys, void* values, size_t n, ls_dtype dtype, uint32_t value_bytes,
+                        void* stream);
+
 /* Waits for `stream`, then returns and clears the status word of `stream`:
  * LS_ERR_TIMEOUT if a bounded device wait of a call on this stream gave up
  * since the last ls_stream_status(stream), LS_ERR_CUDA if a device bounds

@@ -93,6 +93,8 @@ def _L():
             lib.lso_sort.restype = i32
             lib.lso_sort_stages.argtypes = [vp, u64, i32, P(Params), P(Model), i32, P(Trace)]
             lib.lso_sort_stages.restype = i32
+            lib.lso_reference_argsort.argtypes = [vp, u64, i32, vp]
+            lib.lso_reference_argsort.restype = i32
             lib.lso_reference_sort.argtypes = [vp, u64, i32]
             lib.lso_reference_sort.restype = i32
             lib.lso_total_order_key.argtypes = [vp, u64, i32]
@@ -163,6 +165,15 @@ def reference_sort(keys: np.ndarray) -> np.ndarray:
     a = np.ascontiguousarray(keys).copy()
     _L().lso_reference_sort(_ptr(a), a.size, DTYPES[dtype_name(a)])
     return a
+
+
+def reference_argsort(keys: np.ndarray) -> np.ndarray:
+    """The plain definition of the stable argsort (std::stable_sort of the
+    positions by total order); uint32 positions."""
+    a = np.ascontiguousarray(keys)
+    perm = np.empty(a.size, np.uint32)
+    _L().lso_reference_argsort(_ptr(a), a.size, DTYPES[dtype_name(a)], _ptr(perm))
+    return perm
 
 
 def total_order_keys(keys: np.ndarray) -> np.ndarray:

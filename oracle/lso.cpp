@@ -315,6 +315,17 @@ void reference_sort(typename K::T* a, uint64_t n) {
   std::sort(a, a + n, [](typename K::T u, typename K::T v) { return K::tk(u) < K::tk(v); });
 }
 
+// Stable argsort by the total-order key: positions of the keys in ascending
+// order, equal keys in input order (the unique stable permutation).
+template <class K>
+void reference_argsort(const typename K::T* a, uint64_t n, uint32_t* perm) {
+  std::vector<uint32_t> idx(n);
+  for (uint64_t i = 0; i < n; ++i) idx[i] = (uint32_t)i;
+  std::stable_sort(idx.begin(), idx.end(),
+                   [a](uint32_t u, uint32_t v) { return K::tk(a[u]) < K::tk(a[v]); });
+  std::copy(idx.begin(), idx.end(), perm);
+}
+
 }  // namespace
 
 // ============================================================================ C API
@@ -468,6 +479,16 @@ int lso_sort_stages(void* keys, uint64_t n, int dtype, const lso_params* p,
     case LSO_U64: learned_sort<U64>((uint64_t*)keys, n, p, tr, model, t); return 0;
     case LSO_F32: learned_sort<F32>((float*)keys, n, p, tr, model, t); return 0;
     case LSO_U32: learned_sort<U32>((uint32_t*)keys, n, p, tr, model, t); return 0;
+  }
+  return -1;
+}
+
+int lso_reference_argsort(const void* keys, uint64_t n, int dtype, uint32_t* perm) {
+  switch (dtype) {
+    case LSO_F64: reference_argsort<F64>((const double*)keys, n, perm); return 0;
+    case LSO_U64: reference_argsort<U64>((const uint64_t*)keys, n, perm); return 0;
+    case LSO_F32: reference_argsort<F32>((const float*)keys, n, perm); return 0;
+    case LSO_U32: reference_argsort<U32>((const uint32_t*)keys, n, perm); return 0;
   }
   return -1;
 }

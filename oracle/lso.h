@@ -71,6 +71,10 @@ int lso_sort(void* keys, uint64_t n, int dtype, const lso_params* p, lso_trace* 
 int lso_sort_stages(void* keys, uint64_t n, int dtype, const lso_params* p,
                     const lso_model* model, int touch_up, lso_trace* tr);
 
+/* Plain definition of the argsort: std::stable_sort of the positions
+ * 0..n-1 by the total-order key of their keys (n < 2^32). */
+int lso_reference_argsort(const void* keys, uint64_t n, int dtype, uint32_t* perm);
+
 /* The plain definition: std::sort by the total-order key. */
 int lso_reference_sort(void* keys, uint64_t n, int dtype);
 

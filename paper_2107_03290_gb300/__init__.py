@@ -22,7 +22,7 @@ _INC = os.path.join(os.path.dirname(_HERE), "include")
 _SO = os.path.join(_HERE, "libls.so")
 _BUILD = os.path.join(_HERE, "_build")
 SOURCES = ["ls_train.cu", "ls_partition.cu", "ls_bucket.cu", "ls_api.cu", "ls_server.cpp",
-           "ls_noalloc.cu"]
+           "ls_noalloc.cu", "ls_pairs.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 DTYPE_CODES = {"f64": 0, "u64": 1, "f32": 2, "u32": 3}
@@ -128,7 +128,8 @@ class RequestStats(ctypes.Structure):
 
 
 EXPORTED = ["ls_default_params", "ls_status_string", "ls_sort", "ls_sort_ex", "ls_sort_host",
-            "ls_sort_batch", "ls_stream_status", "ls_debug_set_wait", "ls_train",
+            "ls_sort_batch", "ls_argsort", "ls_sort_pairs", "ls_stream_status",
+            "ls_debug_set_wait", "ls_train",
             "ls_level0_histogram",
             "ls_radix_sort_u64", "ls_radix_sort_u64_noalloc", "ls_sample_sort_u64",
             "ls_kernel_launches",
@@ -166,6 +167,8 @@ def load(path: str | None = None):
             "ls_sort_ex": [vp, sz, i32, vp, P(Params), P(Stats)],
             "ls_sort_host": [vp, sz, i32, vp, P(Params)],
             "ls_sort_batch": [vp, vp, sz, i32, vp],
+            "ls_argsort": [vp, vp, sz, i32, vp],
+            "ls_sort_pairs": [vp, vp, sz, i32, u32, vp],
             "ls_stream_status": [vp],
             "ls_debug_set_wait": [vp, u32, u64],
             "ls_train": [vp, sz, i32, vp, P(Params), P(ModelExport)],
@@ -271,6 +274,29 @@ def sort_batch_(tensors, stream=None):
     ns = (ctypes.c_size_t * len(tensors))(*[t.numel() for t in tensors])
     rc = load().ls_sort_batch(ptrs, ns, len(tensors), code, _stream(stream))
     _check(rc, "ls_sort_batch")
+
+
+def argsort(t, stream=None):
+    """Stable argsort of a CUDA tensor (ls_argsort): an int32 tensor whose
+    entry r is the position of the key of rank r (as unsigned 32-bit)."""
+    torch = _torch()
+    t = _device_tensor(t)
+    perm = torch.empty(t.numel(), dtype=torch.int32, device=t.device)
+    _check(load().ls_argsort(t.data_ptr(), perm.data_ptr(), t.numel(), dtype_code(t),
+                             _stream(stream)), "ls_argsort")
+    return perm
+
+
+def sort_pairs_(keys, values, stream=None):
+    """Sort CUDA tensor `keys` in place and permute `values` (4- or 8-byte
+    elements, same length) alongside, stably (ls_sort_pairs)."""
+    keys = _device_tensor(keys)
+    values = _device_tensor(values)
+    if values.numel() != keys.numel():
+        raise ValueError("values must have as many elements as keys")
+    _check(load().ls_sort_pairs(keys.data_ptr(), values.data_ptr(), keys.numel(),
+                                dtype_code(keys), values.element_size(), _stream(stream)),
+           "ls_sort_pairs")
 
 
 def kernel_launches() -> int:

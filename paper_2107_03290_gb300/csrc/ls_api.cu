@@ -595,6 +595,15 @@ static ls_status validate(const void* keys, size_t n, int dt) {
   return LS_OK;
 }
 
+int pool_alloc(void** p, size_t bytes, CUstream_st* st) {
+  Device* d;
+  cudaError_t e = get_device(&d);
+  if (e) return (int)e;
+  return (int)cudaMallocFromPoolAsync(p, bytes, d->pool, (cudaStream_t)st);
+}
+
+void pool_free(void* p, CUstream_st* st) { cudaFreeAsync(p, (cudaStream_t)st); }
+
 static cudaError_t ws_alloc(Device* d, Workspace* w, cudaStream_t st) {
   return cudaMallocFromPoolAsync(&w->base, w->bytes, d->pool, st);
 }

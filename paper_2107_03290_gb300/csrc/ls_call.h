@@ -37,4 +37,10 @@ ls_status sort_call(void* keys, size_t n, ls_dtype dtype, CUstream_st* stream,
 ls_status batch_call(void* const* keys, const size_t* n, size_t count, ls_dtype dtype,
                      CUstream_st* stream, const CallOpts* o);
 
+// Scratch from the library's per-device stream-ordered memory pool (the one
+// every sort call carves its workspace from).  pool_alloc returns 0 on
+// success, else a CUDA error code; pool_free releases in stream order.
+int pool_alloc(void** p, size_t bytes, CUstream_st* stream);
+void pool_free(void* p, CUstream_st* stream);
+
 }  // namespace ls

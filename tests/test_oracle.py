@@ -424,3 +424,22 @@ def test_spec_heavy_and_ext_histogram():
     hist = oracle.spec_ext_histogram(ev1, keys, h)
     # one bucket owning heavies 1 < 3 < 4: slots <1, =1, (1,3), =3, (3,4), =4, >4
     assert hist.tolist() == [0, 5, 1, 3, 0, 4, 0]
+
+
+# --------------------------------------------------------------------- argsort
+def test_reference_argsort_small_example():
+    """Total order with ties in input order: -inf < -0.0 < +0.0 < 1 < 2 = 2 < NaN."""
+    keys = np.array([2.0, -0.0, 1.0, 0.0, 2.0, np.nan, -np.inf])
+    assert oracle.reference_argsort(keys).tolist() == [6, 1, 3, 2, 0, 4, 5]
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.uint64, np.float32, np.uint32])
+def test_reference_argsort_is_numpy_stable_argsort(dt):
+    rng = np.random.default_rng(7)
+    if np.dtype(dt).kind == "f":
+        a = rng.choice(np.array([-np.inf, -2.5, -0.0, 0.0, 1e-30, 3.0, np.inf, np.nan], dt), 5000)
+        a[:2000] = rng.normal(size=2000).astype(dt)
+    else:
+        a = rng.integers(0, 50, 5000).astype(dt)
+    want = np.argsort(oracle.total_order_keys(a), kind="stable").astype(np.uint32)
+    assert np.array_equal(oracle.reference_argsort(a), want)
