@@ -203,16 +203,6 @@ static CallOpts stream_opts(Device* d, cudaStream_t st) {
   return o;
 }
 
-// Zeroes the call's status block (with the list counters in front of it, one
-// memset) and applies the test settings of its waits.
-static cudaError_t begin_call(unsigned long long* counts, size_t n_counts, const CallOpts& o,
-                              cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(counts, 0, (n_counts + 2) * sizeof(unsigned long long), st);
-  if (e || (!o.stall && !o.spin_limit)) return e;
-  CallStatus cs{0u, o.stall, o.spin_limit};
-  return cudaMemcpyAsync(counts + n_counts, &cs, sizeof(cs), cudaMemcpyHostToDevice, st);
-}
-
 static cudaError_t end_call(const unsigned long long* counts, size_t n_counts, const CallOpts& o,
                             cudaStream_t st) {
   launch_k(k_status_fold, 1, 1, 0, st, (const CallStatus*)(counts + n_counts), o.fold_to);
@@ -527,8 +517,13 @@ struct Events {
   } while (0)
 
 static cudaError_t enqueue_train(const Plan& P, const Bound& b, const void* keys, Device* d,
-                                 uint32_t* err, cudaStream_t st) {
-  TrainPlan tp;
+                                 uint32_t* err, cudaStream_t st, const ZeroList* zero = nullptr,
+                                 CallStatus* cs = nullptr, const CallOpts* o = nullptr) {
+  TrainPlan tp{};
+  if (zero) tp.zero = *zero;
+  tp.cs = cs;
+  tp.stall = o ? o->stall : 0u;
+  tp.spin_limit = o ? o->spin_limit : 0ull;
   tp.s = P.s;
   tp.seed = P.seed;
   tp.tau = P.tau;
@@ -567,11 +562,16 @@ static cudaError_t enqueue_sort(const Plan& P, const Workspace& w, void* keys, D
   const Bound b = bind(P, w);
   Marks mk{ev && ev->on ? ev->ev : nullptr, NMARK};
   uint32_t* err = (uint32_t*)(b.counts + 16);  // the call's own CallStatus
-  LS_TRY(begin_call(b.counts, 16, o, st));
+  // the first training kernel zeroes the list counters and the level-0 scan
+  // words and initialises the call's status block (no memsets in the stream)
+  ZeroList z{};
+  z.p[0] = b.counts;
+  z.words[0] = 16 * 2;
+  z.p[1] = at<void>(w, w.o_l0scan);
+  z.words[1] = (uint32_t)(w.l0scan_bytes / 4);
   mark(&mk, 0, st);
-  LS_TRY(enqueue_train(P, b, keys, d, err, st));
+  LS_TRY(enqueue_train(P, b, keys, d, err, st, &z, (CallStatus*)err, &o));
   mark(&mk, 1, st);
-  LS_TRY(cudaMemsetAsync(at<void>(w, w.o_l0scan), 0, w.l0scan_bytes, st));
   const Level0Args a = level0_args(P, b, w, keys, err);
   LS_TRY(level0_enqueue(P.dt, a, P.smem_hist, P.smem_scatter, b.lists, P.lim, st, &mk, 2));
   LS_TRY(level1_enqueue(P.dt, keys, a.scratch, P.n, b.M, b.lists, P.lim, b.l1, P.kf, a.f0kf,

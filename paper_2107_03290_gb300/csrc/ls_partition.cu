@@ -821,6 +821,10 @@ k_l1_plan(LevelArgs la, SortLimits lim, Level1Ws w, uint32_t* err) {
   pdl_begin();
   __shared__ uint64_t ws[33];
   __shared__ uint64_t s_rt, s_rc;
+  // this level's look-back words start at zero (cleared here rather than by a
+  // memset between kernels); the scan runs two launches later
+  for (size_t i = threadIdx.x; i < w.scan_status_bytes / 4; i += blockDim.x)
+    ((uint32_t*)w.scan_status)[i] = 0u;
   L1Aux* aux = (L1Aux*)w.aux;
   const uint64_t nj = min((uint64_t)*la.in.count, min((uint64_t)la.in.cap, w.cap_jobs));
   if (threadIdx.x == 0) { s_rt = 0; s_rc = 0; }
@@ -1222,8 +1226,6 @@ static cudaError_t level_dt(void* keys, void* scratch, uint64_t n, const ModelPt
                             const Lists& lists, const LevelArgs& la, const SortLimits& lim,
                             const Level1Ws& w, uint32_t* err, cudaStream_t st, int num_sms) {
   typedef typename KT<DT>::U U;
-  cudaError_t e = cudaMemsetAsync(w.scan_status, 0, w.scan_status_bytes, st);
-  if (e) return e;
   launch_k(k_l1_plan, 1, 1024, 0, st, la, lim, w, err);
   const int grid = 4 * num_sms;  // the histogram and range passes hold 4 CTAs per SM
   if (la.mode) launch_k(k_l1_minmax<DT>, grid, L1_THREADS, 0, st, (const U*)keys, (const U*)scratch, la, w);

@@ -65,8 +65,15 @@ __global__ void k_sample(const typename KT<DT>::U* __restrict__ keys, uint64_t n
 }
 
 __global__ void k_train_init(DevModel* hdr, uint64_t s, uint32_t* leaf_beg, uint32_t* leaf_end,
-                             int L, double* partials) {
+                             int L, double* partials, ZeroList z, CallStatus* cs, uint32_t stall,
+                             unsigned long long spin_limit) {
   pdl_begin();
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+#pragma unroll
+  for (int r = 0; r < ZERO_REGIONS; ++r)
+    if (z.p[r])
+      for (uint32_t i = tid; i < z.words[r]; i += nth) ((uint32_t*)z.p[r])[i] = 0u;
+  if (cs && tid == 0) { cs->word = 0u; cs->stall = stall; cs->spin_limit = spin_limit; }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     hdr->s = s;
     hdr->s_lo = ~0ull;
@@ -826,8 +833,20 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   const uint64_t s = P.s;
   const int L = (int)P.L;
   const int gs = (int)std::min<uint64_t>((s + 255) / 256, 8ull * num_sms);
-  launch_k(k_train_init, std::max(1, (L + 255) / 256), 256, 0, st, M.hdr, s, M.leaf_beg, M.leaf_end, L,
-                                                             W.partials);
+  ZeroList z = P.zero;
+  // the heavy table, the sample's scan words and the finite-range maximum are
+  // cleared here too (three memsets fewer); the caller's regions come first
+  int zi = 0;
+  while (zi < ZERO_REGIONS && z.p[zi]) ++zi;
+  auto add = [&](void* p, size_t bytes) {
+    if (zi < ZERO_REGIONS) { z.p[zi] = p; z.words[zi] = (uint32_t)(bytes / 4); ++zi; return true; }
+    return false;
+  };
+  const bool z_hkey = add(M.hkey, HASH_SIZE * sizeof(uint64_t));
+  const bool z_scan = add(W.scan_status, W.scan_status_bytes);
+  const bool z_hi = add(W.hi, sizeof(unsigned long long));
+  launch_k(k_train_init, std::max(16, (L + 255) / 256), 256, 0, st, M.hdr, s, M.leaf_beg, M.leaf_end,
+           L, W.partials, z, P.cs, P.stall, P.spin_limit);
   const uint64_t stride = std::max<uint64_t>(1, n / s);
   launch_k(k_sample<DT>, std::max(1, gs), 256, 0, st, keys, n, s, P.seed, make_div64(s), make_div64(stride),
                                                 W.smp_a);
@@ -835,8 +854,7 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   cudaError_t e = KT<DT>::W == 4 ? rs_sort_enqueue(W.smp_a, W.smp_b, s, nullptr, nullptr, W.rs, err, st, num_sms)
                                  : ss_sort_enqueue(W.smp_a, W.smp_b, s, W.ss, err, st, num_sms);
   if (e) return e;
-  e = cudaMemsetAsync(W.hi, 0, sizeof(unsigned long long), st);
-  if (e) return e;
+  if (!z_hi && (e = cudaMemsetAsync(W.hi, 0, sizeof(unsigned long long), st))) return e;
   launch_k(k_finite_range<DT>, std::max(1, gs), 256, 0, st, W.smp_a, s, M.hdr, W.hi);
   launch_k(k_finite_fix, 1, 1, 0, st, M.hdr, W.hi);
   const int fr = (int)std::min<uint64_t>((s + FR_CHUNK - 1) / FR_CHUNK, 4ull * num_sms);
@@ -860,8 +878,7 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   // heavy values
   const uint64_t tau = P.tau;
   launch_k(k_heavy_flags<DT>, std::max(1, gs), 256, 0, st, W.smp_a, M.hdr, tau, W.flags, s);
-  e = cudaMemsetAsync(W.scan_status, 0, W.scan_status_bytes, st);
-  if (e) return e;
+  if (!z_scan && (e = cudaMemsetAsync(W.scan_status, 0, W.scan_status_bytes, st))) return e;
   const unsigned sblocks = (unsigned)std::max<uint64_t>(1, (s + SC_TILE - 1) / SC_TILE);
   launch_k(k_scan<uint32_t>, sblocks, SC_THREADS, 0, st, W.flags, W.cpos, s, nullptr,
            (uint64_t*)W.scan_status, (uint32_t*)((uint64_t*)W.scan_status + sblocks), err, 0u);
@@ -871,8 +888,7 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
                                                      P.f0, (int)P.hpb, W.sel, W.sellen, W.nh, M.hdr);
   launch_k(k_heavy_heads<DT>, 1, 1024, 0, st, W.sel, W.sellen, W.nh, P.f0, (int)P.hpb, M.hdr, M.cleaf,
                                         M.heads, M.heavy, W.hlen);
-  e = cudaMemsetAsync(M.hkey, 0, HASH_SIZE * sizeof(uint64_t), st);
-  if (e) return e;
+  if (!z_hkey && (e = cudaMemsetAsync(M.hkey, 0, HASH_SIZE * sizeof(uint64_t), st))) return e;
   launch_k(k_heavy_hash, 1, 1024, 0, st, M.hdr, M.heavy, W.hlen, (unsigned long long*)M.hkey, M.hval);
   add_launches(21);
   return cudaGetLastError();

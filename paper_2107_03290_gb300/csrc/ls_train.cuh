@@ -6,6 +6,16 @@
 
 namespace ls {
 
+// Regions of the call's workspace that must start at zero, cleared by the
+// first kernel of the training step instead of by separate memsets (a memset
+// between two kernels would also break their dependent-launch overlap).
+// Pointers and sizes are multiples of 4 bytes.
+constexpr int ZERO_REGIONS = 6;
+struct ZeroList {
+  void* p[ZERO_REGIONS];
+  uint32_t words[ZERO_REGIONS];  // 4-byte words
+};
+
 struct TrainPlan {
   uint64_t s;        // sample size
   uint64_t seed;
@@ -13,6 +23,10 @@ struct TrainPlan {
   uint32_t L;        // leaves
   uint32_t f0;       // level-0 fan-out
   uint32_t hpb;      // heavy values per bucket (<= MAX_HPB)
+  ZeroList zero;     // cleared by the first training kernel (unused entries: null)
+  CallStatus* cs;    // the call's status block, initialised there too (null: none)
+  uint32_t stall;
+  unsigned long long spin_limit;
 };
 
 constexpr int FIT_BLOCKS = 304;     // blocks of the root least-squares sums
