@@ -141,6 +141,20 @@ ls_status ls_sort_host(void* host_keys, size_t n, ls_dtype dtype, void* stream,
 ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dtype dtype,
                         void* stream);
 
+/* Tunables of the batched sort.  Arrays of more than 8192 keys are first
+ * split by a line through their own key range into sub-buckets of about
+ * split_target[c] keys, c the array's size class (0: at most 65,536 keys,
+ * 1: at most 524,288, 2: larger).  0 takes the library's tuned table
+ * (written by paper_2107_03290_gb300/autotune.py on a GB300). */
+typedef struct ls_batch_params {
+  uint32_t split_target[3];
+  uint32_t reserved[5];
+} ls_batch_params;
+
+/* ls_sort_batch with explicit tunables (NULL: the tuned table). */
+ls_status ls_sort_batch_ex(void* const* keys, const size_t* n, size_t count, ls_dtype dtype,
+                           void* stream, const ls_batch_params* params);
+
 /* Stable argsort: perm[r] receives the position (in `keys`) of the key of
  * rank r in the ascending order of the ordering contract; equal keys keep
  * their input order, so perm is unique.  `keys` (n keys of `dtype`) is left

@@ -115,6 +115,10 @@ class ModelExport(ctypes.Structure):
                 ("n_heavy", ctypes.c_uint64), ("tau", ctypes.c_uint64)]
 
 
+class BatchParams(ctypes.Structure):
+    _fields_ = [("split_target", ctypes.c_uint32 * 3), ("reserved", ctypes.c_uint32 * 5)]
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
                 ("max_queue", ctypes.c_uint32), ("streams", ctypes.c_uint32),
@@ -128,7 +132,7 @@ class RequestStats(ctypes.Structure):
 
 
 EXPORTED = ["ls_default_params", "ls_status_string", "ls_sort", "ls_sort_ex", "ls_sort_host",
-            "ls_sort_batch", "ls_argsort", "ls_sort_pairs", "ls_stream_status",
+            "ls_sort_batch", "ls_sort_batch_ex", "ls_argsort", "ls_sort_pairs", "ls_stream_status",
             "ls_debug_set_wait", "ls_train",
             "ls_level0_histogram",
             "ls_radix_sort_u64", "ls_radix_sort_u64_noalloc", "ls_sample_sort_u64",
@@ -167,6 +171,7 @@ def load(path: str | None = None):
             "ls_sort_ex": [vp, sz, i32, vp, P(Params), P(Stats)],
             "ls_sort_host": [vp, sz, i32, vp, P(Params)],
             "ls_sort_batch": [vp, vp, sz, i32, vp],
+            "ls_sort_batch_ex": [vp, vp, sz, i32, vp, P(BatchParams)],
             "ls_argsort": [vp, vp, sz, i32, vp],
             "ls_sort_pairs": [vp, vp, sz, i32, u32, vp],
             "ls_stream_status": [vp],
@@ -265,14 +270,21 @@ def sort_host_ptr(ptr: int, n: int, code: int, params: Params | None = None, str
     _check(rc, "ls_sort_host")
 
 
-def sort_batch_(tensors, stream=None):
-    """Sort many CUDA tensors of one dtype in place (ls_sort_batch)."""
+def sort_batch_(tensors, stream=None, split_target=None):
+    """Sort many CUDA tensors of one dtype in place (ls_sort_batch; with
+    split_target, a 3-tuple per array-size class, ls_sort_batch_ex)."""
     if not tensors:
         return
     code = dtype_code(tensors[0])
     ptrs = (ctypes.c_void_p * len(tensors))(*[_device_tensor(t).data_ptr() for t in tensors])
     ns = (ctypes.c_size_t * len(tensors))(*[t.numel() for t in tensors])
-    rc = load().ls_sort_batch(ptrs, ns, len(tensors), code, _stream(stream))
+    if split_target is None:
+        rc = load().ls_sort_batch(ptrs, ns, len(tensors), code, _stream(stream))
+    else:
+        bp = BatchParams()
+        for i, v in enumerate(split_target):
+            bp.split_target[i] = int(v)
+        rc = load().ls_sort_batch_ex(ptrs, ns, len(tensors), code, _stream(stream), ctypes.byref(bp))
     _check(rc, "ls_sort_batch")
 
 

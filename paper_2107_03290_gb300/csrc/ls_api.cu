@@ -28,6 +28,7 @@
 #include "ls_partition.cuh"
 #include "ls_radix.cuh"
 #include "ls_train.cuh"
+#include "ls_tuned.h"
 
 namespace ls {
 
@@ -367,7 +368,7 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->o_tscan = c.take<uint8_t>(w->tscan_bytes);
   w->o_ss_spl = c.take<uint64_t>(SS_P);
   w->o_ss_words = c.take<uint32_t>(ss_work_words());
-  const bool narrow = P.W == 4;  // 4-byte keys sort their sample by radix
+  const bool narrow = sample_by_radix(P.W, s);  // the sample is sorted by radix
   w->o_rs_hist = c.take<uint32_t>(narrow ? 8 * 256 : 0);
   w->o_rs_skip = c.take<uint32_t>(narrow ? 8 : 0);
   w->rs_status_bytes = narrow ? rs_status_words(s) * 4 + 8 * 4 : 0;
@@ -772,10 +773,15 @@ ls_status ls_sort_batch(void* const* keys, const size_t* n, size_t count, ls_dty
   return batch_call(keys, n, count, dtype, (cudaStream_t)stream, nullptr);
 }
 
+ls_status ls_sort_batch_ex(void* const* keys, const size_t* n, size_t count, ls_dtype dtype,
+                           void* stream, const ls_batch_params* params) {
+  return batch_call(keys, n, count, dtype, (cudaStream_t)stream, nullptr, params);
+}
+
 }  // extern "C"
 
 ls_status ls::batch_call(void* const* keys, const size_t* n, size_t count, ls_dtype dtype,
-                         CUstream_st* stream, const CallOpts* opts) {
+                         CUstream_st* stream, const CallOpts* opts, const ls_batch_params* bp) {
   if (count > 0 && (!keys || !n)) return LS_ERR_INVALID;
   if (dtype < LS_F64 || dtype > LS_U32) return LS_ERR_INVALID;
   const int W = width_of(dtype);
@@ -858,7 +864,13 @@ ls_status ls::batch_call(void* const* keys, const size_t* n, size_t count, ls_dt
     else if (n[i] <= lim.c_small) { j.kind = JOB_SORT_RANGE; js.push_back(j); }
     else if (n[i] <= lim.c_mid) { j.kind = JOB_SORT_RANGE; jm.push_back(j); }
     else if (n[i] <= lim.c_large) { j.kind = JOB_SORT_RANGE; jl.push_back(j); }
-    else { j.kind = JOB_REFINE; jr.push_back(j); }
+    else {
+      j.kind = JOB_REFINE;
+      int c = 0;  // the array's size class picks its first split's target
+      while (c < 2 && n[i] > TUNED_CLASS_MAX[c]) ++c;
+      j.pad = (bp && bp->split_target[c]) ? bp->split_target[c] : TUNED_SPLIT_TARGET[c];
+      jr.push_back(j);
+    }
   }
   unsigned long long hc[18] = {0};  // list counters, then the call's CallStatus
   {

@@ -35,7 +35,7 @@ struct CallOpts {
 ls_status sort_call(void* keys, size_t n, ls_dtype dtype, CUstream_st* stream,
                     const ls_params* params, ls_stats* stats, const CallOpts* o);
 ls_status batch_call(void* const* keys, const size_t* n, size_t count, ls_dtype dtype,
-                     CUstream_st* stream, const CallOpts* o);
+                     CUstream_st* stream, const CallOpts* o, const ls_batch_params* bp = nullptr);
 
 // Scratch from the library's per-device stream-ordered memory pool (the one
 // every sort call carves its workspace from).  pool_alloc returns 0 on

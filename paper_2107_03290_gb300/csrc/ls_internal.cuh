@@ -300,7 +300,8 @@ struct Job {
   uint64_t span;       // refine jobs: keys move within [start, start+span) of the other
                        // buffer (m, except for a level-0 bucket with heavy values, whose
                        // non-equality keys spread over the bucket's whole range)
-  uint64_t pad;
+  uint64_t pad;        // range-split jobs of the batched sort: keys per sub-bucket aimed at
+                       // (0: the level's target)
   uint64_t value;      // FILL: the key bits to write
   uint32_t src;
   uint32_t kind;

@@ -837,7 +837,7 @@ k_l1_plan(LevelArgs la, SortLimits lim, Level1Ws w, uint32_t* err) {
       // the model's split has the call's Kf sub-buckets per bucket (ids from
       // K2, plus one per heavy value's interval); a range split aims at
       // la.target keys per sub-bucket, at most la.fmax of them
-      const uint64_t tg = la.target ? la.target : 1;
+      const uint64_t tg = (la.mode && job.pad) ? job.pad : (la.target ? la.target : 1);
       const uint64_t fmx = la.fmax ? min((uint64_t)la.fmax, (uint64_t)MAX_F1) : (uint64_t)MAX_F1;
       uint64_t f = (job.m + tg - 1) / tg;
       f = f < 2 ? 2 : (f > fmx ? fmx : f);

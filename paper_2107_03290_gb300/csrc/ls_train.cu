@@ -850,8 +850,8 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   const uint64_t stride = std::max<uint64_t>(1, n / s);
   launch_k(k_sample<DT>, std::max(1, gs), 256, 0, st, keys, n, s, P.seed, make_div64(s), make_div64(stride),
                                                 W.smp_a);
-  // 4-byte keys: the radix sort skips the four constant high digits; 8-byte keys: sample sort
-  cudaError_t e = KT<DT>::W == 4 ? rs_sort_enqueue(W.smp_a, W.smp_b, s, nullptr, nullptr, W.rs, err, st, num_sms)
+  // the sample sort for large samples of 8-byte keys, else the LSD radix sort (sample_by_radix)
+  cudaError_t e = sample_by_radix(KT<DT>::W, s) ? rs_sort_enqueue(W.smp_a, W.smp_b, s, nullptr, nullptr, W.rs, err, st, num_sms)
                                  : ss_sort_enqueue(W.smp_a, W.smp_b, s, W.ss, err, st, num_sms);
   if (e) return e;
   if (!z_hi && (e = cudaMemsetAsync(W.hi, 0, sizeof(unsigned long long), st))) return e;

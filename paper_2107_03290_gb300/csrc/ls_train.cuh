@@ -31,6 +31,13 @@ struct TrainPlan {
 
 constexpr int FIT_BLOCKS = 304;     // blocks of the root least-squares sums
 
+// The training sample is sorted by the LSD radix sort for 4-byte keys (their
+// four constant high digits are skipped) and for samples of at most 2^17
+// keys, whose few tiles per pass beat the sample sort's fixed cost (measured:
+// 1M keys, a 10K-key sample: training 0.22 -> 0.20 ms); larger samples of
+// 8-byte keys take the sample sort (200M keys: 0.54 ms against 0.61 ms).
+inline bool sample_by_radix(int key_width, uint64_t s) { return key_width == 4 || s <= (1ull << 17); }
+
 struct TrainWs {
   uint64_t* smp_a;           // s
   uint64_t* smp_b;           // s
