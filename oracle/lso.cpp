@@ -400,7 +400,9 @@ void lso_fit_sorted(const double* xs, const uint64_t* tks, uint64_t m, uint32_t 
     sxx += dx * dx;
     sxy += dx * (y[k] - my);
   }
-  double a0 = (sxx > 0) ? sxy / sxx : 0.0;
+  // zero variance (every sample key equal) gets slope 0: tested on the keys
+  // themselves, since the centred sums of equal keys need not round to 0
+  double a0 = (sxx > 0 && xs[m - 1] != xs[0]) ? sxy / sxx : 0.0;
   if (!(a0 >= 0) || !std::isfinite(a0) || !std::isfinite(mx)) a0 = 0.0;
   model->root[0] = a0;
   model->root[1] = std::isfinite(mx) ? mx : 0.0;
@@ -426,7 +428,7 @@ void lso_fit_sorted(const double* xs, const uint64_t* tks, uint64_t m, uint32_t 
       lxx += dx * dx;
       lxy += dx * (y[k] - myl);
     }
-    double a = (cnt >= 2 && lxx > 0) ? lxy / lxx : 0.0;
+    double a = (cnt >= 2 && lxx > 0 && xs[e - 1] != xs[b]) ? lxy / lxx : 0.0;
     if (!(a >= 0) || !std::isfinite(a) || !std::isfinite(mxl)) a = 0.0;
     q[0] = a;
     q[1] = std::isfinite(mxl) ? mxl : 0.0;

@@ -129,6 +129,15 @@ def test_fit_closed_form_degenerate():
     assert fm.predict(0.0) == pytest.approx(0.0) and fm.predict(1.0) == pytest.approx(0.5)
     fm = oracle.fit_sorted(np.zeros(0), 8)                 # no finite sample
     assert 0.0 <= fm.predict(1.0) <= 1.0
+    # zero variance takes slope 0 even when the FP64 mean of the equal keys
+    # does not round back to the key (35 copies of a value with a long mantissa)
+    # (one key, six copies of x, ten keys: the six copies form a leaf, and
+    # their centred FP64 sums are tiny but not zero)
+    x = 104.66245874
+    fm = oracle.fit_sorted(np.array([1.0] * 1 + [x] * 6 + [300.0] * 10), 64)
+    own = [l for l in range(64) if abs(fm.leaf[l, 1] - x) < 1e-6]
+    assert own, "the 35 copies should have a leaf of their own"
+    assert all(fm.leaf[l, 0] == 0.0 for l in own)
 
 
 @pytest.mark.parametrize("gen", ["normal", "zipf", "mix", "uniform_u64"])
