@@ -306,21 +306,27 @@ k_ss_bucket_sort(uint64_t* __restrict__ in, uint64_t* __restrict__ out,
 }
 
 // Sorts a[0..m) (m < 2^32) using b[0..m) as scratch; the result is in a.
+// splitters_done: the splitters and the cleared counters are already in `w`
+// (the training's sampling kernel draws them from the input keys).
 inline cudaError_t ss_sort_enqueue(uint64_t* a, uint64_t* b, uint64_t m, const SsWork& w,
-                                   uint32_t* err, cudaStream_t st, int num_sms) {
+                                   uint32_t* err, cudaStream_t st, int num_sms,
+                                   bool splitters_done = false) {
   if (m < 2) return cudaSuccess;
-  const size_t smem = (size_t)SS_CAND * sizeof(uint64_t);
-  cudaError_t e = cudaFuncSetAttribute(k_ss_splitters, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e) return e;
   const unsigned g = (unsigned)std::max<uint64_t>(
       1, std::min<uint64_t>((m + SS_TILE - 1) / SS_TILE, 2ull * num_sms));
-  launch_k(k_ss_splitters, 1, 1024, smem, st, a, m, w.spl, w.cnt);
+  if (!splitters_done) {
+    const size_t smem = (size_t)SS_CAND * sizeof(uint64_t);
+    cudaError_t e = cudaFuncSetAttribute(k_ss_splitters,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    launch_k(k_ss_splitters, 1, 1024, smem, st, a, m, w.spl, w.cnt);
+    add_launches(1);
+  }
   launch_k(k_ss_count, g, SS_THREADS, 0, st, a, m, w.spl, w.cnt);
   launch_k(k_ss_scan, 1, 1024, 0, st, w.cnt, w.beg, w.cur);
   launch_k(k_ss_scatter, g, SS_THREADS, 0, st, a, m, w.spl, w.cur, b, err);
   launch_k(k_ss_bucket_sort, SS_NB + 2 * num_sms, SS_THREADS, 0, st, b, a, w.beg);
-  add_launches(5);
+  add_launches(4);
   return cudaGetLastError();
 }
 

@@ -48,20 +48,43 @@ __device__ __forceinline__ uint64_t div64(uint64_t x, const Div64& v, uint64_t* 
 }
 
 // Stratified sample: i_k = floor(k n / s) + mix64(seed ^ k) mod max(1, floor(n / s)).
+__device__ __forceinline__ uint64_t sample_index(uint64_t k, uint64_t n, uint64_t s, uint64_t seed,
+                                                 const Div64& ds, const Div64& dst) {
+  uint64_t base, r;
+  if (n < (1ull << 32)) base = div64(k * n, ds, &r);  // k < s <= n: k n < 2^64
+  else base = (uint64_t)(((unsigned __int128)k * n) / s);
+  div64(mix64(seed ^ k), dst, &r);
+  const uint64_t i = base + r;
+  return i < n ? i : n - 1;  // (i < n by the formula; the clamp keeps the load in bounds)
+}
+
+// The sample (total-order keys).  When `spl` is given (the sample sort's
+// path), CTA 0 instead draws the sample sort's evenly spaced oversample of the
+// sample -- sample positions (8 t + q) s / SS_CAND, read from the input keys
+// directly, so it overlaps the other CTAs' gathering -- sorts it and stores
+// every SS_OVER-th key as a splitter, and clears the sample sort's counters.
 template <int DT>
-__global__ void k_sample(const typename KT<DT>::U* __restrict__ keys, uint64_t n, uint64_t s,
-                         uint64_t seed, Div64 ds, Div64 dst, uint64_t* __restrict__ out) {
+__global__ void __launch_bounds__(1024)
+k_sample(const typename KT<DT>::U* __restrict__ keys, uint64_t n, uint64_t s, uint64_t seed,
+         Div64 ds, Div64 dst, uint64_t* __restrict__ out, uint64_t* __restrict__ spl,
+         uint32_t* __restrict__ cnt) {
   pdl_begin();
-  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < s;
-       k += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t base, r;
-    if (n < (1ull << 32)) base = div64(k * n, ds, &r);  // k < s <= n: k n < 2^64
-    else base = (uint64_t)(((unsigned __int128)k * n) / s);
-    div64(mix64(seed ^ k), dst, &r);
-    uint64_t i = base + r;
-    if (i >= n) i = n - 1;  // unreachable by the formula; keeps the load in bounds
-    out[k] = KT<DT>::tk(keys[i]);
+  if (spl && blockIdx.x == 0) {
+    extern __shared__ uint64_t ss_c[];
+    const uint32_t base = 8 * threadIdx.x;
+    uint64_t v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      v[q] = KT<DT>::tk(keys[sample_index((uint64_t)(base + q) * s / SS_CAND, n, s, seed, ds, dst)]);
+    for (uint32_t i = threadIdx.x; i <= SS_NB; i += blockDim.x) cnt[i] = 0;
+    ss_sort_regs(v, ss_c, SS_CAND);
+#pragma unroll
+    for (int q = SS_OVER - 1; q < 8; q += SS_OVER) spl[(base + q) / SS_OVER] = v[q];
+    return;
   }
+  const uint64_t b0 = spl ? blockIdx.x - 1 : blockIdx.x, nb = spl ? gridDim.x - 1 : gridDim.x;
+  for (uint64_t k = b0 * blockDim.x + threadIdx.x; k < s; k += nb * blockDim.x)
+    out[k] = KT<DT>::tk(keys[sample_index(k, n, s, seed, ds, dst)]);
 }
 
 __global__ void k_train_init(DevModel* hdr, uint64_t s, uint32_t* leaf_beg, uint32_t* leaf_end,
@@ -848,11 +871,19 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   launch_k(k_train_init, std::max(16, (L + 255) / 256), 256, 0, st, M.hdr, s, M.leaf_beg, M.leaf_end,
            L, W.partials, z, P.cs, P.stall, P.spin_limit);
   const uint64_t stride = std::max<uint64_t>(1, n / s);
-  launch_k(k_sample<DT>, std::max(1, gs), 256, 0, st, keys, n, s, P.seed, make_div64(s), make_div64(stride),
-                                                W.smp_a);
-  // the sample sort for large samples of 8-byte keys, else the LSD radix sort (sample_by_radix)
-  cudaError_t e = sample_by_radix(KT<DT>::W, s) ? rs_sort_enqueue(W.smp_a, W.smp_b, s, nullptr, nullptr, W.rs, err, st, num_sms)
-                                 : ss_sort_enqueue(W.smp_a, W.smp_b, s, W.ss, err, st, num_sms);
+  // the sample sort for large samples of 8-byte keys (its splitters drawn by
+  // the sampling kernel), else the LSD radix sort (sample_by_radix)
+  const bool radix = sample_by_radix(KT<DT>::W, s);
+  const size_t smem = radix ? 0 : (size_t)SS_CAND * sizeof(uint64_t);
+  cudaError_t e = cudaSuccess;
+  if (!radix && (e = cudaFuncSetAttribute(k_sample<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem)))
+    return e;
+  const int sg = std::max(1, (int)std::min<uint64_t>((s + 1023) / 1024, 2ull * num_sms)) + (radix ? 0 : 1);
+  launch_k(k_sample<DT>, sg, 1024, smem, st, keys, n, s, P.seed, make_div64(s), make_div64(stride),
+           W.smp_a, radix ? nullptr : W.ss.spl, radix ? nullptr : W.ss.cnt);
+  e = radix ? rs_sort_enqueue(W.smp_a, W.smp_b, s, nullptr, nullptr, W.rs, err, st, num_sms)
+            : ss_sort_enqueue(W.smp_a, W.smp_b, s, W.ss, err, st, num_sms, /*splitters_done=*/true);
   if (e) return e;
   if (!z_hi && (e = cudaMemsetAsync(W.hi, 0, sizeof(unsigned long long), st))) return e;
   launch_k(k_finite_range<DT>, std::max(1, gs), 256, 0, st, W.smp_a, s, M.hdr, W.hi);

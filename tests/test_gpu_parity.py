@@ -194,6 +194,29 @@ def test_train_matches_oracle(dist):
     assert np.array_equal(h, m["heavy_tk"])
 
 
+@pytest.mark.parametrize("dist", ["normal", "zipf_lognormal", "uniform_u64"])
+def test_train_large_sample_matches_oracle(dist):
+    """20M keys: a 200K-key sample of 8-byte keys, sorted by the sample sort
+    whose splitters the sampling kernel draws (smaller samples and 4-byte keys
+    take the radix sort); sorted sample exact, fit within rtol 1e-9, and the
+    whole sort bit-exact."""
+    n = 20_000_000
+    keys = make(dist, n)
+    p = ls.default_params(leaves=1000, fanout=256)
+    m = ls.train(torch.from_numpy(keys).cuda(), p, with_sample=True)
+    op = oracle.params(leaves=1000, fanout=256)
+    s = oracle.sample_size(n, op)
+    assert m["sample_size"] == s and s > (1 << 17)
+    idx = oracle.sample_indices(n, s, 0).astype(np.int64)
+    want_tk = np.sort(oracle.total_order_keys(keys[idx]))
+    assert np.array_equal(m["sorted_sample_tk"], want_tk)
+    fm = oracle.train(keys, op)
+    np.testing.assert_allclose(m["root"], fm.root, rtol=1e-9, atol=1e-15)
+    np.testing.assert_allclose(m["leaf"][:, 3:], fm.leaf[:, 3:], rtol=0, atol=0)
+    np.testing.assert_allclose(m["leaf"][:, :3], fm.leaf[:, :3], rtol=1e-9, atol=1e-12)
+    assert_same(gpu_sort(keys), keys)
+
+
 @pytest.mark.parametrize("dist", ["normal", "zipf_lognormal", "two_values", "timestamp_u32",
                                   "exponential_f32", "f64_specials"])
 def test_level0_histogram_matches_spec(dist):
