@@ -162,7 +162,7 @@ __device__ __forceinline__ uint32_t heavy_hash(uint64_t t) {  // slot index
 }
 
 // Level-0 bucket head: first extended slot and heavy list [hoff, hoff+nh).
-struct BucketHead {
+struct __align__(8) BucketHead {   // one 8-byte load
   uint32_t ext_base;
   uint32_t hoff_nh;    // hoff << 4 | nh
 };
@@ -188,7 +188,7 @@ struct CellRoot {          // FP32 RMI of the cell index, on key_f32(x)
   int L;
   int pad;
 };
-struct CellLeaf {          // F = clamp(A x + B, LO, HI), HI_l = LO_{l+1}
+struct __align__(16) CellLeaf {  // F = clamp(A x + B, LO, HI), HI_l = LO_{l+1}; one 16-byte load
   float A, B, LO, HI;
 };
 
