@@ -261,6 +261,7 @@ static void plan_call(const ls_params* prm, int dt, uint64_t n, uintptr_t addr, 
   P->seed = p.seed;
   P->lim.c_tiny = 512;
   P->lim.c_small = 2048;
+  P->lim.c_mid0 = 3072;
   P->lim.c_mid = 4096;
   P->lim.c_large = 8192;
   P->lim.l1_target = 3072;
@@ -334,7 +335,7 @@ struct Workspace {
   // offsets
   size_t o_scratch, o_smp_a, o_smp_b, o_rank, o_flags, o_cpos, o_cand, o_sel, o_sellen, o_hlen, o_nh, o_part, o_hi,
       o_tscan, o_ss_spl, o_ss_words, o_rs_hist, o_rs_skip, o_rs_status, o_hdr, o_leaf64, o_thr, o_cell, o_cleaf, o_hkey, o_hval, o_heads, o_heavy,
-      o_lbeg, o_lend, o_hist, o_offs, o_l0scan, o_jobs_fill, o_jobs_s, o_jobs_l, o_jobs_m, o_jobs_fb2, o_jobs_t, o_jobs_r,
+      o_lbeg, o_lend, o_hist, o_offs, o_l0scan, o_jobs_fill, o_jobs_s, o_jobs_l, o_jobs_m, o_jobs_m0, o_jobs_fb2, o_jobs_t, o_jobs_r,
       o_jobs_fb, o_jobs_r2, o_jobs_r3, o_pk, o_sid, o_ccount, o_counts, o_aux, o_tot, o_l1cnt, o_l1off, o_l1cur, o_jmin, o_jmax, o_l1scan,
       o_ubase, o_units;
   size_t tscan_bytes, rs_status_bytes, l0scan_bytes, l1scan_bytes;
@@ -392,6 +393,7 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->o_jobs_s = c.take<Job>(cap_above(P.n, P.lim.c_tiny));
   w->o_jobs_l = c.take<Job>(cap_above(P.n, P.lim.c_mid));
   w->o_jobs_m = c.take<Job>(cap_above(P.n, P.lim.c_small));
+  w->o_jobs_m0 = c.take<Job>(cap_above(P.n, P.lim.c_small));
   w->o_jobs_fb2 = c.take<Job>(cap_above(P.n, FILL_BIG - 1));
   w->o_jobs_t = c.take<Job>(P.cap1);
   w->o_jobs_r = c.take<Job>(P.cap0);
@@ -401,7 +403,7 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->o_sid = c.take<uint16_t>(with_scratch ? P.n + 16 : 0);
   w->o_jobs_r2 = c.take<Job>(P.cap_r);
   w->o_jobs_r3 = c.take<Job>(P.cap_r);
-  w->o_counts = c.take<unsigned long long>(18);  // 16 counters + the call's CallStatus
+  w->o_counts = c.take<unsigned long long>(N_COUNTS + 2);  // counters + the call's CallStatus
   w->o_aux = c.take<uint8_t>((P.capj + 1) * 32);
   w->o_tot = c.take<unsigned long long>(4);
   w->o_l1cnt = c.take<uint32_t>(P.cap_c);
@@ -483,6 +485,7 @@ static Bound bind(const Plan& P, const Workspace& w) {
   b.lists.sort_m = mk(w.o_jobs_m, b.counts + 7, cap_above(P.n, P.lim.c_small));
   b.lists.fill_big = mk(w.o_jobs_fb2, b.counts + 12, cap_above(P.n, FILL_BIG - 1));
   b.lists.sort_t = mk(w.o_jobs_t, b.counts + 13, P.cap1);
+  b.lists.sort_m0 = mk(w.o_jobs_m0, b.counts + 16, cap_above(P.n, P.lim.c_small));
   b.lists.refine = mk(w.o_jobs_r, b.counts + 3, P.cap0);
   b.lists.fallback = mk(w.o_jobs_fb, b.counts + 4, cap_above(P.n, P.lim.c_large));
   b.lists.refine2 = mk(w.o_jobs_r2, b.counts + 5, P.cap_r);
@@ -562,12 +565,12 @@ static cudaError_t enqueue_sort(const Plan& P, const Workspace& w, void* keys, D
                                 cudaStream_t st, Events* ev, const CallOpts& o) {
   const Bound b = bind(P, w);
   Marks mk{ev && ev->on ? ev->ev : nullptr, NMARK};
-  uint32_t* err = (uint32_t*)(b.counts + 16);  // the call's own CallStatus
+  uint32_t* err = (uint32_t*)(b.counts + N_COUNTS);  // the call's own CallStatus
   // the first training kernel zeroes the list counters and the level-0 scan
   // words and initialises the call's status block (no memsets in the stream)
   ZeroList z{};
   z.p[0] = b.counts;
-  z.words[0] = 16 * 2;
+  z.words[0] = N_COUNTS * 2;
   z.p[1] = at<void>(w, w.o_l0scan);
   z.words[1] = (uint32_t)(w.l0scan_bytes / 4);
   mark(&mk, 0, st);
@@ -582,7 +585,7 @@ static cudaError_t enqueue_sort(const Plan& P, const Workspace& w, void* keys, D
   mark(&mk, 7, st);
   LS_TRY(buckets_enqueue(P.dt, keys, a.scratch, P.n, b.M, b.lists, P.cap1, P.cap1, P.cap1,
                          b.counts + 8, err, st, d->num_sms, &mk, 8));
-  LS_TRY(end_call(b.counts, 16, o, st));
+  LS_TRY(end_call(b.counts, N_COUNTS, o, st));
   mark(&mk, 10, st);
   return cudaSuccess;
 }
@@ -633,7 +636,7 @@ static void fill_stats(const Plan& P, const Workspace& w, Events* ev, ls_stats* 
   stats->n_launches = launches;
   DevModel hdr;
   cudaMemcpy(&hdr, at<void>(w, w.o_hdr), sizeof(hdr), cudaMemcpyDeviceToHost);
-  unsigned long long counts[16];
+  unsigned long long counts[N_COUNTS];
   cudaMemcpy(counts, at<void>(w, w.o_counts), sizeof(counts), cudaMemcpyDeviceToHost);
   stats->sample_size = hdr.s;
   stats->sample_finite = hdr.s_fin;
@@ -642,7 +645,7 @@ static void fill_stats(const Plan& P, const Workspace& w, Events* ev, ls_stats* 
   stats->n_heavy = hdr.nheavy;
   stats->n_ext = hdr.n_ext;
   stats->n_level1 = counts[3];
-  stats->n_segments = counts[1] + counts[2] + counts[7] + counts[13];
+  stats->n_segments = counts[1] + counts[2] + counts[7] + counts[13] + counts[16];
   stats->n_fallback = counts[4];
   stats->n_range = counts[5] + counts[6];
   // largest slot and equality keys from the level-0 offsets
@@ -677,7 +680,8 @@ static void fill_stats(const Plan& P, const Workspace& w, Events* ev, ls_stats* 
   stats->n_fallback_keys = job_keys(w.o_jobs_fb, counts[4], cap_above(P.n, P.lim.c_large),
                                     &stats->max_fallback);
   stats->n_large_keys = job_keys(w.o_jobs_l, counts[2], cap_above(P.n, P.lim.c_mid), nullptr) +
-                        job_keys(w.o_jobs_m, counts[7], cap_above(P.n, P.lim.c_small), nullptr);
+                        job_keys(w.o_jobs_m, counts[7], cap_above(P.n, P.lim.c_small), nullptr) +
+                        job_keys(w.o_jobs_m0, counts[16], cap_above(P.n, P.lim.c_small), nullptr);
 }
 
 }  // namespace ls
@@ -801,6 +805,7 @@ ls_status ls::batch_call(void* const* keys, const size_t* n, size_t count, ls_dt
   SortLimits lim;
   lim.c_tiny = 512;
   lim.c_small = 2048;
+  lim.c_mid0 = 3072;
   lim.c_mid = 4096;
   lim.c_large = 8192;
   lim.l1_target = 3072;
@@ -810,10 +815,10 @@ ls_status ls::batch_call(void* const* keys, const size_t* n, size_t count, ls_dt
   // workspace
   Carver c;
   const size_t o_scr = c.take<uint8_t>(N * W);
-  size_t o_list[10];
-  const uint64_t caps[10] = {cap1, cap1, cap1, cap1, cap1, capj, capj, cap1, capj, cap1};
-  for (int i = 0; i < 10; ++i) o_list[i] = c.take<Job>(caps[i]);
-  const size_t o_counts = c.take<unsigned long long>(18);  // 16 counters + the call's CallStatus
+  size_t o_list[11];
+  const uint64_t caps[11] = {cap1, cap1, cap1, cap1, cap1, capj, capj, cap1, capj, cap1, cap1};
+  for (int i = 0; i < 11; ++i) o_list[i] = c.take<Job>(caps[i]);
+  const size_t o_counts = c.take<unsigned long long>(N_COUNTS + 2);  // counters + CallStatus
   const size_t o_aux = c.take<uint8_t>((capj + 1) * 32);
   const size_t o_tot = c.take<unsigned long long>(4);
   const size_t o_cnt = c.take<uint32_t>(cap_c);
@@ -846,8 +851,9 @@ ls_status ls::batch_call(void* const* keys, const size_t* n, size_t count, ls_dt
   lists.fill_big = mk(7, 12);
   lists.refine = mk(8, 3);
   lists.sort_t = mk(9, 13);
+  lists.sort_m0 = mk(10, 16);
   // initial jobs, one per array
-  std::vector<Job> jt, js, jm, jl, jr;
+  std::vector<Job> jt, js, jm0, jm, jl, jr;
   uint64_t off = 0;
   char* scr = at<char>(w, o_scr);
   for (size_t i = 0; i < count; ++i) {
@@ -862,6 +868,7 @@ ls_status ls::batch_call(void* const* keys, const size_t* n, size_t count, ls_dt
     off += n[i];
     if (n[i] <= lim.c_tiny) { j.kind = JOB_SORT_RANGE; jt.push_back(j); }
     else if (n[i] <= lim.c_small) { j.kind = JOB_SORT_RANGE; js.push_back(j); }
+    else if (n[i] <= lim.c_mid0) { j.kind = JOB_SORT_RANGE; jm0.push_back(j); }
     else if (n[i] <= lim.c_mid) { j.kind = JOB_SORT_RANGE; jm.push_back(j); }
     else if (n[i] <= lim.c_large) { j.kind = JOB_SORT_RANGE; jl.push_back(j); }
     else {
@@ -872,14 +879,15 @@ ls_status ls::batch_call(void* const* keys, const size_t* n, size_t count, ls_dt
       jr.push_back(j);
     }
   }
-  unsigned long long hc[18] = {0};  // list counters, then the call's CallStatus
+  unsigned long long hc[N_COUNTS + 2] = {0};  // list counters, then the call's CallStatus
   {
     CallStatus cs{0u, o.stall, o.spin_limit};
-    std::memcpy(&hc[16], &cs, sizeof(cs));
+    std::memcpy(&hc[N_COUNTS], &cs, sizeof(cs));
   }
   hc[1] = js.size(); hc[7] = jm.size(); hc[2] = jl.size(); hc[5] = jr.size(); hc[13] = jt.size();
+  hc[16] = jm0.size();
   // one pinned upload: the counters, then the five initial lists
-  const size_t up_bytes = sizeof(hc) + (jt.size() + js.size() + jm.size() + jl.size() + jr.size()) * sizeof(Job);
+  const size_t up_bytes = sizeof(hc) + (jt.size() + js.size() + jm0.size() + jm.size() + jl.size() + jr.size()) * sizeof(Job);
   Staging* sg = nullptr;
   if (!e) e = staging_acquire(d, up_bytes, &sg);
   if (!e) {
@@ -897,6 +905,7 @@ ls_status ls::batch_call(void* const* keys, const size_t* n, size_t count, ls_dt
     e = cudaMemcpyAsync(counts, hp, sizeof(hc), cudaMemcpyHostToDevice, st);
     if (!e) e = put(jt, 9);
     if (!e) e = put(js, 1);
+    if (!e) e = put(jm0, 10);
     if (!e) e = put(jm, 4);
     if (!e) e = put(jl, 2);
     if (!e) e = put(jr, 5);
@@ -928,12 +937,12 @@ ls_status ls::batch_call(void* const* keys, const size_t* n, size_t count, ls_dt
     lv[0].fmax = lv[1].fmax = MAX_F1;
     lv[2].fmax = 256;
     ModelPtrs M{};
-    uint32_t* err = (uint32_t*)(counts + 16);
+    uint32_t* err = (uint32_t*)(counts + N_COUNTS);
     e = levels_enqueue(dtype, nullptr, nullptr, N, M, lists, lim, l, lv, 3, err, st, d->num_sms);
     if (!e) e = fill_enqueue(dtype, nullptr, lists, nullptr, nullptr, st, d->num_sms);
     if (!e) e = buckets_enqueue(dtype, nullptr, nullptr, N, M, lists, cap1, cap1, cap1, counts + 8,
                                 err, st, d->num_sms, nullptr, 0);
-    if (!e) e = end_call(counts, 16, o, st);
+    if (!e) e = end_call(counts, N_COUNTS, o, st);
   }
   cudaFreeAsync(w.base, st);
   return to_status(e);
@@ -1055,7 +1064,7 @@ ls_status ls_level0_histogram(const void* keys, size_t n, ls_dtype dtype, void* 
   if ((e = ws_alloc(d, &w, st))) return to_status(e);
   const Bound b = bind(P, w);
   uint32_t* err = &d->slots[slot_of(d->id, st, true)].word;
-  e = cudaMemsetAsync(b.counts, 0, 16 * sizeof(unsigned long long), st);
+  e = cudaMemsetAsync(b.counts, 0, N_COUNTS * sizeof(unsigned long long), st);
   if (!e) e = enqueue_train(P, b, keys, d, err, st);
   if (!e) e = cudaMemsetAsync(at<void>(w, w.o_l0scan), 0, w.l0scan_bytes, st);
   Level0Args a0 = level0_args(P, b, w, keys, err);

@@ -415,6 +415,7 @@ k_fallback(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, ModelPtrs M, J
 // ---------------------------------------------------------------- host enqueue
 constexpr int BS_TINY_T = 128, BS_TINY_K = 4;      // CAP 512
 constexpr int BS_SMALL_T = 256, BS_SMALL_K = 8;    // CAP 2048
+constexpr int BS_MID0_T = 384, BS_MID0_K = 8;      // CAP 3072
 constexpr int BS_MID_T = 512, BS_MID_K = 8;        // CAP 4096
 constexpr int BS_LARGE_T = 512, BS_LARGE_K = 16;   // CAP 8192
 
@@ -427,6 +428,10 @@ static cudaError_t buckets_cfg_dt() {
   e = cudaFuncSetAttribute(k_bucket_sort<DT, BS_SMALL_T, BS_SMALL_K>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)BucketCfg<DT, BS_SMALL_T, BS_SMALL_K>::SMEM);
+  if (e) return e;
+  e = cudaFuncSetAttribute(k_bucket_sort<DT, BS_MID0_T, BS_MID0_K>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)BucketCfg<DT, BS_MID0_T, BS_MID0_K>::SMEM);
   if (e) return e;
   e = cudaFuncSetAttribute(k_bucket_sort<DT, BS_MID_T, BS_MID_K>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -466,6 +471,12 @@ static cudaError_t buckets_dt(void* keys, void* scratch, const ModelPtrs& M, con
   launch_k(k_bucket_sort<DT, BS_SMALL_T, BS_SMALL_K>, gs, BS_SMALL_T, BucketCfg<DT, BS_SMALL_T, BS_SMALL_K>::SMEM, st, (U*)keys, (const U*)scratch, M, lists.sort_s, ctrs + 0, err);
   mark(mk, mb + 0, st);
   {
+    // segments of 2049..3072 keys: 384 threads, so that fewer key slots of a
+    // thread stay empty than in the 4096-key class
+    const unsigned gm0 = (unsigned)std::min<uint64_t>(std::max<uint64_t>(cap_s, 1), 4ull * num_sms);
+    launch_k(k_bucket_sort<DT, BS_MID0_T, BS_MID0_K>, gm0, BS_MID0_T, BucketCfg<DT, BS_MID0_T, BS_MID0_K>::SMEM, st, (U*)keys, (const U*)scratch, M, lists.sort_m0, ctrs + 9, err);
+  }
+  {
     const unsigned gm = (unsigned)std::min<uint64_t>(std::max<uint64_t>(cap_s, 1), 4ull * num_sms);
     launch_k(k_bucket_sort<DT, BS_MID_T, BS_MID_K>, gm, BS_MID_T, BucketCfg<DT, BS_MID_T, BS_MID_K>::SMEM, st, (U*)keys, (const U*)scratch, M, lists.sort_m, ctrs + 3, err);
   }
@@ -473,7 +484,7 @@ static cudaError_t buckets_dt(void* keys, void* scratch, const ModelPtrs& M, con
   mark(mk, mb + 1, st);
   launch_k(k_fallback<DT>, gf, 512, BucketCfg<DT, 512, 16>::SMEM_FB, st, (U*)keys, (U*)scratch, M,
                                                                   lists.fallback, ctrs + 2, err);
-  add_launches(5);
+  add_launches(6);
   return cudaGetLastError();
 }
 

@@ -667,6 +667,7 @@ __global__ void k_classify0(Level0Args a, Lists lists, SortLimits lim) {
     job.m = job.span = size;
     if (size <= lim.c_tiny) { job.kind = JOB_SORT; push_job(lists.sort_t, job, a.err); }
     else if (size <= lim.c_small) { job.kind = JOB_SORT; push_job(lists.sort_s, job, a.err); }
+    else if (size <= lim.c_mid0) { job.kind = JOB_SORT; push_job(lists.sort_m0, job, a.err); }
     else if (size <= lim.c_mid) { job.kind = JOB_SORT; push_job(lists.sort_m, job, a.err); }
     else if (size <= lim.c_large) { job.kind = JOB_SORT; push_job(lists.sort_l, job, a.err); }
     else { job.kind = JOB_REFINE; push_job(lists.refine, job, a.err); }
@@ -1154,6 +1155,7 @@ __global__ void k_l1_classify(Lists lists, LevelArgs la, SortLimits lim, Level1W
     const uint32_t sk = la.mode ? JOB_SORT_RANGE : JOB_SORT;
     if (cntc <= lim.c_tiny) { job.kind = sk; push_job(lists.sort_t, job, err); }
     else if (cntc <= lim.c_small) { job.kind = sk; push_job(lists.sort_s, job, err); }
+    else if (cntc <= lim.c_mid0) { job.kind = sk; push_job(lists.sort_m0, job, err); }
     else if (cntc <= lim.c_mid) { job.kind = sk; push_job(lists.sort_m, job, err); }
     else if (cntc <= lim.c_large) { job.kind = sk; push_job(lists.sort_l, job, err); }
     else { job.kind = la.next_kind; push_job(la.next, job, err); }

@@ -41,6 +41,14 @@ struct Level0Args {
   uint32_t may_compact;  // 0: leave `keys` untouched (read-only callers)
 };
 
+// The call's device counters (unsigned long long each): list counts and the
+// in-bucket kernels' job counters, followed by the call's CallStatus.
+//  [0] fill  [1] sort_s  [2] sort_l  [3] refine  [4] fallback  [5] refine2
+//  [6] refine3  [7] sort_m  [8..11] job counters of sort_s, sort_l, fallback,
+//  sort_m  [12] fill_big  [13] sort_t  [14] job counter of sort_t
+//  [16] sort_m0  [17] job counter of sort_m0
+constexpr int N_COUNTS = 20;
+
 // Lists produced by classification (device-side counters).
 struct Lists {
   JobList fill, sort_s, sort_l, refine, fallback;
@@ -48,6 +56,7 @@ struct Lists {
   JobList sort_m;            // segments in (c_small, c_mid]
   JobList fill_big;          // fills of at least FILL_BIG keys (written by the whole grid)
   JobList sort_t;            // segments of at most c_tiny keys
+  JobList sort_m0;           // segments in (c_small, c_mid0]
 };
 
 // One refinement level: split the jobs of `in` into sub-buckets, by the model
@@ -70,6 +79,7 @@ struct LevelArgs {
 struct SortLimits {
   uint64_t c_tiny;       // segments up to this go to the tiny in-bucket kernel
   uint64_t c_small;      // ... up to this to the small one
+  uint64_t c_mid0;       // ... up to this to the 384-thread one
   uint64_t c_mid;        // ... up to this to the middle one
   uint64_t c_large;      // ... up to this to the large kernel, above: refine/fallback
   uint64_t l1_target;    // target sub-bucket size of the level-1 split
