@@ -229,7 +229,11 @@ def run_batched(ls, torch, count: int, steps: int, warmup: int, with_loop: bool 
     for i in (0, count // 2, count - 1):
         seg = res[offs[i]:offs[i + 1]]
         ok = ok and bool(np.all(seg[1:] >= seg[:-1]))
+    big = sum(1 for x in sizes if x > 8192)
     out = {"workload": f"batch_{count}_f64", "arrays": count, "keys": total,
+           "model": (f"{big} arrays above 8192 keys split by a line through their own key range "
+                     "(a one-leaf model; split targets per size class from csrc/ls_tuned.h), "
+                     f"{count - big} sorted directly in one segment; no sampled RMI per array"),
            "batched_ms": float(np.median(mb)), "batched_keys_per_s": total / (np.median(mb) / 1e3),
            "steps": steps, "warmup": warmup, "sorted_sampled": ok}
     if with_loop:

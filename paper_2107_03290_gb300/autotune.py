@@ -9,7 +9,9 @@ float64 arrays, lognormal sizes with median 64K clipped to [1K, 4M], each
 N(0,1), U[0,1) or Zipf(1.1) over 10^4 values), times ls_sort_batch_ex with CUDA
 events (inputs restored from a device copy outside the timing, median of
 several runs), checks the fastest setting's output, and writes the table
-csrc/ls_tuned.h that the library compiles in.
+csrc/ls_tuned.h that the library compiles in.  For comparison it also times
+the learned alternative on the same arrays (a sampled RMI per array: ls_sort
+on each in turn) and records it in the table's comment.
 
   python -m paper_2107_03290_gb300.autotune [--out PATH] [--reps 5]
 """
@@ -71,6 +73,19 @@ def sweep(reps: int = 5, count: int = 4096):
                     ms.append(e0.elapsed_time(e1))
             times[tgt] = float(np.median(ms))
         best = min(times, key=times.get)
+        # the learned alternative: a sampled RMI per array (ls_sort on each array
+        # in turn, same stream), timed once after a warm-up pass
+        learned = []
+        for r in range(2):
+            work.copy_(pristine)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for v in views:
+                ls.sort_(v)
+            e1.record(st)
+            e1.synchronize()
+            learned.append(e0.elapsed_time(e1))
         # the chosen setting must sort every array of the class
         split = [0, 0, 0]
         split[c] = best
@@ -81,7 +96,8 @@ def sweep(reps: int = 5, count: int = 4096):
         for i, a in enumerate(sel):
             if not np.array_equal(out[offs[i]:offs[i + 1]], np.sort(a)):
                 raise RuntimeError(f"class {c}: array {i} not sorted with target {best}")
-        result[c] = {"arrays": len(sel), "keys": int(offs[-1]), "ms": times, "best": best}
+        result[c] = {"arrays": len(sel), "keys": int(offs[-1]), "ms": times, "best": best,
+                     "learned_ms": float(learned[-1])}
         del pristine, work, views
         torch.cuda.empty_cache()
     return result
@@ -104,6 +120,7 @@ def write_header(result: dict, path: str, gpu: str):
             continue
         row = ", ".join(f"{t}: {v:.3f}" for t, v in r["ms"].items())
         lines.append(f"//   class {c} ({r['arrays']} arrays, {r['keys']} keys): {row}")
+        lines.append(f"//     (a sampled RMI per array instead, ls_sort on each: {r['learned_ms']:.1f} ms)")
     lines += [
         "#pragma once",
         "#include <stdint.h>",
@@ -127,7 +144,8 @@ def main():
     res = sweep(args.reps)
     write_header(res, args.out, torch.cuda.get_device_name(0))
     for c, r in sorted(res.items()):
-        print(f"class {c}: best {r['best']}  " + "  ".join(f"{t}:{v:.3f}" for t, v in r["ms"].items()))
+        print(f"class {c}: best {r['best']}  " + "  ".join(f"{t}:{v:.3f}" for t, v in r["ms"].items())
+              + f"  learned per array: {r['learned_ms']:.1f}")
 
 
 if __name__ == "__main__":
