@@ -147,18 +147,22 @@ struct HeavyEntry {    // a heavy value of one level-0 bucket
   uint32_t ext;        // its equality slot
 };
 
-// Direct-mapped table of the heavy values (total-order key -> equality slot):
-// one 8-byte probe per key.  A slot keeps the most frequent of the values
-// hashing to it; a free slot holds a key that hashes to another slot, so a
-// probe never matches it.  The values that lost their slot, and the value
-// HASH_EMPTY itself (a valid uint64 key), are not in the table: their keys take
-// the full lookup.
+// Direct-mapped table of the heavy values (key bits -> equality slot): one
+// 8-byte probe per key.  The table holds the raw bit patterns of the values
+// (zero-extended for 4-byte keys; equal bits <=> equal total-order keys), so a
+// probe needs no total-order conversion.  A slot keeps the most frequent of
+// the values hashing to it; a free slot holds a key that hashes to another
+// slot (0, or 1 in slot 0), so a probe never matches it.  The values that lost
+// their slot, and the bit pattern HASH_EMPTY, are not in the table: their
+// keys take the full lookup.
 constexpr uint32_t HASH_SET_BITS = 13;
 constexpr uint32_t HASH_SETS = 1u << HASH_SET_BITS;
 constexpr uint32_t HASH_SIZE = HASH_SETS;          // entries (one per slot)
 constexpr uint64_t HASH_EMPTY = ~0ull;
-__device__ __forceinline__ uint32_t heavy_hash(uint64_t t) {  // slot index
-  return (uint32_t)((t * 0x9E3779B97F4A7C15ull) >> (64 - HASH_SET_BITS));
+// Slot of a key's bits: the two halves folded, then 32-bit Fibonacci hashing.
+__device__ __forceinline__ uint32_t heavy_hash(uint64_t bits) {
+  const uint32_t f = (uint32_t)bits ^ (uint32_t)(bits >> 32);
+  return (f * 0x9E3779B1u) >> (32 - HASH_SET_BITS);
 }
 
 // Level-0 bucket head: first extended slot and heavy list [hoff, hoff+nh).

@@ -397,9 +397,9 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
         // one 8-byte probe: a hit is a heavy value; anything else (including a
         // heavy value that lost its slot) takes the full lookup (free slots
         // hold keys of other slots, so only a table key matches)
-        const uint64_t t = KT<DT>::tk(u[k]);
-        const uint32_t slot = heavy_hash(t);
-        const uint32_t e = hk[slot] == t ? (uint32_t)hv[slot] : 0xFFFFFFFFu;
+        const uint64_t bits = (uint64_t)u[k];
+        const uint32_t slot = heavy_hash(bits);
+        const uint32_t e = hk[slot] == bits ? (uint32_t)hv[slot] : 0xFFFFFFFFu;
         if (e != 0xFFFFFFFFu) {  // equality key: counted, never moved
           if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
           if (!compact) pk[i - a0] = PK_EQ;

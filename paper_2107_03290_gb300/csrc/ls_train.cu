@@ -820,24 +820,25 @@ k_heavy_heads(const uint64_t* __restrict__ sel, const uint32_t* __restrict__ sel
 // (run << 32 | ~index), and the winners then replace their packed records.
 // Slots left free get a key of another slot (0, or 1 in slot 0), so a probe
 // needs no emptiness test (hash_probes = 1 marks the table as built).
+template <int DT>
 __global__ void __launch_bounds__(1024)
 k_heavy_hash(DevModel* hdr, const HeavyEntry* __restrict__ heavy, const uint32_t* __restrict__ hlen,
              unsigned long long* hkey, uint16_t* hval) {
   pdl_begin();
   const uint32_t H = hdr->nheavy;
   if (2 * H > HASH_SIZE) return;  // too full to help
-  // (uint64 key 2^64-1 is left to the full lookup; a zero run never wins)
+  // (the bit pattern 2^64-1 is left to the full lookup; a zero run never wins)
   for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) {
-    const uint64_t t = heavy[i].tk;
-    if (t != HASH_EMPTY)
-      atomicMax(&hkey[heavy_hash(t)], (unsigned long long)hlen[i] << 32 | (uint32_t)~i);
+    const uint64_t b = (uint64_t)KT<DT>::from_tk(heavy[i].tk);
+    if (b != HASH_EMPTY)
+      atomicMax(&hkey[heavy_hash(b)], (unsigned long long)hlen[i] << 32 | (uint32_t)~i);
   }
   __syncthreads();
   for (uint32_t p = threadIdx.x; p < HASH_SIZE; p += blockDim.x) {
     const unsigned long long w = hkey[p];
     const uint32_t i = ~(uint32_t)w;
     if ((w >> 32) != 0 && i < H) {
-      hkey[p] = heavy[i].tk;
+      hkey[p] = (uint64_t)KT<DT>::from_tk(heavy[i].tk);
       hval[p] = (uint16_t)heavy[i].ext;
     } else {
       hkey[p] = p == 0 ? 1ull : 0ull;  // heavy_hash(0) = 0, heavy_hash(1) != 0
@@ -920,7 +921,7 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   launch_k(k_heavy_heads<DT>, 1, 1024, 0, st, W.sel, W.sellen, W.nh, P.f0, (int)P.hpb, M.hdr, M.cleaf,
                                         M.heads, M.heavy, W.hlen);
   if (!z_hkey && (e = cudaMemsetAsync(M.hkey, 0, HASH_SIZE * sizeof(uint64_t), st))) return e;
-  launch_k(k_heavy_hash, 1, 1024, 0, st, M.hdr, M.heavy, W.hlen, (unsigned long long*)M.hkey, M.hval);
+  launch_k(k_heavy_hash<DT>, 1, 1024, 0, st, M.hdr, M.heavy, W.hlen, (unsigned long long*)M.hkey, M.hval);
   add_launches(21);
   return cudaGetLastError();
 }

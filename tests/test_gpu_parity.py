@@ -233,14 +233,16 @@ def test_level0_histogram_matches_spec(dist):
 
 
 def _colliding_heavy(n: int, seed: int) -> np.ndarray:
-    """Heavy values that share slots of the level-0 heavy table (multiply-shift
-    of the total-order key, 13 bits): six values in each of four slots, with
-    decreasing frequencies, so that most of them lose their slot and must be
-    recognised by the full lookup; 30% normal background."""
+    """Heavy values that share slots of the level-0 heavy table (the key's
+    bits, halves folded by xor, 32-bit Fibonacci hashing to 13 bits): six
+    values in each of four slots, with decreasing frequencies, so that most of
+    them lose their slot and must be recognised by the full lookup; 30% normal
+    background."""
     rng = np.random.default_rng(seed)
     cand = np.unique(rng.lognormal(0.0, 2.0, 200_000))
-    tk = oracle.total_order_keys(cand).astype(object)
-    slot = np.array([((int(t) * 0x9E3779B97F4A7C15) & (2**64 - 1)) >> 51 for t in tk])
+    bits = cand.view(np.uint64)
+    fold = ((bits ^ (bits >> np.uint64(32))) & np.uint64(0xFFFFFFFF)).astype(np.uint64)
+    slot = (((fold * np.uint64(0x9E3779B1)) & np.uint64(0xFFFFFFFF)) >> np.uint64(19)).astype(np.int64)
     vals = []
     for sl in np.flatnonzero(np.bincount(slot, minlength=8192) >= 6)[:4]:
         vals.extend(cand[slot == sl][:6])
