@@ -5,9 +5,12 @@
 //
 // NVIDIA GB300, 2026-12-04: ls_sort_batch_ex on the batched
 // workload's arrays of each class, median ms per call:
-//   class 0 (1948 arrays, 66320707 keys): 512: 4.021, 768: 4.072, 1024: 4.063, 1536: 4.041, 2048: 4.068, 2560: 4.096, 3072: 4.213, 4096: 4.252
-//   class 1 (1901 arrays, 320226495 keys): 512: 12.152, 768: 12.402, 1024: 12.202, 1536: 12.431, 2048: 12.559, 2560: 13.436, 3072: 13.598, 4096: 14.053
-//   class 2 (132 arrays, 114713439 keys): 512: 4.334, 768: 4.306, 1024: 4.271, 1536: 4.376, 2048: 4.345, 2560: 4.654, 3072: 4.715, 4096: 4.832
+//   class 0 (1948 arrays, 66320707 keys): 512: 3.971, 768: 4.049, 1024: 4.016, 1536: 4.010, 2048: 4.024, 2560: 4.030, 3072: 4.158, 4096: 4.222
+//     (a sampled RMI per array instead, ls_sort on each: 473.9 ms)
+//   class 1 (1901 arrays, 320226495 keys): 512: 11.991, 768: 12.160, 1024: 12.044, 1536: 12.258, 2048: 12.337, 2560: 13.151, 3072: 13.363, 4096: 13.932
+//     (a sampled RMI per array instead, ls_sort on each: 518.6 ms)
+//   class 2 (132 arrays, 114713439 keys): 512: 4.349, 768: 4.320, 1024: 4.293, 1536: 4.412, 2048: 4.390, 2560: 4.601, 3072: 4.740, 4096: 4.889
+//     (a sampled RMI per array instead, ls_sort on each: 46.6 ms)
 #pragma once
 #include <stdint.h>
 
