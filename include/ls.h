@@ -66,6 +66,14 @@ typedef struct ls_params {
 } ls_params;
 
 #define LS_FLAG_NO_HEAVY 1u  /* disable equality buckets                                */
+/* The in-place variant (Sec. 4.2, Alg. 1: fragments flushed over positions
+ * already read, then Defragment).  Every partitioning step works inside the
+ * caller's array: the workspace holds no n-key scratch and no per-key ids,
+ * only per-bucket tables, one byte per 128-byte block of keys and small
+ * per-CTA leftover areas (ls_workspace_bytes gives the exact size).  Level 0
+ * then uses at most 512 buckets and a split at most 256 sub-buckets.  The
+ * result is the same sorted array. */
+#define LS_FLAG_IN_PLACE 2u
 
 /* Per-call statistics.  Passing a non-NULL ls_stats makes the call record CUDA
  * events and synchronize the stream before returning. */
@@ -97,6 +105,7 @@ typedef struct ls_stats {
   uint64_t max_fallback;     /* largest fallback segment                      */
   uint64_t n_large_keys;     /* keys in counting-sort segments > 2048         */
   uint64_t n_range;          /* segments split by key range (levels 2 and 3)  */
+  uint64_t workspace_bytes;  /* device workspace the call allocated            */
 } ls_stats;
 
 /* Model export for parity checks (host buffers owned by the caller). */
@@ -128,6 +137,11 @@ ls_status ls_sort(void* keys, size_t n, ls_dtype dtype, void* stream);
 /* ls_sort with explicit parameters (NULL: defaults) and optional statistics. */
 ls_status ls_sort_ex(void* keys, size_t n, ls_dtype dtype, void* stream,
                      const ls_params* params, ls_stats* stats);
+
+/* Bytes of device workspace that ls_sort_ex(keys, n, dtype, ..., params, ...)
+ * allocates from the library's pool on the current device (0 for n < 2 or an
+ * invalid dtype).  The caller's keys are not included. */
+size_t ls_workspace_bytes(size_t n, ls_dtype dtype, const ls_params* params);
 
 /* End-to-end form: `host_keys` is HOST memory (pinned or pageable).  Copies the
  * keys to the device, sorts them and copies them back; returns when the sorted
@@ -255,7 +269,10 @@ typedef struct ls_server_config {
                                 `stall` for every request                        */
   uint32_t debug_spin_limit; /* test hook (0 in normal use): ls_debug_set_wait's
                                 `spin_limit` for every request                   */
-  uint32_t reserved[3];
+  uint32_t in_place;         /* 1: requests sorted by ls_sort (more than
+                                LS_SERVER_BATCH_MAX keys) use LS_FLAG_IN_PLACE,
+                                and admission charges their in-place workspace */
+  uint32_t reserved[2];
 } ls_server_config;
 
 /* Requests of at most this many keys that are admitted together are sorted

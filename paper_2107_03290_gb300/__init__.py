@@ -22,7 +22,7 @@ _INC = os.path.join(os.path.dirname(_HERE), "include")
 _SO = os.path.join(_HERE, "libls.so")
 _BUILD = os.path.join(_HERE, "_build")
 SOURCES = ["ls_train.cu", "ls_partition.cu", "ls_bucket.cu", "ls_api.cu", "ls_server.cpp",
-           "ls_noalloc.cu", "ls_pairs.cu"]
+           "ls_noalloc.cu", "ls_pairs.cu", "ls_inplace.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 DTYPE_CODES = {"f64": 0, "u64": 1, "f32": 2, "u32": 3}
@@ -88,6 +88,7 @@ class Params(ctypes.Structure):
 
 
 FLAG_NO_HEAVY = 1
+FLAG_IN_PLACE = 2
 
 
 class Stats(ctypes.Structure):
@@ -100,7 +101,7 @@ class Stats(ctypes.Structure):
                                                   "n_level1", "n_segments", "n_fallback",
                                                   "n_fill", "n_launches")]
                 + [(k, ctypes.c_uint64) for k in ("n_fallback_keys", "max_fallback", "n_large_keys",
-                                                  "n_range")])
+                                                  "n_range", "workspace_bytes")])
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -123,7 +124,7 @@ class ServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
                 ("max_queue", ctypes.c_uint32), ("streams", ctypes.c_uint32),
                 ("debug_stall", ctypes.c_uint32), ("debug_spin_limit", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 3)]
+                ("in_place", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 2)]
 
 
 class RequestStats(ctypes.Structure):
@@ -138,7 +139,7 @@ EXPORTED = ["ls_default_params", "ls_status_string", "ls_sort", "ls_sort_ex", "l
             "ls_radix_sort_u64", "ls_radix_sort_u64_noalloc", "ls_sample_sort_u64",
             "ls_kernel_launches",
             "ls_server_create", "ls_server_submit", "ls_server_submit_from", "ls_server_wait",
-            "ls_server_destroy"]
+            "ls_server_destroy", "ls_workspace_bytes"]
 
 _lib = None
 _lock = threading.Lock()
@@ -166,6 +167,8 @@ def load(path: str | None = None):
         lib.ls_status_string.restype = ctypes.c_char_p
         lib.ls_kernel_launches.argtypes = []
         lib.ls_kernel_launches.restype = u64
+        lib.ls_workspace_bytes.argtypes = [sz, i32, P(Params)]
+        lib.ls_workspace_bytes.restype = sz
         for f, a in {
             "ls_sort": [vp, sz, i32, vp],
             "ls_sort_ex": [vp, sz, i32, vp, P(Params), P(Stats)],
@@ -243,6 +246,12 @@ def sort_(t, params: Params | None = None, stats: bool = False, stream=None):
                            ctypes.byref(st) if st is not None else None)
     _check(rc, "ls_sort_ex")
     return st.as_dict() if st is not None else None
+
+
+def workspace_bytes(n: int, code: int, params: Params | None = None) -> int:
+    """Device workspace ls_sort_ex would allocate for n keys of dtype `code`."""
+    return int(load().ls_workspace_bytes(n, code,
+                                         ctypes.byref(params) if params is not None else None))
 
 
 def sort(t, params: Params | None = None, stream=None):
@@ -408,9 +417,9 @@ class Server:
 
     def __init__(self, hbm_budget_bytes: int = 120 << 30, max_inflight: int = 64,
                  max_queue: int = 4096, streams: int = 8, debug_stall: int = 0,
-                 debug_spin_limit: int = 0):
+                 debug_spin_limit: int = 0, in_place: bool = False):
         cfg = ServerConfig(hbm_budget_bytes, max_inflight, max_queue, streams, debug_stall,
-                           debug_spin_limit)
+                           debug_spin_limit, 1 if in_place else 0)
         self._h = ctypes.c_void_p()
         _check(load().ls_server_create(ctypes.byref(cfg), ctypes.byref(self._h)),
                "ls_server_create")

@@ -24,6 +24,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "ls_inplace.cuh"
 #include "ls_internal.cuh"
 #include "ls_partition.cuh"
 #include "ls_radix.cuh"
@@ -218,6 +219,8 @@ static cudaError_t configure(Device* d, int dt) {
   if (e) return e;
   e = buckets_configure(dt);
   if (e) return e;
+  e = ip_configure(dt, 227 * 1024);
+  if (e) return e;
   d->configured[dt] = true;
   return cudaSuccess;
 }
@@ -236,6 +239,10 @@ struct Plan {
   uint32_t kf;
   size_t smem_hist, smem_scatter;
   uint32_t l0_scan_tiles;
+  bool ip;                 // the in-place variant (LS_FLAG_IN_PLACE)
+  uint32_t ip_P;           // in place: level-0 pieces
+  uint64_t ip_PL;          // in place: keys per piece
+  size_t smem_ip0;
 };
 
 static const size_t SMEM_LIMIT = 227 * 1024;
@@ -251,6 +258,9 @@ static void plan_call(const ls_params* prm, int dt, uint64_t n, uintptr_t addr, 
   P->L = std::min<uint32_t>(MAX_LEAVES, std::max<uint32_t>(1, p.leaves ? p.leaves : d.leaves));
   // level 0: 256 buckets, so that a 4096-key tile writes runs of ~16 keys
   P->f0 = std::min<uint32_t>(MAX_FANOUT, std::max<uint32_t>(1, p.fanout ? p.fanout : 256));
+  // in place: one fragment block per bucket stays in shared memory
+  P->ip = (p.flags & LS_FLAG_IN_PLACE) != 0;
+  if (P->ip) P->f0 = std::min<uint32_t>(P->f0, IP_FANOUT_MAX);
   const uint32_t div = p.sample_div ? p.sample_div : d.sample_div;
   uint64_t s = (n + div - 1) / div;
   s = std::max<uint64_t>(s, std::min<uint64_t>(n, 2ull * P->L));
@@ -271,8 +281,9 @@ static void plan_call(const ls_params* prm, int dt, uint64_t n, uintptr_t addr, 
   hpb = std::min<uint32_t>(hpb, MAX_HPB);
   while (true) {
     const uint32_t next = P->f0 * (1 + 2 * hpb);
-    if (next < 65000 && level0_smem_scatter(dt, P->L, P->f0, next) <= SMEM_LIMIT &&
-        level0_smem_hist(dt, P->L, P->f0, next) <= SMEM_LIMIT)
+    if (next < 65000 && (P->ip ? ip_level0_smem(dt, P->L, P->f0, next) <= SMEM_LIMIT
+                               : (level0_smem_scatter(dt, P->L, P->f0, next) <= SMEM_LIMIT &&
+                                  level0_smem_hist(dt, P->L, P->f0, next) <= SMEM_LIMIT)))
       break;
     if (hpb == 0) break;
     --hpb;
@@ -302,12 +313,32 @@ static void plan_call(const ls_params* prm, int dt, uint64_t n, uintptr_t addr, 
   if (ch == 0) ch = V;
   P->c.ch = ch;
   P->c.G = (uint32_t)G;
+  if (P->ip) {
+    // level 0 in place: pieces of whole flush tiles, one CTA each, the level-0
+    // offsets kept once per slot (G = 1)
+    P->c.a0 = 0;
+    P->c.a1 = n;
+    P->c.ch = n;
+    P->c.G = 1;
+    G = 1;
+    const uint64_t tiles = std::max<uint64_t>(1, (n + IP0_TILE - 1) / IP0_TILE);
+    const uint64_t pieces = std::min<uint64_t>((uint64_t)num_sms, tiles);
+    P->ip_PL = (tiles + pieces - 1) / pieces * IP0_TILE;
+    P->ip_P = (uint32_t)((n + P->ip_PL - 1) / P->ip_PL);
+    P->smem_ip0 = ip_level0_smem(dt, P->L, P->f0, P->n_ext_max);
+  } else {
+    P->ip_P = 0;
+    P->ip_PL = 0;
+    P->smem_ip0 = 0;
+  }
   P->smem_hist = level0_smem_hist(dt, P->L, P->f0, P->n_ext_max);
   P->smem_scatter = level0_smem_scatter(dt, P->L, P->f0, P->n_ext_max);
   // level-1 sub-buckets per bucket: buckets of about l1_target keys each
   const uint64_t per = (uint64_t)P->f0 * P->lim.l1_target;
   // (ids sub + interval stay below MAX_F1 with up to MAX_HPB heavy values)
   P->kf = (uint32_t)std::min<uint64_t>(MAX_F1 - MAX_HPB, std::max<uint64_t>(1, (n + per - 1) / per));
+  // in place, a split keeps at most IP_CTA_FMAX sub-buckets (ids sub + interval)
+  if (P->ip) P->kf = std::min<uint32_t>(P->kf, IP_CTA_FMAX - MAX_HPB - 1);
   P->cap0 = P->n_ext_max + 16;
   P->cap_r = n / (P->lim.c_large + 1) + 16;     // jobs a refinement level can pass on
   P->capj = std::max(P->cap0, P->cap_r);        // jobs of one refinement level
@@ -338,6 +369,9 @@ struct Workspace {
       o_lbeg, o_lend, o_hist, o_offs, o_l0scan, o_jobs_fill, o_jobs_s, o_jobs_l, o_jobs_m, o_jobs_m0, o_jobs_fb2, o_jobs_t, o_jobs_r,
       o_jobs_fb, o_jobs_r2, o_jobs_r3, o_pk, o_sid, o_ccount, o_counts, o_aux, o_tot, o_l1cnt, o_l1off, o_l1cur, o_jmin, o_jmax, o_l1scan,
       o_ubase, o_units;
+  // in place
+  size_t o_ip_flags, o_ip_pslots, o_ip_lokeys, o_ip_locnt, o_ip_cntb, o_ip_nbk, o_ip_dsl, o_ip_dend,
+      o_ip_sst, o_ip_pair, o_ip_save, o_ip_ovf;
   size_t tscan_bytes, rs_status_bytes, l0scan_bytes, l1scan_bytes;
   uint64_t cand_cap;
 };
@@ -414,6 +448,22 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   const uint64_t l1tiles = std::max<uint64_t>(1, (P.cap_c + SC_TILE - 1) / SC_TILE);
   w->l1scan_bytes = l1tiles * 8 + 16;
   w->o_l1scan = c.take<uint8_t>(w->l1scan_bytes);
+  if (P.ip) {
+    const uint64_t B = IP_BLOCK_BYTES / P.W;
+    const uint64_t blocks = (uint64_t)P.ip_P * P.f0;
+    w->o_ip_flags = c.take<uint8_t>((P.n + B - 1) / B + 16);
+    w->o_ip_pslots = c.take<uint32_t>(P.ip_P);
+    w->o_ip_lokeys = c.take<uint8_t>(blocks * IP_BLOCK_BYTES);
+    w->o_ip_locnt = c.take<uint32_t>(blocks);
+    w->o_ip_cntb = c.take<unsigned long long>(P.f0);
+    w->o_ip_nbk = c.take<uint32_t>(P.f0);
+    w->o_ip_dsl = c.take<uint32_t>(P.f0);
+    w->o_ip_dend = c.take<uint32_t>(P.f0);
+    w->o_ip_sst = c.take<unsigned long long>(P.f0);
+    w->o_ip_pair = c.take<unsigned long long>(P.f0);
+    w->o_ip_save = c.take<uint8_t>((size_t)P.f0 * IP_BLOCK_BYTES);
+    w->o_ip_ovf = c.take<uint8_t>(IP_BLOCK_BYTES);
+  }
   w->bytes = c.off + 256;
 }
 
@@ -558,11 +608,72 @@ static Level0Args level0_args(const Plan& P, const Bound& b, const Workspace& w,
   a.ccount = at<uint64_t>(w, w.o_ccount);
   a.may_compact = 1;
   a.f0kf = (float)((double)P.f0 * P.kf);
+  a.in_place = P.ip ? 1u : 0u;
   return a;
+}
+
+static InPlace0 inplace0_of(const Plan& P, const Workspace& w) {
+  InPlace0 ip{};
+  ip.P = P.ip_P;
+  ip.PL = P.ip_PL;
+  ip.flags = at<uint8_t>(w, w.o_ip_flags);
+  ip.pslots = at<uint32_t>(w, w.o_ip_pslots);
+  ip.lo_keys = at<void>(w, w.o_ip_lokeys);
+  ip.lo_cnt = at<uint32_t>(w, w.o_ip_locnt);
+  ip.cntb = at<unsigned long long>(w, w.o_ip_cntb);
+  ip.nbk = at<uint32_t>(w, w.o_ip_nbk);
+  ip.dsl = at<uint32_t>(w, w.o_ip_dsl);
+  ip.dend = at<uint32_t>(w, w.o_ip_dend);
+  ip.sst = at<unsigned long long>(w, w.o_ip_sst);
+  ip.pair = at<unsigned long long>(w, w.o_ip_pair);
+  ip.save = at<void>(w, w.o_ip_save);
+  ip.ovf = at<void>(w, w.o_ip_ovf);
+  return ip;
+}
+
+// The in-place variant: level 0 and every refinement split inside the
+// caller's array (no n-key scratch), then the same fills and in-bucket sorts.
+static cudaError_t enqueue_sort_ip(const Plan& P, const Workspace& w, void* keys, Device* d,
+                                   cudaStream_t st, Events* ev, const CallOpts& o) {
+  const Bound b = bind(P, w);
+  Marks mk{ev && ev->on ? ev->ev : nullptr, NMARK};
+  uint32_t* err = (uint32_t*)(b.counts + N_COUNTS);
+  ZeroList z{};
+  z.p[0] = b.counts;
+  z.words[0] = N_COUNTS * 2;
+  z.p[1] = at<void>(w, w.o_l0scan);
+  z.words[1] = (uint32_t)(w.l0scan_bytes / 4);
+  z.p[2] = at<void>(w, w.o_hist);           // level-0 slot counts (accumulated)
+  z.words[2] = P.n_ext_max;
+  z.p[3] = at<void>(w, w.o_ip_cntb);
+  z.words[3] = 2 * P.f0;
+  z.p[4] = at<void>(w, w.o_ip_nbk);
+  z.words[4] = P.f0;
+  mark(&mk, 0, st);
+  LS_TRY(enqueue_train(P, b, keys, d, err, st, &z, (CallStatus*)err, &o));
+  mark(&mk, 1, st);
+  Level0Args a = level0_args(P, b, w, keys, err);
+  a.scratch = nullptr;
+  a.pk = nullptr;
+  a.sid = nullptr;
+  a.may_compact = 0;
+  const InPlace0 ip = inplace0_of(P, w);
+  LS_TRY(ip_level0_enqueue(P.dt, a, ip, b.lists, P.lim, st, d->num_sms, &mk, 2));
+  LS_TRY(ip_levels_enqueue(P.dt, keys, b.M, b.lists, P.lim, b.l1, P.kf, a.f0kf, a.offs, err, st,
+                           d->num_sms));
+  mark(&mk, 6, st);
+  LS_TRY(fill_enqueue(P.dt, keys, b.lists, nullptr, nullptr, st, d->num_sms));
+  mark(&mk, 7, st);
+  LS_TRY(buckets_enqueue(P.dt, keys, nullptr, P.n, b.M, b.lists, P.cap1, P.cap1, P.cap1,
+                         b.counts + 8, err, st, d->num_sms, &mk, 8));
+  LS_TRY(end_call(b.counts, N_COUNTS, o, st));
+  mark(&mk, 10, st);
+  return cudaSuccess;
 }
 
 static cudaError_t enqueue_sort(const Plan& P, const Workspace& w, void* keys, Device* d,
                                 cudaStream_t st, Events* ev, const CallOpts& o) {
+  if (P.ip) return enqueue_sort_ip(P, w, keys, d, st, ev, o);
   const Bound b = bind(P, w);
   Marks mk{ev && ev->on ? ev->ev : nullptr, NMARK};
   uint32_t* err = (uint32_t*)(b.counts + N_COUNTS);  // the call's own CallStatus
@@ -634,6 +745,7 @@ static void fill_stats(const Plan& P, const Workspace& w, Events* ev, ls_stats* 
     stats->ms_fallback = el(9, 10);
   }
   stats->n_launches = launches;
+  stats->workspace_bytes = w.bytes;
   DevModel hdr;
   cudaMemcpy(&hdr, at<void>(w, w.o_hdr), sizeof(hdr), cudaMemcpyDeviceToHost);
   unsigned long long counts[N_COUNTS];
@@ -733,9 +845,10 @@ ls_status ls::sort_call(void* keys, size_t n, ls_dtype dtype, CUstream_st* strea
   if (params) p = *params; else ls_default_params(&p);
   Plan P;
   plan_call(&p, dtype, n, (uintptr_t)keys, d->num_sms, &P);
-  if (P.smem_hist > SMEM_LIMIT || P.smem_scatter > SMEM_LIMIT) return LS_ERR_INVALID;
+  if (P.ip ? P.smem_ip0 > SMEM_LIMIT : (P.smem_hist > SMEM_LIMIT || P.smem_scatter > SMEM_LIMIT))
+    return LS_ERR_INVALID;
   Workspace w;
-  layout_ws(P, &w, true);
+  layout_ws(P, &w, !P.ip);
   if ((e = ws_alloc(d, &w, st))) return to_status(e);
   Events ev;
   if (stats) {
@@ -760,6 +873,19 @@ extern "C" {
 ls_status ls_sort_ex(void* keys, size_t n, ls_dtype dtype, void* stream, const ls_params* params,
                      ls_stats* stats) {
   return sort_call(keys, n, dtype, (cudaStream_t)stream, params, stats, nullptr);
+}
+
+size_t ls_workspace_bytes(size_t n, ls_dtype dtype, const ls_params* params) {
+  if (dtype < LS_F64 || dtype > LS_U32 || n < 2) return 0;
+  Device* d;
+  if (get_device(&d) != cudaSuccess) return 0;
+  ls_params p;
+  if (params) p = *params; else ls_default_params(&p);
+  Plan P;
+  plan_call(&p, dtype, n, 0, d->num_sms, &P);
+  Workspace w;
+  layout_ws(P, &w, !P.ip);
+  return w.bytes;
 }
 
 ls_status ls_sort(void* keys, size_t n, ls_dtype dtype, void* stream) {
@@ -1006,6 +1132,7 @@ ls_status ls_train(const void* keys, size_t n, ls_dtype dtype, void* stream,
   if ((e = configure(d, dtype))) return to_status(e);
   ls_params p;
   if (params) p = *params; else ls_default_params(&p);
+  p.flags &= ~LS_FLAG_IN_PLACE;  // the model alone: the regular plan
   Plan P;
   plan_call(&p, dtype, n, (uintptr_t)keys, d->num_sms, &P);
   if (out->leaves < P.L) return LS_ERR_INVALID;
@@ -1057,6 +1184,7 @@ ls_status ls_level0_histogram(const void* keys, size_t n, ls_dtype dtype, void* 
   if ((e = configure(d, dtype))) return to_status(e);
   ls_params p;
   if (params) p = *params; else ls_default_params(&p);
+  p.flags &= ~LS_FLAG_IN_PLACE;  // the out-of-place histogram pass
   Plan P;
   plan_call(&p, dtype, n, (uintptr_t)keys, d->num_sms, &P);
   Workspace w;

@@ -24,6 +24,7 @@
 // of at most CAP keys with the same counting sort.
 #include <cfloat>
 
+#include "ls_inplace.cuh"
 #include "ls_partition.cuh"
 #include "ls_radix.cuh"
 #include "ls_scan.cuh"
@@ -412,6 +413,109 @@ k_fallback(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, ModelPtrs M, J
   }
 }
 
+// Fallback of the in-place variant: the same MSD splits by the top differing
+// byte, each done inside the segment (fragment flush, defragment, cleanup:
+// ls_inplace.cuh) instead of into scratch.  The split's shared memory and the
+// counting sort's share one region; the work stack follows it.
+template <int DT>
+struct IpFbCfg {
+  typedef typename KT<DT>::U U;
+  typedef BucketCfg<DT, 512, 16> C;
+  static constexpr size_t AREA = C::SMEM > IpCta<U>::SMEM ? C::SMEM : IpCta<U>::SMEM;
+  static constexpr size_t OFF_STACK = (AREA + 15) / 16 * 16;
+  static constexpr size_t SMEM = OFF_STACK + 16 * STACK;
+};
+
+template <int DT>
+struct IpDigit {
+  int shift;
+  __device__ uint32_t operator()(typename KT<DT>::U u) const {
+    return (uint32_t)((KT<DT>::tk(u) >> shift) & 255u);
+  }
+};
+
+template <int DT>
+__global__ void __launch_bounds__(512, 1)
+k_ip_fallback(typename KT<DT>::U* keys, JobList list, unsigned long long* ctr, uint32_t* err) {
+  pdl_begin();
+  typedef typename KT<DT>::U U;
+  typedef IpFbCfg<DT> Q;
+  typedef BucketCfg<DT, 512, 16> C;
+  extern __shared__ __align__(16) unsigned char sm[];
+  StackEnt* stack = (StackEnt*)(sm + Q::OFF_STACK);
+  __shared__ SegShared ss;
+  __shared__ unsigned long long s_job, s_or, s_and;
+  __shared__ int s_top;
+  __shared__ StackEnt s_e;
+  const unsigned long long nj = min(*list.count, list.cap);
+  const int lane = threadIdx.x & 31;
+  const uint32_t* pcnt = (const uint32_t*)(sm + IpCta<U>::OFF_U32) + 4 * IpCta<U>::F;
+  const unsigned long long* pst = (const unsigned long long*)(sm + IpCta<U>::OFF_ST);
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_job = call_failed(err) ? ~0ull : atomicAdd(ctr, 1ull);
+    __syncthreads();
+    const unsigned long long jid = s_job;
+    if (jid >= nj) break;
+    const Job fjob = list.jobs[jid];
+    U* const K = job_keys(fjob, keys);
+    if (threadIdx.x == 0) {
+      stack[0].start = fjob.start;
+      stack[0].m = (uint32_t)fjob.m;
+      stack[0].buf = 0;
+      s_top = 1;
+    }
+    __syncthreads();
+    while (true) {
+      if (threadIdx.x == 0) {
+        if (s_top > 0) { s_e = stack[s_top - 1]; --s_top; }
+        else s_e.m = 0xFFFFFFFFu;
+        s_or = 0;
+        s_and = ~0ull;
+      }
+      __syncthreads();
+      const StackEnt e = s_e;
+      if (e.m == 0xFFFFFFFFu) break;
+      U* D = K + e.start;
+      if (e.m <= (uint32_t)C::CAP) {
+        segment_sort<DT, 512, 16>(D, D, e.m, sm, ss, err);
+        continue;
+      }
+      unsigned long long o = 0, a = ~0ull;
+      for (uint32_t i = threadIdx.x; i < e.m; i += 512) {
+        const uint64_t t = KT<DT>::tk(D[i]);
+        o |= t;
+        a &= t;
+      }
+      for (int s = 16; s > 0; s >>= 1) {
+        o |= __shfl_xor_sync(0xffffffffu, o, s);
+        a &= __shfl_xor_sync(0xffffffffu, a, s);
+      }
+      if (lane == 0) { atomicOr(&s_or, o); atomicAnd(&s_and, a); }
+      __syncthreads();
+      const uint64_t diff = s_or ^ s_and;
+      if (diff == 0) continue;  // one value: already in order
+      const int shift = ((63 - __clzll((long long)diff)) >> 3) << 3;  // top differing byte
+      ip_cta_partition<U, 512, 8>(D, e.m, e.m, 256u, IpDigit<DT>{shift}, IpPrefixStarts{}, sm, err);
+      if (threadIdx.x < 256 && pcnt[threadIdx.x] > 1u) {
+        const int slot = atomicAdd(&s_top, 1);
+        if (slot < STACK) {
+          StackEnt ne;
+          ne.start = e.start + pst[threadIdx.x];
+          ne.m = pcnt[threadIdx.x];
+          ne.buf = 0;
+          stack[slot] = ne;
+        } else {
+          set_error(err, ERR_BOUNDS);
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0 && s_top > STACK) s_top = STACK;
+      __syncthreads();
+    }
+  }
+}
+
 // ---------------------------------------------------------------- host enqueue
 constexpr int BS_TINY_T = 128, BS_TINY_K = 4;      // CAP 512
 constexpr int BS_SMALL_T = 256, BS_SMALL_K = 8;    // CAP 2048
@@ -441,8 +545,12 @@ static cudaError_t buckets_cfg_dt() {
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)BucketCfg<DT, BS_LARGE_T, BS_LARGE_K>::SMEM);
   if (e) return e;
-  return cudaFuncSetAttribute(k_fallback<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)BucketCfg<DT, 512, 16>::SMEM_FB);
+  e = cudaFuncSetAttribute(k_fallback<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)BucketCfg<DT, 512, 16>::SMEM_FB);
+  if (e) return e;
+  static_assert(IpFbCfg<DT>::SMEM <= 227 * 1024, "in-place fallback shared memory");
+  return cudaFuncSetAttribute(k_ip_fallback<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)IpFbCfg<DT>::SMEM);
 }
 
 cudaError_t buckets_configure(int dt) {
@@ -482,8 +590,11 @@ static cudaError_t buckets_dt(void* keys, void* scratch, const ModelPtrs& M, con
   }
   launch_k(k_bucket_sort<DT, BS_LARGE_T, BS_LARGE_K>, gl, BS_LARGE_T, BucketCfg<DT, BS_LARGE_T, BS_LARGE_K>::SMEM, st, (U*)keys, (const U*)scratch, M, lists.sort_l, ctrs + 1, err);
   mark(mk, mb + 1, st);
-  launch_k(k_fallback<DT>, gf, 512, BucketCfg<DT, 512, 16>::SMEM_FB, st, (U*)keys, (U*)scratch, M,
-                                                                  lists.fallback, ctrs + 2, err);
+  if (scratch)
+    launch_k(k_fallback<DT>, gf, 512, BucketCfg<DT, 512, 16>::SMEM_FB, st, (U*)keys, (U*)scratch, M,
+             lists.fallback, ctrs + 2, err);
+  else  // the in-place variant: no scratch
+    launch_k(k_ip_fallback<DT>, gf, 512, IpFbCfg<DT>::SMEM, st, (U*)keys, lists.fallback, ctrs + 2, err);
   add_launches(6);
   return cudaGetLastError();
 }

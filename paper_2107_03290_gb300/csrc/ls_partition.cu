@@ -26,73 +26,11 @@
 #include <cfloat>
 
 #include "ls_partition.cuh"
+#include "ls_partition_dev.cuh"
 #include "ls_scan.cuh"
 #include "ls_tma.cuh"
 
 namespace ls {
-
-struct L0Layout {
-  uint32_t bar, buf, pbuf, thr, cell, cleaf, heads, htk, cnt, ecnt, soff, cursor, gbase, sinfo, sid,
-      ws, hkey, hval, queue, tiles, total;
-  uint32_t hs;           // K2: heavy values per bucket row (power of two > per-bucket maximum)
-};
-
-// Row width of the padded per-bucket heavy table of K2.
-static uint32_t heavy_stride(uint32_t f0, uint32_t next) {
-  const uint32_t hpb = f0 ? (next - f0) / (2 * f0) : 0;
-  if (!hpb) return 0;
-  uint32_t hs = 1;
-  while (hs <= hpb) hs <<= 1;
-  return hs;
-}
-
-// The cell-index leaves stay in global memory (read through L1) when the
-// shared copy would not fit.
-constexpr size_t L0_SMEM_LIMIT = 227 * 1024;
-constexpr uint32_t NOT_SHARED = 0xFFFFFFFFu;
-constexpr int H_KPT = 6;             // keys per thread and step of K2
-
-// K2: the lookup tables and the extended-slot counters.
-static int key_width(int dt) { return (dt == LS_F64 || dt == LS_U64) ? 8 : 4; }
-
-constexpr int QCAP = 64;              // K2 per-warp queue of keys missing the heavy table
-constexpr int H_TILE = H_THREADS * H_KPT;  // K2 keys per TMA tile (calls without heavy values)
-
-static L0Layout l0_layout_hist(int W, uint32_t L, uint32_t f0, uint32_t next, uint32_t hmax,
-                               bool cleaf_shared = true, bool hashed = true) {
-  L0Layout y{};
-  (void)hmax;
-  y.hs = heavy_stride(f0, next);
-  size_t o = 0;
-  auto al = [&](size_t a) { o = (o + a - 1) / a * a; };
-  al(16); y.thr = (uint32_t)o; o += (size_t)f0 * 8;
-  y.cell = (uint32_t)o; o += (size_t)L0_CELLS * 4;
-  y.cleaf = NOT_SHARED;
-  if (cleaf_shared) { al(16); y.cleaf = (uint32_t)o; o += (size_t)L * sizeof(CellLeaf); }
-  al(16); y.heads = (uint32_t)o; o += (size_t)(f0 + 1) * sizeof(BucketHead);
-  y.htk = (uint32_t)o; o += (size_t)f0 * y.hs * 8;
-  y.cnt = (uint32_t)o; o += (size_t)(next + 1) * 4;
-  al(8); y.ws = (uint32_t)o; o += 33 * 8;
-  y.bar = (uint32_t)o; o += 16;  // two mbarriers of the TMA tiles
-  // The rest holds either the heavy table with the miss queues (the HASHED
-  // instantiation) or the double-buffered TMA key tiles (the other one, in
-  // calls without heavy values): the two kernels never use both.
-  al(128);
-  const size_t rest = o;
-  y.hkey = y.hval = y.queue = NOT_SHARED;
-  if (hashed && y.hs) {  // heavy table and per-warp miss queues
-    al(16); y.hkey = (uint32_t)o; o += (size_t)HASH_SIZE * 8;
-    y.hval = (uint32_t)o; o += (size_t)HASH_SIZE * 2;
-    al(16); y.queue = (uint32_t)o; o += (size_t)(H_THREADS / 32) * QCAP * (W + 4);
-  }
-  const size_t tiles_end = rest + 2ull * H_TILE * W;
-  y.tiles = tiles_end <= L0_SMEM_LIMIT ? (uint32_t)rest : NOT_SHARED;
-  if (y.tiles != NOT_SHARED && tiles_end > o) o = tiles_end;
-  y.total = (uint32_t)o;
-  if (hashed && y.hs && o > L0_SMEM_LIMIT) return l0_layout_hist(W, L, f0, next, hmax, cleaf_shared, false);
-  if (cleaf_shared && o > L0_SMEM_LIMIT) return l0_layout_hist(W, L, f0, next, hmax, false, false);
-  return y;
-}
 
 // K4: double-buffered key and id tiles, per-bucket counters, offsets and
 // cursors, staging records.
@@ -140,35 +78,6 @@ __device__ __forceinline__ void chunk_of(const Chunking& c, uint32_t g, uint64_t
   *e = ce;
 }
 
-// Shared-memory copies of the level-0 tables; returns the lookup over them.
-__device__ __forceinline__ L0Map load_tables(const Level0Args& a, unsigned char* sm,
-                                             const L0Layout& lay, uint32_t H) {
-  uint64_t* thr = (uint64_t*)(sm + lay.thr);
-  uint32_t* cell = (uint32_t*)(sm + lay.cell);
-  CellLeaf* cleaf = lay.cleaf == NOT_SHARED ? a.M.cleaf : (CellLeaf*)(sm + lay.cleaf);
-  BucketHead* heads = (BucketHead*)(sm + lay.heads);
-  uint64_t* htk = (uint64_t*)(sm + lay.htk);
-  for (uint32_t i = threadIdx.x; i < a.f0; i += blockDim.x) thr[i] = a.M.thr[i];
-  for (uint32_t i = threadIdx.x; i < L0_CELLS; i += blockDim.x) cell[i] = a.M.cell[i];
-  if (lay.cleaf != NOT_SHARED)
-    for (uint32_t i = threadIdx.x; i < a.L; i += blockDim.x) cleaf[i] = a.M.cleaf[i];
-  for (uint32_t i = threadIdx.x; i <= a.f0; i += blockDim.x) heads[i] = a.M.heads[i];
-  // bucket b's heavy values at htk[j * f0 + b] (column-major, so lanes probing
-  // different buckets hit different banks), padded with the largest key
-  for (uint32_t i = threadIdx.x; i < a.f0 * lay.hs; i += blockDim.x) {
-    const uint32_t j = i / a.f0, b = i % a.f0;
-    const uint32_t hn = a.M.heads[b].hoff_nh;
-    const uint32_t nh = hn & 15u, ho = hn >> 4;
-    htk[i] = (j < nh && ho + j < H) ? a.M.heavy[ho + j].tk : ~0ull;
-  }
-  if (lay.hkey != NOT_SHARED) {
-    uint64_t* hk = (uint64_t*)(sm + lay.hkey);
-    uint16_t* hv = (uint16_t*)(sm + lay.hval);
-    for (uint32_t i = threadIdx.x; i < HASH_SIZE; i += blockDim.x) { hk[i] = a.M.hkey[i]; hv[i] = a.M.hval[i]; }
-  }
-  const DevModel* h = a.M.hdr;
-  return L0Map{thr, cell, cleaf, h->croot, h->pos_max, a.f0};
-}
 
 // ---------------------------------------------------------------- K2
 // One model evaluation per key: extended slot e (counted), and the packed id
@@ -177,59 +86,6 @@ __device__ __forceinline__ L0Map load_tables(const Level0Args& a, unsigned char*
 // interval between the bucket's heavy values: sub is non-decreasing in the key
 // and the heavy values split the key order, so sid is an order-preserving id
 // of the pair (j, sub) in [0, kf + nh).
-// 2 * #{heavy < t} + [t is heavy] over bucket b's padded row (hs entries at
-// stride f0, ascending, padded with the largest key): fixed bisection steps,
-// no divergence.
-__device__ __forceinline__ uint32_t heavy_offset_row(const uint64_t* h, uint32_t f0, uint32_t hs,
-                                                     uint32_t nh, uint64_t t) {
-  uint32_t lo = 0;
-  for (uint32_t s = hs >> 1; s; s >>= 1)
-    if (h[(size_t)(lo + s - 1) * f0] < t) lo += s;
-  if (h[(size_t)lo * f0] < t) lo += 1;  // lo: #{h < t} over the row
-  lo = min(lo, nh);
-  return 2 * lo + ((lo < nh && h[(size_t)lo * f0] == t) ? 1u : 0u);
-}
-
-template <int DT>
-__device__ __forceinline__ uint32_t classify_key(typename KT<DT>::U u, const L0Map& q,
-                                                 const BucketHead* heads, const uint64_t* htk,
-                                                 uint32_t hs, float f0kf, uint32_t kf,
-                                                 uint32_t* packed) {
-  const float F = cell_F<DT>(u, q.croot, q.cleaf);
-  const float v = F * (float)L0_CELLS;
-  const uint32_t cl = v >= 0.0f ? (v < (float)L0_CELLS ? (uint32_t)v : L0_CELLS - 1) : 0u;
-  const uint32_t r = q.cell[cl];
-  const uint64_t t = KT<DT>::tk(u);
-  const uint32_t b = min(thr_search(q.thr, r & 0xFFFFu, r >> 16, t), q.pos_max);
-  const BucketHead h = heads[b];
-  uint32_t e = h.ext_base;
-  const uint32_t nh = h.hoff_nh & 15u;
-  if (nh) e += heavy_offset_row(htk + b, q.f0, hs, nh, t);
-  const float w = F * f0kf;
-  int sub = (w >= 0.0f ? (int)w : 0) - (int)(b * kf);
-  sub = sub < 0 ? 0 : (sub >= (int)kf ? (int)kf - 1 : sub);
-  const uint32_t o = e - h.ext_base;
-  *packed = (o & 1u) ? PK_EQ : (b | ((uint32_t)sub + (o >> 1)) << PK_B_BITS);
-  return e;
-}
-
-// Bucket and packed id of a key in a call without heavy values (every bucket
-// is one slot: e = b).
-template <int DT>
-__device__ __forceinline__ uint32_t classify_plain(typename KT<DT>::U u, const L0Map& q,
-                                                   float f0kf, uint32_t kf, uint32_t* packed) {
-  const float F = cell_F<DT>(u, q.croot, q.cleaf);
-  const float v = F * (float)L0_CELLS;
-  const uint32_t cl = v >= 0.0f ? (v < (float)L0_CELLS ? (uint32_t)v : L0_CELLS - 1) : 0u;
-  const uint32_t r = q.cell[cl];
-  const uint32_t b = min(thr_search(q.thr, r & 0xFFFFu, r >> 16, KT<DT>::tk(u)), q.pos_max);
-  const float w = F * f0kf;
-  int sub = (w >= 0.0f ? (int)w : 0) - (int)(b * kf);
-  sub = sub < 0 ? 0 : (sub >= (int)kf ? (int)kf - 1 : sub);
-  *packed = b | (uint32_t)sub << PK_B_BITS;
-  return b;
-}
-
 // Two instantiations, launched back to back: HASHED handles calls whose
 // heavy table is present (decided on the device by training), the other the
 // rest; each returns at once when the call is not its kind.  In a call
@@ -630,7 +486,7 @@ __global__ void k_classify0(Level0Args a, Lists lists, SortLimits lim) {
     const uint32_t o = e - h.ext_base, nh = h.hoff_nh & 15u, hoff = h.hoff_nh >> 4;
     Job job;
     job.value = 0;
-    job.src = (a.may_compact && a.M.hdr->compact) ? 0u : 1u;  // where K4 put the keys
+    job.src = (a.in_place || (a.may_compact && a.M.hdr->compact)) ? 0u : 1u;  // where level 0 put the keys
     job.pad = 0;
     job.kb = job.sb = 0;
     job.la = b;
@@ -759,64 +615,6 @@ __global__ void __launch_bounds__(256) k_fill(U* __restrict__ keys, JobList smal
 }
 
 // ---------------------------------------------------------------- level 1
-struct L1Aux {
-  uint64_t tile_base;
-  uint64_t cbase;
-  uint64_t pad0;
-  uint32_t f1;
-  uint32_t pad;
-};
-
-// Split of one refine job: by the model's F (the level-1 Partition of Alg. 2)
-// or, for segments the model could not split, linearly over the segment's key
-// range: on the FP32 image of the key for floating-point keys (value space,
-// where a float range is close to linear in density), else, or when the image
-// cannot resolve the range, on the total-order key (an integer map, exact at
-// any width).  Both maps are non-decreasing in the key.
-struct RangeSplit {
-  unsigned long long tmin;
-  unsigned long long mul;
-  uint32_t sh;
-  uint32_t fe;
-  float xmin, xscale;    // value-space map when xscale > 0
-};
-
-template <int DT>
-__device__ __forceinline__ RangeSplit range_split(unsigned long long tmin, unsigned long long tmax,
-                                                  uint32_t f1, bool value_space) {
-  RangeSplit s;
-  const unsigned long long R = tmax - tmin;
-  const int bl = R ? 64 - __clzll((long long)R) : 0;
-  s.sh = bl > 32 ? (uint32_t)(bl - 32) : 0u;
-  const unsigned long long Q = R >> s.sh;                      // < 2^32
-  const unsigned long long fe = min((unsigned long long)f1, Q + 1);
-  s.mul = (fe << 32) / (Q + 1);                                // <= 2^32
-  s.tmin = tmin;
-  s.fe = (uint32_t)fe;
-  s.xmin = 0.0f;
-  s.xscale = 0.0f;
-  if (value_space && (DT == LS_F64 || DT == LS_F32)) {
-    const float x0 = key_f32<DT>(KT<DT>::from_tk(tmin));
-    const float x1 = key_f32<DT>(KT<DT>::from_tk(tmax));
-    const float sc = (float)f1 / (x1 - x0);
-    if (x1 > x0 && isfinite(x0) && isfinite(x1) && isfinite(sc) && sc > 0.0f) {
-      s.xmin = x0;
-      s.xscale = sc;
-      s.fe = f1;
-    }
-  }
-  return s;
-}
-template <int DT>
-__device__ __forceinline__ uint32_t range_sub(typename KT<DT>::U u, const RangeSplit& s) {
-  if (s.xscale > 0.0f) {
-    const float v = (key_f32<DT>(u) - s.xmin) * s.xscale;
-    return v > 0.0f ? min((uint32_t)v, s.fe - 1) : 0u;         // NaN keys cannot occur here
-  }
-  const unsigned long long d = (KT<DT>::tk(u) - s.tmin) >> s.sh;
-  return (uint32_t)((d * s.mul) >> 32);                        // < min(f1, Q + 1)
-}
-
 __global__ void __launch_bounds__(1024)
 k_l1_plan(LevelArgs la, SortLimits lim, Level1Ws w, uint32_t* err) {
   pdl_begin();
@@ -873,27 +671,11 @@ k_l1_plan(LevelArgs la, SortLimits lim, Level1Ws w, uint32_t* err) {
     w.totals[0] = s_rt;
     w.totals[1] = s_rc > w.cap_c ? w.cap_c : s_rc;
     w.totals[2] = nj;
+    w.totals[3] = 0;  // job counter of the in-place split
   }
   // the level's sub-bucket counters (only the ones its jobs use) start at zero
   const uint64_t C = min((uint64_t)s_rc, w.cap_c);
   for (uint64_t i = threadIdx.x; i < C; i += blockDim.x) w.cnt[i] = 0;
-}
-
-__device__ __forceinline__ uint64_t aux_find_tile(const L1Aux* aux, uint64_t nj, uint64_t t) {
-  uint64_t lo = 0, hi = nj;  // first index with tile_base > t, minus one
-  while (lo < hi) {
-    const uint64_t mid = (lo + hi) >> 1;
-    if (aux[mid].tile_base <= t) lo = mid + 1; else hi = mid;
-  }
-  return lo - 1;
-}
-__device__ __forceinline__ uint64_t aux_find_c(const L1Aux* aux, uint64_t nj, uint64_t c) {
-  uint64_t lo = 0, hi = nj;
-  while (lo < hi) {
-    const uint64_t mid = (lo + hi) >> 1;
-    if (aux[mid].cbase <= c) lo = mid + 1; else hi = mid;
-  }
-  return lo - 1;
 }
 
 // The tiles of a level are dealt to the CTAs in contiguous ranges: a CTA finds
@@ -1128,11 +910,12 @@ template <int DT>
 __global__ void k_l1_classify(Lists lists, LevelArgs la, SortLimits lim, Level1Ws w, ModelPtrs M,
                               int L, uint32_t* err) {
   pdl_begin();
+  if (call_failed(err)) return;  // after a failed split no job is made
   const L1Aux* aux = (const L1Aux*)w.aux;
   const uint64_t C = w.totals[1], nj = w.totals[2];
   for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < C;
        c += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t cntc = w.off[c + 1] - w.off[c];
+    const uint64_t cntc = la.in_place ? (uint64_t)w.cnt[c] : w.off[c + 1] - w.off[c];
     if (cntc == 0) continue;
     const uint64_t j = aux_find_c(aux, nj, c);
     const Job pj = la.in.jobs[j];
@@ -1148,7 +931,7 @@ __global__ void k_l1_classify(Lists lists, LevelArgs la, SortLimits lim, Level1W
     job.start = w.cur[c] - cntc;  // the cursor ends past the sub-bucket's keys
     job.m = job.span = cntc;
     job.pad = 0;
-    job.src = pj.src ^ 1u;
+    job.src = la.in_place ? pj.src : pj.src ^ 1u;  // split in place, or into the other buffer
     job.la = job.lb = 0;
     job.kb = pj.kb;
     job.sb = pj.sb;
@@ -1283,6 +1066,56 @@ cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const 
     lvs[lv].f0kf = f0kf;
   }
   return levels_enqueue(dt, keys, scratch, n, M, lists, lim, w, lvs, 3, err, st, num_sms);
+}
+
+cudaError_t launch_classify0(int dt, const Level0Args& a, const Lists& lists, const SortLimits& lim,
+                             cudaStream_t st) {
+  const unsigned g = (a.n_ext_max + 255) / 256;
+  switch (dt) {
+    case LS_F64: launch_k(k_classify0<LS_F64>, g, 256, 0, st, a, lists, lim); break;
+    case LS_U64: launch_k(k_classify0<LS_U64>, g, 256, 0, st, a, lists, lim); break;
+    case LS_F32: launch_k(k_classify0<LS_F32>, g, 256, 0, st, a, lists, lim); break;
+    case LS_U32: launch_k(k_classify0<LS_U32>, g, 256, 0, st, a, lists, lim); break;
+    default: return cudaErrorInvalidValue;
+  }
+  add_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_l1_plan(const LevelArgs& la, const SortLimits& lim, const Level1Ws& w,
+                           uint32_t* err, cudaStream_t st) {
+  launch_k(k_l1_plan, 1, 1024, 0, st, la, lim, w, err);
+  add_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_l1_minmax(int dt, const void* keys, const LevelArgs& la, const Level1Ws& w,
+                             cudaStream_t st, int num_sms) {
+  const int grid = 4 * num_sms;
+  switch (dt) {
+    case LS_F64: launch_k(k_l1_minmax<LS_F64>, grid, L1_THREADS, 0, st, (const uint64_t*)keys, (const uint64_t*)nullptr, la, w); break;
+    case LS_U64: launch_k(k_l1_minmax<LS_U64>, grid, L1_THREADS, 0, st, (const uint64_t*)keys, (const uint64_t*)nullptr, la, w); break;
+    case LS_F32: launch_k(k_l1_minmax<LS_F32>, grid, L1_THREADS, 0, st, (const uint32_t*)keys, (const uint32_t*)nullptr, la, w); break;
+    case LS_U32: launch_k(k_l1_minmax<LS_U32>, grid, L1_THREADS, 0, st, (const uint32_t*)keys, (const uint32_t*)nullptr, la, w); break;
+    default: return cudaErrorInvalidValue;
+  }
+  add_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_l1_classify(int dt, const Lists& lists, const LevelArgs& la,
+                               const SortLimits& lim, const Level1Ws& w, const ModelPtrs& M,
+                               uint32_t* err, cudaStream_t st, int num_sms) {
+  const int grid = 4 * num_sms;
+  switch (dt) {
+    case LS_F64: launch_k(k_l1_classify<LS_F64>, grid, 256, 0, st, lists, la, lim, w, M, M.L, err); break;
+    case LS_U64: launch_k(k_l1_classify<LS_U64>, grid, 256, 0, st, lists, la, lim, w, M, M.L, err); break;
+    case LS_F32: launch_k(k_l1_classify<LS_F32>, grid, 256, 0, st, lists, la, lim, w, M, M.L, err); break;
+    case LS_U32: launch_k(k_l1_classify<LS_U32>, grid, 256, 0, st, lists, la, lim, w, M, M.L, err); break;
+    default: return cudaErrorInvalidValue;
+  }
+  add_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t fill_enqueue(int dt, void* keys, const Lists& lists, const unsigned long long* from,

@@ -39,6 +39,7 @@ struct Level0Args {
   float f0kf;            // f0 * kf
   uint64_t* ccount;      // per CTA: packed non-equality keys (compaction mode)
   uint32_t may_compact;  // 0: leave `keys` untouched (read-only callers)
+  uint32_t in_place;     // 1: the in-place variant (buckets in `keys`, offsets with G = 1)
 };
 
 // The call's device counters (unsigned long long each): list counts and the
@@ -74,6 +75,7 @@ struct LevelArgs {
   const uint64_t* l0offs;
   uint32_t l0G;
   float f0kf;
+  uint32_t in_place;     // 1: jobs split in place (counts in cnt, jobs stay in their buffer)
 };
 
 struct SortLimits {
@@ -100,6 +102,51 @@ struct Level1Ws {
   uint64_t cap_jobs;
   uint64_t cap_tiles;
 };
+
+// In-place variant (ls_inplace.cu): level 0 splits the caller's array in place
+// (fragment flush over read positions, device defragment, cleanup); the
+// refinement levels and the radix fallback split each segment in place inside
+// one CTA.  Per-bucket arrays have f0 entries, per-piece ones P.
+struct InPlace0 {
+  uint32_t P;                  // pieces (one CTA each in the flush pass)
+  uint64_t PL;                 // keys per piece (a multiple of the flush tile)
+  uint8_t* flags;              // per block slot: set once a reader has taken its block
+  uint32_t* pslots;            // per piece: blocks flushed at its front
+  void* lo_keys;               // per piece and bucket: leftover keys (one block each)
+  uint32_t* lo_cnt;            // per piece and bucket: leftover count
+  unsigned long long* cntb;    // per bucket: non-equality keys
+  uint32_t* nbk;               // per bucket: full blocks
+  uint32_t* dsl;               // per bucket: first slot of its range
+  uint32_t* dend;              // per bucket: end of its slot range
+  unsigned long long* sst;     // per bucket: first position
+  unsigned long long* pair;    // per bucket: write pointer << 32 | (read pointer + 1)
+  void* save;                  // per bucket: one block (the overhang into its head)
+  void* ovf;                   // one block: the partial last slot of the array
+};
+constexpr int IP0_THREADS = 1024;
+constexpr int IP0_KPT = 8;
+constexpr uint32_t IP0_TILE = IP0_THREADS * IP0_KPT;
+constexpr uint32_t IP_FANOUT_MAX = 512;   // level-0 buckets of the in-place variant
+size_t ip_level0_smem(int dt, uint32_t L, uint32_t f0, uint32_t n_ext_max);
+size_t ip_cta_smem(int dt);
+cudaError_t ip_configure(int dt, size_t smem0);
+cudaError_t ip_level0_enqueue(int dt, const Level0Args& a, const InPlace0& ip, const Lists& lists,
+                              const SortLimits& lim, cudaStream_t st, int num_sms,
+                              const Marks* mk = nullptr, int mbase = 0);
+cudaError_t ip_levels_enqueue(int dt, void* keys, const ModelPtrs& M, const Lists& lists,
+                              const SortLimits& lim, const Level1Ws& w, uint32_t kf, float f0kf,
+                              const uint64_t* l0offs, uint32_t* err, cudaStream_t st, int num_sms);
+
+// Single launches of the level kernels (each counts itself in add_launches).
+cudaError_t launch_classify0(int dt, const Level0Args& a, const Lists& lists, const SortLimits& lim,
+                             cudaStream_t st);
+cudaError_t launch_l1_plan(const LevelArgs& la, const SortLimits& lim, const Level1Ws& w,
+                           uint32_t* err, cudaStream_t st);
+cudaError_t launch_l1_minmax(int dt, const void* keys, const LevelArgs& la, const Level1Ws& w,
+                             cudaStream_t st, int num_sms);
+cudaError_t launch_l1_classify(int dt, const Lists& lists, const LevelArgs& la,
+                               const SortLimits& lim, const Level1Ws& w, const ModelPtrs& M,
+                               uint32_t* err, cudaStream_t st, int num_sms);
 
 size_t level0_smem_hist(int dt, uint32_t L, uint32_t f0, uint32_t n_ext_max);
 size_t level0_smem_scatter(int dt, uint32_t L, uint32_t f0, uint32_t n_ext_max);

@@ -69,8 +69,14 @@ struct ls_server {
   std::thread th;
 };
 
-static uint64_t request_bytes(size_t n, ls_dtype dt) {
+static uint64_t request_bytes(size_t n, ls_dtype dt, bool in_place) {
   const uint64_t w = (dt == LS_F64 || dt == LS_U64) ? 8 : 4;
+  if (in_place && n > SERVER_BATCH_MAX) {  // keys + the in-place workspace
+    ls_params p;
+    ls_default_params(&p);
+    p.flags |= LS_FLAG_IN_PLACE;
+    return n * w + ls_workspace_bytes(n, dt, &p);
+  }
   return 2 * n * w + (64ull << 20);  // keys + scratch + model/job space
 }
 
@@ -166,7 +172,10 @@ static void dispatcher(ls_server* s) {
         cudaStream_t st = s->streams[si];
         prologue(r, st, si);
         const ls::CallOpts o = opts(r->slot, st);
-        const ls_status rc = ls::sort_call(r->keys, r->n, r->dt, st, nullptr, nullptr, &o);
+        ls_params prm;
+        ls_default_params(&prm);
+        if (s->cfg.in_place) prm.flags |= LS_FLAG_IN_PLACE;
+        const ls_status rc = ls::sort_call(r->keys, r->n, r->dt, st, &prm, nullptr, &o);
         cudaMemcpyAsync(&s->hstat[r->slot], &s->dstat[r->slot].word, sizeof(uint32_t),
                         cudaMemcpyDeviceToHost, st);
         cudaEventRecord(r->ev_end, st);
@@ -231,7 +240,7 @@ ls_status ls_server_submit(ls_server* s, void* keys, size_t n, ls_dtype dtype, u
 ls_status ls_server_submit_from(ls_server* s, const void* src, void* keys, size_t n,
                                 ls_dtype dtype, uint64_t* ticket) {
   if (!s || !ticket || dtype < LS_F64 || dtype > LS_U32 || (n > 0 && !keys)) return LS_ERR_INVALID;
-  const uint64_t bytes = request_bytes(n, dtype);
+  const uint64_t bytes = request_bytes(n, dtype, s && s->cfg.in_place != 0);
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stop) return LS_ERR_CANCELLED;
   if (bytes > s->cfg.hbm_budget_bytes || s->queue.size() >= s->cfg.max_queue) return LS_ERR_BUSY;
