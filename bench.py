@@ -441,6 +441,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=2_000_000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=4096, help="arrays of the batched line (0: skip)")
+    ap.add_argument("--inplace-steps", type=int, default=10,
+                    help="timed sorts of the workload with LS_FLAG_IN_PLACE (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="seconds per arrival rate of the serving line (0: skip)")
     ap.add_argument("--suite", default="",
@@ -578,6 +580,44 @@ def main():
         cpu = {"value": smp / tc, "unit": "keys/s", "cores": 1, "kind": "oracle",
                "sample": f"first {smp} keys of the workload, one oracle LearnedSort 2.0 call"}
 
+    # the in-place variant on the same workload: its own timed sorts (CUDA
+    # events around each call), its exactness, and the workspace it allocates
+    inplace = None
+    if args.inplace_steps > 0 and rank == 0:
+        pip = ls.default_params(fanout=fanout, leaves=args.leaves, flags=ls.FLAG_IN_PLACE)
+        code = {"f64": 0, "u64": 1, "f32": 2, "u32": 3}[dt]
+        for _ in range(2):
+            work.copy_(pristine)
+            ls.sort_(work, pip)
+        torch.cuda.synchronize()
+        ip_ok = bool(np.array_equal(total_order_keys(work.cpu().numpy()),
+                                    np.sort(total_order_keys(keys))))
+        ip_ms = []
+        for _ in range(args.inplace_steps):
+            work.copy_(pristine)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ls.sort_(work, pip)
+            e1.record(stream)
+            e1.synchronize()
+            ip_ms.append(e0.elapsed_time(e1))
+        work.copy_(pristine)
+        ip_st = ls.sort_(work, pip, stats=True)
+        torch.cuda.synchronize()
+        ipm = float(np.mean(ip_ms))
+        inplace = {"ms_per_sort": ipm, "keys_per_s": n / (ipm / 1e3), "steps": args.inplace_steps,
+                   "exact": ip_ok,
+                   "workspace_bytes": ls.workspace_bytes(n, code, pip),
+                   "workspace_bytes_regular": ls.workspace_bytes(n, code, prm),
+                   "phase_ms": {k: ip_st[k] for k in ("ms_train", "ms_hist", "ms_scan", "ms_scatter",
+                                                      "ms_classify", "ms_level1", "ms_fill",
+                                                      "ms_sort_small", "ms_sort_large",
+                                                      "ms_fallback")},
+                   "note": ("LS_FLAG_IN_PLACE: level 0 by fragment flush over read positions, "
+                            "device defragment and cleanup; refinement levels and fallback "
+                            "split in place per CTA; no n-key scratch")}
+
     batched = None
     if args.batch > 0 and rank == 0:
         batched = run_batched(ls, torch, args.batch, steps=5, warmup=2)
@@ -605,7 +645,7 @@ def main():
                "ms_p50": float(np.median(step_ms)),
                "ms_min": float(np.min(step_ms)),
                "ms_with_phase_events": float(np.mean([x["ms_total"] for x in per])),
-               "kernels_ms": kms, "batched": batched, "serving": serving,
+               "kernels_ms": kms, "in_place": inplace, "batched": batched, "serving": serving,
                "path": {k: last[k] for k in ("n_heavy", "n_ext", "max_bucket", "n_eq_keys",
                                              "n_level1", "n_segments", "n_fallback", "n_fill",
                                              "n_launches", "sample_size")}}

@@ -235,7 +235,7 @@ struct Plan {
   uint64_t s, tau, seed;
   Chunking c;
   SortLimits lim;
-  uint64_t cap0, cap1, cap_c, cap_r, capj;
+  uint64_t cap0, cap1, cap_c, cap_r, capj, cap_fill;
   uint32_t kf;
   size_t smem_hist, smem_scatter;
   uint32_t l0_scan_tiles;
@@ -342,8 +342,15 @@ static void plan_call(const ls_params* prm, int dt, uint64_t n, uintptr_t addr, 
   P->cap0 = P->n_ext_max + 16;
   P->cap_r = n / (P->lim.c_large + 1) + 16;     // jobs a refinement level can pass on
   P->capj = std::max(P->cap0, P->cap_r);        // jobs of one refinement level
-  P->cap_c = std::max((uint64_t)(P->kf + MAX_HPB) * P->cap0, n / 32 + n / (P->lim.l1_target / 3) + P->capj) + 64;
+  // sub-buckets of one level: level 1 splits at most one job per level-0
+  // bucket into Kf + (its heavy values) sub-buckets; a key-range level at
+  // most n / 32 + n / (l1_target / 3) + its jobs
+  P->cap_c = std::max((uint64_t)(P->kf + MAX_HPB) * (P->f0 + 16),
+                      n / 32 + n / (P->lim.l1_target / 3) + P->capj) + 64;
   P->cap1 = P->cap_c + P->cap0;
+  // fills: the equality slots, and one per homogeneous job of the two
+  // key-range levels
+  P->cap_fill = P->n_ext_max + 2 * P->cap_r + 64;
   const uint64_t M = (uint64_t)P->n_ext_max * G;
   P->l0_scan_tiles = (uint32_t)std::max<uint64_t>(1, (M + SC_TILE - 1) / SC_TILE);
 }
@@ -423,7 +430,7 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->o_offs = c.take<uint64_t>((size_t)P.n_ext_max * P.c.G + 1);
   w->l0scan_bytes = (size_t)P.l0_scan_tiles * 8 + 16;
   w->o_l0scan = c.take<uint8_t>(w->l0scan_bytes);
-  w->o_jobs_fill = c.take<Job>(P.cap1);
+  w->o_jobs_fill = c.take<Job>(P.cap_fill);
   w->o_jobs_s = c.take<Job>(cap_above(P.n, P.lim.c_tiny));
   w->o_jobs_l = c.take<Job>(cap_above(P.n, P.lim.c_mid));
   w->o_jobs_m = c.take<Job>(cap_above(P.n, P.lim.c_small));
@@ -529,7 +536,7 @@ static Bound bind(const Plan& P, const Workspace& w) {
     l.cap = cap;
     return l;
   };
-  b.lists.fill = mk(w.o_jobs_fill, b.counts + 0, P.cap1);
+  b.lists.fill = mk(w.o_jobs_fill, b.counts + 0, P.cap_fill);
   b.lists.sort_s = mk(w.o_jobs_s, b.counts + 1, cap_above(P.n, P.lim.c_tiny));
   b.lists.sort_l = mk(w.o_jobs_l, b.counts + 2, cap_above(P.n, P.lim.c_mid));
   b.lists.sort_m = mk(w.o_jobs_m, b.counts + 7, cap_above(P.n, P.lim.c_small));
@@ -589,7 +596,7 @@ static cudaError_t enqueue_train(const Plan& P, const Bound& b, const void* keys
 
 static Level0Args level0_args(const Plan& P, const Bound& b, const Workspace& w, const void* keys,
                               uint32_t* err) {
-  Level0Args a;
+  Level0Args a{};
   a.keys = keys;
   a.scratch = at<void>(w, w.o_scratch);
   a.c = P.c;
@@ -665,7 +672,7 @@ static cudaError_t enqueue_sort_ip(const Plan& P, const Workspace& w, void* keys
   LS_TRY(fill_enqueue(P.dt, keys, b.lists, nullptr, nullptr, st, d->num_sms));
   mark(&mk, 7, st);
   LS_TRY(buckets_enqueue(P.dt, keys, nullptr, P.n, b.M, b.lists, P.cap1, P.cap1, P.cap1,
-                         b.counts + 8, err, st, d->num_sms, &mk, 8));
+                         b.counts + 8, err, st, d->num_sms, &mk, 8, true));
   LS_TRY(end_call(b.counts, N_COUNTS, o, st));
   mark(&mk, 10, st);
   return cudaSuccess;

@@ -567,7 +567,7 @@ template <int DT>
 static cudaError_t buckets_dt(void* keys, void* scratch, const ModelPtrs& M, const Lists& lists,
                               uint64_t cap_s, uint64_t cap_l, uint64_t cap_fb,
                               unsigned long long* ctrs, uint32_t* err, cudaStream_t st,
-                              int num_sms, const Marks* mk, int mb) {
+                              int num_sms, const Marks* mk, int mb, bool in_place) {
   typedef typename KT<DT>::U U;
   const unsigned gs = (unsigned)std::min<uint64_t>(std::max<uint64_t>(cap_s, 1), 8ull * num_sms);
   const unsigned gl = (unsigned)std::min<uint64_t>(std::max<uint64_t>(cap_l, 1), 2ull * num_sms);
@@ -590,10 +590,10 @@ static cudaError_t buckets_dt(void* keys, void* scratch, const ModelPtrs& M, con
   }
   launch_k(k_bucket_sort<DT, BS_LARGE_T, BS_LARGE_K>, gl, BS_LARGE_T, BucketCfg<DT, BS_LARGE_T, BS_LARGE_K>::SMEM, st, (U*)keys, (const U*)scratch, M, lists.sort_l, ctrs + 1, err);
   mark(mk, mb + 1, st);
-  if (scratch)
+  if (!in_place)
     launch_k(k_fallback<DT>, gf, 512, BucketCfg<DT, 512, 16>::SMEM_FB, st, (U*)keys, (U*)scratch, M,
              lists.fallback, ctrs + 2, err);
-  else  // the in-place variant: no scratch
+  else  // the in-place variant: no scratch, every job in the caller's array
     launch_k(k_ip_fallback<DT>, gf, 512, IpFbCfg<DT>::SMEM, st, (U*)keys, lists.fallback, ctrs + 2, err);
   add_launches(6);
   return cudaGetLastError();
@@ -602,13 +602,13 @@ static cudaError_t buckets_dt(void* keys, void* scratch, const ModelPtrs& M, con
 cudaError_t buckets_enqueue(int dt, void* keys, void* scratch, uint64_t n, const ModelPtrs& M,
                             const Lists& lists, uint64_t cap_s, uint64_t cap_l, uint64_t cap_fb,
                             unsigned long long* ctrs, uint32_t* err, cudaStream_t st,
-                            int num_sms, const Marks* mk, int mb) {
+                            int num_sms, const Marks* mk, int mb, bool in_place) {
   (void)n;
   switch (dt) {
-    case LS_F64: return buckets_dt<LS_F64>(keys, scratch, M, lists, cap_s, cap_l, cap_fb, ctrs, err, st, num_sms, mk, mb);
-    case LS_U64: return buckets_dt<LS_U64>(keys, scratch, M, lists, cap_s, cap_l, cap_fb, ctrs, err, st, num_sms, mk, mb);
-    case LS_F32: return buckets_dt<LS_F32>(keys, scratch, M, lists, cap_s, cap_l, cap_fb, ctrs, err, st, num_sms, mk, mb);
-    case LS_U32: return buckets_dt<LS_U32>(keys, scratch, M, lists, cap_s, cap_l, cap_fb, ctrs, err, st, num_sms, mk, mb);
+    case LS_F64: return buckets_dt<LS_F64>(keys, scratch, M, lists, cap_s, cap_l, cap_fb, ctrs, err, st, num_sms, mk, mb, in_place);
+    case LS_U64: return buckets_dt<LS_U64>(keys, scratch, M, lists, cap_s, cap_l, cap_fb, ctrs, err, st, num_sms, mk, mb, in_place);
+    case LS_F32: return buckets_dt<LS_F32>(keys, scratch, M, lists, cap_s, cap_l, cap_fb, ctrs, err, st, num_sms, mk, mb, in_place);
+    case LS_U32: return buckets_dt<LS_U32>(keys, scratch, M, lists, cap_s, cap_l, cap_fb, ctrs, err, st, num_sms, mk, mb, in_place);
   }
   return cudaErrorInvalidValue;
 }

@@ -1052,7 +1052,7 @@ cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const 
   const JobList outs[3] = {lists.refine2, lists.refine3, lists.fallback};
   // re-splits of what the model left large: the value range first, then the
   // total-order key range (which separates clustered distinct values)
-  LevelArgs lvs[3];
+  LevelArgs lvs[3] = {};
   for (int lv = 0; lv < 3; ++lv) {
     lvs[lv].in = ins[lv];
     lvs[lv].next = outs[lv];

@@ -171,6 +171,6 @@ cudaError_t buckets_enqueue(int dt, void* keys, void* scratch, uint64_t n, const
                             const Lists& lists, uint64_t cap_s, uint64_t cap_l,
                             uint64_t cap_fb, unsigned long long* job_ctrs, uint32_t* err,
                             cudaStream_t st, int num_sms, const Marks* mk = nullptr,
-                            int mbase = 0);
+                            int mbase = 0, bool in_place = false);
 
 }  // namespace ls
