@@ -377,7 +377,7 @@ struct Workspace {
       o_jobs_fb, o_jobs_r2, o_jobs_r3, o_pk, o_sid, o_ccount, o_counts, o_aux, o_tot, o_l1cnt, o_l1off, o_l1cur, o_jmin, o_jmax, o_l1scan,
       o_ubase, o_units;
   // in place
-  size_t o_ip_flags, o_ip_pslots, o_ip_lokeys, o_ip_locnt, o_ip_cntb, o_ip_nbk, o_ip_dsl, o_ip_dend,
+  size_t o_ip_flags, o_ip_tags, o_ip_pslots, o_ip_lokeys, o_ip_locnt, o_ip_cntb, o_ip_nbk, o_ip_dsl, o_ip_dend,
       o_ip_sst, o_ip_pair, o_ip_save, o_ip_ovf;
   size_t tscan_bytes, rs_status_bytes, l0scan_bytes, l1scan_bytes;
   uint64_t cand_cap;
@@ -459,6 +459,7 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
     const uint64_t B = IP_BLOCK_BYTES / P.W;
     const uint64_t blocks = (uint64_t)P.ip_P * P.f0;
     w->o_ip_flags = c.take<uint8_t>((P.n + B - 1) / B + 16);
+    w->o_ip_tags = c.take<uint16_t>((P.n + B - 1) / B + 16);
     w->o_ip_pslots = c.take<uint32_t>(P.ip_P);
     w->o_ip_lokeys = c.take<uint8_t>(blocks * IP_BLOCK_BYTES);
     w->o_ip_locnt = c.take<uint32_t>(blocks);
@@ -624,6 +625,7 @@ static InPlace0 inplace0_of(const Plan& P, const Workspace& w) {
   ip.P = P.ip_P;
   ip.PL = P.ip_PL;
   ip.flags = at<uint8_t>(w, w.o_ip_flags);
+  ip.tags = at<uint16_t>(w, w.o_ip_tags);
   ip.pslots = at<uint32_t>(w, w.o_ip_pslots);
   ip.lo_keys = at<void>(w, w.o_ip_lokeys);
   ip.lo_cnt = at<uint32_t>(w, w.o_ip_locnt);

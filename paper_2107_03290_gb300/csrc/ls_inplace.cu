@@ -150,8 +150,13 @@ k_ip_frag0(Level0Args a, InPlace0 ip, Ip0Layout y) {
       const uint32_t c = s[k];
       const uint32_t pos = ffill[c] + rk[k];
       const uint32_t full = nfull[c] * B;
-      if (pos < full) X[(uint64_t)(slot0[c] + pos / B) * B + pos % B] = u[k];
-      else frag[c * B + (pos - full)] = u[k];
+      if (pos < full) {
+        const uint32_t sl = slot0[c] + pos / B;
+        X[(uint64_t)sl * B + pos % B] = u[k];
+        if (pos % B == B - 1) ip.tags[pb / B + sl] = (uint16_t)c;  // the block's last key
+      } else {
+        frag[c * B + (pos - full)] = u[k];
+      }
     }
     __syncthreads();
     for (uint32_t c = tid; c < f0; c += NT) {
@@ -219,9 +224,10 @@ constexpr int IP0_PERM_THREADS = 256;
 
 // The device Defragment of level 0.  Every slot of the array is one ticket;
 // ticket k goes to the bucket whose slot range holds k, whose read pointer then
-// names the slot actually taken.  A block's bucket is its first key's.
+// names the slot actually taken.  A block's bucket is the tag the flush pass
+// wrote for its slot (read with the block, no model evaluation).
 template <int DT>
-__global__ void __launch_bounds__(IP0_PERM_THREADS)
+__global__ void __launch_bounds__(IP0_PERM_THREADS, 3)
 k_ip_permute0(Level0Args a, InPlace0 ip) {
   pdl_begin();
   typedef typename KT<DT>::U U;
@@ -237,15 +243,18 @@ k_ip_permute0(Level0Args a, InPlace0 ip) {
   const bool partial = (n % B) != 0;
   const uint64_t ks = n / B;
   const uint64_t spp = ip.PL / B;  // slots per piece
-  const DevModel* h = a.M.hdr;
-  const L0Map q{a.M.thr, a.M.cell, a.M.cleaf, h->croot, h->pos_max, f0};
   const unsigned long long lim = spin_limit_of(a.err);
   auto is_full = [&](uint64_t k) {
     const uint64_t pc = k / spp;
     return (k - pc * spp) < (uint64_t)ip.pslots[pc];
   };
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < nslots; g += stride) {
+  // each thread takes a contiguous run of tickets, so that the threads in
+  // flight spread over all buckets' read pointers
+  const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t per = (nslots + nthr - 1) / nthr;
+  const uint64_t g0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) * per;
+  const uint64_t g1 = min(g0 + per, nslots);
+  for (uint64_t g = g0; g < g1; ++g) {
     const uint32_t c = ip_bucket_of_slot(sdsl, f0, (uint32_t)g);
     unsigned long long old = atomicAdd(&ip.pair[c], ~0ull);
     long long w = (long long)(old >> 32), r = (long long)(old & 0xFFFFFFFFull) - 1;
@@ -253,10 +262,13 @@ k_ip_permute0(Level0Args a, InPlace0 ip) {
     const uint64_t slot = (uint64_t)r;
     U H[B];
     const bool full = is_full(slot);
-    if (full) blk_load<U>(H, keys + slot * B);
+    uint32_t hb = 0;
+    if (full) {
+      hb = min((uint32_t)ip.tags[slot], f0 - 1);
+      blk_load<U>(H, keys + slot * B);
+    }
     st_release_u8(&ip.flags[slot], 1u);
     if (!full) continue;
-    uint32_t hb = min(l0_bucket<DT>(H[0], q), f0 - 1);
     while (true) {
       old = atomicAdd(&ip.pair[hb], 1ull << 32);
       w = (long long)(old >> 32);
@@ -270,11 +282,12 @@ k_ip_permute0(Level0Args a, InPlace0 ip) {
       if (w <= r) {  // a slot no reader has taken
         if (is_full(ws)) {
           U H2[B];
+          const uint32_t hb2 = min((uint32_t)ip.tags[ws], f0 - 1);
           blk_load<U>(H2, keys + ws * B);
           blk_store<U>(dst, H);
 #pragma unroll
           for (uint32_t i = 0; i < B; ++i) H[i] = H2[i];
-          hb = min(l0_bucket<DT>(H[0], q), f0 - 1);
+          hb = hb2;
           continue;
         }
         blk_store<U>(dst, H);

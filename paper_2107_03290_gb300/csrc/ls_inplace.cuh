@@ -239,29 +239,32 @@ __device__ void ip_cta_partition(U* X, uint64_t m, uint64_t span, uint32_t f, co
   const uint32_t ks = (uint32_t)(span / B);  // the partial last slot
   for (uint32_t c = tid; c < f; c += NT) dd[c] = (uint32_t)((st[c] + B - 1) / B);
   __syncthreads();
+  // The blocks of step A fill slots [0, nw); a bucket's read pointer starts at
+  // its last slot below nw (slots above hold no block and need no reader: a
+  // writer that reaches one finds it empty).
   bool bad = false;
   for (uint32_t c = tid; c < f; c += NT) {
     const uint32_t D = c + 1 < f ? dd[c + 1] : nslots;
     if (dd[c] + nbk[c] > D || st[c] + cnt[c] > (c + 1 < f ? st[c + 1] : span)) bad = true;
-    pair[c] = ((unsigned long long)dd[c] << 32) | D;
+    pair[c] = ((unsigned long long)dd[c] << 32) | max(dd[c], min(D, nw));
   }
   if (__syncthreads_or(bad)) {  // inconsistent bucket ranges (cannot happen): keys untouched
     if (tid == 0) set_error(err, ERR_BOUNDS);
     return;
   }
-  // ---- B: defragment, in rounds
+  // ---- B: defragment, in rounds; one ticket per slot below nw
   {
     uint32_t tick = tid;
     bool held = false;
     U H[B];
     uint32_t hs = 0;
     while (true) {
-      if (!held && tick < nslots) {
+      if (!held && tick < nw) {
         const uint32_t c = ip_bucket_of_slot(dd, f, tick);
         tick += NT;
         const unsigned long long old = atomicAdd(&pair[c], ~0ull);
         const long long w = (long long)(old >> 32), r = (long long)(old & 0xFFFFFFFFull) - 1;
-        if (r >= w && (uint64_t)r < nw) {
+        if (r >= w) {  // r < nw: a slot holding a block
           blk_load<U>(H, X + (uint64_t)r * B);
           held = true;
           hs = min(sub(H[0]), f - 1);
@@ -284,13 +287,13 @@ __device__ void ip_cta_partition(U* X, uint64_t m, uint64_t span, uint32_t f, co
 #pragma unroll
             for (uint32_t i = 0; i < B; ++i) H[i] = H2[i];
             hs = min(sub(H[0]), f - 1);
-          } else {  // an empty slot, or one a reader emptied in an earlier half-round
+          } else {  // a slot at or above nw, or one a reader emptied in an earlier half-round
             blk_store<U>(dst, H);
             held = false;
           }
         }
       }
-      if (!__syncthreads_or(held || tick < nslots)) break;
+      if (!__syncthreads_or(held || tick < nw)) break;
     }
   }
   // ---- C: cleanup

@@ -111,6 +111,7 @@ struct InPlace0 {
   uint32_t P;                  // pieces (one CTA each in the flush pass)
   uint64_t PL;                 // keys per piece (a multiple of the flush tile)
   uint8_t* flags;              // per block slot: set once a reader has taken its block
+  uint16_t* tags;              // per flushed block slot: its bucket
   uint32_t* pslots;            // per piece: blocks flushed at its front
   void* lo_keys;               // per piece and bucket: leftover keys (one block each)
   uint32_t* lo_cnt;            // per piece and bucket: leftover count
