@@ -441,6 +441,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=2_000_000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=4096, help="arrays of the batched line (0: skip)")
+    ap.add_argument("--latency-steps", type=int, default=50,
+                    help="timed calls of the 1M-key latency case (fan-out 1000, 1000 leaves; 0: skip)")
     ap.add_argument("--inplace-steps", type=int, default=10,
                     help="timed sorts of the workload with LS_FLAG_IN_PLACE (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
@@ -580,6 +582,39 @@ def main():
         cpu = {"value": smp / tc, "unit": "keys/s", "cores": 1, "kind": "oracle",
                "sample": f"first {smp} keys of the workload, one oracle LearnedSort 2.0 call"}
 
+    # the 1M-key latency case with the paper's setting (fan-out 1000, 1000 leaves,
+    # 1% sample; Sec. 6.1), L2-resident: per-call device time, p50 and p99
+    latency = None
+    if args.latency_steps > 0 and rank == 0 and args.workload != "normal_1m_f64":
+        ldt, lkeys = make_workload("normal_1m_f64", 0)
+        lpr = torch.from_numpy(lkeys).cuda()
+        lwk = torch.empty_like(lpr)
+        lprm = ls.default_params(fanout=1000, leaves=1000)
+        for _ in range(5):
+            lwk.copy_(lpr)
+            ls.sort_(lwk, lprm)
+        torch.cuda.synchronize()
+        l_ok = bool(np.array_equal(total_order_keys(lwk.cpu().numpy()),
+                                   np.sort(total_order_keys(lkeys))))
+        lms = []
+        for _ in range(args.latency_steps):
+            lwk.copy_(lpr)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ls.sort_(lwk, lprm)
+            e1.record(stream)
+            e1.synchronize()
+            lms.append(e0.elapsed_time(e1))
+        lwk.copy_(lpr)
+        lst = ls.sort_(lwk, lprm, stats=True)
+        torch.cuda.synchronize()
+        latency = {"workload": "normal_1m_f64", "n": int(lkeys.size), "fanout": 1000, "leaves": 1000,
+                   "p50_ms": float(np.percentile(lms, 50)), "p99_ms": float(np.percentile(lms, 99)),
+                   "mean_ms": float(np.mean(lms)), "steps": args.latency_steps, "exact": l_ok,
+                   "train_ms": lst["ms_train"], "launches": int(lst["n_launches"])}
+        del lpr, lwk
+
     # the in-place variant on the same workload: its own timed sorts (CUDA
     # events around each call), its exactness, and the workspace it allocates
     inplace = None
@@ -645,7 +680,8 @@ def main():
                "ms_p50": float(np.median(step_ms)),
                "ms_min": float(np.min(step_ms)),
                "ms_with_phase_events": float(np.mean([x["ms_total"] for x in per])),
-               "kernels_ms": kms, "in_place": inplace, "batched": batched, "serving": serving,
+               "kernels_ms": kms, "latency": latency, "in_place": inplace, "batched": batched,
+               "serving": serving,
                "path": {k: last[k] for k in ("n_heavy", "n_ext", "max_bucket", "n_eq_keys",
                                              "n_level1", "n_segments", "n_fallback", "n_fill",
                                              "n_launches", "sample_size")}}

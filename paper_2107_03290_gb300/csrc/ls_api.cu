@@ -620,6 +620,12 @@ static Level0Args level0_args(const Plan& P, const Bound& b, const Workspace& w,
   return a;
 }
 
+// The two key-range levels after the model's level 1 run for arrays above 2^22
+// keys; below, a segment the model's split leaves above the in-bucket limit
+// goes straight to the radix fallback (one CTA per segment), and 13 launches
+// that would find no work are not made.
+static bool range_levels(uint64_t n) { return n > (1ull << 22); }
+
 static InPlace0 inplace0_of(const Plan& P, const Workspace& w) {
   InPlace0 ip{};
   ip.P = P.ip_P;
@@ -669,7 +675,7 @@ static cudaError_t enqueue_sort_ip(const Plan& P, const Workspace& w, void* keys
   const InPlace0 ip = inplace0_of(P, w);
   LS_TRY(ip_level0_enqueue(P.dt, a, ip, b.lists, P.lim, st, d->num_sms, &mk, 2));
   LS_TRY(ip_levels_enqueue(P.dt, keys, b.M, b.lists, P.lim, b.l1, P.kf, a.f0kf, a.offs, err, st,
-                           d->num_sms));
+                           d->num_sms, range_levels(P.n)));
   mark(&mk, 6, st);
   LS_TRY(fill_enqueue(P.dt, keys, b.lists, nullptr, nullptr, st, d->num_sms));
   mark(&mk, 7, st);
@@ -699,7 +705,7 @@ static cudaError_t enqueue_sort(const Plan& P, const Workspace& w, void* keys, D
   const Level0Args a = level0_args(P, b, w, keys, err);
   LS_TRY(level0_enqueue(P.dt, a, P.smem_hist, P.smem_scatter, b.lists, P.lim, st, &mk, 2));
   LS_TRY(level1_enqueue(P.dt, keys, a.scratch, P.n, b.M, b.lists, P.lim, b.l1, P.kf, a.f0kf,
-                        a.offs, P.c.G, err, st, d->num_sms));
+                        a.offs, P.c.G, err, st, d->num_sms, range_levels(P.n)));
   mark(&mk, 6, st);
   LS_TRY(fill_enqueue(P.dt, keys, b.lists, nullptr, nullptr, st, d->num_sms));
   mark(&mk, 7, st);

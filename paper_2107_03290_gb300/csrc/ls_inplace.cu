@@ -598,17 +598,19 @@ static cudaError_t ip_level_dt(void* keys, const ModelPtrs& M, const Lists& list
 
 cudaError_t ip_levels_enqueue(int dt, void* keys, const ModelPtrs& M, const Lists& lists,
                               const SortLimits& lim, const Level1Ws& w, uint32_t kf, float f0kf,
-                              const uint64_t* l0offs, uint32_t* err, cudaStream_t st, int num_sms) {
+                              const uint64_t* l0offs, uint32_t* err, cudaStream_t st, int num_sms,
+                              bool range_levels) {
   // as out of place: the model's split, then the value range, then the
   // total-order key range; at most IP_CTA_FMAX sub-buckets per split
   const JobList ins[3] = {lists.refine, lists.refine2, lists.refine3};
-  const JobList outs[3] = {lists.refine2, lists.refine3, lists.fallback};
-  for (int lv = 0; lv < 3; ++lv) {
+  const JobList outs[3] = {range_levels ? lists.refine2 : lists.fallback, lists.refine3,
+                           lists.fallback};
+  for (int lv = 0; lv < (range_levels ? 3 : 1); ++lv) {
     LevelArgs la{};
     la.in = ins[lv];
     la.next = outs[lv];
     la.mode = lv == 0 ? 0 : (lv == 1 ? 2 : 1);
-    la.next_kind = lv == 2 ? JOB_FALLBACK : JOB_REFINE;
+    la.next_kind = (lv == 2 || !range_levels) ? JOB_FALLBACK : JOB_REFINE;
     la.kf = kf;
     la.target = lv == 2 ? 16 : lim.l1_target / 3;
     la.fmax = IP_CTA_FMAX;

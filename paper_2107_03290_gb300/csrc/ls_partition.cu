@@ -1046,10 +1046,12 @@ cudaError_t levels_enqueue(int dt, void* keys, void* scratch, uint64_t n, const 
 cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const ModelPtrs& M,
                            const Lists& lists, const SortLimits& lim, const Level1Ws& w,
                            uint32_t kf, float f0kf, const uint64_t* l0offs, uint32_t l0G,
-                           uint32_t* err, cudaStream_t st, int num_sms) {
-  // level 1 splits by the model; levels 2 and 3 split what it could not by key range
+                           uint32_t* err, cudaStream_t st, int num_sms, bool range_levels) {
+  // level 1 splits by the model; levels 2 and 3 split what it could not by key
+  // range (without them, level 1's leftovers go to the fallback)
   const JobList ins[3] = {lists.refine, lists.refine2, lists.refine3};
-  const JobList outs[3] = {lists.refine2, lists.refine3, lists.fallback};
+  const JobList outs[3] = {range_levels ? lists.refine2 : lists.fallback, lists.refine3,
+                           lists.fallback};
   // re-splits of what the model left large: the value range first, then the
   // total-order key range (which separates clustered distinct values)
   LevelArgs lvs[3] = {};
@@ -1057,7 +1059,7 @@ cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const 
     lvs[lv].in = ins[lv];
     lvs[lv].next = outs[lv];
     lvs[lv].mode = lv == 0 ? 0 : (lv == 1 ? 2 : 1);
-    lvs[lv].next_kind = lv == 2 ? JOB_FALLBACK : JOB_REFINE;
+    lvs[lv].next_kind = (lv == 2 || !range_levels) ? JOB_FALLBACK : JOB_REFINE;
     lvs[lv].kf = kf;
     lvs[lv].target = lv == 2 ? 16 : lim.l1_target / 3;
     lvs[lv].fmax = lv == 2 ? 256 : MAX_F1;
@@ -1065,7 +1067,8 @@ cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const 
     lvs[lv].l0G = l0G;
     lvs[lv].f0kf = f0kf;
   }
-  return levels_enqueue(dt, keys, scratch, n, M, lists, lim, w, lvs, 3, err, st, num_sms);
+  return levels_enqueue(dt, keys, scratch, n, M, lists, lim, w, lvs, range_levels ? 3 : 1, err, st,
+                        num_sms);
 }
 
 cudaError_t launch_classify0(int dt, const Level0Args& a, const Lists& lists, const SortLimits& lim,

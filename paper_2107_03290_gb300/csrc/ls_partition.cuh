@@ -136,7 +136,8 @@ cudaError_t ip_level0_enqueue(int dt, const Level0Args& a, const InPlace0& ip, c
                               const Marks* mk = nullptr, int mbase = 0);
 cudaError_t ip_levels_enqueue(int dt, void* keys, const ModelPtrs& M, const Lists& lists,
                               const SortLimits& lim, const Level1Ws& w, uint32_t kf, float f0kf,
-                              const uint64_t* l0offs, uint32_t* err, cudaStream_t st, int num_sms);
+                              const uint64_t* l0offs, uint32_t* err, cudaStream_t st, int num_sms,
+                              bool range_levels = true);
 
 // Single launches of the level kernels (each counts itself in add_launches).
 cudaError_t launch_classify0(int dt, const Level0Args& a, const Lists& lists, const SortLimits& lim,
@@ -158,7 +159,7 @@ cudaError_t level0_enqueue(int dt, const Level0Args& a, size_t smem_hist, size_t
 cudaError_t level1_enqueue(int dt, void* keys, void* scratch, uint64_t n, const ModelPtrs& M,
                            const Lists& lists, const SortLimits& lim, const Level1Ws& w,
                            uint32_t kf, float f0kf, const uint64_t* l0offs, uint32_t l0G,
-                           uint32_t* err, cudaStream_t st, int num_sms);
+                           uint32_t* err, cudaStream_t st, int num_sms, bool range_levels = true);
 cudaError_t levels_enqueue(int dt, void* keys, void* scratch, uint64_t n, const ModelPtrs& M,
                            const Lists& lists, const SortLimits& lim, const Level1Ws& w,
                            const LevelArgs* lvs, int nlv, uint32_t* err, cudaStream_t st,

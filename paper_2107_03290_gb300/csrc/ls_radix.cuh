@@ -193,15 +193,20 @@ inline size_t rs_status_words(uint64_t m_cap) {
 
 // Enqueue the 8 passes.  Every pass runs (a skipped digit copies), so after 8
 // passes the sorted keys are back in `a`.
+// `zeroed`: the caller has already cleared w.hist (8 * 256 words) and w.status
+// (rs_status_words(m_cap) + 8 words) in stream order (no memsets here then).
 inline cudaError_t rs_sort_enqueue(uint64_t* a, uint64_t* b, uint64_t m_cap, const uint64_t* m_dev,
                                    const uint64_t* off_dev, const RsWork& w, uint32_t* err,
-                                   cudaStream_t st, int num_sms) {
+                                   cudaStream_t st, int num_sms, bool zeroed = false) {
   const uint64_t tiles = (m_cap + RS_TILE - 1) / RS_TILE;
   if (tiles == 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(w.hist, 0, 8 * 256 * sizeof(uint32_t), st);
-  if (e) return e;
-  e = cudaMemsetAsync(w.status, 0, rs_status_words(m_cap) * sizeof(uint32_t) + 8 * sizeof(uint32_t), st);
-  if (e) return e;
+  cudaError_t e = cudaSuccess;
+  if (!zeroed) {
+    e = cudaMemsetAsync(w.hist, 0, 8 * 256 * sizeof(uint32_t), st);
+    if (e) return e;
+    e = cudaMemsetAsync(w.status, 0, rs_status_words(m_cap) * sizeof(uint32_t) + 8 * sizeof(uint32_t), st);
+    if (e) return e;
+  }
   int hb = (int)((m_cap + 4095) / 4096);
   if (hb > 4 * num_sms) hb = 4 * num_sms;
   if (hb < 1) hb = 1;

@@ -869,21 +869,25 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   const bool z_hkey = add(M.hkey, HASH_SIZE * sizeof(uint64_t));
   const bool z_scan = add(W.scan_status, W.scan_status_bytes);
   const bool z_hi = add(W.hi, sizeof(unsigned long long));
+  // the LSD radix sort's digit histograms and look-back words
+  const bool radix = sample_by_radix(KT<DT>::W, s);
+  const bool z_rs = radix && add(W.rs.hist, 8 * 256 * sizeof(uint32_t)) &&
+                    add(W.rs.status, (rs_status_words(s) + 8) * sizeof(uint32_t));
   launch_k(k_train_init, std::max(16, (L + 255) / 256), 256, 0, st, M.hdr, s, M.leaf_beg, M.leaf_end,
            L, W.partials, z, P.cs, P.stall, P.spin_limit);
   const uint64_t stride = std::max<uint64_t>(1, n / s);
+  cudaError_t e = cudaSuccess;
   // the sample sort for large samples of 8-byte keys (its splitters drawn by
   // the sampling kernel), else the LSD radix sort (sample_by_radix)
-  const bool radix = sample_by_radix(KT<DT>::W, s);
   const size_t smem = radix ? 0 : (size_t)SS_CAND * sizeof(uint64_t);
-  cudaError_t e = cudaSuccess;
   if (!radix && (e = cudaFuncSetAttribute(k_sample<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem)))
     return e;
   const int sg = std::max(1, (int)std::min<uint64_t>((s + 1023) / 1024, 2ull * num_sms)) + (radix ? 0 : 1);
   launch_k(k_sample<DT>, sg, 1024, smem, st, keys, n, s, P.seed, make_div64(s), make_div64(stride),
            W.smp_a, radix ? nullptr : W.ss.spl, radix ? nullptr : W.ss.cnt);
-  e = radix ? rs_sort_enqueue(W.smp_a, W.smp_b, s, nullptr, nullptr, W.rs, err, st, num_sms)
+  add_launches(1);
+  e = radix ? rs_sort_enqueue(W.smp_a, W.smp_b, s, nullptr, nullptr, W.rs, err, st, num_sms, z_rs)
             : ss_sort_enqueue(W.smp_a, W.smp_b, s, W.ss, err, st, num_sms, /*splitters_done=*/true);
   if (e) return e;
   if (!z_hi && (e = cudaMemsetAsync(W.hi, 0, sizeof(unsigned long long), st))) return e;
@@ -922,7 +926,7 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
                                         M.heads, M.heavy, W.hlen);
   if (!z_hkey && (e = cudaMemsetAsync(M.hkey, 0, HASH_SIZE * sizeof(uint64_t), st))) return e;
   launch_k(k_heavy_hash<DT>, 1, 1024, 0, st, M.hdr, M.heavy, W.hlen, (unsigned long long*)M.hkey, M.hval);
-  add_launches(21);
+  add_launches(20);
   return cudaGetLastError();
 }
 

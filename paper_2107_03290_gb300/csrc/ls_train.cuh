@@ -10,7 +10,7 @@ namespace ls {
 // first kernel of the training step instead of by separate memsets (a memset
 // between two kernels would also break their dependent-launch overlap).
 // Pointers and sizes are multiples of 4 bytes.
-constexpr int ZERO_REGIONS = 6;
+constexpr int ZERO_REGIONS = 10;
 struct ZeroList {
   void* p[ZERO_REGIONS];
   uint32_t words[ZERO_REGIONS];  // 4-byte words
