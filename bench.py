@@ -49,6 +49,60 @@ def total_order_keys(a: np.ndarray) -> np.ndarray:
     return np.where(sgn, ~u, u | top)
 
 
+def order_keys_torch(torch, t):
+    """The total order as signed 64-bit keys of a CUDA tensor (floats by IEEE
+    totalOrder, unsigned integers by value), for a check by a library sort."""
+    if t.element_size() == 8:
+        u = t.view(torch.int64)
+        if t.dtype == torch.float64:
+            return torch.where(u < 0, u ^ 0x7FFFFFFFFFFFFFFF, u)
+        return u ^ (-(1 << 63))
+    b = t.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    if t.dtype == torch.float32:
+        return torch.where(b >= (1 << 31), (~b) & 0xFFFFFFFF, b | (1 << 31))
+    return b
+
+
+def run_configs(ls, torch, names, steps: int, warmup: int, peak: float):
+    """The other benchmarked single-array workloads, each timed like the main
+    line (CUDA events around every ls_sort call, input restored outside them)
+    and checked element for element against a library sort of its keys."""
+    out = []
+    stream = torch.cuda.current_stream()
+    for name in names:
+        dt, keys = make_workload(name, 0)
+        n, w = keys.size, WIDTH[dt]
+        pristine = torch.from_numpy(keys).cuda()
+        del keys
+        work = torch.empty_like(pristine)
+        prm = ls.default_params(leaves=1000)
+        for _ in range(warmup):
+            work.copy_(pristine)
+            ls.sort_(work, prm)
+        torch.cuda.synchronize()
+        want = torch.sort(order_keys_torch(torch, pristine)).values
+        exact = bool(torch.equal(order_keys_torch(torch, work), want))
+        del want
+        ms = []
+        for _ in range(steps):
+            work.copy_(pristine)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ls.sort_(work, prm)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        m = float(np.mean(ms))
+        out.append({"workload": name, "n": int(n), "dtype": dt, "ms_per_sort": m,
+                    "keys_per_s": n / (m / 1e3), "frac_4nw": 4 * n * w / (m / 1e3) / 1e9 / peak,
+                    "steps": steps, "exact": exact,
+                    "check": "torch.sort of the total-order keys (a library sort), element for element"})
+        del pristine, work
+        torch.cuda.empty_cache()
+    return out
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -441,6 +495,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=2_000_000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=4096, help="arrays of the batched line (0: skip)")
+    ap.add_argument("--configs", default="uniform_200m_u64,gauss_mix_200m_f64,timestamp_200m_u32,exponential_200m_f32",
+                    help="other workloads timed and checked in the same run (empty: none)")
     ap.add_argument("--latency-steps", type=int, default=50,
                     help="timed calls of the 1M-key latency case (fan-out 1000, 1000 leaves; 0: skip)")
     ap.add_argument("--inplace-steps", type=int, default=10,
@@ -653,6 +709,11 @@ def main():
                             "device defragment and cleanup; refinement levels and fallback "
                             "split in place per CTA; no n-key scratch")}
 
+    configs = None
+    if args.configs and rank == 0 and world == 1:
+        names = [c for c in args.configs.split(",") if c and c != args.workload]
+        configs = run_configs(ls, torch, names, steps=10, warmup=3, peak=load_peaks()[0])
+
     batched = None
     if args.batch > 0 and rank == 0:
         batched = run_batched(ls, torch, args.batch, steps=5, warmup=2)
@@ -680,7 +741,8 @@ def main():
                "ms_p50": float(np.median(step_ms)),
                "ms_min": float(np.min(step_ms)),
                "ms_with_phase_events": float(np.mean([x["ms_total"] for x in per])),
-               "kernels_ms": kms, "latency": latency, "in_place": inplace, "batched": batched,
+               "kernels_ms": kms, "latency": latency, "configs": configs, "in_place": inplace,
+               "batched": batched,
                "serving": serving,
                "path": {k: last[k] for k in ("n_heavy", "n_ext", "max_bucket", "n_eq_keys",
                                              "n_level1", "n_segments", "n_fallback", "n_fill",
