@@ -377,8 +377,10 @@ struct Workspace {
       o_jobs_fb, o_jobs_r2, o_jobs_r3, o_pk, o_sid, o_ccount, o_counts, o_aux, o_tot, o_l1cnt, o_l1off, o_l1cur, o_jmin, o_jmax, o_l1scan,
       o_ubase, o_units;
   // in place
-  size_t o_ip_flags, o_ip_tags, o_ip_pslots, o_ip_lokeys, o_ip_locnt, o_ip_cntb, o_ip_nbk, o_ip_dsl, o_ip_dend,
-      o_ip_sst, o_ip_pair, o_ip_save, o_ip_ovf;
+  size_t o_ip_flags, o_ip_tags, o_ip_prank, o_ip_inv, o_ip_pnb, o_ip_hscr, o_ip_hcount, o_ip_pslots,
+      o_ip_lokeys, o_ip_locnt, o_ip_cntb, o_ip_nbk, o_ip_dsl, o_ip_dend, o_ip_sst, o_ip_save, o_ip_ovf,
+      o_ip_starts;
+  uint32_t ip_hcap, ip_scap;
   size_t tscan_bytes, rs_status_bytes, l0scan_bytes, l1scan_bytes;
   uint64_t cand_cap;
 };
@@ -458,8 +460,20 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   if (P.ip) {
     const uint64_t B = IP_BLOCK_BYTES / P.W;
     const uint64_t blocks = (uint64_t)P.ip_P * P.f0;
-    w->o_ip_flags = c.take<uint8_t>((P.n + B - 1) / B + 16);
-    w->o_ip_tags = c.take<uint16_t>((P.n + B - 1) / B + 16);
+    const uint64_t slots = (P.n + B - 1) / B;
+    w->o_ip_flags = c.take<uint8_t>(slots + 16);
+    w->o_ip_tags = c.take<uint16_t>(slots + 16);
+    w->o_ip_prank = c.take<uint32_t>(slots + 16);
+    w->o_ip_inv = c.take<uint32_t>(slots + 16);
+    w->o_ip_pnb = c.take<uint32_t>(blocks);
+    // holes: one slot in 32 on average; room for twice that
+    w->ip_hcap = (uint32_t)(slots / 16 + 1024);
+    w->o_ip_hscr = c.take<uint8_t>((size_t)w->ip_hcap * IP_BLOCK_BYTES);
+    w->o_ip_hcount = c.take<uint32_t>(4);
+    // chain starts: destinations that are holes or held no block (the slots
+    // freed by equality keys among them), at most one per slot
+    w->ip_scap = (uint32_t)(slots + 16);
+    w->o_ip_starts = c.take<uint32_t>(w->ip_scap);
     w->o_ip_pslots = c.take<uint32_t>(P.ip_P);
     w->o_ip_lokeys = c.take<uint8_t>(blocks * IP_BLOCK_BYTES);
     w->o_ip_locnt = c.take<uint32_t>(blocks);
@@ -468,7 +482,6 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
     w->o_ip_dsl = c.take<uint32_t>(P.f0);
     w->o_ip_dend = c.take<uint32_t>(P.f0);
     w->o_ip_sst = c.take<unsigned long long>(P.f0);
-    w->o_ip_pair = c.take<unsigned long long>(P.f0);
     w->o_ip_save = c.take<uint8_t>((size_t)P.f0 * IP_BLOCK_BYTES);
     w->o_ip_ovf = c.take<uint8_t>(IP_BLOCK_BYTES);
   }
@@ -632,6 +645,14 @@ static InPlace0 inplace0_of(const Plan& P, const Workspace& w) {
   ip.PL = P.ip_PL;
   ip.flags = at<uint8_t>(w, w.o_ip_flags);
   ip.tags = at<uint16_t>(w, w.o_ip_tags);
+  ip.prank = at<uint32_t>(w, w.o_ip_prank);
+  ip.inv = at<uint32_t>(w, w.o_ip_inv);
+  ip.pnb = at<uint32_t>(w, w.o_ip_pnb);
+  ip.hscr = at<void>(w, w.o_ip_hscr);
+  ip.hcap = w.ip_hcap;
+  ip.hcount = at<unsigned int>(w, w.o_ip_hcount);
+  ip.starts = at<uint32_t>(w, w.o_ip_starts);
+  ip.scap = w.ip_scap;
   ip.pslots = at<uint32_t>(w, w.o_ip_pslots);
   ip.lo_keys = at<void>(w, w.o_ip_lokeys);
   ip.lo_cnt = at<uint32_t>(w, w.o_ip_locnt);
@@ -640,7 +661,6 @@ static InPlace0 inplace0_of(const Plan& P, const Workspace& w) {
   ip.dsl = at<uint32_t>(w, w.o_ip_dsl);
   ip.dend = at<uint32_t>(w, w.o_ip_dend);
   ip.sst = at<unsigned long long>(w, w.o_ip_sst);
-  ip.pair = at<unsigned long long>(w, w.o_ip_pair);
   ip.save = at<void>(w, w.o_ip_save);
   ip.ovf = at<void>(w, w.o_ip_ovf);
   return ip;

@@ -11,12 +11,18 @@
 //                  piece has already read.  Leftovers go to a small per-piece
 //                  area (P x f0 blocks, independent of n).
 //   k_scan         slot counts -> slot offsets (the level-0 layout).
-//   k_ip_prep0     per bucket: its slot range and write/read pointers.
-//   k_ip_permute0  the device Defragment: every block slot is claimed once,
-//                  by a reader (through its bucket's read pointer) or by a
-//                  writer (through the write pointer of the bucket of the block
-//                  it carries); a writer that lands on a slot a reader took
-//                  waits for that reader's flag (a bounded wait).
+//   k_ip_prep0     per bucket: its slot range; per piece and bucket: where its
+//                  blocks go among the bucket's.
+//   k_ip_inv0      the device Defragment, by known destinations: a block's
+//   k_ip_chain0    destination is its bucket's first slot + the blocks of its
+//   k_ip_cycle0    bucket in earlier pieces + its rank in its piece.  The inverse
+//                  map (who goes where) is built, about one slot in 32 (chosen
+//                  by a hash of the slot) is copied out to a small area, and
+//                  from every free destination (a copied-out or empty slot) one
+//                  thread pulls blocks backwards along the inverse map until it
+//                  meets a copied-out source or a slot nobody needs; the few
+//                  cycles with no copied-out slot are rotated by their smallest
+//                  slot.  No pointer atomics and no waits.
 //   k_ip_save0     the overhang of a bucket's last block into the next
 //                  bucket's head is saved;
 //   k_ip_gaps0     each bucket's head and tail get its leftovers and its
@@ -153,7 +159,10 @@ k_ip_frag0(Level0Args a, InPlace0 ip, Ip0Layout y) {
       if (pos < full) {
         const uint32_t sl = slot0[c] + pos / B;
         X[(uint64_t)sl * B + pos % B] = u[k];
-        if (pos % B == B - 1) ip.tags[pb / B + sl] = (uint16_t)c;  // the block's last key
+        if (pos % B == B - 1) {  // the block's last key: its bucket and rank in the piece
+          ip.tags[pb / B + sl] = (uint16_t)c;
+          ip.prank[pb / B + sl] = nbk[c] - nfull[c] + pos / B;
+        }
       } else {
         frag[c * B + (pos - full)] = u[k];
       }
@@ -177,6 +186,7 @@ k_ip_frag0(Level0Args a, InPlace0 ip, Ip0Layout y) {
   }
   for (uint32_t c = tid; c < f0; c += NT) {
     ip.lo_cnt[(size_t)p * f0 + c] = ffill[c];
+    ip.pnb[(size_t)p * f0 + c] = nbk[c];
     if (kcnt[c]) atomicAdd(&ip.cntb[c], (unsigned long long)kcnt[c]);
     if (nbk[c]) atomicAdd(&ip.nbk[c], nbk[c]);
   }
@@ -184,7 +194,10 @@ k_ip_frag0(Level0Args a, InPlace0 ip, Ip0Layout y) {
     if (ecnt[e]) atomicAdd(&a.hist[e], ecnt[e]);
   if (tid == 0) ip.pslots[p] = *nsl;
   const uint64_t s0 = pb / B, s1 = (pb + m + B - 1) / B;
-  for (uint64_t k = s0 + tid; k < s1; k += NT) ip.flags[k] = 0;
+  for (uint64_t k = s0 + tid; k < s1; k += NT) {
+    ip.flags[k] = 0;
+    ip.inv[k] = IP_NONE;
+  }
 }
 
 // Slot range and pointers of every bucket: bucket b's non-equality keys take
@@ -207,103 +220,179 @@ __global__ void k_ip_prep0(Level0Args a, InPlace0 ip) {
     ip.sst[b] = s;
     ip.dsl[b] = (uint32_t)d;
     ip.dend[b] = (uint32_t)D;
-    ip.pair[b] = (d << 32) | D;  // w = d, r + 1 = D
+    uint32_t run = 0;  // the bucket's blocks in earlier pieces
+    for (uint32_t p = 0; p < ip.P; ++p) {
+      const uint32_t t = ip.pnb[(size_t)p * f0 + b];
+      ip.pnb[(size_t)p * f0 + b] = run;
+      run += t;
+    }
   }
-}
-
-__device__ __forceinline__ uint32_t ld_acquire_u8(const uint8_t* p) {
-  uint16_t v;
-  asm volatile("ld.acquire.gpu.global.u8 %0, [%1];" : "=h"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_u8(uint8_t* p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u8 [%0], %1;" ::"l"(p), "h"((uint16_t)v) : "memory");
+  if (blockIdx.x == 0 && threadIdx.x < 3) ip.hcount[threadIdx.x] = 0u;
 }
 
 constexpr int IP0_PERM_THREADS = 256;
 
-// The device Defragment of level 0.  Every slot of the array is one ticket;
-// ticket k goes to the bucket whose slot range holds k, whose read pointer then
-// names the slot actually taken.  A block's bucket is the tag the flush pass
-// wrote for its slot (read with the block, no model evaluation).
+// About one slot in 32, spread by a multiplicative hash of the slot index (no
+// regular stride for a permutation to line up with): the holes.  A chain runs
+// from a hole to the next one, so the longest chain (which sets the kernel's
+// time) is about 32 ln(#chains) blocks.
+__device__ __forceinline__ bool ip_hole(uint64_t k) {
+  return (((uint32_t)k * 0x9E3779B1u) >> 27) == 0u;
+}
+
+struct Ip0Geo {
+  uint64_t nslots, spp, ks;
+  bool partial;
+  uint32_t f0;
+};
+template <typename U>
+__device__ __forceinline__ Ip0Geo ip0_geo(const Level0Args& a, const InPlace0& ip) {
+  constexpr uint32_t B = IpBlk<U>::B;
+  Ip0Geo g;
+  g.nslots = (a.c.n + B - 1) / B;
+  g.spp = ip.PL / B;
+  g.ks = a.c.n / B;
+  g.partial = (a.c.n % B) != 0;
+  g.f0 = a.f0;
+  return g;
+}
+__device__ __forceinline__ bool ip0_full(const InPlace0& ip, const Ip0Geo& g, uint64_t k) {
+  const uint64_t pc = k / g.spp;
+  return (k - pc * g.spp) < (uint64_t)ip.pslots[pc];
+}
+__device__ __forceinline__ uint64_t ip0_dest(const InPlace0& ip, const Ip0Geo& g, uint64_t k) {
+  const uint32_t c = min((uint32_t)ip.tags[k], g.f0 - 1);
+  return (uint64_t)ip.dsl[c] + ip.pnb[(size_t)(k / g.spp) * g.f0 + c] + ip.prank[k];
+}
+
+// The inverse map, and the hole blocks copied out.
 template <int DT>
-__global__ void __launch_bounds__(IP0_PERM_THREADS, 3)
-k_ip_permute0(Level0Args a, InPlace0 ip) {
+__global__ void __launch_bounds__(IP0_PERM_THREADS) k_ip_inv0(Level0Args a, InPlace0 ip) {
   pdl_begin();
   typedef typename KT<DT>::U U;
   constexpr uint32_t B = IpBlk<U>::B;
-  extern __shared__ uint32_t sdsl[];  // f0 first slots
-  const uint32_t f0 = a.f0;
-  for (uint32_t b = threadIdx.x; b < f0; b += blockDim.x) sdsl[b] = ip.dsl[b];
-  __syncthreads();
   if (call_failed(a.err)) return;
+  const Ip0Geo g = ip0_geo<U>(a, ip);
+  const U* keys = (const U*)a.keys;
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < g.nslots;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    if (!ip0_full(ip, g, k)) continue;
+    const uint32_t c = min((uint32_t)ip.tags[k], g.f0 - 1);
+    const uint64_t d = ip0_dest(ip, g, k);
+    if (d >= (uint64_t)ip.dend[c]) { set_error(a.err, ERR_BOUNDS); continue; }
+    ip.inv[d] = (uint32_t)k;
+    if (ip_hole(k)) {
+      const uint32_t hp = atomicAdd(ip.hcount, 1u);
+      if (hp >= ip.hcap) { set_error(a.err, ERR_BOUNDS); continue; }
+      U H[B];
+      blk_load<U>(H, keys + k * B);
+      blk_store<U>((U*)ip.hscr + (size_t)hp * B, H);
+      ip.prank[k] = hp;
+    }
+  }
+}
+
+// The free destinations (a hole, or a slot that held no block), listed.
+template <int DT>
+__global__ void __launch_bounds__(IP0_PERM_THREADS) k_ip_starts0(Level0Args a, InPlace0 ip) {
+  pdl_begin();
+  typedef typename KT<DT>::U U;
+  if (call_failed(a.err)) return;
+  const Ip0Geo g = ip0_geo<U>(a, ip);
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j0 = blockIdx.x * (uint64_t)blockDim.x; j0 < g.nslots; j0 += stride) {
+    const uint64_t j = j0 + threadIdx.x;
+    const bool st = j < g.nslots && ip.inv[j] != IP_NONE && (!ip0_full(ip, g, j) || ip_hole(j));
+    const unsigned m = __ballot_sync(0xffffffffu, st);
+    uint32_t base = 0;
+    if (lane == 0 && m) base = atomicAdd(&ip.hcount[1], (unsigned)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (st) {
+      const uint32_t pos = base + __popc(m & ((1u << lane) - 1u));
+      if (pos < ip.scap) ip.starts[pos] = (uint32_t)j;
+      else set_error(a.err, ERR_BOUNDS);
+    }
+  }
+}
+
+// From every free destination, pull blocks backwards along the inverse map:
+// each destination is filled once, by the one chain that reaches it, right
+// after that chain has read the block that was there.  Chains are taken from
+// the start list through a counter (32 at a time per warp), so that no thread
+// walks several long ones while others are idle.
+template <int DT>
+__global__ void __launch_bounds__(IP0_PERM_THREADS) k_ip_chain0(Level0Args a, InPlace0 ip) {
+  pdl_begin();
+  typedef typename KT<DT>::U U;
+  constexpr uint32_t B = IpBlk<U>::B;
+  if (call_failed(a.err)) return;
+  const Ip0Geo g = ip0_geo<U>(a, ip);
   U* keys = (U*)a.keys;
-  const uint64_t n = a.c.n;
-  const uint64_t nslots = (n + B - 1) / B;
-  const bool partial = (n % B) != 0;
-  const uint64_t ks = n / B;
-  const uint64_t spp = ip.PL / B;  // slots per piece
-  const unsigned long long lim = spin_limit_of(a.err);
-  auto is_full = [&](uint64_t k) {
-    const uint64_t pc = k / spp;
-    return (k - pc * spp) < (uint64_t)ip.pslots[pc];
-  };
-  // each thread takes a contiguous run of tickets, so that the threads in
-  // flight spread over all buckets' read pointers
-  const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
-  const uint64_t per = (nslots + nthr - 1) / nthr;
-  const uint64_t g0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) * per;
-  const uint64_t g1 = min(g0 + per, nslots);
-  for (uint64_t g = g0; g < g1; ++g) {
-    const uint32_t c = ip_bucket_of_slot(sdsl, f0, (uint32_t)g);
-    unsigned long long old = atomicAdd(&ip.pair[c], ~0ull);
-    long long w = (long long)(old >> 32), r = (long long)(old & 0xFFFFFFFFull) - 1;
-    if (r < w) continue;  // the slots left were taken by writers
-    const uint64_t slot = (uint64_t)r;
-    U H[B];
-    const bool full = is_full(slot);
-    uint32_t hb = 0;
-    if (full) {
-      hb = min((uint32_t)ip.tags[slot], f0 - 1);
-      blk_load<U>(H, keys + slot * B);
+  const uint32_t ns = min(ip.hcount[1], ip.scap);
+  const uint32_t lane = threadIdx.x & 31;
+  while (true) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&ip.hcount[2], 32u);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= ns) break;
+    const uint32_t si = base + lane;
+    if (si >= ns) continue;
+    const uint64_t j = ip.starts[si];
+    uint32_t k = ip.inv[j];
+    uint64_t cur = j;
+    for (uint64_t step = 0; step <= g.nslots; ++step) {
+      U H[B];
+      const bool hole = ip_hole(k);
+      // the next source is read with this block: one round trip per step
+      const uint32_t nxt = hole ? IP_NONE : ip.inv[k];
+      if (hole) blk_load<U>(H, (const U*)ip.hscr + (size_t)ip.prank[k] * B);
+      else blk_load<U>(H, keys + (uint64_t)k * B);
+      blk_store<U>((g.partial && cur == g.ks) ? (U*)ip.ovf : keys + cur * B, H);
+      ip.flags[k] = 1;
+      if (hole || nxt == IP_NONE) break;  // a hole's slot starts a chain of its own
+      cur = k;
+      k = nxt;
     }
-    st_release_u8(&ip.flags[slot], 1u);
-    if (!full) continue;
-    while (true) {
-      old = atomicAdd(&ip.pair[hb], 1ull << 32);
-      w = (long long)(old >> 32);
-      r = (long long)(old & 0xFFFFFFFFull) - 1;
-      if ((uint64_t)w >= (uint64_t)ip.dend[hb]) {
-        set_error(a.err, ERR_BOUNDS);  // more blocks than room (cannot happen)
-        break;
-      }
-      const uint64_t ws = (uint64_t)w;
-      U* dst = (partial && ws == ks) ? (U*)ip.ovf : keys + ws * B;
-      if (w <= r) {  // a slot no reader has taken
-        if (is_full(ws)) {
-          U H2[B];
-          const uint32_t hb2 = min((uint32_t)ip.tags[ws], f0 - 1);
-          blk_load<U>(H2, keys + ws * B);
-          blk_store<U>(dst, H);
+  }
+}
+
+// Blocks on cycles that hold no hole (short ones, in practice) are rotated by
+// the cycle's smallest slot; a block already at its destination stays.
+constexpr uint64_t IP0_CYCLE_LIMIT = 1ull << 20;
+template <int DT>
+__global__ void __launch_bounds__(IP0_PERM_THREADS) k_ip_cycle0(Level0Args a, InPlace0 ip) {
+  pdl_begin();
+  typedef typename KT<DT>::U U;
+  constexpr uint32_t B = IpBlk<U>::B;
+  if (call_failed(a.err)) return;
+  const Ip0Geo g = ip0_geo<U>(a, ip);
+  U* keys = (U*)a.keys;
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < g.nslots;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    if (!ip0_full(ip, g, k) || ip_hole(k) || ip.flags[k]) continue;
+    uint64_t j = ip0_dest(ip, g, k);
+    if (j == k) continue;
+    uint64_t mn = k, steps = 0;
+    while (j != k && steps < IP0_CYCLE_LIMIT) {
+      mn = j < mn ? j : mn;
+      j = ip0_dest(ip, g, j);
+      ++steps;
+    }
+    if (steps >= IP0_CYCLE_LIMIT) { set_error(a.err, ERR_TIMEOUT); continue; }
+    if (mn != k) continue;  // another slot of the cycle rotates it
+    U C[B];
+    blk_load<U>(C, keys + k * B);
+    j = ip0_dest(ip, g, k);
+    while (j != k) {
+      U T[B];
+      blk_load<U>(T, keys + j * B);
+      blk_store<U>(keys + j * B, C);
 #pragma unroll
-          for (uint32_t i = 0; i < B; ++i) H[i] = H2[i];
-          hb = hb2;
-          continue;
-        }
-        blk_store<U>(dst, H);
-        break;
-      }
-      // a slot a reader has taken: its block may still be on the way out
-      unsigned long long spins = 0;
-      bool ok = true;
-      while (ld_acquire_u8(&ip.flags[ws]) == 0u) {
-        if (++spins > lim) { ok = false; break; }
-        __nanosleep(64);
-      }
-      if (!ok) { set_error(a.err, ERR_TIMEOUT); break; }
-      blk_store<U>(dst, H);
-      break;
+      for (uint32_t i = 0; i < B; ++i) C[i] = T[i];
+      j = ip0_dest(ip, g, j);
     }
+    blk_store<U>(keys + k * B, C);
   }
 }
 
@@ -561,13 +650,19 @@ static cudaError_t ip_level0_dt(const Level0Args& a, const InPlace0& ip, const L
            a.err, STALL_L0_SCAN);
   mark(mk, mb + 1, st);
   launch_k(k_ip_prep0<DT>, (a.f0 + 255) / 256, 256, 0, st, a, ip);
-  launch_k(k_ip_permute0<DT>, 8 * num_sms, IP0_PERM_THREADS, (size_t)a.f0 * 4, st, a, ip);
+  const unsigned pg = (unsigned)std::min<uint64_t>(
+      std::max<uint64_t>(1, (a.c.n / IpBlk<typename KT<DT>::U>::B + IP0_PERM_THREADS - 1) / IP0_PERM_THREADS),
+      16ull * num_sms);
+  launch_k(k_ip_inv0<DT>, pg, IP0_PERM_THREADS, 0, st, a, ip);
+  launch_k(k_ip_starts0<DT>, pg, IP0_PERM_THREADS, 0, st, a, ip);
+  launch_k(k_ip_chain0<DT>, 8 * num_sms, IP0_PERM_THREADS, 0, st, a, ip);
+  launch_k(k_ip_cycle0<DT>, pg, IP0_PERM_THREADS, 0, st, a, ip);
   launch_k(k_ip_save0<DT>, (a.f0 + 255) / 256, 256, 0, st, a, ip);
   launch_k(k_ip_gaps0<DT>, a.f0, IP0_GAP_THREADS, 0, st, a, ip);
   mark(mk, mb + 2, st);
   launch_classify0(DT, a, lists, lim, st);
   mark(mk, mb + 3, st);
-  add_launches(6);
+  add_launches(9);
   return cudaGetLastError();
 }
 

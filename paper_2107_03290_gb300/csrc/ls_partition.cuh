@@ -110,8 +110,17 @@ struct Level1Ws {
 struct InPlace0 {
   uint32_t P;                  // pieces (one CTA each in the flush pass)
   uint64_t PL;                 // keys per piece (a multiple of the flush tile)
-  uint8_t* flags;              // per block slot: set once a reader has taken its block
+  uint8_t* flags;              // per block slot: set once its block has been moved
   uint16_t* tags;              // per flushed block slot: its bucket
+  uint32_t* prank;             // per flushed block slot: its rank among its bucket's blocks
+                               // of its piece (a hole's: its place in hscr)
+  uint32_t* inv;               // per slot: the slot whose block goes there (IP_NONE: none)
+  uint32_t* pnb;               // per piece and bucket: blocks flushed, then their prefix
+  void* hscr;                  // the blocks of the hole slots (hcap blocks)
+  uint32_t hcap;
+  unsigned int* hcount;        // [0] holes copied, [1] chain starts, [2] starts taken
+  uint32_t* starts;            // free destinations: where the defragment's chains start
+  uint32_t scap;
   uint32_t* pslots;            // per piece: blocks flushed at its front
   void* lo_keys;               // per piece and bucket: leftover keys (one block each)
   uint32_t* lo_cnt;            // per piece and bucket: leftover count
@@ -120,7 +129,6 @@ struct InPlace0 {
   uint32_t* dsl;               // per bucket: first slot of its range
   uint32_t* dend;              // per bucket: end of its slot range
   unsigned long long* sst;     // per bucket: first position
-  unsigned long long* pair;    // per bucket: write pointer << 32 | (read pointer + 1)
   void* save;                  // per bucket: one block (the overhang into its head)
   void* ovf;                   // one block: the partial last slot of the array
 };

@@ -108,14 +108,14 @@ def test_inplace_fallback_many_bytes():
 @pytest.mark.parametrize("code,dt", [(0, np.float64), (3, np.uint32)])
 def test_inplace_workspace(code, dt):
     """The in-place workspace drops the regular path's n-key scratch and its
-    6 bytes of ids per key (what is left are per-level tables and job lists);
-    the call reports what it allocated."""
+    per-key ids (what is left: per-level tables, job lists and a few bytes per
+    128-byte block); the call reports what it allocated."""
     n = 20_000_000
     w = np.dtype(dt).itemsize
     ip = ls.workspace_bytes(n, code, ip_params())
     reg = ls.workspace_bytes(n, code, ls.default_params())
-    assert reg - ip >= n * (w + 6), (reg, ip)
-    assert ip < reg // 3, (reg, ip)
+    assert reg - ip >= n * (w + 4), (reg, ip)
+    assert ip < reg // 2, (reg, ip)
     keys = lsgen.uniform_u32(n, 5) if dt == np.uint32 else lsgen.normal_f64(n, 5)
     got, st = ip_sort(keys, stats=True)
     assert st["workspace_bytes"] == ip
