@@ -448,7 +448,7 @@ static void layout_ws(const Plan& P, Workspace* w, bool with_scratch) {
   w->o_jobs_r3 = c.take<Job>(P.cap_r);
   w->o_counts = c.take<unsigned long long>(N_COUNTS + 2);  // counters + the call's CallStatus
   w->o_aux = c.take<uint8_t>((P.capj + 1) * 32);
-  w->o_tot = c.take<unsigned long long>(4);
+  w->o_tot = c.take<unsigned long long>(8);
   w->o_l1cnt = c.take<uint32_t>(P.cap_c);
   w->o_l1off = c.take<uint64_t>(P.cap_c + 1);
   w->o_l1cur = c.take<unsigned long long>(P.cap_c);
@@ -694,8 +694,8 @@ static cudaError_t enqueue_sort_ip(const Plan& P, const Workspace& w, void* keys
   a.may_compact = 0;
   const InPlace0 ip = inplace0_of(P, w);
   LS_TRY(ip_level0_enqueue(P.dt, a, ip, b.lists, P.lim, st, d->num_sms, &mk, 2));
-  LS_TRY(ip_levels_enqueue(P.dt, keys, b.M, b.lists, P.lim, b.l1, P.kf, a.f0kf, a.offs, err, st,
-                           d->num_sms, range_levels(P.n)));
+  LS_TRY(ip_levels_enqueue(P.dt, keys, b.M, b.lists, P.lim, b.l1, ip, P.kf, a.f0kf, a.offs, err,
+                           st, d->num_sms, range_levels(P.n)));
   mark(&mk, 6, st);
   LS_TRY(fill_enqueue(P.dt, keys, b.lists, nullptr, nullptr, st, d->num_sms));
   mark(&mk, 7, st);
@@ -981,7 +981,7 @@ ls_status ls::batch_call(void* const* keys, const size_t* n, size_t count, ls_dt
   for (int i = 0; i < 11; ++i) o_list[i] = c.take<Job>(caps[i]);
   const size_t o_counts = c.take<unsigned long long>(N_COUNTS + 2);  // counters + CallStatus
   const size_t o_aux = c.take<uint8_t>((capj + 1) * 32);
-  const size_t o_tot = c.take<unsigned long long>(4);
+  const size_t o_tot = c.take<unsigned long long>(8);
   const size_t o_cnt = c.take<uint32_t>(cap_c);
   const size_t o_off = c.take<uint64_t>(cap_c + 1);
   const size_t o_cur = c.take<unsigned long long>(cap_c);

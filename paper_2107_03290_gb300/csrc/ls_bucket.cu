@@ -496,7 +496,8 @@ k_ip_fallback(typename KT<DT>::U* keys, JobList list, unsigned long long* ctr, u
       const uint64_t diff = s_or ^ s_and;
       if (diff == 0) continue;  // one value: already in order
       const int shift = ((63 - __clzll((long long)diff)) >> 3) << 3;  // top differing byte
-      ip_cta_partition<U, 512, 8>(D, e.m, e.m, 256u, IpDigit<DT>{shift}, IpPrefixStarts{}, sm, err);
+      ip_cta_partition<U, 512, 8, false>(D, e.m, e.m, 256u, IpDigit<DT>{shift}, IpPrefixStarts{}, sm,
+                                         err, IpChainWs{});  // in rounds
       if (threadIdx.x < 256 && pcnt[threadIdx.x] > 1u) {
         const int slot = atomicAdd(&s_top, 1);
         if (slot < STACK) {

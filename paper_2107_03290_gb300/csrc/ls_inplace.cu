@@ -232,14 +232,6 @@ __global__ void k_ip_prep0(Level0Args a, InPlace0 ip) {
 
 constexpr int IP0_PERM_THREADS = 256;
 
-// About one slot in 32, spread by a multiplicative hash of the slot index (no
-// regular stride for a permutation to line up with): the holes.  A chain runs
-// from a hole to the next one, so the longest chain (which sets the kernel's
-// time) is about 32 ln(#chains) blocks.
-__device__ __forceinline__ bool ip_hole(uint64_t k) {
-  return (((uint32_t)k * 0x9E3779B1u) >> 27) == 0u;
-}
-
 struct Ip0Geo {
   uint64_t nslots, spp, ks;
   bool partial;
@@ -580,9 +572,14 @@ size_t ip_cta_smem(int dt) {
 // a job's segment inside its own range (ls_inplace.cuh), by the model (mode 0)
 // or by the job's key range (modes 1 and 2); sub-bucket counts and end
 // positions go to the level's counters for k_l1_classify.
-template <int DT>
+// CHAINS: the jobs whose range is wider than their keys (a level-0 bucket with
+// heavy values: its sub-buckets sit between equality ranges), split with the
+// defragment by known destinations; else the others, in rounds (measured
+// faster there).  Each instantiation takes its jobs from its own counter.
+template <int DT, bool CHAINS>
 __global__ void __launch_bounds__(IPR_THREADS, 1)
-k_ip_refine(typename KT<DT>::U* keys, ModelPtrs M, LevelArgs la, Level1Ws w, uint32_t* err) {
+k_ip_refine(typename KT<DT>::U* keys, ModelPtrs M, LevelArgs la, Level1Ws w, IpChainWs cw,
+            uint32_t* err) {
   pdl_begin();
   typedef typename KT<DT>::U U;
   typedef IpCta<U> Y;
@@ -594,13 +591,15 @@ k_ip_refine(typename KT<DT>::U* keys, ModelPtrs M, LevelArgs la, Level1Ws w, uin
   const unsigned long long* st = (const unsigned long long*)(sm + Y::OFF_ST);
   while (true) {
     __syncthreads();
-    if (threadIdx.x == 0) s_job = call_failed(err) ? ~0ull : atomicAdd(&w.totals[3], 1ull);
+    if (threadIdx.x == 0) s_job = call_failed(err) ? ~0ull : atomicAdd(&w.totals[CHAINS ? 5 : 3], 1ull);
     __syncthreads();
     const unsigned long long j = s_job;
     if (j >= nj) break;
     const Job job = la.in.jobs[j];
     const L1Aux x = aux[j];
+    if ((job.span > job.m) != CHAINS) continue;  // the other instantiation's job
     U* X = job_keys(job, keys) + job.start;
+    cw.seg_pos = job.start;
     if (la.mode && w.jmin[j] == w.jmax[j]) {  // homogeneous: one sub-bucket, filled later
       for (uint32_t c = threadIdx.x; c < x.f1; c += blockDim.x) {
         w.cnt[x.cbase + c] = c == 0 ? (uint32_t)job.m : 0u;
@@ -621,14 +620,14 @@ k_ip_refine(typename KT<DT>::U* keys, ModelPtrs M, LevelArgs la, Level1Ws w, uin
       sub.nh = job.lb;
       if (job.lb) {
         IpHeavyStarts hs{sub.hv, job.lb, la.f0kf, sub.bkf, sub.kf, la.l0offs, h.ext_base, job.start};
-        ip_cta_partition<U, IPR_THREADS, IPR_KPT>(X, job.m, job.span, x.f1, sub, hs, sm, err);
+        ip_cta_partition<U, IPR_THREADS, IPR_KPT, CHAINS>(X, job.m, job.span, x.f1, sub, hs, sm, err, cw);
       } else {
-        ip_cta_partition<U, IPR_THREADS, IPR_KPT>(X, job.m, job.span, x.f1, sub, IpPrefixStarts{}, sm, err);
+        ip_cta_partition<U, IPR_THREADS, IPR_KPT, CHAINS>(X, job.m, job.span, x.f1, sub, IpPrefixStarts{}, sm, err, cw);
       }
     } else {
       IpRangeSub<DT> sub;
       sub.rs = range_split<DT>(w.jmin[j], w.jmax[j], x.f1, la.mode == 2);
-      ip_cta_partition<U, IPR_THREADS, IPR_KPT>(X, job.m, job.span, x.f1, sub, IpPrefixStarts{}, sm, err);
+      ip_cta_partition<U, IPR_THREADS, IPR_KPT, CHAINS>(X, job.m, job.span, x.f1, sub, IpPrefixStarts{}, sm, err, cw);
     }
     for (uint32_t c = threadIdx.x; c < x.f1; c += blockDim.x) {
       w.cnt[x.cbase + c] = cnt[c];
@@ -681,20 +680,34 @@ cudaError_t ip_level0_enqueue(int dt, const Level0Args& a, const InPlace0& ip, c
 template <int DT>
 static cudaError_t ip_level_dt(void* keys, const ModelPtrs& M, const Lists& lists,
                                const LevelArgs& la, const SortLimits& lim, const Level1Ws& w,
-                               uint32_t* err, cudaStream_t st, int num_sms) {
+                               const IpChainWs& cw, uint32_t* err, cudaStream_t st, int num_sms) {
   typedef typename KT<DT>::U U;
   launch_l1_plan(la, lim, w, err, st);
   if (la.mode) launch_l1_minmax(DT, keys, la, w, st, num_sms);
-  launch_k(k_ip_refine<DT>, num_sms, IPR_THREADS, IpCta<U>::SMEM, st, (U*)keys, M, la, w, err);
+  launch_k(k_ip_refine<DT, false>, num_sms, IPR_THREADS, IpCta<U>::SMEM, st, (U*)keys, M, la, w, cw, err);
+  if (la.mode == 0) {  // only the model's level has jobs wider than their keys
+    launch_k(k_ip_refine<DT, true>, num_sms, IPR_THREADS, IpCta<U>::SMEM, st, (U*)keys, M, la, w, cw, err);
+    add_launches(1);
+  }
   launch_l1_classify(DT, lists, la, lim, w, M, err, st, num_sms);
   add_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t ip_levels_enqueue(int dt, void* keys, const ModelPtrs& M, const Lists& lists,
-                              const SortLimits& lim, const Level1Ws& w, uint32_t kf, float f0kf,
-                              const uint64_t* l0offs, uint32_t* err, cudaStream_t st, int num_sms,
-                              bool range_levels) {
+                              const SortLimits& lim, const Level1Ws& w, const InPlace0& ip,
+                              uint32_t kf, float f0kf, const uint64_t* l0offs, uint32_t* err,
+                              cudaStream_t st, int num_sms, bool range_levels) {
+  // the level-0 defragment's per-slot arrays serve every split of the levels;
+  // holes are reserved through the level's counter totals[4] (zeroed by its plan)
+  IpChainWs cw{};
+  cw.tags = ip.tags;
+  cw.prank = ip.prank;
+  cw.inv = ip.inv;
+  cw.moved = ip.flags;
+  cw.hscr = ip.hscr;
+  cw.hctr = w.totals + 4;
+  cw.hcap = ip.hcap;
   // as out of place: the model's split, then the value range, then the
   // total-order key range; at most IP_CTA_FMAX sub-buckets per split
   const JobList ins[3] = {lists.refine, lists.refine2, lists.refine3};
@@ -715,10 +728,10 @@ cudaError_t ip_levels_enqueue(int dt, void* keys, const ModelPtrs& M, const List
     la.in_place = 1;
     cudaError_t e = cudaErrorInvalidValue;
     switch (dt) {
-      case LS_F64: e = ip_level_dt<LS_F64>(keys, M, lists, la, lim, w, err, st, num_sms); break;
-      case LS_U64: e = ip_level_dt<LS_U64>(keys, M, lists, la, lim, w, err, st, num_sms); break;
-      case LS_F32: e = ip_level_dt<LS_F32>(keys, M, lists, la, lim, w, err, st, num_sms); break;
-      case LS_U32: e = ip_level_dt<LS_U32>(keys, M, lists, la, lim, w, err, st, num_sms); break;
+      case LS_F64: e = ip_level_dt<LS_F64>(keys, M, lists, la, lim, w, cw, err, st, num_sms); break;
+      case LS_U64: e = ip_level_dt<LS_U64>(keys, M, lists, la, lim, w, cw, err, st, num_sms); break;
+      case LS_F32: e = ip_level_dt<LS_F32>(keys, M, lists, la, lim, w, cw, err, st, num_sms); break;
+      case LS_U32: e = ip_level_dt<LS_U32>(keys, M, lists, la, lim, w, cw, err, st, num_sms); break;
     }
     if (e) return e;
   }
@@ -730,7 +743,10 @@ cudaError_t ip_configure(int dt, size_t smem0) {
 #define LS_IPCFG(D)                                                                              \
   e = cudaFuncSetAttribute(k_ip_frag0<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem0); \
   if (e) return e;                                                                               \
-  e = cudaFuncSetAttribute(k_ip_refine<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+  e = cudaFuncSetAttribute(k_ip_refine<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                           (int)IpCta<typename KT<D>::U>::SMEM);                                 \
+  if (e) return e;                                                                               \
+  e = cudaFuncSetAttribute(k_ip_refine<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                            (int)IpCta<typename KT<D>::U>::SMEM);
   switch (dt) {
     case LS_F64: LS_IPCFG(LS_F64); break;

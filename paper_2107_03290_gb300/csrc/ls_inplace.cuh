@@ -121,6 +121,29 @@ struct IpPrefixStarts {
   }
 };
 
+// About one slot in 32, spread by a multiplicative hash of the slot index (no
+// regular stride for a permutation to line up with): the holes of the
+// defragment by known destinations.  A chain runs from a hole to the next one,
+// so the longest chain is about 32 ln(#chains) blocks.
+__device__ __forceinline__ bool ip_hole(uint64_t k) {
+  return (((uint32_t)k * 0x9E3779B1u) >> 27) == 0u;
+}
+
+// Per-slot arrays for a CTA-local defragment by known destinations, indexed by
+// the slot's absolute index floor(pos / B) (pos the slot's first key in the
+// array): distinct for the whole slots of disjoint segments (a segment's
+// partial last slot is kept in shared memory instead).
+struct IpChainWs {
+  uint16_t* tags;          // bucket of a flushed block
+  uint32_t* prank;         // its rank among its bucket's blocks (a hole's: its place in hscr)
+  uint32_t* inv;           // the slot whose block goes here
+  uint8_t* moved;
+  void* hscr;              // hole blocks, reserved through hctr
+  unsigned long long* hctr;
+  uint64_t hcap;
+  uint64_t seg_pos;        // the segment's first key, as a position in the array
+};
+
 // Largest c in [0, f) with d[c] <= k (d[0] = 0, non-decreasing).
 __device__ __forceinline__ uint32_t ip_bucket_of_slot(const uint32_t* d, uint32_t f, uint32_t k) {
   uint32_t lo = 0, hi = f - 1;
@@ -133,7 +156,9 @@ __device__ __forceinline__ uint32_t ip_bucket_of_slot(const uint32_t* d, uint32_
 
 // CTA-local in-place split of X[0, m) into f <= IP_CTA_FMAX buckets laid out in
 // [0, span) (steps A, B, C above, with the whole CTA on one segment).  NT
-// threads, KPT keys per thread and tile.  Sub: `uint32_t operator()(U) const`,
+// threads, KPT keys per thread and tile.  CHAINS: step B by known destinations
+// (the per-slot arrays of `cw`, falling back to rounds when the holes do not
+// fit); else in rounds.  Sub: `uint32_t operator()(U) const`,
 // the bucket of a key; Starts: `run<NT>(cnt, st, f, ws)` filling st.  On return
 // (after a barrier) the CTA's shared memory holds cnt (u32 at OFF_U32 + 4*4*F)
 // and st (u64 at OFF_ST) of every bucket.  Phase B runs in rounds: in each
@@ -141,9 +166,10 @@ __device__ __forceinline__ uint32_t ip_bucket_of_slot(const uint32_t* d, uint32_
 // threads holding a block make one write; a slot a reader took is therefore
 // read before any writer of a later round (or of the same round's write half)
 // stores into it, with no flag or wait.
-template <typename U, int NT, int KPT, class Sub, class Starts>
+template <typename U, int NT, int KPT, bool CHAINS, class Sub, class Starts>
 __device__ void ip_cta_partition(U* X, uint64_t m, uint64_t span, uint32_t f, const Sub& sub,
-                                 const Starts& starts, unsigned char* sm, uint32_t* err) {
+                                 const Starts& starts, unsigned char* sm, uint32_t* err,
+                                 const IpChainWs& cw) {
   typedef IpCta<U> Y;
   constexpr uint32_t B = IpBlk<U>::B;
   constexpr uint32_t F = Y::F;
@@ -216,8 +242,17 @@ __device__ void ip_cta_partition(U* X, uint64_t m, uint64_t span, uint32_t f, co
       const uint32_t c = s[k];
       const uint32_t p = ffill[c] + rk[k];
       const uint32_t full = nfull[c] * B;
-      if (p < full) X[(uint64_t)(slot0[c] + p / B) * B + p % B] = u[k];
-      else frag[c * B + (p - full)] = u[k];
+      if (p < full) {
+        const uint32_t sl = slot0[c] + p / B;
+        X[(uint64_t)sl * B + p % B] = u[k];
+        if (CHAINS && p % B == B - 1) {  // the block's last key: its bucket and rank
+          const uint64_t ab = cw.seg_pos / B + sl;
+          cw.tags[ab] = (uint16_t)c;
+          cw.prank[ab] = nbk[c] - nfull[c] + p / B;
+        }
+      } else {
+        frag[c * B + (p - full)] = u[k];
+      }
     }
     __syncthreads();
     for (uint32_t c = tid; c < f; c += NT) {
@@ -252,8 +287,108 @@ __device__ void ip_cta_partition(U* X, uint64_t m, uint64_t span, uint32_t f, co
     if (tid == 0) set_error(err, ERR_BOUNDS);
     return;
   }
-  // ---- B: defragment, in rounds; one ticket per slot below nw
-  {
+  // ---- B by known destinations: a block goes to dd[c] + its rank in bucket c
+  bool chains = CHAINS;
+  if (CHAINS) {
+    uint32_t* sh_u = (uint32_t*)(ws + 37);  // [0] local hole count, [1] the partial slot's source
+    uint32_t* jctr = (uint32_t*)(ws + 39);  // the next slot to look at for a chain start
+    unsigned long long* hbase = ws + 38;
+    uint32_t hn = 0;
+    for (uint32_t k = tid; k < nw; k += NT) hn += ip_hole(cw.seg_pos / B + k) ? 1u : 0u;
+    unsigned long long htot;
+    block_excl_sum<unsigned long long>((unsigned long long)hn, ws, &htot);
+    if (tid == 0) {
+      const unsigned long long b0 = htot ? atomicAdd(cw.hctr, htot) : 0ull;
+      *hbase = (b0 + htot <= cw.hcap) ? b0 : ~0ull;
+      sh_u[0] = 0;
+      sh_u[1] = IP_NONE;
+      *jctr = 0;
+    }
+    __syncthreads();
+    chains = *hbase != ~0ull;
+  }
+  if (CHAINS && chains) {
+    const uint64_t a0 = cw.seg_pos / B;
+    uint32_t* sh_u = (uint32_t*)(ws + 37);
+    uint32_t* jctr = (uint32_t*)(ws + 39);
+    const unsigned long long hb = ws[38];
+    for (uint32_t j = tid; j < nslots; j += NT) {
+      if (partial && j == ks) continue;
+      cw.inv[a0 + j] = IP_NONE;
+      cw.moved[a0 + j] = 0;
+    }
+    __syncthreads();
+    bool oob = false;
+    for (uint32_t k = tid; k < nw; k += NT) {  // the inverse map, the holes copied out
+      const uint32_t c = min((uint32_t)cw.tags[a0 + k], f - 1);
+      const uint32_t d = dd[c] + cw.prank[a0 + k];
+      if (d >= (c + 1 < f ? dd[c + 1] : nslots)) { oob = true; continue; }
+      if (partial && d == ks) sh_u[1] = k;
+      else cw.inv[a0 + d] = k;
+      if (ip_hole(a0 + k)) {
+        const unsigned long long hp = hb + atomicAdd(&sh_u[0], 1u);
+        U H[B];
+        blk_load<U>(H, X + (uint64_t)k * B);
+        blk_store<U>((U*)cw.hscr + hp * B, H);
+        cw.prank[a0 + k] = (uint32_t)hp;
+      }
+    }
+    if (__syncthreads_or(oob)) {  // cannot happen: keys left as they are
+      if (tid == 0) set_error(err, ERR_BOUNDS);
+      return;
+    }
+    // chains from every free destination: a hole, or a slot at or above nw;
+    // slots are taken from a counter, so that the threads stay busy until the
+    // last chains end
+    while (true) {
+      const uint32_t j = atomicAdd(jctr, 1u);
+      if (j >= nslots) break;
+      uint32_t k = (partial && j == ks) ? sh_u[1] : cw.inv[a0 + j];
+      if (k == IP_NONE || (j < nw && !ip_hole(a0 + j))) continue;
+      uint32_t cur = j;
+      for (uint32_t step = 0; step <= nw; ++step) {
+        U H[B];
+        const bool hole = ip_hole(a0 + k);
+        const uint32_t nxt = hole ? IP_NONE : cw.inv[a0 + k];  // k < nw: a whole slot
+        if (hole) blk_load<U>(H, (const U*)cw.hscr + (uint64_t)cw.prank[a0 + k] * B);
+        else blk_load<U>(H, X + (uint64_t)k * B);
+        blk_store<U>((partial && cur == ks) ? ovf : X + (uint64_t)cur * B, H);
+        cw.moved[a0 + k] = 1;
+        if (hole || nxt == IP_NONE) break;
+        cur = k;
+        k = nxt;
+      }
+    }
+    __syncthreads();
+    // cycles without a hole, rotated by their smallest slot
+    for (uint32_t k = tid; k < nw; k += NT) {
+      if (ip_hole(a0 + k) || cw.moved[a0 + k]) continue;
+      auto dest = [&](uint32_t x) {
+        return dd[min((uint32_t)cw.tags[a0 + x], f - 1)] + cw.prank[a0 + x];
+      };
+      uint32_t j = dest(k);
+      if (j == k) continue;
+      uint32_t mn = k, steps = 0;
+      while (j != k && steps <= nw) { mn = min(mn, j); j = dest(j); ++steps; }
+      if (steps > nw) { set_error(err, ERR_BOUNDS); continue; }
+      if (mn != k) continue;
+      U C[B];
+      blk_load<U>(C, X + (uint64_t)k * B);
+      j = dest(k);
+      while (j != k) {
+        U T[B];
+        blk_load<U>(T, X + (uint64_t)j * B);
+        blk_store<U>(X + (uint64_t)j * B, C);
+#pragma unroll
+        for (uint32_t i = 0; i < B; ++i) C[i] = T[i];
+        j = dest(j);
+      }
+      blk_store<U>(X + (uint64_t)k * B, C);
+    }
+    __syncthreads();
+  }
+  // ---- B in rounds (no hole room, or no per-slot arrays); one ticket per slot below nw
+  if (!chains) {
     uint32_t tick = tid;
     bool held = false;
     U H[B];

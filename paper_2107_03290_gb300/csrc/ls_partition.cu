@@ -672,6 +672,8 @@ k_l1_plan(LevelArgs la, SortLimits lim, Level1Ws w, uint32_t* err) {
     w.totals[1] = s_rc > w.cap_c ? w.cap_c : s_rc;
     w.totals[2] = nj;
     w.totals[3] = 0;  // job counter of the in-place split
+    w.totals[4] = 0;  // its hole counter
+    w.totals[5] = 0;  // job counter of its split by known destinations
   }
   // the level's sub-bucket counters (only the ones its jobs use) start at zero
   const uint64_t C = min((uint64_t)s_rc, w.cap_c);

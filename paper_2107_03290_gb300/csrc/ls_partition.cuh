@@ -89,7 +89,9 @@ struct SortLimits {
 
 struct Level1Ws {
   void* aux;             // per refine job: tile base, count base, f1, S, T
-  unsigned long long* totals;   // [0] tiles, [1] counters
+  unsigned long long* totals;   // [0] tiles, [1] counters, [2] jobs; the in-place split's
+                                // [3] job counter (rounds), [4] hole counter, [5] job
+                                // counter (known destinations) (8 words)
   uint32_t* cnt;         // counters (cap_c)
   uint64_t* off;         // cap_c + 1
   unsigned long long* cur;   // cap_c
@@ -143,9 +145,9 @@ cudaError_t ip_level0_enqueue(int dt, const Level0Args& a, const InPlace0& ip, c
                               const SortLimits& lim, cudaStream_t st, int num_sms,
                               const Marks* mk = nullptr, int mbase = 0);
 cudaError_t ip_levels_enqueue(int dt, void* keys, const ModelPtrs& M, const Lists& lists,
-                              const SortLimits& lim, const Level1Ws& w, uint32_t kf, float f0kf,
-                              const uint64_t* l0offs, uint32_t* err, cudaStream_t st, int num_sms,
-                              bool range_levels = true);
+                              const SortLimits& lim, const Level1Ws& w, const InPlace0& ip,
+                              uint32_t kf, float f0kf, const uint64_t* l0offs, uint32_t* err,
+                              cudaStream_t st, int num_sms, bool range_levels = true);
 
 // Single launches of the level kernels (each counts itself in add_launches).
 cudaError_t launch_classify0(int dt, const Level0Args& a, const Lists& lists, const SortLimits& lim,
