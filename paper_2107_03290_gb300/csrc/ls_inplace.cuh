@@ -14,13 +14,20 @@
 //                       bucket) stay in the fragments.
 //   B (defragment)      the blocks are permuted into bucket order: bucket c's
 //                       blocks go to slots [d_c, d_c + nb_c), d_c =
-//                       ceil(st[c] / B).  Each bucket has a write pointer w
-//                       (from d_c up) and a read pointer r (from the end of its
-//                       slot range down), one 64-bit word w << 32 | (r + 1)
-//                       updated by single atomics, so every slot is claimed
-//                       exactly once, by a reader (its block is taken out and
-//                       classified) or by a writer (a block of the bucket is
-//                       put there; a block found there is carried on).
+//                       ceil(st[c] / B).  Two ways:
+//                       * rounds: each bucket has a write pointer w (from d_c
+//                         up) and a read pointer r (from the end of its slot
+//                         range down), one 64-bit word w << 32 | (r + 1)
+//                         updated by single atomics, so every slot is claimed
+//                         exactly once, by a reader (its block is taken out
+//                         and classified) or by a writer (a block of the
+//                         bucket is put there; a block found there is carried
+//                         on);
+//                       * known destinations: step A records each block's
+//                         bucket and rank, so its destination is d_c + rank;
+//                         the blocks are pulled backwards along the inverse
+//                         map in chains that start at free slots (holes copied
+//                         out, or slots that held no block).
 //   C (cleanup)         a bucket's block range starts at a block boundary, so
 //                       its head [st, d*B) and tail [(d+nb)*B, end) are filled
 //                       from its leftovers; its last block may overhang the
