@@ -222,6 +222,35 @@ __device__ __forceinline__ double sample_x(const uint64_t* tk, uint64_t lo, uint
   return KT<DT>::dbl(KT<DT>::from_tk(tk[lo + k]));
 }
 
+// s += (dx, dy, dx dx, dx dy) over points k0, k0 + step, ... < k1, in that
+// order; the loads of four points are issued before their terms are added.
+template <int DT>
+__device__ __forceinline__ void fit_accumulate(const uint64_t* tk, const uint32_t* rank, uint64_t lo,
+                                               uint64_t k0, uint64_t k1, uint64_t step, double xr,
+                                               double yr, double inv_m, double (&s)[4]) {
+  uint64_t k = k0;
+  for (; k + 3 * step < k1; k += 4 * step) {
+    double x[4];
+    uint32_t rk[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      x[q] = sample_x<DT>(tk, lo, k + q * step);
+      rk[q] = rank[k + q * step];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double dx = x[q] - xr;
+      const double dy = (double)rk[q] * inv_m - yr;
+      s[0] += dx; s[1] += dy; s[2] += dx * dx; s[3] += dx * dy;
+    }
+  }
+  for (; k < k1; k += step) {
+    const double dx = sample_x<DT>(tk, lo, k) - xr;
+    const double dy = (double)rank[k] * inv_m - yr;
+    s[0] += dx; s[1] += dy; s[2] += dx * dx; s[3] += dx * dy;
+  }
+}
+
 // Root least squares in one pass, shifted by the first point (x_r, y_r):
 // sums of dx, dy, dx*dx, dx*dy per block (the leaves use the same formulas).
 template <int DT>
@@ -236,11 +265,7 @@ k_fit_sums(const uint64_t* __restrict__ tk, const uint32_t* __restrict__ rank,
   const double inv_m = m ? 1.0 / (double)m : 0.0;
   const double xr = m ? sample_x<DT>(tk, lo, 0) : 0.0, yr = m ? (double)rank[0] * inv_m : 0.0;
   double s[4] = {0, 0, 0, 0};
-  for (uint64_t k = b + threadIdx.x; k < e; k += blockDim.x) {
-    const double dx = sample_x<DT>(tk, lo, k) - xr;
-    const double dy = (double)rank[k] * inv_m - yr;
-    s[0] += dx; s[1] += dy; s[2] += dx * dx; s[3] += dx * dy;
-  }
+  fit_accumulate<DT>(tk, rank, lo, b + threadIdx.x, e, blockDim.x, xr, yr, inv_m, s);
   for (int i = 0; i < 4; ++i) {
     const double t = block_sum_d(s[i], ws);
     if (threadIdx.x == 0) partials[4 * blockIdx.x + i] = t;
@@ -282,33 +307,51 @@ __device__ __forceinline__ int leaf64(const double* r, int L, double x) {
   return (int)floor(w);
 }
 
-// Leaf ranges of the sorted sample: each key's leaf once; the neighbours'
-// leaves come from shared memory (block ends evaluate one extra key).
-constexpr int RT_THREADS = 512;
+// Leaf ranges of the sorted sample.  The root's leaf is non-decreasing in the
+// key (slope >= 0), so leaf l holds the keys from the first with leaf >= l to
+// the first with leaf >= l + 1: one warp per leaf finds both by a 32-way
+// search (each step probes 32 evenly spaced keys of the remaining range), in
+// about log_33(s) dependent steps instead of a pass over every key.  Empty
+// leaves keep [0, 0).
+constexpr int RT_THREADS = 256;
+
+template <int DT>
+__device__ __forceinline__ uint64_t leaf_lower_bound(const uint64_t* tk, uint64_t lo, uint64_t m,
+                                                     const double* r, int L, int t) {
+  const int lane = threadIdx.x & 31;
+  uint64_t a = 0, b = m;  // the answer lies in [a, b]
+  while (b - a > 32) {
+    const uint64_t p = a + ((b - a) * (uint64_t)(lane + 1)) / 33;
+    const bool ge = leaf64(r, L, sample_x<DT>(tk, lo, p)) >= t;
+    const unsigned bal = __ballot_sync(0xffffffffu, ge);
+    const int f = bal ? __ffs(bal) - 1 : 32;
+    const uint64_t pf = __shfl_sync(0xffffffffu, p, f & 31);
+    const uint64_t pp = __shfl_sync(0xffffffffu, p, (f + 31) & 31);
+    const uint64_t na = f == 0 ? a : pp + 1;
+    const uint64_t nb = f == 32 ? b : pf;
+    a = na;
+    b = nb;
+  }
+  const uint64_t q = a + lane;
+  const bool ge = q < b && leaf64(r, L, sample_x<DT>(tk, lo, q)) >= t;
+  const unsigned bal = __ballot_sync(0xffffffffu, ge);
+  return bal ? a + (uint64_t)(__ffs(bal) - 1) : b;
+}
 
 template <int DT>
 __global__ void __launch_bounds__(RT_THREADS)
 k_fit_route(const uint64_t* __restrict__ tk, const DevModel* hdr, int L, uint32_t* leaf_beg,
             uint32_t* leaf_end) {
   pdl_begin();
-  __shared__ int lf[RT_THREADS + 2];
+  const int l = (int)((blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5);
+  if (l >= L) return;  // whole warps
   const uint64_t m = hdr->s_fin, lo = hdr->s_lo;
   const double r[3] = {hdr->root64[0], hdr->root64[1], hdr->root64[2]};
-  for (uint64_t k0 = (uint64_t)blockIdx.x * RT_THREADS; k0 < m; k0 += (uint64_t)gridDim.x * RT_THREADS) {
-    const uint64_t k = k0 + threadIdx.x;
-    lf[threadIdx.x + 1] = k < m ? leaf64(r, L, sample_x<DT>(tk, lo, k)) : -1;
-    if (threadIdx.x == 0) lf[0] = k0 ? leaf64(r, L, sample_x<DT>(tk, lo, k0 - 1)) : -1;
-    if (threadIdx.x == 1) {
-      const uint64_t kn = k0 + RT_THREADS;
-      lf[RT_THREADS + 1] = kn < m ? leaf64(r, L, sample_x<DT>(tk, lo, kn)) : -1;
-    }
-    __syncthreads();
-    if (k < m) {
-      const int l = lf[threadIdx.x + 1];
-      if (lf[threadIdx.x] != l) leaf_beg[l] = (uint32_t)k;
-      if (lf[threadIdx.x + 2] != l) leaf_end[l] = (uint32_t)(k + 1);
-    }
-    __syncthreads();
+  const uint64_t b = leaf_lower_bound<DT>(tk, lo, m, r, L, l);
+  const uint64_t e = leaf_lower_bound<DT>(tk, lo, m, r, L, l + 1);
+  if ((threadIdx.x & 31) == 0 && b < e) {
+    leaf_beg[l] = (uint32_t)b;
+    leaf_end[l] = (uint32_t)e;
   }
 }
 
@@ -367,11 +410,7 @@ k_fit_unit_sums(const uint64_t* __restrict__ tk, const uint32_t* __restrict__ ra
     const uint64_t ke = min((uint64_t)leaf_end[l], kb + FIT_UNIT);
     const double xr = sample_x<DT>(tk, lo, first), yr = (double)rank[first] * inv_m;
     double s[4] = {0, 0, 0, 0};
-    for (uint64_t k = kb + threadIdx.x; k < ke; k += blockDim.x) {
-      const double dx = sample_x<DT>(tk, lo, k) - xr;
-      const double dy = (double)rank[k] * inv_m - yr;
-      s[0] += dx; s[1] += dy; s[2] += dx * dx; s[3] += dx * dy;
-    }
+    fit_accumulate<DT>(tk, rank, lo, kb + threadIdx.x, ke, blockDim.x, xr, yr, inv_m, s);
     for (int i = 0; i < 4; ++i) {
       const double t = block_sum_d(s[i], ws);
       if (threadIdx.x == 0) unit[4 * (size_t)u + i] = t;
@@ -897,8 +936,8 @@ static cudaError_t train_dt(const void* keys_v, uint64_t n, const TrainPlan& P, 
   launch_k(k_first_rank, std::max(1, fr), FR_THREADS, 0, st, W.smp_a, M.hdr, W.rank, s);
   launch_k(k_fit_sums<DT>, FIT_BLOCKS, FIT_THREADS, 0, st, W.smp_a, W.rank, M.hdr, W.partials);
   launch_k(k_fit_root<DT>, 1, 32, 0, st, M.hdr, W.smp_a, W.rank, W.partials, FIT_BLOCKS);
-  const int rb = (int)std::min<uint64_t>((s + RT_THREADS - 1) / RT_THREADS, 8ull * num_sms);
-  launch_k(k_fit_route<DT>, std::max(1, rb), RT_THREADS, 0, st, W.smp_a, M.hdr, L, M.leaf_beg, M.leaf_end);
+  launch_k(k_fit_route<DT>, (32 * L + RT_THREADS - 1) / RT_THREADS, RT_THREADS, 0, st, W.smp_a, M.hdr, L,
+           M.leaf_beg, M.leaf_end);
   launch_k(k_fit_units_plan, 1, 1024, 0, st, M.leaf_beg, M.leaf_end, L, W.ubase, W.utotal,
                                        (uint32_t)(s / FIT_UNIT + L + 2), err);
   {
