@@ -344,6 +344,21 @@ def test_sort_host_e2e():
     assert_same(b, a)
 
 
+@pytest.mark.parametrize("off", [0, 1, 3])
+@pytest.mark.parametrize("dist", ["zipf_lognormal", "uniform_u64", "exponential_f32"])
+def test_sort_host_pinned(dist, off):
+    """ls_sort_host on a pinned host buffer (copied by the SMs over the link),
+    at an offset that leaves it unaligned to 16 bytes."""
+    keys = make(dist, 300_001)
+    dt = torch.from_numpy(keys[:0]).dtype
+    h = torch.empty(keys.size + off, dtype=dt).pin_memory()
+    v = h[off:]
+    v.copy_(torch.from_numpy(keys))
+    code = {8: 0 if keys.dtype == np.float64 else 1, 4: 2 if keys.dtype == np.float32 else 3}[keys.itemsize]
+    ls.sort_host_ptr(v.data_ptr(), keys.size, code)
+    assert_same(v.numpy().copy(), keys)
+
+
 def test_sort_batch():
     arrays = lsgen.batch_arrays(64, seed=6, scale=0.02)
     ts = [torch.from_numpy(a.copy()).cuda() for a in arrays]
