@@ -260,7 +260,9 @@ static void plan_call(const ls_params* prm, int dt, uint64_t n, uintptr_t addr, 
   P->f0 = std::min<uint32_t>(MAX_FANOUT, std::max<uint32_t>(1, p.fanout ? p.fanout : 256));
   // in place: one fragment block per bucket stays in shared memory
   P->ip = (p.flags & LS_FLAG_IN_PLACE) != 0;
-  if (P->ip) P->f0 = std::min<uint32_t>(P->f0, IP_FANOUT_MAX);
+  // (in place, the planner's fan-out is 512: more, smaller segments for the
+  // one-CTA-per-segment level 1, measured 1-5% faster than 256 at 200M keys)
+  if (P->ip) P->f0 = p.fanout ? std::min<uint32_t>(P->f0, IP_FANOUT_MAX) : IP_FANOUT_MAX;
   const uint32_t div = p.sample_div ? p.sample_div : d.sample_div;
   uint64_t s = (n + div - 1) / div;
   s = std::max<uint64_t>(s, std::min<uint64_t>(n, 2ull * P->L));

@@ -562,7 +562,7 @@ struct IpHeavyStarts {
 };
 
 constexpr int IPR_THREADS = 512;
-constexpr int IPR_KPT = 8;
+constexpr int IPR_KPT = 16;
 
 size_t ip_cta_smem(int dt) {
   return (dt == LS_F64 || dt == LS_U64) ? IpCta<uint64_t>::SMEM : IpCta<uint32_t>::SMEM;
