@@ -152,16 +152,16 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
       const uint32_t c = ts.count(t);
       uint32_t* pko = pk + (cb - a0) + (uint64_t)t * H_TILE;
       // every key of the step is classified before any counter is touched, so
-      // that the table lookups of the six keys overlap (a shared-memory
+      // that the table lookups of the thread's keys overlap (a shared-memory
       // atomic between them would order the loads)
-      uint32_t ee[H_KPT], pp[H_KPT];
+      uint32_t ee[HT_KPT], pp[HT_KPT];
 #pragma unroll
-      for (int k = 0; k < H_KPT; ++k) {
+      for (int k = 0; k < HT_KPT; ++k) {
         const uint32_t i = k * H_THREADS + threadIdx.x;
         ee[k] = classify_plain<DT>(tb[i < c ? i : 0], q, a.f0kf, a.kf, &pp[k]);
       }
 #pragma unroll
-      for (int k = 0; k < H_KPT; ++k) {
+      for (int k = 0; k < HT_KPT; ++k) {
         const uint32_t i = k * H_THREADS + threadIdx.x;
         if (i < c) {
           if (ee[k] < next) atomicAdd(&cnt[ee[k]], 1u); else set_error(a.err, ERR_BOUNDS);
@@ -187,13 +187,18 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
   uint32_t* qi = (uint32_t*)(sm + (hashed ? lay.queue : 0) + (size_t)(H_THREADS / 32) * QCAP * sizeof(U)) +
                  (size_t)wid * QCAP;
   const unsigned lt = lanemask_lt();
+  // Chunk-relative 32-bit positions (chunk lengths < 2^32).
+  const U* kc = keys + cb;
+  uint32_t* pkc = pk + (cb - a0);
+  const uint32_t len = (uint32_t)(ce - cb);
+  U* kwc = keys_w + (cb - a0);
   // full lookup of `valid` lanes' keys, then count and place the id
-  auto finish = [&](bool valid, U x, uint64_t i) {
+  auto finish = [&](bool valid, U x, uint32_t ri) {
     uint32_t pv = PK_EQ;
     if (valid) {
       const uint32_t e = classify_key<DT>(x, q, heads, heavy, lay.hs, a.f0kf, a.kf, &pv);
       if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
-      if (!compact) pk[i - a0] = pv;
+      if (!compact) pkc[ri] = pv;
     }
     if (compact) {
       const bool keep = valid && pv != PK_EQ;
@@ -202,30 +207,30 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
       if (lane == 0 && m) wb = atomicAdd(s_cpos, (uint32_t)__popc(m));
       wb = __shfl_sync(0xffffffffu, wb, 0);
       if (keep) {
-        const uint64_t r = wb + __popc(m & lt);
-        keys_w[cb - a0 + r] = x;
-        pk[cb - a0 + r] = pv;
+        const uint32_t r = wb + __popc(m & lt);
+        kwc[r] = x;
+        pkc[r] = pv;
       }
     }
   };
   uint32_t nq = 0;  // the warp's queued misses, carried from step to step
-  for (uint64_t base = cb; base < ce; base += (uint64_t)H_THREADS * H_KPT) {
+  for (uint32_t base = 0; base < len; base += H_THREADS * H_KPT) {
     U u[H_KPT];
 #pragma unroll
     for (int k = 0; k < H_KPT; ++k) {
-      const uint64_t i = base + (uint64_t)k * H_THREADS + threadIdx.x;
-      u[k] = i < ce ? keys[i] : (U)0;
+      const uint32_t ri = base + k * H_THREADS + threadIdx.x;
+      u[k] = ri < len ? kc[ri] : (U)0;
     }
     if (!HASHED) {  // every key takes the full lookup; the chains interleave
       uint32_t pp[H_KPT];
 #pragma unroll
       for (int k = 0; k < H_KPT; ++k) {
-        const uint64_t i = base + (uint64_t)k * H_THREADS + threadIdx.x;
+        const uint32_t ri = base + k * H_THREADS + threadIdx.x;
         pp[k] = PK_EQ;
-        if (i < ce) {
+        if (ri < len) {
           const uint32_t e = classify_key<DT>(u[k], q, heads, heavy, lay.hs, a.f0kf, a.kf, &pp[k]);
           if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
-          if (!compact) pk[i - a0] = pp[k];
+          if (!compact) pkc[ri] = pp[k];
         }
       }
       if (compact) {
@@ -237,9 +242,9 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
           if (lane == 0 && m) wb = atomicAdd(s_cpos, (uint32_t)__popc(m));
           wb = __shfl_sync(0xffffffffu, wb, 0);
           if (keep) {
-            const uint64_t r = wb + __popc(m & lt);
-            keys_w[cb - a0 + r] = u[k];
-            pk[cb - a0 + r] = pp[k];
+            const uint32_t r = wb + __popc(m & lt);
+            kwc[r] = u[k];
+            pkc[r] = pp[k];
           }
         }
       }
@@ -247,9 +252,9 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
     }
 #pragma unroll
     for (int k = 0; k < H_KPT; ++k) {
-      const uint64_t i = base + (uint64_t)k * H_THREADS + threadIdx.x;
+      const uint32_t ri = base + k * H_THREADS + threadIdx.x;
       bool miss = false;
-      if (i < ce) {
+      if (ri < len) {
         // one 8-byte probe: a hit is a heavy value; anything else (including a
         // heavy value that lost its slot) takes the full lookup (free slots
         // hold keys of other slots, so only a table key matches)
@@ -258,7 +263,7 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
         const uint32_t e = hk[slot] == bits ? (uint32_t)hv[slot] : 0xFFFFFFFFu;
         if (e != 0xFFFFFFFFu) {  // equality key: counted, never moved
           if (e < next) atomicAdd(&cnt[e], 1u); else set_error(a.err, ERR_BOUNDS);
-          if (!compact) pk[i - a0] = PK_EQ;
+          if (!compact) pkc[ri] = PK_EQ;
         } else {
           miss = true;
         }
@@ -267,7 +272,7 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
       if (miss) {
         const uint32_t pos = nq + __popc(m & lt);
         qk[pos] = u[k];
-        qi[pos] = (uint32_t)(i - cb);
+        qi[pos] = ri;
       }
       nq += __popc(m);
       if (nq >= 32) {
@@ -280,7 +285,7 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
         __syncwarp();
         if (lane < nq - 32) { qk[lane] = y; qi[lane] = yi; }
         nq -= 32;
-        finish(true, x, cb + xi);
+        finish(true, x, xi);
         __syncwarp();
       }
     }
@@ -288,7 +293,7 @@ __global__ void __launch_bounds__(H_THREADS, 1) k_l0_hist(Level0Args a, L0Layout
   if (nq) {  // the last queued misses
     __syncwarp();
     const bool v = lane < nq;
-    finish(v, v ? qk[lane] : (U)0, cb + (v ? qi[lane] : 0u));
+    finish(v, v ? qk[lane] : (U)0, v ? qi[lane] : 0u);
     __syncwarp();
   }
   __syncthreads();
@@ -749,13 +754,17 @@ k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Mod
   const uint64_t T = w.totals[0], nj = w.totals[2];
   TileWalk tw;
   if (!tile_walk_begin(aux, T, nj, tw)) return;
-  for (; tw.t < tw.t1; ++tw.t) {
+  // The CTA's consecutive tiles of one job form one span, counted into one
+  // shared histogram that is added to the job's counters once.
+  while (tw.t < tw.t1) {
     tile_walk_job(aux, tw);
-    const uint64_t t = tw.t, j = tw.j;
+    const uint64_t j = tw.j;
     const L1Aux x = aux[j];
     const Job job = la.in.jobs[j];
-    const uint64_t off = (t - x.tile_base) * L1_TILE;
-    const uint32_t c = (uint32_t)min((uint64_t)L1_TILE, job.m - off);
+    const uint64_t te = min(tw.t1, tw.nbase);
+    const uint64_t off = (tw.t - x.tile_base) * (uint64_t)L1_TILE;
+    const uint64_t c = min((te - x.tile_base) * (uint64_t)L1_TILE, job.m) - off;
+    tw.t = te;
     const U* src = (job.src ? job_scratch(job, scratch) : job_keys(job, keys)) + job.start + off;
     const uint16_t* ids = w.sid + job.start + off;
     RangeSplit rs{};
@@ -764,33 +773,43 @@ k_l1_hist(const typename KT<DT>::U* keys, const typename KT<DT>::U* scratch, Mod
     __syncthreads();
     if (la.mode) {
       constexpr int U8 = 8;  // independent loads in flight per thread
-      for (uint32_t base = 0; base < c; base += blockDim.x * U8) {
+      for (uint64_t base = 0; base < c; base += blockDim.x * U8) {
         uint32_t sub[U8];
 #pragma unroll
         for (int k = 0; k < U8; ++k) {
-          const uint32_t i = base + k * blockDim.x + threadIdx.x;
+          const uint64_t i = base + k * blockDim.x + threadIdx.x;
           sub[k] = i < c ? range_sub<DT>(src[i], rs) : 0xFFFFFFFFu;
         }
 #pragma unroll
         for (int k = 0; k < U8; ++k)
           if (sub[k] != 0xFFFFFFFFu) atomicAdd(&hc[sub[k]], 1u);
       }
-    } else {  // the ids: 8 per 16-byte load over the tile's aligned body
+    } else {  // the ids: 8 per 16-byte load over the span's aligned body, 4 loads in flight
+      constexpr int UV = 4;
       const uint32_t f1m = x.f1 - 1;
-      const uint32_t h = min(c, (uint32_t)(((16 - ((uintptr_t)ids & 15)) & 15) >> 1));
-      const uint32_t nv = (c - h) >> 3;
+      const uint64_t h = min(c, (uint64_t)((((16 - ((uintptr_t)ids & 15)) & 15)) >> 1));
+      const uint64_t nv = (c - h) >> 3;
       const uint4* v = (const uint4*)(ids + h);
-      for (uint32_t q = threadIdx.x; q < nv; q += blockDim.x) {
-        const uint4 x4 = v[q];
-        const uint32_t wv[4] = {x4.x, x4.y, x4.z, x4.w};
+      for (uint64_t q0 = threadIdx.x; q0 < nv; q0 += UV * blockDim.x) {
+        uint4 x4[UV];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          atomicAdd(&hc[min(wv[r] & 0xFFFFu, f1m)], 1u);
-          atomicAdd(&hc[min(wv[r] >> 16, f1m)], 1u);
+        for (int r = 0; r < UV; ++r) {
+          const uint64_t q = q0 + r * blockDim.x;
+          x4[r] = q < nv ? v[q] : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int r = 0; r < UV; ++r) {
+          if (q0 + r * blockDim.x >= nv) break;
+          const uint32_t wv[4] = {x4[r].x, x4[r].y, x4[r].z, x4[r].w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            atomicAdd(&hc[min(wv[e] & 0xFFFFu, f1m)], 1u);
+            atomicAdd(&hc[min(wv[e] >> 16, f1m)], 1u);
+          }
         }
       }
-      const uint32_t t0 = h + (nv << 3), ne = h + (c - t0);  // head, then tail
-      for (uint32_t i = threadIdx.x; i < ne; i += blockDim.x)
+      const uint64_t t0 = h + (nv << 3), ne = h + (c - t0);  // head, then tail
+      for (uint64_t i = threadIdx.x; i < ne; i += blockDim.x)
         atomicAdd(&hc[min((uint32_t)ids[i < h ? i : t0 + (i - h)], f1m)], 1u);
     }
     __syncthreads();

@@ -27,13 +27,14 @@ inline uint32_t heavy_stride(uint32_t f0, uint32_t next) {
 // shared copy would not fit.
 constexpr size_t L0_SMEM_LIMIT = 227 * 1024;
 constexpr uint32_t NOT_SHARED = 0xFFFFFFFFu;
-constexpr int H_KPT = 6;             // keys per thread and step of K2
+constexpr int H_KPT = 6;             // keys per thread and step of K2's table-lookup loop
+constexpr int HT_KPT = 8;            // keys per thread of K2's TMA tiles (calls without heavy values)
 
 // K2: the lookup tables and the extended-slot counters.
 inline int key_width(int dt) { return (dt == LS_F64 || dt == LS_U64) ? 8 : 4; }
 
 constexpr int QCAP = 64;              // K2 per-warp queue of keys missing the heavy table
-constexpr int H_TILE = H_THREADS * H_KPT;  // K2 keys per TMA tile (calls without heavy values)
+constexpr int H_TILE = H_THREADS * HT_KPT;  // K2 keys per TMA tile (calls without heavy values)
 
 inline L0Layout l0_layout_hist(int W, uint32_t L, uint32_t f0, uint32_t next, uint32_t hmax,
                                bool cleaf_shared = true, bool hashed = true) {
