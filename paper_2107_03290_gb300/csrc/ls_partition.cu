@@ -855,8 +855,9 @@ __global__ void k_l1_cursor(LevelArgs la, Level1Ws w, ModelPtrs M) {
 
 // Moves the keys of every refine job into its sub-buckets, from the buffer
 // the job lives in to the other one (keys <-> scratch), same positions.
+static_assert(MAX_F1 <= 1024 && L1_TILE <= (1 << 22), "sub | rank << 10 packing of the level-1 scatter");
 template <int DT>
-__global__ void __launch_bounds__(L1_THREADS)
+__global__ void __launch_bounds__(L1_THREADS, 3)
 k_l1_scatter(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, uint64_t n, ModelPtrs M,
              LevelArgs la, Level1Ws w, uint32_t* err) {
   pdl_begin();
@@ -888,7 +889,7 @@ k_l1_scatter(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, uint64_t n, 
     for (uint32_t s = threadIdx.x; s <= x.f1; s += blockDim.x) lc[s] = 0;
     __syncthreads();
     U u[KPT];
-    uint32_t sb[KPT], rk[KPT];
+    uint32_t sb[KPT];  // the id, then sub | rank << 10 (sub < MAX_F1 = 2^10, rank < L1_TILE)
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {  // all loads first, then the ranks
       const uint32_t i = k * L1_THREADS + threadIdx.x;
@@ -898,9 +899,10 @@ k_l1_scatter(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, uint64_t n, 
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
       uint32_t sub = sb[k];
-      if (sub != 0xFFFFFFFFu) sub = la.mode ? range_sub<DT>(u[k], rs) : min(sub, x.f1 - 1);
-      sb[k] = sub;
-      rk[k] = sub != 0xFFFFFFFFu ? atomicAdd(&lc[sub], 1u) : 0u;
+      if (sub != 0xFFFFFFFFu) {
+        sub = la.mode ? range_sub<DT>(u[k], rs) : min(sub, x.f1 - 1);
+        sb[k] = sub | (atomicAdd(&lc[sub], 1u) << 10);
+      }
     }
     __syncthreads();
     block_scan_array<uint32_t>(lc, (int)x.f1, ws);
@@ -913,8 +915,9 @@ k_l1_scatter(typename KT<DT>::U* keys, typename KT<DT>::U* scratch, uint64_t n, 
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
       if (sb[k] != 0xFFFFFFFFu) {
-        const uint32_t p = lc[sb[k]] + rk[k];
-        if (p < (uint32_t)L1_TILE) { stage[p] = u[k]; ids[p] = (uint16_t)sb[k]; }
+        const uint32_t s = sb[k] & 1023u;
+        const uint32_t p = lc[s] + (sb[k] >> 10);
+        if (p < (uint32_t)L1_TILE) { stage[p] = u[k]; ids[p] = (uint16_t)s; }
       }
     }
     __syncthreads();
@@ -1040,7 +1043,8 @@ static cudaError_t level_dt(void* keys, void* scratch, uint64_t n, const ModelPt
   launch_k(k_scan<uint32_t>, tiles, SC_THREADS, 0, st, w.cnt, w.off, w.cap_c, &w.totals[1],
            (uint64_t*)w.scan_status, (uint32_t*)((uint64_t*)w.scan_status + tiles), err, 0u);
   launch_k(k_l1_cursor, grid, 256, 0, st, la, w, M);
-  launch_k(k_l1_scatter<DT>, grid, L1_THREADS, l1_scatter_smem(KT<DT>::W), st, (U*)keys, (U*)scratch, n, M, la, w, err);
+  // the scatter holds 3 CTAs per SM: one wave
+  launch_k(k_l1_scatter<DT>, 3 * num_sms, L1_THREADS, l1_scatter_smem(KT<DT>::W), st, (U*)keys, (U*)scratch, n, M, la, w, err);
   launch_k(k_l1_classify<DT>, grid, 256, 0, st, lists, la, lim, w, M, M.L, err);
   add_launches(la.mode ? 7 : 6);
   return cudaGetLastError();
